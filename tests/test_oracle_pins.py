@@ -1,0 +1,435 @@
+"""Pins of the FP64 oracle against things other than itself: closed forms, exact
+roots of unity, brute force, invariants and the numbers Section 3 prints.
+
+Each test names the oracle function it pins and the mistake it would catch."""
+import os
+
+import numpy as np
+import pytest
+
+from oracle import cgh_oracle as O
+from synth import scenes
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+PITCH, LAM = 8e-6, 532e-9
+
+
+def z_for_rate(a):
+    """Distance at which the Fresnel rate p^2/(2 lambda z) equals a."""
+    return PITCH * PITCH / (2.0 * LAM * a)
+
+
+def all_salient_lists(layer, n_layers, levels=3):
+    """LLL + every occupied detail block (threshold -1 at every level)."""
+    return [O.select_blocks(np.zeros_like(layer), layer, n_layers, -1, levels)] + [
+        O.select_blocks(np.zeros_like(layer), layer, n_layers, -1, l) for l in range(1, levels + 1)]
+
+
+def lll_only_lists(layer, n_layers, levels=3):
+    e = np.zeros(0, np.int32)
+    return [O.select_blocks(np.zeros_like(layer), layer, n_layers, -1, levels), e, e, e]
+
+
+def read_haar_examples():
+    out = []
+    lines = [l.strip() for l in open(os.path.join(GOLDEN, "haar_worked_examples.txt"))
+             if l.strip() and not l.startswith("#")]
+    k = 0
+    while k < len(lines):
+        levels = int(lines[k].split()[1])
+        k += 1
+        inp = []
+        while lines[k] != "->":
+            inp.append([int(v) for v in lines[k].split()])
+            k += 1
+        k += 1
+        n = len(inp)
+        exp = [[int(v) for v in lines[k + r].split()] for r in range(n)]
+        k += n
+        out.append((levels, np.array(inp), np.array(exp)))
+    return out
+
+
+# ---------------------------------------------------------------- fringe (P8)
+
+def test_fringe_quarter_rate_is_exact_roots_of_unity():
+    """P8: a_z = 1/4 gives f(d) = 1 for even d and +j for odd d (d^2 = 0 or 1 mod 4).
+    Catches a wrong sign of the phase (would give -j), a missing square, and a lossy
+    range reduction at large offsets."""
+    a = O.fresnel_rate(PITCH, LAM, z_for_rate(0.25))
+    d = np.arange(-4096, 4097)
+    f = O.point_fringe_1d(d, a)
+    exp = np.where(d % 2 == 0, 1.0 + 0j, 1j)
+    assert np.max(np.abs(f - exp)) < 1e-8
+
+
+def test_fringe_eighth_rate():
+    """P8: a_z = 1/8: d = 0 mod 4 -> 1, d = 2 mod 4 -> -1, d odd -> exp(j pi/4)."""
+    a = O.fresnel_rate(PITCH, LAM, z_for_rate(0.125))
+    d = np.arange(-4096, 4097)
+    f = O.point_fringe_1d(d, a)
+    exp = np.where(d % 4 == 0, 1.0 + 0j, np.where(d % 4 == 2, -1.0 + 0j, np.exp(1j * np.pi / 4)))
+    assert np.max(np.abs(f - exp)) < 1e-8
+
+
+def test_fringe_unit_modulus_and_even():
+    a = O.fresnel_rate(PITCH, LAM, 0.1)
+    d = np.arange(0, 3000)
+    f = O.point_fringe_1d(d, a)
+    assert np.allclose(np.abs(f), 1.0, atol=1e-14)
+    assert np.allclose(f, O.point_fringe_1d(-d, a), atol=0)
+
+
+def test_fresnel_rate_value():
+    """a_z = p^2 / (2 lambda z): at p = 8 um, lambda = 532 nm, z = 0.1 m the
+    paraxial phase pi (d p)^2/(lambda z) is 2 pi * 6.0150e-4 * d^2."""
+    a = O.fresnel_rate(PITCH, LAM, 0.1)
+    assert abs(a - 6.4e-11 / (2 * 532e-9 * 0.1)) < 1e-18
+    assert abs(a - 6.015037593984962e-4) < 1e-15
+
+
+# ---------------------------------------------------------------- Haar (P3)
+
+def test_haar_worked_examples():
+    """Hand-derived examples (tests/golden): catches swapped X/Y bands, a wrong
+    sign in D and a wrong Mallat quadrant."""
+    for levels, inp, exp in read_haar_examples():
+        got = O.haar_forward(inp, levels)
+        assert np.array_equal(got, exp), (levels, got, exp)
+
+
+def test_haar_perfect_reconstruction_all_binary_cells():
+    """P3 brute force: every 2x2 cell with values in {0, 255} (16 cells) and every
+    4x4 ... 8x8 tiling of them inverts exactly."""
+    for bits in range(16):
+        v = [(bits >> k) & 1 for k in range(4)]
+        A = 255 * np.array([[v[0], v[1]], [v[2], v[3]]])
+        C = O.haar_forward(A, 1)
+        assert np.array_equal(O.haar_inverse(C, 1), A)
+    rng = np.random.default_rng(3)
+    for _ in range(20):
+        A = 255 * rng.integers(0, 2, size=(8, 8))
+        assert np.array_equal(O.haar_inverse(O.haar_forward(A, 3), 3), A)
+
+
+def test_haar_perfect_reconstruction_random_and_scaled():
+    rng = np.random.default_rng(0)
+    A = rng.integers(0, 256, size=(32, 48))
+    C = O.haar_forward(A, 3)
+    assert np.array_equal(O.haar_inverse(C, 3), A)
+    keep = {l: np.ones((32 >> l, 48 >> l), bool) for l in (1, 2, 3)}
+    assert np.array_equal(O.haar_synthesis_scaled(C, keep, 3), 64 * A)
+    assert np.allclose(O.haar_synthesis_real(O.haar_forward_real(A, 3), keep, 3), A)
+
+
+def test_haar_ranges():
+    """LL3 of an 8x8 block is at most 64*255 = 16320; |detail| at level 3 at most 32*255."""
+    A = np.full((8, 8), 255)
+    C = O.haar_forward(A, 3)
+    assert C[0, 0] == 16320
+    A = np.zeros((8, 8), int)
+    A[:, :4] = 255
+    C = O.haar_forward(A, 3)
+    assert C[0, 1] == 8160  # X3 = (left half) - (right half) = 32 * 255
+
+
+def test_haar_lowpass_only_gives_block_means():
+    """Dropping every detail gives the 8x8 block means (times 64 exactly)."""
+    rng = np.random.default_rng(1)
+    A = rng.integers(0, 256, size=(16, 24))
+    C = O.haar_forward(A, 3)
+    keep = {l: np.zeros((16 >> l, 24 >> l), bool) for l in (1, 2, 3)}
+    V = O.haar_synthesis_scaled(C, keep, 3)
+    means = A.reshape(2, 8, 3, 8).sum(axis=(1, 3))
+    assert np.array_equal(V, np.kron(means, np.ones((8, 8), int)))
+
+
+# ---------------------------------------------------------------- selection
+
+def brute_select(sal, layer, n_layers, threshold, level):
+    """Pixel-by-pixel scan (no reshapes): independent of the oracle's block max."""
+    k = 1 << level
+    h, w = sal.shape
+    out = []
+    for z in range(n_layers):
+        for by in range(h // k):
+            for bx in range(w // k):
+                occ = False
+                mx = -1
+                for y in range(by * k, by * k + k):
+                    for x in range(bx * k, bx * k + k):
+                        occ = occ or layer[y, x] == z
+                        mx = max(mx, int(sal[y, x]))
+                if occ and (threshold < 0 or mx > threshold):
+                    out.append(z * (1 << 24) + by * 4096 + bx)
+    return out
+
+
+def test_select_blocks_brute_force():
+    rng = np.random.default_rng(5)
+    sal = rng.integers(0, 256, size=(16, 24)).astype(np.uint8)
+    layer = rng.integers(0, 3, size=(16, 24)).astype(np.uint8)
+    layer[:8, :8] = 0  # a block owned by a single layer
+    for level in (1, 2, 3):
+        for t in (-1, 0, 127, 200, 255):
+            got = O.select_blocks(sal, layer, 3, t, level).tolist()
+            assert got == brute_select(sal, layer, 3, t, level), (level, t)
+
+
+def test_select_threshold_is_strict():
+    sal = np.full((8, 8), 127, np.uint8)
+    layer = np.zeros((8, 8), np.uint8)
+    assert O.select_blocks(sal, layer, 1, 127, 3).size == 0
+    assert O.select_blocks(sal, layer, 1, 126, 3).size == 1
+
+
+def test_pack_roundtrip():
+    for z, by, bx in ((0, 0, 0), (31, 4095, 4095), (7, 12, 345)):
+        assert O.unpack_entry(O.pack_entry(z, by, bx)) == (z, by, bx)
+
+
+def test_operator_counts_of_section_3():
+    """P6: at 256x256 the LLL needs 1024 operators and the point-wise hologram
+    65536 (values printed in Section 3, tests/golden/operator_counts.txt); with every
+    detail block selected the detail-basis term count equals the pixel count."""
+    vals = {}
+    for l in open(os.path.join(GOLDEN, "operator_counts.txt")):
+        if l.strip() and not l.startswith("#"):
+            k, v = l.split()
+            vals[k] = int(v)
+    n = vals["object_edge"]
+    layer = np.zeros((n, n), np.uint8)
+    lists = all_salient_lists(layer, 1)
+    assert len(lists[0]) == vals["lll_operators"]
+    assert n * n == vals["pointwise_operators"]
+    assert O.detail_term_count(lists) == vals["pointwise_operators"]
+
+
+# ---------------------------------------------------------------- holograms
+
+def tiny_geom(n=8, s=4, n_layers=1, a=None, z=None):
+    if z is None:
+        z = [z_for_rate(a)] * n_layers if a is not None else np.linspace(0.001, 0.0015, n_layers)
+    return O.Geometry((n, n), (n * s, n * s), PITCH, LAM, z)
+
+
+def test_single_point_closed_form_quarter_rate():
+    """P1: one pixel of value v, everything salient, a = 1/4: H(m, n) = v * j^(odd(dm)
+    + odd(dn)) with dm = m - s i, dn = n - s j.  Catches a wrong stride, a transposed
+    offset, a dropped residual level and a wrong Haar scale."""
+    n, s = 16, 4
+    g = tiny_geom(n, s, 1, a=0.25)
+    for (i, j, v) in ((0, 0, 255), (5, 11, 17), (15, 3, 200)):
+        I = np.zeros((n, n), np.int64)
+        I[i, j] = v
+        layer = np.zeros((n, n), np.uint8)
+        H = O.progressive_hologram(I, layer, all_salient_lists(layer, 1), g)
+        m = np.arange(n * s)[:, None] - s * i
+        q = np.arange(n * s)[None, :] - s * j
+        exp = v * (1j ** ((m % 2) + (q % 2)))
+        assert np.max(np.abs(H - exp)) < 1e-7 * v
+
+
+def test_single_point_closed_form_general_rate():
+    """P1 at a generic rate: H(s i + dm, s j + dn) = v exp(j pi p^2 (dm^2+dn^2)/(lambda z))
+    checked at a few offsets from the physical formula in radians."""
+    n, s = 16, 2
+    z = 0.0123
+    g = O.Geometry((n, n), (n * s, n * s), PITCH, LAM, [z])
+    I = np.zeros((n, n), np.int64)
+    I[6, 9] = 100
+    layer = np.zeros((n, n), np.uint8)
+    H = O.progressive_hologram(I, layer, all_salient_lists(layer, 1), g)
+    for (dm, dn) in ((0, 0), (1, 0), (0, 3), (-7, 5), (13, -11)):
+        phase = np.pi * ((dm * PITCH) ** 2 + (dn * PITCH) ** 2) / (LAM * z)
+        assert abs(H[12 + dm, 18 + dn] - 100 * np.exp(1j * phase)) < 1e-9
+
+
+def test_linearity():
+    """P2: H(alpha A + beta B) = alpha H(A) + beta H(B) with the same masks."""
+    n = 16
+    rng = np.random.default_rng(7)
+    g = tiny_geom(n, 2, 2)
+    layer = rng.integers(0, 2, size=(n, n)).astype(np.uint8)
+    sal = rng.integers(0, 256, size=(n, n)).astype(np.uint8)
+    lists = O.progressive_lists(sal, layer, 2, scenes.THRESHOLDS_U8)
+    A = rng.integers(0, 100, size=(n, n))
+    B = rng.integers(0, 100, size=(n, n))
+    HA = O.progressive_hologram(A, layer, lists, g)
+    HB = O.progressive_hologram(B, layer, lists, g)
+    HAB = O.progressive_hologram(2 * A + 3 * B, layer, lists, g)
+    assert O.rel_l2(HAB, 2 * HA + 3 * HB) < 1e-12
+
+
+def test_all_salient_equals_pointwise():
+    """P4a: with every detail block kept the progressive hologram equals the plain
+    point-wise hologram of the object (the basis is complete)."""
+    n = 16
+    sc = scenes.random_scene(11, n, 2 * n, 3)
+    g = O.geometry_of(sc)
+    lists = all_salient_lists(sc["layer"], 3)
+    H = O.progressive_hologram(sc["intensity"], sc["layer"], lists, g)
+    planes = O.object_planes(sc["intensity"], sc["layer"], 3)
+    Href = O.pointwise_hologram_direct(planes, g)
+    assert O.rel_l2(H, Href) < 1e-11
+
+
+def test_empty_mask_equals_block_mean_image():
+    """P4b: with no detail block selected the hologram equals the point-wise hologram
+    of the per-layer 8x8 block-mean image."""
+    n = 16
+    sc = scenes.random_scene(12, n, 2 * n, 2)
+    g = O.geometry_of(sc)
+    lists = lll_only_lists(sc["layer"], 2)
+    H = O.progressive_hologram(sc["intensity"], sc["layer"], lists, g)
+    planes = O.object_planes(sc["intensity"], sc["layer"], 2).astype(np.float64)
+    means = planes.reshape(2, 2, 8, 2, 8).mean(axis=(2, 4))
+    blocky = np.stack([np.kron(means[z], np.ones((8, 8))) for z in range(2)])
+    Href = O.pointwise_hologram_direct(blocky, g)
+    assert O.rel_l2(H, Href) < 1e-11
+
+
+def test_arbitrary_mask_residual_form_equals_pointwise_of_progressive_object():
+    """P5: the residual-map form (block fringes per level) equals the point-wise
+    hologram of the progressively reconstructed object (two independent paths)."""
+    n = 32
+    sc = scenes.random_scene(13, n, 2 * n, 3, graded=True)
+    g = O.geometry_of(sc)
+    lists = O.progressive_lists(sc["saliency"], sc["layer"], 3, scenes.THRESHOLDS_U8)
+    assert all(len(x) for x in lists)  # every level has work
+    H = O.progressive_hologram(sc["intensity"], sc["layer"], lists, g)
+    Ahat = O.progressive_object(sc["intensity"], sc["layer"], lists, 3) / 64.0
+    Href = O.pointwise_hologram_separable(Ahat, g)
+    assert O.rel_l2(H, Href) < 1e-11
+
+
+def test_progressive_object_extremes():
+    rng = np.random.default_rng(2)
+    I = rng.integers(0, 256, size=(16, 16))
+    layer = np.zeros((16, 16), np.uint8)
+    full = O.progressive_object(I, layer, all_salient_lists(layer, 1), 1)
+    assert np.array_equal(full[0], 64 * I)
+    none = O.progressive_object(I, layer, lll_only_lists(layer, 1), 1)
+    means = I.reshape(2, 8, 2, 8).sum(axis=(1, 3))
+    assert np.array_equal(none[0], np.kron(means, np.ones((8, 8), int)))
+
+
+def test_direct_equals_separable():
+    """P7: brute-force 2-D sum (full squared distance) equals E A E^T (factorised)."""
+    rng = np.random.default_rng(8)
+    g = tiny_geom(12, 3, 2)
+    planes = rng.uniform(-1, 1, size=(2, 12, 12))
+    Hd = O.pointwise_hologram_direct(planes, g)
+    Hs = O.pointwise_hologram_separable(planes, g)
+    assert O.rel_l2(Hs, Hd) < 1e-12
+
+
+def test_direct_sampled_pixels():
+    rng = np.random.default_rng(9)
+    g = tiny_geom(8, 4, 1)
+    planes = rng.uniform(0, 1, size=(1, 8, 8))
+    Hs = O.pointwise_hologram_separable(planes, g)
+    mm = np.array([0, 5, 31, 17])
+    nn = np.array([3, 0, 31, 22])
+    Hp = O.pointwise_hologram_direct(planes, g, (mm, nn))
+    assert np.allclose(Hp, Hs[mm, nn], atol=1e-12)
+
+
+# ---------------------------------------------------------------- reconstruction / adjoint
+
+def test_backprop_of_single_point_peaks_at_point():
+    """The back-propagated field of one point's own hologram equals v * Nh^2 at that
+    point (every hologram pixel adds |f|^2 = 1)."""
+    n, s = 8, 4
+    g = tiny_geom(n, s, 1)
+    planes = np.zeros((1, n, n))
+    planes[0, 3, 5] = 2.0
+    H = O.pointwise_hologram_separable(planes, g)
+    R = O.reconstruct_fields(H, g)
+    assert abs(R[0, 3, 5] - 2.0 * (n * s) ** 2) < 1e-8
+
+
+def test_adjoint_dot_product():
+    """P9: <F(I), G> = <I, F^*(G)> for the real-input progressive operator."""
+    n = 16
+    rng = np.random.default_rng(21)
+    sc = scenes.random_scene(21, n, 2 * n, 2, graded=True)
+    g = O.geometry_of(sc)
+    lists = O.progressive_lists(sc["saliency"], sc["layer"], 2, scenes.THRESHOLDS_U8)
+    I = rng.integers(0, 256, size=(n, n))
+    G = rng.normal(size=(2 * n, 2 * n)) + 1j * rng.normal(size=(2 * n, 2 * n))
+    FI = O.progressive_hologram(I, sc["layer"], lists, g)
+    lhs = np.real(np.vdot(FI, G))
+    rhs = float(np.sum(I * O.progressive_adjoint(G, sc["layer"], lists, g)))
+    assert abs(lhs - rhs) <= 1e-10 * max(1.0, abs(lhs))
+
+
+def test_reconstruct_is_adjoint_of_pointwise():
+    rng = np.random.default_rng(22)
+    g = tiny_geom(8, 2, 2)
+    planes = rng.normal(size=(2, 8, 8))
+    G = rng.normal(size=(16, 16)) + 1j * rng.normal(size=(16, 16))
+    lhs = np.real(np.vdot(O.pointwise_hologram_separable(planes, g), G))
+    R = O.reconstruct_fields(G, g)
+    rhs = float(np.sum(planes * np.real(R)))
+    assert abs(lhs - rhs) <= 1e-10 * abs(lhs)
+
+
+# ---------------------------------------------------------------- SSIM (P10)
+
+def brute_ssim(x, y, win=11, sigma=1.5, c1=1e-4, c2=9e-4):
+    t = np.arange(win) - (win - 1) / 2.0
+    w = np.exp(-(t[:, None] ** 2 + t[None, :] ** 2) / (2 * sigma * sigma))
+    w /= w.sum()
+    vals = []
+    for r in range(x.shape[0] - win + 1):
+        for c in range(x.shape[1] - win + 1):
+            px, py = x[r:r + win, c:c + win], y[r:r + win, c:c + win]
+            mx, my = np.sum(w * px), np.sum(w * py)
+            vx = np.sum(w * (px - mx) ** 2)
+            vy = np.sum(w * (py - my) ** 2)
+            cxy = np.sum(w * (px - mx) * (py - my))
+            vals.append((2 * mx * my + c1) * (2 * cxy + c2) / ((mx * mx + my * my + c1) * (vx + vy + c2)))
+    return float(np.mean(vals))
+
+
+def test_ssim_identity_and_brute_force():
+    rng = np.random.default_rng(4)
+    x = rng.uniform(0, 1, size=(20, 18))
+    y = np.clip(x + rng.normal(0, 0.1, size=x.shape), 0, 1)
+    assert abs(O.ssim(x, x) - 1.0) < 1e-12
+    assert abs(O.ssim(x, y) - brute_ssim(x, y)) < 1e-10
+    assert O.ssim(x, y) < 0.99
+
+
+def test_all_salient_reconstruction_ssim_is_one():
+    """P10: all-salient progressive reconstruction has SSIM 1 against the point-wise one."""
+    n = 32
+    sc = scenes.random_scene(31, n, 2 * n, 2)
+    g = O.geometry_of(sc)
+    Hp = O.progressive_hologram(sc["intensity"], sc["layer"], all_salient_lists(sc["layer"], 2), g)
+    Hf = O.plain_pointwise_hologram(sc["intensity"], sc["layer"], g)
+    a1 = O.composite_amplitude(O.reconstruct_fields(Hp, g), sc["layer"])
+    a2 = O.composite_amplitude(O.reconstruct_fields(Hf, g), sc["layer"])
+    assert abs(O.ssim(a1 / a2.max(), a2 / a2.max()) - 1.0) < 1e-9
+
+
+def test_progressive_levels_improve_quality():
+    """Section 3 (Table 3 trend): the LLL-only reconstruction has lower SSIM against the
+    point-wise reference than the progressive one, which is lower than all-salient."""
+    n = 32
+    sc = scenes.random_scene(32, n, 2 * n, 1, graded=True)
+    g = O.geometry_of(sc)
+    Hf = O.plain_pointwise_hologram(sc["intensity"], sc["layer"], g)
+    ref = O.composite_amplitude(O.reconstruct_fields(Hf, g), sc["layer"])
+    ref = ref / ref.max()
+
+    def q(lists):
+        H = O.progressive_hologram(sc["intensity"], sc["layer"], lists, g)
+        a = O.composite_amplitude(O.reconstruct_fields(H, g), sc["layer"])
+        return O.ssim(a / ref.max() / (a.max() / ref.max()), ref)
+
+    s_lll = q(lll_only_lists(sc["layer"], 1))
+    s_prog = q(O.progressive_lists(sc["saliency"], sc["layer"], 1, {3: 0, 2: 100, 1: 200}))
+    s_all = q(all_salient_lists(sc["layer"], 1))
+    assert s_lll < s_prog < s_all
