@@ -1,0 +1,357 @@
+"""Benchmark: saliency-progressive hologram generation on one GB300 (or N replicas).
+
+A step is one pass of the whole hot path over one synthetic paper-scale scene
+(object 512x512 uint8, 16 depth layers in [0.08, 0.20] m, union-of-3-ellipses
+saliency, hologram 1024x1024 complex64, pitch 8 um, lambda 532 nm):
+  fringe tables -> 3-level integer Haar DWT -> 4 saliency work lists ->
+  progressive superposition (the chosen form).
+Metric: equivalent point-wise work per second, obj_h*obj_w*holo_h*holo_w / t,
+in Gpoint*px/s.
+
+Prints ONE JSON line (rank 0).  --impl reference times the FP64 CPU oracle on the
+same workload instead (the reference arm of this repository).
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+OBJ, HOLO, NLAYERS = 512, 1024, 16
+WORKLOAD = "paper-scale progressive CGH: object 512x512 u8, 16 layers z in [0.08,0.20] m, " \
+           "3-ellipse saliency (20-35%), 3 Haar levels, hologram 1024x1024 c64, p=8um, lambda=532nm"
+UNITS_PER_STEP = OBJ * OBJ * HOLO * HOLO  # point*px equivalent work of one scene
+METRIC = "Gpoint·px/s, saliency-progressive CGH at 1024² vs plain direct; % roofline"
+UNIT = "Gpoint·px/s"
+L2_FLUSH_BYTES = 512 << 20
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return None
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clock and throttle reasons while the GPU works."""
+    Q = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.rows = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        self.t0 = time.time()
+
+    def stop(self):
+        if self.proc is None:
+            return
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        for line in out.splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 10:
+                continue
+            try:
+                self.rows.append(dict(sm=float(f[2]), max=float(f[3]), power=float(f[4]),
+                                      hw=f[6], hwt=f[7], swt=f[8], pcap=f[9]))
+            except ValueError:
+                pass
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no nvidia-smi samples"], "samples": 0}
+        sms = sorted(r["sm"] for r in self.rows)
+        reasons = set()
+        for r in self.rows:
+            if r["hw"].lower() == "active":
+                reasons.add("hw_slowdown")
+            if r["hwt"].lower() == "active":
+                reasons.add("hw_thermal_slowdown")
+            if r["swt"].lower() == "active":
+                reasons.add("sw_thermal_slowdown")
+            if r["pcap"].lower() == "active":
+                reasons.add("sw_power_cap")
+        return {"sm_mhz": sms[len(sms) // 2], "sm_max_mhz": max(r["max"] for r in self.rows),
+                "reasons": sorted(reasons), "samples": len(self.rows),
+                "power_w_max": max(r["power"] for r in self.rows)}
+
+
+def scene_for_rank(rank):
+    from synth import scenes
+    return scenes.paper_scene(seed=2000 + rank)
+
+
+# ---------------------------------------------------------------------------------------
+# reference arm: the FP64 CPU oracle on the same workload
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    import numpy as np
+    from oracle import cgh_oracle as O
+    from synth import scenes
+    sc = scene_for_rank(0)
+    g = O.geometry_of(sc)
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+
+    def step():
+        lists = O.progressive_lists(sc["saliency"], sc["layer"], g.n_layers, scenes.THRESHOLDS_U8)
+        return O.progressive_hologram(sc["intensity"], sc["layer"], lists, g)
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    dt = time.perf_counter() - t0
+    value = UNITS_PER_STEP * args.steps / dt / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "form": "oracle residual-map FP64"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"{args.steps} full paper-scale scenes (selection + residual-map hologram)"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def cpu_baseline(budget_s=12.0):
+    """The oracle as it stands, on whole paper-scale scenes, for about budget_s seconds."""
+    from oracle import cgh_oracle as O
+    from synth import scenes
+    sc = scene_for_rank(0)
+    g = O.geometry_of(sc)
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    n = 0
+    t0 = time.perf_counter()
+    H = None
+    while True:
+        lists = O.progressive_lists(sc["saliency"], sc["layer"], g.n_layers, scenes.THRESHOLDS_U8)
+        H = O.progressive_hologram(sc["intensity"], sc["layer"], lists, g)
+        n += 1
+        if time.perf_counter() - t0 > budget_s or n >= 8:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": UNITS_PER_STEP * n / dt / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{n} whole paper-scale scene(s), selection + residual-map hologram, {dt:.1f} s"}, H
+
+
+# ---------------------------------------------------------------------------------------
+# our arm
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    devn = torch.cuda.current_device()
+    from paper_2211_09938_gb300 import Plan
+    from synth import scenes
+
+    sc = scene_for_rank(rank)
+    stream = torch.cuda.Stream()
+    form = args.form
+    with torch.cuda.stream(stream):
+        plan = Plan.for_scene(sc, stream=stream)
+        I = torch.from_numpy(sc["intensity"]).cuda()
+        L = torch.from_numpy(sc["layer"]).cuda()
+        S = torch.from_numpy(sc["saliency"]).cuda()
+        coeffs = torch.empty((NLAYERS, OBJ, OBJ), dtype=torch.int32, device="cuda")
+        counts = torch.zeros((4, 2), dtype=torch.int32, device="cuda")
+        lists = [torch.empty(plan.max_blocks(3 if k == 0 else k), dtype=torch.int32, device="cuda")
+                 for k in range(4)]
+        holo = torch.empty((HOLO, HOLO), dtype=torch.complex64, device="cuda")
+        flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    launches_per_step = 1 + 1 + 4 * 3 + 1  # tables, DWT, 4 x (count, scan, scatter), superposition
+
+    def step():
+        plan.build_tables(stream=stream)
+        plan.haar_decompose(I, L, coeffs, stream=stream)
+        plan.progressive_lists(S, L, scenes.THRESHOLDS_U8, counts=counts, lists=lists, stream=stream)
+        plan.progressive_hologram(coeffs, lists, counts, holo=holo, form=form, stream=stream)
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            step()
+    stream.synchronize()
+
+    # ---- timed region: K steps, L2 flushed before each, device time from CUDA events
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    sampler = ClockSampler(devn)
+    sampler.start()
+    time.sleep(0.3)
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    wall0 = time.perf_counter()
+    with torch.cuda.stream(stream):
+        for k in range(args.steps):
+            flush.fill_(float(k))
+            evs[k][0].record(stream)
+            step()
+            evs[k][1].record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    if ws > 1:
+        torch.distributed.barrier()
+    sampler.stop()
+    dev_ms = sum(a.elapsed_time(b) for a, b in evs)
+    t = torch.tensor([dev_ms], dtype=torch.float64, device="cuda")
+    if ws > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    dev_ms = float(t.item())
+    value = UNITS_PER_STEP * args.steps * ws / (dev_ms / 1e3) / 1e9
+
+    # ---- dominant kernel alone (the superposition), CUDA events on its stream
+    R = max(5, min(50, args.steps))
+    kev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(R)]
+    with torch.cuda.stream(stream):
+        for k in range(R):
+            flush.fill_(float(k))
+            kev[k][0].record(stream)
+            plan.progressive_hologram(coeffs, lists, counts, holo=holo, accumulate=True, form=form,
+                                      stream=stream)
+            kev[k][1].record(stream)
+    torch.cuda.synchronize()
+    k_ms = sum(a.elapsed_time(b) for a, b in kev) / R
+
+    c = counts.cpu().numpy()
+    n_lll, n1, n2, n3 = (int(c[k, 0]) for k in range(4))
+    rank1_terms = n_lll + 2 * (n1 + n2 + n3)
+    pk = peaks() or {}
+    clocks = sampler.summary()
+    if form == "direct_lut":
+        # FP32 FFMA bound: 8 flop (4 FFMA) per rank-1 term and hologram pixel
+        algo_flop = 8.0 * rank1_terms * HOLO * HOLO
+        sms = torch.cuda.get_device_properties(devn).multi_processor_count
+        peak_tf = sms * 128 * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+        roof = {"bound": "alu", "kernel": "k_direct_lut", "achieved": algo_flop / (k_ms / 1e3) / 1e12,
+                "peak": peak_tf, "unit": "TFLOP/s",
+                "frac": algo_flop / (k_ms / 1e3) / 1e12 / peak_tf, "traffic": None,
+                "peak_note": f"FP32 FFMA: {sms} SMs x 128 lanes x 2 flop x {pk.get('sm_max_mhz', 2070.0):.0f} MHz "
+                             "(max SM clock; derived, not measured)",
+                "kernel_ms": k_ms}
+    else:
+        roof = {"bound": "tensor", "kernel": "tc_gemm", "achieved": None, "peak": pk.get("bf16_tflops"),
+                "unit": "TFLOP/s", "frac": None, "traffic": None, "kernel_ms": k_ms}
+
+    # ---- end to end through the C ABI with host buffers: H2D inputs, step, D2H hologram
+    hI = torch.from_numpy(sc["intensity"]).pin_memory()
+    hL = torch.from_numpy(sc["layer"]).pin_memory()
+    hS = torch.from_numpy(sc["saliency"]).pin_memory()
+    hH = torch.empty((HOLO, HOLO), dtype=torch.complex64).pin_memory()
+    E = max(3, min(args.steps, 20))
+    torch.cuda.synchronize()
+    e0 = time.perf_counter()
+    with torch.cuda.stream(stream):
+        for _ in range(E):
+            I.copy_(hI, non_blocking=True)
+            L.copy_(hL, non_blocking=True)
+            S.copy_(hS, non_blocking=True)
+            step()
+            hH.copy_(holo, non_blocking=True)
+    stream.synchronize()
+    e2e_s = (time.perf_counter() - e0) / E
+    e2e = {"value": UNITS_PER_STEP * ws / e2e_s / 1e9, "unit": UNIT,
+           "h2d_bytes_per_step": 3 * OBJ * OBJ, "d2h_bytes_per_step": 8 * HOLO * HOLO}
+
+    # ---- plain point-wise direct kernel on the same scene (the baseline the metric names)
+    plain = None
+    if not args.skip_plain:
+        with torch.cuda.stream(stream):
+            Hp = plan.plain_direct(I, L, stream=stream)
+            pe = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+            pe[0].record(stream)
+            plan.plain_direct(I, L, holo=Hp, stream=stream)
+            pe[1].record(stream)
+        torch.cuda.synchronize()
+        p_ms = pe[0].elapsed_time(pe[1])
+        plain = {"ms": p_ms, "value": UNITS_PER_STEP / (p_ms / 1e3) / 1e9, "unit": UNIT,
+                 "speedup_of_progressive_step": p_ms / (dev_ms / args.steps)}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": dev_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "form": form, "l2": "flushed (512 MiB write) before every timed step",
+                   "parallelism": f"replicas{ws}" if ws > 1 else "single GPU",
+                   "work_lists": [n_lll, n1, n2, n3], "rank1_terms": rank1_terms},
+        "roofline": roof, "clocks": clocks, "e2e": e2e,
+        "gpu_launches": launches_per_step * args.steps, "wall_s_timed_region": wall,
+    }
+    if plain is not None:
+        line["plain_direct"] = plain
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cb, Href = cpu_baseline()
+        line["cpu_baseline"] = cb
+        from oracle import cgh_oracle as O
+        # the hologram buffer holds the accumulated kernel-timing runs: recompute one step
+        with torch.cuda.stream(stream):
+            step()
+        stream.synchronize()
+        line["accuracy"] = {"rel_l2_vs_fp64_oracle": O.rel_l2(holo.cpu().numpy(), Href)}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    plan.close()
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--form", default="direct_lut", choices=["direct_lut", "tc_bf16x3", "tc_fp16x3"])
+    ap.add_argument("--skip-plain", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

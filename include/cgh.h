@@ -1,0 +1,200 @@
+/*
+ * cgh.h - C ABI of libcgh, saliency-progressive point-source hologram generation
+ * (Rafiei & Shirani, "Progressive hologram generation based on object saliency",
+ * arXiv 2211.09938) on NVIDIA GB300 (sm_103a).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * - Every data pointer is a DEVICE pointer owned by the caller unless a call says
+ *   otherwise; the library never frees caller memory.  Arrays are dense, row-major,
+ *   C order, with no padding between rows.
+ * - `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream).
+ *   Calls only enqueue work on that stream and return; they never synchronise
+ *   except where a call says so.  Counts produced on the device stay there.
+ * - Return value: CGH_OK (0) or an error code below; cgh_last_error() gives a
+ *   thread-local message for the last failing call of the calling thread.
+ *   Argument errors are detected on the host before anything is enqueued.
+ *   CGH_ERR_CUDA reports a CUDA launch or API error (no CPU fallback exists: with
+ *   no usable GPU every call fails with CGH_ERR_CUDA).
+ * - Geometry: object obj_h x obj_w pixels (multiples of 8), hologram holo_h x holo_w
+ *   pixels, with holo_h = s*obj_h and holo_w = s*obj_w for one integer stride s >= 1.
+ *   Object pixel (i, j) sits at hologram pixel (s*i, s*j).  Pixel pitch p, wavelength
+ *   lambda, depth layers z_0..z_{Z-1} (metres), 1 <= Z <= 64.
+ * - Point fringe (Eq. 1 of the paper, paraxial form, 1/r and exp(jkz) dropped): the
+ *   hologram of a unit point at (i, j) on layer z is
+ *       f_z(m - s*i) * f_z(n - s*j),   f_z(d) = exp(j*2*pi*frac(a_z*d^2)),
+ *       a_z = p^2 / (2*lambda*z).
+ * - Holograms are complex64 (float2: re, im) [holo_h][holo_w].
+ */
+#ifndef CGH_H
+#define CGH_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------------------- */
+#define CGH_OK 0
+#define CGH_ERR_ARG 1          /* invalid argument (NULL, size, range)               */
+#define CGH_ERR_CUDA 2         /* CUDA API / launch error, or no usable GPU          */
+#define CGH_ERR_UNSUPPORTED 3  /* valid but not supported by this build / device      */
+#define CGH_ERR_TIMEOUT 4      /* a bounded device-side wait gave up (see cgh_status) */
+#define CGH_ERR_NOMEM 5        /* device allocation failed                            */
+
+/* ---- superposition forms (cgh_progressive_hologram `form`) ------------------------ */
+/* Detail-basis direct form on CUDA cores, FP32: every LLL block and every selected
+ * detail block is added as row-factor x column-factor products read from the fringe
+ * tables (Eq. 3, Section 2 steps 2-5).                                               */
+#define CGH_FORM_DIRECT_LUT 0
+/* Separable dense form on tcgen05 tensor cores: per layer H += E_z * A^_z * E_z^T,
+ * A^_z the progressively reconstructed object plane (inverse DWT of the LLL band and
+ * the selected detail blocks), operands split into hi+lo halves (3 products) with
+ * FP32 accumulation in tensor memory.                                                */
+#define CGH_FORM_TC_BF16X3 1   /* bf16 hi+lo                                            */
+#define CGH_FORM_TC_FP16X3 2   /* fp16 hi+lo                                            */
+
+/* ---- plan --------------------------------------------------------------------------- */
+typedef struct cgh_plan cgh_plan;
+
+/* Thread-local message describing the last error of the calling thread ("" if none). */
+const char* cgh_last_error(void);
+
+/* Library version (major*10000 + minor*100 + patch). */
+int cgh_version(void);
+
+/*
+ * cgh_plan_create - geometry, fringe tables and scratch for one scene shape.
+ * Paper: Section 2 ("hologram blocks ... precomputed in LUT using eq. 1", 8x8, 4x4,
+ * 2x2 and 1x1 blocks) and Table 1 (scene specification).
+ *   out          receives the plan (host pointer to a library-owned object)
+ *   obj_h, obj_w object size, multiples of 8 (3 Haar levels), 8..8192
+ *   holo_h, holo_w hologram size, s*obj_h and s*obj_w for an integer s, <= 16384
+ *   pitch_m, wavelength_m  pixel pitch and wavelength (metres, > 0)
+ *   n_layers     Z, 1..64;   z_m  HOST array of Z layer distances (metres, > 0)
+ *   levels       number of Haar levels; must be 3 (the paper's choice)
+ *   flags        0 (reserved)
+ *   stream       stream on which the fringe tables are built
+ * The plan allocates device memory (tables, scratch, status word) with cudaMalloc on
+ * the current device and builds the fringe tables with cgh_build_tables on `stream`.
+ * Errors: CGH_ERR_ARG, CGH_ERR_NOMEM, CGH_ERR_CUDA.  On error *out is NULL.
+ */
+int cgh_plan_create(cgh_plan** out, int obj_h, int obj_w, int holo_h, int holo_w,
+                    double pitch_m, double wavelength_m, int n_layers, const double* z_m,
+                    int levels, int flags, void* stream);
+
+/* Frees the plan and its device memory (synchronises the device first).  NULL is a no-op. */
+int cgh_plan_destroy(cgh_plan* plan);
+
+/*
+ * cgh_build_tables - (re)build the plan's fringe tables on `stream`.
+ * Paper: Section 2 (LUT hologram blocks of 2^l x 2^l points from Eq. 1).
+ * For every layer z, level l in 0..3 and offset d in [-s*obj, holo) the plan stores the
+ * one-axis block fringes
+ *     b_l(d) = sum_{t < 2^l} f_z(d - s*t)
+ *     w_l(d) = sum_{t < 2^(l-1)} f_z(d - s*t) - sum_{2^(l-1) <= t < 2^l} f_z(d - s*t)
+ * (b_0 = f_z), whose outer products are the hologram blocks of a uniform block and of
+ * the Haar detail functions.  The phase frac(a_z*d^2) is formed in FP64 from the exact
+ * integer d^2 and range-reduced before the FP32 cast.  plan_create already calls it.
+ */
+int cgh_build_tables(cgh_plan* plan, void* stream);
+
+/*
+ * cgh_haar_decompose - per-layer 3-level integer Haar DWT.
+ * Paper: Eq. 2 and Section 2 step 1.  For every layer z the plane
+ * A_z(i,j) = intensity(i,j) * [layer_idx(i,j) == z] is decomposed with the unnormalised
+ * sum/difference Haar on 2x2 cells [a b; c d] (rows i, columns j):
+ *     S = a+b+c+d, X = a-b+c-d, Y = a+b-c-d, D = a-b-c+d, recursing on S.
+ *   intensity  uint8 [obj_h][obj_w];  layer_idx uint8 [obj_h][obj_w] (values >= Z own no layer)
+ *   coeffs     int32 [Z][obj_h][obj_w] output, Mallat layout per layer: at level l
+ *              (h = obj_h>>l, w = obj_w>>l) X in [0,h)x[w,2w), Y in [h,2h)x[0,w),
+ *              D in [h,2h)x[w,2w); LLL (S of level 3) in [0,obj_h>>3)x[0,obj_w>>3).
+ * Bit-exact.  Errors: CGH_ERR_ARG (NULL), CGH_ERR_CUDA.
+ */
+int cgh_haar_decompose(const cgh_plan* plan, const uint8_t* intensity, const uint8_t* layer_idx,
+                       int32_t* coeffs, void* stream);
+
+/*
+ * cgh_select_blocks - saliency quantisation, block selection and ordered compaction.
+ * Paper: Section 2 step 1 (saliency map quantised to the level grids by the block
+ * maximum) and steps 2-5 (blocks above a threshold get that level's hologram).
+ * A level-l block (2^l x 2^l pixels) of layer z is selected iff layer z owns at least
+ * one of its pixels and (threshold < 0 or max(saliency over the block) > threshold).
+ *   saliency   uint8 [obj_h][obj_w] (may be NULL when threshold < 0)
+ *   layer_idx  uint8 [obj_h][obj_w]
+ *   threshold  -1 (occupancy only: the LLL list) or 0..255 (strict comparison)
+ *   level      1..3
+ *   list       int32 [capacity] output, entries (z << 24) | (by << 12) | bx in
+ *              ascending order of z, then block row by, then block column bx
+ *   d_count    int32 [2] output: d_count[0] = entries written = min(total, capacity),
+ *              d_count[1] = total number of selected blocks
+ *   capacity   >= 0
+ * Uses plan scratch for per-chunk counts (calls that share a plan must be ordered on
+ * one stream).  Bit-exact.  Errors: CGH_ERR_ARG, CGH_ERR_CUDA.
+ */
+int cgh_select_blocks(const cgh_plan* plan, const uint8_t* saliency, const uint8_t* layer_idx,
+                      int threshold, int level, int32_t* list, int32_t* d_count, int capacity,
+                      void* stream);
+
+/*
+ * cgh_progressive_hologram - progressive superposition of the selected blocks.
+ * Paper: Eq. 3 (hologram = sum of the holograms of the Haar basis functions times their
+ * coefficients) and Section 2 steps 2-5.
+ *   H(m,n) = sum_z [ sum_{LLL list} LLL/64 * b_3(m-u) b_3(n-v)
+ *            + sum_{l=1..3} sum_{level-l list} 4^-l (X b_l(m-u) w_l(n-v)
+ *                                               + Y w_l(m-u) b_l(n-v) + D w_l(m-u) w_l(n-v)) ]
+ *   with u = s*2^l*by, v = s*2^l*bx for a block (z, by, bx) of level l.
+ *   coeffs    int32 [Z][obj_h][obj_w] from cgh_haar_decompose
+ *   lists     HOST array of 4 device pointers: lists[0] = LLL list (level-3 blocks),
+ *             lists[l] = level-l detail list, l = 1..3 (format of cgh_select_blocks)
+ *   d_counts  int32 [4][2] device array, d_counts[2k] = entries in lists[k] (the
+ *             d_count[0] written by cgh_select_blocks); [2k+1] is ignored
+ *   holo      complex64 [holo_h][holo_w] output
+ *   accumulate 0: holo = H;  1: holo += H
+ *   form      CGH_FORM_* (the tensor-core forms use plan scratch)
+ * Errors: CGH_ERR_ARG, CGH_ERR_UNSUPPORTED (form), CGH_ERR_CUDA.
+ */
+int cgh_progressive_hologram(const cgh_plan* plan, const int32_t* coeffs,
+                             const int32_t* const* lists, const int32_t* d_counts,
+                             float* holo, int accumulate, int form, void* stream);
+
+/*
+ * cgh_plain_direct - plain point-wise hologram, no wavelet and no saliency.
+ * Paper: Eq. 1 (the fully point-wise "1x1 LUT" hologram of Section 3, M x N operators).
+ *   H(m,n) = sum_{(i,j)} intensity(i,j) * exp(j*2*pi*frac(a_{z(i,j)} * ((m-s*i)^2 + (n-s*j)^2)))
+ * with z(i,j) = layer_idx(i,j) (pixels with layer >= Z are skipped).  The phase is
+ * reduced exactly in 64-bit fixed point (a_z mod 1 scaled by 2^64) and evaluated with
+ * the hardware sine/cosine (SFU).
+ *   holo complex64 [holo_h][holo_w] output (overwritten).
+ * Errors: CGH_ERR_ARG, CGH_ERR_CUDA.
+ */
+int cgh_plain_direct(const cgh_plan* plan, const uint8_t* intensity, const uint8_t* layer_idx,
+                     float* holo, void* stream);
+
+/*
+ * cgh_reconstruct - Fresnel back-propagation of a hologram to every layer.
+ * Paper: Section 2 last paragraph (numerical reconstruction; the paper uses the inverse
+ * angular spectrum, this library uses the Fresnel adjoint of Eq. 1 on the object grid).
+ *   R_z(i,j) = sum_{m,n} holo(m,n) * conj(f_z(m-s*i) * f_z(n-s*j))
+ *   holo       complex64 [holo_h][holo_w]
+ *   fields     complex64 [Z][obj_h][obj_w] output, or NULL
+ *   layer_idx  uint8 [obj_h][obj_w] (needed when amplitude != NULL)
+ *   amplitude  float [obj_h][obj_w] output |R_{layer(i,j)}(i,j)|, or NULL
+ * Uses plan scratch.  Errors: CGH_ERR_ARG, CGH_ERR_CUDA.
+ */
+int cgh_reconstruct(const cgh_plan* plan, const float* holo, float* fields,
+                    const uint8_t* layer_idx, float* amplitude, void* stream);
+
+/*
+ * cgh_status - read and clear the plan's device status word (synchronises `stream`).
+ * Bounded device-side waits that give up record CGH_ERR_TIMEOUT there instead of
+ * hanging.  *status_out receives CGH_OK or the recorded code.
+ */
+int cgh_status(const cgh_plan* plan, int* status_out, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CGH_H */

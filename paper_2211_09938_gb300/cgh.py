@@ -1,0 +1,203 @@
+"""Thin ctypes binding of libcgh (include/cgh.h).
+
+Argument marshalling only: every step of the hologram path runs in the CUDA
+kernels of libcgh.so.  There is no CPU fallback; if the library is missing or no
+GPU is usable, calls raise CghError.
+
+Two layers:
+* the raw C functions under their C names (``lib().cgh_plan_create`` ...), for
+  callers that hold raw device pointers;
+* ``Plan``, which owns a cgh_plan and takes torch CUDA tensors (PyTorch is used
+  for device memory and streams only).
+"""
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libcgh.so")
+
+CGH_OK = 0
+CGH_ERR_ARG = 1
+CGH_ERR_CUDA = 2
+CGH_ERR_UNSUPPORTED = 3
+CGH_ERR_TIMEOUT = 4
+CGH_ERR_NOMEM = 5
+
+FORM_DIRECT_LUT = 0
+FORM_TC_BF16X3 = 1
+FORM_TC_FP16X3 = 2
+FORMS = {"direct_lut": FORM_DIRECT_LUT, "tc_bf16x3": FORM_TC_BF16X3, "tc_fp16x3": FORM_TC_FP16X3}
+
+# Every symbol include/cgh.h declares, with (restype, argtypes).
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_D = ctypes.c_double
+SIGNATURES = {
+    "cgh_last_error": (ctypes.c_char_p, []),
+    "cgh_version": (_I, []),
+    "cgh_plan_create": (_I, [ctypes.POINTER(_P), _I, _I, _I, _I, _D, _D, _I,
+                             ctypes.POINTER(_D), _I, _I, _P]),
+    "cgh_plan_destroy": (_I, [_P]),
+    "cgh_build_tables": (_I, [_P, _P]),
+    "cgh_haar_decompose": (_I, [_P, _P, _P, _P, _P]),
+    "cgh_select_blocks": (_I, [_P, _P, _P, _I, _I, _P, _P, _I, _P]),
+    "cgh_progressive_hologram": (_I, [_P, _P, ctypes.POINTER(_P), _P, _P, _I, _I, _P]),
+    "cgh_plain_direct": (_I, [_P, _P, _P, _P, _P]),
+    "cgh_reconstruct": (_I, [_P, _P, _P, _P, _P, _P]),
+    "cgh_status": (_I, [_P, ctypes.POINTER(_I), _P]),
+}
+
+_lib = None
+
+
+class CghError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"libcgh error {code}: {msg}")
+        self.code = code
+
+
+def lib():
+    """Load libcgh.so (built in-tree by __graft_entry__.build()); raise if absent."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise CghError(CGH_ERR_CUDA, f"{LIB_PATH} is not built; run __graft_entry__.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def check(rc):
+    if rc != CGH_OK:
+        raise CghError(rc, lib().cgh_last_error().decode(errors="replace"))
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+class Plan:
+    """A cgh_plan for one scene geometry.  Tensors passed in must be contiguous CUDA
+    tensors of the dtypes include/cgh.h states; outputs are allocated by the caller or
+    by the convenience helpers below (torch.empty on the plan's device)."""
+
+    def __init__(self, obj_shape, holo_shape, pitch, wavelength, z, levels=3, stream=None):
+        import torch
+        self.obj_h, self.obj_w = int(obj_shape[0]), int(obj_shape[1])
+        self.holo_h, self.holo_w = int(holo_shape[0]), int(holo_shape[1])
+        self.z = [float(v) for v in z]
+        self.n_layers = len(self.z)
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        zs = (ctypes.c_double * self.n_layers)(*self.z)
+        h = ctypes.c_void_p()
+        check(lib().cgh_plan_create(ctypes.byref(h), self.obj_h, self.obj_w, self.holo_h, self.holo_w,
+                                    float(pitch), float(wavelength), self.n_layers, zs, levels, 0,
+                                    _stream(stream)))
+        self.handle = h
+
+    @classmethod
+    def for_scene(cls, scene, stream=None):
+        return cls(scene["intensity"].shape, scene["holo"], scene["pitch"], scene["wavelength"],
+                   scene["z"], stream=stream)
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            lib().cgh_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---- C calls -------------------------------------------------------------------
+    def build_tables(self, stream=None):
+        check(lib().cgh_build_tables(self.handle, _stream(stream)))
+
+    def haar_decompose(self, intensity, layer, coeffs=None, stream=None):
+        import torch
+        if coeffs is None:
+            coeffs = torch.empty((self.n_layers, self.obj_h, self.obj_w), dtype=torch.int32,
+                                 device=self.device)
+        check(lib().cgh_haar_decompose(self.handle, _ptr(intensity), _ptr(layer), _ptr(coeffs),
+                                       _stream(stream)))
+        return coeffs
+
+    def max_blocks(self, level):
+        return self.n_layers * (self.obj_h >> level) * (self.obj_w >> level)
+
+    def select_blocks(self, saliency, layer, threshold, level, out=None, count=None,
+                      capacity=None, stream=None):
+        import torch
+        if capacity is None:
+            capacity = self.max_blocks(level) if out is None else out.numel()
+        if out is None:
+            out = torch.empty(max(capacity, 1), dtype=torch.int32, device=self.device)
+        if count is None:
+            count = torch.empty(2, dtype=torch.int32, device=self.device)
+        check(lib().cgh_select_blocks(self.handle, _ptr(saliency), _ptr(layer), int(threshold),
+                                      int(level), _ptr(out), _ptr(count), int(capacity),
+                                      _stream(stream)))
+        return out, count
+
+    def progressive_lists(self, saliency, layer, thresholds, counts=None, lists=None, stream=None):
+        """The four work lists [LLL, level 1, level 2, level 3] and their int32[4][2]
+        counts; thresholds maps level -> uint8 threshold."""
+        import torch
+        if counts is None:
+            counts = torch.zeros((4, 2), dtype=torch.int32, device=self.device)
+        out = []
+        for k in range(4):
+            level = 3 if k == 0 else k
+            thr = -1 if k == 0 else int(thresholds[k])
+            buf = None if lists is None else lists[k]
+            lst, _ = self.select_blocks(saliency, layer, thr, level, out=buf, count=counts[k],
+                                        stream=stream)
+            out.append(lst)
+        return out, counts
+
+    def progressive_hologram(self, coeffs, lists, counts, holo=None, accumulate=False,
+                             form="direct_lut", stream=None):
+        import torch
+        if holo is None:
+            holo = torch.empty((self.holo_h, self.holo_w), dtype=torch.complex64, device=self.device)
+        arr = (ctypes.c_void_p * 4)(*[l.data_ptr() for l in lists])
+        f = FORMS[form] if isinstance(form, str) else int(form)
+        check(lib().cgh_progressive_hologram(self.handle, _ptr(coeffs), arr, _ptr(counts), _ptr(holo),
+                                             1 if accumulate else 0, f, _stream(stream)))
+        return holo
+
+    def plain_direct(self, intensity, layer, holo=None, stream=None):
+        import torch
+        if holo is None:
+            holo = torch.empty((self.holo_h, self.holo_w), dtype=torch.complex64, device=self.device)
+        check(lib().cgh_plain_direct(self.handle, _ptr(intensity), _ptr(layer), _ptr(holo),
+                                     _stream(stream)))
+        return holo
+
+    def reconstruct(self, holo, layer=None, fields=True, amplitude=True, stream=None):
+        import torch
+        f = torch.empty((self.n_layers, self.obj_h, self.obj_w), dtype=torch.complex64,
+                        device=self.device) if fields else None
+        a = torch.empty((self.obj_h, self.obj_w), dtype=torch.float32,
+                        device=self.device) if amplitude else None
+        check(lib().cgh_reconstruct(self.handle, _ptr(holo), _ptr(f), _ptr(layer), _ptr(a),
+                                    _stream(stream)))
+        return f, a
+
+    def status(self, stream=None):
+        v = ctypes.c_int(0)
+        check(lib().cgh_status(self.handle, ctypes.byref(v), _stream(stream)))
+        return v.value

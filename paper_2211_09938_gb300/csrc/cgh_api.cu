@@ -1,0 +1,214 @@
+// C ABI of libcgh: argument checking, plan lifetime, error reporting and launches.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include "cgh_internal.h"
+
+static thread_local char g_err[512] = "";
+
+int cgh_fail(int code, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+  return code;
+}
+
+int cgh_cuda_check(cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return CGH_OK;
+  if (e == cudaErrorMemoryAllocation)
+    return cgh_fail(CGH_ERR_NOMEM, "%s: %s", what, cudaGetErrorString(e));
+  return cgh_fail(CGH_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define CHECK_CUDA(expr, what)                          \
+  do {                                                  \
+    int _rc = cgh_cuda_check((expr), (what));           \
+    if (_rc != CGH_OK) return _rc;                      \
+  } while (0)
+
+extern "C" {
+
+const char* cgh_last_error(void) { return g_err; }
+
+int cgh_version(void) { return 10000; }
+
+int cgh_plan_destroy(cgh_plan* p) {
+  if (!p) return CGH_OK;
+  cudaDeviceSynchronize();
+  tc_destroy(p);
+  cudaFree(p->d_tab);
+  cudaFree(p->d_a_frac);
+  cudaFree(p->d_a_fixed);
+  cudaFree(p->d_status);
+  cudaFree(p->d_chunk_cnt);
+  cudaFree(p->d_chunk_off);
+  free(p);
+  return CGH_OK;
+}
+
+int cgh_build_tables(cgh_plan* p, void* stream) {
+  if (!p) return cgh_fail(CGH_ERR_ARG, "cgh_build_tables: plan is NULL");
+  CHECK_CUDA(launch_build_tables(p, (cudaStream_t)stream), "cgh_build_tables launch");
+  return CGH_OK;
+}
+
+int cgh_plan_create(cgh_plan** out, int obj_h, int obj_w, int holo_h, int holo_w, double pitch_m,
+                    double wavelength_m, int n_layers, const double* z_m, int levels, int flags,
+                    void* stream) {
+  if (!out) return cgh_fail(CGH_ERR_ARG, "cgh_plan_create: out is NULL");
+  *out = NULL;
+  if (levels != CGH_LEVELS)
+    return cgh_fail(CGH_ERR_UNSUPPORTED, "cgh_plan_create: levels must be 3 (got %d)", levels);
+  if (obj_h < 8 || obj_w < 8 || obj_h % 8 || obj_w % 8 || obj_h > 8192 || obj_w > 8192)
+    return cgh_fail(CGH_ERR_ARG, "cgh_plan_create: object %dx%d must be multiples of 8 in [8, 8192]",
+                    obj_h, obj_w);
+  if (holo_h <= 0 || holo_w <= 0 || holo_h % obj_h || holo_w % obj_w ||
+      holo_h / obj_h != holo_w / obj_w || holo_h > 16384 || holo_w > 16384)
+    return cgh_fail(CGH_ERR_ARG,
+                    "cgh_plan_create: hologram %dx%d must be s*object (%dx%d) for one integer s, <= 16384",
+                    holo_h, holo_w, obj_h, obj_w);
+  if (!(pitch_m > 0) || !(wavelength_m > 0))
+    return cgh_fail(CGH_ERR_ARG, "cgh_plan_create: pitch and wavelength must be > 0");
+  if (n_layers < 1 || n_layers > CGH_MAX_LAYERS)
+    return cgh_fail(CGH_ERR_ARG, "cgh_plan_create: n_layers %d outside [1, %d]", n_layers, CGH_MAX_LAYERS);
+  if (!z_m) return cgh_fail(CGH_ERR_ARG, "cgh_plan_create: z_m is NULL");
+  for (int k = 0; k < n_layers; ++k)
+    if (!(z_m[k] > 0)) return cgh_fail(CGH_ERR_ARG, "cgh_plan_create: z[%d] must be > 0", k);
+  if (flags != 0) return cgh_fail(CGH_ERR_ARG, "cgh_plan_create: flags must be 0");
+
+  cgh_plan* p = (cgh_plan*)calloc(1, sizeof(cgh_plan));
+  if (!p) return cgh_fail(CGH_ERR_NOMEM, "cgh_plan_create: host allocation failed");
+  p->obj_h = obj_h;
+  p->obj_w = obj_w;
+  p->holo_h = holo_h;
+  p->holo_w = holo_w;
+  p->s = holo_h / obj_h;
+  p->n_layers = n_layers;
+  p->levels = levels;
+  p->pitch = pitch_m;
+  p->wavelength = wavelength_m;
+  for (int k = 0; k < n_layers; ++k) {
+    const double a = pitch_m * pitch_m / (2.0 * wavelength_m * z_m[k]);
+    const double fr = a - floor(a);
+    p->z[k] = z_m[k];
+    p->a_frac[k] = fr;
+    const double x = floor(ldexp(fr, 64) + 0.5);
+    p->a_fixed[k] = x >= 18446744073709551616.0 ? 0ull : (uint64_t)x;
+  }
+  const int nmax = holo_h > holo_w ? holo_h : holo_w;
+  const int omax = obj_h > obj_w ? obj_h : obj_w;
+  p->tab_off = p->s * omax;
+  p->tab_len = nmax + p->tab_off;
+  cudaGetDevice(&p->device);
+
+  int rc = CGH_OK;
+#define PLAN_TRY(expr, what)                     \
+  do {                                           \
+    rc = cgh_cuda_check((expr), (what));         \
+    if (rc != CGH_OK) {                          \
+      cgh_plan_destroy(p);                       \
+      return rc;                                 \
+    }                                            \
+  } while (0)
+  PLAN_TRY(cudaMalloc(&p->d_tab, (size_t)n_layers * CGH_TAB_PER_LAYER * p->tab_len * sizeof(float2)),
+           "cgh_plan_create: tables");
+  PLAN_TRY(cudaMalloc(&p->d_a_frac, CGH_MAX_LAYERS * sizeof(double)), "cgh_plan_create: a_frac");
+  PLAN_TRY(cudaMalloc(&p->d_a_fixed, CGH_MAX_LAYERS * sizeof(unsigned long long)), "cgh_plan_create: a_fixed");
+  PLAN_TRY(cudaMalloc(&p->d_status, sizeof(int)), "cgh_plan_create: status");
+  p->max_chunks = select_num_chunks(obj_h, obj_w, 1);
+  PLAN_TRY(cudaMalloc(&p->d_chunk_cnt, (size_t)n_layers * p->max_chunks * sizeof(int)),
+           "cgh_plan_create: chunk counts");
+  PLAN_TRY(cudaMalloc(&p->d_chunk_off, (size_t)n_layers * p->max_chunks * sizeof(int)),
+           "cgh_plan_create: chunk offsets");
+  PLAN_TRY(cudaMemcpy(p->d_a_frac, p->a_frac, CGH_MAX_LAYERS * sizeof(double), cudaMemcpyHostToDevice),
+           "cgh_plan_create: copy a_frac");
+  PLAN_TRY(cudaMemcpy(p->d_a_fixed, p->a_fixed, CGH_MAX_LAYERS * sizeof(unsigned long long),
+                      cudaMemcpyHostToDevice),
+           "cgh_plan_create: copy a_fixed");
+  PLAN_TRY(cudaMemset(p->d_status, 0, sizeof(int)), "cgh_plan_create: status clear");
+  PLAN_TRY(launch_build_tables(p, (cudaStream_t)stream), "cgh_plan_create: table build");
+#undef PLAN_TRY
+  *out = p;
+  return CGH_OK;
+}
+
+int cgh_haar_decompose(const cgh_plan* p, const uint8_t* intensity, const uint8_t* layer_idx,
+                       int32_t* coeffs, void* stream) {
+  if (!p || !intensity || !layer_idx || !coeffs)
+    return cgh_fail(CGH_ERR_ARG, "cgh_haar_decompose: NULL argument");
+  if (((uintptr_t)coeffs & 15) || ((uintptr_t)intensity & 7) || ((uintptr_t)layer_idx & 7))
+    return cgh_fail(CGH_ERR_ARG, "cgh_haar_decompose: coeffs must be 16-byte and inputs 8-byte aligned");
+  CHECK_CUDA(launch_haar(p, intensity, layer_idx, coeffs, (cudaStream_t)stream), "cgh_haar_decompose");
+  return CGH_OK;
+}
+
+int cgh_select_blocks(const cgh_plan* p, const uint8_t* saliency, const uint8_t* layer_idx,
+                      int threshold, int level, int32_t* list, int32_t* d_count, int capacity,
+                      void* stream) {
+  if (!p || !layer_idx || !d_count || (capacity > 0 && !list))
+    return cgh_fail(CGH_ERR_ARG, "cgh_select_blocks: NULL argument");
+  if (level < 1 || level > CGH_LEVELS) return cgh_fail(CGH_ERR_ARG, "cgh_select_blocks: level %d not in 1..3", level);
+  if (threshold < -1 || threshold > 255)
+    return cgh_fail(CGH_ERR_ARG, "cgh_select_blocks: threshold %d not in -1..255", threshold);
+  if (threshold >= 0 && !saliency) return cgh_fail(CGH_ERR_ARG, "cgh_select_blocks: saliency is NULL");
+  if (capacity < 0) return cgh_fail(CGH_ERR_ARG, "cgh_select_blocks: capacity < 0");
+  CHECK_CUDA(launch_select(p->obj_h, p->obj_w, p->n_layers, threshold >= 0 ? saliency : NULL, layer_idx,
+                           threshold, level, list, d_count, capacity, p->d_chunk_cnt, p->d_chunk_off,
+                           (cudaStream_t)stream),
+             "cgh_select_blocks");
+  return CGH_OK;
+}
+
+int cgh_progressive_hologram(const cgh_plan* p, const int32_t* coeffs, const int32_t* const* lists,
+                             const int32_t* d_counts, float* holo, int accumulate, int form,
+                             void* stream) {
+  if (!p || !coeffs || !lists || !d_counts || !holo)
+    return cgh_fail(CGH_ERR_ARG, "cgh_progressive_hologram: NULL argument");
+  for (int k = 0; k < 4; ++k)
+    if (!lists[k]) return cgh_fail(CGH_ERR_ARG, "cgh_progressive_hologram: lists[%d] is NULL", k);
+  if (((uintptr_t)holo & 7)) return cgh_fail(CGH_ERR_ARG, "cgh_progressive_hologram: holo must be 8-byte aligned");
+  cudaStream_t st = (cudaStream_t)stream;
+  if (form == CGH_FORM_DIRECT_LUT) {
+    if (!accumulate)
+      CHECK_CUDA(cudaMemsetAsync(holo, 0, (size_t)p->holo_h * p->holo_w * sizeof(float2), st),
+                 "cgh_progressive_hologram: clear");
+    CHECK_CUDA(launch_direct_lut(p, coeffs, lists, d_counts, (float2*)holo, st), "cgh_progressive_hologram");
+    return CGH_OK;
+  }
+  if (form == CGH_FORM_TC_BF16X3 || form == CGH_FORM_TC_FP16X3)
+    return tc_progressive(p, coeffs, lists, d_counts, (float2*)holo, accumulate, form, st);
+  return cgh_fail(CGH_ERR_UNSUPPORTED, "cgh_progressive_hologram: unknown form %d", form);
+}
+
+int cgh_plain_direct(const cgh_plan* p, const uint8_t* intensity, const uint8_t* layer_idx, float* holo,
+                     void* stream) {
+  if (!p || !intensity || !layer_idx || !holo) return cgh_fail(CGH_ERR_ARG, "cgh_plain_direct: NULL argument");
+  CHECK_CUDA(launch_plain_direct(p, intensity, layer_idx, (float2*)holo, (cudaStream_t)stream),
+             "cgh_plain_direct");
+  return CGH_OK;
+}
+
+int cgh_reconstruct(const cgh_plan* p, const float* holo, float* fields, const uint8_t* layer_idx,
+                    float* amplitude, void* stream) {
+  if (!p || !holo) return cgh_fail(CGH_ERR_ARG, "cgh_reconstruct: NULL argument");
+  if (amplitude && !layer_idx) return cgh_fail(CGH_ERR_ARG, "cgh_reconstruct: amplitude needs layer_idx");
+  if (!fields && !amplitude) return cgh_fail(CGH_ERR_ARG, "cgh_reconstruct: nothing to compute");
+  return tc_reconstruct(p, (const float2*)holo, (float2*)fields, layer_idx, amplitude, (cudaStream_t)stream);
+}
+
+int cgh_status(const cgh_plan* p, int* status_out, void* stream) {
+  if (!p || !status_out) return cgh_fail(CGH_ERR_ARG, "cgh_status: NULL argument");
+  int v = 0;
+  CHECK_CUDA(cudaMemcpyAsync(&v, p->d_status, sizeof(int), cudaMemcpyDeviceToHost, (cudaStream_t)stream),
+             "cgh_status: read");
+  CHECK_CUDA(cudaMemsetAsync(p->d_status, 0, sizeof(int), (cudaStream_t)stream), "cgh_status: clear");
+  CHECK_CUDA(cudaStreamSynchronize((cudaStream_t)stream), "cgh_status: sync");
+  *status_out = v;
+  return CGH_OK;
+}
+
+}  // extern "C"

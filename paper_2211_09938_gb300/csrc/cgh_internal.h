@@ -1,0 +1,66 @@
+// Internal declarations shared by the translation units of libcgh.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/cgh.h"
+
+#define CGH_MAX_LAYERS 64
+#define CGH_LEVELS 3
+
+// Offsets of the four tables kept per layer: level l (0..3) x kind (0 = b, 1 = w).
+#define CGH_TAB_PER_LAYER 8
+
+struct cgh_plan {
+  int obj_h, obj_w, holo_h, holo_w, s, n_layers, levels;
+  double pitch, wavelength;
+  double z[CGH_MAX_LAYERS];
+  double a_frac[CGH_MAX_LAYERS];     // frac(a_z) in [0,1)
+  uint64_t a_fixed[CGH_MAX_LAYERS];  // round(frac(a_z) * 2^64)
+  int device;
+
+  // Fringe tables: float2 tab[Z][4 levels][2 kinds][tab_len], offset d -> index d + tab_off.
+  int tab_len, tab_off;
+  float2* d_tab;
+  double* d_a_frac;
+  unsigned long long* d_a_fixed;
+
+  // Status word for bounded device waits.
+  int* d_status;
+
+  // Scratch for block compaction: per (layer, chunk) counts and offsets.
+  int* d_chunk_cnt;
+  int* d_chunk_off;
+  int max_chunks;
+
+  // Separable tensor-core path (allocated lazily by the first call that needs it).
+  struct cgh_tc_state* tc;
+};
+
+// Thread-local error message helpers (cgh_api.cu).
+int cgh_fail(int code, const char* fmt, ...);
+int cgh_cuda_check(cudaError_t e, const char* what);
+
+// Chunk size (blocks) of the ordered compaction.
+#define CGH_SEL_CHUNK 1024
+
+// Kernel launchers (kernels_basic.cu).  All asynchronous on `st`.
+cudaError_t launch_build_tables(const cgh_plan* p, cudaStream_t st);
+cudaError_t launch_haar(const cgh_plan* p, const uint8_t* I, const uint8_t* L, int32_t* coef,
+                        cudaStream_t st);
+cudaError_t launch_select(int obj_h, int obj_w, int n_layers, const uint8_t* sal, const uint8_t* L,
+                          int threshold, int level, int32_t* list, int32_t* d_count, int capacity,
+                          int* chunk_cnt, int* chunk_off, cudaStream_t st);
+cudaError_t launch_direct_lut(const cgh_plan* p, const int32_t* coef, const int32_t* const* lists,
+                              const int32_t* d_counts, float2* holo, cudaStream_t st);
+cudaError_t launch_plain_direct(const cgh_plan* p, const uint8_t* I, const uint8_t* L, float2* holo,
+                                cudaStream_t st);
+int select_num_chunks(int obj_h, int obj_w, int level);
+
+// Separable tensor-core path (kernels_tc.cu).
+int tc_progressive(const cgh_plan* p, const int32_t* coef, const int32_t* const* lists,
+                   const int32_t* d_counts, float2* holo, int accumulate, int form, cudaStream_t st);
+int tc_reconstruct(const cgh_plan* p, const float2* holo, float2* fields, const uint8_t* L,
+                   float* amp, cudaStream_t st);
+void tc_destroy(cgh_plan* p);

@@ -1,0 +1,541 @@
+// Fringe tables, integer Haar DWT, saliency block selection, plain point-wise
+// hologram and the detail-basis direct superposition (CUDA cores).
+//
+// Paper: arXiv 2211.09938, Eq. 1 (point-source fringe, paraxial), Eq. 2 (Haar
+// expansion), Eq. 3 (superposition of basis holograms), Section 2 steps 1-5.
+#include <stdio.h>
+
+#include "cgh_internal.h"
+
+// ---------------------------------------------------------------------------
+// (A1) fringe tables.  tab[z][l][kind][idx], offset d = idx - tab_off:
+//   kind 0: b_l(d) = sum_{t<2^l} f_z(d - s t)
+//   kind 1: w_l(d) = sum_{t<2^(l-1)} f_z(d - s t) - sum_{2^(l-1)<=t<2^l} f_z(d - s t)
+// f_z(d) = exp(j 2 pi frac(a_z d^2)); the product a_z*d^2 and its reduction are FP64
+// with d^2 an exact integer (Eq. 1 under the paraxial approximation).
+__global__ void k_build_tables(float2* __restrict__ tab, const double* __restrict__ a_frac,
+                               int tab_len, int tab_off, int s) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= tab_len) return;
+  const int l = blockIdx.y >> 1, kind = blockIdx.y & 1, z = blockIdx.z;
+  const double az = a_frac[z];
+  const long long d = (long long)idx - tab_off;
+  const int n = 1 << l, half = n >> 1;
+  double re = 0.0, im = 0.0;
+  if (!(l == 0 && kind == 1)) {
+    for (int t = 0; t < n; ++t) {
+      const long long dd = d - (long long)s * t;
+      double x = az * (double)(dd * dd);
+      x -= rint(x);  // exact: |x| < 2^53 and x - rint(x) is representable
+      double sn, cs;
+      sincospi(2.0 * x, &sn, &cs);
+      if (kind == 1 && t >= half) {
+        re -= cs;
+        im -= sn;
+      } else {
+        re += cs;
+        im += sn;
+      }
+    }
+  }
+  tab[((size_t)(z * 4 + l) * 2 + kind) * tab_len + idx] = make_float2((float)re, (float)im);
+}
+
+cudaError_t launch_build_tables(const cgh_plan* p, cudaStream_t st) {
+  dim3 grid((p->tab_len + 255) / 256, 8, p->n_layers);
+  k_build_tables<<<grid, 256, 0, st>>>(p->d_tab, p->d_a_frac, p->tab_len, p->tab_off, p->s);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// (A2) three-level integer Haar DWT of every layer plane (Eq. 2, Section 2 step 1).
+// One thread per (8x8 block, layer).  The 2x2 cell [a b; c d] gives
+// S = a+b+c+d, X = a-b+c-d, Y = a+b-c-d, D = a-b-c+d; Mallat output.
+__global__ void __launch_bounds__(128) k_haar3(const uint8_t* __restrict__ I,
+                                               const uint8_t* __restrict__ L,
+                                               int32_t* __restrict__ coef, int H, int W) {
+  const int bx = blockIdx.x * blockDim.x + threadIdx.x;
+  const int by = blockIdx.y * blockDim.y + threadIdx.y;
+  const int z = blockIdx.z;
+  if (bx >= (W >> 3) || by >= (H >> 3)) return;
+  int a[8][8];
+#pragma unroll
+  for (int r = 0; r < 8; ++r) {
+    const size_t o = (size_t)(8 * by + r) * W + 8 * bx;
+    const uint2 iv = *reinterpret_cast<const uint2*>(I + o);
+    const uint2 lv = *reinterpret_cast<const uint2*>(L + o);
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      const unsigned iw = c < 4 ? iv.x : iv.y, lw = c < 4 ? lv.x : lv.y;
+      const int sh = 8 * (c & 3);
+      a[r][c] = (((lw >> sh) & 0xFF) == (unsigned)z) ? (int)((iw >> sh) & 0xFF) : 0;
+    }
+  }
+  int s1[4][4], x1[4][4], y1[4][4], d1[4][4];
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int A = a[2 * r][2 * c], B = a[2 * r][2 * c + 1], C = a[2 * r + 1][2 * c],
+                D = a[2 * r + 1][2 * c + 1];
+      s1[r][c] = A + B + C + D;
+      x1[r][c] = A - B + C - D;
+      y1[r][c] = A + B - C - D;
+      d1[r][c] = A - B - C + D;
+    }
+  int s2[2][2], x2[2][2], y2[2][2], d2[2][2];
+#pragma unroll
+  for (int r = 0; r < 2; ++r)
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      const int A = s1[2 * r][2 * c], B = s1[2 * r][2 * c + 1], C = s1[2 * r + 1][2 * c],
+                D = s1[2 * r + 1][2 * c + 1];
+      s2[r][c] = A + B + C + D;
+      x2[r][c] = A - B + C - D;
+      y2[r][c] = A + B - C - D;
+      d2[r][c] = A - B - C + D;
+    }
+  const int A = s2[0][0], B = s2[0][1], C = s2[1][0], D = s2[1][1];
+  int32_t* P = coef + (size_t)z * H * W;
+  const int h1 = H >> 1, w1 = W >> 1, h2 = H >> 2, w2 = W >> 2, h3 = H >> 3, w3 = W >> 3;
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    *reinterpret_cast<int4*>(P + (size_t)(4 * by + r) * W + w1 + 4 * bx) =
+        make_int4(x1[r][0], x1[r][1], x1[r][2], x1[r][3]);
+    *reinterpret_cast<int4*>(P + (size_t)(h1 + 4 * by + r) * W + 4 * bx) =
+        make_int4(y1[r][0], y1[r][1], y1[r][2], y1[r][3]);
+    *reinterpret_cast<int4*>(P + (size_t)(h1 + 4 * by + r) * W + w1 + 4 * bx) =
+        make_int4(d1[r][0], d1[r][1], d1[r][2], d1[r][3]);
+  }
+#pragma unroll
+  for (int r = 0; r < 2; ++r) {
+    *reinterpret_cast<int2*>(P + (size_t)(2 * by + r) * W + w2 + 2 * bx) = make_int2(x2[r][0], x2[r][1]);
+    *reinterpret_cast<int2*>(P + (size_t)(h2 + 2 * by + r) * W + 2 * bx) = make_int2(y2[r][0], y2[r][1]);
+    *reinterpret_cast<int2*>(P + (size_t)(h2 + 2 * by + r) * W + w2 + 2 * bx) =
+        make_int2(d2[r][0], d2[r][1]);
+  }
+  P[(size_t)by * W + bx] = A + B + C + D;
+  P[(size_t)by * W + w3 + bx] = A - B + C - D;
+  P[(size_t)(h3 + by) * W + bx] = A + B - C - D;
+  P[(size_t)(h3 + by) * W + w3 + bx] = A - B - C + D;
+}
+
+cudaError_t launch_haar(const cgh_plan* p, const uint8_t* I, const uint8_t* L, int32_t* coef,
+                        cudaStream_t st) {
+  dim3 block(32, 4);
+  dim3 grid(((p->obj_w >> 3) + 31) / 32, ((p->obj_h >> 3) + 3) / 4, p->n_layers);
+  k_haar3<<<grid, block, 0, st>>>(I, L, coef, p->obj_h, p->obj_w);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// (A3) saliency block maximum, selection and ordered compaction (Section 2 steps 1-5).
+// A block is summarised by the bit mask of the layers it may contribute to: the layers
+// owning one of its pixels, cleared when the block maximum of the saliency does not
+// exceed the threshold.
+__device__ __forceinline__ unsigned long long block_layer_mask(const uint8_t* __restrict__ sal,
+                                                               const uint8_t* __restrict__ L,
+                                                               int W, int k, int by, int bx,
+                                                               int threshold, int Z) {
+  unsigned long long occ = 0ull;
+  int mx = 0;
+  for (int r = 0; r < k; ++r) {
+    const size_t o = (size_t)(by * k + r) * W + (size_t)bx * k;
+    for (int c = 0; c < k; ++c) {
+      const int lz = L[o + c];
+      if (lz < Z) occ |= 1ull << lz;
+      if (sal) mx = max(mx, (int)sal[o + c]);
+    }
+  }
+  if (threshold >= 0 && mx <= threshold) occ = 0ull;
+  return occ;
+}
+
+int select_num_chunks(int obj_h, int obj_w, int level) {
+  const long long nb = (long long)(obj_h >> level) * (obj_w >> level);
+  return (int)((nb + CGH_SEL_CHUNK - 1) / CGH_SEL_CHUNK);
+}
+
+// Pass 1: per (chunk, layer) counts.  256 threads, CGH_SEL_CHUNK blocks per CTA.
+__global__ void __launch_bounds__(256) k_select_count(const uint8_t* __restrict__ sal,
+                                                      const uint8_t* __restrict__ L, int H, int W,
+                                                      int Z, int threshold, int level,
+                                                      int* __restrict__ chunk_cnt) {
+  __shared__ int s_cnt[CGH_MAX_LAYERS];
+  const int k = 1 << level, nbx = W >> level, nb = (H >> level) * nbx;
+  const int chunk = blockIdx.x, nchunks = gridDim.x;
+  for (int t = threadIdx.x; t < Z; t += blockDim.x) s_cnt[t] = 0;
+  __syncthreads();
+  unsigned long long m[CGH_SEL_CHUNK / 256];
+#pragma unroll
+  for (int q = 0; q < CGH_SEL_CHUNK / 256; ++q) {
+    const int b = chunk * CGH_SEL_CHUNK + q * 256 + threadIdx.x;
+    m[q] = b < nb ? block_layer_mask(sal, L, W, k, b / nbx, b % nbx, threshold, Z) : 0ull;
+  }
+  for (int z = 0; z < Z; ++z) {
+    int c = 0;
+#pragma unroll
+    for (int q = 0; q < CGH_SEL_CHUNK / 256; ++q) c += (int)((m[q] >> z) & 1ull);
+    c = __reduce_add_sync(0xffffffffu, c);
+    if ((threadIdx.x & 31) == 0 && c) atomicAdd(&s_cnt[z], c);
+  }
+  __syncthreads();
+  for (int z = threadIdx.x; z < Z; z += blockDim.x) chunk_cnt[z * nchunks + chunk] = s_cnt[z];
+}
+
+// Pass 2: exclusive scan of the counts in (layer, chunk) order; one CTA of 1024 threads.
+__global__ void __launch_bounds__(1024) k_select_scan(const int* __restrict__ chunk_cnt,
+                                                      int* __restrict__ chunk_off, int n,
+                                                      int capacity, int32_t* __restrict__ d_count) {
+  __shared__ int s_part[1024];
+  const int per = (n + 1023) / 1024;
+  const int lo = threadIdx.x * per, hi = min(n, lo + per);
+  int sum = 0;
+  for (int i = lo; i < hi; ++i) sum += chunk_cnt[i];
+  s_part[threadIdx.x] = sum;
+  __syncthreads();
+  for (int off = 1; off < 1024; off <<= 1) {  // inclusive Hillis-Steele scan
+    const int v = threadIdx.x >= off ? s_part[threadIdx.x - off] : 0;
+    __syncthreads();
+    s_part[threadIdx.x] += v;
+    __syncthreads();
+  }
+  int run = s_part[threadIdx.x] - sum;
+  for (int i = lo; i < hi; ++i) {
+    chunk_off[i] = run;
+    run += chunk_cnt[i];
+  }
+  if (threadIdx.x == 1023) {
+    const int total = s_part[1023];
+    d_count[0] = min(total, capacity);
+    d_count[1] = total;
+  }
+}
+
+// Pass 3: ordered scatter.  One thread per block of the chunk; per layer a warp ballot
+// gives the rank inside the warp and a shared scan the warp offsets.
+__global__ void __launch_bounds__(CGH_SEL_CHUNK) k_select_scatter(
+    const uint8_t* __restrict__ sal, const uint8_t* __restrict__ L, int H, int W, int Z,
+    int threshold, int level, const int* __restrict__ chunk_cnt, const int* __restrict__ chunk_off,
+    int32_t* __restrict__ list, int capacity) {
+  __shared__ int s_warp[CGH_SEL_CHUNK / 32];
+  const int k = 1 << level, nbx = W >> level, nb = (H >> level) * nbx;
+  const int chunk = blockIdx.x, nchunks = gridDim.x;
+  const int b = chunk * CGH_SEL_CHUNK + threadIdx.x;
+  const int by = b / nbx, bx = b - by * nbx;
+  const unsigned long long m =
+      b < nb ? block_layer_mask(sal, L, W, k, by, bx, threshold, Z) : 0ull;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int z = 0; z < Z; ++z) {
+    if (chunk_cnt[z * nchunks + chunk] == 0) continue;  // uniform over the CTA
+    const bool f = (m >> z) & 1ull;
+    const unsigned bal = __ballot_sync(0xffffffffu, f);
+    if (lane == 0) s_warp[warp] = __popc(bal);
+    __syncthreads();
+    if (warp == 0) {
+      const int v = s_warp[lane];
+      int inc = v;
+#pragma unroll
+      for (int off = 1; off < 32; off <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, inc, off);
+        if (lane >= off) inc += t;
+      }
+      s_warp[lane] = inc - v;
+    }
+    __syncthreads();
+    if (f) {
+      const int pos = chunk_off[z * nchunks + chunk] + s_warp[warp] +
+                      __popc(bal & ((1u << lane) - 1u));
+      if (pos < capacity) list[pos] = (z << 24) | (by << 12) | bx;
+    }
+    __syncthreads();
+  }
+}
+
+cudaError_t launch_select(int obj_h, int obj_w, int n_layers, const uint8_t* sal, const uint8_t* L,
+                          int threshold, int level, int32_t* list, int32_t* d_count, int capacity,
+                          int* chunk_cnt, int* chunk_off, cudaStream_t st) {
+  const int nchunks = select_num_chunks(obj_h, obj_w, level);
+  k_select_count<<<nchunks, 256, 0, st>>>(sal, L, obj_h, obj_w, n_layers, threshold, level, chunk_cnt);
+  k_select_scan<<<1, 1024, 0, st>>>(chunk_cnt, chunk_off, nchunks * n_layers, capacity, d_count);
+  k_select_scatter<<<nchunks, CGH_SEL_CHUNK, 0, st>>>(sal, L, obj_h, obj_w, n_layers, threshold,
+                                                      level, chunk_cnt, chunk_off, list, capacity);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// (A5) plain point-wise hologram (Eq. 1): one SFU sine/cosine per (point, pixel).
+// The phase a_z*(dm^2 + dn^2) mod 1 is exact in 64-bit fixed point: with
+// A = round(frac(a_z) 2^64) and q = dm^2 + dn^2 < 2^31, the top 32 bits of A*q mod 2^64
+// are umulhi(A_lo, q) + A_hi*q (mod 2^32).  Their top 23 bits (rounded) become a float
+// in [-1/2, 1/2) cycles through the exponent trick (no int-to-float conversion).
+#define PD_TM 32
+#define PD_TN 64
+#define PD_CHUNK 256
+
+__global__ void __launch_bounds__(256) k_plain_direct(const uint8_t* __restrict__ I,
+                                                      const uint8_t* __restrict__ L, int H, int W,
+                                                      int Z, int s, const unsigned long long* a_fixed,
+                                                      float2* __restrict__ holo, int HH, int HW) {
+  __shared__ int4 s_pt[PD_CHUNK];  // (s*i, s*j, amp bits, layer)
+  __shared__ unsigned s_alo[CGH_MAX_LAYERS], s_ahi[CGH_MAX_LAYERS];
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int m0 = blockIdx.y * PD_TM, n0 = blockIdx.x * PD_TN;
+  if (threadIdx.x < Z) {
+    s_alo[threadIdx.x] = (unsigned)(a_fixed[threadIdx.x] & 0xffffffffull);
+    s_ahi[threadIdx.x] = (unsigned)(a_fixed[threadIdx.x] >> 32);
+  }
+  int mm[2], nn[4];
+#pragma unroll
+  for (int r = 0; r < 2; ++r) mm[r] = m0 + ty + 16 * r;
+#pragma unroll
+  for (int c = 0; c < 4; ++c) nn[c] = n0 + tx + 16 * c;
+  float re[2][4], im[2][4];
+#pragma unroll
+  for (int r = 0; r < 2; ++r)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) re[r][c] = im[r][c] = 0.f;
+  const int npts = H * W;
+  for (int base = 0; base < npts; base += PD_CHUNK) {
+    __syncthreads();
+    {
+      const int p = base + threadIdx.x;
+      int4 v = make_int4(0, 0, 0, 0);
+      if (p < npts) {
+        const int i = p / W, j = p - (p / W) * W;
+        const int lz = L[p];
+        const float amp = lz < Z ? (float)I[p] : 0.f;
+        v = make_int4(s * i, s * j, __float_as_int(amp), lz < Z ? lz : 0);
+      }
+      s_pt[threadIdx.x] = v;
+    }
+    __syncthreads();
+    const int cnt = min(PD_CHUNK, npts - base);
+    // Two-level accumulation: a chunk of points is summed in fresh registers and then
+    // added to the running total, which keeps the FP32 rounding error near
+    // u*(sqrt(chunk) + sqrt(points/chunk)) instead of u*sqrt(points).
+    float cre[2][4], cim[2][4];
+#pragma unroll
+    for (int r = 0; r < 2; ++r)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) cre[r][c] = cim[r][c] = 0.f;
+#pragma unroll 2
+    for (int k = 0; k < cnt; ++k) {
+      const int4 pt = s_pt[k];
+      const float amp = __int_as_float(pt.z);
+      const unsigned alo = s_alo[pt.w], ahi = s_ahi[pt.w];
+      unsigned dx2[2], dy2[4];
+#pragma unroll
+      for (int r = 0; r < 2; ++r) {
+        const int d = mm[r] - pt.x;
+        dx2[r] = (unsigned)(d * d);
+      }
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const int d = nn[c] - pt.y;
+        dy2[c] = (unsigned)(d * d);
+      }
+#pragma unroll
+      for (int r = 0; r < 2; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          const unsigned q = dx2[r] + dy2[c];
+          const unsigned ph = __umulhi(alo, q) + ahi * q + 256u;  // +half LSB of the 23-bit cut
+          const float cyc = __int_as_float(((ph >> 9) ^ 0x400000u) | 0x3f800000u) - 1.5f;
+          float sn, cs;
+          __sincosf(cyc * 6.28318530717958647692f, &sn, &cs);
+          cre[r][c] = fmaf(amp, cs, cre[r][c]);
+          cim[r][c] = fmaf(amp, sn, cim[r][c]);
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < 2; ++r)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        re[r][c] += cre[r][c];
+        im[r][c] += cim[r][c];
+      }
+  }
+#pragma unroll
+  for (int r = 0; r < 2; ++r)
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+      if (mm[r] < HH && nn[c] < HW) holo[(size_t)mm[r] * HW + nn[c]] = make_float2(re[r][c], im[r][c]);
+}
+
+cudaError_t launch_plain_direct(const cgh_plan* p, const uint8_t* I, const uint8_t* L, float2* holo,
+                                cudaStream_t st) {
+  dim3 grid((p->holo_w + PD_TN - 1) / PD_TN, (p->holo_h + PD_TM - 1) / PD_TM);
+  k_plain_direct<<<grid, 256, 0, st>>>(I, L, p->obj_h, p->obj_w, p->n_layers, p->s, p->d_a_fixed,
+                                       holo, p->holo_h, p->holo_w);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// (A4, direct form) detail-basis superposition on CUDA cores (Eq. 3, Section 2 steps 2-5).
+// Every LLL block adds the rank-1 term  b_3(m-u) x (LLL/64) b_3(n-v); every selected
+// detail block of level l adds the rank-2 update
+//     b_l(m-u) x 4^-l X w_l(n-v)  +  w_l(m-u) x 4^-l (Y b_l(n-v) + D w_l(n-v)),
+// (X pairs with the column difference, Y with the row difference).  A CTA owns a
+// 128x128 hologram tile and a 1/S share of every list (split over the grid's z),
+// stages 32 rank-1 terms at a time in shared memory as row and column factors and
+// accumulates 8x8 complex pixels per thread in registers (4 FFMA per term and pixel).
+#define DL_TM 128
+#define DL_TN 128
+#define DL_KC 32
+
+struct DlTerm {
+  int row_base;  // table index of (row factor) at m = 0
+  int col_b;     // table index of b_l at n = 0
+  int col_w;     // table index of w_l at n = 0
+  float cb, cw;  // column factor = cb*b_l + cw*w_l
+};
+
+__global__ void __launch_bounds__(256, 1) k_direct_lut(
+    const float2* __restrict__ tab, int tab_len, int tab_off, const int32_t* __restrict__ coef,
+    const int32_t* __restrict__ l0, const int32_t* __restrict__ l1, const int32_t* __restrict__ l2,
+    const int32_t* __restrict__ l3, const int32_t* __restrict__ d_counts, int H, int W, int Z, int s,
+    float2* __restrict__ holo, int HH, int HW, int use_atomic) {
+  extern __shared__ float2 dl_smem[];
+  float2* Rs = dl_smem;                  // [DL_KC][DL_TM]
+  float2* Cs = dl_smem + DL_KC * DL_TM;  // [DL_KC][DL_TN]
+  __shared__ DlTerm s_term[DL_KC];
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int m0 = blockIdx.y * DL_TM, n0 = blockIdx.x * DL_TN;
+  const int split = blockIdx.z, nsplit = gridDim.z;
+  float acc[8][8][2];
+#pragma unroll
+  for (int r = 0; r < 8; ++r)
+#pragma unroll
+    for (int c = 0; c < 8; ++c) acc[r][c][0] = acc[r][c][1] = 0.f;
+
+  const int32_t* lists[4] = {l0, l1, l2, l3};
+  for (int li = 0; li < 4; ++li) {
+    const int level = li == 0 ? 3 : li;
+    const bool lll = li == 0;
+    const int cnt = max(0, d_counts[2 * li]);
+    const int e0 = (int)((long long)cnt * split / nsplit);
+    const int e1 = (int)((long long)cnt * (split + 1) / nsplit);
+    const int per = lll ? DL_KC : DL_KC / 2;  // entries per chunk
+    const int hl = H >> level, wl = W >> level;
+    const float kappa = 1.0f / (float)(1 << (2 * level));
+    const int32_t* lst = lists[li];
+    for (int e = e0; e < e1; e += per) {
+      const int ne = min(per, e1 - e);
+      const int nt = lll ? ne : 2 * ne;
+      __syncthreads();  // previous chunk fully consumed
+      if (threadIdx.x < ne) {
+        const int ent = lst[e + threadIdx.x];
+        int z = (ent >> 24) & 0x7F, by = (ent >> 12) & 0xFFF, bx = ent & 0xFFF;
+        // An entry outside the plan (corrupt list) adds nothing instead of reading out of bounds.
+        const bool ok = z < Z && by < hl && bx < wl;
+        if (!ok) z = by = bx = 0;
+        const int32_t* P = coef + (size_t)z * H * W;
+        const int u = s * (by << level), v = s * (bx << level);
+        const int tb = ((z * 4 + level) * 2 + 0) * tab_len + tab_off;
+        const int tw = ((z * 4 + level) * 2 + 1) * tab_len + tab_off;
+        if (lll) {
+          const float S3 = ok ? (float)P[(size_t)by * W + bx] : 0.f;
+          s_term[threadIdx.x] = DlTerm{tb - u, tb - v, tw - v, kappa * S3, 0.f};
+        } else {
+          const float X = ok ? (float)P[(size_t)by * W + wl + bx] : 0.f;
+          const float Y = ok ? (float)P[(size_t)(hl + by) * W + bx] : 0.f;
+          const float D = ok ? (float)P[(size_t)(hl + by) * W + wl + bx] : 0.f;
+          s_term[2 * threadIdx.x] = DlTerm{tb - u, tb - v, tw - v, 0.f, kappa * X};
+          s_term[2 * threadIdx.x + 1] = DlTerm{tw - u, tb - v, tw - v, kappa * Y, kappa * D};
+        }
+      }
+      __syncthreads();
+      for (int q = threadIdx.x; q < nt * DL_TM; q += 256) {
+        const int k = q / DL_TM, r = q - k * DL_TM;
+        const DlTerm t = s_term[k];
+        const int m = m0 + r, n = n0 + r;
+        float2 rv = make_float2(0.f, 0.f), cv = make_float2(0.f, 0.f);
+        if (m < HH) rv = tab[t.row_base + m];
+        if (n < HW) {
+          const float2 b = tab[t.col_b + n], w = tab[t.col_w + n];
+          cv = make_float2(t.cb * b.x + t.cw * w.x, t.cb * b.y + t.cw * w.y);
+        }
+        Rs[k * DL_TM + r] = rv;
+        Cs[k * DL_TN + r] = cv;
+      }
+      __syncthreads();
+#pragma unroll 2
+      for (int k = 0; k < nt; ++k) {
+        float2 rv[8], cv[8];
+#pragma unroll
+        for (int r = 0; r < 8; ++r) rv[r] = Rs[k * DL_TM + ty + 16 * r];
+#pragma unroll
+        for (int c = 0; c < 8; ++c) cv[c] = Cs[k * DL_TN + tx + 16 * c];
+#pragma unroll
+        for (int r = 0; r < 8; ++r)
+#pragma unroll
+          for (int c = 0; c < 8; ++c) {
+            acc[r][c][0] = fmaf(rv[r].x, cv[c].x, acc[r][c][0]);
+            acc[r][c][0] = fmaf(-rv[r].y, cv[c].y, acc[r][c][0]);
+            acc[r][c][1] = fmaf(rv[r].x, cv[c].y, acc[r][c][1]);
+            acc[r][c][1] = fmaf(rv[r].y, cv[c].x, acc[r][c][1]);
+          }
+      }
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < 8; ++r)
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      const int m = m0 + ty + 16 * r, n = n0 + tx + 16 * c;
+      if (m < HH && n < HW) {
+        float2* dst = holo + (size_t)m * HW + n;
+        if (use_atomic)
+          atomicAdd(dst, make_float2(acc[r][c][0], acc[r][c][1]));
+        else
+          *dst = make_float2(acc[r][c][0], acc[r][c][1]);
+      }
+    }
+}
+
+static int g_num_sms = 0;
+
+static int num_sms() {
+  if (!g_num_sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (g_num_sms <= 0) g_num_sms = 148;
+  }
+  return g_num_sms;
+}
+
+// Number of term splits: the smallest S (<= 64) whose CTA count S*tiles fills at least
+// two waves of one CTA per SM with a tail under 5%, else the best found.
+static int direct_lut_splits(int tiles) {
+  const int sms = num_sms();
+  int best = 1;
+  double best_eff = 0.0;
+  for (int S = 1; S <= 64; ++S) {
+    const long long ctas = (long long)S * tiles;
+    const double waves = (double)ctas / sms;
+    const double eff = waves / ceil(waves);
+    if (ctas >= 2LL * sms && eff >= 0.95) return S;
+    if (eff > best_eff + 1e-9) {
+      best_eff = eff;
+      best = S;
+    }
+  }
+  return best;
+}
+
+cudaError_t launch_direct_lut(const cgh_plan* p, const int32_t* coef, const int32_t* const* lists,
+                              const int32_t* d_counts, float2* holo, cudaStream_t st) {
+  const int tn = (p->holo_w + DL_TN - 1) / DL_TN, tm = (p->holo_h + DL_TM - 1) / DL_TM;
+  const int S = direct_lut_splits(tn * tm);
+  const size_t smem = (size_t)DL_KC * (DL_TM + DL_TN) * sizeof(float2);
+  cudaError_t e = cudaFuncSetAttribute(k_direct_lut, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  dim3 grid(tn, tm, S);
+  // holo must be zero (or hold the previous hologram) when S > 1: atomics accumulate.
+  k_direct_lut<<<grid, 256, smem, st>>>(p->d_tab, p->tab_len, p->tab_off, coef, lists[0], lists[1],
+                                        lists[2], lists[3], d_counts, p->obj_h, p->obj_w, p->n_layers, p->s, holo,
+                                        p->holo_h, p->holo_w, 1);
+  return cudaGetLastError();
+}

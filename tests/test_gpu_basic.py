@@ -1,0 +1,238 @@
+"""GPU parity of the DWT, block selection, direct superposition and plain point-wise
+kernels against the FP64 oracle, through the C ABI (ctypes binding).
+
+Bars: bit-exact for DWT coefficients and work lists; relative L2 error <= 1e-5 for
+the FP32 holograms against FP64."""
+import numpy as np
+import pytest
+
+from oracle import cgh_oracle as O
+from synth import scenes
+
+pytestmark = pytest.mark.gpu
+
+FP32_TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2211_09938_gb300 import build_lib, cgh
+    import os
+    if not os.path.exists(cgh.LIB_PATH):
+        build_lib.build()
+    cgh.lib()
+    return torch
+
+
+def dev(torch, a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def plan_for(sc):
+    from paper_2211_09938_gb300 import Plan
+    return Plan.for_scene(sc)
+
+
+SCENES = {
+    "tiny_64_to_256_z4": lambda: scenes.tiny_scene(),
+    "ragged_40x24_s3_z3": lambda: _rect_scene(40, 24, 3, 3, seed=77),
+    "single_layer_32_s2": lambda: scenes.random_scene(78, 32, 64, 1, graded=True),
+    "graded_64_s2_z5": lambda: scenes.random_scene(79, 64, 128, 5, graded=True),
+}
+
+
+def _rect_scene(h, w, s, nl, seed):
+    rng = np.random.default_rng(seed)
+    sc = scenes.random_scene(seed, max(h, w), s * max(h, w), nl, graded=True)
+    sc["intensity"] = np.ascontiguousarray(sc["intensity"][:h, :w])
+    sc["layer"] = np.ascontiguousarray(rng.integers(0, nl, size=(h, w)).astype(np.uint8))
+    sc["saliency"] = np.ascontiguousarray(sc["saliency"][:h, :w])
+    sc["holo"] = (s * h, s * w)
+    return sc
+
+
+def _geom(sc):
+    return O.geometry_of(sc)
+
+
+@pytest.mark.parametrize("name", list(SCENES))
+def test_haar_bit_exact(torch_cuda, name):
+    torch = torch_cuda
+    sc = SCENES[name]()
+    plan = plan_for(sc)
+    C = plan.haar_decompose(dev(torch, sc["intensity"]), dev(torch, sc["layer"])).cpu().numpy()
+    planes = O.object_planes(sc["intensity"], sc["layer"], plan.n_layers)
+    for z in range(plan.n_layers):
+        assert np.array_equal(C[z], O.haar_forward(planes[z], 3)), z
+
+
+def test_haar_bit_exact_paper_scale(torch_cuda):
+    torch = torch_cuda
+    sc = scenes.paper_scene()
+    plan = plan_for(sc)
+    C = plan.haar_decompose(dev(torch, sc["intensity"]), dev(torch, sc["layer"])).cpu().numpy()
+    planes = O.object_planes(sc["intensity"], sc["layer"], plan.n_layers)
+    for z in range(plan.n_layers):
+        assert np.array_equal(C[z], O.haar_forward(planes[z], 3)), z
+
+
+@pytest.mark.parametrize("name", list(SCENES))
+def test_select_bit_exact(torch_cuda, name):
+    torch = torch_cuda
+    sc = SCENES[name]()
+    plan = plan_for(sc)
+    S, L = dev(torch, sc["saliency"]), dev(torch, sc["layer"])
+    for level in (1, 2, 3):
+        for t in (-1, 0, 127, 178, 229, 255):
+            lst, cnt = plan.select_blocks(S, L, t, level)
+            c = cnt.cpu().numpy()
+            ref = O.select_blocks(sc["saliency"], sc["layer"], plan.n_layers, t, level)
+            assert c[0] == c[1] == len(ref), (level, t, c, len(ref))
+            assert np.array_equal(lst[:c[0]].cpu().numpy(), ref), (level, t)
+
+
+def test_select_paper_scale_and_capacity(torch_cuda):
+    torch = torch_cuda
+    sc = scenes.paper_scene()
+    plan = plan_for(sc)
+    S, L = dev(torch, sc["saliency"]), dev(torch, sc["layer"])
+    ref_lists = O.progressive_lists(sc["saliency"], sc["layer"], plan.n_layers, scenes.THRESHOLDS_U8)
+    lists, counts = plan.progressive_lists(S, L, scenes.THRESHOLDS_U8)
+    c = counts.cpu().numpy()
+    for k in range(4):
+        assert c[k, 0] == c[k, 1] == len(ref_lists[k])
+        assert np.array_equal(lists[k][:c[k, 0]].cpu().numpy(), ref_lists[k])
+    # capacity overflow: the first `capacity` entries, the true total reported
+    cap = len(ref_lists[1]) // 3
+    out = torch.full((cap + 4,), -7, dtype=torch.int32, device="cuda")
+    lst, cnt = plan.select_blocks(S, L, scenes.THRESHOLDS_U8[1], 1, out=out, capacity=cap)
+    c = cnt.cpu().numpy()
+    assert c[0] == cap and c[1] == len(ref_lists[1])
+    got = lst.cpu().numpy()
+    assert np.array_equal(got[:cap], ref_lists[1][:cap])
+    assert np.all(got[cap:] == -7)  # nothing written past the capacity
+
+
+def test_select_empty_and_zero_capacity(torch_cuda):
+    torch = torch_cuda
+    sc = scenes.tiny_scene()
+    plan = plan_for(sc)
+    S = torch.zeros(sc["saliency"].shape, dtype=torch.uint8, device="cuda")
+    L = dev(torch, sc["layer"])
+    lst, cnt = plan.select_blocks(S, L, 0, 1)
+    assert cnt.cpu().numpy().tolist() == [0, 0]
+    out = torch.empty(1, dtype=torch.int32, device="cuda")
+    lst, cnt = plan.select_blocks(dev(torch, sc["saliency"]), L, -1, 2, out=out, capacity=0)
+    c = cnt.cpu().numpy()
+    assert c[0] == 0 and c[1] == len(O.select_blocks(sc["saliency"], sc["layer"], 4, -1, 2))
+
+
+def run_progressive(torch, sc, form="direct_lut", thresholds=None, lists_override=None):
+    plan = plan_for(sc)
+    I, L, S = dev(torch, sc["intensity"]), dev(torch, sc["layer"]), dev(torch, sc["saliency"])
+    coeffs = plan.haar_decompose(I, L)
+    thr = thresholds or scenes.THRESHOLDS_U8
+    if lists_override is None:
+        lists, counts = plan.progressive_lists(S, L, thr)
+        ref_lists = O.progressive_lists(sc["saliency"], sc["layer"], plan.n_layers, thr)
+    else:
+        ref_lists = lists_override
+        lists = [dev(torch, np.concatenate([x, np.zeros(1, np.int32)]).astype(np.int32)) for x in ref_lists]
+        counts = dev(torch, np.array([[len(x), len(x)] for x in ref_lists], np.int32))
+    H = plan.progressive_hologram(coeffs, lists, counts, form=form)
+    torch.cuda.synchronize()
+    return plan, H.cpu().numpy(), ref_lists
+
+
+@pytest.mark.parametrize("name", list(SCENES))
+def test_progressive_direct_lut(torch_cuda, name):
+    sc = SCENES[name]()
+    _, H, ref_lists = run_progressive(torch_cuda, sc)
+    Href = O.progressive_hologram(sc["intensity"], sc["layer"], ref_lists, _geom(sc))
+    assert O.rel_l2(H, Href) <= FP32_TOL
+
+
+def test_progressive_direct_lut_mask_extremes(torch_cuda):
+    torch = torch_cuda
+    sc = scenes.random_scene(90, 32, 128, 3)
+    g = _geom(sc)
+    zero = np.zeros_like(sc["layer"])
+    all_lists = [O.select_blocks(zero, sc["layer"], 3, -1, 3)] + [
+        O.select_blocks(zero, sc["layer"], 3, -1, l) for l in (1, 2, 3)]
+    _, H, _ = run_progressive(torch, sc, lists_override=all_lists)
+    Hpw = O.plain_pointwise_hologram(sc["intensity"], sc["layer"], g)
+    assert O.rel_l2(H, Hpw) <= FP32_TOL
+    e = np.zeros(0, np.int32)
+    lll = [all_lists[0], e, e, e]
+    _, H0, _ = run_progressive(torch, sc, lists_override=lll)
+    assert O.rel_l2(H0, O.progressive_hologram(sc["intensity"], sc["layer"], lll, g)) <= FP32_TOL
+    none = [e, e, e, e]
+    _, Hn, _ = run_progressive(torch, sc, lists_override=none)
+    assert np.all(Hn == 0)
+
+
+def test_progressive_accumulate(torch_cuda):
+    torch = torch_cuda
+    sc = scenes.tiny_scene()
+    plan = plan_for(sc)
+    I, L, S = dev(torch, sc["intensity"]), dev(torch, sc["layer"]), dev(torch, sc["saliency"])
+    coeffs = plan.haar_decompose(I, L)
+    lists, counts = plan.progressive_lists(S, L, scenes.THRESHOLDS_U8)
+    H1 = plan.progressive_hologram(coeffs, lists, counts).clone()
+    H2 = plan.progressive_hologram(coeffs, lists, counts, holo=H1.clone(), accumulate=True)
+    torch.cuda.synchronize()
+    assert O.rel_l2(H2.cpu().numpy(), 2 * H1.cpu().numpy()) < 1e-6
+
+
+def test_progressive_direct_lut_paper_scale(torch_cuda):
+    sc = scenes.paper_scene()
+    _, H, ref_lists = run_progressive(torch_cuda, sc)
+    Href = O.progressive_hologram(sc["intensity"], sc["layer"], ref_lists, _geom(sc))
+    err = O.rel_l2(H, Href)
+    print(f"direct_lut 512->1024 Z16 rel-L2 {err:.3e}")
+    assert err <= FP32_TOL
+
+
+@pytest.mark.parametrize("name", ["tiny_64_to_256_z4", "ragged_40x24_s3_z3"])
+def test_plain_direct(torch_cuda, name):
+    torch = torch_cuda
+    sc = SCENES[name]()
+    plan = plan_for(sc)
+    H = plan.plain_direct(dev(torch, sc["intensity"]), dev(torch, sc["layer"]))
+    torch.cuda.synchronize()
+    Href = O.plain_pointwise_hologram(sc["intensity"], sc["layer"], _geom(sc))
+    assert O.rel_l2(H.cpu().numpy(), Href) <= FP32_TOL
+
+
+def test_plain_direct_paper_scale_sampled(torch_cuda):
+    """512->1024, 16 layers: 192 sampled pixels (corners, edges, random) against the
+    brute-force FP64 sum over all 262144 points."""
+    torch = torch_cuda
+    sc = scenes.paper_scene()
+    plan = plan_for(sc)
+    H = plan.plain_direct(dev(torch, sc["intensity"]), dev(torch, sc["layer"])).cpu().numpy()
+    rng = np.random.default_rng(5)
+    mm = np.concatenate([[0, 0, 1023, 1023, 511], rng.integers(0, 1024, 187)])
+    nn = np.concatenate([[0, 1023, 0, 1023, 512], rng.integers(0, 1024, 187)])
+    ref = O.plain_pointwise_hologram(sc["intensity"], sc["layer"], _geom(sc), pixels=(mm, nn))
+    err = O.rel_l2(H[mm, nn], ref)
+    print(f"plain direct sampled rel-L2 {err:.3e}")
+    assert err <= FP32_TOL
+
+
+def test_plain_direct_exact_reduction_large_offsets(torch_cuda):
+    """P8 on the GPU: a_z = 1/4 makes every fringe value 1 or j; one point in the
+    corner of a 512 -> 2048 geometry probes offsets up to 2047 (d^2 ~ 4.2e6)."""
+    torch = torch_cuda
+    from paper_2211_09938_gb300 import Plan
+    z = 8e-6 ** 2 / (2 * 532e-9 * 0.25)
+    plan = Plan((512, 512), (2048, 2048), 8e-6, 532e-9, [z])
+    I = np.zeros((512, 512), np.uint8)
+    I[0, 0] = 200
+    H = plan.plain_direct(dev(torch, I), dev(torch, np.zeros((512, 512), np.uint8))).cpu().numpy()
+    m = np.arange(2048)
+    exp = 200 * (1j ** ((m[:, None] % 2) + (m[None, :] % 2)))
+    assert np.max(np.abs(H - exp)) < 200 * 2e-6
