@@ -138,6 +138,31 @@ int cgh_select_blocks(const cgh_plan* plan, const uint8_t* saliency, const uint8
                       void* stream);
 
 /*
+ * cgh_select_blocks_noalloc - cgh_select_blocks without a plan and without allocating.
+ * The paper has no counterpart: this entry point exists for callers that cannot call
+ * cudaMalloc (for example code running inside a host callback, or an embedder whose
+ * device memory budget is fixed at start-up) and so cannot create a plan.
+ * Same selection, order, output format, d_count[2] semantics and bit-exact results as
+ * cgh_select_blocks for the same inputs.
+ *   obj_h, obj_w  object size (multiples of 8, 8..8192);  n_layers  Z, 1..64
+ *   other arguments as for cgh_select_blocks (device pointers, caller-owned)
+ * Scratch: a static device array built into the library (512 KiB per GPU that loads the
+ * library, held until the process exits).  Limit: n_layers * ceil(blocks at `level` /
+ * 1024) <= 65536, e.g. 64 layers of a 2048x2048 object at level 1; larger requests
+ * return CGH_ERR_ARG with a message and enqueue nothing.
+ * Allocates nothing: no cudaMalloc, no cudaFree, no allocating library routine.  The
+ * first call on each device looks up the array's device address with
+ * cudaGetSymbolAddress (with that device current), so make that first call before any
+ * stream capture.  All calls on a device share the one array: calls that may overlap on
+ * the GPU (different streams, or different host threads) race and must be serialised
+ * by the caller.
+ * Errors: CGH_ERR_ARG, CGH_ERR_UNSUPPORTED (device ordinal >= 64), CGH_ERR_CUDA.
+ */
+int cgh_select_blocks_noalloc(const uint8_t* saliency, const uint8_t* layer_idx, int obj_h, int obj_w,
+                              int n_layers, int threshold, int level, int32_t* list, int32_t* d_count,
+                              int capacity, void* stream);
+
+/*
  * cgh_progressive_hologram - progressive superposition of the selected blocks.
  * Paper: Eq. 3 (hologram = sum of the holograms of the Haar basis functions times their
  * coefficients) and Section 2 steps 2-5.

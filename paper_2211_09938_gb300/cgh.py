@@ -41,6 +41,7 @@ SIGNATURES = {
     "cgh_build_tables": (_I, [_P, _P]),
     "cgh_haar_decompose": (_I, [_P, _P, _P, _P, _P]),
     "cgh_select_blocks": (_I, [_P, _P, _P, _I, _I, _P, _P, _I, _P]),
+    "cgh_select_blocks_noalloc": (_I, [_P, _P, _I, _I, _I, _I, _I, _P, _P, _I, _P]),
     "cgh_progressive_hologram": (_I, [_P, _P, ctypes.POINTER(_P), _P, _P, _I, _I, _P]),
     "cgh_plain_direct": (_I, [_P, _P, _P, _P, _P]),
     "cgh_reconstruct": (_I, [_P, _P, _P, _P, _P, _P]),

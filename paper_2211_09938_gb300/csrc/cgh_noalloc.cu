@@ -1,0 +1,80 @@
+// Allocation-free variant of the block selection (cgh_select_blocks_noalloc).
+//
+// Some callers cannot call cudaMalloc: code that runs where the allocator is off
+// limits, such as a host callback or an embedder with a fixed, pre-reserved memory
+// budget that must not grow after start-up.  They cannot create a plan, because a plan
+// allocates its tables and scratch.  This entry point needs no plan.  Its only scratch,
+// the per-(layer, chunk) counts and offsets of the ordered compaction, lives in the
+// file-scope device array below.  The module loader places that array in device memory
+// when the library is loaded, and every GPU that loads the library keeps it until the
+// process exits.
+#include <mutex>
+
+#include "cgh_internal.h"
+
+// Capacity of the shared scratch in ints: counts in the first half, offsets in the
+// second.  n_layers * ceil(blocks_at_level / 1024) may not exceed the half.
+#define CGH_NOALLOC_HALF 65536
+
+static __device__ __align__(256) int g_noalloc_scratch[2 * CGH_NOALLOC_HALF];
+
+// Host-side device addresses of g_noalloc_scratch, one per device ordinal, filled by
+// the first call on that device.  The array's name in host code is only a stand-in for
+// the symbol and must never be handed to a kernel.
+#define CGH_NOALLOC_MAX_DEVICES 64
+static int* g_scratch_ptr[CGH_NOALLOC_MAX_DEVICES];
+static std::mutex g_scratch_mu;
+
+static int noalloc_scratch(int** out) {
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cgh_cuda_check(e, "cgh_select_blocks_noalloc: cudaGetDevice");
+  if (dev < 0 || dev >= CGH_NOALLOC_MAX_DEVICES)
+    return cgh_fail(CGH_ERR_UNSUPPORTED, "cgh_select_blocks_noalloc: device ordinal %d too large", dev);
+  std::lock_guard<std::mutex> lock(g_scratch_mu);
+  if (!g_scratch_ptr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);  // the current device is `dev`
+    if (e != cudaSuccess || !p)
+      return cgh_cuda_check(e != cudaSuccess ? e : cudaErrorInvalidSymbol,
+                            "cgh_select_blocks_noalloc: cudaGetSymbolAddress");
+    g_scratch_ptr[dev] = (int*)p;
+  }
+  *out = g_scratch_ptr[dev];
+  return CGH_OK;
+}
+
+extern "C" int cgh_select_blocks_noalloc(const uint8_t* saliency, const uint8_t* layer_idx, int obj_h,
+                                         int obj_w, int n_layers, int threshold, int level,
+                                         int32_t* list, int32_t* d_count, int capacity, void* stream) {
+  if (!layer_idx || !d_count || (capacity > 0 && !list))
+    return cgh_fail(CGH_ERR_ARG, "cgh_select_blocks_noalloc: NULL argument");
+  if (obj_h < 8 || obj_w < 8 || obj_h % 8 || obj_w % 8 || obj_h > 8192 || obj_w > 8192)
+    return cgh_fail(CGH_ERR_ARG, "cgh_select_blocks_noalloc: object %dx%d must be multiples of 8 in [8, 8192]",
+                    obj_h, obj_w);
+  if (n_layers < 1 || n_layers > CGH_MAX_LAYERS)
+    return cgh_fail(CGH_ERR_ARG, "cgh_select_blocks_noalloc: n_layers %d outside [1, %d]", n_layers,
+                    CGH_MAX_LAYERS);
+  if (level < 1 || level > CGH_LEVELS)
+    return cgh_fail(CGH_ERR_ARG, "cgh_select_blocks_noalloc: level %d not in 1..3", level);
+  if (threshold < -1 || threshold > 255)
+    return cgh_fail(CGH_ERR_ARG, "cgh_select_blocks_noalloc: threshold %d not in -1..255", threshold);
+  if (threshold >= 0 && !saliency)
+    return cgh_fail(CGH_ERR_ARG, "cgh_select_blocks_noalloc: saliency is NULL");
+  if (capacity < 0) return cgh_fail(CGH_ERR_ARG, "cgh_select_blocks_noalloc: capacity < 0");
+  const long long need = (long long)n_layers * select_num_chunks(obj_h, obj_w, level);
+  if (need > CGH_NOALLOC_HALF)
+    return cgh_fail(CGH_ERR_ARG,
+                    "cgh_select_blocks_noalloc: n_layers * ceil(blocks/1024) = %lld exceeds the static "
+                    "scratch limit of %d (e.g. 64 layers at 2048x2048, level 1); use cgh_select_blocks",
+                    need, CGH_NOALLOC_HALF);
+  int* scratch = nullptr;
+  int rc = noalloc_scratch(&scratch);
+  if (rc != CGH_OK) return rc;
+  // Every count and offset the kernels read is written earlier in the same call, so
+  // the contents left by a previous call need no clearing.
+  return cgh_cuda_check(launch_select(obj_h, obj_w, n_layers, threshold >= 0 ? saliency : NULL, layer_idx,
+                                      threshold, level, list, d_count, capacity, scratch,
+                                      scratch + CGH_NOALLOC_HALF, (cudaStream_t)stream),
+                        "cgh_select_blocks_noalloc");
+}
