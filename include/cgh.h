@@ -212,6 +212,20 @@ int cgh_reconstruct(const cgh_plan* plan, const float* holo, float* fields,
                     const uint8_t* layer_idx, float* amplitude, void* stream);
 
 /*
+ * cgh_tc_selftest_gemm - diagnostic: C = A * B^T through the tensor-core machinery of the
+ * separable form (TMA loads with 64-byte swizzle, shared-memory descriptors, tcgen05.mma
+ * with FP32 accumulation in tensor memory), one real product, no hi+lo split.
+ * The paper has no counterpart; it exists to test that machinery in isolation.
+ *   A       16-bit [M][K] row-major (bf16 or fp16 bit patterns), 16-byte aligned
+ *   B       16-bit [N][K] row-major, 16-byte aligned
+ *   C       float [M][N] output (overwritten)
+ *   K       a positive multiple of 32;  is_fp16  0 = bf16, 1 = fp16
+ * Errors: CGH_ERR_ARG, CGH_ERR_CUDA.
+ */
+int cgh_tc_selftest_gemm(const uint16_t* A, const uint16_t* B, float* C, int M, int N, int K, int is_fp16,
+                         void* stream);
+
+/*
  * cgh_status - read and clear the plan's device status word (synchronises `stream`).
  * Bounded device-side waits that give up record CGH_ERR_TIMEOUT there instead of
  * hanging.  *status_out receives CGH_OK or the recorded code.

@@ -46,6 +46,7 @@ SIGNATURES = {
     "cgh_plain_direct": (_I, [_P, _P, _P, _P, _P]),
     "cgh_reconstruct": (_I, [_P, _P, _P, _P, _P, _P]),
     "cgh_status": (_I, [_P, ctypes.POINTER(_I), _P]),
+    "cgh_tc_selftest_gemm": (_I, [_P, _P, _P, _I, _I, _I, _I, _P]),
 }
 
 _lib = None
@@ -202,3 +203,14 @@ class Plan:
         v = ctypes.c_int(0)
         check(lib().cgh_status(self.handle, ctypes.byref(v), _stream(stream)))
         return v.value
+
+
+def tc_selftest_gemm(A, B, fp16=False, stream=None):
+    """C = A @ B.T on the tcgen05 path (diagnostic); A [M,K], B [N,K] bf16/fp16 CUDA tensors."""
+    import torch
+    M, K = A.shape
+    N = B.shape[0]
+    C = torch.empty((M, N), dtype=torch.float32, device=A.device)
+    check(lib().cgh_tc_selftest_gemm(_ptr(A), _ptr(B), _ptr(C), M, N, K, 1 if fp16 else 0,
+                                     _stream(stream)))
+    return C

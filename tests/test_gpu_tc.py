@@ -1,0 +1,92 @@
+"""Tensor-core (tcgen05) separable form: the GEMM machinery against torch, then the
+progressive hologram against the FP64 oracle.
+
+Bars: the diagnostic GEMM is exact up to FP32 accumulation order (operands are exact
+bf16/fp16 values); the progressive hologram meets rel-L2 <= 1e-3 for the bf16 hi+lo
+path and <= 1e-5 for the fp16 hi+lo path."""
+import numpy as np
+import pytest
+
+from oracle import cgh_oracle as O
+from synth import scenes
+
+pytestmark = pytest.mark.gpu
+
+BF16X3_TOL = 1e-3
+FP16X3_TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    import os
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2211_09938_gb300 import build_lib, cgh
+    if not os.path.exists(cgh.LIB_PATH):
+        build_lib.build()
+    cgh.lib()
+    return torch
+
+
+@pytest.mark.parametrize("M,N,K", [(128, 128, 32), (200, 136, 96), (1024, 512, 512), (384, 640, 1024)])
+@pytest.mark.parametrize("fp16", [False, True])
+def test_selftest_gemm_matches_torch(torch_cuda, M, N, K, fp16):
+    torch = torch_cuda
+    from paper_2211_09938_gb300.cgh import tc_selftest_gemm
+    g = torch.Generator(device="cpu").manual_seed(M * 7 + N * 3 + K)
+    dt = torch.float16 if fp16 else torch.bfloat16
+    A = torch.randn(M, K, generator=g).to(dt)
+    B = torch.randn(N, K, generator=g).to(dt)
+    ref = A.double() @ B.double().T
+    ref_abs = A.double().abs() @ B.double().abs().T
+    C = tc_selftest_gemm(A.cuda().view(torch.int16), B.cuda().view(torch.int16), fp16=fp16)
+    torch.cuda.synchronize()
+    # products of 16-bit values are exact in FP32; only the FP32 summation rounds
+    bound = K * 2.0 ** -24 * ref_abs + 1e-6
+    assert bool(((C.cpu().double() - ref).abs() <= bound).all()), (C.cpu().double() - ref).abs().max()
+
+
+SCENES = {
+    "tiny_64_to_256_z4": lambda: scenes.tiny_scene(),
+    "graded_64_s2_z5": lambda: scenes.random_scene(79, 64, 128, 5, graded=True),
+    "single_layer_32_s2": lambda: scenes.random_scene(78, 32, 64, 1, graded=True),
+    "s3_48_z3": lambda: scenes.random_scene(80, 48, 144, 3, graded=True),
+}
+
+
+def run(torch, sc, form, thresholds=None):
+    from paper_2211_09938_gb300 import Plan
+    plan = Plan.for_scene(sc)
+    I = torch.from_numpy(sc["intensity"]).cuda()
+    L = torch.from_numpy(sc["layer"]).cuda()
+    S = torch.from_numpy(sc["saliency"]).cuda()
+    coeffs = plan.haar_decompose(I, L)
+    thr = thresholds or scenes.THRESHOLDS_U8
+    lists, counts = plan.progressive_lists(S, L, thr)
+    H = plan.progressive_hologram(coeffs, lists, counts, form=form)
+    torch.cuda.synchronize()
+    assert plan.status() == 0
+    ref_lists = O.progressive_lists(sc["saliency"], sc["layer"], plan.n_layers, thr)
+    return H.cpu().numpy(), ref_lists
+
+
+@pytest.mark.parametrize("name", list(SCENES))
+@pytest.mark.parametrize("form,tol", [("tc_bf16x3", BF16X3_TOL), ("tc_fp16x3", FP16X3_TOL)])
+def test_progressive_tc(torch_cuda, name, form, tol):
+    sc = SCENES[name]()
+    H, ref_lists = run(torch_cuda, sc, form)
+    Href = O.progressive_hologram(sc["intensity"], sc["layer"], ref_lists, O.geometry_of(sc))
+    err = O.rel_l2(H, Href)
+    print(f"{form} {name}: rel-L2 {err:.3e}")
+    assert err <= tol
+
+
+@pytest.mark.parametrize("form,tol", [("tc_bf16x3", BF16X3_TOL), ("tc_fp16x3", FP16X3_TOL)])
+def test_progressive_tc_paper_scale(torch_cuda, form, tol):
+    sc = scenes.paper_scene()
+    H, ref_lists = run(torch_cuda, sc, form)
+    Href = O.progressive_hologram(sc["intensity"], sc["layer"], ref_lists, O.geometry_of(sc))
+    err = O.rel_l2(H, Href)
+    print(f"{form} 512->1024 Z16: rel-L2 {err:.3e}")
+    assert err <= tol
