@@ -199,7 +199,9 @@ def run_ours(args):
                  for k in range(4)]
         holo = torch.empty((HOLO, HOLO), dtype=torch.complex64, device="cuda")
         flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
-    launches_per_step = 1 + 1 + 4 * 3 + 1  # tables, DWT, 4 x (count, scan, scatter), superposition
+    # tables, DWT, 4 x (count, scan, scatter), then the superposition: 1 kernel (direct form)
+    # or scatter + compaction + inverse DWT + 2 gathers + 2 GEMMs (tensor forms)
+    launches_per_step = 1 + 1 + 4 * 3 + (1 if form == "direct_lut" else 7)
 
     def step():
         plan.build_tables(stream=stream)
@@ -240,24 +242,39 @@ def run_ours(args):
     dev_ms = float(t.item())
     value = UNITS_PER_STEP * args.steps * ws / (dev_ms / 1e3) / 1e9
 
-    # ---- dominant kernel alone (the superposition), CUDA events on its stream
+    # ---- per-stage device times (CUDA events recorded by the library on `stream`),
+    # L2 flushed before every repetition; the dominant kernel's average launch duration
     R = max(5, min(50, args.steps))
-    kev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(R)]
-    with torch.cuda.stream(stream):
-        for k in range(R):
+    plan.profile(True)
+    stage_sum = {}
+    for k in range(R):
+        with torch.cuda.stream(stream):
             flush.fill_(float(k))
-            kev[k][0].record(stream)
-            plan.progressive_hologram(coeffs, lists, counts, holo=holo, accumulate=True, form=form,
-                                      stream=stream)
-            kev[k][1].record(stream)
-    torch.cuda.synchronize()
-    k_ms = sum(a.elapsed_time(b) for a, b in kev) / R
+            step()
+        for key, v in plan.profile_read(stream=stream).items():
+            stage_sum[key] = stage_sum.get(key, 0.0) + v
+    plan.profile(False)
+    stages = {key: v / R for key, v in stage_sum.items() if v > 0}
+    k_ms = stages.get("direct_lut" if form == "direct_lut" else "tc_stage2", 0.0)
 
     c = counts.cpu().numpy()
     n_lll, n1, n2, n3 = (int(c[k, 0]) for k in range(4))
     rank1_terms = n_lll + 2 * (n1 + n2 + n3)
     pk = peaks() or {}
     clocks = sampler.summary()
+    if form != "direct_lut":
+        kr, kc = plan.tc_layer_dims(stream=stream)
+        ksum = sum(kr)
+        # stage 2: complex GEMM M = N = hologram edge, K = sum of the layers' compacted rows,
+        # 8 flop per complex MAC, x3 for the hi+lo products (the algorithmic count of the form)
+        algo_flop = 3 * 8.0 * HOLO * HOLO * ksum
+        peak_tf = pk.get("bf16_tflops", 1900.0)
+        roof = {"bound": "tensor", "kernel": "k_tc_gemm<KIND_CC,EPI_H> (stage 2)",
+                "achieved": algo_flop / (k_ms / 1e3) / 1e12, "peak": peak_tf, "unit": "TFLOP/s",
+                "frac": algo_flop / (k_ms / 1e3) / 1e12 / peak_tf, "traffic": None,
+                "peak_note": "measured cuBLAS bf16 dense burst (MEASURED_PEAKS.json); fp16 has the same "
+                             "nominal dense rate" if "bf16_tflops" in pk else "fallback 1.9 PFLOP/s",
+                "kernel_ms": k_ms, "k_rows_total": ksum, "k_cols_total": sum(kc)}
     if form == "direct_lut":
         # FP32 FFMA bound: 8 flop (4 FFMA) per rank-1 term and hologram pixel
         algo_flop = 8.0 * rank1_terms * HOLO * HOLO
@@ -269,9 +286,6 @@ def run_ours(args):
                 "peak_note": f"FP32 FFMA: {sms} SMs x 128 lanes x 2 flop x {pk.get('sm_max_mhz', 2070.0):.0f} MHz "
                              "(max SM clock; derived, not measured)",
                 "kernel_ms": k_ms}
-    else:
-        roof = {"bound": "tensor", "kernel": "tc_gemm", "achieved": None, "peak": pk.get("bf16_tflops"),
-                "unit": "TFLOP/s", "frac": None, "traffic": None, "kernel_ms": k_ms}
 
     # ---- end to end through the C ABI with host buffers: H2D inputs, step, D2H hologram
     hI = torch.from_numpy(sc["intensity"]).pin_memory()
@@ -310,15 +324,36 @@ def run_ours(args):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": dev_ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": {"direct_lut": "f32", "tc_bf16x3": "bf16", "tc_fp16x3": "fp16"}[form],
+        "data": "synthetic",
         "config": {"workload": WORKLOAD, "form": form, "l2": "flushed (512 MiB write) before every timed step",
+                   "arithmetic": {"direct_lut": "FP32 FFMA", "tc_bf16x3": "bf16 hi+lo operands, 3 products, FP32 accumulation",
+                                  "tc_fp16x3": "fp16 hi+lo operands, 3 products, FP32 accumulation"}[form],
                    "parallelism": f"replicas{ws}" if ws > 1 else "single GPU",
                    "work_lists": [n_lll, n1, n2, n3], "rank1_terms": rank1_terms},
         "roofline": roof, "clocks": clocks, "e2e": e2e,
         "gpu_launches": launches_per_step * args.steps, "wall_s_timed_region": wall,
     }
+    line["stages_ms"] = stages
     if plain is not None:
         line["plain_direct"] = plain
+    # the other superposition forms on the same scene (device ms of the superposition call)
+    others = {}
+    for f in ("direct_lut", "tc_bf16x3", "tc_fp16x3"):
+        if f == form or args.skip_forms:
+            continue
+        fe = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        with torch.cuda.stream(stream):
+            plan.progressive_hologram(coeffs, lists, counts, holo=holo, form=f, stream=stream)
+            flush.fill_(0.0)
+            fe[0].record(stream)
+            plan.progressive_hologram(coeffs, lists, counts, holo=holo, form=f, stream=stream)
+            fe[1].record(stream)
+        torch.cuda.synchronize()
+        others[f] = fe[0].elapsed_time(fe[1])
+    if others:
+        line["other_forms_superposition_ms"] = others
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cb, Href = cpu_baseline()
         line["cpu_baseline"] = cb
@@ -342,7 +377,8 @@ def main():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--form", default="direct_lut", choices=["direct_lut", "tc_bf16x3", "tc_fp16x3"])
+    ap.add_argument("--form", default="tc_bf16x3", choices=["direct_lut", "tc_bf16x3", "tc_fp16x3"])
+    ap.add_argument("--skip-forms", action="store_true")
     ap.add_argument("--skip-plain", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

@@ -225,6 +225,40 @@ int cgh_reconstruct(const cgh_plan* plan, const float* holo, float* fields,
 int cgh_tc_selftest_gemm(const uint16_t* A, const uint16_t* B, float* C, int M, int N, int K, int is_fp16,
                          void* stream);
 
+/* ---- profiling -------------------------------------------------------------------- */
+/* Stage slots of cgh_profile_read. */
+#define CGH_PROF_TABLES 0      /* fringe-table build                    */
+#define CGH_PROF_HAAR 1        /* Haar DWT                              */
+#define CGH_PROF_SELECT 2      /* block selection (all passes)          */
+#define CGH_PROF_DIRECT_LUT 3  /* direct-form superposition             */
+#define CGH_PROF_TC_PREP 4     /* tensor form: flags, compaction, operands */
+#define CGH_PROF_TC_STAGE1 5   /* tensor form: stage-1 GEMM             */
+#define CGH_PROF_TC_STAGE2 6   /* tensor form: stage-2 GEMM             */
+#define CGH_PROF_PLAIN 7       /* plain point-wise kernel               */
+#define CGH_PROF_RECON 8       /* reconstruction                        */
+#define CGH_PROF_SLOTS 9
+
+/*
+ * cgh_profile - enable (1) or disable (0) CUDA-event timing around the plan's internal
+ * launches.  While enabled, every call records a start and a stop event around each stage
+ * it runs, on the call's stream.  The paper has no counterpart (instrumentation).
+ */
+int cgh_profile(cgh_plan* plan, int enable);
+
+/*
+ * cgh_profile_read - synchronise `stream`, then write into ms[CGH_PROF_SLOTS] (host) the
+ * device time in milliseconds of each stage's most recent run since profiling was enabled
+ * (0 for stages that did not run), and clear the record.
+ */
+int cgh_profile_read(cgh_plan* plan, float* ms, void* stream);
+
+/*
+ * cgh_tc_layer_dims - synchronise `stream` and copy to host the per-layer padded compacted
+ * row and column counts used by the last tensor-form call (kr[Z], kc[Z], host arrays);
+ * zeros before the first such call.  Their sums size the tensor-core GEMMs.
+ */
+int cgh_tc_layer_dims(const cgh_plan* plan, int* kr, int* kc, void* stream);
+
 /*
  * cgh_status - read and clear the plan's device status word (synchronises `stream`).
  * Bounded device-side waits that give up record CGH_ERR_TIMEOUT there instead of

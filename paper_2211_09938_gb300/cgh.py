@@ -47,6 +47,9 @@ SIGNATURES = {
     "cgh_reconstruct": (_I, [_P, _P, _P, _P, _P, _P]),
     "cgh_status": (_I, [_P, ctypes.POINTER(_I), _P]),
     "cgh_tc_selftest_gemm": (_I, [_P, _P, _P, _I, _I, _I, _I, _P]),
+    "cgh_profile": (_I, [_P, _I]),
+    "cgh_profile_read": (_I, [_P, ctypes.POINTER(ctypes.c_float), _P]),
+    "cgh_tc_layer_dims": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(_I), _P]),
 }
 
 _lib = None
@@ -198,6 +201,24 @@ class Plan:
         check(lib().cgh_reconstruct(self.handle, _ptr(holo), _ptr(f), _ptr(layer), _ptr(a),
                                     _stream(stream)))
         return f, a
+
+    PROF_SLOTS = ["tables", "haar", "select", "direct_lut", "tc_prep", "tc_stage1", "tc_stage2",
+                  "plain", "recon"]
+
+    def profile(self, enable=True):
+        check(lib().cgh_profile(self.handle, 1 if enable else 0))
+
+    def profile_read(self, stream=None):
+        """Per-stage device ms of the most recent run of each stage (synchronises)."""
+        ms = (ctypes.c_float * len(self.PROF_SLOTS))()
+        check(lib().cgh_profile_read(self.handle, ms, _stream(stream)))
+        return dict(zip(self.PROF_SLOTS, list(ms)))
+
+    def tc_layer_dims(self, stream=None):
+        kr = (ctypes.c_int * self.n_layers)()
+        kc = (ctypes.c_int * self.n_layers)()
+        check(lib().cgh_tc_layer_dims(self.handle, kr, kc, _stream(stream)))
+        return list(kr), list(kc)
 
     def status(self, stream=None):
         v = ctypes.c_int(0)

@@ -39,8 +39,14 @@ int cgh_version(void) { return 10000; }
 int cgh_plan_destroy(cgh_plan* p) {
   if (!p) return CGH_OK;
   cudaDeviceSynchronize();
+  if (p->prof_ev[0][0])
+    for (int k = 0; k < CGH_PROF_SLOTS; ++k) {
+      cudaEventDestroy(p->prof_ev[k][0]);
+      cudaEventDestroy(p->prof_ev[k][1]);
+    }
   tc_destroy(p);
   cudaFree(p->d_tab);
+  cudaFree(p->d_f64);
   cudaFree(p->d_a_frac);
   cudaFree(p->d_a_fixed);
   cudaFree(p->d_status);
@@ -52,7 +58,9 @@ int cgh_plan_destroy(cgh_plan* p) {
 
 int cgh_build_tables(cgh_plan* p, void* stream) {
   if (!p) return cgh_fail(CGH_ERR_ARG, "cgh_build_tables: plan is NULL");
+  prof_mark(p, CGH_PROF_TABLES, 0, (cudaStream_t)stream);
   CHECK_CUDA(launch_build_tables(p, (cudaStream_t)stream), "cgh_build_tables launch");
+  prof_mark(p, CGH_PROF_TABLES, 1, (cudaStream_t)stream);
   return CGH_OK;
 }
 
@@ -116,6 +124,13 @@ int cgh_plan_create(cgh_plan** out, int obj_h, int obj_w, int holo_h, int holo_w
   } while (0)
   PLAN_TRY(cudaMalloc(&p->d_tab, (size_t)n_layers * CGH_TAB_PER_LAYER * p->tab_len * sizeof(float2)),
            "cgh_plan_create: tables");
+  p->f_len = p->tab_len + 7 * p->s;
+  PLAN_TRY(cudaMalloc(&p->d_f64, (size_t)n_layers * p->f_len * sizeof(double2)), "cgh_plan_create: fringe");
+  PLAN_TRY(basic_init_attributes(), "cgh_plan_create: kernel attributes");
+  if (tc_init_attributes() != CGH_OK) {
+    cgh_plan_destroy(p);
+    return CGH_ERR_CUDA;
+  }
   PLAN_TRY(cudaMalloc(&p->d_a_frac, CGH_MAX_LAYERS * sizeof(double)), "cgh_plan_create: a_frac");
   PLAN_TRY(cudaMalloc(&p->d_a_fixed, CGH_MAX_LAYERS * sizeof(unsigned long long)), "cgh_plan_create: a_fixed");
   PLAN_TRY(cudaMalloc(&p->d_status, sizeof(int)), "cgh_plan_create: status");
@@ -142,7 +157,9 @@ int cgh_haar_decompose(const cgh_plan* p, const uint8_t* intensity, const uint8_
     return cgh_fail(CGH_ERR_ARG, "cgh_haar_decompose: NULL argument");
   if (((uintptr_t)coeffs & 15) || ((uintptr_t)intensity & 7) || ((uintptr_t)layer_idx & 7))
     return cgh_fail(CGH_ERR_ARG, "cgh_haar_decompose: coeffs must be 16-byte and inputs 8-byte aligned");
+  prof_mark(p, CGH_PROF_HAAR, 0, (cudaStream_t)stream);
   CHECK_CUDA(launch_haar(p, intensity, layer_idx, coeffs, (cudaStream_t)stream), "cgh_haar_decompose");
+  prof_mark(p, CGH_PROF_HAAR, 1, (cudaStream_t)stream);
   return CGH_OK;
 }
 
@@ -156,10 +173,12 @@ int cgh_select_blocks(const cgh_plan* p, const uint8_t* saliency, const uint8_t*
     return cgh_fail(CGH_ERR_ARG, "cgh_select_blocks: threshold %d not in -1..255", threshold);
   if (threshold >= 0 && !saliency) return cgh_fail(CGH_ERR_ARG, "cgh_select_blocks: saliency is NULL");
   if (capacity < 0) return cgh_fail(CGH_ERR_ARG, "cgh_select_blocks: capacity < 0");
+  prof_mark(p, CGH_PROF_SELECT, 0, (cudaStream_t)stream);
   CHECK_CUDA(launch_select(p->obj_h, p->obj_w, p->n_layers, threshold >= 0 ? saliency : NULL, layer_idx,
                            threshold, level, list, d_count, capacity, p->d_chunk_cnt, p->d_chunk_off,
                            (cudaStream_t)stream),
              "cgh_select_blocks");
+  prof_mark(p, CGH_PROF_SELECT, 1, (cudaStream_t)stream);
   return CGH_OK;
 }
 
@@ -176,7 +195,9 @@ int cgh_progressive_hologram(const cgh_plan* p, const int32_t* coeffs, const int
     if (!accumulate)
       CHECK_CUDA(cudaMemsetAsync(holo, 0, (size_t)p->holo_h * p->holo_w * sizeof(float2), st),
                  "cgh_progressive_hologram: clear");
+    prof_mark(p, CGH_PROF_DIRECT_LUT, 0, st);
     CHECK_CUDA(launch_direct_lut(p, coeffs, lists, d_counts, (float2*)holo, st), "cgh_progressive_hologram");
+    prof_mark(p, CGH_PROF_DIRECT_LUT, 1, st);
     return CGH_OK;
   }
   if (form == CGH_FORM_TC_BF16X3 || form == CGH_FORM_TC_FP16X3)
@@ -187,8 +208,10 @@ int cgh_progressive_hologram(const cgh_plan* p, const int32_t* coeffs, const int
 int cgh_plain_direct(const cgh_plan* p, const uint8_t* intensity, const uint8_t* layer_idx, float* holo,
                      void* stream) {
   if (!p || !intensity || !layer_idx || !holo) return cgh_fail(CGH_ERR_ARG, "cgh_plain_direct: NULL argument");
+  prof_mark(p, CGH_PROF_PLAIN, 0, (cudaStream_t)stream);
   CHECK_CUDA(launch_plain_direct(p, intensity, layer_idx, (float2*)holo, (cudaStream_t)stream),
              "cgh_plain_direct");
+  prof_mark(p, CGH_PROF_PLAIN, 1, (cudaStream_t)stream);
   return CGH_OK;
 }
 
@@ -198,6 +221,35 @@ int cgh_reconstruct(const cgh_plan* p, const float* holo, float* fields, const u
   if (amplitude && !layer_idx) return cgh_fail(CGH_ERR_ARG, "cgh_reconstruct: amplitude needs layer_idx");
   if (!fields && !amplitude) return cgh_fail(CGH_ERR_ARG, "cgh_reconstruct: nothing to compute");
   return tc_reconstruct(p, (const float2*)holo, (float2*)fields, layer_idx, amplitude, (cudaStream_t)stream);
+}
+
+int cgh_profile(cgh_plan* p, int enable) {
+  if (!p) return cgh_fail(CGH_ERR_ARG, "cgh_profile: plan is NULL");
+  if (enable && !p->prof_ev[0][0])
+    for (int k = 0; k < CGH_PROF_SLOTS; ++k) {
+      CHECK_CUDA(cudaEventCreate(&p->prof_ev[k][0]), "cgh_profile: event");
+      CHECK_CUDA(cudaEventCreate(&p->prof_ev[k][1]), "cgh_profile: event");
+    }
+  p->prof_on = enable ? 1 : 0;
+  for (int k = 0; k < CGH_PROF_SLOTS; ++k) p->prof_used[k] = 0;
+  return CGH_OK;
+}
+
+int cgh_profile_read(cgh_plan* p, float* ms, void* stream) {
+  if (!p || !ms) return cgh_fail(CGH_ERR_ARG, "cgh_profile_read: NULL argument");
+  CHECK_CUDA(cudaStreamSynchronize((cudaStream_t)stream), "cgh_profile_read: sync");
+  for (int k = 0; k < CGH_PROF_SLOTS; ++k) {
+    ms[k] = 0.f;
+    if (p->prof_used[k]) CHECK_CUDA(cudaEventElapsedTime(&ms[k], p->prof_ev[k][0], p->prof_ev[k][1]),
+                                    "cgh_profile_read: elapsed");
+    p->prof_used[k] = 0;
+  }
+  return CGH_OK;
+}
+
+int cgh_tc_layer_dims(const cgh_plan* p, int* kr, int* kc, void* stream) {
+  if (!p || !kr || !kc) return cgh_fail(CGH_ERR_ARG, "cgh_tc_layer_dims: NULL argument");
+  return tc_layer_dims(p, kr, kc, (cudaStream_t)stream);
 }
 
 int cgh_status(const cgh_plan* p, int* status_out, void* stream) {

@@ -23,6 +23,8 @@ struct cgh_plan {
   // Fringe tables: float2 tab[Z][4 levels][2 kinds][tab_len], offset d -> index d + tab_off.
   int tab_len, tab_off;
   float2* d_tab;
+  double2* d_f64;  // FP64 point fringe f_z(d), d in [-(tab_off + 7s), tab_len - tab_off)
+  int f_len;
   double* d_a_frac;
   unsigned long long* d_a_fixed;
 
@@ -36,7 +38,20 @@ struct cgh_plan {
 
   // Separable tensor-core path (allocated lazily by the first call that needs it).
   struct cgh_tc_state* tc;
+
+  // CUDA-event profiling of the internal stages (cgh_profile).
+  int prof_on;
+  int prof_used[CGH_PROF_SLOTS];
+  cudaEvent_t prof_ev[CGH_PROF_SLOTS][2];
 };
+
+// Records the start / stop event of a profiled stage when profiling is on.
+static inline void prof_mark(const cgh_plan* pc, int slot, int stop, cudaStream_t st) {
+  cgh_plan* p = const_cast<cgh_plan*>(pc);
+  if (!p->prof_on) return;
+  cudaEventRecord(p->prof_ev[slot][stop], st);
+  if (stop) p->prof_used[slot] = 1;
+}
 
 // Thread-local error message helpers (cgh_api.cu).
 int cgh_fail(int code, const char* fmt, ...);
@@ -57,6 +72,8 @@ cudaError_t launch_direct_lut(const cgh_plan* p, const int32_t* coef, const int3
 cudaError_t launch_plain_direct(const cgh_plan* p, const uint8_t* I, const uint8_t* L, float2* holo,
                                 cudaStream_t st);
 int select_num_chunks(int obj_h, int obj_w, int level);
+cudaError_t basic_init_attributes();
+int tc_init_attributes();
 
 // Separable tensor-core path (kernels_tc.cu).
 int tc_progressive(const cgh_plan* p, const int32_t* coef, const int32_t* const* lists,
@@ -64,3 +81,4 @@ int tc_progressive(const cgh_plan* p, const int32_t* coef, const int32_t* const*
 int tc_reconstruct(const cgh_plan* p, const float2* holo, float2* fields, const uint8_t* L,
                    float* amp, cudaStream_t st);
 void tc_destroy(cgh_plan* p);
+int tc_layer_dims(const cgh_plan* p, int* kr, int* kc, cudaStream_t st);

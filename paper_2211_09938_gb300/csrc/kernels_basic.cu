@@ -13,37 +13,57 @@
 //   kind 1: w_l(d) = sum_{t<2^(l-1)} f_z(d - s t) - sum_{2^(l-1)<=t<2^l} f_z(d - s t)
 // f_z(d) = exp(j 2 pi frac(a_z d^2)); the product a_z*d^2 and its reduction are FP64
 // with d^2 an exact integer (Eq. 1 under the paraxial approximation).
-__global__ void k_build_tables(float2* __restrict__ tab, const double* __restrict__ a_frac,
-                               int tab_len, int tab_off, int s) {
+__global__ void k_fringe_f64(double2* __restrict__ F, const double* __restrict__ a_frac, int f_len, int f_off) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= f_len) return;
+  const int z = blockIdx.y;
+  const long long d = (long long)q - f_off;
+  double x = a_frac[z] * (double)(d * d);
+  x -= rint(x);  // exact: |x| < 2^53 and x - rint(x) is representable
+  double sn, cs;
+  sincospi(2.0 * x, &sn, &cs);
+  F[(size_t)z * f_len + q] = make_double2(cs, sn);
+}
+
+// F[z][q] = f_z(q - f_off) with f_off = tab_off + 7s, so entry idx of a table needs
+// F[z][idx + 7s - s t] for the shifts t < 8.
+__global__ void k_build_tables(float2* __restrict__ tab, const double2* __restrict__ F, int f_len,
+                               int tab_len, int s) {
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= tab_len) return;
-  const int l = blockIdx.y >> 1, kind = blockIdx.y & 1, z = blockIdx.z;
-  const double az = a_frac[z];
-  const long long d = (long long)idx - tab_off;
-  const int n = 1 << l, half = n >> 1;
-  double re = 0.0, im = 0.0;
-  if (!(l == 0 && kind == 1)) {
+  const int z = blockIdx.y;
+  const double2* Fz = F + (size_t)z * f_len + idx + 7 * s;
+  double2 v[8];
+#pragma unroll
+  for (int t = 0; t < 8; ++t) v[t] = Fz[-s * t];
+  float2* T = tab + (size_t)z * 8 * tab_len + idx;
+#pragma unroll
+  for (int l = 0; l < 4; ++l) {
+    const int n = 1 << l, half = n >> 1;
+    double br = 0.0, bi = 0.0, wr = 0.0, wi = 0.0;
+#pragma unroll
     for (int t = 0; t < n; ++t) {
-      const long long dd = d - (long long)s * t;
-      double x = az * (double)(dd * dd);
-      x -= rint(x);  // exact: |x| < 2^53 and x - rint(x) is representable
-      double sn, cs;
-      sincospi(2.0 * x, &sn, &cs);
-      if (kind == 1 && t >= half) {
-        re -= cs;
-        im -= sn;
+      br += v[t].x;
+      bi += v[t].y;
+      if (t < half) {
+        wr += v[t].x;
+        wi += v[t].y;
       } else {
-        re += cs;
-        im += sn;
+        wr -= v[t].x;
+        wi -= v[t].y;
       }
     }
+    if (l == 0) wr = wi = 0.0;
+    T[(size_t)(2 * l) * tab_len] = make_float2((float)br, (float)bi);
+    T[(size_t)(2 * l + 1) * tab_len] = make_float2((float)wr, (float)wi);
   }
-  tab[((size_t)(z * 4 + l) * 2 + kind) * tab_len + idx] = make_float2((float)re, (float)im);
 }
 
 cudaError_t launch_build_tables(const cgh_plan* p, cudaStream_t st) {
-  dim3 grid((p->tab_len + 255) / 256, 8, p->n_layers);
-  k_build_tables<<<grid, 256, 0, st>>>(p->d_tab, p->d_a_frac, p->tab_len, p->tab_off, p->s);
+  k_fringe_f64<<<dim3((p->f_len + 255) / 256, p->n_layers), 256, 0, st>>>(p->d_f64, p->d_a_frac, p->f_len,
+                                                                        p->tab_off + 7 * p->s);
+  k_build_tables<<<dim3((p->tab_len + 255) / 256, p->n_layers), 256, 0, st>>>(p->d_tab, p->d_f64, p->f_len,
+                                                                            p->tab_len, p->s);
   return cudaGetLastError();
 }
 
@@ -525,13 +545,17 @@ static int direct_lut_splits(int tiles) {
   return best;
 }
 
+#define DL_SMEM ((size_t)DL_KC * (DL_TM + DL_TN) * sizeof(float2))
+
+cudaError_t basic_init_attributes() {
+  return cudaFuncSetAttribute(k_direct_lut, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)DL_SMEM);
+}
+
 cudaError_t launch_direct_lut(const cgh_plan* p, const int32_t* coef, const int32_t* const* lists,
                               const int32_t* d_counts, float2* holo, cudaStream_t st) {
   const int tn = (p->holo_w + DL_TN - 1) / DL_TN, tm = (p->holo_h + DL_TM - 1) / DL_TM;
   const int S = direct_lut_splits(tn * tm);
-  const size_t smem = (size_t)DL_KC * (DL_TM + DL_TN) * sizeof(float2);
-  cudaError_t e = cudaFuncSetAttribute(k_direct_lut, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
+  const size_t smem = DL_SMEM;
   dim3 grid(tn, tm, S);
   // holo must be zero (or hold the previous hologram) when S > 1: atomics accumulate.
   k_direct_lut<<<grid, 256, smem, st>>>(p->d_tab, p->tab_len, p->tab_off, coef, lists[0], lists[1],

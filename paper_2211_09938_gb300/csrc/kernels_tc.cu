@@ -175,7 +175,7 @@ struct TcCfg<KIND_TEST> {
 };
 template <>
 struct TcCfg<KIND_CR> {
-  static constexpr int NA = 4, NB = 2, NST = 4;
+  static constexpr int NA = 4, NB = 2, NST = 2;  // short K loops: two CTAs per SM instead of depth
 };
 template <>
 struct TcCfg<KIND_CC> {
@@ -393,6 +393,32 @@ __global__ void __launch_bounds__(128, 1) k_tc_gemm(const __grid_constant__ CUte
         if (row < args.M) {
           const int nv = min(32, n_valid - c0);
           uint16_t* base = args.Y + (size_t)row * args.ldy + out_col0 + c0;
+          if (nv == 32) {  // 64 contiguous bytes per plane: four 16-byte stores each
+            uint32_t prh[16], prl[16], pih[16], pil[16];
+#pragma unroll
+            for (int j = 0; j < 32; j += 2) {
+              uint16_t a0, a1, b0, b1, c0h, c1h, d0, d1;
+              split_hi_lo<F16>(__uint_as_float(re[j]) * args.scale, a0, b0);
+              split_hi_lo<F16>(__uint_as_float(re[j + 1]) * args.scale, a1, b1);
+              split_hi_lo<F16>(__uint_as_float(im[j]) * args.scale, c0h, d0);
+              split_hi_lo<F16>(__uint_as_float(im[j + 1]) * args.scale, c1h, d1);
+              prh[j / 2] = (uint32_t)a0 | ((uint32_t)a1 << 16);
+              prl[j / 2] = (uint32_t)b0 | ((uint32_t)b1 << 16);
+              pih[j / 2] = (uint32_t)c0h | ((uint32_t)c1h << 16);
+              pil[j / 2] = (uint32_t)d0 | ((uint32_t)d1 << 16);
+            }
+            uint4* q0 = reinterpret_cast<uint4*>(base);
+            uint4* q1 = reinterpret_cast<uint4*>(base + args.y_plane);
+            uint4* q2 = reinterpret_cast<uint4*>(base + 2 * args.y_plane);
+            uint4* q3 = reinterpret_cast<uint4*>(base + 3 * args.y_plane);
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+              q0[v] = make_uint4(prh[4 * v], prh[4 * v + 1], prh[4 * v + 2], prh[4 * v + 3]);
+              q1[v] = make_uint4(prl[4 * v], prl[4 * v + 1], prl[4 * v + 2], prl[4 * v + 3]);
+              q2[v] = make_uint4(pih[4 * v], pih[4 * v + 1], pih[4 * v + 2], pih[4 * v + 3]);
+              q3[v] = make_uint4(pil[4 * v], pil[4 * v + 1], pil[4 * v + 2], pil[4 * v + 3]);
+            }
+          } else
           for (int j = 0; j < nv; ++j) {
             uint16_t rh, rl, ih, il;
             split_hi_lo<F16>(__uint_as_float(re[j]) * args.scale, rh, rl);
@@ -542,12 +568,13 @@ __global__ void k_tc_idwt(const int32_t* __restrict__ coef, TcFlags fl, const in
 // E operand planes: out[p][z*rows_per_z + r][c] = split(f_z(r - s*idx[z][c])) for c below the
 // layer's padded count (idx < 0: zero).  stage 1: idx = columns, rows = hologram width;
 // stage 2 (z_off_from_counts): column index off_z + c, rows = hologram height, z block 0.
+template <bool F16>
 __global__ void k_tc_gather_e(const float2* __restrict__ tab, int tab_len, int tab_off, int s,
                               const int* __restrict__ idx, int ld_idx, const int* __restrict__ cnt_pad,
-                              int rows_out, int stage2, uint16_t* __restrict__ E, long long e_plane, int lde,
-                              int is_f16) {
+                              int rows_out, int stage2, uint16_t* __restrict__ E, long long e_plane, int lde) {
+  // one thread: 8 consecutive columns (padded counts are multiples of 32), 16-byte stores
   const int z = blockIdx.z;
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  const int c = 8 * (blockIdx.x * blockDim.x + threadIdx.x);
   const int r = blockIdx.y * blockDim.y + threadIdx.y;
   if (r >= rows_out || c >= cnt_pad[z]) return;
   int col = c;
@@ -558,22 +585,25 @@ __global__ void k_tc_gather_e(const float2* __restrict__ tab, int tab_len, int t
     col = off + c;
     row = r;
   }
-  const int i = idx[(size_t)z * ld_idx + c];
-  float2 v = make_float2(0.f, 0.f);
-  if (i >= 0) v = tab[(size_t)(z * 4 + 0) * 2 * tab_len + tab_off + r - s * i];
-  uint16_t rh, rl, ih, il;
-  if (is_f16) {
-    split_hi_lo<true>(v.x, rh, rl);
-    split_hi_lo<true>(v.y, ih, il);
-  } else {
-    split_hi_lo<false>(v.x, rh, rl);
-    split_hi_lo<false>(v.y, ih, il);
+  const float2* T = tab + (size_t)(z * 4 + 0) * 2 * tab_len + tab_off + r;
+  uint32_t w[4][4];
+#pragma unroll
+  for (int q = 0; q < 8; q += 2) {
+    uint16_t h[2][4];
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const int i = idx[(size_t)z * ld_idx + c + q + u];
+      const float2 v = i >= 0 ? T[-s * i] : make_float2(0.f, 0.f);
+      split_hi_lo<F16>(v.x, h[u][0], h[u][1]);
+      split_hi_lo<F16>(v.y, h[u][2], h[u][3]);
+    }
+#pragma unroll
+    for (int p = 0; p < 4; ++p) w[p][q / 2] = (uint32_t)h[0][p] | ((uint32_t)h[1][p] << 16);
   }
   uint16_t* dst = E + row * lde + col;
-  dst[0] = rh;
-  dst[e_plane] = rl;
-  dst[2 * e_plane] = ih;
-  dst[3 * e_plane] = il;
+#pragma unroll
+  for (int p = 0; p < 4; ++p)
+    *reinterpret_cast<uint4*>(dst + p * e_plane) = make_uint4(w[p][0], w[p][1], w[p][2], w[p][3]);
 }
 
 // ------------------------------------------------------------------------------------
@@ -612,13 +642,30 @@ static int make_plane_map(CUtensorMap* map, const void* base, int planes, long l
 }
 
 template <int KIND, int EPI, bool F16>
+static cudaError_t set_gemm_attr() {
+  return cudaFuncSetAttribute(k_tc_gemm<KIND, EPI, F16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)tc_smem_bytes<KIND>());
+}
+
+// Shared-memory opt-in of every GEMM instantiation on the current device; called outside
+// any stream capture (plan creation), so that launches inside a captured graph need no
+// attribute calls.
+int tc_init_attributes() {
+  cudaError_t e;
+  if ((e = set_gemm_attr<KIND_TEST, EPI_C, false>()) != cudaSuccess ||
+      (e = set_gemm_attr<KIND_TEST, EPI_C, true>()) != cudaSuccess ||
+      (e = set_gemm_attr<KIND_CR, EPI_Y, false>()) != cudaSuccess ||
+      (e = set_gemm_attr<KIND_CR, EPI_Y, true>()) != cudaSuccess ||
+      (e = set_gemm_attr<KIND_CC, EPI_H, false>()) != cudaSuccess ||
+      (e = set_gemm_attr<KIND_CC, EPI_H, true>()) != cudaSuccess)
+    return cgh_cuda_check(e, "tensor-core kernel attributes");
+  return CGH_OK;
+}
+
+template <int KIND, int EPI, bool F16>
 static cudaError_t launch_gemm(const CUtensorMap& ma, const CUtensorMap& mb, const TcGemmArgs& a, dim3 grid,
                                cudaStream_t st) {
-  const size_t smem = tc_smem_bytes<KIND>();
-  cudaError_t e = cudaFuncSetAttribute(k_tc_gemm<KIND, EPI, F16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
-  if (e != cudaSuccess) return e;
-  k_tc_gemm<KIND, EPI, F16><<<grid, 128, smem, st>>>(ma, mb, a);
+  k_tc_gemm<KIND, EPI, F16><<<grid, 128, tc_smem_bytes<KIND>(), st>>>(ma, mb, a);
   return cudaGetLastError();
 }
 
@@ -738,6 +785,7 @@ static int tc_run(const cgh_plan* p, const int32_t* coef, const int32_t* const* 
     int _rc = cgh_cuda_check((expr), (what));               \
     if (_rc != CGH_OK) return _rc;                          \
   } while (0)
+  prof_mark(p, CGH_PROF_TC_PREP, 0, st);
   TC_CK(cudaMemsetAsync(t->flags, 0, t->flags_bytes, st), "tc: clear flags");
   k_tc_scatter<<<dim3(64, 4), 256, 0, st>>>(lists[0], lists[1], lists[2], lists[3], d_counts, t->fl, H, W, Z);
   TC_CK(cudaGetLastError(), "tc: scatter");
@@ -750,15 +798,16 @@ static int tc_run(const cgh_plan* p, const int32_t* coef, const int32_t* const* 
     TC_CK(cudaGetLastError(), "tc: idwt");
   }
   {
-    dim3 blk(32, 8), grid(t->kc_alloc / 32, (p->holo_w + 7) / 8, Z);
-    k_tc_gather_e<<<grid, blk, 0, st>>>(p->d_tab, p->tab_len, p->tab_off, p->s, t->cols, t->kc_alloc, t->kc_pad,
-                                        p->holo_w, 0, t->A1, t->a1_plane, t->kc_alloc, F16 ? 1 : 0);
+    dim3 blk(8, 32), grid((t->kc_alloc / 8 + 7) / 8, (p->holo_w + 31) / 32, Z);
+    k_tc_gather_e<F16><<<grid, blk, 0, st>>>(p->d_tab, p->tab_len, p->tab_off, p->s, t->cols, t->kc_alloc,
+                                             t->kc_pad, p->holo_w, 0, t->A1, t->a1_plane, t->kc_alloc);
     TC_CK(cudaGetLastError(), "tc: gather E1");
-    dim3 grid2(t->kr_alloc / 32, (p->holo_h + 7) / 8, Z);
-    k_tc_gather_e<<<grid2, blk, 0, st>>>(p->d_tab, p->tab_len, p->tab_off, p->s, t->rows, t->kr_alloc, t->kr_pad,
-                                         p->holo_h, 1, t->A2, t->a2_plane, t->ktot_alloc, F16 ? 1 : 0);
+    dim3 grid2((t->kr_alloc / 8 + 7) / 8, (p->holo_h + 31) / 32, Z);
+    k_tc_gather_e<F16><<<grid2, blk, 0, st>>>(p->d_tab, p->tab_len, p->tab_off, p->s, t->rows, t->kr_alloc,
+                                              t->kr_pad, p->holo_h, 1, t->A2, t->a2_plane, t->ktot_alloc);
     TC_CK(cudaGetLastError(), "tc: gather E2");
   }
+  prof_mark(p, CGH_PROF_TC_PREP, 1, st);
   // stage 1: Y^T = E_z[:, cols] * A^_z[rows, cols]^T / 64, scaled by 2^-4 for fp16 headroom
   const float s1 = F16 ? 1.0f / 1024.0f : 1.0f / 64.0f;
   const float s2 = F16 ? 16.0f : 1.0f;
@@ -778,7 +827,9 @@ static int tc_run(const cgh_plan* p, const int32_t* coef, const int32_t* const* 
     a.ldy = t->ktot_alloc;
     a.status = p->d_status;
     dim3 grid((p->holo_w + TC_BM - 1) / TC_BM, (t->kr_alloc + TC_BN - 1) / TC_BN, Z);
+    prof_mark(p, CGH_PROF_TC_STAGE1, 0, st);
     e = launch_gemm<KIND_CR, EPI_Y, F16>(t->mA1, t->mB1, a, grid, st);
+    prof_mark(p, CGH_PROF_TC_STAGE1, 1, st);
     TC_CK(e, "tc: stage-1 GEMM");
   }
   if (!accumulate) TC_CK(cudaMemsetAsync(holo, 0, (size_t)p->holo_h * p->holo_w * sizeof(float2), st), "tc: clear");
@@ -797,7 +848,9 @@ static int tc_run(const cgh_plan* p, const int32_t* coef, const int32_t* const* 
     a.status = p->d_status;
     const int tm = (p->holo_h + TC_BM - 1) / TC_BM, tn = (p->holo_w + TC_BN - 1) / TC_BN;
     const int S = stage2_splits(tm * tn, t->ktot_alloc / TC_BK);
+    prof_mark(p, CGH_PROF_TC_STAGE2, 0, st);
     e = launch_gemm<KIND_CC, EPI_H, F16>(t->mA2, t->mY, a, dim3(tm, tn, S), st);
+    prof_mark(p, CGH_PROF_TC_STAGE2, 1, st);
     TC_CK(e, "tc: stage-2 GEMM");
   }
 #undef TC_CK
@@ -814,6 +867,21 @@ int tc_progressive(const cgh_plan* p, const int32_t* coef, const int32_t* const*
   return tc_run<false>(p, coef, lists, d_counts, holo, accumulate, st);
 }
 
+int tc_layer_dims(const cgh_plan* p, int* kr, int* kc, cudaStream_t st) {
+  const int Z = p->n_layers;
+  if (!p->tc) {
+    for (int z = 0; z < Z; ++z) kr[z] = kc[z] = 0;
+    return CGH_OK;
+  }
+  int rc = cgh_cuda_check(cudaMemcpyAsync(kr, p->tc->kr_pad, Z * sizeof(int), cudaMemcpyDeviceToHost, st),
+                          "cgh_tc_layer_dims: copy");
+  if (rc != CGH_OK) return rc;
+  rc = cgh_cuda_check(cudaMemcpyAsync(kc, p->tc->kc_pad, Z * sizeof(int), cudaMemcpyDeviceToHost, st),
+                      "cgh_tc_layer_dims: copy");
+  if (rc != CGH_OK) return rc;
+  return cgh_cuda_check(cudaStreamSynchronize(st), "cgh_tc_layer_dims: sync");
+}
+
 int tc_reconstruct(const cgh_plan*, const float2*, float2*, const uint8_t*, float*, cudaStream_t) {
   return cgh_fail(CGH_ERR_UNSUPPORTED, "reconstruction not built");
 }
@@ -827,6 +895,8 @@ extern "C" int cgh_tc_selftest_gemm(const uint16_t* A, const uint16_t* B, float*
   int rc = make_plane_map(&ma, A, 1, M, K);
   if (rc != CGH_OK) return rc;
   rc = make_plane_map(&mb, B, 1, N, K);
+  if (rc != CGH_OK) return rc;
+  rc = tc_init_attributes();
   if (rc != CGH_OK) return rc;
   TcGemmArgs a;
   memset(&a, 0, sizeof(a));
