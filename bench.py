@@ -213,6 +213,22 @@ def run_ours(args):
         for _ in range(args.warmup):
             step()
     stream.synchronize()
+    # the whole step as one CUDA graph (every launch of the path, no host work between)
+    graph = None
+    if not args.no_graph:
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, stream=stream):
+            step()
+        for _ in range(args.warmup):
+            with torch.cuda.stream(stream):
+                graph.replay()
+        stream.synchronize()
+
+    def run_step():
+        if graph is not None:
+            graph.replay()
+        else:
+            step()
 
     # ---- timed region: K steps, L2 flushed before each, device time from CUDA events
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
@@ -228,7 +244,7 @@ def run_ours(args):
         for k in range(args.steps):
             flush.fill_(float(k))
             evs[k][0].record(stream)
-            step()
+            run_step()
             evs[k][1].record(stream)
     torch.cuda.synchronize()
     wall = time.perf_counter() - wall0
@@ -328,6 +344,7 @@ def run_ours(args):
         "dtype": {"direct_lut": "f32", "tc_bf16x3": "bf16", "tc_fp16x3": "fp16"}[form],
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "form": form, "l2": "flushed (512 MiB write) before every timed step",
+                   "cuda_graph": graph is not None,
                    "arithmetic": {"direct_lut": "FP32 FFMA", "tc_bf16x3": "bf16 hi+lo operands, 3 products, FP32 accumulation",
                                   "tc_fp16x3": "fp16 hi+lo operands, 3 products, FP32 accumulation"}[form],
                    "parallelism": f"replicas{ws}" if ws > 1 else "single GPU",
@@ -379,6 +396,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--form", default="tc_bf16x3", choices=["direct_lut", "tc_bf16x3", "tc_fp16x3"])
     ap.add_argument("--skip-forms", action="store_true")
+    ap.add_argument("--no-graph", action="store_true", help="launch the step eagerly instead of as a CUDA graph")
     ap.add_argument("--skip-plain", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

@@ -146,9 +146,9 @@ int cgh_select_blocks(const cgh_plan* plan, const uint8_t* saliency, const uint8
  * cgh_select_blocks for the same inputs.
  *   obj_h, obj_w  object size (multiples of 8, 8..8192);  n_layers  Z, 1..64
  *   other arguments as for cgh_select_blocks (device pointers, caller-owned)
- * Scratch: a static device array built into the library (512 KiB per GPU that loads the
+ * Scratch: a static device array built into the library (2 MiB per GPU that loads the
  * library, held until the process exits).  Limit: n_layers * ceil(blocks at `level` /
- * 1024) <= 65536, e.g. 64 layers of a 2048x2048 object at level 1; larger requests
+ * 256) <= 262144, e.g. 64 layers of a 2048x2048 object at level 1; larger requests
  * return CGH_ERR_ARG with a message and enqueue nothing.
  * Allocates nothing: no cudaMalloc, no cudaFree, no allocating library routine.  The
  * first call on each device looks up the array's device address with
@@ -161,6 +161,23 @@ int cgh_select_blocks(const cgh_plan* plan, const uint8_t* saliency, const uint8
 int cgh_select_blocks_noalloc(const uint8_t* saliency, const uint8_t* layer_idx, int obj_h, int obj_w,
                               int n_layers, int threshold, int level, int32_t* list, int32_t* d_count,
                               int capacity, void* stream);
+
+/*
+ * cgh_select_progressive - the four work lists of one progressive hologram in one go.
+ * Paper: Section 2 steps 1-5 (the LLL band takes every block; the detail levels take the
+ * blocks above their saliency thresholds).  Same results as four cgh_select_blocks calls:
+ *   lists[0]  LLL list    = cgh_select_blocks(threshold -1, level 3)
+ *   lists[l]  level l     = cgh_select_blocks(thresholds[l-1], level l), l = 1, 2, 3
+ *   thresholds  HOST int[3] (levels 1, 2, 3), each -1..255
+ *   lists       HOST array of 4 device pointers;  capacities  HOST int[4]
+ *   d_counts    device int32 [4][2] output, ([written, total] per list, as d_count of
+ *               cgh_select_blocks); directly usable by cgh_progressive_hologram
+ * Runs the three compaction passes once for all four lists (three kernel launches).
+ * Uses plan scratch.  Bit-exact.  Errors: CGH_ERR_ARG, CGH_ERR_CUDA.
+ */
+int cgh_select_progressive(const cgh_plan* plan, const uint8_t* saliency, const uint8_t* layer_idx,
+                           const int* thresholds, int32_t* const* lists, const int* capacities,
+                           int32_t* d_counts, void* stream);
 
 /*
  * cgh_progressive_hologram - progressive superposition of the selected blocks.

@@ -42,6 +42,8 @@ SIGNATURES = {
     "cgh_haar_decompose": (_I, [_P, _P, _P, _P, _P]),
     "cgh_select_blocks": (_I, [_P, _P, _P, _I, _I, _P, _P, _I, _P]),
     "cgh_select_blocks_noalloc": (_I, [_P, _P, _I, _I, _I, _I, _I, _P, _P, _I, _P]),
+    "cgh_select_progressive": (_I, [_P, _P, _P, ctypes.POINTER(_I), ctypes.POINTER(_P),
+                                    ctypes.POINTER(_I), _P, _P]),
     "cgh_progressive_hologram": (_I, [_P, _P, ctypes.POINTER(_P), _P, _P, _I, _I, _P]),
     "cgh_plain_direct": (_I, [_P, _P, _P, _P, _P]),
     "cgh_reconstruct": (_I, [_P, _P, _P, _P, _P, _P]),
@@ -159,19 +161,19 @@ class Plan:
 
     def progressive_lists(self, saliency, layer, thresholds, counts=None, lists=None, stream=None):
         """The four work lists [LLL, level 1, level 2, level 3] and their int32[4][2]
-        counts; thresholds maps level -> uint8 threshold."""
+        counts (cgh_select_progressive); thresholds maps level -> uint8 threshold."""
         import torch
         if counts is None:
             counts = torch.zeros((4, 2), dtype=torch.int32, device=self.device)
-        out = []
-        for k in range(4):
-            level = 3 if k == 0 else k
-            thr = -1 if k == 0 else int(thresholds[k])
-            buf = None if lists is None else lists[k]
-            lst, _ = self.select_blocks(saliency, layer, thr, level, out=buf, count=counts[k],
-                                        stream=stream)
-            out.append(lst)
-        return out, counts
+        if lists is None:
+            lists = [torch.empty(self.max_blocks(3 if k == 0 else k), dtype=torch.int32,
+                                 device=self.device) for k in range(4)]
+        thr = (ctypes.c_int * 3)(*[int(thresholds[l]) for l in (1, 2, 3)])
+        ptrs = (ctypes.c_void_p * 4)(*[l.data_ptr() for l in lists])
+        caps = (ctypes.c_int * 4)(*[l.numel() for l in lists])
+        check(lib().cgh_select_progressive(self.handle, _ptr(saliency), _ptr(layer), thr, ptrs, caps,
+                                           _ptr(counts), _stream(stream)))
+        return lists, counts
 
     def progressive_hologram(self, coeffs, lists, counts, holo=None, accumulate=False,
                              form="direct_lut", stream=None):

@@ -134,7 +134,9 @@ int cgh_plan_create(cgh_plan** out, int obj_h, int obj_w, int holo_h, int holo_w
   PLAN_TRY(cudaMalloc(&p->d_a_frac, CGH_MAX_LAYERS * sizeof(double)), "cgh_plan_create: a_frac");
   PLAN_TRY(cudaMalloc(&p->d_a_fixed, CGH_MAX_LAYERS * sizeof(unsigned long long)), "cgh_plan_create: a_fixed");
   PLAN_TRY(cudaMalloc(&p->d_status, sizeof(int)), "cgh_plan_create: status");
-  p->max_chunks = select_num_chunks(obj_h, obj_w, 1);
+  // room for the four selections of one progressive call (LLL, levels 1, 2, 3)
+  p->max_chunks = select_num_chunks(obj_h, obj_w, 1) + select_num_chunks(obj_h, obj_w, 2) +
+                  2 * select_num_chunks(obj_h, obj_w, 3);
   PLAN_TRY(cudaMalloc(&p->d_chunk_cnt, (size_t)n_layers * p->max_chunks * sizeof(int)),
            "cgh_plan_create: chunk counts");
   PLAN_TRY(cudaMalloc(&p->d_chunk_off, (size_t)n_layers * p->max_chunks * sizeof(int)),
@@ -178,6 +180,34 @@ int cgh_select_blocks(const cgh_plan* p, const uint8_t* saliency, const uint8_t*
                            threshold, level, list, d_count, capacity, p->d_chunk_cnt, p->d_chunk_off,
                            (cudaStream_t)stream),
              "cgh_select_blocks");
+  prof_mark(p, CGH_PROF_SELECT, 1, (cudaStream_t)stream);
+  return CGH_OK;
+}
+
+int cgh_select_progressive(const cgh_plan* p, const uint8_t* saliency, const uint8_t* layer_idx,
+                           const int* thresholds, int32_t* const* lists, const int* capacities,
+                           int32_t* d_counts, void* stream) {
+  if (!p || !saliency || !layer_idx || !thresholds || !lists || !capacities || !d_counts)
+    return cgh_fail(CGH_ERR_ARG, "cgh_select_progressive: NULL argument");
+  SelTasks T;
+  memset(&T, 0, sizeof(T));
+  T.n = 4;
+  for (int k = 0; k < 4; ++k) {
+    if (capacities[k] < 0) return cgh_fail(CGH_ERR_ARG, "cgh_select_progressive: capacities[%d] < 0", k);
+    if (capacities[k] > 0 && !lists[k]) return cgh_fail(CGH_ERR_ARG, "cgh_select_progressive: lists[%d] is NULL", k);
+    const int thr = k == 0 ? -1 : thresholds[k - 1];
+    if (thr < -1 || thr > 255)
+      return cgh_fail(CGH_ERR_ARG, "cgh_select_progressive: threshold %d not in -1..255", thr);
+    T.t[k].level = k == 0 ? CGH_LEVELS : k;
+    T.t[k].threshold = thr;
+    T.t[k].capacity = capacities[k];
+    T.t[k].list = lists[k];
+    T.t[k].count = d_counts + 2 * k;
+  }
+  prof_mark(p, CGH_PROF_SELECT, 0, (cudaStream_t)stream);
+  CHECK_CUDA(launch_select_tasks(p->obj_h, p->obj_w, p->n_layers, saliency, layer_idx, T, p->d_chunk_cnt,
+                                 p->d_chunk_off, (cudaStream_t)stream),
+             "cgh_select_progressive");
   prof_mark(p, CGH_PROF_SELECT, 1, (cudaStream_t)stream);
   return CGH_OK;
 }

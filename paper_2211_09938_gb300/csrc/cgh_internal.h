@@ -58,7 +58,19 @@ int cgh_fail(int code, const char* fmt, ...);
 int cgh_cuda_check(cudaError_t e, const char* what);
 
 // Chunk size (blocks) of the ordered compaction.
-#define CGH_SEL_CHUNK 1024
+#define CGH_SEL_CHUNK 256
+
+// One block selection (a level, a threshold, an output list) inside a launch.
+struct SelTask {
+  int level, threshold, capacity;
+  int nchunks, chunk0, cnt_off;  // filled by launch_select_tasks
+  int32_t* list;
+  int32_t* count;
+};
+struct SelTasks {
+  SelTask t[4];
+  int n;
+};
 
 // Kernel launchers (kernels_basic.cu).  All asynchronous on `st`.
 cudaError_t launch_build_tables(const cgh_plan* p, cudaStream_t st);
@@ -72,6 +84,8 @@ cudaError_t launch_direct_lut(const cgh_plan* p, const int32_t* coef, const int3
 cudaError_t launch_plain_direct(const cgh_plan* p, const uint8_t* I, const uint8_t* L, float2* holo,
                                 cudaStream_t st);
 int select_num_chunks(int obj_h, int obj_w, int level);
+cudaError_t launch_select_tasks(int obj_h, int obj_w, int n_layers, const uint8_t* sal, const uint8_t* L,
+                                SelTasks T, int* chunk_cnt, int* chunk_off, cudaStream_t st);
 cudaError_t basic_init_attributes();
 int tc_init_attributes();
 

@@ -13,8 +13,8 @@
 #include "cgh_internal.h"
 
 // Capacity of the shared scratch in ints: counts in the first half, offsets in the
-// second.  n_layers * ceil(blocks_at_level / 1024) may not exceed the half.
-#define CGH_NOALLOC_HALF 65536
+// second.  n_layers * ceil(blocks_at_level / 256) may not exceed the half.
+#define CGH_NOALLOC_HALF 262144
 
 static __device__ __align__(256) int g_noalloc_scratch[2 * CGH_NOALLOC_HALF];
 
@@ -65,7 +65,7 @@ extern "C" int cgh_select_blocks_noalloc(const uint8_t* saliency, const uint8_t*
   const long long need = (long long)n_layers * select_num_chunks(obj_h, obj_w, level);
   if (need > CGH_NOALLOC_HALF)
     return cgh_fail(CGH_ERR_ARG,
-                    "cgh_select_blocks_noalloc: n_layers * ceil(blocks/1024) = %lld exceeds the static "
+                    "cgh_select_blocks_noalloc: n_layers * ceil(blocks/256) = %lld exceeds the static "
                     "scratch limit of %d (e.g. 64 layers at 2048x2048, level 1); use cgh_select_blocks",
                     need, CGH_NOALLOC_HALF);
   int* scratch = nullptr;

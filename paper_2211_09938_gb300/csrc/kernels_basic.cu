@@ -4,6 +4,7 @@
 // Paper: arXiv 2211.09938, Eq. 1 (point-source fringe, paraxial), Eq. 2 (Haar
 // expansion), Eq. 3 (superposition of basis holograms), Section 2 steps 1-5.
 #include <stdio.h>
+#include <string.h>
 
 #include "cgh_internal.h"
 
@@ -176,111 +177,144 @@ int select_num_chunks(int obj_h, int obj_w, int level) {
   return (int)((nb + CGH_SEL_CHUNK - 1) / CGH_SEL_CHUNK);
 }
 
-// Pass 1: per (chunk, layer) counts.  256 threads, CGH_SEL_CHUNK blocks per CTA.
-__global__ void __launch_bounds__(256) k_select_count(const uint8_t* __restrict__ sal,
-                                                      const uint8_t* __restrict__ L, int H, int W,
-                                                      int Z, int threshold, int level,
-                                                      int* __restrict__ chunk_cnt) {
-  __shared__ int s_cnt[CGH_MAX_LAYERS];
-  const int k = 1 << level, nbx = W >> level, nb = (H >> level) * nbx;
-  const int chunk = blockIdx.x, nchunks = gridDim.x;
-  for (int t = threadIdx.x; t < Z; t += blockDim.x) s_cnt[t] = 0;
-  __syncthreads();
-  unsigned long long m[CGH_SEL_CHUNK / 256];
-#pragma unroll
-  for (int q = 0; q < CGH_SEL_CHUNK / 256; ++q) {
-    const int b = chunk * CGH_SEL_CHUNK + q * 256 + threadIdx.x;
-    m[q] = b < nb ? block_layer_mask(sal, L, W, k, b / nbx, b % nbx, threshold, Z) : 0ull;
-  }
-  for (int z = 0; z < Z; ++z) {
-    int c = 0;
-#pragma unroll
-    for (int q = 0; q < CGH_SEL_CHUNK / 256; ++q) c += (int)((m[q] >> z) & 1ull);
-    c = __reduce_add_sync(0xffffffffu, c);
-    if ((threadIdx.x & 31) == 0 && c) atomicAdd(&s_cnt[z], c);
-  }
-  __syncthreads();
-  for (int z = threadIdx.x; z < Z; z += blockDim.x) chunk_cnt[z * nchunks + chunk] = s_cnt[z];
+// A launch may serve up to four selections (the LLL list and the three detail levels);
+// each owns a contiguous range of the grid's chunks and of the count scratch.
+__device__ __forceinline__ int sel_task_of(const SelTasks& T, int chunk) {
+  int k = 0;
+  for (int q = 1; q < T.n; ++q)
+    if (chunk >= T.t[q].chunk0) k = q;
+  return k;
 }
 
-// Pass 2: exclusive scan of the counts in (layer, chunk) order; one CTA of 1024 threads.
+// Pass 1: per (task, layer, chunk) counts; one thread per block of the chunk.
+__global__ void __launch_bounds__(CGH_SEL_CHUNK) k_select_count(const uint8_t* __restrict__ sal,
+                                                                const uint8_t* __restrict__ L, int H, int W,
+                                                                int Z, const SelTasks T,
+                                                                int* __restrict__ chunk_cnt) {
+  __shared__ int s_cnt[CGH_MAX_LAYERS];
+  const SelTask& tk = T.t[sel_task_of(T, blockIdx.x)];
+  const int chunk = blockIdx.x - tk.chunk0;
+  const int level = tk.level, nbx = W >> level, nb = (H >> level) * nbx;
+  for (int t = threadIdx.x; t < Z; t += blockDim.x) s_cnt[t] = 0;
+  __syncthreads();
+  const int b = chunk * CGH_SEL_CHUNK + threadIdx.x;
+  unsigned long long m =
+      b < nb ? block_layer_mask(sal, L, W, 1 << level, b / nbx, b % nbx, tk.threshold, Z) : 0ull;
+  while (m) {
+    atomicAdd(&s_cnt[__ffsll((long long)m) - 1], 1);
+    m &= m - 1ull;
+  }
+  __syncthreads();
+  for (int z = threadIdx.x; z < Z; z += blockDim.x) chunk_cnt[tk.cnt_off + z * tk.nchunks + chunk] = s_cnt[z];
+}
+
+// Pass 2: per task, exclusive scan of its counts in (layer, chunk) order; one CTA of 1024
+// threads per task.
 __global__ void __launch_bounds__(1024) k_select_scan(const int* __restrict__ chunk_cnt,
-                                                      int* __restrict__ chunk_off, int n,
-                                                      int capacity, int32_t* __restrict__ d_count) {
+                                                      int* __restrict__ chunk_off, int Z, const SelTasks T) {
   __shared__ int s_part[1024];
+  const SelTask& tk = T.t[blockIdx.x];
+  const int n = Z * tk.nchunks;
+  const int* cnt = chunk_cnt + tk.cnt_off;
+  int* off = chunk_off + tk.cnt_off;
   const int per = (n + 1023) / 1024;
   const int lo = threadIdx.x * per, hi = min(n, lo + per);
   int sum = 0;
-  for (int i = lo; i < hi; ++i) sum += chunk_cnt[i];
+  for (int i = lo; i < hi; ++i) sum += cnt[i];
   s_part[threadIdx.x] = sum;
   __syncthreads();
-  for (int off = 1; off < 1024; off <<= 1) {  // inclusive Hillis-Steele scan
-    const int v = threadIdx.x >= off ? s_part[threadIdx.x - off] : 0;
+  for (int o = 1; o < 1024; o <<= 1) {  // inclusive Hillis-Steele scan
+    const int v = threadIdx.x >= o ? s_part[threadIdx.x - o] : 0;
     __syncthreads();
     s_part[threadIdx.x] += v;
     __syncthreads();
   }
   int run = s_part[threadIdx.x] - sum;
   for (int i = lo; i < hi; ++i) {
-    chunk_off[i] = run;
-    run += chunk_cnt[i];
+    off[i] = run;
+    run += cnt[i];
   }
   if (threadIdx.x == 1023) {
     const int total = s_part[1023];
-    d_count[0] = min(total, capacity);
-    d_count[1] = total;
+    tk.count[0] = min(total, tk.capacity);
+    tk.count[1] = total;
   }
 }
 
-// Pass 3: ordered scatter.  One thread per block of the chunk; per layer a warp ballot
-// gives the rank inside the warp and a shared scan the warp offsets.
+// Pass 3: ordered scatter.  Per layer a warp ballot gives the rank inside the warp and a
+// shared scan the warp offsets.
 __global__ void __launch_bounds__(CGH_SEL_CHUNK) k_select_scatter(
-    const uint8_t* __restrict__ sal, const uint8_t* __restrict__ L, int H, int W, int Z,
-    int threshold, int level, const int* __restrict__ chunk_cnt, const int* __restrict__ chunk_off,
-    int32_t* __restrict__ list, int capacity) {
+    const uint8_t* __restrict__ sal, const uint8_t* __restrict__ L, int H, int W, int Z, const SelTasks T,
+    const int* __restrict__ chunk_cnt, const int* __restrict__ chunk_off) {
   __shared__ int s_warp[CGH_SEL_CHUNK / 32];
-  const int k = 1 << level, nbx = W >> level, nb = (H >> level) * nbx;
-  const int chunk = blockIdx.x, nchunks = gridDim.x;
+  const SelTask& tk = T.t[sel_task_of(T, blockIdx.x)];
+  const int chunk = blockIdx.x - tk.chunk0;
+  const int level = tk.level, nbx = W >> level, nb = (H >> level) * nbx;
   const int b = chunk * CGH_SEL_CHUNK + threadIdx.x;
   const int by = b / nbx, bx = b - by * nbx;
   const unsigned long long m =
-      b < nb ? block_layer_mask(sal, L, W, k, by, bx, threshold, Z) : 0ull;
+      b < nb ? block_layer_mask(sal, L, W, 1 << level, by, bx, tk.threshold, Z) : 0ull;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int z = 0; z < Z; ++z) {
-    if (chunk_cnt[z * nchunks + chunk] == 0) continue;  // uniform over the CTA
+    const int ci = tk.cnt_off + z * tk.nchunks + chunk;
+    if (chunk_cnt[ci] == 0) continue;  // uniform over the CTA
     const bool f = (m >> z) & 1ull;
     const unsigned bal = __ballot_sync(0xffffffffu, f);
     if (lane == 0) s_warp[warp] = __popc(bal);
     __syncthreads();
     if (warp == 0) {
-      const int v = s_warp[lane];
+      const int v = lane < CGH_SEL_CHUNK / 32 ? s_warp[lane] : 0;
       int inc = v;
 #pragma unroll
-      for (int off = 1; off < 32; off <<= 1) {
-        const int t = __shfl_up_sync(0xffffffffu, inc, off);
-        if (lane >= off) inc += t;
+      for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += t;
       }
-      s_warp[lane] = inc - v;
+      if (lane < CGH_SEL_CHUNK / 32) s_warp[lane] = inc - v;
     }
     __syncthreads();
     if (f) {
-      const int pos = chunk_off[z * nchunks + chunk] + s_warp[warp] +
-                      __popc(bal & ((1u << lane) - 1u));
-      if (pos < capacity) list[pos] = (z << 24) | (by << 12) | bx;
+      const int pos = chunk_off[ci] + s_warp[warp] + __popc(bal & ((1u << lane) - 1u));
+      if (pos < tk.capacity) tk.list[pos] = (z << 24) | (by << 12) | bx;
     }
     __syncthreads();
   }
 }
 
+int select_tasks_chunks(const SelTasks& T) {
+  int n = 0;
+  for (int k = 0; k < T.n; ++k) n += T.t[k].nchunks;
+  return n;
+}
+
+// Fills chunk0 / cnt_off of the tasks and launches the three passes.
+cudaError_t launch_select_tasks(int obj_h, int obj_w, int n_layers, const uint8_t* sal, const uint8_t* L,
+                                SelTasks T, int* chunk_cnt, int* chunk_off, cudaStream_t st) {
+  int c0 = 0;
+  for (int k = 0; k < T.n; ++k) {
+    T.t[k].nchunks = select_num_chunks(obj_h, obj_w, T.t[k].level);
+    T.t[k].chunk0 = c0;
+    T.t[k].cnt_off = c0 * n_layers;
+    c0 += T.t[k].nchunks;
+  }
+  k_select_count<<<c0, CGH_SEL_CHUNK, 0, st>>>(sal, L, obj_h, obj_w, n_layers, T, chunk_cnt);
+  k_select_scan<<<T.n, 1024, 0, st>>>(chunk_cnt, chunk_off, n_layers, T);
+  k_select_scatter<<<c0, CGH_SEL_CHUNK, 0, st>>>(sal, L, obj_h, obj_w, n_layers, T, chunk_cnt, chunk_off);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_select(int obj_h, int obj_w, int n_layers, const uint8_t* sal, const uint8_t* L,
                           int threshold, int level, int32_t* list, int32_t* d_count, int capacity,
                           int* chunk_cnt, int* chunk_off, cudaStream_t st) {
-  const int nchunks = select_num_chunks(obj_h, obj_w, level);
-  k_select_count<<<nchunks, 256, 0, st>>>(sal, L, obj_h, obj_w, n_layers, threshold, level, chunk_cnt);
-  k_select_scan<<<1, 1024, 0, st>>>(chunk_cnt, chunk_off, nchunks * n_layers, capacity, d_count);
-  k_select_scatter<<<nchunks, CGH_SEL_CHUNK, 0, st>>>(sal, L, obj_h, obj_w, n_layers, threshold,
-                                                      level, chunk_cnt, chunk_off, list, capacity);
-  return cudaGetLastError();
+  SelTasks T;
+  memset(&T, 0, sizeof(T));
+  T.n = 1;
+  T.t[0].level = level;
+  T.t[0].threshold = threshold;
+  T.t[0].capacity = capacity;
+  T.t[0].list = list;
+  T.t[0].count = d_count;
+  return launch_select_tasks(obj_h, obj_w, n_layers, sal, L, T, chunk_cnt, chunk_off, st);
 }
 
 // ---------------------------------------------------------------------------
