@@ -155,6 +155,7 @@ struct TcGemmArgs {
   const int* kc_pad; // [Z] padded compacted column counts
   int n_layers;
   int M, N, K;       // test: sizes; stages: M and N of the output (K from the device)
+  int tm, tn, tz;    // work units: M tiles x N tiles x (layers | K splits | 1)
   float scale;
   float2* H;         // EPI_H: complex output [M][N]
   int ldh;
@@ -171,11 +172,11 @@ template <int KIND>
 struct TcCfg;
 template <>
 struct TcCfg<KIND_TEST> {
-  static constexpr int NA = 1, NB = 1, NST = 6;
+  static constexpr int NA = 1, NB = 1, NST = 8;  // > 114 KiB: one CTA (and one TMEM owner) per SM
 };
 template <>
 struct TcCfg<KIND_CR> {
-  static constexpr int NA = 4, NB = 2, NST = 2;  // short K loops: two CTAs per SM instead of depth
+  static constexpr int NA = 4, NB = 2, NST = 4;
 };
 template <>
 struct TcCfg<KIND_CC> {
@@ -237,8 +238,54 @@ __device__ __forceinline__ void split_hi_lo(float x, uint16_t& hi, uint16_t& lo)
   }
 }
 
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+struct TileInfo {
+  int a_row, b_row, k_lo, nk, out_row0, out_col0, n_valid;
+};
+
+// Work unit t of the persistent grid: (mt fastest, then nt, then the layer / K split).
+// Returns false for units with nothing to do; every role decodes identically.
+__device__ __forceinline__ bool decode_tile(const TcGemmArgs& a, int t, const int* s_off, int ktot, TileInfo& ti) {
+  const int mt = t % a.tm, r = t / a.tm, nt = r % a.tn, zz = r / a.tn;
+  ti.out_row0 = mt * TC_BM;
+  ti.n_valid = TC_BN;
+  if (a.mode == 1) {
+    const int krz = s_off[zz + 1] - s_off[zz];
+    ti.n_valid = min(TC_BN, krz - nt * TC_BN);
+    if (ti.n_valid <= 0) return false;
+    ti.a_row = zz * a.a_rows_per_z + mt * TC_BM;
+    ti.b_row = s_off[zz] + nt * TC_BN;
+    ti.k_lo = 0;
+    ti.nk = a.kc_pad[zz] / TC_BK;
+    ti.out_col0 = s_off[zz] + nt * TC_BN;
+  } else if (a.mode == 2) {
+    const int nkt = ktot / TC_BK, S = a.tz;
+    const int k0 = (int)((long long)nkt * zz / S), k1 = (int)((long long)nkt * (zz + 1) / S);
+    ti.a_row = mt * TC_BM;
+    ti.b_row = nt * TC_BN;
+    ti.k_lo = k0 * TC_BK;
+    ti.nk = k1 - k0;
+    ti.out_col0 = nt * TC_BN;
+  } else {
+    ti.a_row = mt * TC_BM;
+    ti.b_row = nt * TC_BN;
+    ti.k_lo = 0;
+    ti.nk = a.K / TC_BK;
+    ti.out_col0 = nt * TC_BN;
+  }
+  return ti.nk > 0;
+}
+
+// Persistent warp-specialised GEMM.  Warp 0 (one lane) streams operand tiles with TMA
+// through an NST-deep shared-memory ring; warp 1 owns the tensor memory (512 columns:
+// two accumulator buffers of Re | Im) and one lane issues the MMAs; warps 2-5 drain a
+// finished buffer (TMEM -> registers -> global) while the next tile accumulates in the
+// other buffer.
 template <int KIND, int EPI, bool F16>
-__global__ void __launch_bounds__(128, 1) k_tc_gemm(const __grid_constant__ CUtensorMap mapA,
+__global__ void __launch_bounds__(192, 1) k_tc_gemm(const __grid_constant__ CUtensorMap mapA,
                                                      const __grid_constant__ CUtensorMap mapB,
                                                      const TcGemmArgs args) {
   using Cfg = TcCfg<KIND>;
@@ -246,60 +293,33 @@ __global__ void __launch_bounds__(128, 1) k_tc_gemm(const __grid_constant__ CUte
   constexpr uint32_t STAGE = (NA + NB) * TC_PLANE_BYTES;
   extern __shared__ uint8_t tc_smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)tc_smem_raw + 1023) & ~(uintptr_t)1023);
-  __shared__ __align__(8) uint64_t full_bar[NST], empty_bar[NST], accum_bar;
+  __shared__ __align__(8) uint64_t full_bar[NST], empty_bar[NST], tfull_bar[2], tempty_bar[2], done_bar;
   __shared__ uint32_t s_tmem;
   __shared__ volatile int s_abort;
+  __shared__ int s_off[CGH_MAX_LAYERS + 1];
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-
-  // ---- decode the tile
-  int a_row = 0, b_row = 0, k_lo = 0, k_hi = 0, out_row0 = 0, out_col0 = 0, n_valid = TC_BN;
-  const int mt = blockIdx.x, nt = blockIdx.y;
-  if (args.mode == 1) {
-    const int z = blockIdx.z;
-    int off = 0;
-    for (int q = 0; q < z; ++q) off += args.kr_pad[q];
-    const int krz = args.kr_pad[z];
-    n_valid = min(TC_BN, krz - nt * TC_BN);
-    if (n_valid <= 0) return;
-    a_row = z * args.a_rows_per_z + mt * TC_BM;
-    b_row = off + nt * TC_BN;
-    k_lo = 0;
-    k_hi = args.kc_pad[z];
-    out_row0 = mt * TC_BM;
-    out_col0 = off + nt * TC_BN;
-  } else if (args.mode == 2) {
-    int ktot = 0;
-    for (int q = 0; q < args.n_layers; ++q) ktot += args.kr_pad[q];
-    const int nkt = ktot / TC_BK, S = gridDim.z, sp = blockIdx.z;
-    k_lo = (int)((long long)nkt * sp / S) * TC_BK;
-    k_hi = (int)((long long)nkt * (sp + 1) / S) * TC_BK;
-    a_row = mt * TC_BM;
-    b_row = nt * TC_BN;
-    out_row0 = mt * TC_BM;
-    out_col0 = nt * TC_BN;
-  } else {
-    k_lo = 0;
-    k_hi = args.K;
-    a_row = mt * TC_BM;
-    b_row = nt * TC_BN;
-    out_row0 = mt * TC_BM;
-    out_col0 = nt * TC_BN;
-  }
-  const int nk = (k_hi - k_lo) / TC_BK;
-  if (nk <= 0 && EPI == EPI_H) return;  // nothing to add to H
+  const int total = args.tm * args.tn * args.tz;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < NST; ++s) {
       mbar_init(&full_bar[s], 1);
       mbar_init(&empty_bar[s], 1);
     }
-    mbar_init(&accum_bar, 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&tfull_bar[b], 1);
+      mbar_init(&tempty_bar[b], 4);
+    }
+    mbar_init(&done_bar, 1);
     s_abort = 0;
+    int o = 0;
+    s_off[0] = 0;
+    if (args.mode != 0)
+      for (int q = 0; q < args.n_layers; ++q) s_off[q + 1] = (o += args.kr_pad[q]);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 1) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 256;" ::"r"(smem_u32(&s_tmem))
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(smem_u32(&s_tmem))
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -308,140 +328,188 @@ __global__ void __launch_bounds__(128, 1) k_tc_gemm(const __grid_constant__ CUte
   tc_fence_after();
   const uint32_t tmem = s_tmem;
   const uint32_t smem_base = smem_u32(smem);
+  const int ktot = args.mode == 2 ? s_off[args.n_layers] : 0;
 
-  if (warp == 0 && lane == 0) {
-    // ---- TMA producer
-    int issued_phase[NST];
-    bool issued[NST];
-    for (int s = 0; s < NST; ++s) issued[s] = false, issued_phase[s] = 0;
-    for (int kt = 0; kt < nk; ++kt) {
-      const int s = kt % NST;
-      const uint32_t ph = (uint32_t)(kt / NST) & 1u;
-      if (!mbar_wait_bounded(&empty_bar[s], ph ^ 1u, &s_abort, args.status)) break;
-      uint8_t* st = smem + s * STAGE;
-      mbar_arrive_expect_tx(&full_bar[s], STAGE);
-      tma_load_3d(st, &mapA, &full_bar[s], k_lo + kt * TC_BK, a_row, 0);
-      tma_load_3d(st + NA * TC_PLANE_BYTES, &mapB, &full_bar[s], k_lo + kt * TC_BK, b_row, 0);
-      issued[s] = true;
-      issued_phase[s] = (int)ph;
-    }
-    if (s_abort) {  // let the copies in flight land before the CTA's shared memory goes away
-      for (int s = 0; s < NST; ++s)
-        if (issued[s]) {
-          const uint64_t t0 = global_timer();
-          while (!mbar_try_wait(&full_bar[s], (uint32_t)issued_phase[s]) && global_timer() - t0 < TC_WAIT_NS) {
+  if (warp == 0) {
+    if (lane == 0) {
+      // ---- TMA producer
+      int it = 0;
+      bool issued[NST];
+      uint32_t issued_ph[NST];
+      for (int s = 0; s < NST; ++s) issued[s] = false, issued_ph[s] = 0;
+      bool ok = true;
+      for (int t = blockIdx.x; t < total && ok; t += gridDim.x) {
+        TileInfo ti;
+        if (!decode_tile(args, t, s_off, ktot, ti)) continue;
+        for (int kt = 0; kt < ti.nk; ++kt, ++it) {
+          const int s = it % NST;
+          const uint32_t ph = (uint32_t)(it / NST) & 1u;
+          if (!mbar_wait_bounded(&empty_bar[s], ph ^ 1u, &s_abort, args.status)) {
+            ok = false;
+            break;
           }
+          uint8_t* st = smem + s * STAGE;
+          mbar_arrive_expect_tx(&full_bar[s], STAGE);
+          tma_load_3d(st, &mapA, &full_bar[s], ti.k_lo + kt * TC_BK, ti.a_row, 0);
+          tma_load_3d(st + NA * TC_PLANE_BYTES, &mapB, &full_bar[s], ti.k_lo + kt * TC_BK, ti.b_row, 0);
+          issued[s] = true;
+          issued_ph[s] = ph;
         }
+      }
+      if (s_abort) {  // let copies in flight land before shared memory goes away
+        for (int s = 0; s < NST; ++s)
+          if (issued[s]) {
+            const uint64_t t0 = global_timer();
+            while (!mbar_try_wait(&full_bar[s], issued_ph[s]) && global_timer() - t0 < TC_WAIT_NS) {
+            }
+          }
+      }
     }
-  } else if (warp == 1 && lane == 0) {
-    // ---- MMA issuer
-    const uint32_t id_pos = idesc_f16(F16 ? 0 : 1, 0, TC_BM, TC_BN);
-    const uint32_t id_neg = idesc_f16(F16 ? 0 : 1, 1, TC_BM, TC_BN);
-    for (int kt = 0; kt < nk; ++kt) {
-      const int s = kt % NST;
-      const uint32_t ph = (uint32_t)(kt / NST) & 1u;
-      if (!mbar_wait_bounded(&full_bar[s], ph, &s_abort, args.status)) break;
-      tc_fence_after();
-      const uint32_t a_base = smem_base + s * STAGE;
-      const uint32_t b_base = a_base + NA * TC_PLANE_BYTES;
+    __syncwarp();
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // ---- MMA issuer
+      const uint32_t id_pos = idesc_f16(F16 ? 0 : 1, 0, TC_BM, TC_BN);
+      const uint32_t id_neg = idesc_f16(F16 ? 0 : 1, 1, TC_BM, TC_BN);
+      int it = 0, local = 0;
+      bool ok = true;
+      for (int t = blockIdx.x; t < total && ok; t += gridDim.x) {
+        TileInfo ti;
+        if (!decode_tile(args, t, s_off, ktot, ti)) continue;
+        const int buf = local & 1;
+        const uint32_t use_ph = (uint32_t)(local >> 1) & 1u;
+        if (!mbar_wait_bounded(&tempty_bar[buf], use_ph ^ 1u, &s_abort, args.status)) break;
+        tc_fence_after();
+        const uint32_t acc = tmem + buf * 256;
+        for (int kt = 0; kt < ti.nk; ++kt, ++it) {
+          const int s = it % NST;
+          const uint32_t ph = (uint32_t)(it / NST) & 1u;
+          if (!mbar_wait_bounded(&full_bar[s], ph, &s_abort, args.status)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t a_base = smem_base + s * STAGE;
+          const uint32_t b_base = a_base + NA * TC_PLANE_BYTES;
 #pragma unroll
-      for (int kk = 0; kk < TC_BK / 16; ++kk)
-        issue_products<KIND>(tmem, a_base, b_base, kk, id_pos, id_neg, kt == 0 && kk == 0);
-      mma_commit(&empty_bar[s]);
+          for (int kk = 0; kk < TC_BK / 16; ++kk)
+            issue_products<KIND>(acc, a_base, b_base, kk, id_pos, id_neg, kt == 0 && kk == 0);
+          mma_commit(&empty_bar[s]);
+        }
+        mma_commit(&tfull_bar[buf]);
+        ++local;
+      }
+      // every MMA issued above completes before the accumulators are released
+      mma_commit(&done_bar);
+      const uint64_t t0 = global_timer();
+      while (!mbar_try_wait(&done_bar, 0) && global_timer() - t0 < TC_WAIT_NS) {
+      }
     }
-    mma_commit(&accum_bar);  // completes when every MMA issued above has finished
-  }
-  __syncwarp();
-
-  // ---- epilogue: all four warps; warp w reads TMEM lanes 32*w .. 32*w+31
-  bool have = mbar_wait_bounded(&accum_bar, 0, &s_abort, args.status);
-  have = __all_sync(0xffffffffu, have && !s_abort);  // tcgen05.ld below is warp-collective
-  tc_fence_after();
-  const int row = out_row0 + warp * 32 + lane;
-  const uint32_t t_lane = tmem + ((uint32_t)(warp * 32) << 16);
-  if (have || (EPI == EPI_Y && nk == 0)) {
+    __syncwarp();
+  } else {
+    // ---- epilogue warps 2..5: TMEM lane quarter (warp % 4) -> 32 output rows
+    const int quarter = warp & 3;
+    int local = 0;
+    for (int t = blockIdx.x; t < total; t += gridDim.x) {
+      TileInfo ti;
+      if (!decode_tile(args, t, s_off, ktot, ti)) continue;
+      const int buf = local & 1;
+      const uint32_t ph = (uint32_t)(local >> 1) & 1u;
+      bool have = mbar_wait_bounded(&tfull_bar[buf], ph, &s_abort, args.status);
+      have = __all_sync(0xffffffffu, have && !s_abort);  // tcgen05.ld below is warp-collective
+      if (!have) break;
+      tc_fence_after();
+      const int row = ti.out_row0 + quarter * 32 + lane;
+      const uint32_t t_lane = tmem + buf * 256 + ((uint32_t)(quarter * 32) << 16);
 #pragma unroll 1
-    for (int c0 = 0; c0 < TC_BN; c0 += 32) {
-      uint32_t re[32], im[32];
-      if (nk > 0) {
+      for (int c0 = 0; c0 < TC_BN; c0 += 32) {
+        uint32_t re[32], im[32];
         tmem_ld32(t_lane + c0, re);
         if (KIND != KIND_TEST) tmem_ld32(t_lane + 128 + c0, im);
         tmem_ld_wait();
-      } else {
+        if (EPI == EPI_H) {
+          if (row < args.M) {
+            float2* dst = args.H + (size_t)row * args.ldh + ti.out_col0 + c0;
+            const int nv = min(32, args.N - (ti.out_col0 + c0));
+            if (nv == 32 && args.h_vec4) {
 #pragma unroll
-        for (int j = 0; j < 32; ++j) re[j] = im[j] = 0u;
-      }
-      if (EPI == EPI_H) {
-        if (row < args.M) {
-          float2* dst = args.H + (size_t)row * args.ldh + out_col0 + c0;
-          const int nv = min(32, args.N - (out_col0 + c0));
-          if (nv == 32 && args.h_vec4) {
+              for (int j = 0; j < 32; j += 2) {
+                float4 v = make_float4(__uint_as_float(re[j]) * args.scale, __uint_as_float(im[j]) * args.scale,
+                                       __uint_as_float(re[j + 1]) * args.scale,
+                                       __uint_as_float(im[j + 1]) * args.scale);
+                atomicAdd(reinterpret_cast<float4*>(dst + j), v);
+              }
+            } else {
 #pragma unroll
-            for (int j = 0; j < 32; j += 2) {
-              float4 v = make_float4(__uint_as_float(re[j]) * args.scale, __uint_as_float(im[j]) * args.scale,
-                                     __uint_as_float(re[j + 1]) * args.scale,
-                                     __uint_as_float(im[j + 1]) * args.scale);
-              atomicAdd(reinterpret_cast<float4*>(dst + j), v);
+              for (int j = 0; j < 32; ++j)
+                if (j < nv)
+                  atomicAdd(dst + j, make_float2(__uint_as_float(re[j]) * args.scale,
+                                                 __uint_as_float(im[j]) * args.scale));
             }
-          } else {
-            for (int j = 0; j < nv; ++j)
-              atomicAdd(dst + j, make_float2(__uint_as_float(re[j]) * args.scale,
-                                             __uint_as_float(im[j]) * args.scale));
+          }
+        } else if (EPI == EPI_Y) {
+          if (row < args.M) {
+            const int nv = min(32, ti.n_valid - c0);
+            uint16_t* base = args.Y + (size_t)row * args.ldy + ti.out_col0 + c0;
+            if (nv == 32) {  // 64 contiguous bytes per plane: four 16-byte stores each
+              uint32_t prh[16], prl[16], pih[16], pil[16];
+#pragma unroll
+              for (int j = 0; j < 32; j += 2) {
+                uint16_t a0, a1, b0, b1, c0h, c1h, d0, d1;
+                split_hi_lo<F16>(__uint_as_float(re[j]) * args.scale, a0, b0);
+                split_hi_lo<F16>(__uint_as_float(re[j + 1]) * args.scale, a1, b1);
+                split_hi_lo<F16>(__uint_as_float(im[j]) * args.scale, c0h, d0);
+                split_hi_lo<F16>(__uint_as_float(im[j + 1]) * args.scale, c1h, d1);
+                prh[j / 2] = (uint32_t)a0 | ((uint32_t)a1 << 16);
+                prl[j / 2] = (uint32_t)b0 | ((uint32_t)b1 << 16);
+                pih[j / 2] = (uint32_t)c0h | ((uint32_t)c1h << 16);
+                pil[j / 2] = (uint32_t)d0 | ((uint32_t)d1 << 16);
+              }
+              uint4* q0 = reinterpret_cast<uint4*>(base);
+              uint4* q1 = reinterpret_cast<uint4*>(base + args.y_plane);
+              uint4* q2 = reinterpret_cast<uint4*>(base + 2 * args.y_plane);
+              uint4* q3 = reinterpret_cast<uint4*>(base + 3 * args.y_plane);
+#pragma unroll
+              for (int v = 0; v < 4; ++v) {
+                q0[v] = make_uint4(prh[4 * v], prh[4 * v + 1], prh[4 * v + 2], prh[4 * v + 3]);
+                q1[v] = make_uint4(prl[4 * v], prl[4 * v + 1], prl[4 * v + 2], prl[4 * v + 3]);
+                q2[v] = make_uint4(pih[4 * v], pih[4 * v + 1], pih[4 * v + 2], pih[4 * v + 3]);
+                q3[v] = make_uint4(pil[4 * v], pil[4 * v + 1], pil[4 * v + 2], pil[4 * v + 3]);
+              }
+            } else {
+#pragma unroll
+              for (int j = 0; j < 32; ++j)
+                if (j < nv) {
+                  uint16_t rh, rl, ih, il;
+                  split_hi_lo<F16>(__uint_as_float(re[j]) * args.scale, rh, rl);
+                  split_hi_lo<F16>(__uint_as_float(im[j]) * args.scale, ih, il);
+                  base[j] = rh;
+                  base[args.y_plane + j] = rl;
+                  base[2 * args.y_plane + j] = ih;
+                  base[3 * args.y_plane + j] = il;
+                }
+            }
+          }
+        } else {
+          if (row < args.M) {
+#pragma unroll
+            for (int j = 0; j < 32; ++j)
+              if (ti.out_col0 + c0 + j < args.N)
+                args.C[(size_t)row * args.ldc + ti.out_col0 + c0 + j] = __uint_as_float(re[j]) * args.scale;
           }
         }
-      } else if (EPI == EPI_Y) {
-        if (row < args.M) {
-          const int nv = min(32, n_valid - c0);
-          uint16_t* base = args.Y + (size_t)row * args.ldy + out_col0 + c0;
-          if (nv == 32) {  // 64 contiguous bytes per plane: four 16-byte stores each
-            uint32_t prh[16], prl[16], pih[16], pil[16];
-#pragma unroll
-            for (int j = 0; j < 32; j += 2) {
-              uint16_t a0, a1, b0, b1, c0h, c1h, d0, d1;
-              split_hi_lo<F16>(__uint_as_float(re[j]) * args.scale, a0, b0);
-              split_hi_lo<F16>(__uint_as_float(re[j + 1]) * args.scale, a1, b1);
-              split_hi_lo<F16>(__uint_as_float(im[j]) * args.scale, c0h, d0);
-              split_hi_lo<F16>(__uint_as_float(im[j + 1]) * args.scale, c1h, d1);
-              prh[j / 2] = (uint32_t)a0 | ((uint32_t)a1 << 16);
-              prl[j / 2] = (uint32_t)b0 | ((uint32_t)b1 << 16);
-              pih[j / 2] = (uint32_t)c0h | ((uint32_t)c1h << 16);
-              pil[j / 2] = (uint32_t)d0 | ((uint32_t)d1 << 16);
-            }
-            uint4* q0 = reinterpret_cast<uint4*>(base);
-            uint4* q1 = reinterpret_cast<uint4*>(base + args.y_plane);
-            uint4* q2 = reinterpret_cast<uint4*>(base + 2 * args.y_plane);
-            uint4* q3 = reinterpret_cast<uint4*>(base + 3 * args.y_plane);
-#pragma unroll
-            for (int v = 0; v < 4; ++v) {
-              q0[v] = make_uint4(prh[4 * v], prh[4 * v + 1], prh[4 * v + 2], prh[4 * v + 3]);
-              q1[v] = make_uint4(prl[4 * v], prl[4 * v + 1], prl[4 * v + 2], prl[4 * v + 3]);
-              q2[v] = make_uint4(pih[4 * v], pih[4 * v + 1], pih[4 * v + 2], pih[4 * v + 3]);
-              q3[v] = make_uint4(pil[4 * v], pil[4 * v + 1], pil[4 * v + 2], pil[4 * v + 3]);
-            }
-          } else
-          for (int j = 0; j < nv; ++j) {
-            uint16_t rh, rl, ih, il;
-            split_hi_lo<F16>(__uint_as_float(re[j]) * args.scale, rh, rl);
-            split_hi_lo<F16>(__uint_as_float(im[j]) * args.scale, ih, il);
-            base[j] = rh;
-            base[args.y_plane + j] = rl;
-            base[2 * args.y_plane + j] = ih;
-            base[3 * args.y_plane + j] = il;
-          }
-        }
-      } else {
-        if (row < args.M) {
-          for (int j = 0; j < 32 && out_col0 + c0 + j < args.N; ++j)
-            args.C[(size_t)row * args.ldc + out_col0 + c0 + j] = __uint_as_float(re[j]) * args.scale;
-        }
       }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&tempty_bar[buf]);
+      ++local;
     }
   }
   tc_fence_before();
   __syncthreads();
   if (warp == 1) {
     tc_fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;" ::"r"(tmem) : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem) : "memory");
   }
 }
 
@@ -526,43 +594,85 @@ __global__ void __launch_bounds__(1024) k_tc_compact(TcFlags fl, int H, int W, i
 
 // 64 x A^_z at (rows[k], cols[c]) from the Haar coefficients and the selection flags:
 // V = LLL + sum_{l=3,2,1} 4^(3-l) [selected] (sx X + sy Y + sx sy D), with sx = -1 for the
-// right child column and sy = -1 for the lower child row of the level-l cell.
+// right child column and sy = -1 for the lower child row of the level-l cell.  One thread
+// builds 8 consecutive compacted columns: they are one 8-pixel band of the object (or all
+// padding), so they share one LLL block, one level-3 block, two level-2 and four level-1
+// blocks.
+template <bool F16>
 __global__ void k_tc_idwt(const int32_t* __restrict__ coef, TcFlags fl, const int* __restrict__ rows,
                           const int* __restrict__ cols, const int* __restrict__ kr_pad,
                           const int* __restrict__ kc_pad, int H, int W, int ld_rows, int ld_cols,
-                          uint16_t* __restrict__ B1, long long b1_plane, int ldb1, int is_f16) {
+                          uint16_t* __restrict__ B1, long long b1_plane, int ldb1) {
   const int z = blockIdx.z;
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  const int c = 8 * (blockIdx.x * blockDim.x + threadIdx.x);
   const int k = blockIdx.y * blockDim.y + threadIdx.y;
   if (k >= kr_pad[z] || c >= kc_pad[z]) return;
   int off = 0;
   for (int q = 0; q < z; ++q) off += kr_pad[q];
-  const int i = rows[(size_t)z * ld_rows + k], j = cols[(size_t)z * ld_cols + c];
-  int V = 0;
-  if (i >= 0 && j >= 0) {
-    const int32_t* P = coef + (size_t)z * H * W;
-    const int h3 = H >> 3, w3 = W >> 3;
-    if (fl.occ3[((size_t)z * h3 + (i >> 3)) * w3 + (j >> 3)]) V = P[(size_t)(i >> 3) * W + (j >> 3)];
+  const int i = rows[(size_t)z * ld_rows + k], j0 = cols[(size_t)z * ld_cols + c];
+  int V[8];
 #pragma unroll
-    for (int l = 3; l >= 1; --l) {
-      const int hl = H >> l, wl = W >> l, by = i >> l, bx = j >> l;
-      if (fl.sel[l][((size_t)z * hl + by) * wl + bx]) {
-        const int X = P[(size_t)by * W + wl + bx];
-        const int Y = P[(size_t)(hl + by) * W + bx];
-        const int D = P[(size_t)(hl + by) * W + wl + bx];
-        const int sx = ((j >> (l - 1)) & 1) ? -1 : 1, sy = ((i >> (l - 1)) & 1) ? -1 : 1;
-        V += (1 << (2 * (3 - l))) * (sx * X + sy * Y + sx * sy * D);
+  for (int q = 0; q < 8; ++q) V[q] = 0;
+  if (i >= 0 && j0 >= 0) {
+    const int32_t* P = coef + (size_t)z * H * W;
+    const int h3 = H >> 3, w3 = W >> 3, by3 = i >> 3, bx3 = j0 >> 3;
+    const size_t f3 = ((size_t)z * h3 + by3) * w3 + bx3;
+    if (fl.occ3[f3]) {
+      const int LL = P[(size_t)by3 * W + bx3];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) V[q] = LL;
+    }
+    if (fl.sel[3][f3]) {
+      const int X = P[(size_t)by3 * W + w3 + bx3], Y = P[(size_t)(h3 + by3) * W + bx3],
+                D = P[(size_t)(h3 + by3) * W + w3 + bx3];
+      const int sy = ((i >> 2) & 1) ? -1 : 1;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int sx = (q >> 2) ? -1 : 1;
+        V[q] += sx * X + sy * Y + sx * sy * D;
+      }
+    }
+    const int h2 = H >> 2, w2 = W >> 2, by2 = i >> 2, sy2 = ((i >> 1) & 1) ? -1 : 1;
+#pragma unroll
+    for (int g = 0; g < 2; ++g) {
+      const int bx2 = (j0 >> 2) + g;
+      if (fl.sel[2][((size_t)z * h2 + by2) * w2 + bx2]) {
+        const int X = P[(size_t)by2 * W + w2 + bx2], Y = P[(size_t)(h2 + by2) * W + bx2],
+                  D = P[(size_t)(h2 + by2) * W + w2 + bx2];
+#pragma unroll
+        for (int q = 4 * g; q < 4 * g + 4; ++q) {
+          const int sx = ((q >> 1) & 1) ? -1 : 1;
+          V[q] += 4 * (sx * X + sy2 * Y + sx * sy2 * D);
+        }
+      }
+    }
+    const int h1 = H >> 1, w1 = W >> 1, by1 = i >> 1, sy1 = (i & 1) ? -1 : 1;
+#pragma unroll
+    for (int g = 0; g < 4; ++g) {
+      const int bx1 = (j0 >> 1) + g;
+      if (fl.sel[1][((size_t)z * h1 + by1) * w1 + bx1]) {
+        const int X = P[(size_t)by1 * W + w1 + bx1], Y = P[(size_t)(h1 + by1) * W + bx1],
+                  D = P[(size_t)(h1 + by1) * W + w1 + bx1];
+#pragma unroll
+        for (int q = 2 * g; q < 2 * g + 2; ++q) {
+          const int sx = (q & 1) ? -1 : 1;
+          V[q] += 16 * (sx * X + sy1 * Y + sx * sy1 * D);
+        }
       }
     }
   }
-  uint16_t hi, lo;
-  if (is_f16)
-    split_hi_lo<true>((float)V, hi, lo);
-  else
-    split_hi_lo<false>((float)V, hi, lo);
+  uint32_t hi[4], lo[4];
+#pragma unroll
+  for (int q = 0; q < 8; q += 2) {
+    uint16_t h0, l0, h1v, l1v;
+    split_hi_lo<F16>((float)V[q], h0, l0);
+    split_hi_lo<F16>((float)V[q + 1], h1v, l1v);
+    hi[q / 2] = (uint32_t)h0 | ((uint32_t)h1v << 16);
+    lo[q / 2] = (uint32_t)l0 | ((uint32_t)l1v << 16);
+  }
   uint16_t* dst = B1 + (size_t)(off + k) * ldb1 + c;
-  dst[0] = hi;
-  dst[b1_plane] = lo;
+  *reinterpret_cast<uint4*>(dst) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+  *reinterpret_cast<uint4*>(dst + b1_plane) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
 }
 
 // E operand planes: out[p][z*rows_per_z + r][c] = split(f_z(r - s*idx[z][c])) for c below the
@@ -662,10 +772,18 @@ int tc_init_attributes() {
   return CGH_OK;
 }
 
+static int tc_num_sms();
+
 template <int KIND, int EPI, bool F16>
-static cudaError_t launch_gemm(const CUtensorMap& ma, const CUtensorMap& mb, const TcGemmArgs& a, dim3 grid,
+static cudaError_t launch_gemm(const CUtensorMap& ma, const CUtensorMap& mb, TcGemmArgs a, dim3 tiles,
                                cudaStream_t st) {
-  k_tc_gemm<KIND, EPI, F16><<<grid, 128, tc_smem_bytes<KIND>(), st>>>(ma, mb, a);
+  a.tm = (int)tiles.x;
+  a.tn = (int)tiles.y;
+  a.tz = (int)tiles.z;
+  const long long units = (long long)a.tm * a.tn * a.tz;
+  const int grid = (int)(units < tc_num_sms() ? units : tc_num_sms());
+  if (grid <= 0) return cudaSuccess;
+  k_tc_gemm<KIND, EPI, F16><<<grid, 192, tc_smem_bytes<KIND>(), st>>>(ma, mb, a);
   return cudaGetLastError();
 }
 
@@ -762,13 +880,15 @@ static int tc_num_sms() {
 // K splits of stage 2: fill at least two waves of one CTA per SM with a small tail,
 // keeping at least 8 K steps per CTA at the largest possible K.
 static int stage2_splits(int tiles, int kmax_steps) {
+  // units are taken round-robin by one persistent CTA per SM: pick the fewest splits that
+  // give every SM at least one unit and leave under 10% of the last round idle
   const int sms = tc_num_sms();
   int best = 1;
   double best_eff = 0;
-  for (int S = 1; S <= 32 && S * 8 <= kmax_steps; ++S) {
-    const double waves = (double)S * tiles / sms;
-    const double eff = waves / ceil(waves);
-    if (S * tiles >= 2 * sms && eff >= 0.9) return S;
+  for (int S = 1; S <= 32 && S * 4 <= kmax_steps; ++S) {
+    const double rounds = (double)S * tiles / sms;
+    const double eff = rounds / ceil(rounds);
+    if (S * tiles >= sms && eff >= 0.9) return S;
     if (eff > best_eff + 1e-9) best_eff = eff, best = S;
   }
   return best;
@@ -792,9 +912,9 @@ static int tc_run(const cgh_plan* p, const int32_t* coef, const int32_t* const* 
   k_tc_compact<<<Z, 1024, 0, st>>>(t->fl, H, W, t->rows, t->cols, t->kr_pad, t->kc_pad, t->kr_alloc, t->kc_alloc);
   TC_CK(cudaGetLastError(), "tc: compact");
   {
-    dim3 blk(32, 8), grid(t->kc_alloc / 32, (t->kr_alloc + 7) / 8, Z);
-    k_tc_idwt<<<grid, blk, 0, st>>>(coef, t->fl, t->rows, t->cols, t->kr_pad, t->kc_pad, H, W, t->kr_alloc,
-                                    t->kc_alloc, t->B1, t->b1_plane, t->kc_alloc, F16 ? 1 : 0);
+    dim3 blk(8, 32), grid((t->kc_alloc / 8 + 7) / 8, (t->kr_alloc + 31) / 32, Z);
+    k_tc_idwt<F16><<<grid, blk, 0, st>>>(coef, t->fl, t->rows, t->cols, t->kr_pad, t->kc_pad, H, W, t->kr_alloc,
+                                         t->kc_alloc, t->B1, t->b1_plane, t->kc_alloc);
     TC_CK(cudaGetLastError(), "tc: idwt");
   }
   {
