@@ -56,6 +56,10 @@ extern "C" {
 #define CGH_FORM_TC_FP16X3 2   /* fp16 hi+lo                                            */
 
 /* ---- plan --------------------------------------------------------------------------- */
+/* Plan flag: every output element is written by one CTA in a fixed order (no split-K
+ * atomics), so results are bit-reproducible run to run; the split forms are faster. */
+#define CGH_PLAN_DETERMINISTIC 1
+
 typedef struct cgh_plan cgh_plan;
 
 /* Thread-local message describing the last error of the calling thread ("" if none). */
@@ -74,7 +78,7 @@ int cgh_version(void);
  *   pitch_m, wavelength_m  pixel pitch and wavelength (metres, > 0)
  *   n_layers     Z, 1..64;   z_m  HOST array of Z layer distances (metres, > 0)
  *   levels       number of Haar levels; must be 3 (the paper's choice)
- *   flags        0 (reserved)
+ *   flags        0 or CGH_PLAN_DETERMINISTIC
  *   stream       stream on which the fringe tables are built
  * The plan allocates device memory (tables, scratch, status word) with cudaMalloc on
  * the current device and builds the fringe tables with cgh_build_tables on `stream`.
@@ -219,14 +223,63 @@ int cgh_plain_direct(const cgh_plan* plan, const uint8_t* intensity, const uint8
  * Paper: Section 2 last paragraph (numerical reconstruction; the paper uses the inverse
  * angular spectrum, this library uses the Fresnel adjoint of Eq. 1 on the object grid).
  *   R_z(i,j) = sum_{m,n} holo(m,n) * conj(f_z(m-s*i) * f_z(n-s*j))
+ * computed as (E_z^H holo) conj(E_z) on the tensor cores (bf16 hi+lo operands, 3 products,
+ * FP32 accumulation).  Square object and hologram, object edge a multiple of 32.
  *   holo       complex64 [holo_h][holo_w]
- *   fields     complex64 [Z][obj_h][obj_w] output, or NULL
+ *   fields     complex64 [Z][obj_h][obj_w] output, or NULL (then plan scratch is used)
  *   layer_idx  uint8 [obj_h][obj_w] (needed when amplitude != NULL)
- *   amplitude  float [obj_h][obj_w] output |R_{layer(i,j)}(i,j)|, or NULL
- * Uses plan scratch.  Errors: CGH_ERR_ARG, CGH_ERR_CUDA.
+ *   amplitude  float [obj_h][obj_w] output |R_{layer(i,j)}(i,j)| (0 where layer >= Z), or NULL
+ * The first call builds the plan's geometry operands (conj(E_z), E_z: 3 x 8*Z*obj*holo bytes).
+ * Errors: CGH_ERR_ARG, CGH_ERR_UNSUPPORTED (geometry), CGH_ERR_NOMEM, CGH_ERR_CUDA.
  */
 int cgh_reconstruct(const cgh_plan* plan, const float* holo, float* fields,
                     const uint8_t* layer_idx, float* amplitude, void* stream);
+
+/*
+ * cgh_propagate - point-source hologram of complex layer fields: the adjoint of
+ * cgh_reconstruct.  Paper: Eq. 1 (the superposition of point fringes, layer by layer).
+ *   holo(m,n) (+)= sum_z sum_{i,j} fields[z](i,j) * f_z(m-s*i) * f_z(n-s*j)
+ * = sum_z E_z F_z E_z^T on the tensor cores (bf16 hi+lo, 3 products, FP32 accumulation).
+ *   fields      complex64 [Z][obj_h][obj_w];  holo complex64 [holo_h][holo_w] output
+ *   accumulate  0: holo = result;  1: holo += result
+ * Same geometry limits and operands as cgh_reconstruct.  Errors: as cgh_reconstruct.
+ */
+int cgh_propagate(const cgh_plan* plan, const float* fields, float* holo, int accumulate, void* stream);
+
+/*
+ * cgh_adjoint - adjoint of the (real-input) progressive operator intensity -> hologram.
+ * Paper: Eq. 3 (the hologram is linear in the object), Section 2 steps 2-5.
+ * For a hologram-space cotangent G:
+ *   grad_object(i,j) = [P_z Re(R_z)](i,j),  z = layer(i,j),
+ * with R_z = cgh_reconstruct(G) and P_z the layer's progressive approximation: 3-level Haar
+ * of Re R_z, LLL blocks outside lists[0] and detail blocks outside lists[1..3] set to zero,
+ * inverse Haar (an orthogonal projection in the Haar basis, hence self-adjoint).
+ *   grad_holo  complex64 [holo_h][holo_w];  lists, d_counts as for cgh_progressive_hologram
+ *   layer_idx  uint8 [obj_h][obj_w];  grad_object float [obj_h][obj_w] output (0 off-layer)
+ * Errors: as cgh_reconstruct.
+ */
+int cgh_adjoint(const cgh_plan* plan, const float* grad_holo, const int32_t* const* lists,
+                const int32_t* d_counts, const uint8_t* layer_idx, float* grad_object, void* stream);
+
+/*
+ * cgh_amplitude_backward - cotangent of the composite amplitude |R_{layer(i,j)}(i,j)| with
+ * respect to the layer fields: grad_fields[z](i,j) = grad_amp(i,j) * R_z(i,j) / |R_z(i,j)|
+ * where z = layer(i,j) and R_z(i,j) != 0, else 0 (real-pair convention: d/dRe + j d/dIm).
+ *   fields complex64 [Z][obj_h][obj_w]; layer_idx uint8 [obj_h][obj_w]; grad_amp float
+ *   [obj_h][obj_w]; grad_fields complex64 [Z][obj_h][obj_w] output.
+ * The paper has no counterpart (differentiation of the reconstruction for optimisation).
+ */
+int cgh_amplitude_backward(const cgh_plan* plan, const float* fields, const uint8_t* layer_idx,
+                           const float* grad_amp, float* grad_fields, void* stream);
+
+/*
+ * cgh_phase_to_field / cgh_phase_grad - phase-only holograms: field = exp(j*phase) and, for
+ * a real-pair cotangent g of the field, d/dphase = Im(g * conj(field)).  Elementwise over n
+ * values (phase float[n], field / grad_field complex64 [n], grad_phase float[n]).
+ * The paper has no counterpart (phase-only hologram optimisation).
+ */
+int cgh_phase_to_field(const float* phase, float* field, long long n, void* stream);
+int cgh_phase_grad(const float* field, const float* grad_field, float* grad_phase, long long n, void* stream);
 
 /*
  * cgh_tc_selftest_gemm - diagnostic: C = A * B^T through the tensor-core machinery of the
@@ -253,7 +306,8 @@ int cgh_tc_selftest_gemm(const uint16_t* A, const uint16_t* B, float* C, int M, 
 #define CGH_PROF_TC_STAGE2 6   /* tensor form: stage-2 GEMM             */
 #define CGH_PROF_PLAIN 7       /* plain point-wise kernel               */
 #define CGH_PROF_RECON 8       /* reconstruction                        */
-#define CGH_PROF_SLOTS 9
+#define CGH_PROF_PROPAGATE 9   /* propagation of layer fields            */
+#define CGH_PROF_SLOTS 10
 
 /*
  * cgh_profile - enable (1) or disable (0) CUDA-event timing around the plan's internal

@@ -432,6 +432,46 @@ def reconstruct_fields(H, geom, n_obj=None):
     return R
 
 
+def propagate_fields(fields, geom):
+    """Point-source hologram of complex layer fields (Eq. 1 per layer, paraxial):
+    H = sum_z E_z F_z E_z^T; the adjoint of reconstruct_fields."""
+    fields = np.asarray(fields, dtype=np.complex128)
+    H = np.zeros((geom.holo_h, geom.holo_w), dtype=np.complex128)
+    mi = np.arange(geom.holo_h)[:, None] - geom.s * np.arange(fields.shape[1])[None, :]
+    nj = np.arange(geom.holo_w)[:, None] - geom.s * np.arange(fields.shape[2])[None, :]
+    for z in range(fields.shape[0]):
+        Ex = point_fringe_1d(mi, geom.a(z))
+        Ey = point_fringe_1d(nj, geom.a(z))
+        H += Ex @ fields[z] @ Ey.T
+    return H
+
+
+def phase_opt_loss(phase, target, weight, layer, geom, kappa):
+    """Phase-only hologram loss: H = exp(j phase), a = composite amplitude of the Fresnel
+    reconstruction, L = sum w (a / kappa - T)^2."""
+    H = np.exp(1j * np.asarray(phase, dtype=np.float64))
+    a = composite_amplitude(reconstruct_fields(H, geom, np.shape(layer)), layer)
+    return float(np.sum(weight * (a / kappa - target) ** 2))
+
+
+def phase_opt_grad(phase, target, weight, layer, geom, kappa):
+    """Analytic dL/dphase of phase_opt_loss by the chain rule: dL/da = 2 w (a/kappa - T)/kappa;
+    dL/dR_z = dL/da * R/|R| on the pixels of layer z; dL/dH = propagate_fields(dL/dR)
+    (adjoint of the reconstruction); dL/dphase = Im(dL/dH * conj(H))."""
+    H = np.exp(1j * np.asarray(phase, dtype=np.float64))
+    L = np.asarray(layer).astype(np.int64)
+    R = reconstruct_fields(H, geom, L.shape)
+    ii, jj = np.indices(L.shape)
+    Rl = R[L, ii, jj]
+    a = np.abs(Rl)
+    ga = 2.0 * weight * (a / kappa - target) / kappa
+    gR = np.zeros_like(R)
+    unit = np.where(a > 0, Rl / np.where(a > 0, a, 1.0), 0.0)
+    gR[L, ii, jj] = ga * unit
+    gH = propagate_fields(gR, geom)
+    return np.imag(gH * np.conj(H))
+
+
 def composite_amplitude(R, layer):
     """|R_{layer(i,j)}(i, j)|: each object pixel read on its own layer."""
     L = np.asarray(layer).astype(np.int64)

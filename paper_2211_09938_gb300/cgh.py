@@ -47,6 +47,11 @@ SIGNATURES = {
     "cgh_progressive_hologram": (_I, [_P, _P, ctypes.POINTER(_P), _P, _P, _I, _I, _P]),
     "cgh_plain_direct": (_I, [_P, _P, _P, _P, _P]),
     "cgh_reconstruct": (_I, [_P, _P, _P, _P, _P, _P]),
+    "cgh_propagate": (_I, [_P, _P, _P, _I, _P]),
+    "cgh_adjoint": (_I, [_P, _P, ctypes.POINTER(_P), _P, _P, _P, _P]),
+    "cgh_amplitude_backward": (_I, [_P, _P, _P, _P, _P, _P]),
+    "cgh_phase_to_field": (_I, [_P, _P, ctypes.c_longlong, _P]),
+    "cgh_phase_grad": (_I, [_P, _P, _P, ctypes.c_longlong, _P]),
     "cgh_status": (_I, [_P, ctypes.POINTER(_I), _P]),
     "cgh_tc_selftest_gemm": (_I, [_P, _P, _P, _I, _I, _I, _I, _P]),
     "cgh_profile": (_I, [_P, _I]),
@@ -99,7 +104,9 @@ class Plan:
     tensors of the dtypes include/cgh.h states; outputs are allocated by the caller or
     by the convenience helpers below (torch.empty on the plan's device)."""
 
-    def __init__(self, obj_shape, holo_shape, pitch, wavelength, z, levels=3, stream=None):
+    DETERMINISTIC = 1
+
+    def __init__(self, obj_shape, holo_shape, pitch, wavelength, z, levels=3, stream=None, flags=0):
         import torch
         self.obj_h, self.obj_w = int(obj_shape[0]), int(obj_shape[1])
         self.holo_h, self.holo_w = int(holo_shape[0]), int(holo_shape[1])
@@ -109,14 +116,14 @@ class Plan:
         zs = (ctypes.c_double * self.n_layers)(*self.z)
         h = ctypes.c_void_p()
         check(lib().cgh_plan_create(ctypes.byref(h), self.obj_h, self.obj_w, self.holo_h, self.holo_w,
-                                    float(pitch), float(wavelength), self.n_layers, zs, levels, 0,
+                                    float(pitch), float(wavelength), self.n_layers, zs, levels, int(flags),
                                     _stream(stream)))
         self.handle = h
 
     @classmethod
-    def for_scene(cls, scene, stream=None):
+    def for_scene(cls, scene, stream=None, flags=0):
         return cls(scene["intensity"].shape, scene["holo"], scene["pitch"], scene["wavelength"],
-                   scene["z"], stream=stream)
+                   scene["z"], stream=stream, flags=flags)
 
     def close(self):
         if getattr(self, "handle", None) is not None and self.handle.value:
@@ -195,17 +202,47 @@ class Plan:
         return holo
 
     def reconstruct(self, holo, layer=None, fields=True, amplitude=True, stream=None):
+        """(fields [Z, obj, obj] complex64 or None, amplitude [obj, obj] float32 or None).
+        `fields` / `amplitude` may also be preallocated tensors."""
         import torch
-        f = torch.empty((self.n_layers, self.obj_h, self.obj_w), dtype=torch.complex64,
-                        device=self.device) if fields else None
-        a = torch.empty((self.obj_h, self.obj_w), dtype=torch.float32,
-                        device=self.device) if amplitude else None
+        if fields is True:
+            fields = torch.empty((self.n_layers, self.obj_h, self.obj_w), dtype=torch.complex64,
+                                 device=self.device)
+        if amplitude is True:
+            amplitude = torch.empty((self.obj_h, self.obj_w), dtype=torch.float32, device=self.device)
+        f = fields if fields is not False else None
+        a = amplitude if amplitude is not False else None
         check(lib().cgh_reconstruct(self.handle, _ptr(holo), _ptr(f), _ptr(layer), _ptr(a),
                                     _stream(stream)))
         return f, a
 
+    def propagate(self, fields, holo=None, accumulate=False, stream=None):
+        import torch
+        if holo is None:
+            holo = torch.empty((self.holo_h, self.holo_w), dtype=torch.complex64, device=self.device)
+        check(lib().cgh_propagate(self.handle, _ptr(fields), _ptr(holo), 1 if accumulate else 0,
+                                  _stream(stream)))
+        return holo
+
+    def adjoint(self, grad_holo, lists, counts, layer, out=None, stream=None):
+        import torch
+        if out is None:
+            out = torch.empty((self.obj_h, self.obj_w), dtype=torch.float32, device=self.device)
+        arr = (ctypes.c_void_p * 4)(*[l.data_ptr() for l in lists])
+        check(lib().cgh_adjoint(self.handle, _ptr(grad_holo), arr, _ptr(counts), _ptr(layer), _ptr(out),
+                                _stream(stream)))
+        return out
+
+    def amplitude_backward(self, fields, layer, grad_amp, out=None, stream=None):
+        import torch
+        if out is None:
+            out = torch.empty_like(fields)
+        check(lib().cgh_amplitude_backward(self.handle, _ptr(fields), _ptr(layer), _ptr(grad_amp),
+                                           _ptr(out), _stream(stream)))
+        return out
+
     PROF_SLOTS = ["tables", "haar", "select", "direct_lut", "tc_prep", "tc_stage1", "tc_stage2",
-                  "plain", "recon"]
+                  "plain", "recon", "propagate"]
 
     def profile(self, enable=True):
         check(lib().cgh_profile(self.handle, 1 if enable else 0))
@@ -237,3 +274,21 @@ def tc_selftest_gemm(A, B, fp16=False, stream=None):
     check(lib().cgh_tc_selftest_gemm(_ptr(A), _ptr(B), _ptr(C), M, N, K, 1 if fp16 else 0,
                                      _stream(stream)))
     return C
+
+
+def phase_to_field(phase, out=None, stream=None):
+    """exp(j*phase) on the GPU (cgh_phase_to_field); phase float32 CUDA tensor."""
+    import torch
+    if out is None:
+        out = torch.empty(phase.shape, dtype=torch.complex64, device=phase.device)
+    check(lib().cgh_phase_to_field(_ptr(phase), _ptr(out), phase.numel(), _stream(stream)))
+    return out
+
+
+def phase_grad(field, grad_field, out=None, stream=None):
+    """Im(grad_field * conj(field)) (cgh_phase_grad)."""
+    import torch
+    if out is None:
+        out = torch.empty(field.shape, dtype=torch.float32, device=field.device)
+    check(lib().cgh_phase_grad(_ptr(field), _ptr(grad_field), _ptr(out), field.numel(), _stream(stream)))
+    return out

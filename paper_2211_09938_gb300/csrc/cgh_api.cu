@@ -45,6 +45,7 @@ int cgh_plan_destroy(cgh_plan* p) {
       cudaEventDestroy(p->prof_ev[k][1]);
     }
   tc_destroy(p);
+  field_destroy(p);
   cudaFree(p->d_tab);
   cudaFree(p->d_f64);
   cudaFree(p->d_a_frac);
@@ -86,7 +87,7 @@ int cgh_plan_create(cgh_plan** out, int obj_h, int obj_w, int holo_h, int holo_w
   if (!z_m) return cgh_fail(CGH_ERR_ARG, "cgh_plan_create: z_m is NULL");
   for (int k = 0; k < n_layers; ++k)
     if (!(z_m[k] > 0)) return cgh_fail(CGH_ERR_ARG, "cgh_plan_create: z[%d] must be > 0", k);
-  if (flags != 0) return cgh_fail(CGH_ERR_ARG, "cgh_plan_create: flags must be 0");
+  if (flags & ~CGH_PLAN_DETERMINISTIC) return cgh_fail(CGH_ERR_ARG, "cgh_plan_create: unknown flags 0x%x", flags);
 
   cgh_plan* p = (cgh_plan*)calloc(1, sizeof(cgh_plan));
   if (!p) return cgh_fail(CGH_ERR_NOMEM, "cgh_plan_create: host allocation failed");
@@ -97,6 +98,7 @@ int cgh_plan_create(cgh_plan** out, int obj_h, int obj_w, int holo_h, int holo_w
   p->s = holo_h / obj_h;
   p->n_layers = n_layers;
   p->levels = levels;
+  p->deterministic = (flags & CGH_PLAN_DETERMINISTIC) ? 1 : 0;
   p->pitch = pitch_m;
   p->wavelength = wavelength_m;
   for (int k = 0; k < n_layers; ++k) {
@@ -127,7 +129,7 @@ int cgh_plan_create(cgh_plan** out, int obj_h, int obj_w, int holo_h, int holo_w
   p->f_len = p->tab_len + 7 * p->s;
   PLAN_TRY(cudaMalloc(&p->d_f64, (size_t)n_layers * p->f_len * sizeof(double2)), "cgh_plan_create: fringe");
   PLAN_TRY(basic_init_attributes(), "cgh_plan_create: kernel attributes");
-  if (tc_init_attributes() != CGH_OK) {
+  if (tc_init_attributes() != CGH_OK || field_init_attributes() != CGH_OK) {
     cgh_plan_destroy(p);
     return CGH_ERR_CUDA;
   }
@@ -250,7 +252,33 @@ int cgh_reconstruct(const cgh_plan* p, const float* holo, float* fields, const u
   if (!p || !holo) return cgh_fail(CGH_ERR_ARG, "cgh_reconstruct: NULL argument");
   if (amplitude && !layer_idx) return cgh_fail(CGH_ERR_ARG, "cgh_reconstruct: amplitude needs layer_idx");
   if (!fields && !amplitude) return cgh_fail(CGH_ERR_ARG, "cgh_reconstruct: nothing to compute");
+  if (((uintptr_t)holo & 7) || ((uintptr_t)fields & 7))
+    return cgh_fail(CGH_ERR_ARG, "cgh_reconstruct: complex arrays must be 8-byte aligned");
   return tc_reconstruct(p, (const float2*)holo, (float2*)fields, layer_idx, amplitude, (cudaStream_t)stream);
+}
+
+int cgh_propagate(const cgh_plan* p, const float* fields, float* holo, int accumulate, void* stream) {
+  if (!p || !fields || !holo) return cgh_fail(CGH_ERR_ARG, "cgh_propagate: NULL argument");
+  if (((uintptr_t)holo & 7) || ((uintptr_t)fields & 7))
+    return cgh_fail(CGH_ERR_ARG, "cgh_propagate: complex arrays must be 8-byte aligned");
+  return field_propagate(p, (const float2*)fields, (float2*)holo, accumulate, (cudaStream_t)stream);
+}
+
+int cgh_adjoint(const cgh_plan* p, const float* grad_holo, const int32_t* const* lists, const int32_t* d_counts,
+                const uint8_t* layer_idx, float* grad_object, void* stream) {
+  if (!p || !grad_holo || !lists || !d_counts || !layer_idx || !grad_object)
+    return cgh_fail(CGH_ERR_ARG, "cgh_adjoint: NULL argument");
+  for (int k = 0; k < 4; ++k)
+    if (!lists[k]) return cgh_fail(CGH_ERR_ARG, "cgh_adjoint: lists[%d] is NULL", k);
+  return field_adjoint(p, (const float2*)grad_holo, lists, d_counts, layer_idx, grad_object, (cudaStream_t)stream);
+}
+
+int cgh_amplitude_backward(const cgh_plan* p, const float* fields, const uint8_t* layer_idx, const float* grad_amp,
+                           float* grad_fields, void* stream) {
+  if (!p || !fields || !layer_idx || !grad_amp || !grad_fields)
+    return cgh_fail(CGH_ERR_ARG, "cgh_amplitude_backward: NULL argument");
+  return field_amplitude_backward(p, (const float2*)fields, layer_idx, grad_amp, (float2*)grad_fields,
+                                  (cudaStream_t)stream);
 }
 
 int cgh_profile(cgh_plan* p, int enable) {

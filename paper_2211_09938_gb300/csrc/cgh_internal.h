@@ -14,6 +14,7 @@
 
 struct cgh_plan {
   int obj_h, obj_w, holo_h, holo_w, s, n_layers, levels;
+  int deterministic;  // CGH_PLAN_DETERMINISTIC: no split-K atomics
   double pitch, wavelength;
   double z[CGH_MAX_LAYERS];
   double a_frac[CGH_MAX_LAYERS];     // frac(a_z) in [0,1)
@@ -38,6 +39,8 @@ struct cgh_plan {
 
   // Separable tensor-core path (allocated lazily by the first call that needs it).
   struct cgh_tc_state* tc;
+  // Reconstruction / propagation operands and scratch (allocated lazily).
+  struct cgh_field_state* fs;
 
   // CUDA-event profiling of the internal stages (cgh_profile).
   int prof_on;
@@ -89,6 +92,12 @@ cudaError_t launch_select_tasks(int obj_h, int obj_w, int n_layers, const uint8_
 cudaError_t basic_init_attributes();
 int tc_init_attributes();
 
+// Selection flags of one progressive call: occ3 [Z][H/8][W/8] (LLL list), rowband
+// [Z][H/8], colband [Z][W/8], sel[l] [Z][H>>l][W>>l] for l = 1..3 (detail lists).
+struct TcFlags {
+  uint8_t *occ3, *rowband, *colband, *sel[4];
+};
+
 // Separable tensor-core path (kernels_tc.cu).
 int tc_progressive(const cgh_plan* p, const int32_t* coef, const int32_t* const* lists,
                    const int32_t* d_counts, float2* holo, int accumulate, int form, cudaStream_t st);
@@ -96,3 +105,14 @@ int tc_reconstruct(const cgh_plan* p, const float2* holo, float2* fields, const 
                    float* amp, cudaStream_t st);
 void tc_destroy(cgh_plan* p);
 int tc_layer_dims(const cgh_plan* p, int* kr, int* kc, cudaStream_t st);
+int tc_build_flags(const cgh_plan* p, const int32_t* const* lists, const int32_t* d_counts, TcFlags* out,
+                   cudaStream_t st);
+
+// Fields: reconstruction, propagation, adjoints (kernels_field.cu).
+int field_init_attributes();
+int field_propagate(const cgh_plan* p, const float2* fields, float2* holo, int accumulate, cudaStream_t st);
+int field_adjoint(const cgh_plan* p, const float2* grad_holo, const int32_t* const* lists,
+                  const int32_t* d_counts, const uint8_t* L, float* grad_obj, cudaStream_t st);
+int field_amplitude_backward(const cgh_plan* p, const float2* fields, const uint8_t* L, const float* grad_amp,
+                             float2* grad_fields, cudaStream_t st);
+void field_destroy(cgh_plan* p);

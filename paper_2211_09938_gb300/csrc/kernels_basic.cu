@@ -588,7 +588,7 @@ cudaError_t basic_init_attributes() {
 cudaError_t launch_direct_lut(const cgh_plan* p, const int32_t* coef, const int32_t* const* lists,
                               const int32_t* d_counts, float2* holo, cudaStream_t st) {
   const int tn = (p->holo_w + DL_TN - 1) / DL_TN, tm = (p->holo_h + DL_TM - 1) / DL_TM;
-  const int S = direct_lut_splits(tn * tm);
+  const int S = p->deterministic ? 1 : direct_lut_splits(tn * tm);
   const size_t smem = DL_SMEM;
   dim3 grid(tn, tm, S);
   // holo must be zero (or hold the previous hologram) when S > 1: atomics accumulate.

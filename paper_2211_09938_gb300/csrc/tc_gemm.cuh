@@ -1,0 +1,599 @@
+// tcgen05 GEMM engine shared by the tensor-core translation units of libcgh: PTX helpers,
+// the persistent warp-specialised kernel and its host-side launch / tensor-map helpers.
+// Every translation unit that includes it gets its own instantiations (and must opt them
+// in to large shared memory with set_gemm_attr before launching).
+#pragma once
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <mutex>
+
+#include "cgh_internal.h"
+
+#define TC_BM 128
+#define TC_BN 128
+#define TC_BK 32                            // K elements per pipeline stage (64-byte rows)
+#define TC_PLANE_BYTES (128 * TC_BK * 2)    // one 128-row plane tile: 8 KiB
+#define TC_WAIT_NS 2000000000ull            // bounded waits: 2 s, then CGH_ERR_TIMEOUT
+
+enum { KIND_TEST = 0, KIND_CR = 1, KIND_CC = 2 };
+enum { EPI_H = 0, EPI_Y = 1, EPI_C = 2, EPI_F = 3 };
+
+// ------------------------------------------------------------------------------------
+// PTX helpers
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ uint64_t global_timer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Wait for the phase `parity` of `bar` to complete.  Gives up after TC_WAIT_NS or when
+// another role has raised the CTA's abort flag; a timeout records CGH_ERR_TIMEOUT.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
+                                                  int* status) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = global_timer();
+  while (true) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (*abort_flag) return false;
+    if (global_timer() - t0 > TC_WAIT_NS) {
+      *abort_flag = 1;
+      if (status) atomicExch(status, CGH_ERR_TIMEOUT);
+      return false;
+    }
+  }
+}
+
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar, int c0, int c1,
+                                            int c2) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%3, %4, %5}], [%2];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(c0), "r"(c1), "r"(c2)
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// Shared-memory matrix descriptor of a K-major tile with 64-byte swizzling: 128 rows of
+// 64 bytes, 8-row groups 512 bytes apart (stride byte offset), version bits 46-47 = 1,
+// layout type 4 (SWIZZLE_64B) in bits 61-63.  The leading byte offset is unused for
+// swizzled K-major layouts (encoded 1).
+__device__ __forceinline__ uint64_t sdesc_sw64(uint32_t addr) {
+  return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(512 >> 4) << 32) |
+         ((uint64_t)1 << 46) | ((uint64_t)4 << 61);
+}
+
+// Instruction descriptor, kind::f16: D = F32 (bits 4-5 = 1), A/B type (bits 7-9, 10-12:
+// 0 = F16, 1 = BF16), negate A (bit 13), both K-major (bits 15, 16 = 0), N >> 3 in bits
+// 17-22, M >> 4 in bits 24-28.
+__host__ __device__ constexpr uint32_t idesc_f16(int is_bf16, int neg_a, int M, int N) {
+  return (1u << 4) | ((uint32_t)is_bf16 << 7) | ((uint32_t)is_bf16 << 10) | ((uint32_t)neg_a << 13) |
+         ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                   smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+      "%14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+        "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
+        "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]),
+        "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]),
+        "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+      : "r"(taddr));
+}
+
+__device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// ------------------------------------------------------------------------------------
+// the GEMM kernel
+
+struct TcGemmArgs {
+  int mode;          // 1: stage 1 (layers, compacted), 2: split K, 3: per-layer batch, 0: test
+  int a_rows_per_z;  // modes 1, 3: row offset of A per layer
+  int b_rows_per_z;  // mode 3: row offset of B per layer
+  int out_rows_per_z, out_cols_per_z;  // mode 3: output offsets per layer
+  const int* kr_pad; // [Z] padded compacted row counts
+  const int* kc_pad; // [Z] padded compacted column counts
+  int n_layers;
+  int M, N, K;       // test: sizes; stages: M and N of the output (K from the device)
+  int tm, tn, tz;    // work units: M tiles x N tiles x (layers | K splits | 1)
+  float scale;
+  float2* H;         // EPI_H: complex output [M][N]
+  int ldh;
+  int h_vec4;        // H rows 16-byte aligned: add pairs of pixels with float4 atomics
+  uint16_t* Y;       // EPI_Y: 4 planes [plane][M][ldy]
+  long long y_plane;
+  int ldy;
+  float* C;          // EPI_C: real output [M][N]
+  int ldc;
+  float2* F;         // EPI_F: complex output rows (plain stores)
+  int ldf;
+  int* status;
+};
+
+template <int KIND>
+struct TcCfg;
+template <>
+struct TcCfg<KIND_TEST> {
+  static constexpr int NA = 1, NB = 1, NST = 8;  // > 114 KiB: one CTA (and one TMEM owner) per SM
+};
+template <>
+struct TcCfg<KIND_CR> {
+  static constexpr int NA = 4, NB = 2, NST = 4;
+};
+template <>
+struct TcCfg<KIND_CC> {
+  static constexpr int NA = 4, NB = 4, NST = 3;
+};
+
+template <int KIND>
+constexpr size_t tc_smem_bytes() {
+  return (size_t)TcCfg<KIND>::NST * (TcCfg<KIND>::NA + TcCfg<KIND>::NB) * TC_PLANE_BYTES + 1024;
+}
+
+// Products of one 16-wide K slice.  Plane order of complex operands: re_hi, re_lo, im_hi,
+// im_lo; of real operands: hi, lo.  Accumulator 0 holds the real part (columns 0..127 of
+// the TMEM allocation), accumulator 1 the imaginary part (columns 128..255).
+template <int KIND>
+__device__ __forceinline__ void issue_products(uint32_t tmem, uint32_t a_base, uint32_t b_base, int kk,
+                                               uint32_t id_pos, uint32_t id_neg, bool first) {
+  auto A = [&](int p) { return sdesc_sw64(a_base + p * TC_PLANE_BYTES + kk * 32); };
+  auto B = [&](int p) { return sdesc_sw64(b_base + p * TC_PLANE_BYTES + kk * 32); };
+  const uint32_t d0 = tmem, d1 = tmem + 128;
+  const uint32_t f = first ? 0u : 1u;
+  if (KIND == KIND_TEST) {
+    mma_f16(d0, A(0), B(0), id_pos, f);
+  } else if (KIND == KIND_CR) {
+    mma_f16(d0, A(0), B(0), id_pos, f);
+    mma_f16(d0, A(0), B(1), id_pos, 1);
+    mma_f16(d0, A(1), B(0), id_pos, 1);
+    mma_f16(d1, A(2), B(0), id_pos, f);
+    mma_f16(d1, A(2), B(1), id_pos, 1);
+    mma_f16(d1, A(3), B(0), id_pos, 1);
+  } else {
+    mma_f16(d0, A(0), B(0), id_pos, f);
+    mma_f16(d0, A(0), B(1), id_pos, 1);
+    mma_f16(d0, A(1), B(0), id_pos, 1);
+    mma_f16(d0, A(2), B(2), id_neg, 1);
+    mma_f16(d0, A(2), B(3), id_neg, 1);
+    mma_f16(d0, A(3), B(2), id_neg, 1);
+    mma_f16(d1, A(0), B(2), id_pos, f);
+    mma_f16(d1, A(0), B(3), id_pos, 1);
+    mma_f16(d1, A(1), B(2), id_pos, 1);
+    mma_f16(d1, A(2), B(0), id_pos, 1);
+    mma_f16(d1, A(2), B(1), id_pos, 1);
+    mma_f16(d1, A(3), B(0), id_pos, 1);
+  }
+}
+
+template <bool F16>
+__device__ __forceinline__ void split_hi_lo(float x, uint16_t& hi, uint16_t& lo) {
+  if (F16) {
+    const __half h = __float2half_rn(x);
+    const __half l = __float2half_rn(x - __half2float(h));
+    hi = __half_as_ushort(h);
+    lo = __half_as_ushort(l);
+  } else {
+    const __nv_bfloat16 h = __float2bfloat16_rn(x);
+    const __nv_bfloat16 l = __float2bfloat16_rn(x - __bfloat162float(h));
+    hi = __bfloat16_as_ushort(h);
+    lo = __bfloat16_as_ushort(l);
+  }
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+struct TileInfo {
+  int a_row, b_row, k_lo, nk, out_row0, out_col0, n_valid, row_lim, col_lim;
+};
+
+// Work unit t of the persistent grid: (mt fastest, then nt, then the layer / K split).
+// Returns false for units with nothing to do; every role decodes identically.
+__device__ __forceinline__ bool decode_tile(const TcGemmArgs& a, int t, const int* s_off, int ktot, TileInfo& ti) {
+  const int mt = t % a.tm, r = t / a.tm, nt = r % a.tn, zz = r / a.tn;
+  ti.out_row0 = mt * TC_BM;
+  ti.n_valid = TC_BN;
+  ti.row_lim = a.M;
+  ti.col_lim = a.N;
+  if (a.mode == 3) {
+    ti.a_row = zz * a.a_rows_per_z + mt * TC_BM;
+    ti.b_row = zz * a.b_rows_per_z + nt * TC_BN;
+    ti.k_lo = 0;
+    ti.nk = a.K / TC_BK;
+    ti.out_row0 = zz * a.out_rows_per_z + mt * TC_BM;
+    ti.out_col0 = zz * a.out_cols_per_z + nt * TC_BN;
+    ti.row_lim = zz * a.out_rows_per_z + a.M;
+    ti.col_lim = zz * a.out_cols_per_z + a.N;
+    ti.n_valid = min(TC_BN, ti.col_lim - ti.out_col0);
+    return ti.nk > 0 && ti.n_valid > 0;
+  }
+  if (a.mode == 1) {
+    const int krz = s_off[zz + 1] - s_off[zz];
+    ti.n_valid = min(TC_BN, krz - nt * TC_BN);
+    if (ti.n_valid <= 0) return false;
+    ti.a_row = zz * a.a_rows_per_z + mt * TC_BM;
+    ti.b_row = s_off[zz] + nt * TC_BN;
+    ti.k_lo = 0;
+    ti.nk = a.kc_pad[zz] / TC_BK;
+    ti.out_col0 = s_off[zz] + nt * TC_BN;
+    ti.col_lim = ti.out_col0 + ti.n_valid;
+  } else if (a.mode == 2) {
+    const int nkt = ktot / TC_BK, S = a.tz;
+    const int k0 = (int)((long long)nkt * zz / S), k1 = (int)((long long)nkt * (zz + 1) / S);
+    ti.a_row = mt * TC_BM;
+    ti.b_row = nt * TC_BN;
+    ti.k_lo = k0 * TC_BK;
+    ti.nk = k1 - k0;
+    ti.out_col0 = nt * TC_BN;
+  } else {
+    ti.a_row = mt * TC_BM;
+    ti.b_row = nt * TC_BN;
+    ti.k_lo = 0;
+    ti.nk = a.K / TC_BK;
+    ti.out_col0 = nt * TC_BN;
+  }
+  return ti.nk > 0;
+}
+
+// Persistent warp-specialised GEMM.  Warp 0 (one lane) streams operand tiles with TMA
+// through an NST-deep shared-memory ring; warp 1 owns the tensor memory (512 columns:
+// two accumulator buffers of Re | Im) and one lane issues the MMAs; warps 2-5 drain a
+// finished buffer (TMEM -> registers -> global) while the next tile accumulates in the
+// other buffer.
+template <int KIND, int EPI, bool F16>
+__global__ void __launch_bounds__(192, 1) k_tc_gemm(const __grid_constant__ CUtensorMap mapA,
+                                                     const __grid_constant__ CUtensorMap mapB,
+                                                     const TcGemmArgs args) {
+  using Cfg = TcCfg<KIND>;
+  constexpr int NA = Cfg::NA, NB = Cfg::NB, NST = Cfg::NST;
+  constexpr uint32_t STAGE = (NA + NB) * TC_PLANE_BYTES;
+  extern __shared__ uint8_t tc_smem_raw[];
+  uint8_t* smem = (uint8_t*)(((uintptr_t)tc_smem_raw + 1023) & ~(uintptr_t)1023);
+  __shared__ __align__(8) uint64_t full_bar[NST], empty_bar[NST], tfull_bar[2], tempty_bar[2], done_bar;
+  __shared__ uint32_t s_tmem;
+  __shared__ volatile int s_abort;
+  __shared__ int s_off[CGH_MAX_LAYERS + 1];
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int total = args.tm * args.tn * args.tz;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < NST; ++s) {
+      mbar_init(&full_bar[s], 1);
+      mbar_init(&empty_bar[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&tfull_bar[b], 1);
+      mbar_init(&tempty_bar[b], 4);
+    }
+    mbar_init(&done_bar, 1);
+    s_abort = 0;
+    int o = 0;
+    s_off[0] = 0;
+    if (args.kr_pad)
+      for (int q = 0; q < args.n_layers; ++q) s_off[q + 1] = (o += args.kr_pad[q]);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(smem_u32(&s_tmem))
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = s_tmem;
+  const uint32_t smem_base = smem_u32(smem);
+  const int ktot = args.mode == 2 ? (args.kr_pad ? s_off[args.n_layers] : args.K) : 0;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // ---- TMA producer
+      int it = 0;
+      bool issued[NST];
+      uint32_t issued_ph[NST];
+      for (int s = 0; s < NST; ++s) issued[s] = false, issued_ph[s] = 0;
+      bool ok = true;
+      for (int t = blockIdx.x; t < total && ok; t += gridDim.x) {
+        TileInfo ti;
+        if (!decode_tile(args, t, s_off, ktot, ti)) continue;
+        for (int kt = 0; kt < ti.nk; ++kt, ++it) {
+          const int s = it % NST;
+          const uint32_t ph = (uint32_t)(it / NST) & 1u;
+          if (!mbar_wait_bounded(&empty_bar[s], ph ^ 1u, &s_abort, args.status)) {
+            ok = false;
+            break;
+          }
+          uint8_t* st = smem + s * STAGE;
+          mbar_arrive_expect_tx(&full_bar[s], STAGE);
+          tma_load_3d(st, &mapA, &full_bar[s], ti.k_lo + kt * TC_BK, ti.a_row, 0);
+          tma_load_3d(st + NA * TC_PLANE_BYTES, &mapB, &full_bar[s], ti.k_lo + kt * TC_BK, ti.b_row, 0);
+          issued[s] = true;
+          issued_ph[s] = ph;
+        }
+      }
+      if (s_abort) {  // let copies in flight land before shared memory goes away
+        for (int s = 0; s < NST; ++s)
+          if (issued[s]) {
+            const uint64_t t0 = global_timer();
+            while (!mbar_try_wait(&full_bar[s], issued_ph[s]) && global_timer() - t0 < TC_WAIT_NS) {
+            }
+          }
+      }
+    }
+    __syncwarp();
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // ---- MMA issuer
+      const uint32_t id_pos = idesc_f16(F16 ? 0 : 1, 0, TC_BM, TC_BN);
+      const uint32_t id_neg = idesc_f16(F16 ? 0 : 1, 1, TC_BM, TC_BN);
+      int it = 0, local = 0;
+      bool ok = true;
+      for (int t = blockIdx.x; t < total && ok; t += gridDim.x) {
+        TileInfo ti;
+        if (!decode_tile(args, t, s_off, ktot, ti)) continue;
+        const int buf = local & 1;
+        const uint32_t use_ph = (uint32_t)(local >> 1) & 1u;
+        if (!mbar_wait_bounded(&tempty_bar[buf], use_ph ^ 1u, &s_abort, args.status)) break;
+        tc_fence_after();
+        const uint32_t acc = tmem + buf * 256;
+        for (int kt = 0; kt < ti.nk; ++kt, ++it) {
+          const int s = it % NST;
+          const uint32_t ph = (uint32_t)(it / NST) & 1u;
+          if (!mbar_wait_bounded(&full_bar[s], ph, &s_abort, args.status)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t a_base = smem_base + s * STAGE;
+          const uint32_t b_base = a_base + NA * TC_PLANE_BYTES;
+#pragma unroll
+          for (int kk = 0; kk < TC_BK / 16; ++kk)
+            issue_products<KIND>(acc, a_base, b_base, kk, id_pos, id_neg, kt == 0 && kk == 0);
+          mma_commit(&empty_bar[s]);
+        }
+        mma_commit(&tfull_bar[buf]);
+        ++local;
+      }
+      // every MMA issued above completes before the accumulators are released
+      mma_commit(&done_bar);
+      const uint64_t t0 = global_timer();
+      while (!mbar_try_wait(&done_bar, 0) && global_timer() - t0 < TC_WAIT_NS) {
+      }
+    }
+    __syncwarp();
+  } else {
+    // ---- epilogue warps 2..5: TMEM lane quarter (warp % 4) -> 32 output rows
+    const int quarter = warp & 3;
+    int local = 0;
+    for (int t = blockIdx.x; t < total; t += gridDim.x) {
+      TileInfo ti;
+      if (!decode_tile(args, t, s_off, ktot, ti)) continue;
+      const int buf = local & 1;
+      const uint32_t ph = (uint32_t)(local >> 1) & 1u;
+      bool have = mbar_wait_bounded(&tfull_bar[buf], ph, &s_abort, args.status);
+      have = __all_sync(0xffffffffu, have && !s_abort);  // tcgen05.ld below is warp-collective
+      if (!have) break;
+      tc_fence_after();
+      const int row = ti.out_row0 + quarter * 32 + lane;
+      const uint32_t t_lane = tmem + buf * 256 + ((uint32_t)(quarter * 32) << 16);
+#pragma unroll 1
+      for (int c0 = 0; c0 < TC_BN; c0 += 32) {
+        uint32_t re[32], im[32];
+        tmem_ld32(t_lane + c0, re);
+        if (KIND != KIND_TEST) tmem_ld32(t_lane + 128 + c0, im);
+        tmem_ld_wait();
+        if (EPI == EPI_H || EPI == EPI_F) {
+          if (row < ti.row_lim) {
+            float2* dst = (EPI == EPI_H ? args.H + (size_t)row * args.ldh : args.F + (size_t)row * args.ldf) +
+                          ti.out_col0 + c0;
+            const int nv = min(32, ti.col_lim - (ti.out_col0 + c0));
+            if (nv == 32 && args.h_vec4) {
+#pragma unroll
+              for (int j = 0; j < 32; j += 2) {
+                float4 v = make_float4(__uint_as_float(re[j]) * args.scale, __uint_as_float(im[j]) * args.scale,
+                                       __uint_as_float(re[j + 1]) * args.scale,
+                                       __uint_as_float(im[j + 1]) * args.scale);
+                if (EPI == EPI_H)
+                  atomicAdd(reinterpret_cast<float4*>(dst + j), v);
+                else
+                  *reinterpret_cast<float4*>(dst + j) = v;
+              }
+            } else {
+#pragma unroll
+              for (int j = 0; j < 32; ++j)
+                if (j < nv) {
+                  const float2 v = make_float2(__uint_as_float(re[j]) * args.scale, __uint_as_float(im[j]) * args.scale);
+                  if (EPI == EPI_H)
+                    atomicAdd(dst + j, v);
+                  else
+                    dst[j] = v;
+                }
+            }
+          }
+        } else if (EPI == EPI_Y) {
+          if (row < ti.row_lim) {
+            const int nv = min(32, ti.n_valid - c0);
+            uint16_t* base = args.Y + (size_t)row * args.ldy + ti.out_col0 + c0;
+            if (nv == 32) {  // 64 contiguous bytes per plane: four 16-byte stores each
+              uint32_t prh[16], prl[16], pih[16], pil[16];
+#pragma unroll
+              for (int j = 0; j < 32; j += 2) {
+                uint16_t a0, a1, b0, b1, c0h, c1h, d0, d1;
+                split_hi_lo<F16>(__uint_as_float(re[j]) * args.scale, a0, b0);
+                split_hi_lo<F16>(__uint_as_float(re[j + 1]) * args.scale, a1, b1);
+                split_hi_lo<F16>(__uint_as_float(im[j]) * args.scale, c0h, d0);
+                split_hi_lo<F16>(__uint_as_float(im[j + 1]) * args.scale, c1h, d1);
+                prh[j / 2] = (uint32_t)a0 | ((uint32_t)a1 << 16);
+                prl[j / 2] = (uint32_t)b0 | ((uint32_t)b1 << 16);
+                pih[j / 2] = (uint32_t)c0h | ((uint32_t)c1h << 16);
+                pil[j / 2] = (uint32_t)d0 | ((uint32_t)d1 << 16);
+              }
+              uint4* q0 = reinterpret_cast<uint4*>(base);
+              uint4* q1 = reinterpret_cast<uint4*>(base + args.y_plane);
+              uint4* q2 = reinterpret_cast<uint4*>(base + 2 * args.y_plane);
+              uint4* q3 = reinterpret_cast<uint4*>(base + 3 * args.y_plane);
+#pragma unroll
+              for (int v = 0; v < 4; ++v) {
+                q0[v] = make_uint4(prh[4 * v], prh[4 * v + 1], prh[4 * v + 2], prh[4 * v + 3]);
+                q1[v] = make_uint4(prl[4 * v], prl[4 * v + 1], prl[4 * v + 2], prl[4 * v + 3]);
+                q2[v] = make_uint4(pih[4 * v], pih[4 * v + 1], pih[4 * v + 2], pih[4 * v + 3]);
+                q3[v] = make_uint4(pil[4 * v], pil[4 * v + 1], pil[4 * v + 2], pil[4 * v + 3]);
+              }
+            } else {
+#pragma unroll
+              for (int j = 0; j < 32; ++j)
+                if (j < nv) {
+                  uint16_t rh, rl, ih, il;
+                  split_hi_lo<F16>(__uint_as_float(re[j]) * args.scale, rh, rl);
+                  split_hi_lo<F16>(__uint_as_float(im[j]) * args.scale, ih, il);
+                  base[j] = rh;
+                  base[args.y_plane + j] = rl;
+                  base[2 * args.y_plane + j] = ih;
+                  base[3 * args.y_plane + j] = il;
+                }
+            }
+          }
+        } else {
+          if (row < args.M) {
+#pragma unroll
+            for (int j = 0; j < 32; ++j)
+              if (ti.out_col0 + c0 + j < args.N)
+                args.C[(size_t)row * args.ldc + ti.out_col0 + c0 + j] = __uint_as_float(re[j]) * args.scale;
+          }
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&tempty_bar[buf]);
+      ++local;
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem) : "memory");
+  }
+}
+
+// ------------------------------------------------------------------------------------
+// host helpers
+
+static int g_tc_sms = 0;
+
+static int tc_num_sms() {
+  if (!g_tc_sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&g_tc_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (g_tc_sms <= 0) g_tc_sms = 148;
+  }
+  return g_tc_sms;
+}
+
+static PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+static std::mutex g_encode_mu;
+
+static int get_encoder() {
+  std::lock_guard<std::mutex> lock(g_encode_mu);
+  if (g_encode) return CGH_OK;
+  void* fn = nullptr;
+  cudaDriverEntryPointQueryResult q;
+  cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+  if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn)
+    return cgh_fail(CGH_ERR_CUDA, "cuTensorMapEncodeTiled unavailable (%s)", cudaGetErrorString(e));
+  g_encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+  return CGH_OK;
+}
+
+// 3-D map over `planes` planes of a [rows][k_alloc] 16-bit matrix; box 32 x 128 x planes,
+// 64-byte swizzle (matches sdesc_sw64).
+static int make_plane_map(CUtensorMap* map, const void* base, int planes, long long rows, long long k_alloc) {
+  if (get_encoder() != CGH_OK) return CGH_ERR_CUDA;
+  if (((uintptr_t)base & 15) || (k_alloc * 2) % 16)
+    return cgh_fail(CGH_ERR_ARG, "tensor map: base must be 16-byte aligned and rows a multiple of 16 bytes");
+  cuuint64_t dims[3] = {(cuuint64_t)k_alloc, (cuuint64_t)rows, (cuuint64_t)planes};
+  cuuint64_t strides[2] = {(cuuint64_t)(k_alloc * 2), (cuuint64_t)(rows * k_alloc * 2)};
+  cuuint32_t box[3] = {TC_BK, 128, (cuuint32_t)planes};
+  cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_UINT16, 3, const_cast<void*>(base), dims, strides, box, estr,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return cgh_fail(CGH_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+  return CGH_OK;
+}
+
+template <int KIND, int EPI, bool F16>
+static cudaError_t set_gemm_attr() {
+  return cudaFuncSetAttribute(k_tc_gemm<KIND, EPI, F16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)tc_smem_bytes<KIND>());
+}
+
+template <int KIND, int EPI, bool F16>
+static cudaError_t launch_gemm(const CUtensorMap& ma, const CUtensorMap& mb, TcGemmArgs a, dim3 tiles,
+                               cudaStream_t st) {
+  a.tm = (int)tiles.x;
+  a.tn = (int)tiles.y;
+  a.tz = (int)tiles.z;
+  const long long units = (long long)a.tm * a.tn * a.tz;
+  const int grid = (int)(units < tc_num_sms() ? units : tc_num_sms());
+  if (grid <= 0) return cudaSuccess;
+  k_tc_gemm<KIND, EPI, F16><<<grid, 192, tc_smem_bytes<KIND>(), st>>>(ma, mb, a);
+  return cudaGetLastError();
+}
+

@@ -1,0 +1,110 @@
+"""Differentiable reconstruction and phase-only hologram optimisation.
+
+The hologram-to-reconstruction map is linear (the Fresnel back-propagation of the
+plan), so its backward pass is the forward point-source propagation of the layer
+fields: both run in libcgh's tensor-core kernels, wrapped here in a
+torch.autograd.Function.  PyTorch supplies the tensors, the Adam optimiser and
+checkpoint files; it computes no part of the hologram path.
+"""
+import torch
+
+from .cgh import phase_grad, phase_to_field
+
+
+class PhaseReconstruction(torch.autograd.Function):
+    """phase [holo, holo] float32  ->  composite amplitude [obj, obj] float32:
+    H = exp(j phase), R_z = Fresnel back-propagation of H to layer z,
+    amplitude(i, j) = |R_{layer(i,j)}(i, j)|.
+
+    With checkpoint=True the per-layer fields are not kept between forward and
+    backward; the backward recomputes them (activation checkpointing)."""
+
+    @staticmethod
+    def forward(ctx, phase, plan, layer, checkpoint=True):
+        phase = phase.contiguous()
+        H = phase_to_field(phase)
+        F, amp = plan.reconstruct(H, layer)
+        ctx.plan = plan
+        ctx.layer = layer
+        ctx.checkpoint = bool(checkpoint)
+        if ctx.checkpoint:
+            ctx.save_for_backward(phase)
+        else:
+            ctx.save_for_backward(phase, H, F)
+        return amp
+
+    @staticmethod
+    def backward(ctx, g_amp):
+        plan = ctx.plan
+        if ctx.checkpoint:
+            (phase,) = ctx.saved_tensors
+            H = phase_to_field(phase)
+            F, _ = plan.reconstruct(H, ctx.layer, amplitude=False)
+        else:
+            phase, H, F = ctx.saved_tensors
+        gF = plan.amplitude_backward(F, ctx.layer, g_amp.contiguous().float())
+        gH = plan.propagate(gF)
+        return phase_grad(H, gH), None, None, None
+
+
+def reconstruct_amplitude(phase, plan, layer, checkpoint=True):
+    return PhaseReconstruction.apply(phase, plan, layer, checkpoint)
+
+
+def weighted_loss(amp, target, weight, kappa):
+    """sum w (amp / kappa - target)^2, accumulated in float64."""
+    d = amp.double() / kappa - target.double()
+    return (weight.double() * d * d).sum()
+
+
+def fit_kappa(amp, target):
+    """Least-squares scale of the amplitude onto the target: sum(a T) / sum(T^2)."""
+    t = target.double()
+    return float((amp.double() * t).sum() / (t * t).sum())
+
+
+class PhaseOptimiser:
+    """Adam over a batch of phase-only holograms [B, holo, holo] so that each one's
+    reconstructed composite amplitude matches its target (weights per pixel, e.g. 4
+    inside the saliency mask and 1 outside).  state_dict()/load_state_dict() (with
+    torch.save/torch.load) checkpoint and resume the run; with a plan created with
+    Plan.DETERMINISTIC a resumed run reproduces an uninterrupted one bit for bit."""
+
+    def __init__(self, plan, layer, targets, weights, phase0, lr=0.05, checkpoint=True):
+        self.plan = plan
+        self.layer = layer
+        self.targets = targets
+        self.weights = weights
+        self.checkpoint = checkpoint
+        self.phase = phase0.detach().clone().float().contiguous().requires_grad_(True)
+        self.opt = torch.optim.Adam([self.phase], lr=lr)
+        self.step_count = 0
+        with torch.no_grad():
+            self.kappa = [fit_kappa(reconstruct_amplitude(self.phase[b], plan, layer, False), targets[b])
+                          for b in range(self.phase.shape[0])]
+
+    def loss(self):
+        total = 0.0
+        for b in range(self.phase.shape[0]):
+            amp = reconstruct_amplitude(self.phase[b], self.plan, self.layer, self.checkpoint)
+            total = total + weighted_loss(amp, self.targets[b], self.weights, self.kappa[b])
+        return total
+
+    def step(self):
+        self.opt.zero_grad(set_to_none=True)
+        L = self.loss()
+        L.backward()
+        self.opt.step()
+        self.step_count += 1
+        return float(L.detach())
+
+    def state_dict(self):
+        return {"phase": self.phase.detach().clone(), "adam": self.opt.state_dict(),
+                "step": self.step_count, "kappa": list(self.kappa)}
+
+    def load_state_dict(self, st):
+        with torch.no_grad():
+            self.phase.copy_(st["phase"])
+        self.opt.load_state_dict(st["adam"])
+        self.step_count = int(st["step"])
+        self.kappa = list(st["kappa"])

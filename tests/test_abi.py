@@ -55,6 +55,8 @@ def test_host_argument_checks_without_gpu(L):
     assert L.cgh_plan_create(ctypes.byref(h), 60, 60, 240, 240, 8e-6, 532e-9, 1, z, 3, 0, None) == 1
     # bad layer count / distances
     assert L.cgh_plan_create(ctypes.byref(h), 64, 64, 256, 256, 8e-6, 532e-9, 0, z, 3, 0, None) == 1
+    # unknown plan flags
+    assert L.cgh_plan_create(ctypes.byref(h), 64, 64, 256, 256, 8e-6, 532e-9, 1, z, 3, 4, None) == 1
     zneg = (ctypes.c_double * 1)(-0.1)
     assert L.cgh_plan_create(ctypes.byref(h), 64, 64, 256, 256, 8e-6, 532e-9, 1, zneg, 3, 0, None) == 1
     # NULL plan

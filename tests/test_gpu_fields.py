@@ -1,0 +1,213 @@
+"""Reconstruction, propagation, the progressive-operator adjoint and the phase-only
+optimisation on the GPU against the FP64 oracle.
+
+Bars: the bf16 hi+lo tensor-core products with FP32 accumulation stay within rel-L2
+1e-4 of FP64 (typically ~1e-5); adjoint identities hold to the same order; the phase
+gradient matches the FP64 analytic gradient to rel-L2 1e-3 and central finite
+differences (h = 1e-3) on 64 entries."""
+import numpy as np
+import pytest
+
+from oracle import cgh_oracle as O
+from synth import scenes
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    import os
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2211_09938_gb300 import build_lib, cgh
+    if not os.path.exists(cgh.LIB_PATH):
+        build_lib.build()
+    cgh.lib()
+    return torch
+
+
+def cplx(rng, *shape):
+    return (rng.normal(size=shape) + 1j * rng.normal(size=shape)).astype(np.complex64)
+
+
+@pytest.mark.parametrize("name,make", [
+    ("tiny_64_to_256_z4", lambda: scenes.tiny_scene()),
+    ("single_layer_32_s2", lambda: scenes.random_scene(78, 32, 64, 1, graded=True)),
+    ("paper_512_to_1024_z16", lambda: scenes.paper_scene()),
+])
+def test_reconstruct_matches_oracle(torch_cuda, name, make):
+    torch = torch_cuda
+    from paper_2211_09938_gb300 import Plan
+    sc = make()
+    g = O.geometry_of(sc)
+    plan = Plan.for_scene(sc)
+    lists = O.progressive_lists(sc["saliency"], sc["layer"], g.n_layers, scenes.THRESHOLDS_U8)
+    H = O.progressive_hologram(sc["intensity"], sc["layer"], lists, g)
+    Hd = torch.from_numpy(H.astype(np.complex64)).cuda()
+    L = torch.from_numpy(sc["layer"]).cuda()
+    F, A = plan.reconstruct(Hd, L)
+    torch.cuda.synchronize()
+    R = O.reconstruct_fields(H, g)
+    errF = O.rel_l2(F.cpu().numpy(), R)
+    errA = O.rel_l2(A.cpu().numpy(), O.composite_amplitude(R, sc["layer"]))
+    print(f"reconstruct {name}: fields {errF:.2e} amplitude {errA:.2e}")
+    assert errF <= TOL and errA <= TOL
+
+
+def test_propagate_matches_oracle_and_is_adjoint(torch_cuda):
+    torch = torch_cuda
+    from paper_2211_09938_gb300 import Plan
+    rng = np.random.default_rng(12)
+    sc = scenes.tiny_scene()
+    g = O.geometry_of(sc)
+    plan = Plan.for_scene(sc)
+    F = cplx(rng, 4, 64, 64)
+    Hg = plan.propagate(torch.from_numpy(F).cuda())
+    torch.cuda.synchronize()
+    Href = O.propagate_fields(F, g)
+    err = O.rel_l2(Hg.cpu().numpy(), Href)
+    print(f"propagate tiny: {err:.2e}")
+    assert err <= TOL
+    # accumulate adds onto what is there
+    H2 = plan.propagate(torch.from_numpy(F).cuda(), holo=Hg.clone(), accumulate=True)
+    torch.cuda.synchronize()
+    assert O.rel_l2(H2.cpu().numpy(), 2 * Href) <= TOL
+    # <reconstruct(H), F> = <H, propagate(F)> on the GPU
+    Hx = cplx(rng, 256, 256)
+    Rx, _ = plan.reconstruct(torch.from_numpy(Hx).cuda(), amplitude=False)
+    lhs = np.real(np.vdot(Rx.cpu().numpy().astype(np.complex128), F.astype(np.complex128)))
+    rhs = np.real(np.vdot(Hx.astype(np.complex128), Hg.cpu().numpy().astype(np.complex128)))
+    assert abs(lhs - rhs) <= 1e-4 * abs(lhs)
+
+
+def test_adjoint_matches_oracle(torch_cuda):
+    torch = torch_cuda
+    from paper_2211_09938_gb300 import Plan
+    rng = np.random.default_rng(13)
+    sc = scenes.random_scene(81, 64, 128, 3, graded=True)
+    g = O.geometry_of(sc)
+    plan = Plan.for_scene(sc)
+    L = torch.from_numpy(sc["layer"]).cuda()
+    S = torch.from_numpy(sc["saliency"]).cuda()
+    lists, counts = plan.progressive_lists(S, L, scenes.THRESHOLDS_U8)
+    G = cplx(rng, 128, 128)
+    grad = plan.adjoint(torch.from_numpy(G).cuda(), lists, counts, L)
+    torch.cuda.synchronize()
+    ref_lists = O.progressive_lists(sc["saliency"], sc["layer"], 3, scenes.THRESHOLDS_U8)
+    ref = O.progressive_adjoint(G, sc["layer"], ref_lists, g)
+    err = O.rel_l2(grad.cpu().numpy(), ref)
+    print(f"adjoint: {err:.2e}")
+    assert err <= TOL
+    # dot-product identity against the GPU forward (direct form, FP32)
+    I = rng.integers(0, 256, size=(64, 64)).astype(np.uint8)
+    coeffs = plan.haar_decompose(torch.from_numpy(I).cuda(), L)
+    FI = plan.progressive_hologram(coeffs, lists, counts)
+    torch.cuda.synchronize()
+    lhs = np.real(np.vdot(FI.cpu().numpy().astype(np.complex128), G.astype(np.complex128)))
+    rhs = float(np.sum(I.astype(np.float64) * grad.cpu().numpy()))
+    assert abs(lhs - rhs) <= 1e-4 * abs(lhs)
+
+
+def test_amplitude_backward_and_phase_kernels(torch_cuda):
+    torch = torch_cuda
+    from paper_2211_09938_gb300 import Plan
+    from paper_2211_09938_gb300.cgh import phase_grad, phase_to_field
+    rng = np.random.default_rng(14)
+    sc = scenes.tiny_scene()
+    plan = Plan.for_scene(sc)
+    F = cplx(rng, 4, 64, 64)
+    F[0, 0, 0] = 0
+    gA = rng.normal(size=(64, 64)).astype(np.float32)
+    gF = plan.amplitude_backward(torch.from_numpy(F).cuda(), torch.from_numpy(sc["layer"]).cuda(),
+                                 torch.from_numpy(gA).cuda()).cpu().numpy()
+    ref = np.zeros_like(F)
+    lay = sc["layer"].astype(int)
+    ii, jj = np.indices(lay.shape)
+    v = F[lay, ii, jj]
+    a = np.abs(v)
+    ref[lay, ii, jj] = np.where(a > 0, gA * v / np.where(a > 0, a, 1), 0)
+    assert np.allclose(gF, ref, atol=1e-5)
+    phi = rng.uniform(-10, 10, size=(300,)).astype(np.float32)
+    H = phase_to_field(torch.from_numpy(phi).cuda()).cpu().numpy()
+    assert np.allclose(H, np.exp(1j * phi.astype(np.float64)), atol=2e-6)
+    g = cplx(rng, 300)
+    gp = phase_grad(torch.from_numpy(H).cuda(), torch.from_numpy(g).cuda()).cpu().numpy()
+    assert np.allclose(gp, np.imag(g * np.conj(H)), atol=1e-5)
+
+
+def _opt_case(torch, n=64, holo=128, nl=4, seed=15, flags=0):
+    from paper_2211_09938_gb300 import Plan
+    sc = scenes.random_scene(seed, n, holo, nl)
+    rng = np.random.default_rng(seed)
+    plan = Plan.for_scene(sc, flags=flags)
+    target = (sc["intensity"].astype(np.float32) / 255.0)
+    weight = np.where(sc["saliency"] > 0, 4.0, 1.0).astype(np.float32)
+    phase = rng.uniform(-np.pi, np.pi, size=(holo, holo)).astype(np.float32)
+    return sc, plan, target, weight, phase
+
+
+def test_phase_gradient_vs_oracle_and_finite_differences(torch_cuda):
+    torch = torch_cuda
+    from paper_2211_09938_gb300 import optim
+    sc, plan, target, weight, phase = _opt_case(torch)
+    g = O.geometry_of(sc)
+    L = torch.from_numpy(sc["layer"]).cuda()
+    T = torch.from_numpy(target).cuda()
+    W = torch.from_numpy(weight).cuda()
+    with torch.no_grad():
+        kappa = optim.fit_kappa(optim.reconstruct_amplitude(torch.from_numpy(phase).cuda(), plan, L), T)
+    ph = torch.from_numpy(phase).cuda().requires_grad_(True)
+    loss = optim.weighted_loss(optim.reconstruct_amplitude(ph, plan, L, True), T, W, kappa)
+    loss.backward()
+    grad = ph.grad.cpu().numpy().astype(np.float64)
+    ref = O.phase_opt_grad(phase.astype(np.float64), target, weight, sc["layer"], g, kappa)
+    err = O.rel_l2(grad, ref)
+    print(f"phase gradient vs FP64 oracle: {err:.2e}")
+    assert err <= 1e-3
+    # checkpointed and stored-field backward agree exactly
+    ph2 = torch.from_numpy(phase).cuda().requires_grad_(True)
+    optim.weighted_loss(optim.reconstruct_amplitude(ph2, plan, L, False), T, W, kappa).backward()
+    assert torch.equal(ph2.grad, ph.grad)
+    # central finite differences of the FP64 oracle loss, h = 1e-3, 64 random entries
+    rng = np.random.default_rng(16)
+    idx = rng.integers(0, phase.size, size=64)
+    h = 1e-3
+    fd = []
+    for k in idx:
+        e = np.zeros(phase.size)
+        e[k] = h
+        e = e.reshape(phase.shape)
+        fd.append((O.phase_opt_loss(phase + e, target, weight, sc["layer"], g, kappa)
+                   - O.phase_opt_loss(phase - e, target, weight, sc["layer"], g, kappa)) / (2 * h))
+    fd = np.array(fd)
+    gk = grad.reshape(-1)[idx]
+    err_fd = np.linalg.norm(gk - fd) / np.linalg.norm(fd)
+    print(f"phase gradient vs central differences (64 entries): {err_fd:.2e}")
+    assert err_fd <= 1e-2
+
+
+def test_phase_optimisation_decreases_and_resumes_bit_identically(torch_cuda, tmp_path):
+    torch = torch_cuda
+    from paper_2211_09938_gb300 import Plan, optim
+    sc, plan, target, weight, phase = _opt_case(torch, flags=Plan.DETERMINISTIC)
+    L = torch.from_numpy(sc["layer"]).cuda()
+    T = torch.from_numpy(np.stack([target, target[::-1].copy()])).cuda()
+    W = torch.from_numpy(weight).cuda()
+    ph0 = torch.from_numpy(np.stack([phase, -phase])).cuda()
+    a = optim.PhaseOptimiser(plan, L, T, W, ph0, lr=0.05)
+    losses = [a.step() for _ in range(6)]
+    assert losses[-1] < losses[0]
+    b = optim.PhaseOptimiser(plan, L, T, W, ph0, lr=0.05)
+    for _ in range(3):
+        b.step()
+    path = tmp_path / "phase.pt"
+    torch.save(b.state_dict(), path)
+    c = optim.PhaseOptimiser(plan, L, T, W, torch.zeros_like(ph0), lr=0.05)
+    c.load_state_dict(torch.load(path))
+    for _ in range(3):
+        c.step()
+    assert c.step_count == 6
+    assert torch.equal(c.phase.detach(), a.phase.detach())

@@ -433,3 +433,49 @@ def test_progressive_levels_improve_quality():
     s_prog = q(O.progressive_lists(sc["saliency"], sc["layer"], 1, {3: 0, 2: 100, 1: 200}))
     s_all = q(all_salient_lists(sc["layer"], 1))
     assert s_lll < s_prog < s_all
+
+
+# ---------------------------------------------------------------- propagation / phase optimisation
+
+def test_propagate_is_adjoint_of_reconstruct():
+    """<reconstruct(H), F> = <H, propagate(F)> for complex H and F (real inner product)."""
+    rng = np.random.default_rng(41)
+    g = tiny_geom(8, 2, 3)
+    H = rng.normal(size=(16, 16)) + 1j * rng.normal(size=(16, 16))
+    F = rng.normal(size=(3, 8, 8)) + 1j * rng.normal(size=(3, 8, 8))
+    lhs = np.real(np.vdot(O.reconstruct_fields(H, g), F))
+    rhs = np.real(np.vdot(H, O.propagate_fields(F, g)))
+    assert abs(lhs - rhs) <= 1e-10 * abs(lhs)
+
+
+def test_propagate_real_fields_is_pointwise_and_single_point():
+    rng = np.random.default_rng(42)
+    g = tiny_geom(8, 4, 2)
+    planes = rng.uniform(0, 1, size=(2, 8, 8))
+    assert O.rel_l2(O.propagate_fields(planes, g), O.pointwise_hologram_direct(planes, g)) < 1e-12
+    # one complex point of value 2j at a = 1/4: H = 2j * j^(odd(dm) + odd(dn))
+    g4 = tiny_geom(8, 4, 1, a=0.25)
+    F = np.zeros((1, 8, 8), complex)
+    F[0, 2, 5] = 2j
+    m = np.arange(32)[:, None] - 8
+    n = np.arange(32)[None, :] - 20
+    assert np.max(np.abs(O.propagate_fields(F, g4) - 2j * 1j ** ((m % 2) + (n % 2)))) < 1e-7
+
+
+def test_phase_opt_gradient_matches_finite_differences():
+    """O7: the analytic phase gradient against central differences of the FP64 loss."""
+    rng = np.random.default_rng(43)
+    g = tiny_geom(8, 2, 2)
+    layer = rng.integers(0, 2, size=(8, 8)).astype(np.uint8)
+    target = rng.uniform(0, 1, size=(8, 8))
+    weight = np.where(rng.uniform(size=(8, 8)) > 0.5, 4.0, 1.0)
+    phase = rng.uniform(-np.pi, np.pi, size=(16, 16))
+    kappa = 20.0
+    grad = O.phase_opt_grad(phase, target, weight, layer, g, kappa)
+    h = 1e-6
+    for (m, n) in ((0, 0), (3, 7), (15, 15), (8, 2), (11, 13)):
+        e = np.zeros_like(phase)
+        e[m, n] = h
+        fd = (O.phase_opt_loss(phase + e, target, weight, layer, g, kappa)
+              - O.phase_opt_loss(phase - e, target, weight, layer, g, kappa)) / (2 * h)
+        assert abs(fd - grad[m, n]) <= 1e-6 * max(1.0, abs(fd)), (m, n, fd, grad[m, n])
