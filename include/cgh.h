@@ -295,6 +295,45 @@ int cgh_phase_grad(const float* field, const float* grad_field, float* grad_phas
 int cgh_tc_selftest_gemm(const uint16_t* A, const uint16_t* B, float* C, int M, int N, int K, int is_fp16,
                          void* stream);
 
+/* ---- batches ----------------------------------------------------------------------- */
+typedef struct cgh_batch cgh_batch;
+
+/*
+ * cgh_batch_create - many scenes, each with its own plan, run as one batch.
+ * Paper: Section 2 steps 1-5 for every scene; the batch is this library's scheduling.
+ * For scene k: plans[k], device inputs intensity[k], layer_idx[k], saliency[k] (uint8
+ * [obj_h][obj_w] of that plan), output holos[k] (complex64 [holo_h][holo_w]), shared
+ * thresholds (HOST int[3], levels 1, 2, 3).  The buffers are bound at creation and reused by
+ * every cgh_batch_run (fill the inputs, run, read the outputs), so a run can be captured in
+ * a CUDA graph.  form: CGH_FORM_TC_BF16X3 or CGH_FORM_TC_FP16X3.  The batch allocates the
+ * per-scene coefficients and work lists; it does not own the plans.  1 <= n <= 1024.
+ * Errors: CGH_ERR_ARG, CGH_ERR_UNSUPPORTED (form), CGH_ERR_NOMEM, CGH_ERR_CUDA.
+ */
+int cgh_batch_create(cgh_batch** out, cgh_plan* const* plans, int n, const uint8_t* const* intensity,
+                     const uint8_t* const* layer_idx, const uint8_t* const* saliency, const int* thresholds,
+                     float* const* holos, int form, void* stream);
+
+/*
+ * cgh_batch_run - enqueue one progressive hologram per scene: per scene the DWT, the fused
+ * selection and the operand build; then ONE persistent stage-1 launch and ONE persistent
+ * stage-2 launch whose work units span every scene (uneven sizes and work lists included).
+ */
+int cgh_batch_run(cgh_batch* batch, void* stream);
+
+/*
+ * cgh_batch_set_tuning - target number of 32-wide K steps per stage-2 work unit (splits of
+ * each scene's K); synchronises the device and re-uploads the work descriptors.  Chosen by
+ * the autotuner of the Python package; default 32.
+ */
+int cgh_batch_set_tuning(cgh_batch* batch, int ksteps_per_unit);
+
+/* cgh_batch_lists - device pointers of scene k's work lists [4], counts int32[4][2] and
+ * coefficients (owned by the batch; valid after a run has completed). */
+int cgh_batch_lists(const cgh_batch* batch, int scene, int32_t** lists, int32_t** d_counts, int32_t** coeffs);
+
+/* Frees the batch (synchronises the device first).  NULL is a no-op. */
+int cgh_batch_destroy(cgh_batch* batch);
+
 /* ---- profiling -------------------------------------------------------------------- */
 /* Stage slots of cgh_profile_read. */
 #define CGH_PROF_TABLES 0      /* fringe-table build                    */

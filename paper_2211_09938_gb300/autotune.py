@@ -1,0 +1,53 @@
+"""Autotuner for the batched tensor-core launch: picks the number of 32-wide K steps per
+stage-2 work unit (how finely each scene's K is split across the persistent CTAs) by
+timing the batch with CUDA events, and caches the choice in a JSON file keyed by the
+batch's shape signature, the form and the GPU name."""
+import json
+import os
+
+CANDIDATES = (8, 16, 32, 64, 128)
+
+
+def signature(plans, form):
+    dims = sorted((p.obj_h, p.holo_h, p.n_layers) for p in plans)
+    return f"{form}|" + ";".join(f"{a}-{b}-{c}" for a, b, c in dims)
+
+
+def tune_batch(batch, plans, form, stream, cache_path=None, reps=3, candidates=CANDIDATES):
+    import torch
+    gpu = torch.cuda.get_device_name()
+    key = gpu + "|" + signature(plans, form)
+    cache = {}
+    if cache_path and os.path.exists(cache_path):
+        try:
+            cache = json.load(open(cache_path))
+        except Exception:
+            cache = {}
+    if key in cache:
+        batch.set_tuning(cache[key]["ksteps"])
+        return cache[key]
+    results = {}
+    for c in candidates:
+        batch.set_tuning(c)
+        with torch.cuda.stream(stream):
+            batch.run(stream=stream)  # warm
+        times = []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            with torch.cuda.stream(stream):
+                e0.record(stream)
+                batch.run(stream=stream)
+                e1.record(stream)
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+        results[c] = sorted(times)[len(times) // 2]
+    best = min(results, key=results.get)
+    batch.set_tuning(best)
+    entry = {"ksteps": best, "ms": results[best], "tried": {str(k): v for k, v in results.items()}}
+    if cache_path:
+        cache[key] = entry
+        tmp = cache_path + ".tmp"
+        with open(tmp, "w") as f:
+            json.dump(cache, f, indent=1)
+        os.replace(tmp, cache_path)
+    return entry

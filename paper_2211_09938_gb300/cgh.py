@@ -54,6 +54,13 @@ SIGNATURES = {
     "cgh_phase_grad": (_I, [_P, _P, _P, ctypes.c_longlong, _P]),
     "cgh_status": (_I, [_P, ctypes.POINTER(_I), _P]),
     "cgh_tc_selftest_gemm": (_I, [_P, _P, _P, _I, _I, _I, _I, _P]),
+    "cgh_batch_create": (_I, [ctypes.POINTER(_P), ctypes.POINTER(_P), _I, ctypes.POINTER(_P),
+                              ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_I),
+                              ctypes.POINTER(_P), _I, _P]),
+    "cgh_batch_run": (_I, [_P, _P]),
+    "cgh_batch_set_tuning": (_I, [_P, _I]),
+    "cgh_batch_lists": (_I, [_P, _I, ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_P)]),
+    "cgh_batch_destroy": (_I, [_P]),
     "cgh_profile": (_I, [_P, _I]),
     "cgh_profile_read": (_I, [_P, ctypes.POINTER(ctypes.c_float), _P]),
     "cgh_tc_layer_dims": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(_I), _P]),
@@ -292,3 +299,49 @@ def phase_grad(field, grad_field, out=None, stream=None):
         out = torch.empty(field.shape, dtype=torch.float32, device=field.device)
     check(lib().cgh_phase_grad(_ptr(field), _ptr(grad_field), _ptr(out), field.numel(), _stream(stream)))
     return out
+
+
+class Batch:
+    """cgh_batch: many scenes (each with its Plan) run as one batch.  Inputs and outputs
+    are bound at creation; run() enqueues every scene's hologram with one persistent
+    launch per GEMM stage across all scenes."""
+
+    def __init__(self, plans, intensity, layer, saliency, thresholds, holos, form="tc_bf16x3",
+                 stream=None):
+        n = len(plans)
+        self.plans = list(plans)
+        self._keep = (list(intensity), list(layer), list(saliency), list(holos))
+        P = ctypes.c_void_p
+        arr = lambda xs: (P * n)(*[x.data_ptr() for x in xs])
+        thr = (ctypes.c_int * 3)(*[int(thresholds[l]) for l in (1, 2, 3)])
+        h = P()
+        check(lib().cgh_batch_create(ctypes.byref(h), (P * n)(*[p.handle.value for p in plans]), n,
+                                     arr(intensity), arr(layer), arr(saliency), thr, arr(holos),
+                                     FORMS[form] if isinstance(form, str) else int(form), _stream(stream)))
+        self.handle = h
+        self.holos = list(holos)
+
+    def run(self, stream=None):
+        check(lib().cgh_batch_run(self.handle, _stream(stream)))
+
+    def set_tuning(self, ksteps_per_unit):
+        check(lib().cgh_batch_set_tuning(self.handle, int(ksteps_per_unit)))
+
+    def lists(self, k):
+        """(lists [4] as raw device pointers, counts pointer, coeffs pointer) of scene k."""
+        P = ctypes.c_void_p
+        lp = (P * 4)()
+        cp, kp = P(), P()
+        check(lib().cgh_batch_lists(self.handle, int(k), lp, ctypes.byref(cp), ctypes.byref(kp)))
+        return [lp[i] for i in range(4)], cp.value, kp.value
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            lib().cgh_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -325,18 +325,19 @@ static int stage2_splits(int tiles, int kmax_steps) {
   return best;
 }
 
-template <bool F16>
-static int tc_run(const cgh_plan* p, const int32_t* coef, const int32_t* const* lists, const int32_t* d_counts,
-                  float2* holo, int accumulate, cudaStream_t st) {
-  cgh_tc_state* t = p->tc;
-  const int H = p->obj_h, W = p->obj_w, Z = p->n_layers;
-  cudaError_t e;
 #define TC_CK(expr, what)                                   \
   do {                                                      \
     int _rc = cgh_cuda_check((expr), (what));               \
     if (_rc != CGH_OK) return _rc;                          \
   } while (0)
-  prof_mark(p, CGH_PROF_TC_PREP, 0, st);
+
+// Operands of both GEMM stages for one scene: selection flags, per-layer band compaction,
+// the inverse-DWT operand (stage-1 B) and the gathered fringe operands (stage-1 and 2 A).
+template <bool F16>
+static int tc_prep(const cgh_plan* p, const int32_t* coef, const int32_t* const* lists, const int32_t* d_counts,
+                   cudaStream_t st) {
+  cgh_tc_state* t = p->tc;
+  const int H = p->obj_h, W = p->obj_w, Z = p->n_layers;
   TC_CK(cudaMemsetAsync(t->flags, 0, t->flags_bytes, st), "tc: clear flags");
   k_tc_scatter<<<dim3(64, 4), 256, 0, st>>>(lists[0], lists[1], lists[2], lists[3], d_counts, t->fl, H, W, Z);
   TC_CK(cudaGetLastError(), "tc: scatter");
@@ -358,53 +359,294 @@ static int tc_run(const cgh_plan* p, const int32_t* coef, const int32_t* const* 
                                               t->kr_pad, p->holo_h, 1, t->A2, t->a2_plane, t->ktot_alloc);
     TC_CK(cudaGetLastError(), "tc: gather E2");
   }
+  return CGH_OK;
+}
+
+// Stage 1: Y^T = E_z[:, cols] * A^_z[rows, cols]^T / 64 (scaled by a further 2^-4 for fp16
+// headroom); units (M tiles, N tiles, layers).
+static void stage1_args(const cgh_plan* p, bool f16, TcGemmArgs& a, dim3& tiles) {
+  cgh_tc_state* t = p->tc;
+  memset(&a, 0, sizeof(a));
+  a.mode = 1;
+  a.a_rows_per_z = p->holo_w;
+  a.kr_pad = t->kr_pad;
+  a.kc_pad = t->kc_pad;
+  a.n_layers = p->n_layers;
+  a.M = p->holo_w;
+  a.N = t->ktot_alloc;
+  a.scale = f16 ? 1.0f / 1024.0f : 1.0f / 64.0f;
+  a.Y = t->Y;
+  a.y_plane = t->y_plane;
+  a.ldy = t->ktot_alloc;
+  a.status = p->d_status;
+  tiles = dim3((p->holo_w + TC_BM - 1) / TC_BM, (t->kr_alloc + TC_BN - 1) / TC_BN, p->n_layers);
+  a.tm = tiles.x;
+  a.tn = tiles.y;
+  a.tz = tiles.z;
+}
+
+// Stage 2: H += sum_kappa E[m][kappa] Y^T[n][kappa] over the concatenated layer rows,
+// K split S ways; units (M tiles, N tiles, S).
+static void stage2_args(const cgh_plan* p, bool f16, float2* holo, int S, TcGemmArgs& a, dim3& tiles) {
+  cgh_tc_state* t = p->tc;
+  memset(&a, 0, sizeof(a));
+  a.mode = 2;
+  a.kr_pad = t->kr_pad;
+  a.n_layers = p->n_layers;
+  a.M = p->holo_h;
+  a.N = p->holo_w;
+  a.scale = f16 ? 16.0f : 1.0f;
+  a.H = holo;
+  a.ldh = p->holo_w;
+  a.h_vec4 = ((p->holo_w & 1) == 0) && (((uintptr_t)holo & 15) == 0);
+  a.status = p->d_status;
+  tiles = dim3((p->holo_h + TC_BM - 1) / TC_BM, (p->holo_w + TC_BN - 1) / TC_BN, S);
+  a.tm = tiles.x;
+  a.tn = tiles.y;
+  a.tz = tiles.z;
+}
+
+template <bool F16>
+static int tc_run(const cgh_plan* p, const int32_t* coef, const int32_t* const* lists, const int32_t* d_counts,
+                  float2* holo, int accumulate, cudaStream_t st) {
+  cgh_tc_state* t = p->tc;
+  prof_mark(p, CGH_PROF_TC_PREP, 0, st);
+  int rc = tc_prep<F16>(p, coef, lists, d_counts, st);
+  if (rc != CGH_OK) return rc;
   prof_mark(p, CGH_PROF_TC_PREP, 1, st);
-  // stage 1: Y^T = E_z[:, cols] * A^_z[rows, cols]^T / 64, scaled by 2^-4 for fp16 headroom
-  const float s1 = F16 ? 1.0f / 1024.0f : 1.0f / 64.0f;
-  const float s2 = F16 ? 16.0f : 1.0f;
-  {
-    TcGemmArgs a;
-    memset(&a, 0, sizeof(a));
-    a.mode = 1;
-    a.a_rows_per_z = p->holo_w;
-    a.kr_pad = t->kr_pad;
-    a.kc_pad = t->kc_pad;
-    a.n_layers = Z;
-    a.M = p->holo_w;
-    a.N = t->ktot_alloc;
-    a.scale = s1;
-    a.Y = t->Y;
-    a.y_plane = t->y_plane;
-    a.ldy = t->ktot_alloc;
-    a.status = p->d_status;
-    dim3 grid((p->holo_w + TC_BM - 1) / TC_BM, (t->kr_alloc + TC_BN - 1) / TC_BN, Z);
-    prof_mark(p, CGH_PROF_TC_STAGE1, 0, st);
-    e = launch_gemm<KIND_CR, EPI_Y, F16>(t->mA1, t->mB1, a, grid, st);
-    prof_mark(p, CGH_PROF_TC_STAGE1, 1, st);
-    TC_CK(e, "tc: stage-1 GEMM");
-  }
+  TcGemmArgs a;
+  dim3 tiles;
+  stage1_args(p, F16, a, tiles);
+  prof_mark(p, CGH_PROF_TC_STAGE1, 0, st);
+  cudaError_t e = launch_gemm<KIND_CR, EPI_Y, F16>(t->mA1, t->mB1, a, tiles, st);
+  prof_mark(p, CGH_PROF_TC_STAGE1, 1, st);
+  TC_CK(e, "tc: stage-1 GEMM");
   if (!accumulate) TC_CK(cudaMemsetAsync(holo, 0, (size_t)p->holo_h * p->holo_w * sizeof(float2), st), "tc: clear");
-  {
-    TcGemmArgs a;
-    memset(&a, 0, sizeof(a));
-    a.mode = 2;
-    a.kr_pad = t->kr_pad;
-    a.n_layers = Z;
-    a.M = p->holo_h;
-    a.N = p->holo_w;
-    a.scale = s2;
-    a.H = holo;
-    a.ldh = p->holo_w;
-    a.h_vec4 = ((p->holo_w & 1) == 0) && (((uintptr_t)holo & 15) == 0);
-    a.status = p->d_status;
-    const int tm = (p->holo_h + TC_BM - 1) / TC_BM, tn = (p->holo_w + TC_BN - 1) / TC_BN;
-    const int S = p->deterministic ? 1 : stage2_splits(tm * tn, t->ktot_alloc / TC_BK);
-    prof_mark(p, CGH_PROF_TC_STAGE2, 0, st);
-    e = launch_gemm<KIND_CC, EPI_H, F16>(t->mA2, t->mY, a, dim3(tm, tn, S), st);
-    prof_mark(p, CGH_PROF_TC_STAGE2, 1, st);
-    TC_CK(e, "tc: stage-2 GEMM");
+  const int tm = (p->holo_h + TC_BM - 1) / TC_BM, tn = (p->holo_w + TC_BN - 1) / TC_BN;
+  const int S = p->deterministic ? 1 : stage2_splits(tm * tn, t->ktot_alloc / TC_BK);
+  stage2_args(p, F16, holo, S, a, tiles);
+  prof_mark(p, CGH_PROF_TC_STAGE2, 0, st);
+  e = launch_gemm<KIND_CC, EPI_H, F16>(t->mA2, t->mY, a, tiles, st);
+  prof_mark(p, CGH_PROF_TC_STAGE2, 1, st);
+  TC_CK(e, "tc: stage-2 GEMM");
+  return CGH_OK;
+}
+
+// ------------------------------------------------------------------------------------
+// batches: many scenes, each with its own plan, through one persistent launch per stage
+
+__global__ void k_batch_koff(TcBatchItem* __restrict__ a, TcBatchItem* __restrict__ b, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int o = 0;
+  a[i].koff[0] = b[i].koff[0] = 0;
+  for (int q = 0; q < a[i].a.n_layers; ++q) {
+    o += a[i].a.kr_pad[q];
+    a[i].koff[q + 1] = b[i].koff[q + 1] = o;
   }
-#undef TC_CK
+}
+
+struct cgh_batch {
+  int n, form, ksteps;
+  cgh_plan** plans;
+  const uint8_t **I, **L, **S;
+  float2** H;
+  int thr[3];
+  int32_t** coeffs;
+  int32_t** lists;  // [n][4]
+  int32_t* counts;  // device [n][4][2]
+  TcBatchItem *h1, *h2, *d1, *d2;
+  int units1, units2;
+};
+
+static int batch_upload(cgh_batch* b) {
+  const bool f16 = b->form == CGH_FORM_TC_FP16X3;
+  int u1 = 0, u2 = 0;
+  for (int i = 0; i < b->n; ++i) {
+    const cgh_plan* p = b->plans[i];
+    cgh_tc_state* t = p->tc;
+    dim3 tiles;
+    b->h1[i].ma = t->mA1;
+    b->h1[i].mb = t->mB1;
+    stage1_args(p, f16, b->h1[i].a, tiles);
+    b->h1[i].unit0 = u1;
+    u1 += tiles.x * tiles.y * tiles.z;
+    const int tm = (p->holo_h + TC_BM - 1) / TC_BM, tn = (p->holo_w + TC_BN - 1) / TC_BN;
+    const int kst = t->ktot_alloc / TC_BK;
+    int S = p->deterministic ? 1 : (kst + b->ksteps - 1) / b->ksteps;
+    if (S < 1) S = 1;
+    b->h2[i].ma = t->mA2;
+    b->h2[i].mb = t->mY;
+    stage2_args(p, f16, b->H[i], S, b->h2[i].a, tiles);
+    b->h2[i].unit0 = u2;
+    u2 += tiles.x * tiles.y * tiles.z;
+  }
+  b->units1 = u1;
+  b->units2 = u2;
+  TC_CK(cudaMemcpy(b->d1, b->h1, b->n * sizeof(TcBatchItem), cudaMemcpyHostToDevice), "batch: upload");
+  TC_CK(cudaMemcpy(b->d2, b->h2, b->n * sizeof(TcBatchItem), cudaMemcpyHostToDevice), "batch: upload");
+  return CGH_OK;
+}
+
+extern "C" int cgh_batch_destroy(cgh_batch* b) {
+  if (!b) return CGH_OK;
+  cudaDeviceSynchronize();
+  for (int i = 0; i < b->n; ++i) {
+    if (b->coeffs) cudaFree(b->coeffs[i]);
+    if (b->lists)
+      for (int k = 0; k < 4; ++k) cudaFree(b->lists[4 * i + k]);
+  }
+  cudaFree(b->counts);
+  cudaFree(b->d1);
+  cudaFree(b->d2);
+  free(b->h1);
+  free(b->h2);
+  free(b->coeffs);
+  free(b->lists);
+  free(b->plans);
+  free(b->I);
+  free(b->L);
+  free(b->S);
+  free(b->H);
+  free(b);
+  return CGH_OK;
+}
+
+extern "C" int cgh_batch_create(cgh_batch** out, cgh_plan* const* plans, int n, const uint8_t* const* intensity,
+                                const uint8_t* const* layer_idx, const uint8_t* const* saliency,
+                                const int* thresholds, float* const* holos, int form, void* stream) {
+  if (!out || !plans || !intensity || !layer_idx || !saliency || !thresholds || !holos)
+    return cgh_fail(CGH_ERR_ARG, "cgh_batch_create: NULL argument");
+  *out = nullptr;
+  if (n < 1 || n > TC_BATCH_MAX) return cgh_fail(CGH_ERR_ARG, "cgh_batch_create: n %d not in 1..%d", n, TC_BATCH_MAX);
+  if (form != CGH_FORM_TC_BF16X3 && form != CGH_FORM_TC_FP16X3)
+    return cgh_fail(CGH_ERR_UNSUPPORTED, "cgh_batch_create: batches run the tensor-core forms");
+  for (int k = 0; k < 3; ++k)
+    if (thresholds[k] < -1 || thresholds[k] > 255) return cgh_fail(CGH_ERR_ARG, "cgh_batch_create: bad threshold");
+  for (int i = 0; i < n; ++i) {
+    if (!plans[i] || !intensity[i] || !layer_idx[i] || !saliency[i] || !holos[i])
+      return cgh_fail(CGH_ERR_ARG, "cgh_batch_create: NULL pointer for scene %d", i);
+    if (((uintptr_t)intensity[i] & 7) || ((uintptr_t)layer_idx[i] & 7) || ((uintptr_t)holos[i] & 7))
+      return cgh_fail(CGH_ERR_ARG, "cgh_batch_create: misaligned buffer for scene %d", i);
+  }
+  cgh_batch* b = (cgh_batch*)calloc(1, sizeof(cgh_batch));
+  if (!b) return cgh_fail(CGH_ERR_NOMEM, "cgh_batch_create: host allocation");
+  b->n = n;
+  b->form = form;
+  b->ksteps = 32;
+  for (int k = 0; k < 3; ++k) b->thr[k] = thresholds[k];
+  b->plans = (cgh_plan**)calloc(n, sizeof(cgh_plan*));
+  b->I = (const uint8_t**)calloc(n, sizeof(void*));
+  b->L = (const uint8_t**)calloc(n, sizeof(void*));
+  b->S = (const uint8_t**)calloc(n, sizeof(void*));
+  b->H = (float2**)calloc(n, sizeof(void*));
+  b->coeffs = (int32_t**)calloc(n, sizeof(void*));
+  b->lists = (int32_t**)calloc(4 * (size_t)n, sizeof(void*));
+  b->h1 = (TcBatchItem*)aligned_alloc(128, n * sizeof(TcBatchItem));
+  b->h2 = (TcBatchItem*)aligned_alloc(128, n * sizeof(TcBatchItem));
+  int rc = CGH_OK;
+  if (!b->plans || !b->I || !b->L || !b->S || !b->H || !b->coeffs || !b->lists || !b->h1 || !b->h2) {
+    cgh_batch_destroy(b);
+    return cgh_fail(CGH_ERR_NOMEM, "cgh_batch_create: host allocation");
+  }
+  memset(b->h1, 0, n * sizeof(TcBatchItem));
+  memset(b->h2, 0, n * sizeof(TcBatchItem));
+#define B_TRY(expr, what)                  \
+  do {                                     \
+    rc = cgh_cuda_check((expr), (what));   \
+    if (rc != CGH_OK) {                    \
+      cgh_batch_destroy(b);                \
+      return rc;                           \
+    }                                      \
+  } while (0)
+  B_TRY(cudaMalloc(&b->counts, (size_t)n * 8 * sizeof(int32_t)), "cgh_batch_create: counts");
+  B_TRY(cudaMalloc(&b->d1, n * sizeof(TcBatchItem)), "cgh_batch_create: items");
+  B_TRY(cudaMalloc(&b->d2, n * sizeof(TcBatchItem)), "cgh_batch_create: items");
+  for (int i = 0; i < n; ++i) {
+    cgh_plan* p = plans[i];
+    b->plans[i] = p;
+    b->I[i] = intensity[i];
+    b->L[i] = layer_idx[i];
+    b->S[i] = saliency[i];
+    b->H[i] = (float2*)holos[i];
+    if ((rc = tc_ensure(p)) != CGH_OK) {
+      cgh_batch_destroy(b);
+      return rc;
+    }
+    B_TRY(cudaMalloc(&b->coeffs[i], (size_t)p->n_layers * p->obj_h * p->obj_w * sizeof(int32_t)),
+          "cgh_batch_create: coefficients");
+    for (int k = 0; k < 4; ++k) {
+      const int lvl = k == 0 ? 3 : k;
+      const size_t cap = (size_t)p->n_layers * (p->obj_h >> lvl) * (p->obj_w >> lvl);
+      B_TRY(cudaMalloc(&b->lists[4 * i + k], cap * sizeof(int32_t)), "cgh_batch_create: lists");
+    }
+  }
+#undef B_TRY
+  if ((rc = batch_upload(b)) != CGH_OK) {
+    cgh_batch_destroy(b);
+    return rc;
+  }
+  (void)stream;
+  *out = b;
+  return CGH_OK;
+}
+
+extern "C" int cgh_batch_set_tuning(cgh_batch* b, int ksteps_per_unit) {
+  if (!b || ksteps_per_unit < 1) return cgh_fail(CGH_ERR_ARG, "cgh_batch_set_tuning: bad argument");
+  cudaDeviceSynchronize();
+  b->ksteps = ksteps_per_unit;
+  return batch_upload(b);
+}
+
+template <bool F16>
+static int batch_run(cgh_batch* b, cudaStream_t st) {
+  for (int i = 0; i < b->n; ++i) {
+    cgh_plan* p = b->plans[i];
+    TC_CK(launch_haar(p, b->I[i], b->L[i], b->coeffs[i], st), "batch: DWT");
+    SelTasks T;
+    memset(&T, 0, sizeof(T));
+    T.n = 4;
+    for (int k = 0; k < 4; ++k) {
+      const int lvl = k == 0 ? CGH_LEVELS : k;
+      T.t[k].level = lvl;
+      T.t[k].threshold = k == 0 ? -1 : b->thr[k - 1];
+      T.t[k].capacity = p->n_layers * (p->obj_h >> lvl) * (p->obj_w >> lvl);
+      T.t[k].list = b->lists[4 * i + k];
+      T.t[k].count = b->counts + 8 * i + 2 * k;
+    }
+    TC_CK(launch_select_tasks(p->obj_h, p->obj_w, p->n_layers, b->S[i], b->L[i], T, p->d_chunk_cnt, p->d_chunk_off,
+                              st),
+          "batch: selection");
+    const int rc = tc_prep<F16>(p, b->coeffs[i], b->lists + 4 * i, b->counts + 8 * i, st);
+    if (rc != CGH_OK) return rc;
+    TC_CK(cudaMemsetAsync(b->H[i], 0, (size_t)p->holo_h * p->holo_w * sizeof(float2), st), "batch: clear");
+  }
+  k_batch_koff<<<(b->n + 127) / 128, 128, 0, st>>>(b->d1, b->d2, b->n);
+  TC_CK(cudaGetLastError(), "batch: offsets");
+  const int sms = tc_num_sms();
+  int* status = b->plans[0]->d_status;
+  k_tc_gemm_batch<KIND_CR, EPI_Y, F16><<<b->units1 < sms ? b->units1 : sms, 192, tc_smem_bytes<KIND_CR>(), st>>>(
+      b->d1, b->n, b->units1, status);
+  TC_CK(cudaGetLastError(), "batch: stage 1");
+  k_tc_gemm_batch<KIND_CC, EPI_H, F16><<<b->units2 < sms ? b->units2 : sms, 192, tc_smem_bytes<KIND_CC>(), st>>>(
+      b->d2, b->n, b->units2, status);
+  TC_CK(cudaGetLastError(), "batch: stage 2");
+  return CGH_OK;
+}
+
+extern "C" int cgh_batch_run(cgh_batch* b, void* stream) {
+  if (!b) return cgh_fail(CGH_ERR_ARG, "cgh_batch_run: batch is NULL");
+  if (b->form == CGH_FORM_TC_FP16X3) return batch_run<true>(b, (cudaStream_t)stream);
+  return batch_run<false>(b, (cudaStream_t)stream);
+}
+
+extern "C" int cgh_batch_lists(const cgh_batch* b, int scene, int32_t** lists, int32_t** d_counts,
+                               int32_t** coeffs) {
+  if (!b || scene < 0 || scene >= b->n || !lists || !d_counts || !coeffs)
+    return cgh_fail(CGH_ERR_ARG, "cgh_batch_lists: bad argument");
+  for (int k = 0; k < 4; ++k) lists[k] = b->lists[4 * scene + k];
+  *d_counts = b->counts + 8 * scene;
+  *coeffs = b->coeffs[scene];
   return CGH_OK;
 }
 

@@ -238,7 +238,7 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
 }
 
 struct TileInfo {
-  int a_row, b_row, k_lo, nk, out_row0, out_col0, n_valid, row_lim, col_lim;
+  int a_row, b_row, k_lo, nk, out_row0, out_col0, n_valid, row_lim, col_lim, item;
 };
 
 // Work unit t of the persistent grid: (mt fastest, then nt, then the layer / K split).
@@ -294,22 +294,17 @@ __device__ __forceinline__ bool decode_tile(const TcGemmArgs& a, int t, const in
 // two accumulator buffers of Re | Im) and one lane issues the MMAs; warps 2-5 drain a
 // finished buffer (TMEM -> registers -> global) while the next tile accumulates in the
 // other buffer.
-template <int KIND, int EPI, bool F16>
-__global__ void __launch_bounds__(192, 1) k_tc_gemm(const __grid_constant__ CUtensorMap mapA,
-                                                     const __grid_constant__ CUtensorMap mapB,
-                                                     const TcGemmArgs args) {
+template <int KIND, int EPI, bool F16, class Src>
+__device__ __forceinline__ void tc_gemm_body(const Src& src, uint8_t* smem, uint64_t* full_bar, uint64_t* empty_bar,
+                                             uint64_t* tfull_bar, uint64_t* tempty_bar, uint64_t* done_bar,
+                                             uint32_t* s_tmem_p, volatile int* s_abort_p) {
   using Cfg = TcCfg<KIND>;
   constexpr int NA = Cfg::NA, NB = Cfg::NB, NST = Cfg::NST;
   constexpr uint32_t STAGE = (NA + NB) * TC_PLANE_BYTES;
-  extern __shared__ uint8_t tc_smem_raw[];
-  uint8_t* smem = (uint8_t*)(((uintptr_t)tc_smem_raw + 1023) & ~(uintptr_t)1023);
-  __shared__ __align__(8) uint64_t full_bar[NST], empty_bar[NST], tfull_bar[2], tempty_bar[2], done_bar;
-  __shared__ uint32_t s_tmem;
-  __shared__ volatile int s_abort;
-  __shared__ int s_off[CGH_MAX_LAYERS + 1];
-
+  volatile int& s_abort = *s_abort_p;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int total = args.tm * args.tn * args.tz;
+  const int total = src.total();
+  int* const status = src.status();
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < NST; ++s) {
@@ -320,25 +315,20 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm(const __grid_constant__ CUte
       mbar_init(&tfull_bar[b], 1);
       mbar_init(&tempty_bar[b], 4);
     }
-    mbar_init(&done_bar, 1);
+    mbar_init(done_bar, 1);
     s_abort = 0;
-    int o = 0;
-    s_off[0] = 0;
-    if (args.kr_pad)
-      for (int q = 0; q < args.n_layers; ++q) s_off[q + 1] = (o += args.kr_pad[q]);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 1) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(smem_u32(&s_tmem))
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(smem_u32(s_tmem_p))
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  const uint32_t tmem = s_tmem;
+  const uint32_t tmem = *s_tmem_p;
   const uint32_t smem_base = smem_u32(smem);
-  const int ktot = args.mode == 2 ? (args.kr_pad ? s_off[args.n_layers] : args.K) : 0;
 
   if (warp == 0) {
     if (lane == 0) {
@@ -350,18 +340,21 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm(const __grid_constant__ CUte
       bool ok = true;
       for (int t = blockIdx.x; t < total && ok; t += gridDim.x) {
         TileInfo ti;
-        if (!decode_tile(args, t, s_off, ktot, ti)) continue;
+        if (!src.decode(t, ti)) continue;
+        const CUtensorMap* mA = src.mapA(ti);
+        const CUtensorMap* mB = src.mapB(ti);
+        src.acquire_maps(mA, mB);
         for (int kt = 0; kt < ti.nk; ++kt, ++it) {
           const int s = it % NST;
           const uint32_t ph = (uint32_t)(it / NST) & 1u;
-          if (!mbar_wait_bounded(&empty_bar[s], ph ^ 1u, &s_abort, args.status)) {
+          if (!mbar_wait_bounded(&empty_bar[s], ph ^ 1u, &s_abort, status)) {
             ok = false;
             break;
           }
           uint8_t* st = smem + s * STAGE;
           mbar_arrive_expect_tx(&full_bar[s], STAGE);
-          tma_load_3d(st, &mapA, &full_bar[s], ti.k_lo + kt * TC_BK, ti.a_row, 0);
-          tma_load_3d(st + NA * TC_PLANE_BYTES, &mapB, &full_bar[s], ti.k_lo + kt * TC_BK, ti.b_row, 0);
+          tma_load_3d(st, mA, &full_bar[s], ti.k_lo + kt * TC_BK, ti.a_row, 0);
+          tma_load_3d(st + NA * TC_PLANE_BYTES, mB, &full_bar[s], ti.k_lo + kt * TC_BK, ti.b_row, 0);
           issued[s] = true;
           issued_ph[s] = ph;
         }
@@ -385,16 +378,16 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm(const __grid_constant__ CUte
       bool ok = true;
       for (int t = blockIdx.x; t < total && ok; t += gridDim.x) {
         TileInfo ti;
-        if (!decode_tile(args, t, s_off, ktot, ti)) continue;
+        if (!src.decode(t, ti)) continue;
         const int buf = local & 1;
         const uint32_t use_ph = (uint32_t)(local >> 1) & 1u;
-        if (!mbar_wait_bounded(&tempty_bar[buf], use_ph ^ 1u, &s_abort, args.status)) break;
+        if (!mbar_wait_bounded(&tempty_bar[buf], use_ph ^ 1u, &s_abort, status)) break;
         tc_fence_after();
         const uint32_t acc = tmem + buf * 256;
         for (int kt = 0; kt < ti.nk; ++kt, ++it) {
           const int s = it % NST;
           const uint32_t ph = (uint32_t)(it / NST) & 1u;
-          if (!mbar_wait_bounded(&full_bar[s], ph, &s_abort, args.status)) {
+          if (!mbar_wait_bounded(&full_bar[s], ph, &s_abort, status)) {
             ok = false;
             break;
           }
@@ -410,9 +403,9 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm(const __grid_constant__ CUte
         ++local;
       }
       // every MMA issued above completes before the accumulators are released
-      mma_commit(&done_bar);
+      mma_commit(done_bar);
       const uint64_t t0 = global_timer();
-      while (!mbar_try_wait(&done_bar, 0) && global_timer() - t0 < TC_WAIT_NS) {
+      while (!mbar_try_wait(done_bar, 0) && global_timer() - t0 < TC_WAIT_NS) {
       }
     }
     __syncwarp();
@@ -422,10 +415,11 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm(const __grid_constant__ CUte
     int local = 0;
     for (int t = blockIdx.x; t < total; t += gridDim.x) {
       TileInfo ti;
-      if (!decode_tile(args, t, s_off, ktot, ti)) continue;
+      if (!src.decode(t, ti)) continue;
+      const TcGemmArgs& args = src.args(ti);
       const int buf = local & 1;
       const uint32_t ph = (uint32_t)(local >> 1) & 1u;
-      bool have = mbar_wait_bounded(&tfull_bar[buf], ph, &s_abort, args.status);
+      bool have = mbar_wait_bounded(&tfull_bar[buf], ph, &s_abort, status);
       have = __all_sync(0xffffffffu, have && !s_abort);  // tcgen05.ld below is warp-collective
       if (!have) break;
       tc_fence_after();
@@ -531,6 +525,113 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm(const __grid_constant__ CUte
   }
 }
 
+// Work units of one problem: tensor maps and arguments in kernel parameters, per-layer K
+// offsets in shared memory.
+struct TcSingleSrc {
+  const CUtensorMap* ma;
+  const CUtensorMap* mb;
+  const TcGemmArgs* a;
+  const int* s_off;
+  int ktot;
+  __device__ int total() const { return a->tm * a->tn * a->tz; }
+  __device__ bool decode(int t, TileInfo& ti) const {
+    ti.item = 0;
+    return decode_tile(*a, t, s_off, ktot, ti);
+  }
+  __device__ const CUtensorMap* mapA(const TileInfo&) const { return ma; }
+  __device__ const CUtensorMap* mapB(const TileInfo&) const { return mb; }
+  __device__ void acquire_maps(const CUtensorMap*, const CUtensorMap*) const {}
+  __device__ const TcGemmArgs& args(const TileInfo&) const { return *a; }
+  __device__ int* status() const { return a->status; }
+};
+
+template <int KIND, int EPI, bool F16>
+__global__ void __launch_bounds__(192, 1) k_tc_gemm(const __grid_constant__ CUtensorMap mapA,
+                                                     const __grid_constant__ CUtensorMap mapB,
+                                                     const TcGemmArgs args) {
+  constexpr int NST = TcCfg<KIND>::NST;
+  extern __shared__ uint8_t tc_smem_raw[];
+  uint8_t* smem = (uint8_t*)(((uintptr_t)tc_smem_raw + 1023) & ~(uintptr_t)1023);
+  __shared__ __align__(8) uint64_t full_bar[NST], empty_bar[NST], tfull_bar[2], tempty_bar[2], done_bar;
+  __shared__ uint32_t s_tmem;
+  __shared__ volatile int s_abort;
+  __shared__ int s_off[CGH_MAX_LAYERS + 1];
+  if (threadIdx.x == 0) {
+    int o = 0;
+    s_off[0] = 0;
+    if (args.kr_pad)
+      for (int q = 0; q < args.n_layers; ++q) s_off[q + 1] = (o += args.kr_pad[q]);
+  }
+  __syncthreads();
+  TcSingleSrc src{&mapA, &mapB, &args, s_off,
+                  args.mode == 2 ? (args.kr_pad ? s_off[args.n_layers] : args.K) : 0};
+  tc_gemm_body<KIND, EPI, F16>(src, smem, full_bar, empty_bar, tfull_bar, tempty_bar, &done_bar, &s_tmem,
+                               &s_abort);
+}
+
+// One problem of a batch, in global memory: its tensor maps, arguments, first work unit
+// and per-layer K offsets (filled on the device once the compaction has run).
+struct alignas(128) TcBatchItem {
+  CUtensorMap ma;
+  CUtensorMap mb;
+  TcGemmArgs a;
+  int unit0;
+  int koff[CGH_MAX_LAYERS + 1];
+};
+
+// Work units of many problems: unit t belongs to the last item whose first unit is <= t.
+struct TcBatchSrc {
+  const TcBatchItem* items;
+  const int* s_unit0;
+  int n, tot;
+  int* st;
+  __device__ int total() const { return tot; }
+  __device__ bool decode(int t, TileInfo& ti) const {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (s_unit0[mid] <= t)
+        lo = mid;
+      else
+        hi = mid - 1;
+    }
+    ti.item = lo;
+    const TcBatchItem& it = items[lo];
+    const int ktot = it.a.mode == 2 ? (it.a.kr_pad ? it.koff[it.a.n_layers] : it.a.K) : 0;
+    return decode_tile(it.a, t - s_unit0[lo], it.koff, ktot, ti);
+  }
+  __device__ const CUtensorMap* mapA(const TileInfo& ti) const { return &items[ti.item].ma; }
+  __device__ const CUtensorMap* mapB(const TileInfo& ti) const { return &items[ti.item].mb; }
+  __device__ void acquire_maps(const CUtensorMap* a, const CUtensorMap* b) const {
+    // tensor maps written to global memory by a copy before the launch
+    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(reinterpret_cast<uint64_t>(a))
+                 : "memory");
+    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(reinterpret_cast<uint64_t>(b))
+                 : "memory");
+  }
+  __device__ const TcGemmArgs& args(const TileInfo& ti) const { return items[ti.item].a; }
+  __device__ int* status() const { return st; }
+};
+
+#define TC_BATCH_MAX 1024
+
+template <int KIND, int EPI, bool F16>
+__global__ void __launch_bounds__(192, 1) k_tc_gemm_batch(const TcBatchItem* __restrict__ items, int n,
+                                                           int total, int* status) {
+  constexpr int NST = TcCfg<KIND>::NST;
+  extern __shared__ uint8_t tc_smem_raw[];
+  uint8_t* smem = (uint8_t*)(((uintptr_t)tc_smem_raw + 1023) & ~(uintptr_t)1023);
+  __shared__ __align__(8) uint64_t full_bar[NST], empty_bar[NST], tfull_bar[2], tempty_bar[2], done_bar;
+  __shared__ uint32_t s_tmem;
+  __shared__ volatile int s_abort;
+  __shared__ int s_unit0[TC_BATCH_MAX];
+  for (int i = threadIdx.x; i < n; i += blockDim.x) s_unit0[i] = items[i].unit0;
+  __syncthreads();
+  TcBatchSrc src{items, s_unit0, n, total, status};
+  tc_gemm_body<KIND, EPI, F16>(src, smem, full_bar, empty_bar, tfull_bar, tempty_bar, &done_bar, &s_tmem,
+                               &s_abort);
+}
+
 // ------------------------------------------------------------------------------------
 // host helpers
 
@@ -580,7 +681,10 @@ static int make_plane_map(CUtensorMap* map, const void* base, int planes, long l
 
 template <int KIND, int EPI, bool F16>
 static cudaError_t set_gemm_attr() {
-  return cudaFuncSetAttribute(k_tc_gemm<KIND, EPI, F16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaError_t e = cudaFuncSetAttribute(k_tc_gemm<KIND, EPI, F16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)tc_smem_bytes<KIND>());
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_tc_gemm_batch<KIND, EPI, F16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)tc_smem_bytes<KIND>());
 }
 
