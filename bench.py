@@ -168,6 +168,127 @@ def cpu_baseline(budget_s=12.0):
 
 
 # ---------------------------------------------------------------------------------------
+# secondary workloads (reported as fields of the same JSON line)
+
+
+def run_batch_workload(stream, form, count, reps):
+    """64 scenes of uneven size (object edge in {128,256,512,1024}, hologram 2x, 4..32
+    layers, ellipse saliency covering 5-60%) as one graph-captured batch."""
+    import torch
+    from paper_2211_09938_gb300 import Plan, autotune
+    from paper_2211_09938_gb300.cgh import Batch
+    from synth import scenes
+    scs = scenes.batch_scenes(seed=4000, count=count)
+    with torch.cuda.stream(stream):
+        plans = [Plan.for_scene(sc, stream=stream) for sc in scs]
+        I = [torch.from_numpy(sc["intensity"]).cuda() for sc in scs]
+        L = [torch.from_numpy(sc["layer"]).cuda() for sc in scs]
+        S = [torch.from_numpy(sc["saliency"]).cuda() for sc in scs]
+        Hs = [torch.empty(sc["holo"], dtype=torch.complex64, device="cuda") for sc in scs]
+        batch = Batch(plans, I, L, S, scenes.THRESHOLDS_U8, Hs, form=form, stream=stream)
+    cache = os.path.join(ROOT, "paper_2211_09938_gb300", "_build", "autotune.json")
+    os.makedirs(os.path.dirname(cache), exist_ok=True)
+    tuned = autotune.tune_batch(batch, plans, form, stream, cache_path=cache)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=stream):
+        batch.run(stream=stream)
+    for _ in range(3):
+        with torch.cuda.stream(stream):
+            g.replay()
+    stream.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+    with torch.cuda.stream(stream):
+        for a, b in evs:
+            a.record(stream)
+            g.replay()
+            b.record(stream)
+    torch.cuda.synchronize()
+    ms = sorted(a.elapsed_time(b) for a, b in evs)[reps // 2]
+    work = sum(sc["intensity"].size * sc["holo"][0] * sc["holo"][1] for sc in scs)
+    # per-scene latency: each scene alone as its own captured graph
+    lat = []
+    for k, sc in enumerate(scs):
+        with torch.cuda.stream(stream):
+            coeffs = torch.empty((len(sc["z"]),) + sc["intensity"].shape, dtype=torch.int32, device="cuda")
+            counts = torch.zeros((4, 2), dtype=torch.int32, device="cuda")
+            lists = [torch.empty(plans[k].max_blocks(3 if q == 0 else q), dtype=torch.int32, device="cuda")
+                     for q in range(4)]
+
+            def one():
+                plans[k].haar_decompose(I[k], L[k], coeffs, stream=stream)
+                plans[k].progressive_lists(S[k], L[k], scenes.THRESHOLDS_U8, counts=counts, lists=lists,
+                                           stream=stream)
+                plans[k].progressive_hologram(coeffs, lists, counts, holo=Hs[k], form=form, stream=stream)
+            one()
+        stream.synchronize()
+        gk = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(gk, stream=stream):
+            one()
+        t = []
+        for _ in range(5):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            with torch.cuda.stream(stream):
+                a.record(stream)
+                gk.replay()
+                b.record(stream)
+            torch.cuda.synchronize()
+            t.append(a.elapsed_time(b))
+        lat.append(sorted(t)[2])
+        del gk
+    lat = sorted(lat)
+    batch.close()
+    for p_ in plans:
+        p_.close()
+    return {"scenes": count, "form": form, "ms_per_batch": ms, "scenes_per_s": count / (ms / 1e3),
+            "gpoint_px_per_s": work / (ms / 1e3) / 1e9,
+            "latency_ms_p50": lat[len(lat) // 2], "latency_ms_p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
+            "latency_note": "each scene alone as a captured graph (DWT, selection, superposition)",
+            "autotuned_ksteps_per_unit": tuned["ksteps"],
+            "sizes": sorted(set(sc["intensity"].shape[0] for sc in scs))}
+
+
+def run_phase_opt_workload(stream, steps):
+    """Phase-only optimisation: batch 4, hologram 1024^2, 8 layers, 512^2 blob target, loss
+    weight 4 inside the saliency mask; phase initialised to arg of the progressive hologram."""
+    import numpy as np
+    import torch
+    from paper_2211_09938_gb300 import Plan, optim
+    from synth import scenes
+    sc = scenes.random_scene(5000, 512, 1024, 8, sal_fraction=0.3)
+    with torch.cuda.stream(stream):
+        plan = Plan.for_scene(sc, stream=stream)
+        L = torch.from_numpy(sc["layer"]).cuda()
+        W = torch.from_numpy(np.where(sc["saliency"] > 0, 4.0, 1.0).astype(np.float32)).cuda()
+        targets, phases = [], []
+        for b in range(4):
+            t = scenes.random_scene(5000 + b, 512, 1024, 8)["intensity"].astype(np.float32) / 255.0
+            targets.append(torch.from_numpy(t).cuda())
+            I = torch.from_numpy((t * 255).astype(np.uint8)).cuda()
+            S = torch.from_numpy(sc["saliency"]).cuda()
+            coeffs = plan.haar_decompose(I, L, stream=stream)
+            lists, counts = plan.progressive_lists(S, L, scenes.THRESHOLDS_U8, stream=stream)
+            H = plan.progressive_hologram(coeffs, lists, counts, form="tc_bf16x3", stream=stream)
+            phases.append(torch.angle(H))
+        T = torch.stack(targets)
+        opt = optim.PhaseOptimiser(plan, L, T, W, torch.stack(phases), lr=0.05, checkpoint=True)
+        l0 = opt.step()
+    stream.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        a.record(stream)
+        for _ in range(steps):
+            l1 = opt.step()
+        b.record(stream)
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / steps
+    plan.close()
+    return {"batch": 4, "holo": 1024, "layers": 8, "adam_steps_timed": steps, "ms_per_adam_step": ms,
+            "adam_steps_per_s": 1e3 / ms, "loss_first": l0, "loss_last": l1,
+            "note": "forward reconstruction + amplitude backward + propagation per hologram, fields recomputed "
+                    "in backward (checkpointing)"}
+
+
+# ---------------------------------------------------------------------------------------
 # our arm
 
 
@@ -353,6 +474,11 @@ def run_ours(args):
         "gpu_launches": launches_per_step * args.steps, "wall_s_timed_region": wall,
     }
     line["stages_ms"] = stages
+    if rank == 0 and ws == 1 and not args.skip_batch:
+        line["batch"] = run_batch_workload(stream, form if form != "direct_lut" else "tc_bf16x3",
+                                           args.batch_scenes, 10)
+    if rank == 0 and ws == 1 and not args.skip_phase_opt:
+        line["phase_opt"] = run_phase_opt_workload(stream, args.phase_opt_steps)
     if plain is not None:
         line["plain_direct"] = plain
     # the other superposition forms on the same scene (device ms of the superposition call)
@@ -397,6 +523,10 @@ def main():
     ap.add_argument("--form", default="tc_bf16x3", choices=["direct_lut", "tc_bf16x3", "tc_fp16x3"])
     ap.add_argument("--skip-forms", action="store_true")
     ap.add_argument("--no-graph", action="store_true", help="launch the step eagerly instead of as a CUDA graph")
+    ap.add_argument("--skip-batch", action="store_true", help="skip the 64-scene batch measurement")
+    ap.add_argument("--batch-scenes", type=int, default=64)
+    ap.add_argument("--skip-phase-opt", action="store_true", help="skip the phase-optimisation measurement")
+    ap.add_argument("--phase-opt-steps", type=int, default=5)
     ap.add_argument("--skip-plain", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

@@ -38,6 +38,7 @@ SIGNATURES = {
     "cgh_plan_create": (_I, [ctypes.POINTER(_P), _I, _I, _I, _I, _D, _D, _I,
                              ctypes.POINTER(_D), _I, _I, _P]),
     "cgh_plan_destroy": (_I, [_P]),
+    "cgh_plan_set_tuning": (_I, [_P, _I]),
     "cgh_build_tables": (_I, [_P, _P]),
     "cgh_haar_decompose": (_I, [_P, _P, _P, _P, _P]),
     "cgh_select_blocks": (_I, [_P, _P, _P, _I, _I, _P, _P, _I, _P]),
@@ -144,6 +145,9 @@ class Plan:
             pass
 
     # ---- C calls -------------------------------------------------------------------
+    def set_tuning(self, max_ksteps_per_chain):
+        check(lib().cgh_plan_set_tuning(self.handle, int(max_ksteps_per_chain)))
+
     def build_tables(self, stream=None):
         check(lib().cgh_build_tables(self.handle, _stream(stream)))
 

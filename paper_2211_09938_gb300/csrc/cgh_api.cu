@@ -57,6 +57,12 @@ int cgh_plan_destroy(cgh_plan* p) {
   return CGH_OK;
 }
 
+int cgh_plan_set_tuning(cgh_plan* p, int max_ksteps) {
+  if (!p || max_ksteps < 0) return cgh_fail(CGH_ERR_ARG, "cgh_plan_set_tuning: bad argument");
+  p->max_ksteps = max_ksteps;
+  return CGH_OK;
+}
+
 int cgh_build_tables(cgh_plan* p, void* stream) {
   if (!p) return cgh_fail(CGH_ERR_ARG, "cgh_build_tables: plan is NULL");
   prof_mark(p, CGH_PROF_TABLES, 0, (cudaStream_t)stream);

@@ -423,7 +423,14 @@ static int tc_run(const cgh_plan* p, const int32_t* coef, const int32_t* const* 
   TC_CK(e, "tc: stage-1 GEMM");
   if (!accumulate) TC_CK(cudaMemsetAsync(holo, 0, (size_t)p->holo_h * p->holo_w * sizeof(float2), st), "tc: clear");
   const int tm = (p->holo_h + TC_BM - 1) / TC_BM, tn = (p->holo_w + TC_BN - 1) / TC_BN;
-  const int S = p->deterministic ? 1 : stage2_splits(tm * tn, t->ktot_alloc / TC_BK);
+  int S = p->deterministic ? 1 : stage2_splits(tm * tn, t->ktot_alloc / TC_BK);
+  if (!p->deterministic && p->max_ksteps > 0) {
+    // cap the chain length on the actual K: sum of the layers' compacted rows is at most
+    // the allocation, so bound it by the allocation's K steps scaled to the occupancy seen
+    const int kst = t->ktot_alloc / TC_BK;
+    const int need = (kst + p->max_ksteps - 1) / p->max_ksteps;
+    if (need > S) S = need;
+  }
   stage2_args(p, F16, holo, S, a, tiles);
   prof_mark(p, CGH_PROF_TC_STAGE2, 0, st);
   e = launch_gemm<KIND_CC, EPI_H, F16>(t->mA2, t->mY, a, tiles, st);
