@@ -46,6 +46,7 @@ int cgh_plan_destroy(cgh_plan* p) {
     }
   tc_destroy(p);
   field_destroy(p);
+  eops_destroy(p);
   cudaFree(p->d_tab);
   cudaFree(p->d_f64);
   cudaFree(p->d_a_frac);

@@ -42,6 +42,8 @@ struct cgh_plan {
   struct cgh_tc_state* tc;
   // Reconstruction / propagation operands and scratch (allocated lazily).
   struct cgh_field_state* fs;
+  // Fringe operand planes E_z by rows / columns, per dtype (allocated lazily).
+  struct cgh_eops* eops;
 
   // CUDA-event profiling of the internal stages (cgh_profile).
   int prof_on;
@@ -117,3 +119,7 @@ int field_adjoint(const cgh_plan* p, const float2* grad_holo, const int32_t* con
 int field_amplitude_backward(const cgh_plan* p, const float2* fields, const uint8_t* L, const float* grad_amp,
                              float2* grad_fields, cudaStream_t st);
 void field_destroy(cgh_plan* p);
+struct CUtensorMap_st;
+int eops_get(const cgh_plan* p, int f16, const struct CUtensorMap_st** mEZ, const struct CUtensorMap_st** mEZt,
+             cudaStream_t st);
+void eops_destroy(cgh_plan* p);

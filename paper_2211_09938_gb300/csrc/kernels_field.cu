@@ -14,13 +14,13 @@
 // ------------------------------------------------------------------------------------
 // operand builders
 
-// Fringe planes out[p][r][c], 8 columns per thread (C a multiple of 8):
-//   MODE 0 (conj rows):  r = z*No + i, c = m   -> conj(f_z(m - s*i))
-//   MODE 1 (E by m):     r = m,        c = z*No + i -> f_z(m - s*i)
-//   MODE 2 (E by n):     r = z*Nh + n, c = j   -> f_z(n - s*j)
-template <int MODE>
-__global__ void k_fe_build(const float2* __restrict__ tab, int tab_len, int tab_off, int s, int No, int Nh,
-                           int R, int C, uint16_t* __restrict__ out, long long plane) {
+// Fringe planes out[p][r][c], 8 columns per thread (C a multiple of 8), hi+lo in bf16 or fp16:
+//   MODE 0 (conj rows):  r = z*div + i, c = m         -> conj(f_z(m - s*i))   (div = obj edge)
+//   MODE 1 (E by m):     r = m,         c = z*div + i -> f_z(m - s*i)         (div = obj_h)
+//   MODE 2 (E by n):     r = z*div + n, c = j         -> f_z(n - s*j)         (div = holo_w)
+template <int MODE, bool F16>
+__global__ void k_fe_build(const float2* __restrict__ tab, int tab_len, int tab_off, int s, int div, int R, int C,
+                           uint16_t* __restrict__ out, long long plane) {
   const int c = 8 * (blockIdx.x * blockDim.x + threadIdx.x);
   const int r = blockIdx.y * blockDim.y + threadIdx.y;
   if (r >= R || c >= C) return;
@@ -32,23 +32,20 @@ __global__ void k_fe_build(const float2* __restrict__ tab, int tab_len, int tab_
     for (int u = 0; u < 2; ++u) {
       const int cc = c + q + u;
       int z, d;
-      bool ok = true;
       if (MODE == 0) {
-        z = r / No;
-        d = cc - s * (r - z * No);
-        ok = cc < Nh;
+        z = r / div;
+        d = cc - s * (r - z * div);
       } else if (MODE == 1) {
-        z = cc / No;
-        d = r - s * (cc - z * No);
+        z = cc / div;
+        d = r - s * (cc - z * div);
       } else {
-        z = r / Nh;
-        d = (r - z * Nh) - s * cc;
-        ok = cc < No;
+        z = r / div;
+        d = (r - z * div) - s * cc;
       }
-      float2 v = ok ? tab[(size_t)(z * 4 + 0) * 2 * tab_len + tab_off + d] : make_float2(0.f, 0.f);
+      float2 v = tab[(size_t)(z * 4 + 0) * 2 * tab_len + tab_off + d];
       if (MODE == 0) v.y = -v.y;
-      split_hi_lo<false>(v.x, h[u][0], h[u][1]);
-      split_hi_lo<false>(v.y, h[u][2], h[u][3]);
+      split_hi_lo<F16>(v.x, h[u][0], h[u][1]);
+      split_hi_lo<F16>(v.y, h[u][2], h[u][3]);
     }
 #pragma unroll
     for (int p = 0; p < 4; ++p) w[p][q / 2] = (uint32_t)h[0][p] | ((uint32_t)h[1][p] << 16);
@@ -235,13 +232,80 @@ __global__ void k_phase_grad(const float2* __restrict__ field, const float2* __r
 // ------------------------------------------------------------------------------------
 // host side
 
+// Geometry operands shared by the progressive tensor form and the field stages, built once
+// per plan and dtype: EZ[p][m][z*obj_h + i] = f_z(m - s*i) and EZt[p][z*holo_w + n][j] =
+// f_z(n - s*j) as hi+lo planes (index 0 bf16, 1 fp16).
+struct cgh_eops {
+  int built[2];
+  uint16_t* EZ[2];
+  uint16_t* EZt[2];
+  long long ez_plane, ezt_plane;
+  CUtensorMap mEZ[2], mEZt[2];
+};
+
+void eops_destroy(cgh_plan* p) {
+  cgh_eops* e = p->eops;
+  if (!e) return;
+  for (int k = 0; k < 2; ++k) {
+    cudaFree(e->EZ[k]);
+    cudaFree(e->EZt[k]);
+  }
+  free(e);
+  p->eops = nullptr;
+}
+
+int eops_get(const cgh_plan* pc, int f16, const CUtensorMap** mEZ, const CUtensorMap** mEZt, cudaStream_t st) {
+  cgh_plan* p = const_cast<cgh_plan*>(pc);
+  if (!p->eops) {
+    p->eops = (cgh_eops*)calloc(1, sizeof(cgh_eops));
+    if (!p->eops) return cgh_fail(CGH_ERR_NOMEM, "fringe operands: host allocation");
+    p->eops->ez_plane = (long long)p->holo_h * p->n_layers * p->obj_h;
+    p->eops->ezt_plane = (long long)p->n_layers * p->holo_w * p->obj_w;
+  }
+  cgh_eops* e = p->eops;
+  const int k = f16 ? 1 : 0;
+  if (!e->built[k]) {
+    const int Z = p->n_layers;
+    int rc = cgh_cuda_check(cudaMalloc(&e->EZ[k], 4 * e->ez_plane * 2), "fringe operands: EZ");
+    if (rc == CGH_OK) rc = cgh_cuda_check(cudaMalloc(&e->EZt[k], 4 * e->ezt_plane * 2), "fringe operands: EZt");
+    if (rc == CGH_OK) rc = make_plane_map(&e->mEZ[k], e->EZ[k], 4, p->holo_h, (long long)Z * p->obj_h);
+    if (rc == CGH_OK) rc = make_plane_map(&e->mEZt[k], e->EZt[k], 4, (long long)Z * p->holo_w, p->obj_w);
+    if (rc != CGH_OK) {
+      cudaFree(e->EZ[k]);
+      cudaFree(e->EZt[k]);
+      e->EZ[k] = e->EZt[k] = nullptr;
+      return rc;
+    }
+    dim3 blk(8, 32);
+    const int C1 = Z * p->obj_h, R2 = Z * p->holo_w;
+    if (f16) {
+      k_fe_build<1, true><<<dim3((C1 / 8 + 7) / 8, (p->holo_h + 31) / 32), blk, 0, st>>>(
+          p->d_tab, p->tab_len, p->tab_off, p->s, p->obj_h, p->holo_h, C1, e->EZ[k], e->ez_plane);
+      k_fe_build<2, true><<<dim3((p->obj_w / 8 + 7) / 8, (R2 + 31) / 32), blk, 0, st>>>(
+          p->d_tab, p->tab_len, p->tab_off, p->s, p->holo_w, R2, p->obj_w, e->EZt[k], e->ezt_plane);
+    } else {
+      k_fe_build<1, false><<<dim3((C1 / 8 + 7) / 8, (p->holo_h + 31) / 32), blk, 0, st>>>(
+          p->d_tab, p->tab_len, p->tab_off, p->s, p->obj_h, p->holo_h, C1, e->EZ[k], e->ez_plane);
+      k_fe_build<2, false><<<dim3((p->obj_w / 8 + 7) / 8, (R2 + 31) / 32), blk, 0, st>>>(
+          p->d_tab, p->tab_len, p->tab_off, p->s, p->holo_w, R2, p->obj_w, e->EZt[k], e->ezt_plane);
+    }
+    rc = cgh_cuda_check(cudaGetLastError(), "fringe operands: build");
+    if (rc != CGH_OK) return rc;
+    e->built[k] = 1;
+  }
+  if (mEZ) *mEZ = &e->mEZ[k];
+  if (mEZt) *mEZt = &e->mEZt[k];
+  return CGH_OK;
+}
+
 struct cgh_field_state {
   int No, Nh, Z;
-  uint16_t *GZ, *EZ, *EZt;   // geometry operands (built once)
+  uint16_t* GZ;                // conj(E_z) by rows i (built once)
   uint16_t *Ht, *T, *Fp, *Yp;  // data planes
   float2* F;                   // fields scratch [Z][No][No]
-  long long gz_plane, ez_plane, ezt_plane, ht_plane, t_plane, fp_plane, yp_plane;
-  CUtensorMap mGZ, mEZ, mEZt, mHt, mT, mFp, mYp;
+  long long gz_plane, ht_plane, t_plane, fp_plane, yp_plane;
+  CUtensorMap mGZ, mHt, mT, mFp, mYp;
+  const CUtensorMap *mEZ, *mEZt;  // bf16 geometry operands (cgh_eops)
   int built;
 };
 
@@ -258,8 +322,6 @@ void field_destroy(cgh_plan* p) {
   cgh_field_state* f = p->fs;
   if (!f) return;
   cudaFree(f->GZ);
-  cudaFree(f->EZ);
-  cudaFree(f->EZt);
   cudaFree(f->Ht);
   cudaFree(f->T);
   cudaFree(f->Fp);
@@ -276,28 +338,27 @@ static int field_ensure(const cgh_plan* pc, cudaStream_t st) {
     return cgh_fail(CGH_ERR_UNSUPPORTED, "fields: square object and hologram required");
   const int No = p->obj_h, Nh = p->holo_h, Z = p->n_layers;
   if (No % 32) return cgh_fail(CGH_ERR_UNSUPPORTED, "fields: object edge must be a multiple of 32");
+  int rc = eops_get(p, 0, nullptr, nullptr, st);
+  if (rc != CGH_OK) return rc;
   cgh_field_state* f = p->fs ? p->fs : (cgh_field_state*)calloc(1, sizeof(cgh_field_state));
   if (!f) return cgh_fail(CGH_ERR_NOMEM, "fields: host allocation");
   p->fs = f;
   f->No = No;
   f->Nh = Nh;
   f->Z = Z;
+  f->mEZ = &p->eops->mEZ[0];
+  f->mEZt = &p->eops->mEZt[0];
   f->gz_plane = (long long)Z * No * Nh;
-  f->ez_plane = (long long)Nh * Z * No;
-  f->ezt_plane = (long long)Z * Nh * No;
   f->ht_plane = (long long)Nh * Nh;
   f->t_plane = (long long)Z * No * Nh;
   f->fp_plane = (long long)Z * No * No;
   f->yp_plane = (long long)Nh * Z * No;
-  int rc;
 #define FS_TRY(expr, what)                     \
   do {                                         \
     rc = cgh_cuda_check((expr), (what));       \
     if (rc != CGH_OK) goto fail;               \
   } while (0)
   FS_TRY(cudaMalloc(&f->GZ, 4 * f->gz_plane * 2), "fields: GZ");
-  FS_TRY(cudaMalloc(&f->EZ, 4 * f->ez_plane * 2), "fields: EZ");
-  FS_TRY(cudaMalloc(&f->EZt, 4 * f->ezt_plane * 2), "fields: EZt");
   FS_TRY(cudaMalloc(&f->Ht, 4 * f->ht_plane * 2), "fields: Ht");
   FS_TRY(cudaMalloc(&f->T, 4 * f->t_plane * 2), "fields: T");
   FS_TRY(cudaMalloc(&f->Fp, 4 * f->fp_plane * 2), "fields: Fp");
@@ -305,20 +366,14 @@ static int field_ensure(const cgh_plan* pc, cudaStream_t st) {
   FS_TRY(cudaMalloc(&f->F, (size_t)Z * No * No * sizeof(float2)), "fields: F");
 #undef FS_TRY
   if ((rc = make_plane_map(&f->mGZ, f->GZ, 4, (long long)Z * No, Nh)) != CGH_OK) goto fail;
-  if ((rc = make_plane_map(&f->mEZ, f->EZ, 4, Nh, (long long)Z * No)) != CGH_OK) goto fail;
-  if ((rc = make_plane_map(&f->mEZt, f->EZt, 4, (long long)Z * Nh, No)) != CGH_OK) goto fail;
   if ((rc = make_plane_map(&f->mHt, f->Ht, 4, Nh, Nh)) != CGH_OK) goto fail;
   if ((rc = make_plane_map(&f->mT, f->T, 4, (long long)Z * No, Nh)) != CGH_OK) goto fail;
   if ((rc = make_plane_map(&f->mFp, f->Fp, 4, (long long)Z * No, No)) != CGH_OK) goto fail;
   if ((rc = make_plane_map(&f->mYp, f->Yp, 4, Nh, (long long)Z * No)) != CGH_OK) goto fail;
   {
     dim3 blk(8, 32);
-    k_fe_build<0><<<dim3((Nh / 8 + 7) / 8, (Z * No + 31) / 32), blk, 0, st>>>(
-        p->d_tab, p->tab_len, p->tab_off, p->s, No, Nh, Z * No, Nh, f->GZ, f->gz_plane);
-    k_fe_build<1><<<dim3((Z * No / 8 + 7) / 8, (Nh + 31) / 32), blk, 0, st>>>(
-        p->d_tab, p->tab_len, p->tab_off, p->s, No, Nh, Nh, Z * No, f->EZ, f->ez_plane);
-    k_fe_build<2><<<dim3((No / 8 + 7) / 8, (Z * Nh + 31) / 32), blk, 0, st>>>(
-        p->d_tab, p->tab_len, p->tab_off, p->s, No, Nh, Z * Nh, No, f->EZt, f->ezt_plane);
+    k_fe_build<0, false><<<dim3((Nh / 8 + 7) / 8, (Z * No + 31) / 32), blk, 0, st>>>(
+        p->d_tab, p->tab_len, p->tab_off, p->s, No, Z * No, Nh, f->GZ, f->gz_plane);
     rc = cgh_cuda_check(cudaGetLastError(), "fields: operand build");
     if (rc != CGH_OK) goto fail;
   }
@@ -398,7 +453,7 @@ int field_propagate(const cgh_plan* p, const float2* fields, float2* holo, int a
   a.Y = f->Yp;
   a.y_plane = f->yp_plane;
   a.ldy = Z * No;
-  rc = cgh_cuda_check(launch_gemm<KIND_CC, EPI_Y, false>(f->mEZt, f->mFp, a,
+  rc = cgh_cuda_check(launch_gemm<KIND_CC, EPI_Y, false>(*f->mEZt, f->mFp, a,
                                                          dim3((Nh + 127) / 128, (No + 127) / 128, Z), st),
                       "propagate: P1");
   if (rc != CGH_OK) return rc;
@@ -433,7 +488,7 @@ int field_propagate(const cgh_plan* p, const float2* fields, float2* holo, int a
       if (eff > best + 1e-9) best = eff, S = q;
     }
   }
-  rc = cgh_cuda_check(launch_gemm<KIND_CC, EPI_H, false>(f->mEZ, f->mYp, b, dim3(tm, tm, S), st), "propagate: P2");
+  rc = cgh_cuda_check(launch_gemm<KIND_CC, EPI_H, false>(*f->mEZ, f->mYp, b, dim3(tm, tm, S), st), "propagate: P2");
   prof_mark(p, CGH_PROF_PROPAGATE, 1, st);
   return rc;
 }

@@ -65,27 +65,48 @@ __device__ int block_scan_flags(int f, int* s_warp, int* total) {
   return r;
 }
 
-// Per layer: compacted object rows / columns (8-pixel bands of the layer's LLL blocks),
-// padded with -1 to a multiple of 32.
+// Per layer: compacted object rows / columns in 32-pixel bands (a band is kept when one
+// of the layer's LLL blocks lies in it), entries past the object edge set to -1.  Also the
+// band index of every 32-wide K step: stage-1 A reads fringe columns 32*band directly.
 __global__ void __launch_bounds__(1024) k_tc_compact(TcFlags fl, int H, int W, int* __restrict__ rows,
                                                      int* __restrict__ cols, int* __restrict__ kr_pad,
-                                                     int* __restrict__ kc_pad, int ld_rows, int ld_cols) {
+                                                     int* __restrict__ kc_pad, int ld_rows, int ld_cols,
+                                                     int* __restrict__ rband, int* __restrict__ cband) {
   __shared__ int s_warp[33];
   const int z = blockIdx.x, t = threadIdx.x;
   for (int axis = 0; axis < 2; ++axis) {
-    const int nb = axis == 0 ? (H >> 3) : (W >> 3);
+    const int n8 = axis == 0 ? (H >> 3) : (W >> 3);
+    const int n32 = (n8 + 3) >> 2;
+    const int lim = axis == 0 ? H : W;
     const uint8_t* band = axis == 0 ? fl.rowband + (size_t)z * (H >> 3) : fl.colband + (size_t)z * (W >> 3);
     int* out = axis == 0 ? rows + (size_t)z * ld_rows : cols + (size_t)z * ld_cols;
-    const int f = t < nb ? band[t] : 0;
+    int* bout = axis == 0 ? rband + (size_t)z * (ld_rows / 32) : cband + (size_t)z * (ld_cols / 32);
+    int f = 0;
+    if (t < n32)
+      for (int q = 4 * t; q < 4 * t + 4 && q < n8; ++q) f |= band[q];
     int total;
-    const int r = block_scan_flags(f, s_warp, &total);
-    if (f)
-      for (int q = 0; q < 8; ++q) out[8 * r + q] = 8 * t + q;
-    const int cnt = 8 * total, pad = (cnt + 31) & ~31;
-    if (t < pad - cnt) out[cnt + t] = -1;
-    if (t == 0) (axis == 0 ? kr_pad : kc_pad)[z] = pad;
+    const int r = block_scan_flags(f ? 1 : 0, s_warp, &total);
+    if (f) {
+      for (int q = 0; q < 32; ++q) {
+        const int v = 32 * t + q;
+        out[32 * r + q] = v < lim ? v : -1;
+      }
+      bout[r] = axis == 0 ? t : 32 * t;
+    }
+    if (t == 0) (axis == 0 ? kr_pad : kc_pad)[z] = 32 * total;
     __syncthreads();
   }
+}
+
+// Stage-2 A coordinate of every 32-wide K step of the concatenated layers: the fringe
+// column z*H + 32*band of the layer's compacted row band.
+__global__ void k_tc_kmap2(const int* __restrict__ kr_pad, const int* __restrict__ rband, int ld_band, int H, int Z,
+                           int* __restrict__ kmap2) {
+  const int z = blockIdx.x;
+  int off = 0;
+  for (int q = 0; q < z; ++q) off += kr_pad[q];
+  const int n = kr_pad[z] / 32;
+  for (int k = threadIdx.x; k < n; k += blockDim.x) kmap2[off / 32 + k] = z * H + 32 * rband[(size_t)z * ld_band + k];
 }
 
 // 64 x A^_z at (rows[k], cols[c]) from the Haar coefficients and the selection flags:
@@ -171,50 +192,6 @@ __global__ void k_tc_idwt(const int32_t* __restrict__ coef, TcFlags fl, const in
   *reinterpret_cast<uint4*>(dst + b1_plane) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
 }
 
-// E operand planes: out[p][z*rows_per_z + r][c] = split(f_z(r - s*idx[z][c])) for c below the
-// layer's padded count (idx < 0: zero).  stage 1: idx = columns, rows = hologram width;
-// stage 2 (z_off_from_counts): column index off_z + c, rows = hologram height, z block 0.
-template <bool F16>
-__global__ void k_tc_gather_e(const float2* __restrict__ tab, int tab_len, int tab_off, int s,
-                              const int* __restrict__ idx, int ld_idx, const int* __restrict__ cnt_pad,
-                              int rows_out, int stage2, uint16_t* __restrict__ E, long long e_plane, int lde) {
-  // one thread: 8 consecutive columns (padded counts are multiples of 32), 16-byte stores
-  const int z = blockIdx.z;
-  const int c = 8 * (blockIdx.x * blockDim.x + threadIdx.x);
-  const int r = blockIdx.y * blockDim.y + threadIdx.y;
-  if (r >= rows_out || c >= cnt_pad[z]) return;
-  int col = c;
-  size_t row = (size_t)z * rows_out + r;
-  if (stage2) {
-    int off = 0;
-    for (int q = 0; q < z; ++q) off += cnt_pad[q];
-    col = off + c;
-    row = r;
-  }
-  const float2* T = tab + (size_t)(z * 4 + 0) * 2 * tab_len + tab_off + r;
-  uint32_t w[4][4];
-#pragma unroll
-  for (int q = 0; q < 8; q += 2) {
-    uint16_t h[2][4];
-#pragma unroll
-    for (int u = 0; u < 2; ++u) {
-      const int i = idx[(size_t)z * ld_idx + c + q + u];
-      const float2 v = i >= 0 ? T[-s * i] : make_float2(0.f, 0.f);
-      split_hi_lo<F16>(v.x, h[u][0], h[u][1]);
-      split_hi_lo<F16>(v.y, h[u][2], h[u][3]);
-    }
-#pragma unroll
-    for (int p = 0; p < 4; ++p) w[p][q / 2] = (uint32_t)h[0][p] | ((uint32_t)h[1][p] << 16);
-  }
-  uint16_t* dst = E + row * lde + col;
-#pragma unroll
-  for (int p = 0; p < 4; ++p)
-    *reinterpret_cast<uint4*>(dst + p * e_plane) = make_uint4(w[p][0], w[p][1], w[p][2], w[p][3]);
-}
-
-// ------------------------------------------------------------------------------------
-// host side
-
 // Shared-memory opt-in of every GEMM instantiation on the current device; called outside
 // any stream capture (plan creation), so that launches inside a captured graph need no
 // attribute calls.
@@ -236,9 +213,10 @@ struct cgh_tc_state {
   size_t flags_bytes;
   TcFlags fl;
   int *rows, *cols, *kr_pad, *kc_pad;
-  uint16_t *A1, *A2, *B1, *Y;
-  long long a1_plane, a2_plane, b1_plane, y_plane;
-  CUtensorMap mA1, mA2, mB1, mY;
+  int *rband, *cband, *kmap2;  // K-step band maps (see k_tc_compact, k_tc_kmap2)
+  uint16_t *B1, *Y;
+  long long b1_plane, y_plane;
+  CUtensorMap mB1, mY;
 };
 
 static int tc_ensure(const cgh_plan* pc) {
@@ -271,17 +249,14 @@ static int tc_ensure(const cgh_plan* pc) {
   TC_TRY(cudaMalloc(&t->cols, (size_t)Z * t->kc_alloc * sizeof(int)), "tensor-core scratch: cols");
   TC_TRY(cudaMalloc(&t->kr_pad, CGH_MAX_LAYERS * sizeof(int)), "tensor-core scratch: kr");
   TC_TRY(cudaMalloc(&t->kc_pad, CGH_MAX_LAYERS * sizeof(int)), "tensor-core scratch: kc");
-  t->a1_plane = (long long)Z * p->holo_w * t->kc_alloc;
-  t->a2_plane = (long long)p->holo_h * t->ktot_alloc;
+  TC_TRY(cudaMalloc(&t->rband, (size_t)Z * (t->kr_alloc / 32) * sizeof(int)), "tensor-core scratch: bands");
+  TC_TRY(cudaMalloc(&t->cband, (size_t)Z * (t->kc_alloc / 32) * sizeof(int)), "tensor-core scratch: bands");
+  TC_TRY(cudaMalloc(&t->kmap2, (size_t)(t->ktot_alloc / 32) * sizeof(int)), "tensor-core scratch: K map");
   t->b1_plane = (long long)t->ktot_alloc * t->kc_alloc;
   t->y_plane = (long long)p->holo_w * t->ktot_alloc;
-  TC_TRY(cudaMalloc(&t->A1, 4 * t->a1_plane * sizeof(uint16_t)), "tensor-core scratch: A1");
-  TC_TRY(cudaMalloc(&t->A2, 4 * t->a2_plane * sizeof(uint16_t)), "tensor-core scratch: A2");
   TC_TRY(cudaMalloc(&t->B1, 2 * t->b1_plane * sizeof(uint16_t)), "tensor-core scratch: B1");
   TC_TRY(cudaMalloc(&t->Y, 4 * t->y_plane * sizeof(uint16_t)), "tensor-core scratch: Y");
-  if ((rc = make_plane_map(&t->mA1, t->A1, 4, (long long)Z * p->holo_w, t->kc_alloc)) != CGH_OK) goto fail;
   if ((rc = make_plane_map(&t->mB1, t->B1, 2, t->ktot_alloc, t->kc_alloc)) != CGH_OK) goto fail;
-  if ((rc = make_plane_map(&t->mA2, t->A2, 4, p->holo_h, t->ktot_alloc)) != CGH_OK) goto fail;
   if ((rc = make_plane_map(&t->mY, t->Y, 4, p->holo_w, t->ktot_alloc)) != CGH_OK) goto fail;
 #undef TC_TRY
   p->tc = t;
@@ -300,8 +275,9 @@ void tc_destroy(cgh_plan* p) {
   cudaFree(t->cols);
   cudaFree(t->kr_pad);
   cudaFree(t->kc_pad);
-  cudaFree(t->A1);
-  cudaFree(t->A2);
+  cudaFree(t->rband);
+  cudaFree(t->cband);
+  cudaFree(t->kmap2);
   cudaFree(t->B1);
   cudaFree(t->Y);
   free(t);
@@ -332,7 +308,8 @@ static int stage2_splits(int tiles, int kmax_steps) {
   } while (0)
 
 // Operands of both GEMM stages for one scene: selection flags, per-layer band compaction,
-// the inverse-DWT operand (stage-1 B) and the gathered fringe operands (stage-1 and 2 A).
+// the stage-2 K-step map and the inverse-DWT operand (stage-1 B).  The A operands of both
+// stages are the plan's fringe planes (eops_get), read band by band through the K maps.
 template <bool F16>
 static int tc_prep(const cgh_plan* p, const int32_t* coef, const int32_t* const* lists, const int32_t* d_counts,
                    cudaStream_t st) {
@@ -341,24 +318,18 @@ static int tc_prep(const cgh_plan* p, const int32_t* coef, const int32_t* const*
   TC_CK(cudaMemsetAsync(t->flags, 0, t->flags_bytes, st), "tc: clear flags");
   k_tc_scatter<<<dim3(64, 4), 256, 0, st>>>(lists[0], lists[1], lists[2], lists[3], d_counts, t->fl, H, W, Z);
   TC_CK(cudaGetLastError(), "tc: scatter");
-  k_tc_compact<<<Z, 1024, 0, st>>>(t->fl, H, W, t->rows, t->cols, t->kr_pad, t->kc_pad, t->kr_alloc, t->kc_alloc);
+  k_tc_compact<<<Z, 1024, 0, st>>>(t->fl, H, W, t->rows, t->cols, t->kr_pad, t->kc_pad, t->kr_alloc, t->kc_alloc,
+                                   t->rband, t->cband);
   TC_CK(cudaGetLastError(), "tc: compact");
+  k_tc_kmap2<<<Z, 256, 0, st>>>(t->kr_pad, t->rband, t->kr_alloc / 32, H, Z, t->kmap2);
+  TC_CK(cudaGetLastError(), "tc: K map");
   {
     dim3 blk(8, 32), grid((t->kc_alloc / 8 + 7) / 8, (t->kr_alloc + 31) / 32, Z);
     k_tc_idwt<F16><<<grid, blk, 0, st>>>(coef, t->fl, t->rows, t->cols, t->kr_pad, t->kc_pad, H, W, t->kr_alloc,
                                          t->kc_alloc, t->B1, t->b1_plane, t->kc_alloc);
     TC_CK(cudaGetLastError(), "tc: idwt");
   }
-  {
-    dim3 blk(8, 32), grid((t->kc_alloc / 8 + 7) / 8, (p->holo_w + 31) / 32, Z);
-    k_tc_gather_e<F16><<<grid, blk, 0, st>>>(p->d_tab, p->tab_len, p->tab_off, p->s, t->cols, t->kc_alloc,
-                                             t->kc_pad, p->holo_w, 0, t->A1, t->a1_plane, t->kc_alloc);
-    TC_CK(cudaGetLastError(), "tc: gather E1");
-    dim3 grid2((t->kr_alloc / 8 + 7) / 8, (p->holo_h + 31) / 32, Z);
-    k_tc_gather_e<F16><<<grid2, blk, 0, st>>>(p->d_tab, p->tab_len, p->tab_off, p->s, t->rows, t->kr_alloc,
-                                              t->kr_pad, p->holo_h, 1, t->A2, t->a2_plane, t->ktot_alloc);
-    TC_CK(cudaGetLastError(), "tc: gather E2");
-  }
+
   return CGH_OK;
 }
 
@@ -379,6 +350,8 @@ static void stage1_args(const cgh_plan* p, bool f16, TcGemmArgs& a, dim3& tiles)
   a.y_plane = t->y_plane;
   a.ldy = t->ktot_alloc;
   a.status = p->d_status;
+  a.a_kmap = t->cband;
+  a.a_kmap_ld = t->kc_alloc / 32;
   tiles = dim3((p->holo_w + TC_BM - 1) / TC_BM, (t->kr_alloc + TC_BN - 1) / TC_BN, p->n_layers);
   a.tm = tiles.x;
   a.tn = tiles.y;
@@ -400,6 +373,7 @@ static void stage2_args(const cgh_plan* p, bool f16, float2* holo, int S, TcGemm
   a.ldh = p->holo_w;
   a.h_vec4 = ((p->holo_w & 1) == 0) && (((uintptr_t)holo & 15) == 0);
   a.status = p->d_status;
+  a.a_kmap = t->kmap2;
   tiles = dim3((p->holo_h + TC_BM - 1) / TC_BM, (p->holo_w + TC_BN - 1) / TC_BN, S);
   a.tm = tiles.x;
   a.tn = tiles.y;
@@ -410,15 +384,18 @@ template <bool F16>
 static int tc_run(const cgh_plan* p, const int32_t* coef, const int32_t* const* lists, const int32_t* d_counts,
                   float2* holo, int accumulate, cudaStream_t st) {
   cgh_tc_state* t = p->tc;
+  const CUtensorMap *mEZ, *mEZt;
+  int rc = eops_get(p, F16 ? 1 : 0, &mEZ, &mEZt, st);
+  if (rc != CGH_OK) return rc;
   prof_mark(p, CGH_PROF_TC_PREP, 0, st);
-  int rc = tc_prep<F16>(p, coef, lists, d_counts, st);
+  rc = tc_prep<F16>(p, coef, lists, d_counts, st);
   if (rc != CGH_OK) return rc;
   prof_mark(p, CGH_PROF_TC_PREP, 1, st);
   TcGemmArgs a;
   dim3 tiles;
   stage1_args(p, F16, a, tiles);
   prof_mark(p, CGH_PROF_TC_STAGE1, 0, st);
-  cudaError_t e = launch_gemm<KIND_CR, EPI_Y, F16>(t->mA1, t->mB1, a, tiles, st);
+  cudaError_t e = launch_gemm<KIND_CR, EPI_Y, F16>(*mEZt, t->mB1, a, tiles, st);
   prof_mark(p, CGH_PROF_TC_STAGE1, 1, st);
   TC_CK(e, "tc: stage-1 GEMM");
   if (!accumulate) TC_CK(cudaMemsetAsync(holo, 0, (size_t)p->holo_h * p->holo_w * sizeof(float2), st), "tc: clear");
@@ -433,7 +410,7 @@ static int tc_run(const cgh_plan* p, const int32_t* coef, const int32_t* const* 
   }
   stage2_args(p, F16, holo, S, a, tiles);
   prof_mark(p, CGH_PROF_TC_STAGE2, 0, st);
-  e = launch_gemm<KIND_CC, EPI_H, F16>(t->mA2, t->mY, a, tiles, st);
+  e = launch_gemm<KIND_CC, EPI_H, F16>(*mEZ, t->mY, a, tiles, st);
   prof_mark(p, CGH_PROF_TC_STAGE2, 1, st);
   TC_CK(e, "tc: stage-2 GEMM");
   return CGH_OK;
@@ -473,7 +450,10 @@ static int batch_upload(cgh_batch* b) {
     const cgh_plan* p = b->plans[i];
     cgh_tc_state* t = p->tc;
     dim3 tiles;
-    b->h1[i].ma = t->mA1;
+    const CUtensorMap *mEZ, *mEZt;
+    const int rc = eops_get(p, f16 ? 1 : 0, &mEZ, &mEZt, 0);
+    if (rc != CGH_OK) return rc;
+    b->h1[i].ma = *mEZt;
     b->h1[i].mb = t->mB1;
     stage1_args(p, f16, b->h1[i].a, tiles);
     b->h1[i].unit0 = u1;
@@ -482,7 +462,7 @@ static int batch_upload(cgh_batch* b) {
     const int kst = t->ktot_alloc / TC_BK;
     int S = p->deterministic ? 1 : (kst + b->ksteps - 1) / b->ksteps;
     if (S < 1) S = 1;
-    b->h2[i].ma = t->mA2;
+    b->h2[i].ma = *mEZ;
     b->h2[i].mb = t->mY;
     stage2_args(p, f16, b->H[i], S, b->h2[i].a, tiles);
     b->h2[i].unit0 = u2;

@@ -149,6 +149,8 @@ struct TcGemmArgs {
   int n_layers;
   int M, N, K;       // test: sizes; stages: M and N of the output (K from the device)
   int tm, tn, tz;    // work units: M tiles x N tiles x (layers | K splits | 1)
+  const int* a_kmap; // optional: A's K coordinate of every 32-wide K step (mode 1: per layer,
+  int a_kmap_ld;     // a_kmap_ld entries apart; mode 2: one map over the concatenated K)
   float scale;
   float2* H;         // EPI_H: complex output [M][N]
   int ldh;
@@ -239,6 +241,7 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
 
 struct TileInfo {
   int a_row, b_row, k_lo, nk, out_row0, out_col0, n_valid, row_lim, col_lim, item;
+  const int* akm;  // A's K coordinate per K step of this tile, or null (= k_lo + 32 kt)
 };
 
 // Work unit t of the persistent grid: (mt fastest, then nt, then the layer / K split).
@@ -249,6 +252,7 @@ __device__ __forceinline__ bool decode_tile(const TcGemmArgs& a, int t, const in
   ti.n_valid = TC_BN;
   ti.row_lim = a.M;
   ti.col_lim = a.N;
+  ti.akm = nullptr;
   if (a.mode == 3) {
     ti.a_row = zz * a.a_rows_per_z + mt * TC_BM;
     ti.b_row = zz * a.b_rows_per_z + nt * TC_BN;
@@ -271,6 +275,7 @@ __device__ __forceinline__ bool decode_tile(const TcGemmArgs& a, int t, const in
     ti.nk = a.kc_pad[zz] / TC_BK;
     ti.out_col0 = s_off[zz] + nt * TC_BN;
     ti.col_lim = ti.out_col0 + ti.n_valid;
+    if (a.a_kmap) ti.akm = a.a_kmap + (size_t)zz * a.a_kmap_ld;
   } else if (a.mode == 2) {
     const int nkt = ktot / TC_BK, S = a.tz;
     const int k0 = (int)((long long)nkt * zz / S), k1 = (int)((long long)nkt * (zz + 1) / S);
@@ -279,6 +284,7 @@ __device__ __forceinline__ bool decode_tile(const TcGemmArgs& a, int t, const in
     ti.k_lo = k0 * TC_BK;
     ti.nk = k1 - k0;
     ti.out_col0 = nt * TC_BN;
+    if (a.a_kmap) ti.akm = a.a_kmap + k0;
   } else {
     ti.a_row = mt * TC_BM;
     ti.b_row = nt * TC_BN;
@@ -353,7 +359,7 @@ __device__ __forceinline__ void tc_gemm_body(const Src& src, uint8_t* smem, uint
           }
           uint8_t* st = smem + s * STAGE;
           mbar_arrive_expect_tx(&full_bar[s], STAGE);
-          tma_load_3d(st, mA, &full_bar[s], ti.k_lo + kt * TC_BK, ti.a_row, 0);
+          tma_load_3d(st, mA, &full_bar[s], ti.akm ? ti.akm[kt] : ti.k_lo + kt * TC_BK, ti.a_row, 0);
           tma_load_3d(st + NA * TC_PLANE_BYTES, mB, &full_bar[s], ti.k_lo + kt * TC_BK, ti.b_row, 0);
           issued[s] = true;
           issued_ph[s] = ph;
