@@ -37,6 +37,20 @@ def peaks():
         return None
 
 
+def kernel_traffic(key):
+    """DRAM bytes per launch of `key` from the committed ncu summary (profiles/traffic.json),
+    or None when the kernel's sources changed since those counters were taken."""
+    import hashlib
+    try:
+        entry = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))[key]
+        h = hashlib.sha256()
+        for f in entry["src_files"]:
+            h.update(open(os.path.join(ROOT, f), "rb").read())
+        return entry["bytes"] if h.hexdigest()[:16] == entry["src_hash"] else None
+    except Exception:
+        return None
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -408,7 +422,10 @@ def run_ours(args):
         peak_tf = pk.get("bf16_tflops", 1900.0)
         roof = {"bound": "tensor", "kernel": "k_tc_gemm<KIND_CC,EPI_H> (stage 2)",
                 "achieved": algo_flop / (k_ms / 1e3) / 1e12, "peak": peak_tf, "unit": "TFLOP/s",
-                "frac": algo_flop / (k_ms / 1e3) / 1e12 / peak_tf, "traffic": None,
+                "frac": algo_flop / (k_ms / 1e3) / 1e12 / peak_tf,
+                "traffic": kernel_traffic("k_tc_gemm<KIND_CC,EPI_H> (stage 2)") if form == "tc_bf16x3" else None,
+                "traffic_note": "ncu dram__bytes_read.sum + dram__bytes_write.sum per launch "
+                                "(profiles/k_tc_gemm_stage2_paper_scale.md); null if the kernel changed since",
                 "peak_note": "measured cuBLAS bf16 dense burst (MEASURED_PEAKS.json); fp16 has the same "
                              "nominal dense rate" if "bf16_tflops" in pk else "fallback 1.9 PFLOP/s",
                 "kernel_ms": k_ms, "k_rows_total": ksum, "k_cols_total": sum(kc)}
@@ -419,7 +436,7 @@ def run_ours(args):
         peak_tf = sms * 128 * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
         roof = {"bound": "alu", "kernel": "k_direct_lut", "achieved": algo_flop / (k_ms / 1e3) / 1e12,
                 "peak": peak_tf, "unit": "TFLOP/s",
-                "frac": algo_flop / (k_ms / 1e3) / 1e12 / peak_tf, "traffic": None,
+                "frac": algo_flop / (k_ms / 1e3) / 1e12 / peak_tf, "traffic": kernel_traffic("k_direct_lut"),
                 "peak_note": f"FP32 FFMA: {sms} SMs x 128 lanes x 2 flop x {pk.get('sm_max_mhz', 2070.0):.0f} MHz "
                              "(max SM clock; derived, not measured)",
                 "kernel_ms": k_ms}
