@@ -379,6 +379,15 @@ int cgh_profile_read(cgh_plan* plan, float* ms, void* stream);
 int cgh_tc_layer_dims(const cgh_plan* plan, int* kr, int* kc, void* stream);
 
 /*
+ * cgh_selftest_timeout - failure-detection self-test (the paper has no counterpart).
+ * Enqueues a kernel whose bounded device wait, the same one the tensor-core pipeline uses,
+ * waits on a barrier that nothing completes; after limit_us microseconds (1..1000000) it
+ * gives up, records CGH_ERR_TIMEOUT in the plan's status word and returns, so no GPU hangs
+ * and the context stays usable.  Read the result with cgh_status.
+ */
+int cgh_selftest_timeout(const cgh_plan* plan, int limit_us, void* stream);
+
+/*
  * cgh_status - read and clear the plan's device status word (synchronises `stream`).
  * Bounded device-side waits that give up record CGH_ERR_TIMEOUT there instead of
  * hanging.  *status_out receives CGH_OK or the recorded code.

@@ -54,6 +54,7 @@ SIGNATURES = {
     "cgh_phase_to_field": (_I, [_P, _P, ctypes.c_longlong, _P]),
     "cgh_phase_grad": (_I, [_P, _P, _P, ctypes.c_longlong, _P]),
     "cgh_status": (_I, [_P, ctypes.POINTER(_I), _P]),
+    "cgh_selftest_timeout": (_I, [_P, _I, _P]),
     "cgh_tc_selftest_gemm": (_I, [_P, _P, _P, _I, _I, _I, _I, _P]),
     "cgh_batch_create": (_I, [ctypes.POINTER(_P), ctypes.POINTER(_P), _I, ctypes.POINTER(_P),
                               ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_I),
@@ -269,6 +270,9 @@ class Plan:
         kc = (ctypes.c_int * self.n_layers)()
         check(lib().cgh_tc_layer_dims(self.handle, kr, kc, _stream(stream)))
         return list(kr), list(kc)
+
+    def selftest_timeout(self, limit_us, stream=None):
+        check(lib().cgh_selftest_timeout(self.handle, int(limit_us), _stream(stream)))
 
     def status(self, stream=None):
         v = ctypes.c_int(0)

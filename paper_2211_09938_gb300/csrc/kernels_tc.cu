@@ -705,3 +705,25 @@ extern "C" int cgh_tc_selftest_gemm(const uint16_t* A, const uint16_t* B, float*
                           : launch_gemm<KIND_TEST, EPI_C, false>(ma, mb, a, grid, (cudaStream_t)stream);
   return cgh_cuda_check(e, "cgh_tc_selftest_gemm");
 }
+
+// Failure-detection self-test: one thread waits, with the same bounded wait as the GEMM
+// pipeline, on an mbarrier that nothing ever completes; the wait gives up after limit_ns
+// and records CGH_ERR_TIMEOUT in the status word, and the kernel returns normally.
+__global__ void k_wait_timeout(int* status, unsigned long long limit_ns) {
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ volatile int s_abort;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    s_abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) mbar_wait_bounded(&bar, 0, &s_abort, status, limit_ns);
+}
+
+extern "C" int cgh_selftest_timeout(const cgh_plan* p, int limit_us, void* stream) {
+  if (!p || limit_us < 1 || limit_us > 1000000)
+    return cgh_fail(CGH_ERR_ARG, "cgh_selftest_timeout: plan NULL or limit outside 1..1000000 us");
+  k_wait_timeout<<<1, 32, 0, (cudaStream_t)stream>>>(p->d_status, 1000ull * (unsigned long long)limit_us);
+  return cgh_cuda_check(cudaGetLastError(), "cgh_selftest_timeout");
+}

@@ -60,13 +60,13 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
 // Wait for the phase `parity` of `bar` to complete.  Gives up after TC_WAIT_NS or when
 // another role has raised the CTA's abort flag; a timeout records CGH_ERR_TIMEOUT.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
-                                                  int* status) {
+                                                  int* status, uint64_t limit_ns = TC_WAIT_NS) {
   if (mbar_try_wait(bar, parity)) return true;
   const uint64_t t0 = global_timer();
   while (true) {
     if (mbar_try_wait(bar, parity)) return true;
     if (*abort_flag) return false;
-    if (global_timer() - t0 > TC_WAIT_NS) {
+    if (global_timer() - t0 > limit_ns) {
       *abort_flag = 1;
       if (status) atomicExch(status, CGH_ERR_TIMEOUT);
       return false;

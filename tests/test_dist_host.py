@@ -1,0 +1,54 @@
+"""Host logic of bench.py's multi-GPU (replica) path on CPU: two gloo ranks, each with its
+own step time; both see the maximum, and the whole-job value counts every rank's work."""
+import os
+import socket
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    return port
+
+
+def _rank_main(rank, world, port, out):
+    import sys
+    sys.path.insert(0, ROOT)
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
+    import torch.distributed as dist
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    import bench
+    mine = 10.0 + 5.0 * rank  # rank 1 is slower
+    mx = bench.reduce_max(mine)
+    dist.barrier()
+    out[rank] = (mx, bench.whole_job_value(1e9, 4, world, mx))
+    dist.destroy_process_group()
+
+
+def test_two_rank_max_and_whole_job_value():
+    import torch.multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    mgr = ctx.Manager()
+    out = mgr.dict()
+    port = _free_port()
+    procs = [ctx.Process(target=_rank_main, args=(r, 2, port, out)) for r in range(2)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(120)
+        assert p.exitcode == 0
+    assert out[0][0] == out[1][0] == 15.0
+    # 2 ranks x 4 steps x 1e9 units in 15 ms -> 5.333e11 units/s = 533.3 G units/s
+    assert abs(out[0][1] - 2 * 4 * 1e9 / 0.015 / 1e9) < 1e-6
+
+
+def test_single_process_reduce_is_identity():
+    import sys
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.reduce_max(3.5) == 3.5
