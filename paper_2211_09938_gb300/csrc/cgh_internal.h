@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <utility>
+
 #include "../../include/cgh.h"
 
 #define CGH_MAX_LAYERS 64
@@ -58,6 +60,33 @@ static inline void prof_mark(const cgh_plan* pc, int slot, int stop, cudaStream_
   cudaEventRecord(p->prof_ev[slot][stop], st);
   if (stop) p->prof_used[slot] = 1;
 }
+
+// Programmatic dependent launch: a kernel launched with launch_pdl may start while its
+// predecessor in the stream finishes; pdl_wait() blocks until that predecessor has
+// completed and its memory is visible, pdl_trigger() lets the successor start.  Kernels
+// call pdl_wait() before reading anything a predecessor wrote, and pdl_trigger() only
+// after their own wait, so data written two or more kernels back is always complete when a
+// kernel starts.  Both are no-ops for ordinary launches.
+#ifdef __CUDACC__
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+template <typename... Exp, typename... Act>
+static inline cudaError_t launch_pdl(void (*k)(Exp...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                                     Act&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k, std::forward<Act>(args)...);
+}
+#endif
 
 // Thread-local error message helpers (cgh_api.cu).
 int cgh_fail(int code, const char* fmt, ...);

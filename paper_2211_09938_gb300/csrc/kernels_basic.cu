@@ -192,6 +192,8 @@ __global__ void __launch_bounds__(CGH_SEL_CHUNK) k_select_count(const uint8_t* _
                                                                 int Z, const SelTasks T,
                                                                 int* __restrict__ chunk_cnt) {
   __shared__ int s_cnt[CGH_MAX_LAYERS];
+  pdl_wait();
+  pdl_trigger();
   const SelTask& tk = T.t[sel_task_of(T, blockIdx.x)];
   const int chunk = blockIdx.x - tk.chunk0;
   const int level = tk.level, nbx = W >> level, nb = (H >> level) * nbx;
@@ -213,6 +215,8 @@ __global__ void __launch_bounds__(CGH_SEL_CHUNK) k_select_count(const uint8_t* _
 __global__ void __launch_bounds__(1024) k_select_scan(const int* __restrict__ chunk_cnt,
                                                       int* __restrict__ chunk_off, int Z, const SelTasks T) {
   __shared__ int s_part[1024];
+  pdl_wait();
+  pdl_trigger();
   const SelTask& tk = T.t[blockIdx.x];
   const int n = Z * tk.nchunks;
   const int* cnt = chunk_cnt + tk.cnt_off;
@@ -241,12 +245,16 @@ __global__ void __launch_bounds__(1024) k_select_scan(const int* __restrict__ ch
   }
 }
 
-// Pass 3: ordered scatter.  Per layer a warp ballot gives the rank inside the warp and a
-// shared scan the warp offsets.
+// Pass 3: ordered scatter.  Per layer, warp ballots give every warp's count and every
+// thread's rank inside its warp; one shared exclusive scan over the warps (per layer) gives
+// the warp offsets.  Two barriers per CTA whatever the number of layers.
 __global__ void __launch_bounds__(CGH_SEL_CHUNK) k_select_scatter(
     const uint8_t* __restrict__ sal, const uint8_t* __restrict__ L, int H, int W, int Z, const SelTasks T,
     const int* __restrict__ chunk_cnt, const int* __restrict__ chunk_off) {
-  __shared__ int s_warp[CGH_SEL_CHUNK / 32];
+  constexpr int NW = CGH_SEL_CHUNK / 32;
+  __shared__ int s_wcnt[NW][CGH_MAX_LAYERS];
+  pdl_wait();
+  pdl_trigger();
   const SelTask& tk = T.t[sel_task_of(T, blockIdx.x)];
   const int chunk = blockIdx.x - tk.chunk0;
   const int level = tk.level, nbx = W >> level, nb = (H >> level) * nbx;
@@ -255,29 +263,29 @@ __global__ void __launch_bounds__(CGH_SEL_CHUNK) k_select_scatter(
   const unsigned long long m =
       b < nb ? block_layer_mask(sal, L, W, 1 << level, by, bx, tk.threshold, Z) : 0ull;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const unsigned below = (1u << lane) - 1u;
   for (int z = 0; z < Z; ++z) {
-    const int ci = tk.cnt_off + z * tk.nchunks + chunk;
-    if (chunk_cnt[ci] == 0) continue;  // uniform over the CTA
+    const unsigned bal = __ballot_sync(0xffffffffu, (m >> z) & 1ull);
+    if (lane == 0) s_wcnt[warp][z] = __popc(bal);
+  }
+  __syncthreads();
+  if (threadIdx.x < Z) {
+    int run = 0;
+#pragma unroll
+    for (int w = 0; w < NW; ++w) {
+      const int c = s_wcnt[w][threadIdx.x];
+      s_wcnt[w][threadIdx.x] = run;
+      run += c;
+    }
+  }
+  __syncthreads();
+  for (int z = 0; z < Z; ++z) {
     const bool f = (m >> z) & 1ull;
     const unsigned bal = __ballot_sync(0xffffffffu, f);
-    if (lane == 0) s_warp[warp] = __popc(bal);
-    __syncthreads();
-    if (warp == 0) {
-      const int v = lane < CGH_SEL_CHUNK / 32 ? s_warp[lane] : 0;
-      int inc = v;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const int t = __shfl_up_sync(0xffffffffu, inc, o);
-        if (lane >= o) inc += t;
-      }
-      if (lane < CGH_SEL_CHUNK / 32) s_warp[lane] = inc - v;
-    }
-    __syncthreads();
     if (f) {
-      const int pos = chunk_off[ci] + s_warp[warp] + __popc(bal & ((1u << lane) - 1u));
+      const int pos = chunk_off[tk.cnt_off + z * tk.nchunks + chunk] + s_wcnt[warp][z] + __popc(bal & below);
       if (pos < tk.capacity) tk.list[pos] = (z << 24) | (by << 12) | bx;
     }
-    __syncthreads();
   }
 }
 
@@ -297,10 +305,14 @@ cudaError_t launch_select_tasks(int obj_h, int obj_w, int n_layers, const uint8_
     T.t[k].cnt_off = c0 * n_layers;
     c0 += T.t[k].nchunks;
   }
-  k_select_count<<<c0, CGH_SEL_CHUNK, 0, st>>>(sal, L, obj_h, obj_w, n_layers, T, chunk_cnt);
-  k_select_scan<<<T.n, 1024, 0, st>>>(chunk_cnt, chunk_off, n_layers, T);
-  k_select_scatter<<<c0, CGH_SEL_CHUNK, 0, st>>>(sal, L, obj_h, obj_w, n_layers, T, chunk_cnt, chunk_off);
-  return cudaGetLastError();
+  cudaError_t e = launch_pdl(k_select_count, dim3(c0), dim3(CGH_SEL_CHUNK), 0, st, sal, L, obj_h, obj_w, n_layers,
+                             T, chunk_cnt);
+  if (e == cudaSuccess)
+    e = launch_pdl(k_select_scan, dim3(T.n), dim3(1024), 0, st, (const int*)chunk_cnt, chunk_off, n_layers, T);
+  if (e == cudaSuccess)
+    e = launch_pdl(k_select_scatter, dim3(c0), dim3(CGH_SEL_CHUNK), 0, st, sal, L, obj_h, obj_w, n_layers, T,
+                   (const int*)chunk_cnt, (const int*)chunk_off);
+  return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 cudaError_t launch_select(int obj_h, int obj_w, int n_layers, const uint8_t* sal, const uint8_t* L,

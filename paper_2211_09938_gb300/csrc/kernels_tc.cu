@@ -21,6 +21,8 @@
 __global__ void k_tc_scatter(const int32_t* __restrict__ l0, const int32_t* __restrict__ l1,
                              const int32_t* __restrict__ l2, const int32_t* __restrict__ l3,
                              const int32_t* __restrict__ d_counts, TcFlags fl, int H, int W, int Z) {
+  pdl_wait();
+  pdl_trigger();
   const int li = blockIdx.y;
   const int32_t* lst = li == 0 ? l0 : li == 1 ? l1 : li == 2 ? l2 : l3;
   const int level = li == 0 ? 3 : li;
@@ -73,6 +75,8 @@ __global__ void __launch_bounds__(1024) k_tc_compact(TcFlags fl, int H, int W, i
                                                      int* __restrict__ kc_pad, int ld_rows, int ld_cols,
                                                      int* __restrict__ rband, int* __restrict__ cband) {
   __shared__ int s_warp[33];
+  pdl_wait();
+  pdl_trigger();
   const int z = blockIdx.x, t = threadIdx.x;
   for (int axis = 0; axis < 2; ++axis) {
     const int n8 = axis == 0 ? (H >> 3) : (W >> 3);
@@ -102,6 +106,8 @@ __global__ void __launch_bounds__(1024) k_tc_compact(TcFlags fl, int H, int W, i
 // column z*H + 32*band of the layer's compacted row band.
 __global__ void k_tc_kmap2(const int* __restrict__ kr_pad, const int* __restrict__ rband, int ld_band, int H, int Z,
                            int* __restrict__ kmap2) {
+  pdl_wait();
+  pdl_trigger();
   const int z = blockIdx.x;
   int off = 0;
   for (int q = 0; q < z; ++q) off += kr_pad[q];
@@ -120,6 +126,8 @@ __global__ void k_tc_idwt(const int32_t* __restrict__ coef, TcFlags fl, const in
                           const int* __restrict__ cols, const int* __restrict__ kr_pad,
                           const int* __restrict__ kc_pad, int H, int W, int ld_rows, int ld_cols,
                           uint16_t* __restrict__ B1, long long b1_plane, int ldb1) {
+  pdl_wait();
+  pdl_trigger();
   const int z = blockIdx.z;
   const int c = 8 * (blockIdx.x * blockDim.x + threadIdx.x);
   const int k = blockIdx.y * blockDim.y + threadIdx.y;
@@ -316,18 +324,21 @@ static int tc_prep(const cgh_plan* p, const int32_t* coef, const int32_t* const*
   cgh_tc_state* t = p->tc;
   const int H = p->obj_h, W = p->obj_w, Z = p->n_layers;
   TC_CK(cudaMemsetAsync(t->flags, 0, t->flags_bytes, st), "tc: clear flags");
-  k_tc_scatter<<<dim3(64, 4), 256, 0, st>>>(lists[0], lists[1], lists[2], lists[3], d_counts, t->fl, H, W, Z);
-  TC_CK(cudaGetLastError(), "tc: scatter");
-  k_tc_compact<<<Z, 1024, 0, st>>>(t->fl, H, W, t->rows, t->cols, t->kr_pad, t->kc_pad, t->kr_alloc, t->kc_alloc,
-                                   t->rband, t->cband);
-  TC_CK(cudaGetLastError(), "tc: compact");
-  k_tc_kmap2<<<Z, 256, 0, st>>>(t->kr_pad, t->rband, t->kr_alloc / 32, H, Z, t->kmap2);
-  TC_CK(cudaGetLastError(), "tc: K map");
+  TC_CK(launch_pdl(k_tc_scatter, dim3(64, 4), dim3(256), 0, st, lists[0], lists[1], lists[2], lists[3], d_counts,
+                   t->fl, H, W, Z),
+        "tc: scatter");
+  TC_CK(launch_pdl(k_tc_compact, dim3(Z), dim3(1024), 0, st, t->fl, H, W, t->rows, t->cols, t->kr_pad, t->kc_pad,
+                   t->kr_alloc, t->kc_alloc, t->rband, t->cband),
+        "tc: compact");
+  TC_CK(launch_pdl(k_tc_kmap2, dim3(Z), dim3(256), 0, st, (const int*)t->kr_pad, (const int*)t->rband,
+                   t->kr_alloc / 32, H, Z, t->kmap2),
+        "tc: K map");
   {
     dim3 blk(8, 32), grid((t->kc_alloc / 8 + 7) / 8, (t->kr_alloc + 31) / 32, Z);
-    k_tc_idwt<F16><<<grid, blk, 0, st>>>(coef, t->fl, t->rows, t->cols, t->kr_pad, t->kc_pad, H, W, t->kr_alloc,
-                                         t->kc_alloc, t->B1, t->b1_plane, t->kc_alloc);
-    TC_CK(cudaGetLastError(), "tc: idwt");
+    TC_CK(launch_pdl(k_tc_idwt<F16>, grid, blk, 0, st, coef, t->fl, (const int*)t->rows, (const int*)t->cols,
+                     (const int*)t->kr_pad, (const int*)t->kc_pad, H, W, t->kr_alloc, t->kc_alloc, t->B1, t->b1_plane,
+                     t->kc_alloc),
+          "tc: idwt");
   }
 
   return CGH_OK;
@@ -387,6 +398,7 @@ static int tc_run(const cgh_plan* p, const int32_t* coef, const int32_t* const* 
   const CUtensorMap *mEZ, *mEZt;
   int rc = eops_get(p, F16 ? 1 : 0, &mEZ, &mEZt, st);
   if (rc != CGH_OK) return rc;
+  if (!accumulate) TC_CK(cudaMemsetAsync(holo, 0, (size_t)p->holo_h * p->holo_w * sizeof(float2), st), "tc: clear");
   prof_mark(p, CGH_PROF_TC_PREP, 0, st);
   rc = tc_prep<F16>(p, coef, lists, d_counts, st);
   if (rc != CGH_OK) return rc;
@@ -398,7 +410,6 @@ static int tc_run(const cgh_plan* p, const int32_t* coef, const int32_t* const* 
   cudaError_t e = launch_gemm<KIND_CR, EPI_Y, F16>(*mEZt, t->mB1, a, tiles, st);
   prof_mark(p, CGH_PROF_TC_STAGE1, 1, st);
   TC_CK(e, "tc: stage-1 GEMM");
-  if (!accumulate) TC_CK(cudaMemsetAsync(holo, 0, (size_t)p->holo_h * p->holo_w * sizeof(float2), st), "tc: clear");
   const int tm = (p->holo_h + TC_BM - 1) / TC_BM, tn = (p->holo_w + TC_BN - 1) / TC_BN;
   int S = p->deterministic ? 1 : stage2_splits(tm * tn, t->ktot_alloc / TC_BK);
   if (!p->deterministic && p->max_ksteps > 0) {

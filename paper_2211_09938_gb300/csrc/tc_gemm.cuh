@@ -333,6 +333,7 @@ __device__ __forceinline__ void tc_gemm_body(const Src& src, uint8_t* smem, uint
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
+  pdl_wait();  // barriers and tensor memory are set up; operands may now be read
   const uint32_t tmem = *s_tmem_p;
   const uint32_t smem_base = smem_u32(smem);
 
@@ -562,6 +563,7 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm(const __grid_constant__ CUte
   __shared__ uint32_t s_tmem;
   __shared__ volatile int s_abort;
   __shared__ int s_off[CGH_MAX_LAYERS + 1];
+  pdl_wait();
   if (threadIdx.x == 0) {
     int o = 0;
     s_off[0] = 0;
@@ -631,6 +633,7 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm_batch(const TcBatchItem* __r
   __shared__ uint32_t s_tmem;
   __shared__ volatile int s_abort;
   __shared__ int s_unit0[TC_BATCH_MAX];
+  pdl_wait();
   for (int i = threadIdx.x; i < n; i += blockDim.x) s_unit0[i] = items[i].unit0;
   __syncthreads();
   TcBatchSrc src{items, s_unit0, n, total, status};
@@ -703,7 +706,6 @@ static cudaError_t launch_gemm(const CUtensorMap& ma, const CUtensorMap& mb, TcG
   const long long units = (long long)a.tm * a.tn * a.tz;
   const int grid = (int)(units < tc_num_sms() ? units : tc_num_sms());
   if (grid <= 0) return cudaSuccess;
-  k_tc_gemm<KIND, EPI, F16><<<grid, 192, tc_smem_bytes<KIND>(), st>>>(ma, mb, a);
-  return cudaGetLastError();
+  return launch_pdl(k_tc_gemm<KIND, EPI, F16>, dim3(grid), dim3(192), tc_smem_bytes<KIND>(), st, ma, mb, a);
 }
 
