@@ -409,7 +409,8 @@ static int field_reconstruct_into(const cgh_plan* p, const float2* holo, float2*
   a.Y = f->T;
   a.y_plane = f->t_plane;
   a.ldy = Nh;
-  rc = cgh_cuda_check(launch_gemm<KIND_CC, EPI_Y, false>(f->mGZ, f->mHt, a,
+  a.y_rows = Z * No;
+  rc = cgh_cuda_check(launch_gemm<KIND_CC, EPI_Y, false>(f->mGZ, f->mHt, f->mT, a,
                                                          dim3((No + 127) / 128, (Nh + 127) / 128, Z), st),
                       "reconstruct: R1");
   if (rc != CGH_OK) return rc;
@@ -421,7 +422,7 @@ static int field_reconstruct_into(const cgh_plan* p, const float2* holo, float2*
   a.F = fields;
   a.ldf = No;
   a.h_vec4 = ((No & 1) == 0) && (((uintptr_t)fields & 15) == 0);
-  return cgh_cuda_check(launch_gemm<KIND_CC, EPI_F, false>(f->mT, f->mGZ, a,
+  return cgh_cuda_check(launch_gemm<KIND_CC, EPI_F, false>(f->mT, f->mGZ, f->mGZ, a,
                                                            dim3((No + 127) / 128, (No + 127) / 128, Z), st),
                         "reconstruct: R2");
 }
@@ -453,7 +454,8 @@ int field_propagate(const cgh_plan* p, const float2* fields, float2* holo, int a
   a.Y = f->Yp;
   a.y_plane = f->yp_plane;
   a.ldy = Z * No;
-  rc = cgh_cuda_check(launch_gemm<KIND_CC, EPI_Y, false>(*f->mEZt, f->mFp, a,
+  a.y_rows = Nh;
+  rc = cgh_cuda_check(launch_gemm<KIND_CC, EPI_Y, false>(*f->mEZt, f->mFp, f->mYp, a,
                                                          dim3((Nh + 127) / 128, (No + 127) / 128, Z), st),
                       "propagate: P1");
   if (rc != CGH_OK) return rc;
@@ -488,7 +490,8 @@ int field_propagate(const cgh_plan* p, const float2* fields, float2* holo, int a
       if (eff > best + 1e-9) best = eff, S = q;
     }
   }
-  rc = cgh_cuda_check(launch_gemm<KIND_CC, EPI_H, false>(*f->mEZ, f->mYp, b, dim3(tm, tm, S), st), "propagate: P2");
+  rc = cgh_cuda_check(launch_gemm<KIND_CC, EPI_H, false>(*f->mEZ, f->mYp, f->mYp, b, dim3(tm, tm, S), st),
+                      "propagate: P2");
   prof_mark(p, CGH_PROF_PROPAGATE, 1, st);
   return rc;
 }

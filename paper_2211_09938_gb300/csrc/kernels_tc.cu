@@ -360,6 +360,7 @@ static void stage1_args(const cgh_plan* p, bool f16, TcGemmArgs& a, dim3& tiles)
   a.Y = t->Y;
   a.y_plane = t->y_plane;
   a.ldy = t->ktot_alloc;
+  a.y_rows = p->holo_w;
   a.status = p->d_status;
   a.a_kmap = t->cband;
   a.a_kmap_ld = t->kc_alloc / 32;
@@ -407,7 +408,7 @@ static int tc_run(const cgh_plan* p, const int32_t* coef, const int32_t* const* 
   dim3 tiles;
   stage1_args(p, F16, a, tiles);
   prof_mark(p, CGH_PROF_TC_STAGE1, 0, st);
-  cudaError_t e = launch_gemm<KIND_CR, EPI_Y, F16>(*mEZt, t->mB1, a, tiles, st);
+  cudaError_t e = launch_gemm<KIND_CR, EPI_Y, F16>(*mEZt, t->mB1, t->mY, a, tiles, st);
   prof_mark(p, CGH_PROF_TC_STAGE1, 1, st);
   TC_CK(e, "tc: stage-1 GEMM");
   const int tm = (p->holo_h + TC_BM - 1) / TC_BM, tn = (p->holo_w + TC_BN - 1) / TC_BN;
@@ -421,7 +422,7 @@ static int tc_run(const cgh_plan* p, const int32_t* coef, const int32_t* const* 
   }
   stage2_args(p, F16, holo, S, a, tiles);
   prof_mark(p, CGH_PROF_TC_STAGE2, 0, st);
-  e = launch_gemm<KIND_CC, EPI_H, F16>(*mEZ, t->mY, a, tiles, st);
+  e = launch_gemm<KIND_CC, EPI_H, F16>(*mEZ, t->mY, t->mY, a, tiles, st);
   prof_mark(p, CGH_PROF_TC_STAGE2, 1, st);
   TC_CK(e, "tc: stage-2 GEMM");
   return CGH_OK;
@@ -466,6 +467,7 @@ static int batch_upload(cgh_batch* b) {
     if (rc != CGH_OK) return rc;
     b->h1[i].ma = *mEZt;
     b->h1[i].mb = t->mB1;
+    b->h1[i].mc = t->mY;
     stage1_args(p, f16, b->h1[i].a, tiles);
     b->h1[i].unit0 = u1;
     u1 += tiles.x * tiles.y * tiles.z;
@@ -475,6 +477,7 @@ static int batch_upload(cgh_batch* b) {
     if (S < 1) S = 1;
     b->h2[i].ma = *mEZ;
     b->h2[i].mb = t->mY;
+    b->h2[i].mc = t->mY;
     stage2_args(p, f16, b->H[i], S, b->h2[i].a, tiles);
     b->h2[i].unit0 = u2;
     u2 += tiles.x * tiles.y * tiles.z;
@@ -623,10 +626,10 @@ static int batch_run(cgh_batch* b, cudaStream_t st) {
   TC_CK(cudaGetLastError(), "batch: offsets");
   const int sms = tc_num_sms();
   int* status = b->plans[0]->d_status;
-  k_tc_gemm_batch<KIND_CR, EPI_Y, F16><<<b->units1 < sms ? b->units1 : sms, 192, tc_smem_bytes<KIND_CR>(), st>>>(
+  k_tc_gemm_batch<KIND_CR, EPI_Y, F16><<<b->units1 < sms ? b->units1 : sms, 192, tc_smem_bytes<KIND_CR, EPI_Y>(), st>>>(
       b->d1, b->n, b->units1, status);
   TC_CK(cudaGetLastError(), "batch: stage 1");
-  k_tc_gemm_batch<KIND_CC, EPI_H, F16><<<b->units2 < sms ? b->units2 : sms, 192, tc_smem_bytes<KIND_CC>(), st>>>(
+  k_tc_gemm_batch<KIND_CC, EPI_H, F16><<<b->units2 < sms ? b->units2 : sms, 192, tc_smem_bytes<KIND_CC, EPI_H>(), st>>>(
       b->d2, b->n, b->units2, status);
   TC_CK(cudaGetLastError(), "batch: stage 2");
   return CGH_OK;
@@ -712,8 +715,8 @@ extern "C" int cgh_tc_selftest_gemm(const uint16_t* A, const uint16_t* B, float*
   a.ldc = N;
   a.status = nullptr;
   dim3 grid((M + TC_BM - 1) / TC_BM, (N + TC_BN - 1) / TC_BN, 1);
-  cudaError_t e = is_fp16 ? launch_gemm<KIND_TEST, EPI_C, true>(ma, mb, a, grid, (cudaStream_t)stream)
-                          : launch_gemm<KIND_TEST, EPI_C, false>(ma, mb, a, grid, (cudaStream_t)stream);
+  cudaError_t e = is_fp16 ? launch_gemm<KIND_TEST, EPI_C, true>(ma, mb, ma, a, grid, (cudaStream_t)stream)
+                          : launch_gemm<KIND_TEST, EPI_C, false>(ma, mb, ma, a, grid, (cudaStream_t)stream);
   return cgh_cuda_check(e, "cgh_tc_selftest_gemm");
 }
 

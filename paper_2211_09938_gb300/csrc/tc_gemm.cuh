@@ -158,6 +158,7 @@ struct TcGemmArgs {
   uint16_t* Y;       // EPI_Y: 4 planes [plane][M][ldy]
   long long y_plane;
   int ldy;
+  int y_rows;        // EPI_Y: rows of the output tensor (the store map's row extent)
   float* C;          // EPI_C: real output [M][N]
   int ldc;
   float2* F;         // EPI_F: complex output rows (plain stores)
@@ -169,21 +170,60 @@ template <int KIND>
 struct TcCfg;
 template <>
 struct TcCfg<KIND_TEST> {
-  static constexpr int NA = 1, NB = 1, NST = 8;  // > 114 KiB: one CTA (and one TMEM owner) per SM
+  static constexpr int NA = 1, NB = 1;
 };
 template <>
 struct TcCfg<KIND_CR> {
-  static constexpr int NA = 4, NB = 2, NST = 4;
+  static constexpr int NA = 4, NB = 2;
 };
 template <>
 struct TcCfg<KIND_CC> {
-  static constexpr int NA = 4, NB = 4, NST = 3;
+  static constexpr int NA = 4, NB = 4;
 };
 
-template <int KIND>
-constexpr size_t tc_smem_bytes() {
-  return (size_t)TcCfg<KIND>::NST * (TcCfg<KIND>::NA + TcCfg<KIND>::NB) * TC_PLANE_BYTES + 1024;
+// Epilogue staging for EPI_Y: two 32-column chunks of the four output planes (128 rows x
+// 64 bytes x 4 planes each), written by the epilogue warps and stored by TMA.
+#define TC_STAGE_Y_BYTES (4 * TC_PLANE_BYTES)
+
+// Pipeline depth per kind and epilogue, sized so that one CTA per SM fits in shared memory
+// (and owns the tensor memory): > 114 KiB, <= 227 KiB.
+template <int KIND, int EPI>
+constexpr int tc_nst() {
+  return KIND == KIND_TEST ? 8 : (EPI == EPI_Y ? (KIND == KIND_CR ? 3 : 2) : (KIND == KIND_CR ? 4 : 3));
 }
+
+template <int KIND, int EPI>
+constexpr size_t tc_smem_bytes() {
+  return (size_t)tc_nst<KIND, EPI>() * (TcCfg<KIND>::NA + TcCfg<KIND>::NB) * TC_PLANE_BYTES +
+         (EPI == EPI_Y ? 2 * TC_STAGE_Y_BYTES : 0) + 1024;
+}
+
+__device__ __forceinline__ void tma_store_3d(const CUtensorMap* map, const void* src, int c0, int c1, int c2) {
+  asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%2, %3, %4}], [%1];" ::"l"(
+                   reinterpret_cast<uint64_t>(map)),
+               "r"(smem_u32(src)), "r"(c0), "r"(c1), "r"(c2)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read1() { asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read0() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+// AND of `pred` over the four epilogue warps (named barrier 2), uniform result
+__device__ __forceinline__ bool epi_all(bool pred) {
+  uint32_t out;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\t"
+      "setp.ne.u32 p, %1, 0;\n\t"
+      "barrier.red.and.pred q, 2, 128, p;\n\t"
+      "selp.u32 %0, 1, 0, q;\n\t}"
+      : "=r"(out)
+      : "r"((uint32_t)pred)
+      : "memory");
+  return out != 0;
+}
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+// named barrier of the four epilogue warps (ids 0 is __syncthreads)
+__device__ __forceinline__ void epi_barrier() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
 
 // Products of one 16-wide K slice.  Plane order of complex operands: re_hi, re_lo, im_hi,
 // im_lo; of real operands: hi, lo.  Accumulator 0 holds the real part (columns 0..127 of
@@ -305,9 +345,10 @@ __device__ __forceinline__ void tc_gemm_body(const Src& src, uint8_t* smem, uint
                                              uint64_t* tfull_bar, uint64_t* tempty_bar, uint64_t* done_bar,
                                              uint32_t* s_tmem_p, volatile int* s_abort_p) {
   using Cfg = TcCfg<KIND>;
-  constexpr int NA = Cfg::NA, NB = Cfg::NB, NST = Cfg::NST;
+  constexpr int NA = Cfg::NA, NB = Cfg::NB, NST = tc_nst<KIND, EPI>();
   constexpr uint32_t STAGE = (NA + NB) * TC_PLANE_BYTES;
   volatile int& s_abort = *s_abort_p;
+  uint8_t* const stage_y = smem + NST * STAGE;  // EPI_Y staging (2 x TC_STAGE_Y_BYTES)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int total = src.total();
   int* const status = src.status();
@@ -419,7 +460,8 @@ __device__ __forceinline__ void tc_gemm_body(const Src& src, uint8_t* smem, uint
   } else {
     // ---- epilogue warps 2..5: TMEM lane quarter (warp % 4) -> 32 output rows
     const int quarter = warp & 3;
-    int local = 0;
+    int local = 0, chunk = 0;
+    bool prev_committed = false;  // (issuing thread) the previous chunk committed a store
     for (int t = blockIdx.x; t < total; t += gridDim.x) {
       TileInfo ti;
       if (!src.decode(t, ti)) continue;
@@ -427,13 +469,18 @@ __device__ __forceinline__ void tc_gemm_body(const Src& src, uint8_t* smem, uint
       const int buf = local & 1;
       const uint32_t ph = (uint32_t)(local >> 1) & 1u;
       bool have = mbar_wait_bounded(&tfull_bar[buf], ph, &s_abort, status);
-      have = __all_sync(0xffffffffu, have && !s_abort);  // tcgen05.ld below is warp-collective
+      // one decision for all four epilogue warps: tcgen05.ld is warp-collective and the
+      // staged stores meet at named barriers
+      have = epi_all(have && !s_abort);
       if (!have) break;
       tc_fence_after();
       const int row = ti.out_row0 + quarter * 32 + lane;
       const uint32_t t_lane = tmem + buf * 256 + ((uint32_t)(quarter * 32) << 16);
+      // TMA stores write whole 128-row boxes: only where no row of the box belongs to
+      // another layer (rows past the tensor's end are clipped by the store itself)
+      const bool use_tma_y = EPI == EPI_Y && (ti.out_row0 + TC_BM <= ti.row_lim || ti.row_lim >= args.y_rows);
 #pragma unroll 1
-      for (int c0 = 0; c0 < TC_BN; c0 += 32) {
+      for (int c0 = 0; c0 < TC_BN; c0 += 32, ++chunk) {
         uint32_t re[32], im[32];
         tmem_ld32(t_lane + c0, re);
         if (KIND != KIND_TEST) tmem_ld32(t_lane + 128 + c0, im);
@@ -467,47 +514,61 @@ __device__ __forceinline__ void tc_gemm_body(const Src& src, uint8_t* smem, uint
             }
           }
         } else if (EPI == EPI_Y) {
-          if (row < ti.row_lim) {
-            const int nv = min(32, ti.n_valid - c0);
-            uint16_t* base = args.Y + (size_t)row * args.ldy + ti.out_col0 + c0;
-            if (nv == 32) {  // 64 contiguous bytes per plane: four 16-byte stores each
-              uint32_t prh[16], prl[16], pih[16], pil[16];
-#pragma unroll
-              for (int j = 0; j < 32; j += 2) {
-                uint16_t a0, a1, b0, b1, c0h, c1h, d0, d1;
-                split_hi_lo<F16>(__uint_as_float(re[j]) * args.scale, a0, b0);
-                split_hi_lo<F16>(__uint_as_float(re[j + 1]) * args.scale, a1, b1);
-                split_hi_lo<F16>(__uint_as_float(im[j]) * args.scale, c0h, d0);
-                split_hi_lo<F16>(__uint_as_float(im[j + 1]) * args.scale, c1h, d1);
-                prh[j / 2] = (uint32_t)a0 | ((uint32_t)a1 << 16);
-                prl[j / 2] = (uint32_t)b0 | ((uint32_t)b1 << 16);
-                pih[j / 2] = (uint32_t)c0h | ((uint32_t)c1h << 16);
-                pil[j / 2] = (uint32_t)d0 | ((uint32_t)d1 << 16);
-              }
-              uint4* q0 = reinterpret_cast<uint4*>(base);
-              uint4* q1 = reinterpret_cast<uint4*>(base + args.y_plane);
-              uint4* q2 = reinterpret_cast<uint4*>(base + 2 * args.y_plane);
-              uint4* q3 = reinterpret_cast<uint4*>(base + 3 * args.y_plane);
-#pragma unroll
-              for (int v = 0; v < 4; ++v) {
-                q0[v] = make_uint4(prh[4 * v], prh[4 * v + 1], prh[4 * v + 2], prh[4 * v + 3]);
-                q1[v] = make_uint4(prl[4 * v], prl[4 * v + 1], prl[4 * v + 2], prl[4 * v + 3]);
-                q2[v] = make_uint4(pih[4 * v], pih[4 * v + 1], pih[4 * v + 2], pih[4 * v + 3]);
-                q3[v] = make_uint4(pil[4 * v], pil[4 * v + 1], pil[4 * v + 2], pil[4 * v + 3]);
-              }
-            } else {
-#pragma unroll
-              for (int j = 0; j < 32; ++j)
-                if (j < nv) {
-                  uint16_t rh, rl, ih, il;
-                  split_hi_lo<F16>(__uint_as_float(re[j]) * args.scale, rh, rl);
-                  split_hi_lo<F16>(__uint_as_float(im[j]) * args.scale, ih, il);
-                  base[j] = rh;
-                  base[args.y_plane + j] = rl;
-                  base[2 * args.y_plane + j] = ih;
-                  base[3 * args.y_plane + j] = il;
-                }
+          const int nv = min(32, ti.n_valid - c0);
+          if (use_tma_y) {
+            // stage the chunk (64-byte swizzled, as the tensor map stores it), then one TMA store
+            uint8_t* buf = stage_y + (chunk & 1) * TC_STAGE_Y_BYTES;
+            if (lane == 0 && quarter == 0) {  // the buffer's previous store has read its data
+              if (prev_committed)
+                bulk_wait_read1();
+              else
+                bulk_wait_read0();
             }
+            epi_barrier();
+            const int r = quarter * 32 + lane;
+            uint32_t w[4][16];
+#pragma unroll
+            for (int j = 0; j < 32; j += 2) {
+              uint16_t a0, a1, b0, b1, c0h, c1h, d0, d1;
+              split_hi_lo<F16>(__uint_as_float(re[j]) * args.scale, a0, b0);
+              split_hi_lo<F16>(__uint_as_float(re[j + 1]) * args.scale, a1, b1);
+              split_hi_lo<F16>(__uint_as_float(im[j]) * args.scale, c0h, d0);
+              split_hi_lo<F16>(__uint_as_float(im[j + 1]) * args.scale, c1h, d1);
+              w[0][j / 2] = (uint32_t)a0 | ((uint32_t)a1 << 16);
+              w[1][j / 2] = (uint32_t)b0 | ((uint32_t)b1 << 16);
+              w[2][j / 2] = (uint32_t)c0h | ((uint32_t)c1h << 16);
+              w[3][j / 2] = (uint32_t)d0 | ((uint32_t)d1 << 16);
+            }
+#pragma unroll
+            for (int pl = 0; pl < 4; ++pl)
+#pragma unroll
+              for (int q = 0; q < 4; ++q) {
+                const int sw = q ^ ((r >> 1) & 3);
+                *reinterpret_cast<uint4*>(buf + pl * TC_PLANE_BYTES + r * 64 + sw * 16) =
+                    make_uint4(w[pl][4 * q], w[pl][4 * q + 1], w[pl][4 * q + 2], w[pl][4 * q + 3]);
+              }
+            fence_async_smem();
+            epi_barrier();
+            if (lane == 0 && quarter == 0) {
+              prev_committed = nv > 0;
+              if (nv > 0) {
+                tma_store_3d(src.mapC(ti), buf, ti.out_col0 + c0, ti.out_row0, 0);
+                bulk_commit();
+              }
+            }
+          } else if (row < ti.row_lim) {
+            uint16_t* base = args.Y + (size_t)row * args.ldy + ti.out_col0 + c0;
+#pragma unroll
+            for (int j = 0; j < 32; ++j)
+              if (j < nv) {
+                uint16_t rh, rl, ih, il;
+                split_hi_lo<F16>(__uint_as_float(re[j]) * args.scale, rh, rl);
+                split_hi_lo<F16>(__uint_as_float(im[j]) * args.scale, ih, il);
+                base[j] = rh;
+                base[args.y_plane + j] = rl;
+                base[2 * args.y_plane + j] = ih;
+                base[3 * args.y_plane + j] = il;
+              }
           }
         } else {
           if (row < args.M) {
@@ -523,6 +584,7 @@ __device__ __forceinline__ void tc_gemm_body(const Src& src, uint8_t* smem, uint
       if (lane == 0) mbar_arrive(&tempty_bar[buf]);
       ++local;
     }
+    if (EPI == EPI_Y && lane == 0 && quarter == 0) bulk_wait_all();  // staged stores complete
   }
   tc_fence_before();
   __syncthreads();
@@ -537,6 +599,7 @@ __device__ __forceinline__ void tc_gemm_body(const Src& src, uint8_t* smem, uint
 struct TcSingleSrc {
   const CUtensorMap* ma;
   const CUtensorMap* mb;
+  const CUtensorMap* mc;
   const TcGemmArgs* a;
   const int* s_off;
   int ktot;
@@ -547,6 +610,7 @@ struct TcSingleSrc {
   }
   __device__ const CUtensorMap* mapA(const TileInfo&) const { return ma; }
   __device__ const CUtensorMap* mapB(const TileInfo&) const { return mb; }
+  __device__ const CUtensorMap* mapC(const TileInfo&) const { return mc; }
   __device__ void acquire_maps(const CUtensorMap*, const CUtensorMap*) const {}
   __device__ const TcGemmArgs& args(const TileInfo&) const { return *a; }
   __device__ int* status() const { return a->status; }
@@ -555,8 +619,9 @@ struct TcSingleSrc {
 template <int KIND, int EPI, bool F16>
 __global__ void __launch_bounds__(192, 1) k_tc_gemm(const __grid_constant__ CUtensorMap mapA,
                                                      const __grid_constant__ CUtensorMap mapB,
+                                                     const __grid_constant__ CUtensorMap mapC,
                                                      const TcGemmArgs args) {
-  constexpr int NST = TcCfg<KIND>::NST;
+  constexpr int NST = tc_nst<KIND, EPI>();
   extern __shared__ uint8_t tc_smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)tc_smem_raw + 1023) & ~(uintptr_t)1023);
   __shared__ __align__(8) uint64_t full_bar[NST], empty_bar[NST], tfull_bar[2], tempty_bar[2], done_bar;
@@ -571,7 +636,7 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm(const __grid_constant__ CUte
       for (int q = 0; q < args.n_layers; ++q) s_off[q + 1] = (o += args.kr_pad[q]);
   }
   __syncthreads();
-  TcSingleSrc src{&mapA, &mapB, &args, s_off,
+  TcSingleSrc src{&mapA, &mapB, &mapC, &args, s_off,
                   args.mode == 2 ? (args.kr_pad ? s_off[args.n_layers] : args.K) : 0};
   tc_gemm_body<KIND, EPI, F16>(src, smem, full_bar, empty_bar, tfull_bar, tempty_bar, &done_bar, &s_tmem,
                                &s_abort);
@@ -582,6 +647,7 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm(const __grid_constant__ CUte
 struct alignas(128) TcBatchItem {
   CUtensorMap ma;
   CUtensorMap mb;
+  CUtensorMap mc;
   TcGemmArgs a;
   int unit0;
   int koff[CGH_MAX_LAYERS + 1];
@@ -610,12 +676,16 @@ struct TcBatchSrc {
   }
   __device__ const CUtensorMap* mapA(const TileInfo& ti) const { return &items[ti.item].ma; }
   __device__ const CUtensorMap* mapB(const TileInfo& ti) const { return &items[ti.item].mb; }
+  __device__ const CUtensorMap* mapC(const TileInfo& ti) const { return &items[ti.item].mc; }
   __device__ void acquire_maps(const CUtensorMap* a, const CUtensorMap* b) const {
     // tensor maps written to global memory by a copy before the launch
     asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(reinterpret_cast<uint64_t>(a))
                  : "memory");
     asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(reinterpret_cast<uint64_t>(b))
                  : "memory");
+    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(
+                     reinterpret_cast<uint64_t>(a + 2))
+                 : "memory");  // the store map follows the two load maps in the item
   }
   __device__ const TcGemmArgs& args(const TileInfo& ti) const { return items[ti.item].a; }
   __device__ int* status() const { return st; }
@@ -626,7 +696,7 @@ struct TcBatchSrc {
 template <int KIND, int EPI, bool F16>
 __global__ void __launch_bounds__(192, 1) k_tc_gemm_batch(const TcBatchItem* __restrict__ items, int n,
                                                            int total, int* status) {
-  constexpr int NST = TcCfg<KIND>::NST;
+  constexpr int NST = tc_nst<KIND, EPI>();
   extern __shared__ uint8_t tc_smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)tc_smem_raw + 1023) & ~(uintptr_t)1023);
   __shared__ __align__(8) uint64_t full_bar[NST], empty_bar[NST], tfull_bar[2], tempty_bar[2], done_bar;
@@ -691,21 +761,22 @@ static int make_plane_map(CUtensorMap* map, const void* base, int planes, long l
 template <int KIND, int EPI, bool F16>
 static cudaError_t set_gemm_attr() {
   cudaError_t e = cudaFuncSetAttribute(k_tc_gemm<KIND, EPI, F16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)tc_smem_bytes<KIND>());
+                                       (int)tc_smem_bytes<KIND, EPI>());
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(k_tc_gemm_batch<KIND, EPI, F16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)tc_smem_bytes<KIND>());
+                              (int)tc_smem_bytes<KIND, EPI>());
 }
 
 template <int KIND, int EPI, bool F16>
-static cudaError_t launch_gemm(const CUtensorMap& ma, const CUtensorMap& mb, TcGemmArgs a, dim3 tiles,
-                               cudaStream_t st) {
+static cudaError_t launch_gemm(const CUtensorMap& ma, const CUtensorMap& mb, const CUtensorMap& mc, TcGemmArgs a,
+                               dim3 tiles, cudaStream_t st) {
   a.tm = (int)tiles.x;
   a.tn = (int)tiles.y;
   a.tz = (int)tiles.z;
   const long long units = (long long)a.tm * a.tn * a.tz;
   const int grid = (int)(units < tc_num_sms() ? units : tc_num_sms());
   if (grid <= 0) return cudaSuccess;
-  return launch_pdl(k_tc_gemm<KIND, EPI, F16>, dim3(grid), dim3(192), tc_smem_bytes<KIND>(), st, ma, mb, a);
+  return launch_pdl(k_tc_gemm<KIND, EPI, F16>, dim3(grid), dim3(192), tc_smem_bytes<KIND, EPI>(), st, ma, mb, mc,
+                    a);
 }
 
