@@ -445,7 +445,8 @@ cudaError_t launch_plain_direct(const cgh_plan* p, const uint8_t* I, const uint8
 // (X pairs with the column difference, Y with the row difference).  A CTA owns a
 // 128x128 hologram tile and a 1/S share of every list (split over the grid's z),
 // stages 32 rank-1 terms at a time in shared memory as row and column factors and
-// accumulates 8x8 complex pixels per thread in registers (4 FFMA per term and pixel).
+// accumulates 8x8 complex pixels per thread in registers (two packed FP32x2 FMAs, i.e. 4
+// fused multiply-adds, per term and pixel).
 #define DL_TM 128
 #define DL_TN 128
 #define DL_KC 32
@@ -462,18 +463,20 @@ __global__ void __launch_bounds__(256, 1) k_direct_lut(
     const int32_t* __restrict__ l0, const int32_t* __restrict__ l1, const int32_t* __restrict__ l2,
     const int32_t* __restrict__ l3, const int32_t* __restrict__ d_counts, int H, int W, int Z, int s,
     float2* __restrict__ holo, int HH, int HW, int use_atomic) {
-  extern __shared__ float2 dl_smem[];
-  float2* Rs = dl_smem;                  // [DL_KC][DL_TM]
-  float2* Cs = dl_smem + DL_KC * DL_TM;  // [DL_KC][DL_TN]
+  // Row factors staged as (x, x, -y, y) and column factors as (x, y, y, x): a complex
+  // multiply-accumulate is then two packed FP32x2 FMAs, (x,x)*(cx,cy) + (-y,y)*(cy,cx).
+  extern __shared__ float4 dl_smem[];
+  float4* Rs = dl_smem;                  // [DL_KC][DL_TM]
+  float4* Cs = dl_smem + DL_KC * DL_TM;  // [DL_KC][DL_TN]
   __shared__ DlTerm s_term[DL_KC];
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   const int m0 = blockIdx.y * DL_TM, n0 = blockIdx.x * DL_TN;
   const int split = blockIdx.z, nsplit = gridDim.z;
-  float acc[8][8][2];
+  float2 acc[8][8];
 #pragma unroll
   for (int r = 0; r < 8; ++r)
 #pragma unroll
-    for (int c = 0; c < 8; ++c) acc[r][c][0] = acc[r][c][1] = 0.f;
+    for (int c = 0; c < 8; ++c) acc[r][c] = make_float2(0.f, 0.f);
 
   const int32_t* lists[4] = {l0, l1, l2, l3};
   for (int li = 0; li < 4; ++li) {
@@ -522,13 +525,13 @@ __global__ void __launch_bounds__(256, 1) k_direct_lut(
           const float2 b = tab[t.col_b + n], w = tab[t.col_w + n];
           cv = make_float2(t.cb * b.x + t.cw * w.x, t.cb * b.y + t.cw * w.y);
         }
-        Rs[k * DL_TM + r] = rv;
-        Cs[k * DL_TN + r] = cv;
+        Rs[k * DL_TM + r] = make_float4(rv.x, rv.x, -rv.y, rv.y);
+        Cs[k * DL_TN + r] = make_float4(cv.x, cv.y, cv.y, cv.x);
       }
       __syncthreads();
 #pragma unroll 2
       for (int k = 0; k < nt; ++k) {
-        float2 rv[8], cv[8];
+        float4 rv[8], cv[8];
 #pragma unroll
         for (int r = 0; r < 8; ++r) rv[r] = Rs[k * DL_TM + ty + 16 * r];
 #pragma unroll
@@ -537,10 +540,8 @@ __global__ void __launch_bounds__(256, 1) k_direct_lut(
         for (int r = 0; r < 8; ++r)
 #pragma unroll
           for (int c = 0; c < 8; ++c) {
-            acc[r][c][0] = fmaf(rv[r].x, cv[c].x, acc[r][c][0]);
-            acc[r][c][0] = fmaf(-rv[r].y, cv[c].y, acc[r][c][0]);
-            acc[r][c][1] = fmaf(rv[r].x, cv[c].y, acc[r][c][1]);
-            acc[r][c][1] = fmaf(rv[r].y, cv[c].x, acc[r][c][1]);
+            acc[r][c] = __ffma2_rn(make_float2(rv[r].x, rv[r].y), make_float2(cv[c].x, cv[c].y), acc[r][c]);
+            acc[r][c] = __ffma2_rn(make_float2(rv[r].z, rv[r].w), make_float2(cv[c].z, cv[c].w), acc[r][c]);
           }
       }
     }
@@ -553,9 +554,9 @@ __global__ void __launch_bounds__(256, 1) k_direct_lut(
       if (m < HH && n < HW) {
         float2* dst = holo + (size_t)m * HW + n;
         if (use_atomic)
-          atomicAdd(dst, make_float2(acc[r][c][0], acc[r][c][1]));
+          atomicAdd(dst, acc[r][c]);
         else
-          *dst = make_float2(acc[r][c][0], acc[r][c][1]);
+          *dst = acc[r][c];
       }
     }
 }
@@ -591,7 +592,7 @@ static int direct_lut_splits(int tiles) {
   return best;
 }
 
-#define DL_SMEM ((size_t)DL_KC * (DL_TM + DL_TN) * sizeof(float2))
+#define DL_SMEM ((size_t)DL_KC * (DL_TM + DL_TN) * sizeof(float4))
 
 cudaError_t basic_init_attributes() {
   return cudaFuncSetAttribute(k_direct_lut, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)DL_SMEM);
