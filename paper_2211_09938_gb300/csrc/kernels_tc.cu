@@ -412,6 +412,9 @@ static int tc_run(const cgh_plan* p, const int32_t* coef, const int32_t* const* 
   prof_mark(p, CGH_PROF_TC_STAGE1, 1, st);
   TC_CK(e, "tc: stage-1 GEMM");
   const int tm = (p->holo_h + TC_BM - 1) / TC_BM, tn = (p->holo_w + TC_BN - 1) / TC_BN;
+  // Stream-K over the (tile, K step) space (chains of at most 32 K steps, or the plan's
+  // cap) unless the plan asks for single-writer tiles (deterministic).
+  const int streamk = p->deterministic ? 0 : (p->max_ksteps > 0 ? p->max_ksteps : 32);
   int S = p->deterministic ? 1 : stage2_splits(tm * tn, t->ktot_alloc / TC_BK);
   if (!p->deterministic && p->max_ksteps > 0) {
     // cap the chain length on the actual K: sum of the layers' compacted rows is at most
@@ -421,6 +424,7 @@ static int tc_run(const cgh_plan* p, const int32_t* coef, const int32_t* const* 
     if (need > S) S = need;
   }
   stage2_args(p, F16, holo, S, a, tiles);
+  a.streamk = streamk;
   prof_mark(p, CGH_PROF_TC_STAGE2, 0, st);
   e = launch_gemm<KIND_CC, EPI_H, F16>(*mEZ, t->mY, t->mY, a, tiles, st);
   prof_mark(p, CGH_PROF_TC_STAGE2, 1, st);

@@ -149,6 +149,9 @@ struct TcGemmArgs {
   int n_layers;
   int M, N, K;       // test: sizes; stages: M and N of the output (K from the device)
   int tm, tn, tz;    // work units: M tiles x N tiles x (layers | K splits | 1)
+  int streamk;       // mode 2: equal slices of the (tile, K step) space per CTA instead of units,
+                     // cut into chains of at most `streamk` K steps (tensor-memory accumulation
+                     // error grows with the chain length)
   const int* a_kmap; // optional: A's K coordinate of every 32-wide K step (mode 1: per layer,
   int a_kmap_ld;     // a_kmap_ld entries apart; mode 2: one map over the concatenated K)
   float scale;
@@ -350,7 +353,6 @@ __device__ __forceinline__ void tc_gemm_body(const Src& src, uint8_t* smem, uint
   volatile int& s_abort = *s_abort_p;
   uint8_t* const stage_y = smem + NST * STAGE;  // EPI_Y staging (2 x TC_STAGE_Y_BYTES)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int total = src.total();
   int* const status = src.status();
 
   if (threadIdx.x == 0) {
@@ -386,9 +388,8 @@ __device__ __forceinline__ void tc_gemm_body(const Src& src, uint8_t* smem, uint
       uint32_t issued_ph[NST];
       for (int s = 0; s < NST; ++s) issued[s] = false, issued_ph[s] = 0;
       bool ok = true;
-      for (int t = blockIdx.x; t < total && ok; t += gridDim.x) {
-        TileInfo ti;
-        if (!src.decode(t, ti)) continue;
+      TileInfo ti;
+      for (int cur = src.begin(); ok && src.next(cur, ti);) {
         const CUtensorMap* mA = src.mapA(ti);
         const CUtensorMap* mB = src.mapB(ti);
         src.acquire_maps(mA, mB);
@@ -424,9 +425,8 @@ __device__ __forceinline__ void tc_gemm_body(const Src& src, uint8_t* smem, uint
       const uint32_t id_neg = idesc_f16(F16 ? 0 : 1, 1, TC_BM, TC_BN);
       int it = 0, local = 0;
       bool ok = true;
-      for (int t = blockIdx.x; t < total && ok; t += gridDim.x) {
-        TileInfo ti;
-        if (!src.decode(t, ti)) continue;
+      TileInfo ti;
+      for (int cur = src.begin(); ok && src.next(cur, ti);) {
         const int buf = local & 1;
         const uint32_t use_ph = (uint32_t)(local >> 1) & 1u;
         if (!mbar_wait_bounded(&tempty_bar[buf], use_ph ^ 1u, &s_abort, status)) break;
@@ -462,9 +462,8 @@ __device__ __forceinline__ void tc_gemm_body(const Src& src, uint8_t* smem, uint
     const int quarter = warp & 3;
     int local = 0, chunk = 0;
     bool prev_committed = false;  // (issuing thread) the previous chunk committed a store
-    for (int t = blockIdx.x; t < total; t += gridDim.x) {
-      TileInfo ti;
-      if (!src.decode(t, ti)) continue;
+    TileInfo ti;
+    for (int cur = src.begin(); src.next(cur, ti);) {
       const TcGemmArgs& args = src.args(ti);
       const int buf = local & 1;
       const uint32_t ph = (uint32_t)(local >> 1) & 1u;
@@ -608,6 +607,45 @@ struct TcSingleSrc {
     ti.item = 0;
     return decode_tile(*a, t, s_off, ktot, ti);
   }
+  // Units of this CTA.  Round robin over the work units, or (stream-K, split-K mode) one
+  // contiguous slice of the (tile, K step) space cut at tile boundaries.
+  __device__ int begin() const {
+    if (a->mode == 2 && a->streamk) {
+      const long long W = (long long)a->tm * a->tn * (ktot / TC_BK);
+      return (int)(W * blockIdx.x / gridDim.x);
+    }
+    return blockIdx.x;
+  }
+  __device__ bool next(int& cur, TileInfo& ti) const {
+    if (a->mode == 2 && a->streamk) {
+      const int nkt = ktot / TC_BK;
+      const long long W = (long long)a->tm * a->tn * nkt;
+      const int w1 = (int)(W * (blockIdx.x + 1) / gridDim.x);
+      if (nkt <= 0 || cur >= w1) return false;
+      const int tile = cur / nkt, kk = cur - tile * nkt;
+      const int seg = min(min(w1, (tile + 1) * nkt) - cur, a->streamk);
+      const int mt = tile % a->tm, nt = tile / a->tm;
+      ti.item = 0;
+      ti.akm = a->a_kmap ? a->a_kmap + kk : nullptr;
+      ti.a_row = mt * TC_BM;
+      ti.b_row = nt * TC_BN;
+      ti.k_lo = kk * TC_BK;
+      ti.nk = seg;
+      ti.out_row0 = mt * TC_BM;
+      ti.out_col0 = nt * TC_BN;
+      ti.n_valid = TC_BN;
+      ti.row_lim = a->M;
+      ti.col_lim = a->N;
+      cur += seg;
+      return true;
+    }
+    for (; cur < total(); cur += gridDim.x)
+      if (decode(cur, ti)) {
+        cur += gridDim.x;
+        return true;
+      }
+    return false;
+  }
   __device__ const CUtensorMap* mapA(const TileInfo&) const { return ma; }
   __device__ const CUtensorMap* mapB(const TileInfo&) const { return mb; }
   __device__ const CUtensorMap* mapC(const TileInfo&) const { return mc; }
@@ -660,6 +698,15 @@ struct TcBatchSrc {
   int n, tot;
   int* st;
   __device__ int total() const { return tot; }
+  __device__ int begin() const { return blockIdx.x; }
+  __device__ bool next(int& cur, TileInfo& ti) const {
+    for (; cur < tot; cur += gridDim.x)
+      if (decode(cur, ti)) {
+        cur += gridDim.x;
+        return true;
+      }
+    return false;
+  }
   __device__ bool decode(int t, TileInfo& ti) const {
     int lo = 0, hi = n - 1;
     while (lo < hi) {
@@ -773,7 +820,7 @@ static cudaError_t launch_gemm(const CUtensorMap& ma, const CUtensorMap& mb, con
   a.tm = (int)tiles.x;
   a.tn = (int)tiles.y;
   a.tz = (int)tiles.z;
-  const long long units = (long long)a.tm * a.tn * a.tz;
+  const long long units = a.streamk ? (long long)tc_num_sms() : (long long)a.tm * a.tn * a.tz;
   const int grid = (int)(units < tc_num_sms() ? units : tc_num_sms());
   if (grid <= 0) return cudaSuccess;
   return launch_pdl(k_tc_gemm<KIND, EPI, F16>, dim3(grid), dim3(192), tc_smem_bytes<KIND, EPI>(), st, ma, mb, mc,
