@@ -322,6 +322,34 @@ def run_phase_opt_workload(stream, steps):
 # our arm
 
 
+def run_level_sweep(plan, coeffs, lists, counts, I, L, stream, form, flush):
+    """Section 3's level sweep on the bench scene: for each cumulative stage (LLL, LL, L,
+    object) the operator count (Table 2), the SSIM of the reconstructed amplitude against
+    the plain point-wise hologram's (Table 3), and the device time of the stage's
+    superposition with L2 flushed; reconstruction and SSIM run in the library's kernels."""
+    import torch
+    from paper_2211_09938_gb300 import Plan
+    from paper_2211_09938_gb300.cgh import ssim
+    with torch.cuda.stream(stream):
+        _, ref = plan.reconstruct(plan.plain_direct(I, L, stream=stream), L, fields=False, stream=stream)
+        out = []
+        for stage, name in enumerate(Plan.LEVEL_STAGES):
+            c = Plan.level_counts(counts, stage)
+            H = plan.progressive_hologram(coeffs, lists, c, form=form, stream=stream)
+            flush.fill_(1.0)
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+            ev[0].record(stream)
+            plan.progressive_hologram(coeffs, lists, c, holo=H, form=form, stream=stream)
+            ev[1].record(stream)
+            _, A = plan.reconstruct(H, L, fields=False, stream=stream)
+            s = ssim(A, ref, stream=stream)
+            n = c[:, 0].cpu().numpy()
+            stream.synchronize()
+            out.append({"stage": name, "operators": int(n[0] + 4 * n[1:].sum()),
+                        "ssim_vs_pointwise": s.item(), "superposition_ms": ev[0].elapsed_time(ev[1])})
+    return {"form": form, "pointwise_operators": int(I.numel()), "stages": out}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -526,6 +554,8 @@ def run_ours(args):
         line["phase_opt"] = run_phase_opt_workload(stream, args.phase_opt_steps)
     if plain is not None:
         line["plain_direct"] = plain
+    if rank == 0 and not args.skip_level_sweep:
+        line["level_sweep"] = run_level_sweep(plan, coeffs, lists, counts, I, L, stream, form, flush)
     # the other superposition forms on the same scene (device ms of the superposition call)
     others = {}
     for f in ("direct_lut", "tc_bf16x3", "tc_fp16x3"):
@@ -573,6 +603,7 @@ def main():
     ap.add_argument("--skip-phase-opt", action="store_true", help="skip the phase-optimisation measurement")
     ap.add_argument("--phase-opt-steps", type=int, default=5)
     ap.add_argument("--skip-plain", action="store_true")
+    ap.add_argument("--skip-level-sweep", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:

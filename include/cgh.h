@@ -291,6 +291,22 @@ int cgh_phase_to_field(const float* phase, float* field, long long n, void* stre
 int cgh_phase_grad(const float* field, const float* grad_field, float* grad_phase, long long n, void* stream);
 
 /*
+ * cgh_ssim - mean SSIM of two reconstructed amplitude images, the quality measure of
+ * Section 3 (Table 3: each progressive level against the fully point-wise reconstruction).
+ * Wang et al. 2004 with an 11x11 Gaussian window (sigma 1.5) over the valid positions,
+ * K1 = 0.01, K2 = 0.03, data range 1.
+ *   x, y       device float [h][w] row-major, non-negative (amplitudes)
+ *   normalize  1: each image is divided by its own maximum first (amplitudes of different
+ *              holograms differ in scale); 0: used as given
+ *   out_mean   device double[1], overwritten with the mean SSIM
+ *   scratch    device 8 bytes (two uint32 maxima) when normalize = 1, else may be NULL
+ * Stream-ordered; the caller owns every buffer.
+ * Errors: CGH_ERR_ARG (NULL pointer, h or w outside [11, 65536]), CGH_ERR_CUDA.
+ */
+int cgh_ssim(const float* x, const float* y, int h, int w, int normalize, double* out_mean, void* scratch,
+             void* stream);
+
+/*
  * cgh_tc_selftest_gemm - diagnostic: C = A * B^T through the tensor-core machinery of the
  * separable form (TMA loads with 64-byte swizzle, shared-memory descriptors, tcgen05.mma
  * with FP32 accumulation in tensor memory), one real product, no hi+lo split.

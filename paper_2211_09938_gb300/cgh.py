@@ -53,6 +53,7 @@ SIGNATURES = {
     "cgh_amplitude_backward": (_I, [_P, _P, _P, _P, _P, _P]),
     "cgh_phase_to_field": (_I, [_P, _P, ctypes.c_longlong, _P]),
     "cgh_phase_grad": (_I, [_P, _P, _P, ctypes.c_longlong, _P]),
+    "cgh_ssim": (_I, [_P, _P, _I, _I, _I, _P, _P, _P]),
     "cgh_status": (_I, [_P, ctypes.POINTER(_I), _P]),
     "cgh_selftest_timeout": (_I, [_P, _I, _P]),
     "cgh_tc_selftest_gemm": (_I, [_P, _P, _P, _I, _I, _I, _I, _P]),
@@ -194,6 +195,21 @@ class Plan:
                                            _ptr(counts), _stream(stream)))
         return lists, counts
 
+    LEVEL_STAGES = ("LLL", "LL", "L", "object")
+    _STAGE_LISTS = ((0,), (0, 3), (0, 3, 2), (0, 3, 2, 1))
+
+    @classmethod
+    def level_counts(cls, counts, stage):
+        """Counts for the cumulative hologram at one stage of the progression of Section 2
+        (steps 2-5): 0 = LLL blocks only, 1 = + level-3 residuals (LL), 2 = + level 2 (L),
+        3 = + level 1 (object level, the full progressive hologram).  Lists left out get
+        zero counts; the lists themselves are not touched."""
+        c = counts.clone()
+        for k in range(4):
+            if k not in cls._STAGE_LISTS[stage]:
+                c[k].zero_()
+        return c
+
     def progressive_hologram(self, coeffs, lists, counts, holo=None, accumulate=False,
                              form="direct_lut", stream=None):
         import torch
@@ -306,6 +322,19 @@ def phase_grad(field, grad_field, out=None, stream=None):
     if out is None:
         out = torch.empty(field.shape, dtype=torch.float32, device=field.device)
     check(lib().cgh_phase_grad(_ptr(field), _ptr(grad_field), _ptr(out), field.numel(), _stream(stream)))
+    return out
+
+
+def ssim(x, y, normalize=True, out=None, stream=None):
+    """Mean SSIM of two float32 [h, w] CUDA images (cgh_ssim); returns a device float64
+    scalar tensor (read it with .item())."""
+    import torch
+    h, w = x.shape
+    if out is None:
+        out = torch.empty((), dtype=torch.float64, device=x.device)
+    scratch = torch.empty(2, dtype=torch.int32, device=x.device) if normalize else None
+    check(lib().cgh_ssim(_ptr(x), _ptr(y), h, w, 1 if normalize else 0, _ptr(out),
+                         _ptr(scratch) if scratch is not None else None, _stream(stream)))
     return out
 
 

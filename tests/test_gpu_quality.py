@@ -1,0 +1,154 @@
+"""Reconstruction quality on the GPU: the SSIM kernel and the level sweep of Section 3
+(Table 2: cumulative operator counts per level; Table 3: SSIM of each level against the
+fully point-wise reconstruction).
+
+cgh_ssim against the FP64 oracle SSIM: the kernel accumulates the Gaussian moments in
+FP32 about the window's centre value, so each local moment carries ~1e-7 relative
+rounding and the constants c1 = 1e-4, c2 = 9e-4 bound the denominators from below; the
+mean over windows is held to 1e-5 absolute.  Level sweep: at every cumulative stage
+(LLL, LL, L, object) the operator count matches the oracle's exactly and the GPU SSIM
+(direct hologram, tensor-core reconstruction) matches the oracle's to 1e-4; the SSIM
+rises stage by stage, as Table 3 reports, and the object-level operator count stays below
+half of the point-wise count (Section 3)."""
+import numpy as np
+import pytest
+
+from oracle import cgh_oracle as O
+from synth import scenes
+
+pytestmark = pytest.mark.gpu
+
+TOL_SSIM = 1e-5
+TOL_SWEEP = 1e-4
+STAGE_LISTS = ((0,), (0, 3), (0, 3, 2), (0, 3, 2, 1))
+STAGE_NAMES = ("LLL", "LL", "L", "object")
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    import os
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2211_09938_gb300 import build_lib, cgh
+    if not os.path.exists(cgh.LIB_PATH):
+        build_lib.build()
+    cgh.lib()
+    return torch
+
+
+@pytest.mark.parametrize("h,w", [(11, 11), (64, 64), (300, 257), (1024, 1024)])
+def test_ssim_matches_oracle(torch_cuda, h, w):
+    torch = torch_cuda
+    from paper_2211_09938_gb300.cgh import ssim
+    rng = np.random.default_rng(h * 7 + w)
+    x = rng.uniform(0, 3, size=(h, w)).astype(np.float32)
+    # a smooth field plus noise, so that windows span flat and textured regions
+    yy, xx = np.mgrid[0:h, 0:w]
+    y = (x * 0.6 + 1.2 * np.exp(-((yy - h / 2) ** 2 + (xx - w / 3) ** 2) / (0.1 * h * w))
+         + rng.normal(0, 0.2, size=(h, w))).clip(0).astype(np.float32)
+    xd, yd = torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda()
+    got = ssim(xd, yd).item()
+    x64, y64 = x.astype(np.float64), y.astype(np.float64)
+    ref = O.ssim(x64 / x64.max(), y64 / y64.max())
+    print(f"ssim {h}x{w}: gpu {got:.8f} oracle {ref:.8f} diff {abs(got - ref):.1e}")
+    assert abs(got - ref) <= TOL_SSIM
+    # unnormalised on [0, 1] data, and the identity
+    xn = torch.from_numpy(x / x.max()).cuda()
+    yn = torch.from_numpy((y / y.max()).astype(np.float32)).cuda()
+    assert abs(ssim(xn, yn, normalize=False).item()
+               - O.ssim((x / x.max()).astype(np.float64), (y / y.max()).astype(np.float32).astype(np.float64))) <= TOL_SSIM
+    assert abs(ssim(xd, xd).item() - 1.0) <= 1e-6
+
+
+def test_ssim_rejects_bad_sizes(torch_cuda):
+    torch = torch_cuda
+    from paper_2211_09938_gb300.cgh import CghError, ssim
+    x = torch.zeros((10, 40), device="cuda")
+    with pytest.raises(CghError):
+        ssim(x, x)
+
+
+def _stage_lists(lists, stage):
+    e = np.zeros(0, np.int32)
+    return [lists[k] if k in STAGE_LISTS[stage] else e for k in range(4)]
+
+
+def _gpu_sweep(torch, sc, form):
+    from paper_2211_09938_gb300 import Plan
+    from paper_2211_09938_gb300.cgh import ssim
+    plan = Plan.for_scene(sc)
+    I = torch.from_numpy(sc["intensity"]).cuda()
+    L = torch.from_numpy(sc["layer"]).cuda()
+    S = torch.from_numpy(sc["saliency"]).cuda()
+    coeffs = plan.haar_decompose(I, L)
+    lists, counts = plan.progressive_lists(S, L, scenes.THRESHOLDS_U8)
+    _, ref = plan.reconstruct(plan.plain_direct(I, L), L, fields=False)
+    out = []
+    for stage in range(4):
+        c = Plan.level_counts(counts, stage)
+        H = plan.progressive_hologram(coeffs, lists, c, form=form)
+        _, A = plan.reconstruct(H, L, fields=False)
+        n = c[:, 0].cpu().numpy()
+        ops = int(n[0] + 4 * n[1:].sum())
+        out.append((ops, ssim(A, ref).item()))
+    torch.cuda.synchronize()
+    return out
+
+
+@pytest.mark.parametrize("form", ["direct_lut", "tc_bf16x3"])
+def test_level_sweep_matches_oracle(torch_cuda, form):
+    torch = torch_cuda
+    sc = scenes.random_scene(91, 64, 128, 3, graded=True)
+    g = O.geometry_of(sc)
+    lists = O.progressive_lists(sc["saliency"], sc["layer"], g.n_layers, scenes.THRESHOLDS_U8)
+    Hf = O.plain_pointwise_hologram(sc["intensity"], sc["layer"], g)
+    ref = O.composite_amplitude(O.reconstruct_fields(Hf, g), sc["layer"])
+    want = []
+    for stage in range(4):
+        st = _stage_lists(lists, stage)
+        a = O.composite_amplitude(O.reconstruct_fields(O.progressive_hologram(
+            sc["intensity"], sc["layer"], st, g), g), sc["layer"])
+        want.append((O.operator_count(st), O.ssim(a / a.max(), ref / ref.max())))
+    got = _gpu_sweep(torch, sc, form)
+    for stage, ((og, sg), (ow, sw)) in enumerate(zip(got, want)):
+        print(f"{form} {STAGE_NAMES[stage]}: operators {og} (oracle {ow}) ssim {sg:.6f} (oracle {sw:.6f})")
+        assert og == ow
+        assert abs(sg - sw) <= TOL_SWEEP
+    assert all(got[k][1] < got[k + 1][1] for k in range(3))
+
+
+def test_level_sweep_paper_scale_shape(torch_cuda):
+    """512x512 object, 16 layers, 1024x1024 hologram: operators rise with each stage and
+    stay below half of the point-wise 512^2 at the object level; SSIM rises with each stage."""
+    torch = torch_cuda
+    sc = scenes.paper_scene()
+    got = _gpu_sweep(torch, sc, "tc_bf16x3")
+    for stage, (ops, s) in enumerate(got):
+        print(f"paper scale {STAGE_NAMES[stage]}: operators {ops} ssim {s:.5f}")
+    ops = [o for o, _ in got]
+    ss = [s for _, s in got]
+    assert ops == sorted(ops) and ops[-1] < sc["intensity"].size // 2
+    assert all(ss[k] < ss[k + 1] for k in range(3))
+    assert 0.0 < ss[0] and ss[-1] <= 1.0
+
+
+def test_all_salient_equals_pointwise(torch_cuda):
+    """With every occupied block selected at every level the progressive hologram is the
+    point-wise one (Section 2): SSIM 1 against the plain direct sum."""
+    torch = torch_cuda
+    from paper_2211_09938_gb300 import Plan
+    from paper_2211_09938_gb300.cgh import ssim
+    sc = scenes.random_scene(92, 128, 256, 4)
+    plan = Plan.for_scene(sc)
+    I = torch.from_numpy(sc["intensity"]).cuda()
+    L = torch.from_numpy(sc["layer"]).cuda()
+    S = torch.from_numpy(sc["saliency"]).cuda()
+    coeffs = plan.haar_decompose(I, L)
+    lists, counts = plan.progressive_lists(S, L, {1: -1, 2: -1, 3: -1})
+    _, ref = plan.reconstruct(plan.plain_direct(I, L), L, fields=False)
+    _, A = plan.reconstruct(plan.progressive_hologram(coeffs, lists, counts, form="tc_bf16x3"), L,
+                            fields=False)
+    s = ssim(A, ref).item()
+    print(f"all-salient ssim {s:.8f}")
+    assert abs(s - 1.0) <= 1e-5
