@@ -30,8 +30,8 @@ object saliency"):
   plane is A_z = I * [layer == z] and each plane has its own DWT and fringes
   (the per-depth extension sketched at the end of Section 2).
 * Reconstruction (Section 2, last paragraph) by Fresnel back-propagation,
-  i.e. the adjoint of the per-layer forward operator, and SSIM (Section 3)
-  after Wang et al. 2004.
+  i.e. the adjoint of the per-layer forward operator, or by the inverse angular
+  spectrum method the paper names, and SSIM (Section 3) after Wang et al. 2004.
 
 Readings where the paper is silent or garbled (distance term of Eq. 1, sign,
 amplitude, thresholds, saliency scale, residual definition, depth handling,
@@ -429,6 +429,52 @@ def reconstruct_fields(H, geom, n_obj=None):
         Ex = point_fringe_1d(mi, geom.a(z))
         Ey = point_fringe_1d(nj, geom.a(z))
         R[z] = Ex.conj().T @ H @ Ey.conj()
+    return R
+
+
+def asm_transfer(geom, k, P, band_limit=False):
+    """Angular-spectrum transfer function that back-propagates the hologram plane by z_k
+    (to layer k's plane) on a P x P DFT grid of pitch p (Section 2, last paragraph:
+    inverse angular spectrum at the scene's own parameters).  A plane wave of spatial frequency (fx, fy) advances by
+    2 pi z sqrt(1/lambda^2 - fx^2 - fy^2) over a distance z; back-propagation takes that
+    phase off.  The common carrier exp(j 2 pi z / lambda) is removed (the holograms here
+    omit it), so T = exp(-j 2 pi z (sqrt(1/lambda^2 - f^2) - 1/lambda)); evanescent
+    frequencies (f >= 1/lambda) get 0.  band_limit additionally zeroes |fx| or |fy| above
+    1 / (lambda sqrt((2 df z)^2 + 1)), df = 1/(P p) (Matsushima and Shimobaba 2009)."""
+    f = np.fft.fftfreq(P, d=geom.pitch)
+    fx, fy = f[None, :], f[:, None]
+    lam, z = geom.wavelength, geom.z[k]
+    arg = 1.0 / lam ** 2 - fx ** 2 - fy ** 2
+    prop = arg > 0
+    T = np.where(prop, np.exp(-2j * np.pi * z * (np.sqrt(np.where(prop, arg, 0.0)) - 1.0 / lam)), 0.0)
+    if band_limit:
+        df = 1.0 / (P * geom.pitch)
+        flim = 1.0 / (lam * np.sqrt((2.0 * df * z) ** 2 + 1.0))
+        T = T * ((np.abs(fx) <= flim) & (np.abs(fy) <= flim))
+    return T
+
+
+def asm_reconstruct_fields(H, geom, pad=2, band_limit=False):
+    """Reconstruction by the inverse angular spectrum method (Section 2, last paragraph),
+    sampled on the object grid: the hologram is zero-padded to P = pad * holo (pad 2 makes
+    the DFT's circular convolution a linear one), transformed, multiplied by each layer's
+    back-propagation transfer function, inverse transformed and read at the object
+    pixels (s i, s j).  Scaled by p^2 / (lambda z) so that an unbounded Fresnel point
+    fringe of amplitude A comes back as A at its point (the Fresnel kernel's
+    1 / (j lambda z) per unit area, which the holograms omit)."""
+    H = np.asarray(H, dtype=np.complex128)
+    P = pad * geom.holo_h
+    if geom.holo_h != geom.holo_w:
+        raise ValueError("square holograms only")
+    Hp = np.zeros((P, P), dtype=np.complex128)
+    Hp[:geom.holo_h, :geom.holo_w] = H
+    X = np.fft.fft2(Hp)
+    oh, ow = geom.holo_h // geom.s, geom.holo_w // geom.s
+    R = np.empty((geom.n_layers, oh, ow), dtype=np.complex128)
+    for k in range(geom.n_layers):
+        U = np.fft.ifft2(X * asm_transfer(geom, k, P, band_limit))
+        scale = geom.pitch ** 2 / (geom.wavelength * geom.z[k])
+        R[k] = scale * U[:geom.s * oh:geom.s, :geom.s * ow:geom.s]
     return R
 
 

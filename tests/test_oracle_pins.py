@@ -479,3 +479,120 @@ def test_phase_opt_gradient_matches_finite_differences():
         fd = (O.phase_opt_loss(phase + e, target, weight, layer, g, kappa)
               - O.phase_opt_loss(phase - e, target, weight, layer, g, kappa)) / (2 * h)
         assert abs(fd - grad[m, n]) <= 1e-6 * max(1.0, abs(fd)), (m, n, fd, grad[m, n])
+
+
+# ---------------------------------------------------------------- angular spectrum (A1-A5)
+
+def _signed(k, P):
+    return k if k < P // 2 else k - P
+
+
+def test_asm_brute_force_tiny():
+    """A1: the ASM reconstruction against its definition written as explicit sums: the
+    forward DFT of the zero-padded hologram, the plane-wave phase advance through the
+    direction cosine gamma = sqrt(1 - (lambda fx)^2 - (lambda fy)^2), the inverse DFT at
+    the object pixels (s i, s j), and the p^2/(lambda z) scale.  Catches a DFT sign or
+    normalisation slip, frequency ordering, the sampling stride and a transposed axis."""
+    rng = np.random.default_rng(51)
+    n, s = 4, 2
+    g = O.Geometry((n, n), (n * s, n * s), PITCH, LAM, [0.004, 0.0065])
+    N = n * s
+    H = rng.normal(size=(N, N)) + 1j * rng.normal(size=(N, N))
+    H[0, 1] += 3.0  # break any symmetry between the axes
+    for pad in (1, 2):
+        P = pad * N
+        X = np.zeros((P, P), complex)
+        for k in range(P):
+            for l in range(P):
+                acc = 0j
+                for m in range(N):
+                    for q in range(N):
+                        acc += H[m, q] * np.exp(-2j * np.pi * (k * m + l * q) / P)
+                X[k, l] = acc
+        R = O.asm_reconstruct_fields(H, g, pad=pad)
+        for zi in range(2):
+            z = g.z[zi]
+            for i in range(n):
+                for j in range(n):
+                    acc = 0j
+                    for k in range(P):
+                        for l in range(P):
+                            sy, sx = LAM * _signed(k, P) / (P * PITCH), LAM * _signed(l, P) / (P * PITCH)
+                            gamma = np.sqrt(1.0 - sx * sx - sy * sy)
+                            T = np.exp(-2j * np.pi * z * (gamma - 1.0) / LAM)
+                            acc += X[k, l] * T * np.exp(2j * np.pi * (k * s * i + l * s * j) / P)
+                    want = acc / P ** 2 * PITCH ** 2 / (LAM * z)
+                    assert abs(R[zi, i, j] - want) <= 1e-12 * max(1.0, abs(want)), (pad, zi, i, j)
+
+
+def test_asm_is_unitary():
+    """A2: |T| = 1 on propagating waves, so with no padding and s = 1 the back-propagated
+    field has the hologram's energy (Parseval), up to the p^2/(lambda z) scale."""
+    rng = np.random.default_rng(52)
+    g = O.Geometry((32, 32), (32, 32), PITCH, LAM, [0.05, 0.12])
+    H = rng.normal(size=(32, 32)) + 1j * rng.normal(size=(32, 32))
+    R = O.asm_reconstruct_fields(H, g, pad=1)
+    for zi in range(2):
+        scale = PITCH ** 2 / (LAM * g.z[zi])
+        assert abs(np.linalg.norm(R[zi]) / scale / np.linalg.norm(H) - 1.0) < 1e-12
+
+
+def test_asm_plane_wave_phase():
+    """A3: a grid plane wave exp(j 2 pi (ky m + kx n) / N) comes back as itself times
+    exp(-j k z (cos(theta) - 1)), cos(theta) the direction cosine along the axis."""
+    N = 64
+    g = O.Geometry((N, N), (N, N), PITCH, LAM, [0.1])
+    m = np.arange(N)
+    for ky, kx in ((0, 0), (5, -3), (-31, 17), (32, 32)):
+        H = np.exp(2j * np.pi * (ky * m[:, None] + kx * m[None, :]) / N)
+        R = O.asm_reconstruct_fields(H, g, pad=1)[0] / (PITCH ** 2 / (LAM * 0.1))
+        sin2 = (LAM * ky / (N * PITCH)) ** 2 + (LAM * kx / (N * PITCH)) ** 2
+        cos_t = np.sqrt(1.0 - sin2)
+        want = H * np.exp(-2j * np.pi / LAM * 0.1 * (cos_t - 1.0))
+        assert np.max(np.abs(R - want)) < 1e-9
+
+
+def test_asm_transfer_fresnel_limit():
+    """A4: for lambda f << 1 the transfer function tends to the Fresnel one,
+    exp(+j pi lambda z f^2) (the sign that back-propagates the point fringes of Eq. 1),
+    with the next term (z / lambda) (lambda f)^4 / 8 cycles bounding the difference."""
+    g = O.Geometry((64, 64), (64, 64), PITCH, LAM, [0.2])
+    P = 64
+    T = O.asm_transfer(g, 0, P)
+    f = np.fft.fftfreq(P, d=PITCH)
+    f2 = f[None, :] ** 2 + f[:, None] ** 2
+    fres = np.exp(1j * np.pi * LAM * 0.2 * f2)
+    err_cycles = np.abs(np.angle(T * np.conj(fres))) / (2 * np.pi)
+    bound = 1.05 * (0.2 / LAM) * (LAM * LAM * f2) ** 2 / 8.0 + 1e-12
+    assert np.all(err_cycles <= bound)
+    assert np.all(np.abs(np.abs(T) - 1.0) < 1e-12)
+
+
+def test_asm_refocuses_a_point_fringe():
+    """A5: the Fresnel point fringe of one object pixel (Eq. 1) reconstructs with its
+    amplitude maximum at that pixel, for both paddings and several layers."""
+    n, s = 16, 4
+    g = O.Geometry((n, n), (n * s, n * s), PITCH, LAM, [0.02, 0.03])
+    for zi in range(2):
+        for (i, j) in ((3, 4), (8, 8), (12, 2)):
+            F = np.zeros((2, n, n), complex)
+            F[zi, i, j] = 1.0
+            H = O.propagate_fields(F, g)
+            for pad in (1, 2):
+                A = np.abs(O.asm_reconstruct_fields(H, g, pad=pad)[zi])
+                assert np.unravel_index(np.argmax(A), A.shape) == (i, j), (zi, i, j, pad)
+
+
+def test_asm_band_limit():
+    """A6: the band limit zeroes exactly the frequencies with |fx| or |fy| above
+    1 / (lambda sqrt((2 df z)^2 + 1)), and changes nothing when that exceeds Nyquist."""
+    g = O.Geometry((64, 64), (64, 64), PITCH, LAM, [0.2, 0.001])
+    P = 64
+    T0, T1 = O.asm_transfer(g, 0, P), O.asm_transfer(g, 0, P, band_limit=True)
+    df = 1.0 / (P * PITCH)
+    k = np.array([_signed(x, P) for x in range(P)])
+    lim = 1.0 / (LAM * np.sqrt((2 * df * 0.2) ** 2 + 1.0))
+    keep = (np.abs(k)[None, :] * df <= lim) & (np.abs(k)[:, None] * df <= lim)
+    assert 0 < keep.sum() < P * P
+    assert np.array_equal(T1 != 0, keep) and np.allclose(T1[keep], T0[keep], rtol=0, atol=0)
+    assert np.array_equal(O.asm_transfer(g, 1, P, band_limit=True), O.asm_transfer(g, 1, P))
