@@ -245,6 +245,34 @@ int cgh_reconstruct(const cgh_plan* plan, const float* holo, float* fields,
                     const uint8_t* layer_idx, float* amplitude, void* stream);
 
 /*
+ * cgh_reconstruct_asm - reconstruction by the inverse angular spectrum method, the one the
+ * paper renders its results with (Section 2, last paragraph: "inverse angular spectrum ...
+ * using the same parameters of the scene").
+ *   P = pad * holo edge; the hologram is zero-padded to P x P (pad 2: linear convolution),
+ *   X = DFT_PxP(holo); per layer z
+ *     T_z(fx, fy) = exp(-j*2*pi*z*(sqrt(1/lambda^2 - fx^2 - fy^2) - 1/lambda)),
+ *     fx, fy = signed DFT index / (P*p); 0 for evanescent waves and, with band_limit = 1,
+ *     for |fx| or |fy| above 1/(lambda*sqrt((2*z/(P*p))^2 + 1)) (Matsushima-Shimobaba
+ *     band limit);
+ *     R_z(i, j) = p^2/(lambda*z) * IDFT_PxP(X * T_z)(s*i, s*j)   (IDFT normalised by 1/P^2).
+ * The carrier exp(j*2*pi*z/lambda) is left out of T_z (the holograms omit it) and the
+ * p^2/(lambda*z) factor makes an unbounded point fringe reconstruct to its amplitude.
+ * All arithmetic FP32: hand-written shared-memory FFTs (radix 8), the phase of T_z
+ * reduced exactly in 64-bit fixed point.  Square power-of-two hologram, power-of-two s,
+ * P and P/s in [64, 4096].
+ *   holo       complex64 [holo_h][holo_w]
+ *   fields     complex64 [Z][obj_h][obj_w] output, or NULL
+ *   layer_idx  uint8 [obj_h][obj_w] (needed when amplitude != NULL)
+ *   amplitude  float [obj_h][obj_w] output |R_{layer(i,j)}(i,j)| (0 where layer >= Z), or NULL
+ *   pad        1 or 2;  band_limit 0 or 1
+ * The first call for a padding allocates the plan's buffers (8*(holo*P + P*P + Z*obj*P/s)
+ * bytes) and synchronises `stream` once; later calls only enqueue.
+ * Errors: CGH_ERR_ARG, CGH_ERR_UNSUPPORTED (geometry), CGH_ERR_NOMEM, CGH_ERR_CUDA.
+ */
+int cgh_reconstruct_asm(const cgh_plan* plan, const float* holo, float* fields, const uint8_t* layer_idx,
+                        float* amplitude, int pad, int band_limit, void* stream);
+
+/*
  * cgh_propagate - point-source hologram of complex layer fields: the adjoint of
  * cgh_reconstruct.  Paper: Eq. 1 (the superposition of point fringes, layer by layer).
  *   holo(m,n) (+)= sum_z sum_{i,j} fields[z](i,j) * f_z(m-s*i) * f_z(n-s*j)
@@ -371,7 +399,9 @@ int cgh_batch_destroy(cgh_batch* batch);
 #define CGH_PROF_PLAIN 7       /* plain point-wise kernel               */
 #define CGH_PROF_RECON 8       /* reconstruction                        */
 #define CGH_PROF_PROPAGATE 9   /* propagation of layer fields            */
-#define CGH_PROF_SLOTS 10
+#define CGH_PROF_ASM_FFT 10    /* angular spectrum: forward 2-D FFT      */
+#define CGH_PROF_ASM_INV 11    /* angular spectrum: transfer + inverse FFTs */
+#define CGH_PROF_SLOTS 12
 
 /*
  * cgh_profile - enable (1) or disable (0) CUDA-event timing around the plan's internal

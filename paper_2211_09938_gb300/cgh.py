@@ -48,6 +48,7 @@ SIGNATURES = {
     "cgh_progressive_hologram": (_I, [_P, _P, ctypes.POINTER(_P), _P, _P, _I, _I, _P]),
     "cgh_plain_direct": (_I, [_P, _P, _P, _P, _P]),
     "cgh_reconstruct": (_I, [_P, _P, _P, _P, _P, _P]),
+    "cgh_reconstruct_asm": (_I, [_P, _P, _P, _P, _P, _I, _I, _P]),
     "cgh_propagate": (_I, [_P, _P, _P, _I, _P]),
     "cgh_adjoint": (_I, [_P, _P, ctypes.POINTER(_P), _P, _P, _P, _P]),
     "cgh_amplitude_backward": (_I, [_P, _P, _P, _P, _P, _P]),
@@ -244,6 +245,22 @@ class Plan:
                                     _stream(stream)))
         return f, a
 
+    def reconstruct_asm(self, holo, layer=None, fields=True, amplitude=True, pad=2, band_limit=False,
+                        stream=None):
+        """Inverse angular-spectrum reconstruction (cgh_reconstruct_asm): (fields [Z, obj, obj]
+        complex64 or None, amplitude [obj, obj] float32 or None)."""
+        import torch
+        if fields is True:
+            fields = torch.empty((self.n_layers, self.obj_h, self.obj_w), dtype=torch.complex64,
+                                 device=self.device)
+        if amplitude is True:
+            amplitude = torch.empty((self.obj_h, self.obj_w), dtype=torch.float32, device=self.device)
+        f = fields if fields is not False else None
+        a = amplitude if amplitude is not False else None
+        check(lib().cgh_reconstruct_asm(self.handle, _ptr(holo), _ptr(f), _ptr(layer), _ptr(a), int(pad),
+                                        1 if band_limit else 0, _stream(stream)))
+        return f, a
+
     def propagate(self, fields, holo=None, accumulate=False, stream=None):
         import torch
         if holo is None:
@@ -270,7 +287,7 @@ class Plan:
         return out
 
     PROF_SLOTS = ["tables", "haar", "select", "direct_lut", "tc_prep", "tc_stage1", "tc_stage2",
-                  "plain", "recon", "propagate"]
+                  "plain", "recon", "propagate", "asm_fft", "asm_inv"]
 
     def profile(self, enable=True):
         check(lib().cgh_profile(self.handle, 1 if enable else 0))

@@ -47,6 +47,7 @@ int cgh_plan_destroy(cgh_plan* p) {
   tc_destroy(p);
   field_destroy(p);
   eops_destroy(p);
+  asm_destroy(p);
   cudaFree(p->d_tab);
   cudaFree(p->d_f64);
   cudaFree(p->d_a_frac);
@@ -136,7 +137,7 @@ int cgh_plan_create(cgh_plan** out, int obj_h, int obj_w, int holo_h, int holo_w
   p->f_len = p->tab_len + 7 * p->s;
   PLAN_TRY(cudaMalloc(&p->d_f64, (size_t)n_layers * p->f_len * sizeof(double2)), "cgh_plan_create: fringe");
   PLAN_TRY(basic_init_attributes(), "cgh_plan_create: kernel attributes");
-  if (tc_init_attributes() != CGH_OK || field_init_attributes() != CGH_OK) {
+  if (tc_init_attributes() != CGH_OK || field_init_attributes() != CGH_OK || asm_init_attributes() != CGH_OK) {
     cgh_plan_destroy(p);
     return CGH_ERR_CUDA;
   }

@@ -46,6 +46,8 @@ struct cgh_plan {
   struct cgh_field_state* fs;
   // Fringe operand planes E_z by rows / columns, per dtype (allocated lazily).
   struct cgh_eops* eops;
+  // Angular-spectrum reconstruction buffers (allocated lazily).
+  struct cgh_asm_state* asmst;
 
   // CUDA-event profiling of the internal stages (cgh_profile).
   int prof_on;
@@ -152,3 +154,7 @@ struct CUtensorMap_st;
 int eops_get(const cgh_plan* p, int f16, const struct CUtensorMap_st** mEZ, const struct CUtensorMap_st** mEZt,
              cudaStream_t st);
 void eops_destroy(cgh_plan* p);
+
+// Angular-spectrum reconstruction (kernels_asm.cu).
+int asm_init_attributes();
+void asm_destroy(cgh_plan* p);
