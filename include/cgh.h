@@ -258,7 +258,7 @@ int cgh_reconstruct(const cgh_plan* plan, const float* holo, float* fields,
  * The carrier exp(j*2*pi*z/lambda) is left out of T_z (the holograms omit it) and the
  * p^2/(lambda*z) factor makes an unbounded point fringe reconstruct to its amplitude.
  * All arithmetic FP32: hand-written shared-memory FFTs (radix 8), the phase of T_z
- * reduced exactly in 64-bit fixed point.  Square power-of-two hologram, power-of-two s,
+ * reduced exactly in 64-bit fixed point.  Square power-of-two hologram, s in {1, 2, 4, 8},
  * P and P/s in [64, 4096].
  *   holo       complex64 [holo_h][holo_w]
  *   fields     complex64 [Z][obj_h][obj_w] output, or NULL

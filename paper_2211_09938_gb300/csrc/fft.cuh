@@ -133,8 +133,10 @@ struct Smem {
 #ifdef __CUDACC__
 // Transforms the B lines of one tile.  T threads; B * L / T elements live in each thread's
 // registers during a pass.  ld(b, i) -> float2 gives input element i of line b; st(b, i, v)
-// receives output element i.  s must hold Smem<L, B>::floats2 float2 values.
-template <int L, int B, int T, bool INV, class Ld, class St>
+// receives output element i.  s must hold Smem<L, B>::floats2 float2 values.  LD_SMEM:
+// the loader reads the tile from s itself (filled by the caller, followed by a barrier),
+// so pass 0 waits for every thread's loads before it overwrites s.
+template <int L, int B, int T, bool INV, bool LD_SMEM = false, class Ld, class St>
 __device__ __forceinline__ void fft_tile(float2* s, const float2* __restrict__ tw, Ld&& ld, St&& st) {
   using S = Smem<L, B>;
   constexpr int NP = n_passes(L);
@@ -152,6 +154,7 @@ __device__ __forceinline__ void fft_tile(float2* s, const float2* __restrict__ t
 #pragma unroll
       for (int r = 0; r < R; ++r) v[g][r] = ld(b, j + r * G);
     }
+    if constexpr (LD_SMEM) __syncthreads();
 #pragma unroll
     for (int g = 0; g < NG; ++g) {
       const int gi = threadIdx.x + g * T, b = gi % B, j = gi / B;

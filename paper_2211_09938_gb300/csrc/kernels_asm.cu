@@ -30,7 +30,8 @@
 #include "cgh_internal.h"
 #include "fft.cuh"
 
-#define ASM_T 256       // threads per CTA
+#define ASM_T 512       // threads per CTA
+#define ASM_MINB 2      // CTAs per SM the register budget is sized for (64 registers a thread)
 #define ASM_TILE 8192   // elements per tile: B lines of length L with B * L = ASM_TILE
 
 struct AsmLayer {
@@ -43,6 +44,7 @@ struct AsmLayer {
 
 struct cgh_asm_state {
   int P, pad, band_limit;
+  int exact;          // 1: exact correction term with band-limit / evanescent checks; 0: series, no checks
   float2* Xr;         // [Nh][P]
   float2* X;          // [P][P]
   float2* Y;          // [Z][No][P/s]
@@ -50,24 +52,38 @@ struct cgh_asm_state {
   AsmLayer* layers;   // [Z]
 };
 
-__device__ __forceinline__ float2 asm_transfer(const AsmLayer& a, int ky, int kx, int P) {
-  const int sy = ky < (P >> 1) ? ky : ky - P;
-  const int sx = kx < (P >> 1) ? kx : kx - P;
-  if (abs(sy) > a.kmax || abs(sx) > a.kmax) return make_float2(0.f, 0.f);
-  const unsigned int q = (unsigned int)(sy * sy + sx * sx);
-  const float u = a.c * (float)q;
-  if (u >= 1.f) return make_float2(0.f, 0.f);  // evanescent
-  const unsigned long long ph = a.bfix * (unsigned long long)q;  // frac(b q) in units of 2^-64
-  const float fres = (float)(unsigned int)(ph >> 40) * 5.9604644775390625e-8f;  // top 24 bits / 2^24
-  const float d = 1.f + sqrtf(1.f - u);
-  const float corr = a.zl * u * u / (2.f * d * d);
+// exp(j 2 pi (b q + corr(u))) from the Fresnel phase fr = frac(b q) in [-1/2, 1/2) cycles
+// (from the fixed-point sum) and u = c q.  EXACT: corr = (z/lambda) u^2 / (2 (1 + sqrt(1-u))^2)
+// with rsqrtf / __fdividef; otherwise its power series (z/lambda) sum_{n=2..6} c_n u^n, c_n the
+// coefficients of 1 - sqrt(1-u) = u/2 + u^2/8 + u^3/16 + 5u^4/128 + 7u^5/256 + 21u^6/1024 + ...,
+// used only when the host has bounded the truncated tail below 1e-8 cycles.  The phase is
+// reduced to [-1/2, 1/2] cycles before __sincosf; each step stays within a few 1e-7 of the
+// exact value, far below the FFTs' own rounding budget.
+template <bool EXACT>
+__device__ __forceinline__ float2 asm_phasor(float fr, float u, float zl) {
+  float corr;
+  if constexpr (EXACT) {
+    const float w = 1.f - u;
+    const float d = 1.f + w * rsqrtf(w);  // 1 + sqrt(1 - u)
+    corr = __fdividef(zl * u * u, 2.f * d * d);
+  } else {
+    const float poly = fmaf(u, fmaf(u, fmaf(u, fmaf(u, 0.0205078125f, 0.02734375f), 0.0390625f), 0.0625f), 0.125f);
+    corr = zl * (u * u) * poly;
+  }
+  float t = fr + corr;
+  t -= rintf(t);
   float sn, cs;
-  sincospif(2.f * (fres + corr), &sn, &cs);
+  __sincosf(6.28318530717958648f * t, &sn, &cs);
   return make_float2(cs, sn);
 }
 
+// frac(b * k^2) as the top 32 bits of the 64-bit fixed-point product (k^2 < 2^32).
+__device__ __forceinline__ unsigned int fresnel_fix32(unsigned long long bfix, int k) {
+  return (unsigned int)((bfix * (unsigned long long)(unsigned int)(k * k)) >> 32);
+}
+
 template <int L, int B>
-__global__ void __launch_bounds__(ASM_T) k_asm_fwd_rows(const float2* __restrict__ H, int Nh,
+__global__ void __launch_bounds__(ASM_T, ASM_MINB) k_asm_fwd_rows(const float2* __restrict__ H, int Nh,
                                                         float2* __restrict__ Xr, const float2* __restrict__ tw) {
   extern __shared__ float2 sm[];
   const int r0 = blockIdx.x * B;
@@ -82,7 +98,7 @@ __global__ void __launch_bounds__(ASM_T) k_asm_fwd_rows(const float2* __restrict
 }
 
 template <int L, int B>
-__global__ void __launch_bounds__(ASM_T) k_asm_fwd_cols(const float2* __restrict__ Xr, int Nh,
+__global__ void __launch_bounds__(ASM_T, ASM_MINB) k_asm_fwd_cols(const float2* __restrict__ Xr, int Nh,
                                                         float2* __restrict__ X, const float2* __restrict__ tw) {
   extern __shared__ float2 sm[];
   const int c0 = blockIdx.x * B;
@@ -96,41 +112,90 @@ __global__ void __launch_bounds__(ASM_T) k_asm_fwd_cols(const float2* __restrict
       });
 }
 
-// L = P / s: folded column c0 + b of layer blockIdx.y.
-template <int L, int B>
-__global__ void __launch_bounds__(ASM_T) k_asm_inv_cols(const float2* __restrict__ X, int P, int s, int No,
-                                                        const AsmLayer* __restrict__ layers,
-                                                        float2* __restrict__ Y, const float2* __restrict__ tw) {
+// L = P / S: folded column c0 + b of layer blockIdx.y.  The tile (spectrum times T_z,
+// summed over the S x S aliases) is built in shared memory first, then transformed.
+// T_z separates into x and y parts except for the correction term: every thread keeps one
+// column (b = thread mod B), so the x part of its S aliases is computed once, and the y
+// part once per row for the S aliases along x.  The Fresnel phase is the sum of the two
+// parts' fixed-point fractions (top 32 bits each: error below 2^-31 cycles).  EXACT also
+// applies the band limit and the evanescent cut (the fast path runs only where the host
+// has found neither active).
+template <int L, int B, int S, bool EXACT>
+__global__ void __launch_bounds__(ASM_T, ASM_MINB) k_asm_inv_cols(const float2* __restrict__ X, int No,
+                                                                  const AsmLayer* __restrict__ layers,
+                                                                  float2* __restrict__ Y,
+                                                                  const float2* __restrict__ tw) {
   extern __shared__ float2 sm[];
+  using SM = fft::Smem<L, B>;
+  constexpr int P = L * S, HALF = P / 2;
+  static_assert(ASM_T % B == 0, "a thread keeps one column");
   const int c0 = blockIdx.x * B, z = blockIdx.y;
   const AsmLayer a = layers[z];
-  fft::fft_tile<L, B, ASM_T, true>(
-      sm, tw,
-      [&](int b, int ky) {
-        float2 acc = make_float2(0.f, 0.f);
-        if (c0 + b < L) {
-          for (int ty = 0; ty < s; ++ty)
-            for (int tx = 0; tx < s; ++tx) {
-              const int kyf = ky + ty * L, kxf = c0 + b + tx * L;
-              const float2 v = fft::cmul(X[(size_t)kyf * P + kxf], asm_transfer(a, kyf, kxf, P));
-              acc = fft::cadd(acc, v);
-            }
+  const int b = threadIdx.x % B, kx = c0 + b;
+  unsigned int ex[S];
+  float ux[S];
+  bool okx[S];
+#pragma unroll
+  for (int tx = 0; tx < S; ++tx) {
+    const int kxf = kx + tx * L, sx = kxf < HALF ? kxf : kxf - P;
+    ex[tx] = fresnel_fix32(a.bfix, sx);
+    ux[tx] = a.c * (float)(sx * sx);
+    okx[tx] = !EXACT || abs(sx) <= a.kmax;
+  }
+  if (kx < L) {
+#pragma unroll 2
+    for (int it = 0; it < B * L / ASM_T; ++it) {
+      const int ky = threadIdx.x / B + it * (ASM_T / B);
+      float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int ty = 0; ty < S; ++ty) {
+        const int kyf = ky + ty * L, sy = kyf < HALF ? kyf : kyf - P;
+        if (EXACT && abs(sy) > a.kmax) continue;
+        const unsigned int ey = fresnel_fix32(a.bfix, sy);
+        const float uy = a.c * (float)(sy * sy);
+        const float2* xr = X + (size_t)kyf * P + kx;
+#pragma unroll
+        for (int tx = 0; tx < S; ++tx) {
+          const float u = ux[tx] + uy;
+          if (EXACT && (!okx[tx] || u >= 1.f)) continue;  // outside the band limit, or evanescent
+          const float fr = (float)(int)(ex[tx] + ey) * 2.3283064365386963e-10f;  // signed, / 2^32
+          const float2 t = asm_phasor<EXACT>(fr, u, a.zl);
+          const float2 v = xr[tx * L];
+          acc.x = fmaf(v.x, t.x, fmaf(-v.y, t.y, acc.x));
+          acc.y = fmaf(v.x, t.y, fmaf(v.y, t.x, acc.y));
         }
-        return acc;
-      },
-      [&](int b, int i, float2 v) {
-        if (i < No && c0 + b < L) Y[((size_t)z * No + i) * L + c0 + b] = v;
+      }
+      sm[SM::at(b, ky)] = acc;
+    }
+  } else {
+    for (int it = 0; it < B * L / ASM_T; ++it) sm[SM::at(b, threadIdx.x / B + it * (ASM_T / B))] = make_float2(0.f, 0.f);
+  }
+  __syncthreads();
+  fft::fft_tile<L, B, ASM_T, true, true>(
+      sm, tw, [&](int bb, int i) { return sm[SM::at(bb, i)]; },
+      [&](int bb, int i, float2 v) {
+        if (i < No && c0 + bb < L) Y[((size_t)z * No + i) * L + c0 + bb] = v;
       });
 }
 
+// Rows i0 .. i0+B-1 of layer blockIdx.y.  The layer indices of the tile's output pixels
+// are staged in shared memory (after the FFT tile) before the transform.
 template <int L, int B>
-__global__ void __launch_bounds__(ASM_T) k_asm_inv_rows(const float2* __restrict__ Y, int No, int Z,
-                                                        const AsmLayer* __restrict__ layers,
-                                                        const uint8_t* __restrict__ lay, float2* __restrict__ F,
-                                                        float* __restrict__ amp, const float2* __restrict__ tw) {
+__global__ void __launch_bounds__(ASM_T, ASM_MINB) k_asm_inv_rows(const float2* __restrict__ Y, int No, int Z,
+                                                                  const AsmLayer* __restrict__ layers,
+                                                                  const uint8_t* __restrict__ lay,
+                                                                  float2* __restrict__ F, float* __restrict__ amp,
+                                                                  const float2* __restrict__ tw) {
   extern __shared__ float2 sm[];
+  uint8_t* lsm = reinterpret_cast<uint8_t*>(sm + fft::Smem<L, B>::floats2);
   const int i0 = blockIdx.x * B, z = blockIdx.y;
   const float scale = layers[z].scale;
+  if (amp)
+    for (int e = threadIdx.x; e < B * No; e += ASM_T) {
+      const int i = i0 + e / No;
+      lsm[e] = i < No ? lay[(size_t)i * No + e % No] : (uint8_t)0;
+    }
+  // (the barrier at the end of the first FFT pass orders these stores before the reads)
   fft::fft_tile<L, B, ASM_T, true>(
       sm, tw,
       [&](int b, int kx) {
@@ -143,7 +208,7 @@ __global__ void __launch_bounds__(ASM_T) k_asm_inv_rows(const float2* __restrict
         const size_t pix = (size_t)i * No + j;
         if (F) F[(size_t)z * No * No + pix] = v;
         if (amp) {
-          const int l = lay[pix];
+          const int l = lsm[b * No + j];
           if (l == z)
             amp[pix] = sqrtf(v.x * v.x + v.y * v.y);
           else if (z == 0 && l >= Z)
@@ -171,20 +236,46 @@ template <int L>
 static constexpr size_t tile_smem() {
   return (size_t)fft::Smem<L, ASM_TILE / L>::floats2 * sizeof(float2);
 }
+// the inverse-row kernel also stages B rows of layer indices (at most B * L bytes)
+template <int L>
+static constexpr size_t rows_smem() {
+  return tile_smem<L>() + ASM_TILE;
+}
+
+// Calls f(std::integral_constant<int, S>) for a supported sampling stride.
+template <class F>
+static bool with_stride(int s, F&& f) {
+  switch (s) {
+    case 1: f(std::integral_constant<int, 1>{}); return true;
+    case 2: f(std::integral_constant<int, 2>{}); return true;
+    case 4: f(std::integral_constant<int, 4>{}); return true;
+    case 8: f(std::integral_constant<int, 8>{}); return true;
+    default: return false;
+  }
+}
 
 int asm_init_attributes() {
   cudaError_t e = cudaSuccess;
+  auto keep = [&](cudaError_t x) {
+    if (x != cudaSuccess && e == cudaSuccess) e = x;
+  };
   for (int L = 64; L <= 4096; L <<= 1)
     with_len(L, [&](auto lc) {
       constexpr int Lc = decltype(lc)::value, B = ASM_TILE / Lc;
       const int sm = (int)tile_smem<Lc>();
-      cudaError_t r[4] = {
-          cudaFuncSetAttribute(k_asm_fwd_rows<Lc, B>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm),
-          cudaFuncSetAttribute(k_asm_fwd_cols<Lc, B>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm),
-          cudaFuncSetAttribute(k_asm_inv_cols<Lc, B>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm),
-          cudaFuncSetAttribute(k_asm_inv_rows<Lc, B>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm)};
-      for (cudaError_t x : r)
-        if (x != cudaSuccess && e == cudaSuccess) e = x;
+      keep(cudaFuncSetAttribute(k_asm_fwd_rows<Lc, B>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+      keep(cudaFuncSetAttribute(k_asm_fwd_cols<Lc, B>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+      keep(cudaFuncSetAttribute(k_asm_inv_rows<Lc, B>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)rows_smem<Lc>()));
+      for (int s = 1; s <= 8; s <<= 1)
+        with_stride(s, [&](auto sc) {
+          constexpr int Sc = decltype(sc)::value;
+          if constexpr (Lc * Sc <= 4096) {
+            keep(cudaFuncSetAttribute(k_asm_inv_cols<Lc, B, Sc, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+            keep(cudaFuncSetAttribute(k_asm_inv_cols<Lc, B, Sc, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      sm));
+          }
+        });
     });
   return cgh_cuda_check(e, "angular spectrum kernel attributes");
 }
@@ -258,6 +349,14 @@ static int asm_ensure(const cgh_plan* pc, int pad, int band_limit, cudaStream_t 
       h[k].kmax = km < P ? (int)km : P;
     }
   }
+  // The series form of the correction term is used when its truncated tail,
+  // (z/lambda) * (33/2048) u^7 / (1 - u) at the largest u of the grid, stays below 1e-8
+  // cycles for every layer, and no band limit or evanescent cut applies.
+  const double umax = lam * lam * df * df * 2.0 * (P / 2) * (P / 2);
+  bool exact = band_limit != 0 || umax >= 0.5;
+  for (int k = 0; k < Z && !exact; ++k)
+    if (p->z[k] / lam * (33.0 / 2048.0) * pow(umax, 7) / (1.0 - umax) > 1e-8) exact = true;
+  a->exact = exact ? 1 : 0;
   ASM_TRY(cudaMemcpyAsync(a->layers, h, sizeof(h), cudaMemcpyHostToDevice, st), "angular spectrum: layers");
   ASM_TRY(cudaStreamSynchronize(st), "angular spectrum: layers");
   a->band_limit = band_limit;
@@ -276,9 +375,9 @@ extern "C" int cgh_reconstruct_asm(const cgh_plan* p, const float* holo, float* 
   if (band_limit != 0 && band_limit != 1)
     return cgh_fail(CGH_ERR_ARG, "cgh_reconstruct_asm: band_limit %d not 0 or 1", band_limit);
   const int Nh = p->holo_h, No = p->obj_h, s = p->s, Z = p->n_layers;
-  if (p->holo_w != Nh || p->obj_w != No || !pow2(Nh) || !pow2(s))
+  if (p->holo_w != Nh || p->obj_w != No || !pow2(Nh) || !pow2(s) || s > 8)
     return cgh_fail(CGH_ERR_UNSUPPORTED,
-                    "cgh_reconstruct_asm: square power-of-two hologram and power-of-two sampling stride required");
+                    "cgh_reconstruct_asm: square power-of-two hologram and sampling stride 1, 2, 4 or 8 required");
   const int P = pad * Nh, L = P / s;
   if (P < 64 || P > 4096 || L < 64)
     return cgh_fail(CGH_ERR_UNSUPPORTED, "cgh_reconstruct_asm: padded edge %d and folded edge %d must lie in [64, 4096]",
@@ -302,9 +401,17 @@ extern "C" int cgh_reconstruct_asm(const cgh_plan* p, const float* holo, float* 
   prof_mark(p, CGH_PROF_ASM_INV, 0, st);
   with_len(L, [&](auto lc) {
     constexpr int Lc = decltype(lc)::value, B = ASM_TILE / Lc;
-    k_asm_inv_cols<Lc, B><<<dim3((Lc + B - 1) / B, Z), ASM_T, tile_smem<Lc>(), st>>>(a->X, P, s, No, a->layers,
-                                                                                    a->Y, a->tw);
-    k_asm_inv_rows<Lc, B><<<dim3((No + B - 1) / B, Z), ASM_T, tile_smem<Lc>(), st>>>(
+    with_stride(s, [&](auto sc) {
+      constexpr int Sc = decltype(sc)::value;
+      if constexpr (Lc * Sc <= 4096) {
+        const dim3 grid((Lc + B - 1) / B, Z);
+        if (a->exact)
+          k_asm_inv_cols<Lc, B, Sc, true><<<grid, ASM_T, tile_smem<Lc>(), st>>>(a->X, No, a->layers, a->Y, a->tw);
+        else
+          k_asm_inv_cols<Lc, B, Sc, false><<<grid, ASM_T, tile_smem<Lc>(), st>>>(a->X, No, a->layers, a->Y, a->tw);
+      }
+    });
+    k_asm_inv_rows<Lc, B><<<dim3((No + B - 1) / B, Z), ASM_T, rows_smem<Lc>(), st>>>(
         a->Y, No, Z, a->layers, layer_idx, (float2*)fields, amplitude, a->tw);
   });
   prof_mark(p, CGH_PROF_ASM_INV, 1, st);
