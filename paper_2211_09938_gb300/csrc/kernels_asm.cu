@@ -30,9 +30,16 @@
 #include "cgh_internal.h"
 #include "fft.cuh"
 
-#define ASM_T 512       // threads per CTA
-#define ASM_MINB 2      // CTAs per SM the register budget is sized for (64 registers a thread)
-#define ASM_TILE 8192   // elements per tile: B lines of length L with B * L = ASM_TILE
+// Tile shapes (threads T, elements B * L per tile; 16 elements a thread, 64 registers a
+// thread, so 1024 / T CTAs fill an SM's register file).  The column kernels take the large
+// tile so that every row segment they read is at least a 32-byte sector (B >= 4 lines up
+// to L = 2048); the row kernels run smaller tiles, more of them per SM, which hides the
+// latency of their load, transform and store phases better.
+#define ASM_BIG_T 512
+#define ASM_BIG_TILE 8192
+#define ASM_SMALL_T 256
+#define ASM_SMALL_TILE 4096
+#define ASM_MINB(T) (1024 / (T))
 
 struct AsmLayer {
   unsigned long long bfix;  // round(frac(b_z) * 2^64)
@@ -82,12 +89,12 @@ __device__ __forceinline__ unsigned int fresnel_fix32(unsigned long long bfix, i
   return (unsigned int)((bfix * (unsigned long long)(unsigned int)(k * k)) >> 32);
 }
 
-template <int L, int B>
-__global__ void __launch_bounds__(ASM_T, ASM_MINB) k_asm_fwd_rows(const float2* __restrict__ H, int Nh,
+template <int L, int B, int T>
+__global__ void __launch_bounds__(T, ASM_MINB(T)) k_asm_fwd_rows(const float2* __restrict__ H, int Nh,
                                                         float2* __restrict__ Xr, const float2* __restrict__ tw) {
   extern __shared__ float2 sm[];
   const int r0 = blockIdx.x * B;
-  fft::fft_tile<L, B, ASM_T, false>(
+  fft::fft_tile<L, B, T, false>(
       sm, tw,
       [&](int b, int i) {
         return (i < Nh && r0 + b < Nh) ? H[(size_t)(r0 + b) * Nh + i] : make_float2(0.f, 0.f);
@@ -97,12 +104,12 @@ __global__ void __launch_bounds__(ASM_T, ASM_MINB) k_asm_fwd_rows(const float2* 
       });
 }
 
-template <int L, int B>
-__global__ void __launch_bounds__(ASM_T, ASM_MINB) k_asm_fwd_cols(const float2* __restrict__ Xr, int Nh,
+template <int L, int B, int T>
+__global__ void __launch_bounds__(T, ASM_MINB(T)) k_asm_fwd_cols(const float2* __restrict__ Xr, int Nh,
                                                         float2* __restrict__ X, const float2* __restrict__ tw) {
   extern __shared__ float2 sm[];
   const int c0 = blockIdx.x * B;
-  fft::fft_tile<L, B, ASM_T, false>(
+  fft::fft_tile<L, B, T, false>(
       sm, tw,
       [&](int b, int i) {
         return (i < Nh && c0 + b < L) ? Xr[(size_t)i * L + c0 + b] : make_float2(0.f, 0.f);
@@ -120,15 +127,15 @@ __global__ void __launch_bounds__(ASM_T, ASM_MINB) k_asm_fwd_cols(const float2* 
 // parts' fixed-point fractions (top 32 bits each: error below 2^-31 cycles).  EXACT also
 // applies the band limit and the evanescent cut (the fast path runs only where the host
 // has found neither active).
-template <int L, int B, int S, bool EXACT>
-__global__ void __launch_bounds__(ASM_T, ASM_MINB) k_asm_inv_cols(const float2* __restrict__ X, int No,
+template <int L, int B, int T, int S, bool EXACT>
+__global__ void __launch_bounds__(T, ASM_MINB(T)) k_asm_inv_cols(const float2* __restrict__ X, int No,
                                                                   const AsmLayer* __restrict__ layers,
                                                                   float2* __restrict__ Y,
                                                                   const float2* __restrict__ tw) {
   extern __shared__ float2 sm[];
   using SM = fft::Smem<L, B>;
   constexpr int P = L * S, HALF = P / 2;
-  static_assert(ASM_T % B == 0, "a thread keeps one column");
+  static_assert(T % B == 0, "a thread keeps one column");
   const int c0 = blockIdx.x * B, z = blockIdx.y;
   const AsmLayer a = layers[z];
   const int b = threadIdx.x % B, kx = c0 + b;
@@ -144,8 +151,8 @@ __global__ void __launch_bounds__(ASM_T, ASM_MINB) k_asm_inv_cols(const float2* 
   }
   if (kx < L) {
 #pragma unroll 2
-    for (int it = 0; it < B * L / ASM_T; ++it) {
-      const int ky = threadIdx.x / B + it * (ASM_T / B);
+    for (int it = 0; it < B * L / T; ++it) {
+      const int ky = threadIdx.x / B + it * (T / B);
       float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
       for (int ty = 0; ty < S; ++ty) {
@@ -168,10 +175,10 @@ __global__ void __launch_bounds__(ASM_T, ASM_MINB) k_asm_inv_cols(const float2* 
       sm[SM::at(b, ky)] = acc;
     }
   } else {
-    for (int it = 0; it < B * L / ASM_T; ++it) sm[SM::at(b, threadIdx.x / B + it * (ASM_T / B))] = make_float2(0.f, 0.f);
+    for (int it = 0; it < B * L / T; ++it) sm[SM::at(b, threadIdx.x / B + it * (T / B))] = make_float2(0.f, 0.f);
   }
   __syncthreads();
-  fft::fft_tile<L, B, ASM_T, true, true>(
+  fft::fft_tile<L, B, T, true, true>(
       sm, tw, [&](int bb, int i) { return sm[SM::at(bb, i)]; },
       [&](int bb, int i, float2 v) {
         if (i < No && c0 + bb < L) Y[((size_t)z * No + i) * L + c0 + bb] = v;
@@ -180,8 +187,8 @@ __global__ void __launch_bounds__(ASM_T, ASM_MINB) k_asm_inv_cols(const float2* 
 
 // Rows i0 .. i0+B-1 of layer blockIdx.y.  The layer indices of the tile's output pixels
 // are staged in shared memory (after the FFT tile) before the transform.
-template <int L, int B>
-__global__ void __launch_bounds__(ASM_T, ASM_MINB) k_asm_inv_rows(const float2* __restrict__ Y, int No, int Z,
+template <int L, int B, int T>
+__global__ void __launch_bounds__(T, ASM_MINB(T)) k_asm_inv_rows(const float2* __restrict__ Y, int No, int Z,
                                                                   const AsmLayer* __restrict__ layers,
                                                                   const uint8_t* __restrict__ lay,
                                                                   float2* __restrict__ F, float* __restrict__ amp,
@@ -191,12 +198,12 @@ __global__ void __launch_bounds__(ASM_T, ASM_MINB) k_asm_inv_rows(const float2* 
   const int i0 = blockIdx.x * B, z = blockIdx.y;
   const float scale = layers[z].scale;
   if (amp)
-    for (int e = threadIdx.x; e < B * No; e += ASM_T) {
+    for (int e = threadIdx.x; e < B * No; e += T) {
       const int i = i0 + e / No;
       lsm[e] = i < No ? lay[(size_t)i * No + e % No] : (uint8_t)0;
     }
   // (the barrier at the end of the first FFT pass orders these stores before the reads)
-  fft::fft_tile<L, B, ASM_T, true>(
+  fft::fft_tile<L, B, T, true>(
       sm, tw,
       [&](int b, int kx) {
         return i0 + b < No ? Y[((size_t)z * No + i0 + b) * L + kx] : make_float2(0.f, 0.f);
@@ -232,14 +239,14 @@ static bool with_len(int L, F&& f) {
   }
 }
 
-template <int L>
+template <int L, int TILE>
 static constexpr size_t tile_smem() {
-  return (size_t)fft::Smem<L, ASM_TILE / L>::floats2 * sizeof(float2);
+  return (size_t)fft::Smem<L, TILE / L>::floats2 * sizeof(float2);
 }
 // the inverse-row kernel also stages B rows of layer indices (at most B * L bytes)
-template <int L>
+template <int L, int TILE>
 static constexpr size_t rows_smem() {
-  return tile_smem<L>() + ASM_TILE;
+  return tile_smem<L, TILE>() + TILE;
 }
 
 // Calls f(std::integral_constant<int, S>) for a supported sampling stride.
@@ -261,19 +268,22 @@ int asm_init_attributes() {
   };
   for (int L = 64; L <= 4096; L <<= 1)
     with_len(L, [&](auto lc) {
-      constexpr int Lc = decltype(lc)::value, B = ASM_TILE / Lc;
-      const int sm = (int)tile_smem<Lc>();
-      keep(cudaFuncSetAttribute(k_asm_fwd_rows<Lc, B>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
-      keep(cudaFuncSetAttribute(k_asm_fwd_cols<Lc, B>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
-      keep(cudaFuncSetAttribute(k_asm_inv_rows<Lc, B>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)rows_smem<Lc>()));
+      constexpr int Lc = decltype(lc)::value;
+      constexpr int BB = ASM_BIG_TILE / Lc, BS = ASM_SMALL_TILE / Lc;
+      constexpr int smb = (int)tile_smem<Lc, ASM_BIG_TILE>(), sms = (int)tile_smem<Lc, ASM_SMALL_TILE>();
+      keep(cudaFuncSetAttribute(k_asm_fwd_rows<Lc, BS, ASM_SMALL_T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                sms));
+      keep(cudaFuncSetAttribute(k_asm_fwd_cols<Lc, BB, ASM_BIG_T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smb));
+      keep(cudaFuncSetAttribute(k_asm_inv_rows<Lc, BS, ASM_SMALL_T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)rows_smem<Lc, ASM_SMALL_TILE>()));
       for (int s = 1; s <= 8; s <<= 1)
         with_stride(s, [&](auto sc) {
           constexpr int Sc = decltype(sc)::value;
           if constexpr (Lc * Sc <= 4096) {
-            keep(cudaFuncSetAttribute(k_asm_inv_cols<Lc, B, Sc, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
-            keep(cudaFuncSetAttribute(k_asm_inv_cols<Lc, B, Sc, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      sm));
+            keep(cudaFuncSetAttribute(k_asm_inv_cols<Lc, BB, ASM_BIG_T, Sc, true>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, smb));
+            keep(cudaFuncSetAttribute(k_asm_inv_cols<Lc, BB, ASM_BIG_T, Sc, false>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, smb));
           }
         });
     });
@@ -390,9 +400,12 @@ extern "C" int cgh_reconstruct_asm(const cgh_plan* p, const float* holo, float* 
 
   prof_mark(p, CGH_PROF_ASM_FFT, 0, st);
   with_len(P, [&](auto lc) {
-    constexpr int Lc = decltype(lc)::value, B = ASM_TILE / Lc;
-    k_asm_fwd_rows<Lc, B><<<(Nh + B - 1) / B, ASM_T, tile_smem<Lc>(), st>>>(H, Nh, a->Xr, a->tw);
-    k_asm_fwd_cols<Lc, B><<<(Lc + B - 1) / B, ASM_T, tile_smem<Lc>(), st>>>(a->Xr, Nh, a->X, a->tw);
+    constexpr int Lc = decltype(lc)::value;
+    constexpr int BB = ASM_BIG_TILE / Lc, BS = ASM_SMALL_TILE / Lc;
+    k_asm_fwd_rows<Lc, BS, ASM_SMALL_T><<<(Nh + BS - 1) / BS, ASM_SMALL_T, tile_smem<Lc, ASM_SMALL_TILE>(), st>>>(
+        H, Nh, a->Xr, a->tw);
+    k_asm_fwd_cols<Lc, BB, ASM_BIG_T><<<(Lc + BB - 1) / BB, ASM_BIG_T, tile_smem<Lc, ASM_BIG_TILE>(), st>>>(
+        a->Xr, Nh, a->X, a->tw);
   });
   prof_mark(p, CGH_PROF_ASM_FFT, 1, st);
   rc = cgh_cuda_check(cudaGetLastError(), "cgh_reconstruct_asm: forward transform");
@@ -400,19 +413,21 @@ extern "C" int cgh_reconstruct_asm(const cgh_plan* p, const float* holo, float* 
 
   prof_mark(p, CGH_PROF_ASM_INV, 0, st);
   with_len(L, [&](auto lc) {
-    constexpr int Lc = decltype(lc)::value, B = ASM_TILE / Lc;
+    constexpr int Lc = decltype(lc)::value;
+    constexpr int BB = ASM_BIG_TILE / Lc, BS = ASM_SMALL_TILE / Lc;
     with_stride(s, [&](auto sc) {
       constexpr int Sc = decltype(sc)::value;
       if constexpr (Lc * Sc <= 4096) {
-        const dim3 grid((Lc + B - 1) / B, Z);
+        const dim3 grid((Lc + BB - 1) / BB, Z);
+        constexpr size_t smb = tile_smem<Lc, ASM_BIG_TILE>();
         if (a->exact)
-          k_asm_inv_cols<Lc, B, Sc, true><<<grid, ASM_T, tile_smem<Lc>(), st>>>(a->X, No, a->layers, a->Y, a->tw);
+          k_asm_inv_cols<Lc, BB, ASM_BIG_T, Sc, true><<<grid, ASM_BIG_T, smb, st>>>(a->X, No, a->layers, a->Y, a->tw);
         else
-          k_asm_inv_cols<Lc, B, Sc, false><<<grid, ASM_T, tile_smem<Lc>(), st>>>(a->X, No, a->layers, a->Y, a->tw);
+          k_asm_inv_cols<Lc, BB, ASM_BIG_T, Sc, false><<<grid, ASM_BIG_T, smb, st>>>(a->X, No, a->layers, a->Y, a->tw);
       }
     });
-    k_asm_inv_rows<Lc, B><<<dim3((No + B - 1) / B, Z), ASM_T, rows_smem<Lc>(), st>>>(
-        a->Y, No, Z, a->layers, layer_idx, (float2*)fields, amplitude, a->tw);
+    k_asm_inv_rows<Lc, BS, ASM_SMALL_T><<<dim3((No + BS - 1) / BS, Z), ASM_SMALL_T, rows_smem<Lc, ASM_SMALL_TILE>(),
+                                          st>>>(a->Y, No, Z, a->layers, layer_idx, (float2*)fields, amplitude, a->tw);
   });
   prof_mark(p, CGH_PROF_ASM_INV, 1, st);
   return cgh_cuda_check(cudaGetLastError(), "cgh_reconstruct_asm: inverse transforms");
