@@ -350,6 +350,47 @@ def run_level_sweep(plan, coeffs, lists, counts, I, L, stream, form, flush):
     return {"form": form, "pointwise_operators": int(I.numel()), "stages": out}
 
 
+def run_asm_workload(plan, H, L, stream, flush, reps=10):
+    """Inverse angular-spectrum reconstruction of the bench hologram (Section 2, last
+    paragraph) for both paddings: device ms per call with L2 flushed, the split between
+    the forward FFT and the per-layer transfer + inverse FFTs, and the HBM bytes the
+    four-kernel pipeline must move (hologram in; row spectra, spectrum, layer columns out
+    and back; fields and amplitude out; the spectrum read from HBM once, its re-reads by
+    the other layers served from L2) against the measured copy bandwidth."""
+    import torch
+    Z, No, Nh, s = plan.n_layers, plan.obj_h, plan.holo_h, plan.holo_h // plan.obj_h
+    F = torch.empty((Z, No, No), dtype=torch.complex64, device="cuda")
+    A = torch.empty((No, No), dtype=torch.float32, device="cuda")
+    out = {}
+    pk = peaks() or {}
+    for pad in (2, 1):
+        P = pad * Nh
+        Lf = P // s
+        with torch.cuda.stream(stream):
+            for _ in range(3):
+                plan.reconstruct_asm(H, L, F, A, pad=pad, stream=stream)
+            plan.profile(True)
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+            split = {"asm_fft": 0.0, "asm_inv": 0.0}
+            for k in range(reps):
+                flush.fill_(float(k))
+                ev[k][0].record(stream)
+                plan.reconstruct_asm(H, L, F, A, pad=pad, stream=stream)
+                ev[k][1].record(stream)
+                st = plan.profile_read(stream=stream)
+                for key in split:
+                    split[key] += st[key] / reps
+            plan.profile(False)
+        torch.cuda.synchronize()
+        ms = sum(a.elapsed_time(b) for a, b in ev) / reps
+        nbytes = 8 * (Nh * Nh + 2 * Nh * P + 2 * P * P + 2 * Z * No * Lf + Z * No * No) + 4 * No * No + Z * No * No
+        gbs = nbytes / (ms / 1e3) / 1e9
+        out[f"pad{pad}"] = {"ms": ms, "stages_ms": split, "hbm_bytes_algorithmic": nbytes,
+                            "achieved_GBps": gbs,
+                            "frac_of_measured_hbm": gbs / pk["hbm_gbs"] if "hbm_gbs" in pk else None}
+    return out
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -554,6 +595,8 @@ def run_ours(args):
         line["phase_opt"] = run_phase_opt_workload(stream, args.phase_opt_steps)
     if plain is not None:
         line["plain_direct"] = plain
+    if rank == 0 and not args.skip_asm:
+        line["asm_reconstruct"] = run_asm_workload(plan, holo, L, stream, flush)
     if rank == 0 and not args.skip_level_sweep:
         line["level_sweep"] = run_level_sweep(plan, coeffs, lists, counts, I, L, stream, form, flush)
     # the other superposition forms on the same scene (device ms of the superposition call)
@@ -604,6 +647,7 @@ def main():
     ap.add_argument("--phase-opt-steps", type=int, default=5)
     ap.add_argument("--skip-plain", action="store_true")
     ap.add_argument("--skip-level-sweep", action="store_true")
+    ap.add_argument("--skip-asm", action="store_true", help="skip the angular-spectrum reconstruction timing")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
