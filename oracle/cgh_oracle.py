@@ -414,6 +414,36 @@ def plain_pointwise_hologram(intensity, layer, geom, pixels=None):
     return pointwise_hologram_separable(planes, geom)
 
 
+def pointcloud_hologram(intensity, depth, geom, pixels=None):
+    """Point-source hologram of an object whose every pixel has its own depth: Eq. 1 in
+    its paraxial form, for the 3-D extension sketched at the end of Section 2 without
+    quantising depth into layers.  Pixel (i, j) with a finite depth z_ij > 0 (metres) is a
+    point of amplitude intensity(i, j) at hologram pixel (s i, s j) on the plane at z_ij,
+    with its own rate a_ij = p^2 / (2 lambda z_ij); other pixels are no point.  Direct sum
+    at the given pixels ((m, n) index arrays; default every hologram pixel), each fringe
+    from the exact integer squared distance."""
+    I = np.asarray(intensity, dtype=np.float64)
+    zz = np.asarray(depth, dtype=np.float64)
+    valid = np.isfinite(zz) & (zz > 0)
+    ii, jj = np.nonzero(valid)
+    amp = I[ii, jj]
+    a = fresnel_rate(geom.pitch, geom.wavelength, zz[ii, jj])
+    if pixels is None:
+        mm, nn = np.meshgrid(np.arange(geom.holo_h), np.arange(geom.holo_w), indexing="ij")
+        mm, nn = mm.reshape(-1), nn.reshape(-1)
+        shape = (geom.holo_h, geom.holo_w)
+    else:
+        mm = np.asarray(pixels[0], dtype=np.int64).reshape(-1)
+        nn = np.asarray(pixels[1], dtype=np.int64).reshape(-1)
+        shape = mm.shape
+    out = np.zeros(mm.shape, dtype=np.complex128)
+    for p in range(mm.size):
+        dm = mm[p] - geom.s * ii
+        dn = nn[p] - geom.s * jj
+        out[p] = np.sum(amp * np.exp(2j * np.pi * _phase_cycles(a, dm * dm + dn * dn)))
+    return out.reshape(shape)
+
+
 # ----------------------------------------------------------------------------
 # reconstruction, adjoint, quality
 

@@ -596,3 +596,57 @@ def test_asm_band_limit():
     assert 0 < keep.sum() < P * P
     assert np.array_equal(T1 != 0, keep) and np.allclose(T1[keep], T0[keep], rtol=0, atol=0)
     assert np.array_equal(O.asm_transfer(g, 1, P, band_limit=True), O.asm_transfer(g, 1, P))
+
+
+# ---------------------------------------------------------------- per-point depth (D1-D3)
+
+def test_pointcloud_reduces_to_layers():
+    """D1: with every pixel's depth set to its layer's distance, the per-point sum is the
+    layered point-wise hologram (separable evaluation, pinned above).  The distances are
+    float32 values, so the float32 depth map holds them exactly."""
+    sc = scenes.random_scene(61, 16, 32, 3)
+    zs = [float(np.float32(z)) for z in (0.05, 0.0625, 0.09)]
+    g = O.Geometry((16, 16), (32, 32), PITCH, LAM, zs)
+    lay = sc["layer"].copy()
+    lay[0, :4] = 7  # pixels of no layer are no point
+    depth = np.where(lay < 3, np.asarray(zs)[np.minimum(lay, 2)], np.nan).astype(np.float32)
+    H1 = O.pointcloud_hologram(sc["intensity"], depth, g)
+    H2 = O.plain_pointwise_hologram(sc["intensity"], lay, g)
+    assert O.rel_l2(H1, H2) < 1e-12
+
+
+def test_pointcloud_single_point_closed_form():
+    """D2: one point at rate exactly 1/4 (wavelength chosen so that z = 2 p^2 / lambda is
+    a power of two): H(m, n) = v * j^(odd(dm) + odd(dn)); every other pixel's depth is 0,
+    negative, NaN or infinite (no point)."""
+    n, s = 8, 4
+    z = 2.0 ** -12
+    lam = 2 * PITCH * PITCH / z
+    g = O.Geometry((n, n), (n * s, n * s), PITCH, lam, [1.0])
+    depth = np.full((n, n), np.nan, np.float32)
+    depth[1, 1], depth[2, 2], depth[3, 3] = 0.0, -0.1, np.inf
+    depth[5, 2] = z
+    I = np.full((n, n), 200, np.uint8)
+    I[5, 2] = 17
+    H = O.pointcloud_hologram(I, depth, g)
+    m = np.arange(n * s)[:, None] - 5 * s
+    q = np.arange(n * s)[None, :] - 2 * s
+    assert np.max(np.abs(H - 17 * 1j ** ((m % 2) + (q % 2)))) < 1e-10
+
+
+def test_pointcloud_brute_force_two_depths():
+    """D3: two points at different depths against Eq. 1's paraxial phase written out,
+    pi (d p)^2 / (lambda z), summed by hand (no reduction needed at these offsets)."""
+    g = O.Geometry((4, 4), (8, 8), PITCH, LAM, [1.0])
+    depth = np.full((4, 4), np.nan, np.float32)
+    depth[0, 3], depth[2, 1] = 0.013, 0.021
+    I = np.zeros((4, 4), np.uint8)
+    I[0, 3], I[2, 1] = 50, 90
+    H = O.pointcloud_hologram(I, depth, g)
+    for m in range(8):
+        for n in range(8):
+            want = 0j
+            for (i, j) in ((0, 3), (2, 1)):
+                r2 = ((m - 2 * i) * PITCH) ** 2 + ((n - 2 * j) * PITCH) ** 2
+                want += I[i, j] * np.exp(1j * np.pi * r2 / (LAM * float(depth[i, j])))
+            assert abs(H[m, n] - want) < 1e-9
