@@ -228,6 +228,23 @@ int cgh_plain_direct(const cgh_plan* plan, const uint8_t* intensity, const uint8
                      float* holo, void* stream);
 
 /*
+ * cgh_pointcloud_direct - point-wise hologram with a depth per object point.
+ * Paper: Eq. 1 (paraxial) for the 3-D scenes the end of Section 2 extends the method to,
+ * here without quantising depth into the plan's layers.  Object pixel (i, j) with a finite
+ * depth z_ij > 0 is a point of amplitude intensity(i, j) at hologram pixel (s*i, s*j):
+ *   holo(m,n) (+)= sum_{i,j} intensity(i,j) * exp(j*2*pi*frac(a_ij*((m-s*i)^2 + (n-s*j)^2))),
+ *   a_ij = p^2 / (2*lambda*z_ij)   (formed in FP64, then reduced exactly in 64-bit fixed point)
+ * Pixels with depth <= 0, NaN or infinite are no point.  The plan's layer distances are not
+ * used; a depth map holding them reproduces cgh_plain_direct bit for bit.  FP32 SFU
+ * sine/cosine per (point, pixel), as cgh_plain_direct.
+ *   intensity  uint8 [obj_h][obj_w];  depth_m float [obj_h][obj_w] (metres)
+ *   holo       complex64 [holo_h][holo_w], overwritten (accumulate = 0) or added to (1)
+ * Errors: CGH_ERR_ARG, CGH_ERR_CUDA.
+ */
+int cgh_pointcloud_direct(const cgh_plan* plan, const uint8_t* intensity, const float* depth_m, float* holo,
+                          int accumulate, void* stream);
+
+/*
  * cgh_reconstruct - Fresnel back-propagation of a hologram to every layer.
  * Paper: Section 2 last paragraph (numerical reconstruction; the paper uses the inverse
  * angular spectrum, this library uses the Fresnel adjoint of Eq. 1 on the object grid).
@@ -401,7 +418,8 @@ int cgh_batch_destroy(cgh_batch* batch);
 #define CGH_PROF_PROPAGATE 9   /* propagation of layer fields            */
 #define CGH_PROF_ASM_FFT 10    /* angular spectrum: forward 2-D FFT      */
 #define CGH_PROF_ASM_INV 11    /* angular spectrum: transfer + inverse FFTs */
-#define CGH_PROF_SLOTS 12
+#define CGH_PROF_POINTCLOUD 12 /* per-point depth direct kernel          */
+#define CGH_PROF_SLOTS 13
 
 /*
  * cgh_profile - enable (1) or disable (0) CUDA-event timing around the plan's internal

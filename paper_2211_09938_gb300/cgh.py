@@ -47,6 +47,7 @@ SIGNATURES = {
                                     ctypes.POINTER(_I), _P, _P]),
     "cgh_progressive_hologram": (_I, [_P, _P, ctypes.POINTER(_P), _P, _P, _I, _I, _P]),
     "cgh_plain_direct": (_I, [_P, _P, _P, _P, _P]),
+    "cgh_pointcloud_direct": (_I, [_P, _P, _P, _P, _I, _P]),
     "cgh_reconstruct": (_I, [_P, _P, _P, _P, _P, _P]),
     "cgh_reconstruct_asm": (_I, [_P, _P, _P, _P, _P, _I, _I, _P]),
     "cgh_propagate": (_I, [_P, _P, _P, _I, _P]),
@@ -230,6 +231,16 @@ class Plan:
                                      _stream(stream)))
         return holo
 
+    def pointcloud_direct(self, intensity, depth, holo=None, accumulate=False, stream=None):
+        """Point-wise hologram with a depth (float32 metres) per object pixel
+        (cgh_pointcloud_direct); pixels with depth <= 0 or non-finite are no point."""
+        import torch
+        if holo is None:
+            holo = torch.empty((self.holo_h, self.holo_w), dtype=torch.complex64, device=self.device)
+        check(lib().cgh_pointcloud_direct(self.handle, _ptr(intensity), _ptr(depth), _ptr(holo),
+                                          1 if accumulate else 0, _stream(stream)))
+        return holo
+
     def reconstruct(self, holo, layer=None, fields=True, amplitude=True, stream=None):
         """(fields [Z, obj, obj] complex64 or None, amplitude [obj, obj] float32 or None).
         `fields` / `amplitude` may also be preallocated tensors."""
@@ -287,7 +298,7 @@ class Plan:
         return out
 
     PROF_SLOTS = ["tables", "haar", "select", "direct_lut", "tc_prep", "tc_stage1", "tc_stage2",
-                  "plain", "recon", "propagate", "asm_fft", "asm_inv"]
+                  "plain", "recon", "propagate", "asm_fft", "asm_inv", "pointcloud"]
 
     def profile(self, enable=True):
         check(lib().cgh_profile(self.handle, 1 if enable else 0))

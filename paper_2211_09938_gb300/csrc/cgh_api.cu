@@ -255,6 +255,19 @@ int cgh_plain_direct(const cgh_plan* p, const uint8_t* intensity, const uint8_t*
   return CGH_OK;
 }
 
+int cgh_pointcloud_direct(const cgh_plan* p, const uint8_t* intensity, const float* depth_m, float* holo,
+                          int accumulate, void* stream) {
+  if (!p || !intensity || !depth_m || !holo) return cgh_fail(CGH_ERR_ARG, "cgh_pointcloud_direct: NULL argument");
+  if (accumulate != 0 && accumulate != 1)
+    return cgh_fail(CGH_ERR_ARG, "cgh_pointcloud_direct: accumulate %d not 0 or 1", accumulate);
+  if ((uintptr_t)holo & 7) return cgh_fail(CGH_ERR_ARG, "cgh_pointcloud_direct: holo must be 8-byte aligned");
+  prof_mark(p, CGH_PROF_POINTCLOUD, 0, (cudaStream_t)stream);
+  CHECK_CUDA(launch_pointcloud_direct(p, intensity, depth_m, (float2*)holo, accumulate, (cudaStream_t)stream),
+             "cgh_pointcloud_direct");
+  prof_mark(p, CGH_PROF_POINTCLOUD, 1, (cudaStream_t)stream);
+  return CGH_OK;
+}
+
 int cgh_reconstruct(const cgh_plan* p, const float* holo, float* fields, const uint8_t* layer_idx,
                     float* amplitude, void* stream) {
   if (!p || !holo) return cgh_fail(CGH_ERR_ARG, "cgh_reconstruct: NULL argument");

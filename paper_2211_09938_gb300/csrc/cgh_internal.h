@@ -120,6 +120,8 @@ cudaError_t launch_direct_lut(const cgh_plan* p, const int32_t* coef, const int3
                               const int32_t* d_counts, float2* holo, cudaStream_t st);
 cudaError_t launch_plain_direct(const cgh_plan* p, const uint8_t* I, const uint8_t* L, float2* holo,
                                 cudaStream_t st);
+cudaError_t launch_pointcloud_direct(const cgh_plan* p, const uint8_t* I, const float* depth, float2* holo,
+                                     int accumulate, cudaStream_t st);
 int select_num_chunks(int obj_h, int obj_w, int level);
 cudaError_t launch_select_tasks(int obj_h, int obj_w, int n_layers, const uint8_t* sal, const uint8_t* L,
                                 SelTasks T, int* chunk_cnt, int* chunk_off, cudaStream_t st);

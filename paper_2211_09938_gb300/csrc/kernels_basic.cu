@@ -331,26 +331,33 @@ cudaError_t launch_select(int obj_h, int obj_w, int n_layers, const uint8_t* sal
 
 // ---------------------------------------------------------------------------
 // (A5) plain point-wise hologram (Eq. 1): one SFU sine/cosine per (point, pixel).
-// The phase a_z*(dm^2 + dn^2) mod 1 is exact in 64-bit fixed point: with
-// A = round(frac(a_z) 2^64) and q = dm^2 + dn^2 < 2^31, the top 32 bits of A*q mod 2^64
+// The phase a*(dm^2 + dn^2) mod 1 is exact in 64-bit fixed point: with
+// A = round(frac(a) 2^64) and q = dm^2 + dn^2 < 2^31, the top 32 bits of A*q mod 2^64
 // are umulhi(A_lo, q) + A_hi*q (mod 2^32).  Their top 23 bits (rounded) become a float
 // in [-1/2, 1/2) cycles through the exponent trick (no int-to-float conversion).
+// Layered (DEPTH = false): a point takes its layer's rate.  Per-point depth (DEPTH = true,
+// the 3-D extension at the end of Section 2 without depth layers): a pixel with a finite
+// depth z > 0 takes a = p^2 / (2 lambda z), formed in FP64 with the same operations and
+// rounding as the plan's per-layer rates (so a depth map equal to the layer distances
+// gives the layered result bit for bit); other pixels are no point.
 #define PD_TM 32
 #define PD_TN 64
 #define PD_CHUNK 256
 
+template <bool DEPTH>
 __global__ void __launch_bounds__(256) k_plain_direct(const uint8_t* __restrict__ I,
-                                                      const uint8_t* __restrict__ L, int H, int W,
+                                                      const uint8_t* __restrict__ L,
+                                                      const float* __restrict__ depth, int H, int W,
                                                       int Z, int s, const unsigned long long* a_fixed,
-                                                      float2* __restrict__ holo, int HH, int HW) {
-  __shared__ int4 s_pt[PD_CHUNK];  // (s*i, s*j, amp bits, layer)
-  __shared__ unsigned s_alo[CGH_MAX_LAYERS], s_ahi[CGH_MAX_LAYERS];
+                                                      double pitch, double wavelength,
+                                                      float2* __restrict__ holo, int HH, int HW,
+                                                      int accumulate) {
+  __shared__ int4 s_pt[PD_CHUNK];      // (s*i, s*j, amp bits, low word of the rate)
+  __shared__ unsigned s_ph[PD_CHUNK];  // high word of the rate
+  __shared__ unsigned long long s_a[CGH_MAX_LAYERS];
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   const int m0 = blockIdx.y * PD_TM, n0 = blockIdx.x * PD_TN;
-  if (threadIdx.x < Z) {
-    s_alo[threadIdx.x] = (unsigned)(a_fixed[threadIdx.x] & 0xffffffffull);
-    s_ahi[threadIdx.x] = (unsigned)(a_fixed[threadIdx.x] >> 32);
-  }
+  if (!DEPTH && threadIdx.x < Z) s_a[threadIdx.x] = a_fixed[threadIdx.x];
   int mm[2], nn[4];
 #pragma unroll
   for (int r = 0; r < 2; ++r) mm[r] = m0 + ty + 16 * r;
@@ -367,13 +374,28 @@ __global__ void __launch_bounds__(256) k_plain_direct(const uint8_t* __restrict_
     {
       const int p = base + threadIdx.x;
       int4 v = make_int4(0, 0, 0, 0);
+      unsigned long long af = 0;
       if (p < npts) {
         const int i = p / W, j = p - (p / W) * W;
-        const int lz = L[p];
-        const float amp = lz < Z ? (float)I[p] : 0.f;
-        v = make_int4(s * i, s * j, __float_as_int(amp), lz < Z ? lz : 0);
+        float amp;
+        if constexpr (DEPTH) {
+          const float zf = depth[p];
+          const bool ok = zf > 0.f && isfinite(zf);
+          amp = ok ? (float)I[p] : 0.f;
+          if (ok) {
+            const double a = pitch * pitch / (2.0 * wavelength * (double)zf);
+            const double x = floor((a - floor(a)) * 18446744073709551616.0 + 0.5);
+            af = x >= 18446744073709551616.0 ? 0ull : (unsigned long long)x;
+          }
+        } else {
+          const int lz = L[p];
+          amp = lz < Z ? (float)I[p] : 0.f;
+          af = s_a[lz < Z ? lz : 0];
+        }
+        v = make_int4(s * i, s * j, __float_as_int(amp), (int)(unsigned)(af & 0xffffffffull));
       }
       s_pt[threadIdx.x] = v;
+      s_ph[threadIdx.x] = (unsigned)(af >> 32);
     }
     __syncthreads();
     const int cnt = min(PD_CHUNK, npts - base);
@@ -389,7 +411,7 @@ __global__ void __launch_bounds__(256) k_plain_direct(const uint8_t* __restrict_
     for (int k = 0; k < cnt; ++k) {
       const int4 pt = s_pt[k];
       const float amp = __int_as_float(pt.z);
-      const unsigned alo = s_alo[pt.w], ahi = s_ahi[pt.w];
+      const unsigned alo = (unsigned)pt.w, ahi = s_ph[k];
       unsigned dx2[2], dy2[4];
 #pragma unroll
       for (int r = 0; r < 2; ++r) {
@@ -426,14 +448,30 @@ __global__ void __launch_bounds__(256) k_plain_direct(const uint8_t* __restrict_
   for (int r = 0; r < 2; ++r)
 #pragma unroll
     for (int c = 0; c < 4; ++c)
-      if (mm[r] < HH && nn[c] < HW) holo[(size_t)mm[r] * HW + nn[c]] = make_float2(re[r][c], im[r][c]);
+      if (mm[r] < HH && nn[c] < HW) {
+        float2* o = holo + (size_t)mm[r] * HW + nn[c];
+        if (accumulate) {
+          const float2 prev = *o;
+          *o = make_float2(prev.x + re[r][c], prev.y + im[r][c]);
+        } else {
+          *o = make_float2(re[r][c], im[r][c]);
+        }
+      }
 }
 
 cudaError_t launch_plain_direct(const cgh_plan* p, const uint8_t* I, const uint8_t* L, float2* holo,
                                 cudaStream_t st) {
   dim3 grid((p->holo_w + PD_TN - 1) / PD_TN, (p->holo_h + PD_TM - 1) / PD_TM);
-  k_plain_direct<<<grid, 256, 0, st>>>(I, L, p->obj_h, p->obj_w, p->n_layers, p->s, p->d_a_fixed,
-                                       holo, p->holo_h, p->holo_w);
+  k_plain_direct<false><<<grid, 256, 0, st>>>(I, L, nullptr, p->obj_h, p->obj_w, p->n_layers, p->s, p->d_a_fixed,
+                                              p->pitch, p->wavelength, holo, p->holo_h, p->holo_w, 0);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pointcloud_direct(const cgh_plan* p, const uint8_t* I, const float* depth, float2* holo,
+                                     int accumulate, cudaStream_t st) {
+  dim3 grid((p->holo_w + PD_TN - 1) / PD_TN, (p->holo_h + PD_TM - 1) / PD_TM);
+  k_plain_direct<true><<<grid, 256, 0, st>>>(I, nullptr, depth, p->obj_h, p->obj_w, p->n_layers, p->s, nullptr,
+                                             p->pitch, p->wavelength, holo, p->holo_h, p->holo_w, accumulate);
   return cudaGetLastError();
 }
 

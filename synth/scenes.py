@@ -133,6 +133,25 @@ def random_scene(seed, n, holo, n_layers, sal_fraction=None, graded=False):
                 holo=(holo, holo), pitch=PITCH, wavelength=WAVELENGTH)
 
 
+def depth_map(seed, n, z_lo=0.08, z_hi=0.20, holes=0.0):
+    """Continuous per-pixel depth (float32 metres) for the per-point-depth path: a smooth
+    field from 3 broad blobs scaled to [z_lo, z_hi] plus a small seeded jitter; a fraction
+    `holes` of pixels gets no depth (NaN, 0 or negative) at random."""
+    rng = _rng(seed)
+    f = _blobs(rng, n, 3, 0.20, 0.40, 0.5, 1.0)
+    lo, hi = f.min(), f.max()
+    d = (f - lo) / (hi - lo) if hi > lo else np.zeros_like(f)
+    z = z_lo + (z_hi - z_lo) * np.clip(d + rng.normal(0.0, 0.01, size=d.shape), 0.0, 1.0)
+    z = z.astype(np.float32)
+    if holes > 0:
+        pick = rng.uniform(size=z.shape) < holes
+        kind = rng.integers(0, 3, size=z.shape)
+        z[pick & (kind == 0)] = np.nan
+        z[pick & (kind == 1)] = 0.0
+        z[pick & (kind == 2)] = -0.05
+    return z
+
+
 def batch_scenes(seed=4000, count=64):
     """Batched workload: uneven object edges from {128,256,512,1024}, hologram 2x,
     4..32 layers each, ellipse saliency with area fraction U[0.05, 0.6]."""
