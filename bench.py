@@ -391,6 +391,36 @@ def run_asm_workload(plan, H, L, stream, flush, reps=10):
     return out
 
 
+def run_rgb_workload(stream, form, flush, reps=10):
+    """Colour frame: the bench scene's three colour channels (R, G, B at 638, 532 and 450
+    nm) as one three-scene batch; device ms per colour frame with L2 flushed."""
+    import numpy as np
+    import torch
+    from synth import scenes
+    from paper_2211_09938_gb300.rgb import RGBHologram, WAVELENGTHS_RGB
+    sc = scenes.rgb_scene(2002, OBJ, HOLO, NLAYERS)
+    Ic = [torch.from_numpy(np.ascontiguousarray(sc["intensity"][c])).cuda() for c in range(3)]
+    L = torch.from_numpy(sc["layer"]).cuda()
+    S = torch.from_numpy(sc["saliency"]).cuda()
+    holos = [torch.empty((HOLO, HOLO), dtype=torch.complex64, device="cuda") for _ in range(3)]
+    with torch.cuda.stream(stream):
+        rgb = RGBHologram((OBJ, OBJ), (HOLO, HOLO), sc["pitch"], sc["z"], Ic, L, S, scenes.THRESHOLDS_U8, holos,
+                          form=form, stream=stream)
+        for _ in range(3):
+            rgb.run(stream)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+        for k in range(reps):
+            flush.fill_(float(k))
+            ev[k][0].record(stream)
+            rgb.run(stream)
+            ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    ms = sum(a.elapsed_time(b) for a, b in ev) / reps
+    rgb.close()
+    return {"form": form, "wavelengths_nm": [w * 1e9 for w in WAVELENGTHS_RGB], "ms_per_colour_frame": ms,
+            "value": 3 * UNITS_PER_STEP / (ms / 1e3) / 1e9, "unit": UNIT}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -570,6 +600,28 @@ def run_ours(args):
         plain = {"ms": p_ms, "value": UNITS_PER_STEP / (p_ms / 1e3) / 1e9, "unit": UNIT,
                  "speedup_of_progressive_step": p_ms / (dev_ms / args.steps)}
 
+    # ---- per-point depth (no depth layers) on the same object, continuous depth map
+    pointcloud = None
+    if rank == 0 and not args.skip_plain:
+        D = torch.from_numpy(scenes.depth_map(2001, OBJ)).cuda()
+        with torch.cuda.stream(stream):
+            Hc = plan.pointcloud_direct(I, D, stream=stream)
+            pe = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+            pe[0].record(stream)
+            plan.pointcloud_direct(I, D, holo=Hc, stream=stream)
+            pe[1].record(stream)
+        torch.cuda.synchronize()
+        c_ms = pe[0].elapsed_time(pe[1])
+        sms = torch.cuda.get_device_properties(devn).multi_processor_count
+        # two SFU operations (sine, cosine) per point and pixel; 16 SFU lanes per SM per clock
+        xu_peak = sms * 16 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 2 / 1e9
+        c_val = UNITS_PER_STEP / (c_ms / 1e3) / 1e9
+        pointcloud = {"ms": c_ms, "value": c_val, "unit": UNIT,
+                      "roofline": {"bound": "xu", "achieved": c_val, "peak": xu_peak, "unit": UNIT,
+                                   "frac": c_val / xu_peak,
+                                   "peak_note": f"{sms} SMs x 16 SFU lanes x max SM clock / 2 SFU ops per "
+                                                "point-pixel (derived, not measured)"}}
+
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": dev_ms / args.steps, "higher_is_better": True,
@@ -595,6 +647,10 @@ def run_ours(args):
         line["phase_opt"] = run_phase_opt_workload(stream, args.phase_opt_steps)
     if plain is not None:
         line["plain_direct"] = plain
+    if pointcloud is not None:
+        line["pointcloud_direct"] = pointcloud
+    if rank == 0 and not args.skip_rgb:
+        line["rgb"] = run_rgb_workload(stream, form if form != "direct_lut" else "tc_bf16x3", flush)
     if rank == 0 and not args.skip_asm:
         line["asm_reconstruct"] = run_asm_workload(plan, holo, L, stream, flush)
     if rank == 0 and not args.skip_level_sweep:
@@ -648,6 +704,7 @@ def main():
     ap.add_argument("--skip-plain", action="store_true")
     ap.add_argument("--skip-level-sweep", action="store_true")
     ap.add_argument("--skip-asm", action="store_true", help="skip the angular-spectrum reconstruction timing")
+    ap.add_argument("--skip-rgb", action="store_true", help="skip the three-channel colour frame timing")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:

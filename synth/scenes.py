@@ -152,6 +152,22 @@ def depth_map(seed, n, z_lo=0.08, z_hi=0.20, holes=0.0):
     return z
 
 
+def rgb_scene(seed, n, holo, n_layers):
+    """Colour scene: a random_scene whose intensity becomes three correlated channels
+    (uint8 [3, n, n], R G B): the grey image scaled by seeded per-channel gains plus
+    per-channel blobs and noise; layers and saliency are shared by the channels."""
+    sc = random_scene(seed, n, holo, n_layers)
+    rng = _rng(seed + 1)
+    base = sc["intensity"].astype(np.float64)
+    chans = []
+    for _ in range(3):
+        g = rng.uniform(0.5, 1.0)
+        img = g * base + _blobs(rng, n, 3, 0.05, 0.15, 20, 80) + rng.normal(0.0, 4.0, size=base.shape)
+        chans.append(np.clip(np.round(img), 0, 255).astype(np.uint8))
+    sc["intensity"] = np.stack(chans)
+    return sc
+
+
 def batch_scenes(seed=4000, count=64):
     """Batched workload: uneven object edges from {128,256,512,1024}, hologram 2x,
     4..32 layers each, ellipse saliency with area fraction U[0.05, 0.6]."""

@@ -650,3 +650,26 @@ def test_pointcloud_brute_force_two_depths():
                 r2 = ((m - 2 * i) * PITCH) ** 2 + ((n - 2 * j) * PITCH) ** 2
                 want += I[i, j] * np.exp(1j * np.pi * r2 / (LAM * float(depth[i, j])))
             assert abs(H[m, n] - want) < 1e-9
+
+
+# ---------------------------------------------------------------- colour channels (C1)
+
+def test_wavelength_enters_only_through_the_rate():
+    """C1: lambda appears only in a_z = p^2 / (2 lambda z): a channel at wavelength l1 and
+    distances z equals a channel at l2 and distances z l1 / l2, for the progressive
+    hologram, the point-wise one and the Fresnel reconstruction."""
+    sc = scenes.rgb_scene(71, 16, 32, 2)
+    lam_r, lam_b = 638e-9, 450e-9
+    z = np.array([0.05, 0.07])
+    gr = O.Geometry((16, 16), (32, 32), PITCH, lam_r, z)
+    gb = O.Geometry((16, 16), (32, 32), PITCH, lam_b, z * lam_r / lam_b)
+    I = sc["intensity"][0]
+    lists = O.progressive_lists(sc["saliency"], sc["layer"], 2, scenes.THRESHOLDS_U8)
+    Hr = O.progressive_hologram(I, sc["layer"], lists, gr)
+    Hb = O.progressive_hologram(I, sc["layer"], lists, gb)
+    assert O.rel_l2(Hb, Hr) < 1e-12
+    assert O.rel_l2(O.plain_pointwise_hologram(I, sc["layer"], gb), O.plain_pointwise_hologram(I, sc["layer"], gr)) < 1e-12
+    assert O.rel_l2(O.reconstruct_fields(Hr, gb), O.reconstruct_fields(Hr, gr)) < 1e-12
+    # and a different wavelength at the same distances gives a different hologram
+    g2 = O.Geometry((16, 16), (32, 32), PITCH, lam_b, z)
+    assert O.rel_l2(O.progressive_hologram(I, sc["layer"], lists, g2), Hr) > 0.1
