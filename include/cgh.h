@@ -97,6 +97,21 @@ int cgh_plan_create(cgh_plan** out, int obj_h, int obj_w, int holo_h, int holo_w
  */
 int cgh_plan_set_tuning(cgh_plan* plan, int max_ksteps_per_chain);
 
+/*
+ * cgh_plan_set_contraction - order of the separable tensor form's two GEMMs.
+ * H = sum_z E_z A^_z E_z^T can be contracted over the layers' compacted object rows
+ * (stage 2 K = sum of the row counts) or, for a square object, over their columns (the
+ * transposed problem, H written transposed); the cost of stage 2 follows that K.
+ *   CGH_CONTRACT_AUTO  (default) on the device, per call: columns when their sum is smaller
+ *   CGH_CONTRACT_ROWS  always rows;  CGH_CONTRACT_COLS  columns whenever the object is square
+ * Results agree to rounding.  Applies to later calls of the plan.  The paper has no
+ * counterpart (it superposes block fringes directly).
+ */
+#define CGH_CONTRACT_AUTO 0
+#define CGH_CONTRACT_ROWS 1
+#define CGH_CONTRACT_COLS 2
+int cgh_plan_set_contraction(cgh_plan* plan, int order);
+
 /* Frees the plan and its device memory (synchronises the device first).  NULL is a no-op. */
 int cgh_plan_destroy(cgh_plan* plan);
 
@@ -437,8 +452,10 @@ int cgh_profile_read(cgh_plan* plan, float* ms, void* stream);
 
 /*
  * cgh_tc_layer_dims - synchronise `stream` and copy to host the per-layer padded compacted
- * row and column counts used by the last tensor-form call (kr[Z], kc[Z], host arrays);
- * zeros before the first such call.  Their sums size the tensor-core GEMMs.
+ * counts used by the last tensor-form call (kr[Z], kc[Z], host arrays); zeros before the
+ * first such call.  kr is along the stage-2 contraction axis (object rows, or object columns
+ * when that call contracted over columns, see cgh_plan_set_contraction), kc along the other.
+ * Their sums size the tensor-core GEMMs.
  */
 int cgh_tc_layer_dims(const cgh_plan* plan, int* kr, int* kc, void* stream);
 

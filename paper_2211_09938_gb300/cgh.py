@@ -39,6 +39,7 @@ SIGNATURES = {
                              ctypes.POINTER(_D), _I, _I, _P]),
     "cgh_plan_destroy": (_I, [_P]),
     "cgh_plan_set_tuning": (_I, [_P, _I]),
+    "cgh_plan_set_contraction": (_I, [_P, _I]),
     "cgh_build_tables": (_I, [_P, _P]),
     "cgh_haar_decompose": (_I, [_P, _P, _P, _P, _P]),
     "cgh_select_blocks": (_I, [_P, _P, _P, _I, _I, _P, _P, _I, _P]),
@@ -149,6 +150,13 @@ class Plan:
             pass
 
     # ---- C calls -------------------------------------------------------------------
+    CONTRACT_AUTO, CONTRACT_ROWS, CONTRACT_COLS = 0, 1, 2
+
+    def set_contraction(self, order):
+        """Contraction order of the tensor form (cgh_plan_set_contraction): CONTRACT_AUTO,
+        CONTRACT_ROWS or CONTRACT_COLS."""
+        check(lib().cgh_plan_set_contraction(self.handle, int(order)))
+
     def set_tuning(self, max_ksteps_per_chain):
         check(lib().cgh_plan_set_tuning(self.handle, int(max_ksteps_per_chain)))
 

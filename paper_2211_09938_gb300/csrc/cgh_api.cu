@@ -65,6 +65,13 @@ int cgh_plan_set_tuning(cgh_plan* p, int max_ksteps) {
   return CGH_OK;
 }
 
+int cgh_plan_set_contraction(cgh_plan* p, int order) {
+  if (!p || order < CGH_CONTRACT_AUTO || order > CGH_CONTRACT_COLS)
+    return cgh_fail(CGH_ERR_ARG, "cgh_plan_set_contraction: bad argument");
+  p->contraction = order;
+  return CGH_OK;
+}
+
 int cgh_build_tables(cgh_plan* p, void* stream) {
   if (!p) return cgh_fail(CGH_ERR_ARG, "cgh_build_tables: plan is NULL");
   prof_mark(p, CGH_PROF_TABLES, 0, (cudaStream_t)stream);

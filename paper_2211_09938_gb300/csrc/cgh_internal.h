@@ -18,6 +18,7 @@ struct cgh_plan {
   int obj_h, obj_w, holo_h, holo_w, s, n_layers, levels;
   int deterministic;  // CGH_PLAN_DETERMINISTIC: no split-K atomics
   int max_ksteps;     // cgh_plan_set_tuning: cap on K steps per stage-2 chain (0 = automatic)
+  int contraction;    // cgh_plan_set_contraction: CGH_CONTRACT_AUTO / _ROWS / _COLS
   double pitch, wavelength;
   double z[CGH_MAX_LAYERS];
   double a_frac[CGH_MAX_LAYERS];     // frac(a_z) in [0,1)

@@ -70,21 +70,58 @@ __device__ int block_scan_flags(int f, int* s_warp, int* total) {
 // Per layer: compacted object rows / columns in 32-pixel bands (a band is kept when one
 // of the layer's LLL blocks lies in it), entries past the object edge set to -1.  Also the
 // band index of every 32-wide K step: stage-1 A reads fringe columns 32*band directly.
-__global__ void __launch_bounds__(1024) k_tc_compact(TcFlags fl, int H, int W, int* __restrict__ rows,
-                                                     int* __restrict__ cols, int* __restrict__ kr_pad,
-                                                     int* __restrict__ kc_pad, int ld_rows, int ld_cols,
-                                                     int* __restrict__ rband, int* __restrict__ cband) {
+// Contraction order: the "rows" outputs (stage-2 K) take the object rows, or, for a square
+// object, the object columns when their sum over the layers is the smaller (or the plan
+// asks for columns): H^T = sum_z E_z A^_z^T E_z^T is then computed and written transposed.
+// Every CTA derives the same decision from the band flags of all layers; CTA 0 records it.
+__global__ void __launch_bounds__(1024) k_tc_compact(TcFlags fl, int H, int W, int Z, int order,
+                                                     int* __restrict__ rows, int* __restrict__ cols,
+                                                     int* __restrict__ kr_pad, int* __restrict__ kc_pad, int ld_rows,
+                                                     int ld_cols, int* __restrict__ rband, int* __restrict__ cband,
+                                                     int* __restrict__ orient) {
   __shared__ int s_warp[33];
+  __shared__ int s_sum[2];
   pdl_wait();
   pdl_trigger();
   const int z = blockIdx.x, t = threadIdx.x;
+  int tr = 0;
+  if (H == W && order != CGH_CONTRACT_ROWS) {
+    if (order == CGH_CONTRACT_COLS) {
+      tr = 1;
+    } else {
+      if (t < 2) s_sum[t] = 0;
+      __syncthreads();
+      const int n8 = H >> 3, n32 = (n8 + 3) >> 2;
+      int cr = 0, cc = 0;
+      for (int e = t; e < Z * n32; e += blockDim.x) {
+        const int zz = e / n32, b = e - (e / n32) * n32;
+        int fr = 0, fc = 0;
+        for (int q = 4 * b; q < 4 * b + 4 && q < n8; ++q) {
+          fr |= fl.rowband[(size_t)zz * n8 + q];
+          fc |= fl.colband[(size_t)zz * n8 + q];
+        }
+        cr += fr ? 1 : 0;
+        cc += fc ? 1 : 0;
+      }
+      cr = __reduce_add_sync(0xffffffffu, cr);
+      cc = __reduce_add_sync(0xffffffffu, cc);
+      if ((t & 31) == 0) {
+        atomicAdd(&s_sum[0], cr);
+        atomicAdd(&s_sum[1], cc);
+      }
+      __syncthreads();
+      tr = s_sum[1] < s_sum[0] ? 1 : 0;
+    }
+  }
+  if (z == 0 && t == 0) *orient = tr;
   for (int axis = 0; axis < 2; ++axis) {
+    const int role = axis ^ tr;  // 0: the stage-2 contraction ("rows") outputs, 1: "cols"
     const int n8 = axis == 0 ? (H >> 3) : (W >> 3);
     const int n32 = (n8 + 3) >> 2;
     const int lim = axis == 0 ? H : W;
     const uint8_t* band = axis == 0 ? fl.rowband + (size_t)z * (H >> 3) : fl.colband + (size_t)z * (W >> 3);
-    int* out = axis == 0 ? rows + (size_t)z * ld_rows : cols + (size_t)z * ld_cols;
-    int* bout = axis == 0 ? rband + (size_t)z * (ld_rows / 32) : cband + (size_t)z * (ld_cols / 32);
+    int* out = role == 0 ? rows + (size_t)z * ld_rows : cols + (size_t)z * ld_cols;
+    int* bout = role == 0 ? rband + (size_t)z * (ld_rows / 32) : cband + (size_t)z * (ld_cols / 32);
     int f = 0;
     if (t < n32)
       for (int q = 4 * t; q < 4 * t + 4 && q < n8; ++q) f |= band[q];
@@ -95,9 +132,9 @@ __global__ void __launch_bounds__(1024) k_tc_compact(TcFlags fl, int H, int W, i
         const int v = 32 * t + q;
         out[32 * r + q] = v < lim ? v : -1;
       }
-      bout[r] = axis == 0 ? t : 32 * t;
+      bout[r] = role == 0 ? t : 32 * t;
     }
-    if (t == 0) (axis == 0 ? kr_pad : kc_pad)[z] = 32 * total;
+    if (t == 0) (role == 0 ? kr_pad : kc_pad)[z] = 32 * total;
     __syncthreads();
   }
 }
@@ -115,17 +152,72 @@ __global__ void k_tc_kmap2(const int* __restrict__ kr_pad, const int* __restrict
   for (int k = threadIdx.x; k < n; k += blockDim.x) kmap2[off / 32 + k] = z * H + 32 * rband[(size_t)z * ld_band + k];
 }
 
-// 64 x A^_z at (rows[k], cols[c]) from the Haar coefficients and the selection flags:
+// 64 x A^_z at eight consecutive pixels of one object row (ALONG_Y = false: (y0, x0 + q))
+// or one object column (ALONG_Y = true: (y0 + q, x0)), the run starting on a multiple of 8,
+// from the Haar coefficients and the selection flags:
 // V = LLL + sum_{l=3,2,1} 4^(3-l) [selected] (sx X + sy Y + sx sy D), with sx = -1 for the
-// right child column and sy = -1 for the lower child row of the level-l cell.  One thread
-// builds 8 consecutive compacted columns: they are one 8-pixel band of the object (or all
-// padding), so they share one LLL block, one level-3 block, two level-2 and four level-1
-// blocks.
+// right child column and sy = -1 for the lower child row of the level-l cell.  The run
+// shares one LLL block and one level-3 block, and spans two level-2 and four level-1 blocks.
+template <bool ALONG_Y>
+__device__ __forceinline__ void idwt_run8(const int32_t* __restrict__ P, const TcFlags& fl, int z, int H, int W,
+                                          int y0, int x0, int* V) {
+  const int h3 = H >> 3, w3 = W >> 3, by3 = y0 >> 3, bx3 = x0 >> 3;
+  const size_t f3 = ((size_t)z * h3 + by3) * w3 + bx3;
+  if (fl.occ3[f3]) {
+    const int LL = P[(size_t)by3 * W + bx3];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) V[q] = LL;
+  }
+  if (fl.sel[3][f3]) {
+    const int X = P[(size_t)by3 * W + w3 + bx3], Y = P[(size_t)(h3 + by3) * W + bx3],
+              D = P[(size_t)(h3 + by3) * W + w3 + bx3];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int y = ALONG_Y ? y0 + q : y0, x = ALONG_Y ? x0 : x0 + q;
+      const int sx = ((x >> 2) & 1) ? -1 : 1, sy = ((y >> 2) & 1) ? -1 : 1;
+      V[q] += sx * X + sy * Y + sx * sy * D;
+    }
+  }
+  const int h2 = H >> 2, w2 = W >> 2;
+#pragma unroll
+  for (int g = 0; g < 2; ++g) {
+    const int by2 = ALONG_Y ? (y0 >> 2) + g : y0 >> 2, bx2 = ALONG_Y ? x0 >> 2 : (x0 >> 2) + g;
+    if (fl.sel[2][((size_t)z * h2 + by2) * w2 + bx2]) {
+      const int X = P[(size_t)by2 * W + w2 + bx2], Y = P[(size_t)(h2 + by2) * W + bx2],
+                D = P[(size_t)(h2 + by2) * W + w2 + bx2];
+#pragma unroll
+      for (int q = 4 * g; q < 4 * g + 4; ++q) {
+        const int y = ALONG_Y ? y0 + q : y0, x = ALONG_Y ? x0 : x0 + q;
+        const int sx = ((x >> 1) & 1) ? -1 : 1, sy = ((y >> 1) & 1) ? -1 : 1;
+        V[q] += 4 * (sx * X + sy * Y + sx * sy * D);
+      }
+    }
+  }
+  const int h1 = H >> 1, w1 = W >> 1;
+#pragma unroll
+  for (int g = 0; g < 4; ++g) {
+    const int by1 = ALONG_Y ? (y0 >> 1) + g : y0 >> 1, bx1 = ALONG_Y ? x0 >> 1 : (x0 >> 1) + g;
+    if (fl.sel[1][((size_t)z * h1 + by1) * w1 + bx1]) {
+      const int X = P[(size_t)by1 * W + w1 + bx1], Y = P[(size_t)(h1 + by1) * W + bx1],
+                D = P[(size_t)(h1 + by1) * W + w1 + bx1];
+#pragma unroll
+      for (int q = 2 * g; q < 2 * g + 2; ++q) {
+        const int y = ALONG_Y ? y0 + q : y0, x = ALONG_Y ? x0 : x0 + q;
+        const int sx = (x & 1) ? -1 : 1, sy = (y & 1) ? -1 : 1;
+        V[q] += 16 * (sx * X + sy * Y + sx * sy * D);
+      }
+    }
+  }
+}
+
+// Stage-1 B operand: 64 x A^_z at (rows[k], cols[c .. c+7]), or, in the transposed order,
+// at (cols[c .. c+7], rows[k]) (the "rows" then hold object columns).  One thread builds the
+// eight compacted columns of one 8-pixel band (or of padding).
 template <bool F16>
 __global__ void k_tc_idwt(const int32_t* __restrict__ coef, TcFlags fl, const int* __restrict__ rows,
                           const int* __restrict__ cols, const int* __restrict__ kr_pad,
-                          const int* __restrict__ kc_pad, int H, int W, int ld_rows, int ld_cols,
-                          uint16_t* __restrict__ B1, long long b1_plane, int ldb1) {
+                          const int* __restrict__ kc_pad, const int* __restrict__ orient, int H, int W,
+                          int ld_rows, int ld_cols, uint16_t* __restrict__ B1, long long b1_plane, int ldb1) {
   pdl_wait();
   pdl_trigger();
   const int z = blockIdx.z;
@@ -140,51 +232,10 @@ __global__ void k_tc_idwt(const int32_t* __restrict__ coef, TcFlags fl, const in
   for (int q = 0; q < 8; ++q) V[q] = 0;
   if (i >= 0 && j0 >= 0) {
     const int32_t* P = coef + (size_t)z * H * W;
-    const int h3 = H >> 3, w3 = W >> 3, by3 = i >> 3, bx3 = j0 >> 3;
-    const size_t f3 = ((size_t)z * h3 + by3) * w3 + bx3;
-    if (fl.occ3[f3]) {
-      const int LL = P[(size_t)by3 * W + bx3];
-#pragma unroll
-      for (int q = 0; q < 8; ++q) V[q] = LL;
-    }
-    if (fl.sel[3][f3]) {
-      const int X = P[(size_t)by3 * W + w3 + bx3], Y = P[(size_t)(h3 + by3) * W + bx3],
-                D = P[(size_t)(h3 + by3) * W + w3 + bx3];
-      const int sy = ((i >> 2) & 1) ? -1 : 1;
-#pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        const int sx = (q >> 2) ? -1 : 1;
-        V[q] += sx * X + sy * Y + sx * sy * D;
-      }
-    }
-    const int h2 = H >> 2, w2 = W >> 2, by2 = i >> 2, sy2 = ((i >> 1) & 1) ? -1 : 1;
-#pragma unroll
-    for (int g = 0; g < 2; ++g) {
-      const int bx2 = (j0 >> 2) + g;
-      if (fl.sel[2][((size_t)z * h2 + by2) * w2 + bx2]) {
-        const int X = P[(size_t)by2 * W + w2 + bx2], Y = P[(size_t)(h2 + by2) * W + bx2],
-                  D = P[(size_t)(h2 + by2) * W + w2 + bx2];
-#pragma unroll
-        for (int q = 4 * g; q < 4 * g + 4; ++q) {
-          const int sx = ((q >> 1) & 1) ? -1 : 1;
-          V[q] += 4 * (sx * X + sy2 * Y + sx * sy2 * D);
-        }
-      }
-    }
-    const int h1 = H >> 1, w1 = W >> 1, by1 = i >> 1, sy1 = (i & 1) ? -1 : 1;
-#pragma unroll
-    for (int g = 0; g < 4; ++g) {
-      const int bx1 = (j0 >> 1) + g;
-      if (fl.sel[1][((size_t)z * h1 + by1) * w1 + bx1]) {
-        const int X = P[(size_t)by1 * W + w1 + bx1], Y = P[(size_t)(h1 + by1) * W + bx1],
-                  D = P[(size_t)(h1 + by1) * W + w1 + bx1];
-#pragma unroll
-        for (int q = 2 * g; q < 2 * g + 2; ++q) {
-          const int sx = (q & 1) ? -1 : 1;
-          V[q] += 16 * (sx * X + sy1 * Y + sx * sy1 * D);
-        }
-      }
-    }
+    if (*orient)
+      idwt_run8<true>(P, fl, z, H, W, j0, i, V);
+    else
+      idwt_run8<false>(P, fl, z, H, W, i, j0, V);
   }
   uint32_t hi[4], lo[4];
 #pragma unroll
@@ -222,6 +273,7 @@ struct cgh_tc_state {
   TcFlags fl;
   int *rows, *cols, *kr_pad, *kc_pad;
   int *rband, *cband, *kmap2;  // K-step band maps (see k_tc_compact, k_tc_kmap2)
+  int* orient;                 // device: 1 when the last call contracted over object columns
   uint16_t *B1, *Y;
   long long b1_plane, y_plane;
   CUtensorMap mB1, mY;
@@ -260,6 +312,8 @@ static int tc_ensure(const cgh_plan* pc) {
   TC_TRY(cudaMalloc(&t->rband, (size_t)Z * (t->kr_alloc / 32) * sizeof(int)), "tensor-core scratch: bands");
   TC_TRY(cudaMalloc(&t->cband, (size_t)Z * (t->kc_alloc / 32) * sizeof(int)), "tensor-core scratch: bands");
   TC_TRY(cudaMalloc(&t->kmap2, (size_t)(t->ktot_alloc / 32) * sizeof(int)), "tensor-core scratch: K map");
+  TC_TRY(cudaMalloc(&t->orient, sizeof(int)), "tensor-core scratch: order");
+  TC_TRY(cudaMemset(t->orient, 0, sizeof(int)), "tensor-core scratch: order");
   t->b1_plane = (long long)t->ktot_alloc * t->kc_alloc;
   t->y_plane = (long long)p->holo_w * t->ktot_alloc;
   TC_TRY(cudaMalloc(&t->B1, 2 * t->b1_plane * sizeof(uint16_t)), "tensor-core scratch: B1");
@@ -286,6 +340,7 @@ void tc_destroy(cgh_plan* p) {
   cudaFree(t->rband);
   cudaFree(t->cband);
   cudaFree(t->kmap2);
+  cudaFree(t->orient);
   cudaFree(t->B1);
   cudaFree(t->Y);
   free(t);
@@ -327,8 +382,8 @@ static int tc_prep(const cgh_plan* p, const int32_t* coef, const int32_t* const*
   TC_CK(launch_pdl(k_tc_scatter, dim3(64, 4), dim3(256), 0, st, lists[0], lists[1], lists[2], lists[3], d_counts,
                    t->fl, H, W, Z),
         "tc: scatter");
-  TC_CK(launch_pdl(k_tc_compact, dim3(Z), dim3(1024), 0, st, t->fl, H, W, t->rows, t->cols, t->kr_pad, t->kc_pad,
-                   t->kr_alloc, t->kc_alloc, t->rband, t->cband),
+  TC_CK(launch_pdl(k_tc_compact, dim3(Z), dim3(1024), 0, st, t->fl, H, W, Z, p->contraction, t->rows, t->cols,
+                   t->kr_pad, t->kc_pad, t->kr_alloc, t->kc_alloc, t->rband, t->cband, t->orient),
         "tc: compact");
   TC_CK(launch_pdl(k_tc_kmap2, dim3(Z), dim3(256), 0, st, (const int*)t->kr_pad, (const int*)t->rband,
                    t->kr_alloc / 32, H, Z, t->kmap2),
@@ -336,8 +391,8 @@ static int tc_prep(const cgh_plan* p, const int32_t* coef, const int32_t* const*
   {
     dim3 blk(8, 32), grid((t->kc_alloc / 8 + 7) / 8, (t->kr_alloc + 31) / 32, Z);
     TC_CK(launch_pdl(k_tc_idwt<F16>, grid, blk, 0, st, coef, t->fl, (const int*)t->rows, (const int*)t->cols,
-                     (const int*)t->kr_pad, (const int*)t->kc_pad, H, W, t->kr_alloc, t->kc_alloc, t->B1, t->b1_plane,
-                     t->kc_alloc),
+                     (const int*)t->kr_pad, (const int*)t->kc_pad, (const int*)t->orient, H, W, t->kr_alloc,
+                     t->kc_alloc, t->B1, t->b1_plane, t->kc_alloc),
           "tc: idwt");
   }
 
@@ -384,6 +439,7 @@ static void stage2_args(const cgh_plan* p, bool f16, float2* holo, int S, TcGemm
   a.H = holo;
   a.ldh = p->holo_w;
   a.h_vec4 = ((p->holo_w & 1) == 0) && (((uintptr_t)holo & 15) == 0);
+  a.h_transposed = t->orient;
   a.status = p->d_status;
   a.a_kmap = t->kmap2;
   tiles = dim3((p->holo_h + TC_BM - 1) / TC_BM, (p->holo_w + TC_BN - 1) / TC_BN, S);

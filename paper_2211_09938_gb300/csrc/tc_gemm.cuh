@@ -158,6 +158,7 @@ struct TcGemmArgs {
   float2* H;         // EPI_H: complex output [M][N]
   int ldh;
   int h_vec4;        // H rows 16-byte aligned: add pairs of pixels with float4 atomics
+  const int* h_transposed;  // EPI_H, optional device flag: add C[m][n] into H[n][m] (square H)
   uint16_t* Y;       // EPI_Y: 4 planes [plane][M][ldy]
   long long y_plane;
   int ldy;
@@ -484,7 +485,19 @@ __device__ __forceinline__ void tc_gemm_body(const Src& src, uint8_t* smem, uint
         tmem_ld32(t_lane + c0, re);
         if (KIND != KIND_TEST) tmem_ld32(t_lane + 128 + c0, im);
         tmem_ld_wait();
-        if (EPI == EPI_H || EPI == EPI_F) {
+        if (EPI == EPI_H && args.h_transposed && *args.h_transposed) {
+          // transposed problem: C[m][n] belongs at H[n][m]; the 32 lanes hold 32 consecutive
+          // m, so each atomic instruction covers 256 contiguous bytes of one H row
+          if (row < ti.row_lim) {
+            const int nv = min(32, ti.col_lim - (ti.out_col0 + c0));
+            float2* dst = args.H + (size_t)(ti.out_col0 + c0) * args.ldh + row;
+#pragma unroll
+            for (int j = 0; j < 32; ++j)
+              if (j < nv)
+                atomicAdd(dst + (size_t)j * args.ldh,
+                          make_float2(__uint_as_float(re[j]) * args.scale, __uint_as_float(im[j]) * args.scale));
+          }
+        } else if (EPI == EPI_H || EPI == EPI_F) {
           if (row < ti.row_lim) {
             float2* dst = (EPI == EPI_H ? args.H + (size_t)row * args.ldh : args.F + (size_t)row * args.ldf) +
                           ti.out_col0 + c0;

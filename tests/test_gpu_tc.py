@@ -55,9 +55,11 @@ SCENES = {
 }
 
 
-def run(torch, sc, form, thresholds=None):
+def run(torch, sc, form, thresholds=None, order=None, dims=False):
     from paper_2211_09938_gb300 import Plan
     plan = Plan.for_scene(sc)
+    if order is not None:
+        plan.set_contraction(order)
     I = torch.from_numpy(sc["intensity"]).cuda()
     L = torch.from_numpy(sc["layer"]).cuda()
     S = torch.from_numpy(sc["saliency"]).cuda()
@@ -68,6 +70,9 @@ def run(torch, sc, form, thresholds=None):
     torch.cuda.synchronize()
     assert plan.status() == 0
     ref_lists = O.progressive_lists(sc["saliency"], sc["layer"], plan.n_layers, thr)
+    if dims:
+        kr, kc = plan.tc_layer_dims()
+        return H.cpu().numpy(), ref_lists, (sum(kr), sum(kc))
     return H.cpu().numpy(), ref_lists
 
 
@@ -90,3 +95,46 @@ def test_progressive_tc_paper_scale(torch_cuda, form, tol):
     err = O.rel_l2(H, Href)
     print(f"{form} 512->1024 Z16: rel-L2 {err:.3e}")
     assert err <= tol
+
+
+def _transposed(sc):
+    t = dict(sc)
+    for k in ("intensity", "layer", "saliency"):
+        t[k] = np.ascontiguousarray(sc[k].T)
+    return t
+
+
+def test_contraction_orders(torch_cuda):
+    """H = sum_z E_z A^_z E_z^T contracted over the layers' object rows, or (square object)
+    over their columns with H written transposed: both orders match the oracle; the
+    automatic choice takes the smaller contraction; transposing the scene transposes the
+    hologram and flips the automatic choice; a non-square object keeps rows."""
+    from paper_2211_09938_gb300 import Plan
+    torch = torch_cuda
+    sc = scenes.paper_scene()
+    Href = O.progressive_hologram(sc["intensity"], sc["layer"],
+                                  O.progressive_lists(sc["saliency"], sc["layer"], 16, scenes.THRESHOLDS_U8),
+                                  O.geometry_of(sc))
+    got = {}
+    for order in (Plan.CONTRACT_ROWS, Plan.CONTRACT_COLS, Plan.CONTRACT_AUTO):
+        H, _, (sr, sc_) = run(torch, sc, "tc_fp16x3", order=order, dims=True)
+        err = O.rel_l2(H, Href)
+        print(f"order {order}: contraction K {sr} (other axis {sc_}), rel-L2 {err:.3e}")
+        assert err <= FP16X3_TOL
+        got[order] = (H, sr, sc_)
+    r_rows, r_cols = got[Plan.CONTRACT_ROWS][1], got[Plan.CONTRACT_COLS][1]
+    assert r_rows != r_cols and got[Plan.CONTRACT_AUTO][1] == min(r_rows, r_cols)
+    # the transposed scene: same hologram transposed, the other order chosen
+    st = _transposed(sc)
+    Ht, _, (srt, _) = run(torch, st, "tc_fp16x3", dims=True)
+    assert O.rel_l2(Ht, got[Plan.CONTRACT_AUTO][0].T) <= 2 * FP16X3_TOL
+    assert srt == min(r_rows, r_cols)
+    # non-square object: the column order is not available and rows are used
+    rect = dict(scenes.random_scene(83, 64, 128, 3, graded=True))
+    rect["intensity"] = np.ascontiguousarray(rect["intensity"][:, :40])
+    rect["layer"] = np.ascontiguousarray(rect["layer"][:, :40])
+    rect["saliency"] = np.ascontiguousarray(rect["saliency"][:, :40])
+    rect["holo"] = (128, 80)
+    H, ref_lists = run(torch, rect, "tc_fp16x3", order=Plan.CONTRACT_COLS)
+    Hr = O.progressive_hologram(rect["intensity"], rect["layer"], ref_lists, O.geometry_of(rect))
+    assert O.rel_l2(H, Hr) <= FP16X3_TOL
