@@ -149,8 +149,8 @@ int cgh_haar_decompose(const cgh_plan* plan, const uint8_t* intensity, const uin
  * maximum) and steps 2-5 (blocks above a threshold get that level's hologram).
  * A level-l block (2^l x 2^l pixels) of layer z is selected iff layer z owns at least
  * one of its pixels and (threshold < 0 or max(saliency over the block) > threshold).
- *   saliency   uint8 [obj_h][obj_w] (may be NULL when threshold < 0)
- *   layer_idx  uint8 [obj_h][obj_w]
+ *   saliency   uint8 [obj_h][obj_w] (may be NULL when threshold < 0), 8-byte aligned
+ *   layer_idx  uint8 [obj_h][obj_w], 8-byte aligned (blocks are read a row at a time)
  *   threshold  -1 (occupancy only: the LLL list) or 0..255 (strict comparison)
  *   level      1..3
  *   list       int32 [capacity] output, entries (z << 24) | (by << 12) | bx in
@@ -196,6 +196,7 @@ int cgh_select_blocks_noalloc(const uint8_t* saliency, const uint8_t* layer_idx,
  * blocks above their saliency thresholds).  Same results as four cgh_select_blocks calls:
  *   lists[0]  LLL list    = cgh_select_blocks(threshold -1, level 3)
  *   lists[l]  level l     = cgh_select_blocks(thresholds[l-1], level l), l = 1, 2, 3
+ *   saliency, layer_idx  uint8 [obj_h][obj_w], 8-byte aligned
  *   thresholds  HOST int[3] (levels 1, 2, 3), each -1..255
  *   lists       HOST array of 4 device pointers;  capacities  HOST int[4]
  *   d_counts    device int32 [4][2] output, ([written, total] per list, as d_count of

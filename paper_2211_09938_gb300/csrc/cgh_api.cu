@@ -192,6 +192,8 @@ int cgh_select_blocks(const cgh_plan* p, const uint8_t* saliency, const uint8_t*
     return cgh_fail(CGH_ERR_ARG, "cgh_select_blocks: threshold %d not in -1..255", threshold);
   if (threshold >= 0 && !saliency) return cgh_fail(CGH_ERR_ARG, "cgh_select_blocks: saliency is NULL");
   if (capacity < 0) return cgh_fail(CGH_ERR_ARG, "cgh_select_blocks: capacity < 0");
+  if (((uintptr_t)layer_idx & 7) || (threshold >= 0 && ((uintptr_t)saliency & 7)))
+    return cgh_fail(CGH_ERR_ARG, "cgh_select_blocks: saliency and layer_idx must be 8-byte aligned");
   prof_mark(p, CGH_PROF_SELECT, 0, (cudaStream_t)stream);
   CHECK_CUDA(launch_select(p->obj_h, p->obj_w, p->n_layers, threshold >= 0 ? saliency : NULL, layer_idx,
                            threshold, level, list, d_count, capacity, p->d_chunk_cnt, p->d_chunk_off,
@@ -206,6 +208,8 @@ int cgh_select_progressive(const cgh_plan* p, const uint8_t* saliency, const uin
                            int32_t* d_counts, void* stream) {
   if (!p || !saliency || !layer_idx || !thresholds || !lists || !capacities || !d_counts)
     return cgh_fail(CGH_ERR_ARG, "cgh_select_progressive: NULL argument");
+  if (((uintptr_t)layer_idx & 7) || ((uintptr_t)saliency & 7))
+    return cgh_fail(CGH_ERR_ARG, "cgh_select_progressive: saliency and layer_idx must be 8-byte aligned");
   SelTasks T;
   memset(&T, 0, sizeof(T));
   T.n = 4;

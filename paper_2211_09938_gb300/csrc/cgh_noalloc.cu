@@ -62,6 +62,8 @@ extern "C" int cgh_select_blocks_noalloc(const uint8_t* saliency, const uint8_t*
   if (threshold >= 0 && !saliency)
     return cgh_fail(CGH_ERR_ARG, "cgh_select_blocks_noalloc: saliency is NULL");
   if (capacity < 0) return cgh_fail(CGH_ERR_ARG, "cgh_select_blocks_noalloc: capacity < 0");
+  if (((uintptr_t)layer_idx & 7) || (threshold >= 0 && ((uintptr_t)saliency & 7)))
+    return cgh_fail(CGH_ERR_ARG, "cgh_select_blocks_noalloc: saliency and layer_idx must be 8-byte aligned");
   const long long need = (long long)n_layers * select_num_chunks(obj_h, obj_w, level);
   if (need > CGH_NOALLOC_HALF)
     return cgh_fail(CGH_ERR_ARG,

@@ -8,6 +8,8 @@
 
 #include "cgh_internal.h"
 
+#include <type_traits>
+
 // ---------------------------------------------------------------------------
 // (A1) fringe tables.  tab[z][l][kind][idx], offset d = idx - tab_off:
 //   kind 0: b_l(d) = sum_{t<2^l} f_z(d - s t)
@@ -154,22 +156,48 @@ cudaError_t launch_haar(const cgh_plan* p, const uint8_t* I, const uint8_t* L, i
 // A block is summarised by the bit mask of the layers it may contribute to: the layers
 // owning one of its pixels, cleared when the block maximum of the saliency does not
 // exceed the threshold.
-__device__ __forceinline__ unsigned long long block_layer_mask(const uint8_t* __restrict__ sal,
-                                                               const uint8_t* __restrict__ L,
-                                                               int W, int k, int by, int bx,
-                                                               int threshold, int Z) {
+// The k x k block (k = 2^LEVEL) is read one row at a time as a k-byte vector (rows start on
+// multiples of k bytes because the object width is a multiple of 8), so a thread issues 2k
+// independent loads instead of 2k^2 dependent byte loads.
+template <int LEVEL>
+__device__ __forceinline__ unsigned long long block_layer_mask_k(const uint8_t* __restrict__ sal,
+                                                                 const uint8_t* __restrict__ L, int W, int by,
+                                                                 int bx, int threshold, int Z) {
+  constexpr int k = 1 << LEVEL;
+  using V = typename std::conditional<k == 8, uint2, typename std::conditional<k == 4, unsigned, unsigned short>::type>::type;
   unsigned long long occ = 0ull;
   int mx = 0;
+  V lv[k], sv[k];
+#pragma unroll
   for (int r = 0; r < k; ++r) {
     const size_t o = (size_t)(by * k + r) * W + (size_t)bx * k;
+    lv[r] = *reinterpret_cast<const V*>(L + o);
+    if (sal) sv[r] = *reinterpret_cast<const V*>(sal + o);
+  }
+#pragma unroll
+  for (int r = 0; r < k; ++r) {
+    uint8_t lb[k], sb[k];
+    memcpy(lb, &lv[r], k);
+    if (sal) memcpy(sb, &sv[r], k);
+#pragma unroll
     for (int c = 0; c < k; ++c) {
-      const int lz = L[o + c];
+      const int lz = lb[c];
       if (lz < Z) occ |= 1ull << lz;
-      if (sal) mx = max(mx, (int)sal[o + c]);
+      if (sal) mx = max(mx, (int)sb[c]);
     }
   }
   if (threshold >= 0 && mx <= threshold) occ = 0ull;
   return occ;
+}
+
+__device__ __forceinline__ unsigned long long block_layer_mask(const uint8_t* __restrict__ sal,
+                                                               const uint8_t* __restrict__ L, int W, int level,
+                                                               int by, int bx, int threshold, int Z) {
+  switch (level) {
+    case 1: return block_layer_mask_k<1>(sal, L, W, by, bx, threshold, Z);
+    case 2: return block_layer_mask_k<2>(sal, L, W, by, bx, threshold, Z);
+    default: return block_layer_mask_k<3>(sal, L, W, by, bx, threshold, Z);
+  }
 }
 
 int select_num_chunks(int obj_h, int obj_w, int level) {
@@ -201,7 +229,7 @@ __global__ void __launch_bounds__(CGH_SEL_CHUNK) k_select_count(const uint8_t* _
   __syncthreads();
   const int b = chunk * CGH_SEL_CHUNK + threadIdx.x;
   unsigned long long m =
-      b < nb ? block_layer_mask(sal, L, W, 1 << level, b / nbx, b % nbx, tk.threshold, Z) : 0ull;
+      b < nb ? block_layer_mask(sal, L, W, level, b / nbx, b % nbx, tk.threshold, Z) : 0ull;
   while (m) {
     atomicAdd(&s_cnt[__ffsll((long long)m) - 1], 1);
     m &= m - 1ull;
@@ -261,7 +289,7 @@ __global__ void __launch_bounds__(CGH_SEL_CHUNK) k_select_scatter(
   const int b = chunk * CGH_SEL_CHUNK + threadIdx.x;
   const int by = b / nbx, bx = b - by * nbx;
   const unsigned long long m =
-      b < nb ? block_layer_mask(sal, L, W, 1 << level, by, bx, tk.threshold, Z) : 0ull;
+      b < nb ? block_layer_mask(sal, L, W, level, by, bx, tk.threshold, Z) : 0ull;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const unsigned below = (1u << lane) - 1u;
   for (int z = 0; z < Z; ++z) {

@@ -269,7 +269,8 @@ int tc_init_attributes() {
 struct cgh_tc_state {
   int kc_alloc, kr_alloc, ktot_alloc;
   uint8_t* flags;  // one block: occ3 | rowband | colband | sel1 | sel2 | sel3
-  size_t flags_bytes;
+  size_t flags_bytes, flags_alloc;  // used / allocated (a multiple of 16 bytes)
+  int flags_dirty;  // host: flags may hold a previous call's marks (see tc_run)
   TcFlags fl;
   int *rows, *cols, *kr_pad, *kc_pad;
   int *rband, *cband, *kmap2;  // K-step band maps (see k_tc_compact, k_tc_kmap2)
@@ -297,7 +298,9 @@ static int tc_ensure(const cgh_plan* pc) {
     rc = cgh_cuda_check((expr), (what));    \
     if (rc != CGH_OK) goto fail;            \
   } while (0)
-  TC_TRY(cudaMalloc(&t->flags, t->flags_bytes), "tensor-core scratch: flags");
+  t->flags_alloc = (t->flags_bytes + 15) & ~(size_t)15;
+  TC_TRY(cudaMalloc(&t->flags, t->flags_alloc), "tensor-core scratch: flags");
+  TC_TRY(cudaMemset(t->flags, 0, t->flags_alloc), "tensor-core scratch: flags");
   t->fl.occ3 = t->flags;
   t->fl.rowband = t->fl.occ3 + n3;
   t->fl.colband = t->fl.rowband + (size_t)Z * (H >> 3);
@@ -378,7 +381,10 @@ static int tc_prep(const cgh_plan* p, const int32_t* coef, const int32_t* const*
                    cudaStream_t st) {
   cgh_tc_state* t = p->tc;
   const int H = p->obj_h, W = p->obj_w, Z = p->n_layers;
-  TC_CK(cudaMemsetAsync(t->flags, 0, t->flags_bytes, st), "tc: clear flags");
+  // the flags are clear unless a call left them marked (the single-scene path clears them in
+  // its stage-1 kernel for the next call)
+  if (t->flags_dirty) TC_CK(cudaMemsetAsync(t->flags, 0, t->flags_bytes, st), "tc: clear flags");
+  t->flags_dirty = 1;
   TC_CK(launch_pdl(k_tc_scatter, dim3(64, 4), dim3(256), 0, st, lists[0], lists[1], lists[2], lists[3], d_counts,
                    t->fl, H, W, Z),
         "tc: scatter");
@@ -455,7 +461,10 @@ static int tc_run(const cgh_plan* p, const int32_t* coef, const int32_t* const* 
   const CUtensorMap *mEZ, *mEZt;
   int rc = eops_get(p, F16 ? 1 : 0, &mEZ, &mEZt, st);
   if (rc != CGH_OK) return rc;
-  if (!accumulate) TC_CK(cudaMemsetAsync(holo, 0, (size_t)p->holo_h * p->holo_w * sizeof(float2), st), "tc: clear");
+  // H is cleared by the stage-1 kernel's idle warps when it can be cleared in float4 units
+  const size_t hpix = (size_t)p->holo_h * p->holo_w;
+  const bool h_zero_in_stage1 = !accumulate && (hpix % 2 == 0) && (((uintptr_t)holo & 15) == 0);
+  if (!accumulate && !h_zero_in_stage1) TC_CK(cudaMemsetAsync(holo, 0, hpix * sizeof(float2), st), "tc: clear");
   prof_mark(p, CGH_PROF_TC_PREP, 0, st);
   rc = tc_prep<F16>(p, coef, lists, d_counts, st);
   if (rc != CGH_OK) return rc;
@@ -463,10 +472,17 @@ static int tc_run(const cgh_plan* p, const int32_t* coef, const int32_t* const* 
   TcGemmArgs a;
   dim3 tiles;
   stage1_args(p, F16, a, tiles);
+  a.zero_ptr[0] = reinterpret_cast<float4*>(t->flags);  // marks of this call, for the next one
+  a.zero_n[0] = (long long)(t->flags_alloc / 16);
+  if (h_zero_in_stage1) {
+    a.zero_ptr[1] = reinterpret_cast<float4*>(holo);
+    a.zero_n[1] = (long long)(hpix / 2);
+  }
   prof_mark(p, CGH_PROF_TC_STAGE1, 0, st);
   cudaError_t e = launch_gemm<KIND_CR, EPI_Y, F16>(*mEZt, t->mB1, t->mY, a, tiles, st);
   prof_mark(p, CGH_PROF_TC_STAGE1, 1, st);
   TC_CK(e, "tc: stage-1 GEMM");
+  t->flags_dirty = 0;
   const int tm = (p->holo_h + TC_BM - 1) / TC_BM, tn = (p->holo_w + TC_BN - 1) / TC_BN;
   // Stream-K over the (tile, K step) space (chains of at most 32 K steps, or the plan's
   // cap) unless the plan asks for single-writer tiles (deterministic).
@@ -587,7 +603,8 @@ extern "C" int cgh_batch_create(cgh_batch** out, cgh_plan* const* plans, int n, 
   for (int i = 0; i < n; ++i) {
     if (!plans[i] || !intensity[i] || !layer_idx[i] || !saliency[i] || !holos[i])
       return cgh_fail(CGH_ERR_ARG, "cgh_batch_create: NULL pointer for scene %d", i);
-    if (((uintptr_t)intensity[i] & 7) || ((uintptr_t)layer_idx[i] & 7) || ((uintptr_t)holos[i] & 7))
+    if (((uintptr_t)intensity[i] & 7) || ((uintptr_t)layer_idx[i] & 7) || ((uintptr_t)saliency[i] & 7) ||
+        ((uintptr_t)holos[i] & 7))
       return cgh_fail(CGH_ERR_ARG, "cgh_batch_create: misaligned buffer for scene %d", i);
   }
   cgh_batch* b = (cgh_batch*)calloc(1, sizeof(cgh_batch));
@@ -727,6 +744,7 @@ int tc_build_flags(const cgh_plan* p, const int32_t* const* lists, const int32_t
   if (rc != CGH_OK) return rc;
   cgh_tc_state* t = p->tc;
   rc = cgh_cuda_check(cudaMemsetAsync(t->flags, 0, t->flags_bytes, st), "flags: clear");
+  t->flags_dirty = 1;
   if (rc != CGH_OK) return rc;
   k_tc_scatter<<<dim3(64, 4), 256, 0, st>>>(lists[0], lists[1], lists[2], lists[3], d_counts, t->fl, p->obj_h,
                                           p->obj_w, p->n_layers);

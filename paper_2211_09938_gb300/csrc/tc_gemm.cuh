@@ -168,6 +168,8 @@ struct TcGemmArgs {
   float2* F;         // EPI_F: complex output rows (plain stores)
   int ldf;
   int* status;
+  float4* zero_ptr[2];    // single-problem launches: regions the epilogue warps clear before their
+  long long zero_n[2];    // first tile (float4 counts; for the next kernels or the next call)
 };
 
 template <int KIND>
@@ -685,6 +687,12 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm(const __grid_constant__ CUte
     s_off[0] = 0;
     if (args.kr_pad)
       for (int q = 0; q < args.n_layers; ++q) s_off[q + 1] = (o += args.kr_pad[q]);
+  }
+  if (threadIdx.x >= 64) {  // the epilogue warps are idle until the first tile has accumulated
+    const long long t0 = (long long)blockIdx.x * 128 + (threadIdx.x - 64), nt = (long long)gridDim.x * 128;
+#pragma unroll 1
+    for (int r = 0; r < 2; ++r)
+      for (long long i = t0; i < args.zero_n[r]; i += nt) args.zero_ptr[r][i] = make_float4(0.f, 0.f, 0.f, 0.f);
   }
   __syncthreads();
   TcSingleSrc src{&mapA, &mapB, &mapC, &args, s_off,

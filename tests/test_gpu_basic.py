@@ -236,3 +236,19 @@ def test_plain_direct_exact_reduction_large_offsets(torch_cuda):
     m = np.arange(2048)
     exp = 200 * (1j ** ((m[:, None] % 2) + (m[None, :] % 2)))
     assert np.max(np.abs(H - exp)) < 200 * 2e-6
+
+
+def test_selection_rejects_misaligned_inputs(torch_cuda):
+    """Blocks are read a row at a time as 8-byte vectors: saliency and layer maps that do
+    not start on an 8-byte boundary are refused on the host, before anything runs."""
+    torch = torch_cuda
+    from paper_2211_09938_gb300.cgh import CghError
+    sc = scenes.tiny_scene()
+    plan = plan_for(sc)
+    buf = torch.zeros(64 * 64 + 8, dtype=torch.uint8, device="cuda")
+    L = buf[1:1 + 64 * 64].view(64, 64)  # one byte off
+    S = dev(torch, sc["saliency"])
+    with pytest.raises(CghError):
+        plan.select_blocks(S, L, 127, 1)
+    with pytest.raises(CghError):
+        plan.progressive_lists(S, L, scenes.THRESHOLDS_U8)
