@@ -292,6 +292,22 @@ struct TileInfo {
 
 // Work unit t of the persistent grid: (mt fastest, then nt, then the layer / K split).
 // Returns false for units with nothing to do; every role decodes identically.
+// Mode 1 (per layer, compacted): tile (mt, nt) of layer zz.
+__device__ __forceinline__ bool decode_stage1(const TcGemmArgs& a, int mt, int nt, int zz, const int* s_off,
+                                              TileInfo& ti) {
+  const int krz = s_off[zz + 1] - s_off[zz];
+  ti.n_valid = min(TC_BN, krz - nt * TC_BN);
+  if (ti.n_valid <= 0) return false;
+  ti.a_row = zz * a.a_rows_per_z + mt * TC_BM;
+  ti.b_row = s_off[zz] + nt * TC_BN;
+  ti.k_lo = 0;
+  ti.nk = a.kc_pad[zz] / TC_BK;
+  ti.out_col0 = s_off[zz] + nt * TC_BN;
+  ti.col_lim = ti.out_col0 + ti.n_valid;
+  if (a.a_kmap) ti.akm = a.a_kmap + (size_t)zz * a.a_kmap_ld;
+  return ti.nk > 0;
+}
+
 __device__ __forceinline__ bool decode_tile(const TcGemmArgs& a, int t, const int* s_off, int ktot, TileInfo& ti) {
   const int mt = t % a.tm, r = t / a.tm, nt = r % a.tn, zz = r / a.tn;
   ti.out_row0 = mt * TC_BM;
@@ -312,16 +328,7 @@ __device__ __forceinline__ bool decode_tile(const TcGemmArgs& a, int t, const in
     return ti.nk > 0 && ti.n_valid > 0;
   }
   if (a.mode == 1) {
-    const int krz = s_off[zz + 1] - s_off[zz];
-    ti.n_valid = min(TC_BN, krz - nt * TC_BN);
-    if (ti.n_valid <= 0) return false;
-    ti.a_row = zz * a.a_rows_per_z + mt * TC_BM;
-    ti.b_row = s_off[zz] + nt * TC_BN;
-    ti.k_lo = 0;
-    ti.nk = a.kc_pad[zz] / TC_BK;
-    ti.out_col0 = s_off[zz] + nt * TC_BN;
-    ti.col_lim = ti.out_col0 + ti.n_valid;
-    if (a.a_kmap) ti.akm = a.a_kmap + (size_t)zz * a.a_kmap_ld;
+    return decode_stage1(a, mt, nt, zz, s_off, ti);
   } else if (a.mode == 2) {
     const int nkt = ktot / TC_BK, S = a.tz;
     const int k0 = (int)((long long)nkt * zz / S), k1 = (int)((long long)nkt * (zz + 1) / S);
@@ -617,9 +624,21 @@ struct TcSingleSrc {
   const TcGemmArgs* a;
   const int* s_off;
   int ktot;
-  __device__ int total() const { return a->tm * a->tn * a->tz; }
+  const int* s_toff;  // mode 1: first unit of every layer over the non-empty tiles only
+  __device__ int total() const { return a->mode == 1 ? s_toff[a->n_layers] : a->tm * a->tn * a->tz; }
   __device__ bool decode(int t, TileInfo& ti) const {
     ti.item = 0;
+    if (a->mode == 1) {
+      // round robin over the layers' non-empty tiles only, so that no CTA draws more
+      // than its share of real work
+      int zz = 0;
+      while (zz + 1 < a->n_layers && t >= s_toff[zz + 1]) ++zz;
+      const int local = t - s_toff[zz];
+      ti.out_row0 = (local % a->tm) * TC_BM;
+      ti.row_lim = a->M;
+      ti.akm = nullptr;
+      return decode_stage1(*a, local % a->tm, local / a->tm, zz, s_off, ti);
+    }
     return decode_tile(*a, t, s_off, ktot, ti);
   }
   // Units of this CTA.  Round robin over the work units, or (stream-K, split-K mode) one
@@ -681,12 +700,18 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm(const __grid_constant__ CUte
   __shared__ uint32_t s_tmem;
   __shared__ volatile int s_abort;
   __shared__ int s_off[CGH_MAX_LAYERS + 1];
+  __shared__ int s_toff[CGH_MAX_LAYERS + 1];
   pdl_wait();
   if (threadIdx.x == 0) {
-    int o = 0;
+    int o = 0, u = 0;
     s_off[0] = 0;
+    s_toff[0] = 0;
     if (args.kr_pad)
-      for (int q = 0; q < args.n_layers; ++q) s_off[q + 1] = (o += args.kr_pad[q]);
+      for (int q = 0; q < args.n_layers; ++q) {
+        const int kr = args.kr_pad[q];
+        s_off[q + 1] = (o += kr);
+        s_toff[q + 1] = (u += args.tm * ((kr + TC_BN - 1) / TC_BN));
+      }
   }
   if (threadIdx.x >= 64) {  // the epilogue warps are idle until the first tile has accumulated
     const long long t0 = (long long)blockIdx.x * 128 + (threadIdx.x - 64), nt = (long long)gridDim.x * 128;
@@ -696,7 +721,7 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm(const __grid_constant__ CUte
   }
   __syncthreads();
   TcSingleSrc src{&mapA, &mapB, &mapC, &args, s_off,
-                  args.mode == 2 ? (args.kr_pad ? s_off[args.n_layers] : args.K) : 0};
+                  args.mode == 2 ? (args.kr_pad ? s_off[args.n_layers] : args.K) : 0, s_toff};
   tc_gemm_body<KIND, EPI, F16>(src, smem, full_bar, empty_bar, tfull_bar, tempty_bar, &done_bar, &s_tmem,
                                &s_abort);
 }
