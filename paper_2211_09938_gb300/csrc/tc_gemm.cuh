@@ -187,21 +187,27 @@ struct TcCfg<KIND_CC> {
   static constexpr int NA = 4, NB = 4;
 };
 
-// Epilogue staging for EPI_Y: two 32-column chunks of the four output planes (128 rows x
-// 64 bytes x 4 planes each), written by the epilogue warps and stored by TMA.
+// Epilogue staging for EPI_Y: 32-column chunks of the four output planes (128 rows x
+// 64 bytes x 4 planes each), written by the epilogue warps and stored by TMA.  KIND_CR keeps
+// one chunk buffer so that its operand ring gets a fourth stage (its loads, not its
+// epilogue, bound it); the other kinds double-buffer the chunks.
 #define TC_STAGE_Y_BYTES (4 * TC_PLANE_BYTES)
+template <int KIND>
+constexpr int tc_stage_y_bufs() {
+  return KIND == KIND_CR ? 1 : 2;
+}
 
 // Pipeline depth per kind and epilogue, sized so that one CTA per SM fits in shared memory
 // (and owns the tensor memory): > 114 KiB, <= 227 KiB.
 template <int KIND, int EPI>
 constexpr int tc_nst() {
-  return KIND == KIND_TEST ? 8 : (EPI == EPI_Y ? (KIND == KIND_CR ? 3 : 2) : (KIND == KIND_CR ? 4 : 3));
+  return KIND == KIND_TEST ? 8 : (EPI == EPI_Y ? (KIND == KIND_CR ? 4 : 2) : (KIND == KIND_CR ? 4 : 3));
 }
 
 template <int KIND, int EPI>
 constexpr size_t tc_smem_bytes() {
   return (size_t)tc_nst<KIND, EPI>() * (TcCfg<KIND>::NA + TcCfg<KIND>::NB) * TC_PLANE_BYTES +
-         (EPI == EPI_Y ? 2 * TC_STAGE_Y_BYTES : 0) + 1024;
+         (EPI == EPI_Y ? tc_stage_y_bufs<KIND>() * TC_STAGE_Y_BYTES : 0) + 1024;
 }
 
 __device__ __forceinline__ void tma_store_3d(const CUtensorMap* map, const void* src, int c0, int c1, int c2) {
@@ -361,7 +367,8 @@ __device__ __forceinline__ void tc_gemm_body(const Src& src, uint8_t* smem, uint
   constexpr int NA = Cfg::NA, NB = Cfg::NB, NST = tc_nst<KIND, EPI>();
   constexpr uint32_t STAGE = (NA + NB) * TC_PLANE_BYTES;
   volatile int& s_abort = *s_abort_p;
-  uint8_t* const stage_y = smem + NST * STAGE;  // EPI_Y staging (2 x TC_STAGE_Y_BYTES)
+  uint8_t* const stage_y = smem + NST * STAGE;  // EPI_Y staging (tc_stage_y_bufs x TC_STAGE_Y_BYTES)
+  constexpr int YBUFS = tc_stage_y_bufs<KIND>();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   int* const status = src.status();
 
@@ -538,9 +545,9 @@ __device__ __forceinline__ void tc_gemm_body(const Src& src, uint8_t* smem, uint
           const int nv = min(32, ti.n_valid - c0);
           if (use_tma_y) {
             // stage the chunk (64-byte swizzled, as the tensor map stores it), then one TMA store
-            uint8_t* buf = stage_y + (chunk & 1) * TC_STAGE_Y_BYTES;
+            uint8_t* buf = stage_y + (chunk % YBUFS) * TC_STAGE_Y_BYTES;
             if (lane == 0 && quarter == 0) {  // the buffer's previous store has read its data
-              if (prev_committed)
+              if (YBUFS == 2 && prev_committed)
                 bulk_wait_read1();
               else
                 bulk_wait_read0();
@@ -737,10 +744,10 @@ struct alignas(128) TcBatchItem {
   int koff[CGH_MAX_LAYERS + 1];
 };
 
-// Work units of many problems: unit t belongs to the last item whose first unit is <= t.
+// Work units of many problems: unit t belongs to the last item whose first unit is <= t
+// (binary search over the items' first units, read from global memory).
 struct TcBatchSrc {
   const TcBatchItem* items;
-  const int* s_unit0;
   int n, tot;
   int* st;
   __device__ int total() const { return tot; }
@@ -757,7 +764,7 @@ struct TcBatchSrc {
     int lo = 0, hi = n - 1;
     while (lo < hi) {
       const int mid = (lo + hi + 1) >> 1;
-      if (s_unit0[mid] <= t)
+      if (items[mid].unit0 <= t)
         lo = mid;
       else
         hi = mid - 1;
@@ -765,7 +772,7 @@ struct TcBatchSrc {
     ti.item = lo;
     const TcBatchItem& it = items[lo];
     const int ktot = it.a.mode == 2 ? (it.a.kr_pad ? it.koff[it.a.n_layers] : it.a.K) : 0;
-    return decode_tile(it.a, t - s_unit0[lo], it.koff, ktot, ti);
+    return decode_tile(it.a, t - it.unit0, it.koff, ktot, ti);
   }
   __device__ const CUtensorMap* mapA(const TileInfo& ti) const { return &items[ti.item].ma; }
   __device__ const CUtensorMap* mapB(const TileInfo& ti) const { return &items[ti.item].mb; }
@@ -795,11 +802,8 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm_batch(const TcBatchItem* __r
   __shared__ __align__(8) uint64_t full_bar[NST], empty_bar[NST], tfull_bar[2], tempty_bar[2], done_bar;
   __shared__ uint32_t s_tmem;
   __shared__ volatile int s_abort;
-  __shared__ int s_unit0[TC_BATCH_MAX];
   pdl_wait();
-  for (int i = threadIdx.x; i < n; i += blockDim.x) s_unit0[i] = items[i].unit0;
-  __syncthreads();
-  TcBatchSrc src{items, s_unit0, n, total, status};
+  TcBatchSrc src{items, n, total, status};
   tc_gemm_body<KIND, EPI, F16>(src, smem, full_bar, empty_bar, tfull_bar, tempty_bar, &done_bar, &s_tmem,
                                &s_abort);
 }
