@@ -90,7 +90,7 @@ int cgh_plan_create(cgh_plan** out, int obj_h, int obj_w, int holo_h, int holo_w
 
 /*
  * cgh_plan_set_tuning - cap on the 32-wide K steps accumulated in one tensor-memory chain of
- * the stage-2 GEMM (0 = automatic, chosen for occupancy only).  Longer chains are faster;
+ * the stage-2 GEMM (0 = automatic: 32 for fp16 hi+lo, 128 for bf16 hi+lo).  Longer chains are faster;
  * the tensor pipe's FP32 accumulation error grows with the chain length (about 2e-5 rel-L2
  * for ~14k-term chains at a 2048x2048 hologram with 32 layers), shorter chains add their
  * partial sums in L2 with round-to-nearest atomics.  Applies to later calls of the plan.

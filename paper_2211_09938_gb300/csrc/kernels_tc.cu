@@ -484,9 +484,12 @@ static int tc_run(const cgh_plan* p, const int32_t* coef, const int32_t* const* 
   TC_CK(e, "tc: stage-1 GEMM");
   t->flags_dirty = 0;
   const int tm = (p->holo_h + TC_BM - 1) / TC_BM, tn = (p->holo_w + TC_BN - 1) / TC_BN;
-  // Stream-K over the (tile, K step) space (chains of at most 32 K steps, or the plan's
-  // cap) unless the plan asks for single-writer tiles (deterministic).
-  const int streamk = p->deterministic ? 0 : (p->max_ksteps > 0 ? p->max_ksteps : 32);
+  // Stream-K over the (tile, K step) space unless the plan asks for single-writer tiles
+  // (deterministic).  Chains of at most the plan's cap, else 32 K steps for fp16 hi+lo
+  // (whose 1e-5 bar the tensor pipe's chain-length error would otherwise approach) and 128
+  // for bf16 hi+lo (whose error is its operand split, far above that of the chains), which
+  // halves the partial-sum atomics.
+  const int streamk = p->deterministic ? 0 : (p->max_ksteps > 0 ? p->max_ksteps : (F16 ? 32 : 128));
   int S = p->deterministic ? 1 : stage2_splits(tm * tn, t->ktot_alloc / TC_BK);
   if (!p->deterministic && p->max_ksteps > 0) {
     // cap the chain length on the actual K: sum of the layers' compacted rows is at most
