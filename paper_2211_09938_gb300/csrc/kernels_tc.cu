@@ -68,52 +68,49 @@ __device__ int block_scan_flags(int f, int* s_warp, int* total) {
 }
 
 // Per layer: compacted object rows / columns in 32-pixel bands (a band is kept when one
-// of the layer's LLL blocks lies in it), entries past the object edge set to -1.  Also the
-// band index of every 32-wide K step: stage-1 A reads fringe columns 32*band directly.
+// of the layer's LLL blocks lies in it), entries past the object edge set to -1, and the
+// band of every 32-wide K step: stage-1 A reads fringe columns 32*band directly, and the
+// stage-2 A coordinate of K step k of the concatenated layers is the fringe column
+// z*H + 32*band (kmap2).
 // Contraction order: the "rows" outputs (stage-2 K) take the object rows, or, for a square
 // object, the object columns when their sum over the layers is the smaller (or the plan
 // asks for columns): H^T = sum_z E_z A^_z^T E_z^T is then computed and written transposed.
-// Every CTA derives the same decision from the band flags of all layers; CTA 0 records it.
+// Every CTA counts the kept bands of all layers (for the decision and for its layer's
+// offset in the concatenated K); CTA 0 records the decision.
 __global__ void __launch_bounds__(1024) k_tc_compact(TcFlags fl, int H, int W, int Z, int order,
                                                      int* __restrict__ rows, int* __restrict__ cols,
                                                      int* __restrict__ kr_pad, int* __restrict__ kc_pad, int ld_rows,
                                                      int ld_cols, int* __restrict__ rband, int* __restrict__ cband,
-                                                     int* __restrict__ orient) {
+                                                     int* __restrict__ kmap2, int* __restrict__ orient) {
   __shared__ int s_warp[33];
-  __shared__ int s_sum[2];
+  __shared__ int s_cnt[2][CGH_MAX_LAYERS];  // kept bands per layer: object rows, object columns
   pdl_wait();
   pdl_trigger();
   const int z = blockIdx.x, t = threadIdx.x;
-  int tr = 0;
-  if (H == W && order != CGH_CONTRACT_ROWS) {
-    if (order == CGH_CONTRACT_COLS) {
-      tr = 1;
-    } else {
-      if (t < 2) s_sum[t] = 0;
-      __syncthreads();
-      const int n8 = H >> 3, n32 = (n8 + 3) >> 2;
-      int cr = 0, cc = 0;
-      for (int e = t; e < Z * n32; e += blockDim.x) {
-        const int zz = e / n32, b = e - (e / n32) * n32;
-        int fr = 0, fc = 0;
-        for (int q = 4 * b; q < 4 * b + 4 && q < n8; ++q) {
-          fr |= fl.rowband[(size_t)zz * n8 + q];
-          fc |= fl.colband[(size_t)zz * n8 + q];
-        }
-        cr += fr ? 1 : 0;
-        cc += fc ? 1 : 0;
-      }
-      cr = __reduce_add_sync(0xffffffffu, cr);
-      cc = __reduce_add_sync(0xffffffffu, cc);
-      if ((t & 31) == 0) {
-        atomicAdd(&s_sum[0], cr);
-        atomicAdd(&s_sum[1], cc);
-      }
-      __syncthreads();
-      tr = s_sum[1] < s_sum[0] ? 1 : 0;
+  for (int e = t; e < 2 * CGH_MAX_LAYERS; e += blockDim.x) s_cnt[e / CGH_MAX_LAYERS][e % CGH_MAX_LAYERS] = 0;
+  __syncthreads();
+  for (int axis = 0; axis < 2; ++axis) {
+    const int n8 = axis == 0 ? (H >> 3) : (W >> 3), n32 = (n8 + 3) >> 2;
+    const uint8_t* band = axis == 0 ? fl.rowband : fl.colband;
+    for (int e = t; e < Z * n32; e += blockDim.x) {
+      const int zz = e / n32, b = e - (e / n32) * n32;
+      int f = 0;
+      for (int q = 4 * b; q < 4 * b + 4 && q < n8; ++q) f |= band[(size_t)zz * n8 + q];
+      if (f) atomicAdd(&s_cnt[axis][zz], 1);
     }
   }
+  __syncthreads();
+  int tr = 0;
+  if (H == W && order == CGH_CONTRACT_COLS) {
+    tr = 1;
+  } else if (H == W && order != CGH_CONTRACT_ROWS) {
+    int sr = 0, sc = 0;
+    for (int q = 0; q < Z; ++q) sr += s_cnt[0][q], sc += s_cnt[1][q];
+    tr = sc < sr ? 1 : 0;
+  }
   if (z == 0 && t == 0) *orient = tr;
+  int koff = 0;  // this layer's first K step in the concatenated stage-2 K
+  for (int q = 0; q < z; ++q) koff += s_cnt[tr][q];
   for (int axis = 0; axis < 2; ++axis) {
     const int role = axis ^ tr;  // 0: the stage-2 contraction ("rows") outputs, 1: "cols"
     const int n8 = axis == 0 ? (H >> 3) : (W >> 3);
@@ -133,23 +130,11 @@ __global__ void __launch_bounds__(1024) k_tc_compact(TcFlags fl, int H, int W, i
         out[32 * r + q] = v < lim ? v : -1;
       }
       bout[r] = role == 0 ? t : 32 * t;
+      if (role == 0) kmap2[koff + r] = z * H + 32 * t;
     }
     if (t == 0) (role == 0 ? kr_pad : kc_pad)[z] = 32 * total;
     __syncthreads();
   }
-}
-
-// Stage-2 A coordinate of every 32-wide K step of the concatenated layers: the fringe
-// column z*H + 32*band of the layer's compacted row band.
-__global__ void k_tc_kmap2(const int* __restrict__ kr_pad, const int* __restrict__ rband, int ld_band, int H, int Z,
-                           int* __restrict__ kmap2) {
-  pdl_wait();
-  pdl_trigger();
-  const int z = blockIdx.x;
-  int off = 0;
-  for (int q = 0; q < z; ++q) off += kr_pad[q];
-  const int n = kr_pad[z] / 32;
-  for (int k = threadIdx.x; k < n; k += blockDim.x) kmap2[off / 32 + k] = z * H + 32 * rband[(size_t)z * ld_band + k];
 }
 
 // 64 x A^_z at eight consecutive pixels of one object row (ALONG_Y = false: (y0, x0 + q))
@@ -273,7 +258,7 @@ struct cgh_tc_state {
   int flags_dirty;  // host: flags may hold a previous call's marks (see tc_run)
   TcFlags fl;
   int *rows, *cols, *kr_pad, *kc_pad;
-  int *rband, *cband, *kmap2;  // K-step band maps (see k_tc_compact, k_tc_kmap2)
+  int *rband, *cband, *kmap2;  // K-step band maps (see k_tc_compact)
   int* orient;                 // device: 1 when the last call contracted over object columns
   uint16_t *B1, *Y;
   long long b1_plane, y_plane;
@@ -389,11 +374,8 @@ static int tc_prep(const cgh_plan* p, const int32_t* coef, const int32_t* const*
                    t->fl, H, W, Z),
         "tc: scatter");
   TC_CK(launch_pdl(k_tc_compact, dim3(Z), dim3(1024), 0, st, t->fl, H, W, Z, p->contraction, t->rows, t->cols,
-                   t->kr_pad, t->kc_pad, t->kr_alloc, t->kc_alloc, t->rband, t->cband, t->orient),
+                   t->kr_pad, t->kc_pad, t->kr_alloc, t->kc_alloc, t->rband, t->cband, t->kmap2, t->orient),
         "tc: compact");
-  TC_CK(launch_pdl(k_tc_kmap2, dim3(Z), dim3(256), 0, st, (const int*)t->kr_pad, (const int*)t->rband,
-                   t->kr_alloc / 32, H, Z, t->kmap2),
-        "tc: K map");
   {
     dim3 blk(8, 32), grid((t->kc_alloc / 8 + 7) / 8, (t->kr_alloc + 31) / 32, Z);
     TC_CK(launch_pdl(k_tc_idwt<F16>, grid, blk, 0, st, coef, t->fl, (const int*)t->rows, (const int*)t->cols,

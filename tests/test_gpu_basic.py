@@ -252,3 +252,25 @@ def test_selection_rejects_misaligned_inputs(torch_cuda):
         plan.select_blocks(S, L, 127, 1)
     with pytest.raises(CghError):
         plan.progressive_lists(S, L, scenes.THRESHOLDS_U8)
+
+
+def test_select_large_count_table(torch_cuda):
+    """A 512x512 object with 40 layers: the level-1 count table (40 layers x 256 chunks)
+    exceeds the single-pass limit, so the lists go through the separate scan kernel; both
+    paths must give the oracle's lists bit for bit, capacity overflow included."""
+    torch = torch_cuda
+    sc = scenes.random_scene(99, 512, 1024, 40, graded=True)
+    plan = plan_for(sc)
+    S, L = dev(torch, sc["saliency"]), dev(torch, sc["layer"])
+    ref_lists = O.progressive_lists(sc["saliency"], sc["layer"], 40, scenes.THRESHOLDS_U8)
+    lists, counts = plan.progressive_lists(S, L, scenes.THRESHOLDS_U8)
+    c = counts.cpu().numpy()
+    for k in range(4):
+        assert c[k, 0] == c[k, 1] == len(ref_lists[k]), k
+        assert np.array_equal(lists[k][:c[k, 0]].cpu().numpy(), ref_lists[k]), k
+    cap = len(ref_lists[1]) // 3
+    out = torch.empty(cap, dtype=torch.int32, device="cuda")
+    lst, cnt = plan.select_blocks(S, L, scenes.THRESHOLDS_U8[1], 1, out=out, capacity=cap)
+    cc = cnt.cpu().numpy()
+    assert cc[0] == cap and cc[1] == len(ref_lists[1])
+    assert np.array_equal(lst.cpu().numpy(), ref_lists[1][:cap])
