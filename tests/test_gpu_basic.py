@@ -255,9 +255,8 @@ def test_selection_rejects_misaligned_inputs(torch_cuda):
 
 
 def test_select_large_count_table(torch_cuda):
-    """A 512x512 object with 40 layers: the level-1 count table (40 layers x 256 chunks)
-    exceeds the single-pass limit, so the lists go through the separate scan kernel; both
-    paths must give the oracle's lists bit for bit, capacity overflow included."""
+    """A 512x512 object with 40 layers (a level-1 count table of 40 layers x 256 chunks):
+    the oracle's lists bit for bit, capacity overflow included."""
     torch = torch_cuda
     sc = scenes.random_scene(99, 512, 1024, 40, graded=True)
     plan = plan_for(sc)
