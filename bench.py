@@ -449,9 +449,10 @@ def run_ours(args):
                  for k in range(4)]
         holo = torch.empty((HOLO, HOLO), dtype=torch.complex64, device="cuda")
         flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
-    # tables, DWT, 4 x (count, scan, scatter), then the superposition: 1 kernel (direct form)
-    # or scatter + compaction + inverse DWT + 2 gathers + 2 GEMMs (tensor forms)
-    launches_per_step = 1 + 1 + 4 * 3 + (1 if form == "direct_lut" else 7)
+    # fringe tables (FP64 point fringes, block tables), DWT, the four-list selection (count,
+    # scan, scatter), then the superposition: 1 kernel (direct form), or list scatter,
+    # compaction, inverse DWT and the two GEMMs (tensor forms)
+    launches_per_step = 2 + 1 + 3 + (1 if form == "direct_lut" else 5)
 
     # The fringe-table build, the DWT and the block selection are independent: the first two
     # run on side streams forked from (and joined back into) the step's stream, which the
