@@ -567,25 +567,29 @@ def run_ours(args):
                              "(max SM clock; derived, not measured)",
                 "kernel_ms": k_ms}
 
-    # ---- end to end through the C ABI with host buffers: H2D inputs, step, D2H hologram
+    # ---- end to end from pinned host inputs to the host hologram, every step: the library's
+    # streaming pipeline (copies in and out on their own streams, overlapping the neighbouring
+    # scenes' compute; two device slots, each step a captured graph)
+    from paper_2211_09938_gb300.pipeline import ProgressivePipeline
     hI = torch.from_numpy(sc["intensity"]).pin_memory()
     hL = torch.from_numpy(sc["layer"]).pin_memory()
     hS = torch.from_numpy(sc["saliency"]).pin_memory()
-    hH = torch.empty((HOLO, HOLO), dtype=torch.complex64).pin_memory()
-    E = max(3, min(args.steps, 20))
+    hH = [torch.empty((HOLO, HOLO), dtype=torch.complex64).pin_memory() for _ in range(2)]
+    pipe = ProgressivePipeline(plan, scenes.THRESHOLDS_U8, form=form, graphs=not args.no_graph)
+    for k in range(3):
+        pipe.submit(hI, hL, hS, hH[k % 2])
+    pipe.synchronize()
+    E = max(3, min(args.steps, 50))
     torch.cuda.synchronize()
     e0 = time.perf_counter()
-    with torch.cuda.stream(stream):
-        for _ in range(E):
-            I.copy_(hI, non_blocking=True)
-            L.copy_(hL, non_blocking=True)
-            S.copy_(hS, non_blocking=True)
-            step()
-            hH.copy_(holo, non_blocking=True)
-    stream.synchronize()
+    for k in range(E):
+        pipe.submit(hI, hL, hS, hH[k % 2])
+    pipe.synchronize()
     e2e_s = (time.perf_counter() - e0) / E
     e2e = {"value": UNITS_PER_STEP * ws / e2e_s / 1e9, "unit": UNIT,
-           "h2d_bytes_per_step": 3 * OBJ * OBJ, "d2h_bytes_per_step": 8 * HOLO * HOLO}
+           "h2d_bytes_per_step": 3 * OBJ * OBJ, "d2h_bytes_per_step": 8 * HOLO * HOLO,
+           "note": "ProgressivePipeline: inputs copied in and the hologram copied out every step on copy "
+                   "streams, overlapping the neighbouring steps' compute"}
 
     # ---- plain point-wise direct kernel on the same scene (the baseline the metric names)
     plain = None

@@ -1,0 +1,111 @@
+"""Streaming many scenes of one geometry from host memory to host holograms.
+
+Each submitted scene is copied in (intensity, layer and saliency maps, pinned host
+memory), taken through the whole progressive path (fringe tables, Haar DWT, block
+selection, superposition; Section 2 steps 1-5) and copied back out.  The device buffers
+come in `depth` slots used round robin: while one slot's hologram is copied out on the
+copy stream, the next slot's inputs are copied in and its step runs on the compute
+stream.  Each slot's step is one captured CUDA graph.  Every kernel is the library's;
+this module only orders copies and graph replays with events.
+"""
+import torch
+
+from .cgh import Plan
+
+
+class _Slot:
+    def __init__(self, plan, device):
+        obj = (plan.obj_h, plan.obj_w)
+        self.I = torch.empty(obj, dtype=torch.uint8, device=device)
+        self.L = torch.empty(obj, dtype=torch.uint8, device=device)
+        self.S = torch.empty(obj, dtype=torch.uint8, device=device)
+        self.coeffs = torch.empty((plan.n_layers,) + obj, dtype=torch.int32, device=device)
+        self.counts = torch.zeros((4, 2), dtype=torch.int32, device=device)
+        self.lists = [torch.empty(plan.max_blocks(3 if k == 0 else k), dtype=torch.int32, device=device)
+                      for k in range(4)]
+        self.holo = torch.empty((plan.holo_h, plan.holo_w), dtype=torch.complex64, device=device)
+        self.graph = None
+        self.in_done = torch.cuda.Event()
+        self.step_done = torch.cuda.Event()
+        self.out_done = torch.cuda.Event()
+
+
+class ProgressivePipeline:
+    """plan: a Plan; thresholds: level -> uint8 threshold; form: superposition form.
+    submit(hI, hL, hS, hH) copies the pinned host maps in, runs the step and copies the
+    hologram into the pinned complex64 host tensor hH, all asynchronously; hH is complete
+    once synchronize() returns (or the event returned by submit has completed)."""
+
+    def __init__(self, plan, thresholds, form="tc_bf16x3", depth=2, graphs=True):
+        self.plan = plan
+        self.thresholds = dict(thresholds)
+        self.form = form
+        dev = plan.device
+        self.compute = torch.cuda.Stream(dev)
+        self.copy_in = torch.cuda.Stream(dev)
+        self.copy_out = torch.cuda.Stream(dev)
+        self.side = (torch.cuda.Stream(dev), torch.cuda.Stream(dev))
+        self.slots = [_Slot(plan, dev) for _ in range(depth)]
+        self.k = 0
+        # one eager pass per slot (plan scratch, operand planes), then the captured step
+        for sl in self.slots:
+            self._step(sl)
+        self.compute.synchronize()
+        if graphs:
+            for sl in self.slots:
+                g = torch.cuda.CUDAGraph()
+                with torch.cuda.graph(g, stream=self.compute):
+                    self._step(sl)
+                sl.graph = g
+            self.compute.synchronize()
+
+    def _step(self, sl):
+        """The whole path on one slot: tables and DWT on side streams forked from the
+        compute stream, the selection on it, then the superposition after the join."""
+        st = self.compute
+        s_tab, s_dwt = self.side
+        fork = torch.cuda.Event()
+        fork.record(st)
+        s_tab.wait_event(fork)
+        s_dwt.wait_event(fork)
+        self.plan.build_tables(stream=s_tab)
+        self.plan.haar_decompose(sl.I, sl.L, sl.coeffs, stream=s_dwt)
+        self.plan.progressive_lists(sl.S, sl.L, self.thresholds, counts=sl.counts, lists=sl.lists, stream=st)
+        j1, j2 = torch.cuda.Event(), torch.cuda.Event()
+        j1.record(s_tab)
+        j2.record(s_dwt)
+        st.wait_event(j1)
+        st.wait_event(j2)
+        self.plan.progressive_hologram(sl.coeffs, sl.lists, sl.counts, holo=sl.holo, form=self.form, stream=st)
+
+    def submit(self, hI, hL, hS, hH):
+        sl = self.slots[self.k % len(self.slots)]
+        self.k += 1
+        # inputs: the slot's previous step must have read them
+        self.copy_in.wait_event(sl.step_done)
+        with torch.cuda.stream(self.copy_in):
+            sl.I.copy_(hI, non_blocking=True)
+            sl.L.copy_(hL, non_blocking=True)
+            sl.S.copy_(hS, non_blocking=True)
+        sl.in_done.record(self.copy_in)
+        # step: inputs in, and the slot's previous hologram copied out
+        self.compute.wait_event(sl.in_done)
+        self.compute.wait_event(sl.out_done)
+        if sl.graph is not None:
+            with torch.cuda.stream(self.compute):
+                sl.graph.replay()
+        else:
+            self._step(sl)
+        sl.step_done.record(self.compute)
+        self.copy_out.wait_event(sl.step_done)
+        with torch.cuda.stream(self.copy_out):
+            hH.copy_(sl.holo, non_blocking=True)
+        sl.out_done.record(self.copy_out)
+        return sl.out_done
+
+    def synchronize(self):
+        for s in (self.copy_in, self.compute, self.copy_out):
+            s.synchronize()
+
+
+__all__ = ["ProgressivePipeline", "Plan"]

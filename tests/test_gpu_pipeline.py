@@ -1,0 +1,48 @@
+"""The streaming pipeline: scenes submitted back to back through two device slots (copies
+overlapping compute) give exactly the holograms of the plain library calls, scene by
+scene, for both superposition forms."""
+import numpy as np
+import pytest
+
+from synth import scenes
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    import os
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2211_09938_gb300 import build_lib, cgh
+    if not os.path.exists(cgh.LIB_PATH):
+        build_lib.build()
+    cgh.lib()
+    return torch
+
+
+@pytest.mark.parametrize("form,graphs", [("tc_bf16x3", True), ("direct_lut", False)])
+def test_pipeline_matches_direct_calls(torch_cuda, form, graphs):
+    torch = torch_cuda
+    from paper_2211_09938_gb300 import Plan
+    from paper_2211_09938_gb300.pipeline import ProgressivePipeline
+    base = scenes.random_scene(120, 64, 128, 3, graded=True)
+    plan = Plan.for_scene(base, flags=Plan.DETERMINISTIC)
+    seeds = [121, 122, 123, 124, 125]
+    scs = [scenes.random_scene(sd, 64, 128, 3, graded=True) for sd in seeds]
+    pipe = ProgressivePipeline(plan, scenes.THRESHOLDS_U8, form=form, graphs=graphs)
+    outs = [torch.empty((128, 128), dtype=torch.complex64).pin_memory() for _ in scs]
+    for sc, hH in zip(scs, outs):
+        pipe.submit(torch.from_numpy(sc["intensity"]).pin_memory(), torch.from_numpy(sc["layer"]).pin_memory(),
+                    torch.from_numpy(sc["saliency"]).pin_memory(), hH)
+    pipe.synchronize()
+    for sc, hH in zip(scs, outs):
+        I = torch.from_numpy(sc["intensity"]).cuda()
+        L = torch.from_numpy(sc["layer"]).cuda()
+        S = torch.from_numpy(sc["saliency"]).cuda()
+        coeffs = plan.haar_decompose(I, L)
+        lists, counts = plan.progressive_lists(S, L, scenes.THRESHOLDS_U8)
+        H = plan.progressive_hologram(coeffs, lists, counts, form=form).cpu()
+        torch.cuda.synchronize()
+        assert torch.equal(H, hH), (form, np.abs((H - hH).numpy()).max())
