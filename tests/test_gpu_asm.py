@@ -131,3 +131,19 @@ def test_asm_rejects_bad_arguments(torch_cuda):
     odd = Plan((96, 96), (192, 192), 8e-6, 532e-9, [0.01])
     with pytest.raises(CghError):
         odd.reconstruct_asm(torch.zeros((192, 192), dtype=torch.complex64, device="cuda"), None)
+
+
+def test_asm_stride_8_and_single_layer(torch_cuda):
+    """s = 8 (folded edge P/8) and a single layer, both paddings."""
+    torch = torch_cuda
+    from paper_2211_09938_gb300 import Plan
+    sc = scenes.random_scene(126, 64, 512, 1)
+    g = O.geometry_of(sc)
+    H = _holo(sc, g).astype(np.complex64)
+    plan = Plan.for_scene(sc)
+    for pad in (1, 2):
+        F, _ = plan.reconstruct_asm(torch.from_numpy(H).cuda(), amplitude=False, pad=pad)
+        torch.cuda.synchronize()
+        err = O.rel_l2(F.cpu().numpy(), O.asm_reconstruct_fields(H.astype(np.complex128), g, pad=pad))
+        print(f"asm s=8 pad {pad}: {err:.2e}")
+        assert err <= TOL

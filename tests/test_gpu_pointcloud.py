@@ -121,3 +121,22 @@ def test_pointcloud_rejects_bad_arguments(torch_cuda):
     with pytest.raises(CghError):
         check(lib().cgh_pointcloud_direct(plan.handle, I.data_ptr(), I.data_ptr(),
                                           torch.zeros(64, 64, dtype=torch.complex64, device="cuda").data_ptr(), 2, None))
+
+
+def test_pointcloud_no_points(torch_cuda):
+    """A depth map without a single valid depth gives a zero hologram, and accumulating it
+    leaves the buffer as it was."""
+    torch = torch_cuda
+    from paper_2211_09938_gb300 import Plan
+    plan = Plan((32, 32), (64, 64), 8e-6, 532e-9, [0.1])
+    I = torch.full((32, 32), 255, dtype=torch.uint8, device="cuda")
+    D = torch.full((32, 32), float("nan"), dtype=torch.float32, device="cuda")
+    D[0, :8] = 0.0
+    D[1, :8] = -1.0
+    D[2, :8] = float("inf")
+    H = plan.pointcloud_direct(I, D)
+    prev = torch.randn(64, 64, dtype=torch.complex64, device="cuda")
+    H2 = plan.pointcloud_direct(I, D, holo=prev.clone(), accumulate=True)
+    torch.cuda.synchronize()
+    assert torch.count_nonzero(H).item() == 0
+    assert torch.equal(H2, prev)

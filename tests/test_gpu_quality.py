@@ -152,3 +152,19 @@ def test_all_salient_equals_pointwise(torch_cuda):
     s = ssim(A, ref).item()
     print(f"all-salient ssim {s:.8f}")
     assert abs(s - 1.0) <= 1e-5
+
+
+def test_ssim_constant_images(torch_cuda):
+    """Identical constant images (zero variance) and two all-zero images have SSIM 1; a
+    constant against a textured image is well below 1, as in the oracle."""
+    torch = torch_cuda
+    from paper_2211_09938_gb300.cgh import ssim
+    c = torch.full((40, 40), 0.5, device="cuda")
+    z = torch.zeros((40, 40), device="cuda")
+    assert abs(ssim(c, c, normalize=False).item() - 1.0) <= 1e-6
+    assert abs(ssim(z, z).item() - 1.0) <= 1e-6
+    rng = np.random.default_rng(5)
+    x = rng.uniform(0, 1, size=(40, 40)).astype(np.float32)
+    got = ssim(c, torch.from_numpy(x).cuda(), normalize=False).item()
+    ref = O.ssim(np.full((40, 40), 0.5), x.astype(np.float64))
+    assert abs(got - ref) <= TOL_SSIM and got < 0.5
