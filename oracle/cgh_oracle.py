@@ -26,6 +26,9 @@ object saliency"):
   DWT with zero low band of the details of the salient blocks) is superposed
   with 2^(l-1) x 2^(l-1) block fringes.  Block fringes are sums of point
   fringes evaluated here in FP64.
+* Eq. 1's amplitude 1/r and carrier exp(jkr) are a per-layer constant for a layer;
+  they are dropped by default and kept, as exp(j 2 pi frac(z/lambda)) / z per layer,
+  when the geometry asks for them (layer_factor).
 * Depth: every object pixel belongs to one depth layer; the per-layer object
   plane is A_z = I * [layer == z] and each plane has its own DWT and fringes
   (the per-depth extension sketched at the end of Section 2).
@@ -52,7 +55,7 @@ class Geometry:
     pixel (s*i, s*j) with s = holo/obj an integer; Table 1 of the paper is an
     image that is not available)."""
 
-    def __init__(self, obj_shape, holo_shape, pitch, wavelength, z):
+    def __init__(self, obj_shape, holo_shape, pitch, wavelength, z, layer_factor=False):
         self.obj_h, self.obj_w = int(obj_shape[0]), int(obj_shape[1])
         self.holo_h, self.holo_w = int(holo_shape[0]), int(holo_shape[1])
         if self.holo_h % self.obj_h or self.holo_w % self.obj_w:
@@ -63,6 +66,7 @@ class Geometry:
         self.pitch = float(pitch)
         self.wavelength = float(wavelength)
         self.z = np.asarray(z, dtype=np.float64).reshape(-1)
+        self.layer_factor = bool(layer_factor)
 
     @property
     def n_layers(self):
@@ -72,10 +76,23 @@ class Geometry:
         """Fresnel rate a_z = p^2 / (2 lambda z) in cycles per squared pixel offset."""
         return fresnel_rate(self.pitch, self.wavelength, self.z[k])
 
+    def factor(self, k):
+        """Per-layer factor of Eq. 1 that the default reading drops: exp(j k z) / z for the
+        layer's distance (only with layer_factor), else 1."""
+        return layer_factor(self.wavelength, self.z[k]) if self.layer_factor else 1.0
+
 
 def geometry_of(scene):
-    n_h, n_w = scene["intensity"].shape
-    return Geometry((n_h, n_w), scene["holo"], scene["pitch"], scene["wavelength"], scene["z"])
+    n_h, n_w = scene["intensity"].shape[-2:]
+    return Geometry((n_h, n_w), scene["holo"], scene["pitch"], scene["wavelength"], scene["z"],
+                    scene.get("layer_factor", False))
+
+
+def layer_factor(wavelength, z):
+    """exp(j 2 pi z / lambda) / z: Eq. 1's amplitude 1/r and carrier exp(j k r) at r = z,
+    with the carrier's phase reduced to frac(z / lambda) cycles in FP64."""
+    x = np.asarray(z, dtype=np.float64) / wavelength
+    return np.exp(2j * np.pi * (x - np.floor(x))) / np.asarray(z, dtype=np.float64)
 
 
 def fresnel_rate(pitch, wavelength, z):
@@ -342,11 +359,12 @@ def progressive_hologram(intensity, layer, lists, geom, levels=3):
     Ho, Wo = planes.shape[1:]
     for z in range(geom.n_layers):
         a = geom.a(z)
+        Hz = np.zeros_like(H)
         C = haar_forward(planes[z], levels)
         hL, wL = Ho >> levels, Wo >> levels
         lll = C[:hL, :wL] * masks[0][z]
         kL = 1 << levels
-        H += superpose_cells(geom, a, kL, lll / float(kL * kL))
+        Hz += superpose_cells(geom, a, kL, lll / float(kL * kL))
         for l in range(levels, 0, -1):
             h, w = Ho >> l, Wo >> l
             keep = masks[l][z]
@@ -360,7 +378,8 @@ def progressive_hologram(intensity, layer, lists, geom, levels=3):
                 res4[r::2, c::2] = sx * X + sy * Y + sx * sy * D
             k = 1 << (l - 1)
             # residual sum of a level-(l-1) cell is res4/4, spread over k*k pixels
-            H += superpose_cells(geom, a, k, res4 / float(4 * k * k))
+            Hz += superpose_cells(geom, a, k, res4 / float(4 * k * k))
+        H += geom.factor(z) * Hz
     return H
 
 
@@ -376,7 +395,7 @@ def pointwise_hologram_separable(planes, geom):
             continue
         Ex = point_fringe_1d(mi, geom.a(z))
         Ey = point_fringe_1d(nj, geom.a(z))
-        H += Ex @ planes[z] @ Ey.T
+        H += geom.factor(z) * (Ex @ planes[z] @ Ey.T)
     return H
 
 
@@ -400,8 +419,9 @@ def pointwise_hologram_direct(planes, geom, pixels=None):
             continue
         amp = planes[z][ii, jj]
         a = geom.a(z)
+        c = geom.factor(z)
         for p in range(mm.size):
-            out[p] += np.sum(amp * point_fringe_2d(mm[p] - geom.s * ii, nn[p] - geom.s * jj, a))
+            out[p] += c * np.sum(amp * point_fringe_2d(mm[p] - geom.s * ii, nn[p] - geom.s * jj, a))
     return out.reshape(shape)
 
 
@@ -426,7 +446,7 @@ def pointcloud_hologram(intensity, depth, geom, pixels=None):
     zz = np.asarray(depth, dtype=np.float64)
     valid = np.isfinite(zz) & (zz > 0)
     ii, jj = np.nonzero(valid)
-    amp = I[ii, jj]
+    amp = I[ii, jj] * (layer_factor(geom.wavelength, zz[ii, jj]) if geom.layer_factor else 1.0)
     a = fresnel_rate(geom.pitch, geom.wavelength, zz[ii, jj])
     if pixels is None:
         mm, nn = np.meshgrid(np.arange(geom.holo_h), np.arange(geom.holo_w), indexing="ij")
@@ -450,7 +470,8 @@ def pointcloud_hologram(intensity, depth, geom, pixels=None):
 
 def reconstruct_fields(H, geom, n_obj=None):
     """Fresnel back-propagation of the hologram to every layer, sampled on the object
-    grid: R_z = E_z^H H conj(E_z), the adjoint of A -> E_z A E_z^T."""
+    grid: R_z = conj(c_z) E_z^H H conj(E_z), the adjoint of A -> c_z E_z A E_z^T (c_z the
+    layer factor, 1 unless the geometry keeps it)."""
     oh, ow = n_obj if n_obj is not None else (geom.holo_h // geom.s, geom.holo_w // geom.s)
     mi = np.arange(geom.holo_h)[:, None] - geom.s * np.arange(oh)[None, :]
     nj = np.arange(geom.holo_w)[:, None] - geom.s * np.arange(ow)[None, :]
@@ -458,7 +479,7 @@ def reconstruct_fields(H, geom, n_obj=None):
     for z in range(geom.n_layers):
         Ex = point_fringe_1d(mi, geom.a(z))
         Ey = point_fringe_1d(nj, geom.a(z))
-        R[z] = Ex.conj().T @ H @ Ey.conj()
+        R[z] = np.conj(geom.factor(z)) * (Ex.conj().T @ H @ Ey.conj())
     return R
 
 
@@ -510,7 +531,7 @@ def asm_reconstruct_fields(H, geom, pad=2, band_limit=False):
 
 def propagate_fields(fields, geom):
     """Point-source hologram of complex layer fields (Eq. 1 per layer, paraxial):
-    H = sum_z E_z F_z E_z^T; the adjoint of reconstruct_fields."""
+    H = sum_z c_z E_z F_z E_z^T; the adjoint of reconstruct_fields."""
     fields = np.asarray(fields, dtype=np.complex128)
     H = np.zeros((geom.holo_h, geom.holo_w), dtype=np.complex128)
     mi = np.arange(geom.holo_h)[:, None] - geom.s * np.arange(fields.shape[1])[None, :]
@@ -518,7 +539,7 @@ def propagate_fields(fields, geom):
     for z in range(fields.shape[0]):
         Ex = point_fringe_1d(mi, geom.a(z))
         Ey = point_fringe_1d(nj, geom.a(z))
-        H += Ex @ fields[z] @ Ey.T
+        H += geom.factor(z) * (Ex @ fields[z] @ Ey.T)
     return H
 
 

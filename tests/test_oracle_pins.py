@@ -673,3 +673,57 @@ def test_wavelength_enters_only_through_the_rate():
     # and a different wavelength at the same distances gives a different hologram
     g2 = O.Geometry((16, 16), (32, 32), PITCH, lam_b, z)
     assert O.rel_l2(O.progressive_hologram(I, sc["layer"], lists, g2), Hr) > 0.1
+
+
+# ---------------------------------------------------------------- the layer factor (F1-F3)
+
+def test_layer_factor_single_point_is_eq1():
+    """F1: with the layer factor kept, one salient point of value v at (i, j) on the layer at
+    z gives Eq. 1 in its paraxial form written out, v/z exp(j 2 pi z / lambda)
+    exp(j pi (d p)^2 / (lambda z)), for the progressive, point-wise and propagated forms."""
+    n, s = 8, 2
+    z = 0.0123
+    g = O.Geometry((n, n), (n * s, n * s), PITCH, LAM, [z], layer_factor=True)
+    I = np.zeros((n, n), np.uint8)
+    I[3, 5] = 91
+    lay = np.zeros((n, n), np.uint8)
+    m = np.arange(n * s)[:, None] - s * 3
+    q = np.arange(n * s)[None, :] - s * 5
+    r2 = (m * PITCH) ** 2 + (q * PITCH) ** 2
+    want = 91 / z * np.exp(2j * np.pi * z / LAM) * np.exp(1j * np.pi * r2 / (LAM * z))
+    Hp = O.progressive_hologram(I, lay, all_salient_lists(lay, 1), g)
+    assert np.max(np.abs(Hp - want)) <= 1e-9 * np.max(np.abs(want))
+    Hd = O.plain_pointwise_hologram(I, lay, g, pixels=np.nonzero(np.ones((n * s, n * s))))
+    assert np.max(np.abs(Hd.reshape(n * s, n * s) - want)) <= 1e-9 * np.max(np.abs(want))
+    F = np.zeros((1, n, n), complex)
+    F[0, 3, 5] = 91
+    assert np.max(np.abs(O.propagate_fields(F, g) - want)) <= 1e-9 * np.max(np.abs(want))
+
+
+def test_layer_factor_adjoint_and_scaling():
+    """F2: reconstruction stays the adjoint of propagation with the factor, and every
+    layer's hologram is the factorless one times exp(j 2 pi frac(z/lambda)) / z."""
+    rng = np.random.default_rng(44)
+    g = O.Geometry((8, 8), (16, 16), PITCH, LAM, [0.05, 0.07, 0.11], layer_factor=True)
+    g0 = O.Geometry((8, 8), (16, 16), PITCH, LAM, [0.05, 0.07, 0.11])
+    H = rng.normal(size=(16, 16)) + 1j * rng.normal(size=(16, 16))
+    F = rng.normal(size=(3, 8, 8)) + 1j * rng.normal(size=(3, 8, 8))
+    lhs = np.vdot(O.reconstruct_fields(H, g), F)
+    rhs = np.vdot(H, O.propagate_fields(F, g))
+    assert abs(lhs - rhs) <= 1e-10 * abs(lhs)
+    for k, z in enumerate(g.z):
+        Fk = np.zeros_like(F)
+        Fk[k] = F[k]
+        c = np.exp(2j * np.pi * z / LAM) / z  # unreduced: ~1e-10 rad of FP64 rounding
+        assert O.rel_l2(O.propagate_fields(Fk, g), c * O.propagate_fields(Fk, g0)) < 1e-9
+
+
+def test_layer_factor_pointcloud_reduces_to_layers():
+    """F3: with the factor, a depth map holding the layer distances gives the layered
+    point-wise hologram (each point's factor is its own depth's)."""
+    sc = scenes.random_scene(62, 16, 32, 3)
+    zs = [float(np.float32(z)) for z in (0.05, 0.0625, 0.09)]
+    g = O.Geometry((16, 16), (32, 32), PITCH, LAM, zs, layer_factor=True)
+    depth = np.asarray(zs, np.float32)[sc["layer"]]
+    assert O.rel_l2(O.pointcloud_hologram(sc["intensity"], depth, g),
+                    O.plain_pointwise_hologram(sc["intensity"], sc["layer"], g)) < 1e-12
