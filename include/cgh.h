@@ -59,6 +59,12 @@ extern "C" {
 /* Plan flag: every output element is written by one CTA in a fixed order (no split-K
  * atomics), so results are bit-reproducible run to run; the split forms are faster. */
 #define CGH_PLAN_DETERMINISTIC 1
+/* Plan flag: keep Eq. 1's amplitude 1/r and carrier exp(jkr) at r = z as a per-layer factor
+ * c_z = exp(j*2*pi*frac(z/lambda)) / z (the default reading drops this constant of each
+ * layer).  Every hologram and reconstruction of the plan includes it (the reconstructions
+ * as conj(c_z), the adjoint); the point-wise per-point-depth call takes each point's own
+ * exp(j*2*pi*frac(z/lambda)) / z.  cgh_reconstruct_asm treats the hologram as given. */
+#define CGH_PLAN_LAYER_FACTOR 2
 
 typedef struct cgh_plan cgh_plan;
 
@@ -78,7 +84,7 @@ int cgh_version(void);
  *   pitch_m, wavelength_m  pixel pitch and wavelength (metres, > 0)
  *   n_layers     Z, 1..64;   z_m  HOST array of Z layer distances (metres, > 0)
  *   levels       number of Haar levels; must be 3 (the paper's choice)
- *   flags        0 or CGH_PLAN_DETERMINISTIC
+ *   flags        0, or CGH_PLAN_DETERMINISTIC and / or CGH_PLAN_LAYER_FACTOR
  *   stream       stream on which the fringe tables are built
  * The plan allocates device memory (tables, scratch, status word) with cudaMalloc on
  * the current device and builds the fringe tables with cgh_build_tables on `stream`.

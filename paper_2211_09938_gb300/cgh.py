@@ -118,6 +118,7 @@ class Plan:
     by the convenience helpers below (torch.empty on the plan's device)."""
 
     DETERMINISTIC = 1
+    LAYER_FACTOR = 2  # keep exp(jkz)/z of Eq. 1 per layer (cgh.h: CGH_PLAN_LAYER_FACTOR)
 
     def __init__(self, obj_shape, holo_shape, pitch, wavelength, z, levels=3, stream=None, flags=0):
         import torch
@@ -135,7 +136,9 @@ class Plan:
 
     @classmethod
     def for_scene(cls, scene, stream=None, flags=0):
-        return cls(scene["intensity"].shape, scene["holo"], scene["pitch"], scene["wavelength"],
+        if scene.get("layer_factor", False):
+            flags |= cls.LAYER_FACTOR
+        return cls(scene["intensity"].shape[-2:], scene["holo"], scene["pitch"], scene["wavelength"],
                    scene["z"], stream=stream, flags=flags)
 
     def close(self):

@@ -52,6 +52,8 @@ int cgh_plan_destroy(cgh_plan* p) {
   cudaFree(p->d_f64);
   cudaFree(p->d_a_frac);
   cudaFree(p->d_a_fixed);
+  cudaFree(p->d_lf_half);
+  cudaFree(p->d_lf_full);
   cudaFree(p->d_status);
   cudaFree(p->d_chunk_cnt);
   cudaFree(p->d_chunk_off);
@@ -102,7 +104,8 @@ int cgh_plan_create(cgh_plan** out, int obj_h, int obj_w, int holo_h, int holo_w
   if (!z_m) return cgh_fail(CGH_ERR_ARG, "cgh_plan_create: z_m is NULL");
   for (int k = 0; k < n_layers; ++k)
     if (!(z_m[k] > 0)) return cgh_fail(CGH_ERR_ARG, "cgh_plan_create: z[%d] must be > 0", k);
-  if (flags & ~CGH_PLAN_DETERMINISTIC) return cgh_fail(CGH_ERR_ARG, "cgh_plan_create: unknown flags 0x%x", flags);
+  if (flags & ~(CGH_PLAN_DETERMINISTIC | CGH_PLAN_LAYER_FACTOR))
+    return cgh_fail(CGH_ERR_ARG, "cgh_plan_create: unknown flags 0x%x", flags);
 
   cgh_plan* p = (cgh_plan*)calloc(1, sizeof(cgh_plan));
   if (!p) return cgh_fail(CGH_ERR_NOMEM, "cgh_plan_create: host allocation failed");
@@ -114,6 +117,7 @@ int cgh_plan_create(cgh_plan** out, int obj_h, int obj_w, int holo_h, int holo_w
   p->n_layers = n_layers;
   p->levels = levels;
   p->deterministic = (flags & CGH_PLAN_DETERMINISTIC) ? 1 : 0;
+  p->layer_factor = (flags & CGH_PLAN_LAYER_FACTOR) ? 1 : 0;
   p->pitch = pitch_m;
   p->wavelength = wavelength_m;
   for (int k = 0; k < n_layers; ++k) {
@@ -164,6 +168,27 @@ int cgh_plan_create(cgh_plan** out, int obj_h, int obj_w, int holo_h, int holo_w
                       cudaMemcpyHostToDevice),
            "cgh_plan_create: copy a_fixed");
   PLAN_TRY(cudaMemset(p->d_status, 0, sizeof(int)), "cgh_plan_create: status clear");
+  if (p->layer_factor) {
+    // c_z = exp(j 2 pi frac(z/lambda)) / z; its square root goes into the point fringe of
+    // both axes (so every separable product carries c_z once), c_z itself into the
+    // point-wise kernel
+    double2 half[CGH_MAX_LAYERS];
+    float2 full[CGH_MAX_LAYERS];
+    double mag_max = 0.0;
+    for (int k = 0; k < n_layers; ++k) {
+      const double x = z_m[k] / wavelength_m, fr = x - floor(x);
+      half[k] = make_double2(cos(M_PI * fr) / sqrt(z_m[k]), sin(M_PI * fr) / sqrt(z_m[k]));
+      full[k] = make_float2((float)(cos(2.0 * M_PI * fr) / z_m[k]), (float)(sin(2.0 * M_PI * fr) / z_m[k]));
+      if (1.0 / sqrt(z_m[k]) > mag_max) mag_max = 1.0 / sqrt(z_m[k]);
+    }
+    p->lf_extra = mag_max > 1.0 ? (int)ceil(log2(mag_max)) : 0;
+    PLAN_TRY(cudaMalloc(&p->d_lf_half, n_layers * sizeof(double2)), "cgh_plan_create: layer factor");
+    PLAN_TRY(cudaMalloc(&p->d_lf_full, n_layers * sizeof(float2)), "cgh_plan_create: layer factor");
+    PLAN_TRY(cudaMemcpy(p->d_lf_half, half, n_layers * sizeof(double2), cudaMemcpyHostToDevice),
+             "cgh_plan_create: layer factor");
+    PLAN_TRY(cudaMemcpy(p->d_lf_full, full, n_layers * sizeof(float2), cudaMemcpyHostToDevice),
+             "cgh_plan_create: layer factor");
+  }
   PLAN_TRY(launch_build_tables(p, (cudaStream_t)stream), "cgh_plan_create: table build");
 #undef PLAN_TRY
   *out = p;

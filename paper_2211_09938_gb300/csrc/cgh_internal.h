@@ -17,6 +17,7 @@
 struct cgh_plan {
   int obj_h, obj_w, holo_h, holo_w, s, n_layers, levels;
   int deterministic;  // CGH_PLAN_DETERMINISTIC: no split-K atomics
+  int layer_factor;   // CGH_PLAN_LAYER_FACTOR: keep exp(jkz)/z per layer
   int max_ksteps;     // cgh_plan_set_tuning: cap on K steps per stage-2 chain (0 = automatic)
   int contraction;    // cgh_plan_set_contraction: CGH_CONTRACT_AUTO / _ROWS / _COLS
   double pitch, wavelength;
@@ -32,6 +33,9 @@ struct cgh_plan {
   int f_len;
   double* d_a_frac;
   unsigned long long* d_a_fixed;
+  double2* d_lf_half;  // layer factor: sqrt(c_z) folded into the point fringe (null without the flag)
+  float2* d_lf_full;   // layer factor c_z for the point-wise kernel (null without the flag)
+  int lf_extra;        // fp16 headroom: extra power of two taken off stage 1 (>= 0)
 
   // Status word for bounded device waits.
   int* d_status;

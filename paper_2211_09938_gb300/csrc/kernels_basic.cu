@@ -16,7 +16,8 @@
 //   kind 1: w_l(d) = sum_{t<2^(l-1)} f_z(d - s t) - sum_{2^(l-1)<=t<2^l} f_z(d - s t)
 // f_z(d) = exp(j 2 pi frac(a_z d^2)); the product a_z*d^2 and its reduction are FP64
 // with d^2 an exact integer (Eq. 1 under the paraxial approximation).
-__global__ void k_fringe_f64(double2* __restrict__ F, const double* __restrict__ a_frac, int f_len, int f_off) {
+__global__ void k_fringe_f64(double2* __restrict__ F, const double* __restrict__ a_frac, int f_len, int f_off,
+                             const double2* __restrict__ lf_half) {
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= f_len) return;
   const int z = blockIdx.y;
@@ -25,6 +26,12 @@ __global__ void k_fringe_f64(double2* __restrict__ F, const double* __restrict__
   x -= rint(x);  // exact: |x| < 2^53 and x - rint(x) is representable
   double sn, cs;
   sincospi(2.0 * x, &sn, &cs);
+  if (lf_half) {  // the square root of the layer factor, on each axis's fringe
+    const double2 c = lf_half[z];
+    const double re = c.x * cs - c.y * sn, im = c.x * sn + c.y * cs;
+    cs = re;
+    sn = im;
+  }
   F[(size_t)z * f_len + q] = make_double2(cs, sn);
 }
 
@@ -64,7 +71,7 @@ __global__ void k_build_tables(float2* __restrict__ tab, const double2* __restri
 
 cudaError_t launch_build_tables(const cgh_plan* p, cudaStream_t st) {
   k_fringe_f64<<<dim3((p->f_len + 255) / 256, p->n_layers), 256, 0, st>>>(p->d_f64, p->d_a_frac, p->f_len,
-                                                                        p->tab_off + 7 * p->s);
+                                                                        p->tab_off + 7 * p->s, p->d_lf_half);
   k_build_tables<<<dim3((p->tab_len + 255) / 256, p->n_layers), 256, 0, st>>>(p->d_tab, p->d_f64, p->f_len,
                                                                             p->tab_len, p->s);
   return cudaGetLastError();
@@ -372,20 +379,28 @@ cudaError_t launch_select(int obj_h, int obj_w, int n_layers, const uint8_t* sal
 #define PD_TN 64
 #define PD_CHUNK 256
 
-template <bool DEPTH>
+// LF (the plan's layer factor): each point's amplitude is complex, intensity times
+// exp(j 2 pi frac(z/lambda)) / z of its layer or of its own depth.
+template <bool DEPTH, bool LF>
 __global__ void __launch_bounds__(256) k_plain_direct(const uint8_t* __restrict__ I,
                                                       const uint8_t* __restrict__ L,
                                                       const float* __restrict__ depth, int H, int W,
                                                       int Z, int s, const unsigned long long* a_fixed,
+                                                      const float2* __restrict__ lf_full,
                                                       double pitch, double wavelength,
                                                       float2* __restrict__ holo, int HH, int HW,
                                                       int accumulate) {
-  __shared__ int4 s_pt[PD_CHUNK];      // (s*i, s*j, amp bits, low word of the rate)
+  __shared__ int4 s_pt[PD_CHUNK];      // (s*i, s*j, amp bits (real part), low word of the rate)
   __shared__ unsigned s_ph[PD_CHUNK];  // high word of the rate
+  __shared__ float s_ai[LF ? PD_CHUNK : 1];  // imaginary part of the amplitude
   __shared__ unsigned long long s_a[CGH_MAX_LAYERS];
+  __shared__ float2 s_lf[LF && !DEPTH ? CGH_MAX_LAYERS : 1];
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   const int m0 = blockIdx.y * PD_TM, n0 = blockIdx.x * PD_TN;
   if (!DEPTH && threadIdx.x < Z) s_a[threadIdx.x] = a_fixed[threadIdx.x];
+  if constexpr (LF && !DEPTH) {
+    if (threadIdx.x < Z) s_lf[threadIdx.x] = lf_full[threadIdx.x];
+  }
   int mm[2], nn[4];
 #pragma unroll
   for (int r = 0; r < 2; ++r) mm[r] = m0 + ty + 16 * r;
@@ -403,6 +418,7 @@ __global__ void __launch_bounds__(256) k_plain_direct(const uint8_t* __restrict_
       const int p = base + threadIdx.x;
       int4 v = make_int4(0, 0, 0, 0);
       unsigned long long af = 0;
+      float ai = 0.f;
       if (p < npts) {
         const int i = p / W, j = p - (p / W) * W;
         float amp;
@@ -414,16 +430,29 @@ __global__ void __launch_bounds__(256) k_plain_direct(const uint8_t* __restrict_
             const double a = pitch * pitch / (2.0 * wavelength * (double)zf);
             const double x = floor((a - floor(a)) * 18446744073709551616.0 + 0.5);
             af = x >= 18446744073709551616.0 ? 0ull : (unsigned long long)x;
+            if constexpr (LF) {  // exp(j 2 pi frac(z/lambda)) / z of the point's own depth
+              const double zl = (double)zf / wavelength;
+              double sn, cs;
+              sincospi(2.0 * (zl - floor(zl)), &sn, &cs);
+              ai = (float)(amp * sn / (double)zf);
+              amp = (float)(amp * cs / (double)zf);
+            }
           }
         } else {
           const int lz = L[p];
           amp = lz < Z ? (float)I[p] : 0.f;
           af = s_a[lz < Z ? lz : 0];
+          if constexpr (LF) {
+            const float2 c = s_lf[lz < Z ? lz : 0];
+            ai = amp * c.y;
+            amp = amp * c.x;
+          }
         }
         v = make_int4(s * i, s * j, __float_as_int(amp), (int)(unsigned)(af & 0xffffffffull));
       }
       s_pt[threadIdx.x] = v;
       s_ph[threadIdx.x] = (unsigned)(af >> 32);
+      if constexpr (LF) s_ai[threadIdx.x] = ai;
     }
     __syncthreads();
     const int cnt = min(PD_CHUNK, npts - base);
@@ -439,6 +468,7 @@ __global__ void __launch_bounds__(256) k_plain_direct(const uint8_t* __restrict_
     for (int k = 0; k < cnt; ++k) {
       const int4 pt = s_pt[k];
       const float amp = __int_as_float(pt.z);
+      const float amp_i = LF ? s_ai[k] : 0.f;
       const unsigned alo = (unsigned)pt.w, ahi = s_ph[k];
       unsigned dx2[2], dy2[4];
 #pragma unroll
@@ -460,8 +490,13 @@ __global__ void __launch_bounds__(256) k_plain_direct(const uint8_t* __restrict_
           const float cyc = __int_as_float(((ph >> 9) ^ 0x400000u) | 0x3f800000u) - 1.5f;
           float sn, cs;
           __sincosf(cyc * 6.28318530717958647692f, &sn, &cs);
-          cre[r][c] = fmaf(amp, cs, cre[r][c]);
-          cim[r][c] = fmaf(amp, sn, cim[r][c]);
+          if constexpr (LF) {
+            cre[r][c] = fmaf(amp, cs, fmaf(-amp_i, sn, cre[r][c]));
+            cim[r][c] = fmaf(amp, sn, fmaf(amp_i, cs, cim[r][c]));
+          } else {
+            cre[r][c] = fmaf(amp, cs, cre[r][c]);
+            cim[r][c] = fmaf(amp, sn, cim[r][c]);
+          }
         }
     }
 #pragma unroll
@@ -490,16 +525,28 @@ __global__ void __launch_bounds__(256) k_plain_direct(const uint8_t* __restrict_
 cudaError_t launch_plain_direct(const cgh_plan* p, const uint8_t* I, const uint8_t* L, float2* holo,
                                 cudaStream_t st) {
   dim3 grid((p->holo_w + PD_TN - 1) / PD_TN, (p->holo_h + PD_TM - 1) / PD_TM);
-  k_plain_direct<false><<<grid, 256, 0, st>>>(I, L, nullptr, p->obj_h, p->obj_w, p->n_layers, p->s, p->d_a_fixed,
-                                              p->pitch, p->wavelength, holo, p->holo_h, p->holo_w, 0);
+  if (p->layer_factor)
+    k_plain_direct<false, true><<<grid, 256, 0, st>>>(I, L, nullptr, p->obj_h, p->obj_w, p->n_layers, p->s,
+                                                      p->d_a_fixed, p->d_lf_full, p->pitch, p->wavelength, holo,
+                                                      p->holo_h, p->holo_w, 0);
+  else
+    k_plain_direct<false, false><<<grid, 256, 0, st>>>(I, L, nullptr, p->obj_h, p->obj_w, p->n_layers, p->s,
+                                                       p->d_a_fixed, nullptr, p->pitch, p->wavelength, holo,
+                                                       p->holo_h, p->holo_w, 0);
   return cudaGetLastError();
 }
 
 cudaError_t launch_pointcloud_direct(const cgh_plan* p, const uint8_t* I, const float* depth, float2* holo,
                                      int accumulate, cudaStream_t st) {
   dim3 grid((p->holo_w + PD_TN - 1) / PD_TN, (p->holo_h + PD_TM - 1) / PD_TM);
-  k_plain_direct<true><<<grid, 256, 0, st>>>(I, nullptr, depth, p->obj_h, p->obj_w, p->n_layers, p->s, nullptr,
-                                             p->pitch, p->wavelength, holo, p->holo_h, p->holo_w, accumulate);
+  if (p->layer_factor)
+    k_plain_direct<true, true><<<grid, 256, 0, st>>>(I, nullptr, depth, p->obj_h, p->obj_w, p->n_layers, p->s,
+                                                     nullptr, nullptr, p->pitch, p->wavelength, holo, p->holo_h,
+                                                     p->holo_w, accumulate);
+  else
+    k_plain_direct<true, false><<<grid, 256, 0, st>>>(I, nullptr, depth, p->obj_h, p->obj_w, p->n_layers, p->s,
+                                                      nullptr, nullptr, p->pitch, p->wavelength, holo, p->holo_h,
+                                                      p->holo_w, accumulate);
   return cudaGetLastError();
 }
 

@@ -399,7 +399,8 @@ static void stage1_args(const cgh_plan* p, bool f16, TcGemmArgs& a, dim3& tiles)
   a.n_layers = p->n_layers;
   a.M = p->holo_w;
   a.N = t->ktot_alloc;
-  a.scale = f16 ? 1.0f / 1024.0f : 1.0f / 64.0f;
+  // fp16: a further 2^-4, and 2^-lf_extra for the layer factor's 1/sqrt(z) on each fringe
+  a.scale = f16 ? ldexpf(1.0f, -10 - p->lf_extra) : 1.0f / 64.0f;
   a.Y = t->Y;
   a.y_plane = t->y_plane;
   a.ldy = t->ktot_alloc;
@@ -423,7 +424,7 @@ static void stage2_args(const cgh_plan* p, bool f16, float2* holo, int S, TcGemm
   a.n_layers = p->n_layers;
   a.M = p->holo_h;
   a.N = p->holo_w;
-  a.scale = f16 ? 16.0f : 1.0f;
+  a.scale = f16 ? ldexpf(1.0f, 4 + p->lf_extra) : 1.0f;
   a.H = holo;
   a.ldh = p->holo_w;
   a.h_vec4 = ((p->holo_w & 1) == 0) && (((uintptr_t)holo & 15) == 0);
