@@ -233,6 +233,7 @@ __global__ void __launch_bounds__(CGH_SEL_CHUNK) k_select_count(const uint8_t* _
   const int chunk = blockIdx.x - tk.chunk0;
   const int level = tk.level, nbx = W >> level, nb = (H >> level) * nbx;
   for (int t = threadIdx.x; t < Z; t += blockDim.x) s_cnt[t] = 0;
+  if (chunk == 0 && threadIdx.x == 0) tk.count[1] = 0;  // the scan's CTA counter
   __syncthreads();
   const int b = chunk * CGH_SEL_CHUNK + threadIdx.x;
   unsigned long long m =
@@ -245,38 +246,90 @@ __global__ void __launch_bounds__(CGH_SEL_CHUNK) k_select_count(const uint8_t* _
   for (int z = threadIdx.x; z < Z; z += blockDim.x) chunk_cnt[tk.cnt_off + z * tk.nchunks + chunk] = s_cnt[z];
 }
 
-// Pass 2: per task, exclusive scan of its counts in (layer, chunk) order; one CTA of 1024
-// threads per task.
-__global__ void __launch_bounds__(1024) k_select_scan(const int* __restrict__ chunk_cnt,
-                                                      int* __restrict__ chunk_off, int Z, const SelTasks T) {
-  __shared__ int s_part[1024];
+// Pass 2: per task, exclusive scan of its counts in (layer, chunk) order, in blocks of
+// SEL_SCAN_BLOCK entries (1024 threads x 4 consecutive entries; grid: blocks x tasks).  Each
+// CTA writes the offsets within its block and leaves the block's total in the count table
+// at the block's first entry (which it has read by then).  The task's last CTA to finish
+// (counted on count[1], zeroed by pass 1) replaces the totals by their exclusive prefix
+// and writes the list length; the scatter adds the prefix of its block.
+#define SEL_SCAN_BLOCK 4096
+
+// Exclusive scan of one int per thread over a 1024-thread CTA; returns the CTA total too.
+__device__ __forceinline__ int cta_exclusive_scan(int x, int* s_warp, int& total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int inc = x;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int t = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += t;
+  }
+  if (lane == 31) s_warp[warp] = inc;
+  __syncthreads();
+  if (warp == 0) {
+    const int w = s_warp[lane];
+    int wi = w;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t = __shfl_up_sync(0xffffffffu, wi, o);
+      if (lane >= o) wi += t;
+    }
+    s_warp[lane] = wi - w;
+    if (lane == 31) s_warp[32] = wi;
+  }
+  __syncthreads();
+  total = s_warp[32];
+  const int r = s_warp[warp] + inc - x;
+  __syncthreads();  // s_warp may be reused
+  return r;
+}
+
+__global__ void __launch_bounds__(1024) k_select_scan(int* chunk_cnt, int* __restrict__ chunk_off,
+                                                      int Z, const SelTasks T) {
+  __shared__ int s_warp[33];
+  __shared__ int s_last;
   pdl_wait();
   pdl_trigger();
-  const SelTask& tk = T.t[blockIdx.x];
-  const int n = Z * tk.nchunks;
-  const int* cnt = chunk_cnt + tk.cnt_off;
+  const SelTask& tk = T.t[blockIdx.y];
+  const int n = Z * tk.nchunks, nblk = (n + SEL_SCAN_BLOCK - 1) / SEL_SCAN_BLOCK;
+  const int b0 = blockIdx.x * SEL_SCAN_BLOCK;
+  if (b0 >= n) return;
+  int* cnt = chunk_cnt + tk.cnt_off;
   int* off = chunk_off + tk.cnt_off;
-  const int per = (n + 1023) / 1024;
-  const int lo = threadIdx.x * per, hi = min(n, lo + per);
-  int sum = 0;
-  for (int i = lo; i < hi; ++i) sum += cnt[i];
-  s_part[threadIdx.x] = sum;
+  const int i0 = b0 + 4 * threadIdx.x;
+  int v[4], sum = 0;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    v[q] = i0 + q < n ? cnt[i0 + q] : 0;
+    sum += v[q];
+  }
+  int block_total;
+  int run = cta_exclusive_scan(sum, s_warp, block_total);
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+    if (i0 + q < n) {
+      off[i0 + q] = run;
+      run += v[q];
+    }
+  if (threadIdx.x == 0) {  // every count of the block was read before the scan's barriers
+    cnt[b0] = block_total;
+    __threadfence();
+    s_last = atomicAdd(&tk.count[1], 1) == nblk - 1;
+  }
   __syncthreads();
-  for (int o = 1; o < 1024; o <<= 1) {  // inclusive Hillis-Steele scan
-    const int v = threadIdx.x >= o ? s_part[threadIdx.x - o] : 0;
-    __syncthreads();
-    s_part[threadIdx.x] += v;
-    __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  int carry = 0;
+  for (int r0 = 0; r0 < nblk; r0 += 1024) {
+    const int b = r0 + threadIdx.x;
+    const int t = b < nblk ? __ldcg(cnt + (size_t)b * SEL_SCAN_BLOCK) : 0;
+    int round_total;
+    const int e = cta_exclusive_scan(t, s_warp, round_total);
+    if (b < nblk) cnt[(size_t)b * SEL_SCAN_BLOCK] = carry + e;
+    carry += round_total;
   }
-  int run = s_part[threadIdx.x] - sum;
-  for (int i = lo; i < hi; ++i) {
-    off[i] = run;
-    run += cnt[i];
-  }
-  if (threadIdx.x == 1023) {
-    const int total = s_part[1023];
-    tk.count[0] = min(total, tk.capacity);
-    tk.count[1] = total;
+  if (threadIdx.x == 0) {
+    tk.count[0] = min(carry, tk.capacity);
+    tk.count[1] = carry;
   }
 }
 
@@ -288,6 +341,7 @@ __global__ void __launch_bounds__(CGH_SEL_CHUNK) k_select_scatter(
     const int* __restrict__ chunk_cnt, const int* __restrict__ chunk_off) {
   constexpr int NW = CGH_SEL_CHUNK / 32;
   __shared__ int s_wcnt[NW][CGH_MAX_LAYERS];
+  __shared__ int s_pre[CGH_MAX_LAYERS];
   pdl_wait();
   pdl_trigger();
   const SelTask& tk = T.t[sel_task_of(T, blockIdx.x)];
@@ -312,13 +366,17 @@ __global__ void __launch_bounds__(CGH_SEL_CHUNK) k_select_scatter(
       s_wcnt[w][threadIdx.x] = run;
       run += c;
     }
+    // the prefix of the scan block holding this layer's entry
+    const int blk = (threadIdx.x * tk.nchunks + chunk) / SEL_SCAN_BLOCK;
+    s_pre[threadIdx.x] = chunk_cnt[tk.cnt_off + blk * SEL_SCAN_BLOCK];
   }
   __syncthreads();
   for (int z = 0; z < Z; ++z) {
     const bool f = (m >> z) & 1ull;
     const unsigned bal = __ballot_sync(0xffffffffu, f);
     if (f) {
-      const int pos = chunk_off[tk.cnt_off + z * tk.nchunks + chunk] + s_wcnt[warp][z] + __popc(bal & below);
+      const int pos =
+          chunk_off[tk.cnt_off + z * tk.nchunks + chunk] + s_pre[z] + s_wcnt[warp][z] + __popc(bal & below);
       if (pos < tk.capacity) tk.list[pos] = (z << 24) | (by << 12) | bx;
     }
   }
@@ -342,8 +400,13 @@ cudaError_t launch_select_tasks(int obj_h, int obj_w, int n_layers, const uint8_
   }
   cudaError_t e = launch_pdl(k_select_count, dim3(c0), dim3(CGH_SEL_CHUNK), 0, st, sal, L, obj_h, obj_w, n_layers,
                              T, chunk_cnt);
+  int nblk = 1;
+  for (int k = 0; k < T.n; ++k) {
+    const int b = (n_layers * T.t[k].nchunks + SEL_SCAN_BLOCK - 1) / SEL_SCAN_BLOCK;
+    nblk = b > nblk ? b : nblk;
+  }
   if (e == cudaSuccess)
-    e = launch_pdl(k_select_scan, dim3(T.n), dim3(1024), 0, st, (const int*)chunk_cnt, chunk_off, n_layers, T);
+    e = launch_pdl(k_select_scan, dim3(nblk, T.n), dim3(1024), 0, st, chunk_cnt, chunk_off, n_layers, T);
   if (e == cudaSuccess)
     e = launch_pdl(k_select_scatter, dim3(c0), dim3(CGH_SEL_CHUNK), 0, st, sal, L, obj_h, obj_w, n_layers, T,
                    (const int*)chunk_cnt, (const int*)chunk_off);

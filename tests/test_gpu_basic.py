@@ -273,3 +273,19 @@ def test_select_large_count_table(torch_cuda):
     cc = cnt.cpu().numpy()
     assert cc[0] == cap and cc[1] == len(ref_lists[1])
     assert np.array_equal(lst.cpu().numpy(), ref_lists[1][:cap])
+
+
+def test_select_many_scan_blocks(torch_cuda):
+    """A 1024x1024 object with 64 layers: the level-1 count table (64 layers x 1024 chunks)
+    spans 16 scan blocks, so list offsets cross block boundaries in every layer."""
+    torch = torch_cuda
+    sc = scenes.random_scene(98, 1024, 1024, 64, graded=True)
+    plan = plan_for(sc)
+    S, L = dev(torch, sc["saliency"]), dev(torch, sc["layer"])
+    ref_lists = O.progressive_lists(sc["saliency"], sc["layer"], 64, scenes.THRESHOLDS_U8)
+    for _ in range(2):  # the scan's CTA counter restarts on every call
+        lists, counts = plan.progressive_lists(S, L, scenes.THRESHOLDS_U8)
+        c = counts.cpu().numpy()
+        for k in range(4):
+            assert c[k, 0] == c[k, 1] == len(ref_lists[k]), k
+            assert np.array_equal(lists[k][:c[k, 0]].cpu().numpy(), ref_lists[k]), k
