@@ -467,6 +467,19 @@ int cgh_profile_read(cgh_plan* plan, float* ms, void* stream);
 int cgh_tc_layer_dims(const cgh_plan* plan, int* kr, int* kc, void* stream);
 
 /*
+ * cgh_probe_sfu / cgh_probe_ffma - microbenchmarks for the roofline peaks of the direct
+ * kernels (the paper has no counterpart).  `grid` CTAs of 256 threads; every thread runs
+ * iters x 8 independent SFU sine-cosine pairs (__sincosf on [0, 1.1]), or iters x 32 FP32
+ * fused multiply-adds (16 packed FP32x2 chains); sink (device float[grid*256]) receives one
+ * value per thread.  Time the call with CUDA events on `stream`: pairs (or flops = 2 x FMAs)
+ * per second give the measured peak that the point-wise (or detail-basis direct) kernel is
+ * compared with.  Errors: CGH_ERR_ARG (NULL sink, grid outside 1..2^20, iters outside
+ * 1..2^32), CGH_ERR_CUDA.
+ */
+int cgh_probe_sfu(float* sink, int grid, long long iters, void* stream);
+int cgh_probe_ffma(float* sink, int grid, long long iters, void* stream);
+
+/*
  * cgh_selftest_timeout - failure-detection self-test (the paper has no counterpart).
  * Enqueues a kernel whose bounded device wait, the same one the tensor-core pipeline uses,
  * waits on a barrier that nothing completes; after limit_us microseconds (1..1000000) it

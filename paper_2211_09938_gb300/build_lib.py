@@ -11,7 +11,7 @@ LIB = os.path.join(HERE, "libcgh.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2", "--expt-relaxed-constexpr"]
 SOURCES = ["cgh_api.cu", "kernels_basic.cu", "kernels_tc.cu", "kernels_field.cu", "kernels_quality.cu",
-           "kernels_asm.cu", "cgh_noalloc.cu"]
+           "kernels_asm.cu", "kernels_probe.cu", "cgh_noalloc.cu"]
 
 
 def nvcc():

@@ -59,6 +59,8 @@ SIGNATURES = {
     "cgh_ssim": (_I, [_P, _P, _I, _I, _I, _P, _P, _P]),
     "cgh_status": (_I, [_P, ctypes.POINTER(_I), _P]),
     "cgh_selftest_timeout": (_I, [_P, _I, _P]),
+    "cgh_probe_sfu": (_I, [_P, _I, ctypes.c_longlong, _P]),
+    "cgh_probe_ffma": (_I, [_P, _I, ctypes.c_longlong, _P]),
     "cgh_tc_selftest_gemm": (_I, [_P, _P, _P, _I, _I, _I, _I, _P]),
     "cgh_batch_create": (_I, [ctypes.POINTER(_P), ctypes.POINTER(_P), _I, ctypes.POINTER(_P),
                               ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_I),
@@ -344,6 +346,28 @@ def tc_selftest_gemm(A, B, fp16=False, stream=None):
     check(lib().cgh_tc_selftest_gemm(_ptr(A), _ptr(B), _ptr(C), M, N, K, 1 if fp16 else 0,
                                      _stream(stream)))
     return C
+
+
+def probe_peaks(iters=4096, stream=None):
+    """Measured peaks of the SFU and FP32 FMA units (cgh_probe_sfu / cgh_probe_ffma), timed
+    with CUDA events: {"sfu_pairs_per_s", "ffma_flops_per_s"}.  Synchronises."""
+    import torch
+    dev = torch.cuda.current_device()
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    grid = sms * 8
+    sink = torch.empty(grid * 256, dtype=torch.float32, device="cuda")
+    st = stream or torch.cuda.current_stream()
+    out = {}
+    for name, fn, per in (("sfu_pairs_per_s", lib().cgh_probe_sfu, 8), ("ffma_flops_per_s", lib().cgh_probe_ffma, 64)):
+        check(fn(_ptr(sink), grid, 64, _stream(st)))  # warm-up
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        with torch.cuda.stream(st):
+            ev[0].record(st)
+            check(fn(_ptr(sink), grid, int(iters), _stream(st)))
+            ev[1].record(st)
+        ev[1].synchronize()
+        out[name] = grid * 256.0 * iters * per / (ev[0].elapsed_time(ev[1]) / 1e3)
+    return out
 
 
 def phase_to_field(phase, out=None, stream=None):
