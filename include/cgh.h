@@ -207,7 +207,8 @@ int cgh_select_blocks_noalloc(const uint8_t* saliency, const uint8_t* layer_idx,
  *   lists       HOST array of 4 device pointers;  capacities  HOST int[4]
  *   d_counts    device int32 [4][2] output, ([written, total] per list, as d_count of
  *               cgh_select_blocks); directly usable by cgh_progressive_hologram
- * Runs the three compaction passes once for all four lists (three kernel launches).
+ * Runs the compaction once for all four lists: one cooperative launch with a single grid
+ * barrier when the count tables are small (see cgh_progressive_step), else three passes.
  * Uses plan scratch.  Bit-exact.  Errors: CGH_ERR_ARG, CGH_ERR_CUDA.
  */
 int cgh_select_progressive(const cgh_plan* plan, const uint8_t* saliency, const uint8_t* layer_idx,
@@ -235,6 +236,34 @@ int cgh_select_progressive(const cgh_plan* plan, const uint8_t* saliency, const 
 int cgh_progressive_hologram(const cgh_plan* plan, const int32_t* coeffs,
                              const int32_t* const* lists, const int32_t* d_counts,
                              float* holo, int accumulate, int form, void* stream);
+
+/*
+ * cgh_progressive_step - block selection and progressive superposition in one call.
+ * Paper: Section 2 steps 1-5 (selection of the LLL band and of the detail blocks above
+ * their saliency thresholds) followed by Eq. 3 (superposition of the selected blocks).
+ * Same outputs as cgh_select_progressive(saliency, layer_idx, thresholds, lists,
+ * capacities, d_counts) followed by cgh_progressive_hologram(coeffs, lists, d_counts,
+ * holo, accumulate, form):
+ *   lists, d_counts  the four work lists and their [written, total] counts, bit-exact
+ *   holo             the hologram of the written list entries
+ * Arguments as for those two calls (saliency, layer_idx 8-byte aligned; thresholds,
+ * lists, capacities HOST arrays; all four lists non-NULL), plus
+ *   coeffs_ready  a cudaEvent_t or NULL: when given, `stream` waits for it after the
+ *                 selection and before coeffs is first read, so that a DWT running on
+ *                 another stream overlaps the selection
+ * For the tensor-core forms,
+ * when the selection's count tables are small (at most 8192 per-layer chunk counts per
+ * list and a grid the device holds at once, e.g. a 512x512 object with 16 layers), the
+ * selection runs as one cooperative launch with a single grid barrier and marks the
+ * operands' selection flags itself, so the lists are not read back.  Its wait is bounded:
+ * on timeout it records CGH_ERR_TIMEOUT in the status word (cgh_status); the plan's
+ * barrier state is then undefined and the plan must be destroyed.  Uses plan scratch.
+ * Errors: CGH_ERR_ARG, CGH_ERR_UNSUPPORTED (form), CGH_ERR_CUDA.
+ */
+int cgh_progressive_step(const cgh_plan* plan, const uint8_t* saliency, const uint8_t* layer_idx,
+                         const int32_t* coeffs, const void* coeffs_ready, const int* thresholds,
+                         int32_t* const* lists, const int* capacities, int32_t* d_counts, float* holo,
+                         int accumulate, int form, void* stream);
 
 /*
  * cgh_plain_direct - plain point-wise hologram, no wavelet and no saliency.

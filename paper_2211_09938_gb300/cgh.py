@@ -47,6 +47,8 @@ SIGNATURES = {
     "cgh_select_progressive": (_I, [_P, _P, _P, ctypes.POINTER(_I), ctypes.POINTER(_P),
                                     ctypes.POINTER(_I), _P, _P]),
     "cgh_progressive_hologram": (_I, [_P, _P, ctypes.POINTER(_P), _P, _P, _I, _I, _P]),
+    "cgh_progressive_step": (_I, [_P, _P, _P, _P, _P, ctypes.POINTER(_I), ctypes.POINTER(_P),
+                                  ctypes.POINTER(_I), _P, _P, _I, _I, _P]),
     "cgh_plain_direct": (_I, [_P, _P, _P, _P, _P]),
     "cgh_pointcloud_direct": (_I, [_P, _P, _P, _P, _I, _P]),
     "cgh_reconstruct": (_I, [_P, _P, _P, _P, _P, _P]),
@@ -235,6 +237,30 @@ class Plan:
         check(lib().cgh_progressive_hologram(self.handle, _ptr(coeffs), arr, _ptr(counts), _ptr(holo),
                                              1 if accumulate else 0, f, _stream(stream)))
         return holo
+
+    def progressive_step(self, saliency, layer, coeffs, thresholds, counts=None, lists=None, holo=None,
+                         accumulate=False, form="tc_bf16x3", coeffs_ready=None, stream=None):
+        """Selection and superposition in one call (cgh_progressive_step): the outputs of
+        progressive_lists followed by progressive_hologram.  coeffs_ready: a torch.cuda.Event
+        the call waits for after the selection, before it reads coeffs (a DWT on another
+        stream then overlaps the selection).  Returns (holo, lists, counts)."""
+        import torch
+        if counts is None:
+            counts = torch.zeros((4, 2), dtype=torch.int32, device=self.device)
+        if lists is None:
+            lists = [torch.empty(self.max_blocks(3 if k == 0 else k), dtype=torch.int32,
+                                 device=self.device) for k in range(4)]
+        if holo is None:
+            holo = torch.empty((self.holo_h, self.holo_w), dtype=torch.complex64, device=self.device)
+        thr = (ctypes.c_int * 3)(*[int(thresholds[l]) for l in (1, 2, 3)])
+        ptrs = (ctypes.c_void_p * 4)(*[l.data_ptr() for l in lists])
+        caps = (ctypes.c_int * 4)(*[l.numel() for l in lists])
+        f = FORMS[form] if isinstance(form, str) else int(form)
+        ev = None if coeffs_ready is None else ctypes.c_void_p(coeffs_ready.cuda_event)
+        check(lib().cgh_progressive_step(self.handle, _ptr(saliency), _ptr(layer), _ptr(coeffs), ev, thr, ptrs,
+                                         caps, _ptr(counts), _ptr(holo), 1 if accumulate else 0, f,
+                                         _stream(stream)))
+        return holo, lists, counts
 
     def plain_direct(self, intensity, layer, holo=None, stream=None):
         import torch

@@ -57,6 +57,7 @@ int cgh_plan_destroy(cgh_plan* p) {
   cudaFree(p->d_status);
   cudaFree(p->d_chunk_cnt);
   cudaFree(p->d_chunk_off);
+  cudaFree(p->d_sel_bar);
   free(p);
   return CGH_OK;
 }
@@ -168,6 +169,13 @@ int cgh_plan_create(cgh_plan** out, int obj_h, int obj_w, int holo_h, int holo_w
                       cudaMemcpyHostToDevice),
            "cgh_plan_create: copy a_fixed");
   PLAN_TRY(cudaMemset(p->d_status, 0, sizeof(int)), "cgh_plan_create: status clear");
+  PLAN_TRY(cudaMalloc(&p->d_sel_bar, sizeof(unsigned)), "cgh_plan_create: selection barrier");
+  PLAN_TRY(cudaMemset(p->d_sel_bar, 0, sizeof(unsigned)), "cgh_plan_create: selection barrier clear");
+  {
+    int sms = 0;
+    PLAN_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device), "cgh_plan_create: SM count");
+    p->sel_coop_ctas = select_fused_ctas_per_sm() * sms;
+  }
   if (p->layer_factor) {
     // c_z = exp(j 2 pi frac(z/lambda)) / z; its square root goes into the point fringe of
     // both axes (so every separable product carries c_z once), c_z itself into the
@@ -220,11 +228,31 @@ int cgh_select_blocks(const cgh_plan* p, const uint8_t* saliency, const uint8_t*
   if (((uintptr_t)layer_idx & 7) || (threshold >= 0 && ((uintptr_t)saliency & 7)))
     return cgh_fail(CGH_ERR_ARG, "cgh_select_blocks: saliency and layer_idx must be 8-byte aligned");
   prof_mark(p, CGH_PROF_SELECT, 0, (cudaStream_t)stream);
+  const SelCoop coop = plan_sel_coop(p);
   CHECK_CUDA(launch_select(p->obj_h, p->obj_w, p->n_layers, threshold >= 0 ? saliency : NULL, layer_idx,
                            threshold, level, list, d_count, capacity, p->d_chunk_cnt, p->d_chunk_off,
-                           (cudaStream_t)stream),
+                           (cudaStream_t)stream, &coop),
              "cgh_select_blocks");
   prof_mark(p, CGH_PROF_SELECT, 1, (cudaStream_t)stream);
+  return CGH_OK;
+}
+
+// The four selections of one progressive call (LLL, levels 1, 2, 3) from the host arguments.
+static int progressive_tasks(const int* thresholds, int32_t* const* lists, const int* capacities, int32_t* d_counts,
+                             SelTasks* T, const char* name) {
+  memset(T, 0, sizeof(*T));
+  T->n = 4;
+  for (int k = 0; k < 4; ++k) {
+    if (capacities[k] < 0) return cgh_fail(CGH_ERR_ARG, "%s: capacities[%d] < 0", name, k);
+    if (capacities[k] > 0 && !lists[k]) return cgh_fail(CGH_ERR_ARG, "%s: lists[%d] is NULL", name, k);
+    const int thr = k == 0 ? -1 : thresholds[k - 1];
+    if (thr < -1 || thr > 255) return cgh_fail(CGH_ERR_ARG, "%s: threshold %d not in -1..255", name, thr);
+    T->t[k].level = k == 0 ? CGH_LEVELS : k;
+    T->t[k].threshold = thr;
+    T->t[k].capacity = capacities[k];
+    T->t[k].list = lists[k];
+    T->t[k].count = d_counts + 2 * k;
+  }
   return CGH_OK;
 }
 
@@ -236,26 +264,41 @@ int cgh_select_progressive(const cgh_plan* p, const uint8_t* saliency, const uin
   if (((uintptr_t)layer_idx & 7) || ((uintptr_t)saliency & 7))
     return cgh_fail(CGH_ERR_ARG, "cgh_select_progressive: saliency and layer_idx must be 8-byte aligned");
   SelTasks T;
-  memset(&T, 0, sizeof(T));
-  T.n = 4;
-  for (int k = 0; k < 4; ++k) {
-    if (capacities[k] < 0) return cgh_fail(CGH_ERR_ARG, "cgh_select_progressive: capacities[%d] < 0", k);
-    if (capacities[k] > 0 && !lists[k]) return cgh_fail(CGH_ERR_ARG, "cgh_select_progressive: lists[%d] is NULL", k);
-    const int thr = k == 0 ? -1 : thresholds[k - 1];
-    if (thr < -1 || thr > 255)
-      return cgh_fail(CGH_ERR_ARG, "cgh_select_progressive: threshold %d not in -1..255", thr);
-    T.t[k].level = k == 0 ? CGH_LEVELS : k;
-    T.t[k].threshold = thr;
-    T.t[k].capacity = capacities[k];
-    T.t[k].list = lists[k];
-    T.t[k].count = d_counts + 2 * k;
-  }
+  int rc = progressive_tasks(thresholds, lists, capacities, d_counts, &T, "cgh_select_progressive");
+  if (rc != CGH_OK) return rc;
   prof_mark(p, CGH_PROF_SELECT, 0, (cudaStream_t)stream);
+  const SelCoop coop = plan_sel_coop(p);
   CHECK_CUDA(launch_select_tasks(p->obj_h, p->obj_w, p->n_layers, saliency, layer_idx, T, p->d_chunk_cnt,
-                                 p->d_chunk_off, (cudaStream_t)stream),
+                                 p->d_chunk_off, (cudaStream_t)stream, &coop),
              "cgh_select_progressive");
   prof_mark(p, CGH_PROF_SELECT, 1, (cudaStream_t)stream);
   return CGH_OK;
+}
+
+int cgh_progressive_step(const cgh_plan* p, const uint8_t* saliency, const uint8_t* layer_idx,
+                         const int32_t* coeffs, const void* coeffs_ready, const int* thresholds,
+                         int32_t* const* lists, const int* capacities, int32_t* d_counts, float* holo,
+                         int accumulate, int form, void* stream) {
+  if (!p || !saliency || !layer_idx || !coeffs || !thresholds || !lists || !capacities || !d_counts || !holo)
+    return cgh_fail(CGH_ERR_ARG, "cgh_progressive_step: NULL argument");
+  for (int k = 0; k < 4; ++k)
+    if (!lists[k]) return cgh_fail(CGH_ERR_ARG, "cgh_progressive_step: lists[%d] is NULL", k);
+  if (((uintptr_t)layer_idx & 7) || ((uintptr_t)saliency & 7))
+    return cgh_fail(CGH_ERR_ARG, "cgh_progressive_step: saliency and layer_idx must be 8-byte aligned");
+  if (((uintptr_t)holo & 7)) return cgh_fail(CGH_ERR_ARG, "cgh_progressive_step: holo must be 8-byte aligned");
+  SelTasks T;
+  int rc = progressive_tasks(thresholds, lists, capacities, d_counts, &T, "cgh_progressive_step");
+  if (rc != CGH_OK) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (form == CGH_FORM_TC_BF16X3 || form == CGH_FORM_TC_FP16X3)
+    return tc_progressive_step(p, saliency, layer_idx, coeffs, (cudaEvent_t)coeffs_ready, T, lists, d_counts,
+                               (float2*)holo, accumulate, form, st);
+  if (form != CGH_FORM_DIRECT_LUT) return cgh_fail(CGH_ERR_UNSUPPORTED, "cgh_progressive_step: unknown form %d", form);
+  rc = cgh_select_progressive(p, saliency, layer_idx, thresholds, lists, capacities, d_counts, stream);
+  if (rc != CGH_OK) return rc;
+  if (coeffs_ready)
+    CHECK_CUDA(cudaStreamWaitEvent(st, (cudaEvent_t)coeffs_ready, 0), "cgh_progressive_step: wait for coeffs");
+  return cgh_progressive_hologram(p, coeffs, lists, d_counts, holo, accumulate, form, stream);
 }
 
 int cgh_progressive_hologram(const cgh_plan* p, const int32_t* coeffs, const int32_t* const* lists,

@@ -40,10 +40,13 @@ struct cgh_plan {
   // Status word for bounded device waits.
   int* d_status;
 
-  // Scratch for block compaction: per (layer, chunk) counts and offsets.
+  // Scratch for block compaction: per (layer, chunk) counts and offsets; the fused
+  // selection's grid-barrier word and the largest grid it may launch.
   int* d_chunk_cnt;
   int* d_chunk_off;
   int max_chunks;
+  unsigned* d_sel_bar;
+  int sel_coop_ctas;
 
   // Separable tensor-core path (allocated lazily by the first call that needs it).
   struct cgh_tc_state* tc;
@@ -103,15 +106,26 @@ int cgh_cuda_check(cudaError_t e, const char* what);
 #define CGH_SEL_CHUNK 256
 
 // One block selection (a level, a threshold, an output list) inside a launch.
+#define SEL_FLAGS_NONE 0
+#define SEL_FLAGS_LLL 1     // mark occ3 / rowband / colband (the LLL list)
+#define SEL_FLAGS_DETAIL 2  // mark sel[level] (a detail list)
 struct SelTask {
   int level, threshold, capacity;
   int nchunks, chunk0, cnt_off;  // filled by launch_select_tasks
+  int flag_kind;                 // SEL_FLAGS_*: tensor-core flags the fused selection marks
   int32_t* list;
   int32_t* count;
 };
 struct SelTasks {
   SelTask t[4];
   int n;
+};
+// The fused single-launch selection: the plan's grid-barrier word, its status word and the
+// largest grid the device holds at once (0: use the three-pass selection).
+struct SelCoop {
+  unsigned* bar;
+  int* status;
+  int max_ctas;
 };
 
 // Kernel launchers (kernels_basic.cu).  All asynchronous on `st`.
@@ -120,7 +134,7 @@ cudaError_t launch_haar(const cgh_plan* p, const uint8_t* I, const uint8_t* L, i
                         cudaStream_t st);
 cudaError_t launch_select(int obj_h, int obj_w, int n_layers, const uint8_t* sal, const uint8_t* L,
                           int threshold, int level, int32_t* list, int32_t* d_count, int capacity,
-                          int* chunk_cnt, int* chunk_off, cudaStream_t st);
+                          int* chunk_cnt, int* chunk_off, cudaStream_t st, const SelCoop* coop = nullptr);
 cudaError_t launch_direct_lut(const cgh_plan* p, const int32_t* coef, const int32_t* const* lists,
                               const int32_t* d_counts, float2* holo, cudaStream_t st);
 cudaError_t launch_plain_direct(const cgh_plan* p, const uint8_t* I, const uint8_t* L, float2* holo,
@@ -128,8 +142,13 @@ cudaError_t launch_plain_direct(const cgh_plan* p, const uint8_t* I, const uint8
 cudaError_t launch_pointcloud_direct(const cgh_plan* p, const uint8_t* I, const float* depth, float2* holo,
                                      int accumulate, cudaStream_t st);
 int select_num_chunks(int obj_h, int obj_w, int level);
+struct TcFlags;
 cudaError_t launch_select_tasks(int obj_h, int obj_w, int n_layers, const uint8_t* sal, const uint8_t* L,
-                                SelTasks T, int* chunk_cnt, int* chunk_off, cudaStream_t st);
+                                SelTasks T, int* chunk_cnt, int* chunk_off, cudaStream_t st,
+                                const SelCoop* coop = nullptr, const TcFlags* fl = nullptr,
+                                bool* flags_done = nullptr);
+int select_fused_ctas_per_sm();
+static inline SelCoop plan_sel_coop(const cgh_plan* p) { return SelCoop{p->d_sel_bar, p->d_status, p->sel_coop_ctas}; }
 cudaError_t basic_init_attributes();
 int tc_init_attributes();
 
@@ -146,6 +165,10 @@ int tc_reconstruct(const cgh_plan* p, const float2* holo, float2* fields, const 
                    float* amp, cudaStream_t st);
 void tc_destroy(cgh_plan* p);
 int tc_layer_dims(const cgh_plan* p, int* kr, int* kc, cudaStream_t st);
+int tc_progressive_step(const cgh_plan* p, const uint8_t* sal, const uint8_t* L, const int32_t* coef,
+                        cudaEvent_t coef_ready, SelTasks T,
+                        const int32_t* const* lists, const int32_t* d_counts, float2* holo, int accumulate,
+                        int form, cudaStream_t st);
 int tc_build_flags(const cgh_plan* p, const int32_t* const* lists, const int32_t* d_counts, TcFlags* out,
                    cudaStream_t st);
 

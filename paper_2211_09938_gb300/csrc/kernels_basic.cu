@@ -366,20 +366,174 @@ __global__ void __launch_bounds__(CGH_SEL_CHUNK) k_select_scatter(
       s_wcnt[w][threadIdx.x] = run;
       run += c;
     }
-    // the prefix of the scan block holding this layer's entry
-    const int blk = (threadIdx.x * tk.nchunks + chunk) / SEL_SCAN_BLOCK;
-    s_pre[threadIdx.x] = chunk_cnt[tk.cnt_off + blk * SEL_SCAN_BLOCK];
+    // this layer's first position: the prefix of the scan block holding its entry plus the
+    // entry's offset in the block (loaded here, off the ballot loop below)
+    const int e = threadIdx.x * tk.nchunks + chunk;
+    s_pre[threadIdx.x] = chunk_cnt[tk.cnt_off + (e / SEL_SCAN_BLOCK) * SEL_SCAN_BLOCK] + chunk_off[tk.cnt_off + e];
   }
   __syncthreads();
   for (int z = 0; z < Z; ++z) {
     const bool f = (m >> z) & 1ull;
     const unsigned bal = __ballot_sync(0xffffffffu, f);
     if (f) {
-      const int pos =
-          chunk_off[tk.cnt_off + z * tk.nchunks + chunk] + s_pre[z] + s_wcnt[warp][z] + __popc(bal & below);
+      const int pos = s_pre[z] + s_wcnt[warp][z] + __popc(bal & below);
       if (pos < tk.capacity) tk.list[pos] = (z << 24) | (by << 12) | bx;
     }
   }
+}
+
+// ---------------------------------------------------------------------------
+// Single-launch selection for small count tables: one CTA per chunk, all co-resident
+// (cooperative launch), one grid barrier between the counts and the scatter.
+//   1. each CTA computes its blocks' layer masks (kept in registers), its per-layer warp
+//      counts and chunk counts, and stores the chunk counts;
+//   2. grid barrier;
+//   3. each CTA reads its task's whole count table (at most SEL_FUSED_MAX_TABLE entries)
+//      and forms, per layer, the task's total and the count of the chunks before its own;
+//      an exclusive scan of the totals over the layers gives each layer's first position;
+//   4. ordered scatter as in pass 3, optionally marking the selection flags of the
+//      tensor-core operands (exactly the marks the written list entries would give).
+// The barrier is a sense-reversing counter: CTA 0 adds 2^31 - (G - 1) and the others 1, so
+// the top bit flips when the last CTA arrives and the low bits return to their value; it
+// needs no reset between launches.  Its wait is bounded (CGH_ERR_TIMEOUT in *status).
+#define SEL_FUSED_MAX_TABLE 8192
+#define SEL_WAIT_NS 2000000000ull
+
+__device__ __forceinline__ unsigned long long sel_timer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ bool sel_grid_barrier(unsigned* bar, int* status) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned add = blockIdx.x == 0 ? 0x80000000u - (gridDim.x - 1u) : 1u;
+    __threadfence();
+    const unsigned old = atomicAdd(bar, add);
+    const unsigned long long t0 = sel_timer();
+    int ok = 1;
+    while (((ld_acquire_u32(bar) ^ old) & 0x80000000u) == 0u) {
+      if (sel_timer() - t0 > SEL_WAIT_NS) {
+        ok = 0;
+        if (status) atomicExch(status, CGH_ERR_TIMEOUT);
+        break;
+      }
+    }
+    __threadfence();
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+template <bool FLAGS>
+__global__ void __launch_bounds__(CGH_SEL_CHUNK) k_select_fused(const uint8_t* __restrict__ sal,
+                                                                const uint8_t* __restrict__ L, int H, int W,
+                                                                int Z, const SelTasks T, int* cnt_tab,
+                                                                unsigned* bar, int* status, TcFlags fl) {
+  constexpr int NW = CGH_SEL_CHUNK / 32;
+  __shared__ int s_wcnt[NW][CGH_MAX_LAYERS];
+  __shared__ int s_tot[CGH_MAX_LAYERS], s_pre[CGH_MAX_LAYERS];
+  pdl_wait();
+  pdl_trigger();
+  const SelTask& tk = T.t[sel_task_of(T, blockIdx.x)];
+  const int chunk = blockIdx.x - tk.chunk0, nch = tk.nchunks;
+  const int level = tk.level, nbx = W >> level, nb = (H >> level) * nbx;
+  const int b = chunk * CGH_SEL_CHUNK + threadIdx.x;
+  const int by = b / nbx, bx = b - by * nbx;
+  const unsigned long long m = b < nb ? block_layer_mask(sal, L, W, level, by, bx, tk.threshold, Z) : 0ull;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const unsigned below = (1u << lane) - 1u;
+  for (int z = 0; z < Z; ++z) {
+    const unsigned bal = __ballot_sync(0xffffffffu, (m >> z) & 1ull);
+    if (lane == 0) s_wcnt[warp][z] = __popc(bal);
+  }
+  __syncthreads();
+  int* cnt = cnt_tab + tk.cnt_off;
+  if (threadIdx.x < Z) {
+    int run = 0;
+#pragma unroll
+    for (int w = 0; w < NW; ++w) {
+      const int c = s_wcnt[w][threadIdx.x];
+      s_wcnt[w][threadIdx.x] = run;
+      run += c;
+    }
+    cnt[threadIdx.x * nch + chunk] = run;
+  }
+  if (!sel_grid_barrier(bar, status)) return;
+  for (int z = warp; z < Z; z += NW) {
+    int tot = 0, bef = 0;
+#pragma unroll 4
+    for (int c = lane; c < nch; c += 32) {
+      const int v = __ldcg(cnt + z * nch + c);
+      tot += v;
+      bef += c < chunk ? v : 0;
+    }
+    tot = __reduce_add_sync(0xffffffffu, tot);
+    bef = __reduce_add_sync(0xffffffffu, bef);
+    if (lane == 0) {
+      s_tot[z] = tot;
+      s_pre[z] = bef;
+    }
+  }
+  __syncthreads();
+  if (warp == 0) {  // exclusive scan of the layer totals, two layers per lane
+    const int z0 = 2 * lane, z1 = z0 + 1;
+    const int a0 = z0 < Z ? s_tot[z0] : 0, a1 = z1 < Z ? s_tot[z1] : 0;
+    int inc = a0 + a1;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= o) inc += t;
+    }
+    const int ex = inc - a0 - a1;
+    if (z0 < Z) s_pre[z0] += ex;
+    if (z1 < Z) s_pre[z1] += ex + a0;
+    if (chunk == 0 && lane == 31) {
+      tk.count[0] = min(inc, tk.capacity);
+      tk.count[1] = inc;
+    }
+  }
+  __syncthreads();
+  const int hl = H >> level, wl = W >> level;
+  for (int z = 0; z < Z; ++z) {
+    const bool f = (m >> z) & 1ull;
+    const unsigned bal = __ballot_sync(0xffffffffu, f);
+    if (f) {
+      const int pos = s_pre[z] + s_wcnt[warp][z] + __popc(bal & below);
+      if (pos < tk.capacity) {
+        tk.list[pos] = (z << 24) | (by << 12) | bx;
+        if (FLAGS) {
+          if (tk.flag_kind == SEL_FLAGS_LLL) {
+            fl.occ3[((size_t)z * hl + by) * wl + bx] = 1;
+            fl.rowband[(size_t)z * hl + by] = 1;
+            fl.colband[(size_t)z * wl + bx] = 1;
+          } else if (tk.flag_kind == SEL_FLAGS_DETAIL) {
+            uint8_t* sel = level == 1 ? fl.sel[1] : level == 2 ? fl.sel[2] : fl.sel[3];  // no local copy of fl
+            sel[((size_t)z * hl + by) * wl + bx] = 1;
+            // the block's 8-pixel bands are kept even when no LLL entry covers them
+            fl.rowband[(size_t)z * (H >> 3) + (by >> (3 - level))] = 1;
+            fl.colband[(size_t)z * (W >> 3) + (bx >> (3 - level))] = 1;
+          }
+        }
+      }
+    }
+  }
+}
+
+// CTAs of the fused selection that one SM holds at once (the smaller of the two variants).
+int select_fused_ctas_per_sm() {
+  int a = 0, b = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_select_fused<false>, CGH_SEL_CHUNK, 0) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_select_fused<true>, CGH_SEL_CHUNK, 0) != cudaSuccess)
+    return 0;
+  return a < b ? a : b;
 }
 
 int select_tasks_chunks(const SelTasks& T) {
@@ -388,15 +542,42 @@ int select_tasks_chunks(const SelTasks& T) {
   return n;
 }
 
-// Fills chunk0 / cnt_off of the tasks and launches the three passes.
+// Fills chunk0 / cnt_off of the tasks and launches the fused selection when its grid fits
+// on the device at once and every count table is small, else the three passes.  With `fl`
+// the fused kernel also marks the tensor-core selection flags; *flags_done says whether it
+// did (the caller derives them from the lists otherwise).
 cudaError_t launch_select_tasks(int obj_h, int obj_w, int n_layers, const uint8_t* sal, const uint8_t* L,
-                                SelTasks T, int* chunk_cnt, int* chunk_off, cudaStream_t st) {
+                                SelTasks T, int* chunk_cnt, int* chunk_off, cudaStream_t st, const SelCoop* coop,
+                                const TcFlags* fl, bool* flags_done) {
+  if (flags_done) *flags_done = false;
   int c0 = 0;
+  bool small = true;
   for (int k = 0; k < T.n; ++k) {
     T.t[k].nchunks = select_num_chunks(obj_h, obj_w, T.t[k].level);
     T.t[k].chunk0 = c0;
     T.t[k].cnt_off = c0 * n_layers;
     c0 += T.t[k].nchunks;
+    small = small && (long long)n_layers * T.t[k].nchunks <= SEL_FUSED_MAX_TABLE;
+  }
+  if (coop && coop->bar && small && c0 <= coop->max_ctas) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(c0);
+    cfg.blockDim = dim3(CGH_SEL_CHUNK);
+    cfg.stream = st;
+    cudaLaunchAttribute attr[2];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[1].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 2;
+    const TcFlags f = fl ? *fl : TcFlags{};
+    cudaError_t e = fl ? cudaLaunchKernelEx(&cfg, k_select_fused<true>, sal, L, obj_h, obj_w, n_layers, T, chunk_cnt,
+                                            coop->bar, coop->status, f)
+                       : cudaLaunchKernelEx(&cfg, k_select_fused<false>, sal, L, obj_h, obj_w, n_layers, T, chunk_cnt,
+                                            coop->bar, coop->status, f);
+    if (e == cudaSuccess && flags_done) *flags_done = fl != nullptr;
+    return e != cudaSuccess ? e : cudaGetLastError();
   }
   cudaError_t e = launch_pdl(k_select_count, dim3(c0), dim3(CGH_SEL_CHUNK), 0, st, sal, L, obj_h, obj_w, n_layers,
                              T, chunk_cnt);
@@ -415,7 +596,7 @@ cudaError_t launch_select_tasks(int obj_h, int obj_w, int n_layers, const uint8_
 
 cudaError_t launch_select(int obj_h, int obj_w, int n_layers, const uint8_t* sal, const uint8_t* L,
                           int threshold, int level, int32_t* list, int32_t* d_count, int capacity,
-                          int* chunk_cnt, int* chunk_off, cudaStream_t st) {
+                          int* chunk_cnt, int* chunk_off, cudaStream_t st, const SelCoop* coop) {
   SelTasks T;
   memset(&T, 0, sizeof(T));
   T.n = 1;
@@ -424,7 +605,7 @@ cudaError_t launch_select(int obj_h, int obj_w, int n_layers, const uint8_t* sal
   T.t[0].capacity = capacity;
   T.t[0].list = list;
   T.t[0].count = d_count;
-  return launch_select_tasks(obj_h, obj_w, n_layers, sal, L, T, chunk_cnt, chunk_off, st);
+  return launch_select_tasks(obj_h, obj_w, n_layers, sal, L, T, chunk_cnt, chunk_off, st, coop);
 }
 
 // ---------------------------------------------------------------------------

@@ -38,6 +38,10 @@ __global__ void k_tc_scatter(const int32_t* __restrict__ l0, const int32_t* __re
       fl.colband[(size_t)z * wl + bx] = 1;
     } else {
       fl.sel[level][((size_t)z * hl + by) * wl + bx] = 1;
+      // keep the block's 8-pixel bands even when no LLL entry covers them (lists that are
+      // not nested, e.g. a truncated LLL list)
+      fl.rowband[(size_t)z * (H >> 3) + (by >> (3 - level))] = 1;
+      fl.colband[(size_t)z * (W >> 3) + (bx >> (3 - level))] = 1;
     }
   }
 }
@@ -68,7 +72,8 @@ __device__ int block_scan_flags(int f, int* s_warp, int* total) {
 }
 
 // Per layer: compacted object rows / columns in 32-pixel bands (a band is kept when one
-// of the layer's LLL blocks lies in it), entries past the object edge set to -1, and the
+// of the layer's listed blocks, LLL or detail, lies in it), entries past the object edge
+// set to -1, and the
 // band of every 32-wide K step: stage-1 A reads fringe columns 32*band directly, and the
 // stage-2 A coordinate of K step k of the concatenated layers is the fringe column
 // z*H + 32*band (kmap2).
@@ -361,21 +366,26 @@ static int stage2_splits(int tiles, int kmax_steps) {
 // Operands of both GEMM stages for one scene: selection flags, per-layer band compaction,
 // the stage-2 K-step map and the inverse-DWT operand (stage-1 B).  The A operands of both
 // stages are the plan's fringe planes (eops_get), read band by band through the K maps.
+// flags_ready: the selection flags were marked by the fused selection (tc_progressive_step)
+// instead of being derived here from the lists.
 template <bool F16>
 static int tc_prep(const cgh_plan* p, const int32_t* coef, const int32_t* const* lists, const int32_t* d_counts,
-                   cudaStream_t st) {
+                   cudaStream_t st, bool flags_ready = false, cudaEvent_t coef_ready = nullptr) {
   cgh_tc_state* t = p->tc;
   const int H = p->obj_h, W = p->obj_w, Z = p->n_layers;
-  // the flags are clear unless a call left them marked (the single-scene path clears them in
-  // its stage-1 kernel for the next call)
-  if (t->flags_dirty) TC_CK(cudaMemsetAsync(t->flags, 0, t->flags_bytes, st), "tc: clear flags");
-  t->flags_dirty = 1;
-  TC_CK(launch_pdl(k_tc_scatter, dim3(64, 4), dim3(256), 0, st, lists[0], lists[1], lists[2], lists[3], d_counts,
-                   t->fl, H, W, Z),
-        "tc: scatter");
+  if (!flags_ready) {
+    // the flags are clear unless a call left them marked (the single-scene path clears them
+    // in its stage-1 kernel for the next call)
+    if (t->flags_dirty) TC_CK(cudaMemsetAsync(t->flags, 0, t->flags_bytes, st), "tc: clear flags");
+    t->flags_dirty = 1;
+    TC_CK(launch_pdl(k_tc_scatter, dim3(64, 4), dim3(256), 0, st, lists[0], lists[1], lists[2], lists[3],
+                     d_counts, t->fl, H, W, Z),
+          "tc: scatter");
+  }
   TC_CK(launch_pdl(k_tc_compact, dim3(Z), dim3(1024), 0, st, t->fl, H, W, Z, p->contraction, t->rows, t->cols,
                    t->kr_pad, t->kc_pad, t->kr_alloc, t->kc_alloc, t->rband, t->cband, t->kmap2, t->orient),
         "tc: compact");
+  if (coef_ready) TC_CK(cudaStreamWaitEvent(st, coef_ready, 0), "tc: wait for the coefficients");
   {
     dim3 blk(8, 32), grid((t->kc_alloc / 8 + 7) / 8, (t->kr_alloc + 31) / 32, Z);
     TC_CK(launch_pdl(k_tc_idwt<F16>, grid, blk, 0, st, coef, t->fl, (const int*)t->rows, (const int*)t->cols,
@@ -439,7 +449,8 @@ static void stage2_args(const cgh_plan* p, bool f16, float2* holo, int S, TcGemm
 
 template <bool F16>
 static int tc_run(const cgh_plan* p, const int32_t* coef, const int32_t* const* lists, const int32_t* d_counts,
-                  float2* holo, int accumulate, cudaStream_t st) {
+                  float2* holo, int accumulate, cudaStream_t st, bool flags_ready = false,
+                  cudaEvent_t coef_ready = nullptr) {
   cgh_tc_state* t = p->tc;
   const CUtensorMap *mEZ, *mEZt;
   int rc = eops_get(p, F16 ? 1 : 0, &mEZ, &mEZt, st);
@@ -449,7 +460,7 @@ static int tc_run(const cgh_plan* p, const int32_t* coef, const int32_t* const* 
   const bool h_zero_in_stage1 = !accumulate && (hpix % 2 == 0) && (((uintptr_t)holo & 15) == 0);
   if (!accumulate && !h_zero_in_stage1) TC_CK(cudaMemsetAsync(holo, 0, hpix * sizeof(float2), st), "tc: clear");
   prof_mark(p, CGH_PROF_TC_PREP, 0, st);
-  rc = tc_prep<F16>(p, coef, lists, d_counts, st);
+  rc = tc_prep<F16>(p, coef, lists, d_counts, st, flags_ready, coef_ready);
   if (rc != CGH_OK) return rc;
   prof_mark(p, CGH_PROF_TC_PREP, 1, st);
   TcGemmArgs a;
@@ -678,10 +689,21 @@ static int batch_run(cgh_batch* b, cudaStream_t st) {
       T.t[k].list = b->lists[4 * i + k];
       T.t[k].count = b->counts + 8 * i + 2 * k;
     }
+    cgh_tc_state* t = p->tc;
+    if (t->flags_dirty) TC_CK(cudaMemsetAsync(t->flags, 0, t->flags_bytes, st), "batch: clear flags");
+    t->flags_dirty = 1;
+    for (int k = 0; k < 4; ++k) T.t[k].flag_kind = k == 0 ? SEL_FLAGS_LLL : SEL_FLAGS_DETAIL;
+    const SelCoop coop = plan_sel_coop(p);
+    bool done = false;
     TC_CK(launch_select_tasks(p->obj_h, p->obj_w, p->n_layers, b->S[i], b->L[i], T, p->d_chunk_cnt, p->d_chunk_off,
-                              st),
+                              st, &coop, &t->fl, &done),
           "batch: selection");
-    const int rc = tc_prep<F16>(p, b->coeffs[i], b->lists + 4 * i, b->counts + 8 * i, st);
+    if (!done)
+      TC_CK(launch_pdl(k_tc_scatter, dim3(64, 4), dim3(256), 0, st, b->lists[4 * i], b->lists[4 * i + 1],
+                       b->lists[4 * i + 2], b->lists[4 * i + 3], (const int32_t*)(b->counts + 8 * i), t->fl,
+                       p->obj_h, p->obj_w, p->n_layers),
+            "batch: scatter");
+    const int rc = tc_prep<F16>(p, b->coeffs[i], b->lists + 4 * i, b->counts + 8 * i, st, true);
     if (rc != CGH_OK) return rc;
     TC_CK(cudaMemsetAsync(b->H[i], 0, (size_t)p->holo_h * p->holo_w * sizeof(float2), st), "batch: clear");
   }
@@ -722,6 +744,34 @@ int tc_progressive(const cgh_plan* p, const int32_t* coef, const int32_t* const*
   if (rc != CGH_OK) return rc;
   if (form == CGH_FORM_TC_FP16X3) return tc_run<true>(p, coef, lists, d_counts, holo, accumulate, st);
   return tc_run<false>(p, coef, lists, d_counts, holo, accumulate, st);
+}
+
+// Selection and superposition in one call: the fused selection writes the lists and marks
+// the selection flags itself when its tables are small (else the flags come from the lists).
+int tc_progressive_step(const cgh_plan* p, const uint8_t* sal, const uint8_t* L, const int32_t* coef,
+                        cudaEvent_t coef_ready, SelTasks T, const int32_t* const* lists, const int32_t* d_counts,
+                        float2* holo, int accumulate, int form, cudaStream_t st) {
+  if (p->obj_h > 8192 || p->obj_w > 8192)
+    return cgh_fail(CGH_ERR_UNSUPPORTED, "tensor-core form: object too large");
+  int rc = tc_ensure(p);
+  if (rc != CGH_OK) return rc;
+  cgh_tc_state* t = p->tc;
+  if (t->flags_dirty) TC_CK(cudaMemsetAsync(t->flags, 0, t->flags_bytes, st), "tc: clear flags");
+  t->flags_dirty = 1;
+  for (int k = 0; k < T.n; ++k) T.t[k].flag_kind = k == 0 ? SEL_FLAGS_LLL : SEL_FLAGS_DETAIL;
+  const SelCoop coop = plan_sel_coop(p);
+  bool done = false;
+  prof_mark(p, CGH_PROF_SELECT, 0, st);
+  TC_CK(launch_select_tasks(p->obj_h, p->obj_w, p->n_layers, sal, L, T, p->d_chunk_cnt, p->d_chunk_off, st, &coop,
+                            &t->fl, &done),
+        "tc: selection");
+  prof_mark(p, CGH_PROF_SELECT, 1, st);
+  if (!done)
+    TC_CK(launch_pdl(k_tc_scatter, dim3(64, 4), dim3(256), 0, st, lists[0], lists[1], lists[2], lists[3], d_counts,
+                     t->fl, p->obj_h, p->obj_w, p->n_layers),
+          "tc: scatter");
+  if (form == CGH_FORM_TC_FP16X3) return tc_run<true>(p, coef, lists, d_counts, holo, accumulate, st, true, coef_ready);
+  return tc_run<false>(p, coef, lists, d_counts, holo, accumulate, st, true, coef_ready);
 }
 
 int tc_build_flags(const cgh_plan* p, const int32_t* const* lists, const int32_t* d_counts, TcFlags* out,
