@@ -500,14 +500,17 @@ def run_ours(args):
                  for k in range(4)]
         holo = torch.empty((HOLO, HOLO), dtype=torch.complex64, device="cuda")
         flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
-    # fringe tables (FP64 point fringes, block tables), DWT, the four-list selection (count,
-    # scan, scatter), then the superposition: 1 kernel (direct form), or list scatter,
-    # compaction, inverse DWT and the two GEMMs (tensor forms)
-    launches_per_step = 2 + 1 + 3 + (1 if form == "direct_lut" else 5)
+    tensor_form = form != "direct_lut"
+    # fringe tables (FP64 point fringes, block tables) and the DWT, then: tensor forms, one
+    # cgh_progressive_step (the single-launch selection, which also marks the operand flags,
+    # compaction, inverse DWT, the two GEMMs); direct form, the three selection passes and
+    # the direct kernel
+    launches_per_step = 2 + 1 + (1 + 4 if tensor_form else 3 + 1)
 
     # The fringe-table build, the DWT and the block selection are independent: the first two
     # run on side streams forked from (and joined back into) the step's stream, which the
-    # CUDA graph capture records as parallel branches.
+    # CUDA graph capture records as parallel branches.  The tensor-form step waits for the DWT
+    # only before its inverse-DWT kernel (coeffs_ready), so the selection overlaps the DWT.
     s_tab, s_dwt = torch.cuda.Stream(), torch.cuda.Stream()
 
     def step():
@@ -517,10 +520,16 @@ def run_ours(args):
         s_dwt.wait_event(fork)
         plan.build_tables(stream=s_tab)
         plan.haar_decompose(I, L, coeffs, stream=s_dwt)
-        plan.progressive_lists(S, L, scenes.THRESHOLDS_U8, counts=counts, lists=lists, stream=stream)
         j1, j2 = torch.cuda.Event(), torch.cuda.Event()
-        j1.record(s_tab)
         j2.record(s_dwt)
+        if tensor_form:
+            plan.progressive_step(S, L, coeffs, scenes.THRESHOLDS_U8, counts=counts, lists=lists, holo=holo,
+                                  form=form, coeffs_ready=j2, stream=stream)
+            j1.record(s_tab)
+            stream.wait_event(j1)
+            return
+        plan.progressive_lists(S, L, scenes.THRESHOLDS_U8, counts=counts, lists=lists, stream=stream)
+        j1.record(s_tab)
         stream.wait_event(j1)
         stream.wait_event(j2)
         plan.progressive_hologram(coeffs, lists, counts, holo=holo, form=form, stream=stream)

@@ -708,14 +708,19 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm(const __grid_constant__ CUte
   __shared__ volatile int s_abort;
   __shared__ int s_off[CGH_MAX_LAYERS + 1];
   __shared__ int s_toff[CGH_MAX_LAYERS + 1];
+  __shared__ int s_kr[CGH_MAX_LAYERS];
   pdl_wait();
+  // the per-layer sizes, loaded in parallel (a serial loop of global loads in thread 0
+  // would cost a memory latency per layer before any role starts)
+  if (args.kr_pad && threadIdx.x < args.n_layers) s_kr[threadIdx.x] = args.kr_pad[threadIdx.x];
+  __syncthreads();
   if (threadIdx.x == 0) {
     int o = 0, u = 0;
     s_off[0] = 0;
     s_toff[0] = 0;
     if (args.kr_pad)
       for (int q = 0; q < args.n_layers; ++q) {
-        const int kr = args.kr_pad[q];
+        const int kr = s_kr[q];
         s_off[q + 1] = (o += kr);
         s_toff[q + 1] = (u += args.tm * ((kr + TC_BN - 1) / TC_BN));
       }

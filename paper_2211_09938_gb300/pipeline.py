@@ -5,7 +5,8 @@ memory), taken through the whole progressive path (fringe tables, Haar DWT, bloc
 selection, superposition; Section 2 steps 1-5) and copied back out.  The device buffers
 come in `depth` slots used round robin: while one slot's hologram is copied out on the
 copy stream, the next slot's inputs are copied in and its step runs on the compute
-stream.  Each slot's step is one captured CUDA graph.  Every kernel is the library's;
+stream.  Each slot's step is one captured CUDA graph; for the tensor forms the selection
+and superposition inside it are one cgh_progressive_step.  Every kernel is the library's;
 this module only orders copies and graph replays with events.
 """
 import torch
@@ -61,7 +62,9 @@ class ProgressivePipeline:
 
     def _step(self, sl):
         """The whole path on one slot: tables and DWT on side streams forked from the
-        compute stream, the selection on it, then the superposition after the join."""
+        compute stream, the selection on it, then the superposition.  The tensor forms run
+        selection and superposition as one cgh_progressive_step, which waits for the DWT only
+        before it reads the coefficients; the direct form joins both side streams first."""
         st = self.compute
         s_tab, s_dwt = self.side
         fork = torch.cuda.Event()
@@ -70,10 +73,16 @@ class ProgressivePipeline:
         s_dwt.wait_event(fork)
         self.plan.build_tables(stream=s_tab)
         self.plan.haar_decompose(sl.I, sl.L, sl.coeffs, stream=s_dwt)
-        self.plan.progressive_lists(sl.S, sl.L, self.thresholds, counts=sl.counts, lists=sl.lists, stream=st)
         j1, j2 = torch.cuda.Event(), torch.cuda.Event()
-        j1.record(s_tab)
         j2.record(s_dwt)
+        if self.form != "direct_lut":
+            self.plan.progressive_step(sl.S, sl.L, sl.coeffs, self.thresholds, counts=sl.counts, lists=sl.lists,
+                                       holo=sl.holo, form=self.form, coeffs_ready=j2, stream=st)
+            j1.record(s_tab)
+            st.wait_event(j1)
+            return
+        self.plan.progressive_lists(sl.S, sl.L, self.thresholds, counts=sl.counts, lists=sl.lists, stream=st)
+        j1.record(s_tab)
         st.wait_event(j1)
         st.wait_event(j2)
         self.plan.progressive_hologram(sl.coeffs, sl.lists, sl.counts, holo=sl.holo, form=self.form, stream=st)
