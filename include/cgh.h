@@ -57,7 +57,9 @@ extern "C" {
 
 /* ---- plan --------------------------------------------------------------------------- */
 /* Plan flag: every output element is written by one CTA in a fixed order (no split-K
- * atomics), so results are bit-reproducible run to run; the split forms are faster. */
+ * atomics), so results are bit-reproducible run to run; the split forms are faster.  The
+ * unsplit FP32 accumulation chains are longer: fp16 hi+lo then reaches ~2e-5 rel-L2 on a
+ * 512x512 object with 16 layers (the split default stays below 1e-5). */
 #define CGH_PLAN_DETERMINISTIC 1
 /* Plan flag: keep Eq. 1's amplitude 1/r and carrier exp(jkr) at r = z as a per-layer factor
  * c_z = exp(j*2*pi*frac(z/lambda)) / z (the default reading drops this constant of each
