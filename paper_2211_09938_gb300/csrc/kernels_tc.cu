@@ -208,14 +208,20 @@ __global__ void k_tc_idwt(const int32_t* __restrict__ coef, TcFlags fl, const in
                           const int* __restrict__ cols, const int* __restrict__ kr_pad,
                           const int* __restrict__ kc_pad, const int* __restrict__ orient, int H, int W,
                           int ld_rows, int ld_cols, uint16_t* __restrict__ B1, long long b1_plane, int ldb1) {
+  __shared__ int s_kr[CGH_MAX_LAYERS];
   pdl_wait();
   pdl_trigger();
   const int z = blockIdx.z;
+  // the layers' row counts, loaded in parallel (a per-thread loop of loads would cost a memory
+  // latency per earlier layer)
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+  if (tid <= z) s_kr[tid] = kr_pad[tid];
+  __syncthreads();
   const int c = 8 * (blockIdx.x * blockDim.x + threadIdx.x);
   const int k = blockIdx.y * blockDim.y + threadIdx.y;
-  if (k >= kr_pad[z] || c >= kc_pad[z]) return;
+  if (k >= s_kr[z] || c >= kc_pad[z]) return;
   int off = 0;
-  for (int q = 0; q < z; ++q) off += kr_pad[q];
+  for (int q = 0; q < z; ++q) off += s_kr[q];
   const int i = rows[(size_t)z * ld_rows + k], j0 = cols[(size_t)z * ld_cols + c];
   int V[8];
 #pragma unroll

@@ -289,3 +289,25 @@ def test_select_many_scan_blocks(torch_cuda):
         for k in range(4):
             assert c[k, 0] == c[k, 1] == len(ref_lists[k]), k
             assert np.array_equal(lists[k][:c[k, 0]].cpu().numpy(), ref_lists[k]), k
+
+
+@pytest.mark.parametrize("n_layers", [32, 33])
+def test_select_fused_table_limit(torch_cuda, n_layers):
+    """512x512 object: 32 layers give a level-1 count table of exactly 8192 entries (the
+    single-launch selection), 33 layers one chunk column more (the three passes).  Both give
+    the oracle's lists bit for bit, through cgh_select_progressive and cgh_select_blocks."""
+    torch = torch_cuda
+    sc = scenes.random_scene(300 + n_layers, 512, 1024, n_layers, graded=True)
+    plan = plan_for(sc)
+    S, L = dev(torch, sc["saliency"]), dev(torch, sc["layer"])
+    ref_lists = O.progressive_lists(sc["saliency"], sc["layer"], n_layers, scenes.THRESHOLDS_U8)
+    lists, counts = plan.progressive_lists(S, L, scenes.THRESHOLDS_U8)
+    c = counts.cpu().numpy()
+    for k in range(4):
+        assert c[k, 0] == c[k, 1] == len(ref_lists[k]), k
+        assert np.array_equal(lists[k][:c[k, 0]].cpu().numpy(), ref_lists[k]), k
+    lst, cnt = plan.select_blocks(S, L, scenes.THRESHOLDS_U8[1], 1)
+    cc = cnt.cpu().numpy()
+    assert cc[0] == cc[1] == len(ref_lists[1])
+    assert np.array_equal(lst[:cc[0]].cpu().numpy(), ref_lists[1])
+    assert plan.status() == 0
