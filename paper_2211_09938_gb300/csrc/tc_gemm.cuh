@@ -240,11 +240,15 @@ __device__ __forceinline__ void epi_barrier() { asm volatile("bar.sync 1, 128;" 
 // Products of one 16-wide K slice.  Plane order of complex operands: re_hi, re_lo, im_hi,
 // im_lo; of real operands: hi, lo.  Accumulator 0 holds the real part (columns 0..127 of
 // the TMEM allocation), accumulator 1 the imaginary part (columns 128..255).
+// The descriptors of a stage's operand tiles differ from the stage's base descriptors only
+// in the start-address field (address >> 4, 14 bits; shared-memory offsets stay below
+// 256 KiB, so adding the tile offset >> 4 never carries out of it): one 64-bit add each,
+// which keeps the single issuing thread ahead of the tensor pipe.
 template <int KIND>
-__device__ __forceinline__ void issue_products(uint32_t tmem, uint32_t a_base, uint32_t b_base, int kk,
+__device__ __forceinline__ void issue_products(uint32_t tmem, uint64_t a_desc, uint64_t b_desc, int kk,
                                                uint32_t id_pos, uint32_t id_neg, bool first) {
-  auto A = [&](int p) { return sdesc_sw64(a_base + p * TC_PLANE_BYTES + kk * 32); };
-  auto B = [&](int p) { return sdesc_sw64(b_base + p * TC_PLANE_BYTES + kk * 32); };
+  auto A = [&](int p) { return a_desc + (uint64_t)((p * TC_PLANE_BYTES + kk * 32) >> 4); };
+  auto B = [&](int p) { return b_desc + (uint64_t)((p * TC_PLANE_BYTES + kk * 32) >> 4); };
   const uint32_t d0 = tmem, d1 = tmem + 128;
   const uint32_t f = first ? 0u : 1u;
   if (KIND == KIND_TEST) {
@@ -458,10 +462,10 @@ __device__ __forceinline__ void tc_gemm_body(const Src& src, uint8_t* smem, uint
           }
           tc_fence_after();
           const uint32_t a_base = smem_base + s * STAGE;
-          const uint32_t b_base = a_base + NA * TC_PLANE_BYTES;
+          const uint64_t a_desc = sdesc_sw64(a_base), b_desc = sdesc_sw64(a_base + NA * TC_PLANE_BYTES);
 #pragma unroll
           for (int kk = 0; kk < TC_BK / 16; ++kk)
-            issue_products<KIND>(acc, a_base, b_base, kk, id_pos, id_neg, kt == 0 && kk == 0);
+            issue_products<KIND>(acc, a_desc, b_desc, kk, id_pos, id_neg, kt == 0 && kk == 0);
           mma_commit(&empty_bar[s]);
         }
         mma_commit(&tfull_bar[buf]);
