@@ -311,3 +311,24 @@ def test_select_fused_table_limit(torch_cuda, n_layers):
     assert cc[0] == cc[1] == len(ref_lists[1])
     assert np.array_equal(lst[:cc[0]].cpu().numpy(), ref_lists[1])
     assert plan.status() == 0
+
+
+def test_select_max_object(torch_cuda):
+    """The largest object the plan accepts (8192 x 8192, 4 layers plus unassigned pixels):
+    the four lists (up to 5.8 million entries, block coordinates up to 4095) equal the
+    oracle's bit for bit; the count table takes the three-pass selection."""
+    torch = torch_cuda
+    from paper_2211_09938_gb300 import Plan
+    n, Z = 8192, 4
+    rng = np.random.default_rng(8192)
+    layer = np.repeat(np.arange(Z, dtype=np.uint8), n // Z)[:, None].repeat(n, 1)
+    layer[rng.random((n, n)) < 0.01] = 255  # pixels owned by no layer
+    sal = rng.integers(0, 256, size=(n, n), dtype=np.uint8)
+    plan = Plan((n, n), (n, n), 8e-6, 532e-9, [0.10, 0.11, 0.12, 0.13])
+    lists, counts = plan.progressive_lists(dev(torch, sal), dev(torch, layer), scenes.THRESHOLDS_U8)
+    c = counts.cpu().numpy()
+    ref = O.progressive_lists(sal, layer, Z, scenes.THRESHOLDS_U8)
+    for k in range(4):
+        assert c[k, 0] == c[k, 1] == len(ref[k]), k
+        assert np.array_equal(lists[k][:c[k, 0]].cpu().numpy(), ref[k]), k
+    assert plan.status() == 0
