@@ -128,6 +128,7 @@ class Plan:
         import torch
         self.obj_h, self.obj_w = int(obj_shape[0]), int(obj_shape[1])
         self.holo_h, self.holo_w = int(holo_shape[0]), int(holo_shape[1])
+        self.pitch, self.wavelength, self.levels, self.flags = float(pitch), float(wavelength), int(levels), int(flags)
         self.z = [float(v) for v in z]
         self.n_layers = len(self.z)
         self.device = torch.device("cuda", torch.cuda.current_device())
@@ -144,6 +145,12 @@ class Plan:
             flags |= cls.LAYER_FACTOR
         return cls(scene["intensity"].shape[-2:], scene["holo"], scene["pitch"], scene["wavelength"],
                    scene["z"], stream=stream, flags=flags)
+
+    def clone(self, stream=None):
+        """A new plan of the same geometry and flags, with its own scratch (so that two scenes
+        can be in flight at once, one per plan)."""
+        return Plan((self.obj_h, self.obj_w), (self.holo_h, self.holo_w), self.pitch, self.wavelength, self.z,
+                    levels=self.levels, stream=stream, flags=self.flags)
 
     def close(self):
         if getattr(self, "handle", None) is not None and self.handle.value:

@@ -1,6 +1,7 @@
 """The streaming pipeline: scenes submitted back to back through two device slots (copies
-overlapping compute) give exactly the holograms of the plain library calls, scene by
-scene, for both superposition forms."""
+overlapping compute; with concurrent slots, one plan and compute stream each, so that
+consecutive scenes' steps overlap) give exactly the holograms of the plain library calls,
+scene by scene, for both superposition forms."""
 import numpy as np
 import pytest
 
@@ -22,8 +23,9 @@ def torch_cuda():
     return torch
 
 
-@pytest.mark.parametrize("form,graphs", [("tc_bf16x3", True), ("direct_lut", False)])
-def test_pipeline_matches_direct_calls(torch_cuda, form, graphs):
+@pytest.mark.parametrize("form,graphs,concurrent,depth", [("tc_bf16x3", True, False, 2), ("direct_lut", False, False, 2),
+                                                           ("tc_bf16x3", True, True, 3), ("tc_fp16x3", False, True, 2)])
+def test_pipeline_matches_direct_calls(torch_cuda, form, graphs, concurrent, depth):
     torch = torch_cuda
     from paper_2211_09938_gb300 import Plan
     from paper_2211_09938_gb300.pipeline import ProgressivePipeline
@@ -31,7 +33,8 @@ def test_pipeline_matches_direct_calls(torch_cuda, form, graphs):
     plan = Plan.for_scene(base, flags=Plan.DETERMINISTIC)
     seeds = [121, 122, 123, 124, 125]
     scs = [scenes.random_scene(sd, 64, 128, 3, graded=True) for sd in seeds]
-    pipe = ProgressivePipeline(plan, scenes.THRESHOLDS_U8, form=form, graphs=graphs)
+    pipe = ProgressivePipeline(plan, scenes.THRESHOLDS_U8, form=form, depth=depth, graphs=graphs,
+                               concurrent=concurrent)
     outs = [torch.empty((128, 128), dtype=torch.complex64).pin_memory() for _ in scs]
     for sc, hH in zip(scs, outs):
         pipe.submit(torch.from_numpy(sc["intensity"]).pin_memory(), torch.from_numpy(sc["layer"]).pin_memory(),
