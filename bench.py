@@ -657,6 +657,8 @@ def run_ours(args):
         pipe.submit(hI, hL, hS, hH[k % 2])
     pipe.synchronize()
     e2e_s = (time.perf_counter() - e0) / E
+    if pipe.status() != 0:
+        raise RuntimeError("end-to-end pipeline: a bounded device wait gave up (cgh_status)")
     e2e = {"value": UNITS_PER_STEP * ws / e2e_s / 1e9, "unit": UNIT,
            "h2d_bytes_per_step": 3 * OBJ * OBJ, "d2h_bytes_per_step": 8 * HOLO * HOLO,
            "note": f"ProgressivePipeline, {E2E_DEPTH} concurrent slots (one plan and compute stream each): "

@@ -133,5 +133,12 @@ class ProgressivePipeline:
         for s in [self.copy_in, self.compute, self.copy_out] + [sl.compute for sl in self.slots]:
             s.synchronize()
 
+    def status(self):
+        """First nonzero device status word of the slots' plans (cgh_status; read and cleared),
+        else 0.  Synchronises."""
+        self.synchronize()
+        codes = [sl.plan.status() for sl in self.slots]
+        return next((c for c in codes if c), 0)
+
 
 __all__ = ["ProgressivePipeline", "Plan"]
