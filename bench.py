@@ -198,10 +198,19 @@ def cpu_baseline(budget_s=12.0):
     t1 = time.perf_counter()
     O.plain_pointwise_hologram(sc["intensity"], sc["layer"], g)
     dt_sep = time.perf_counter() - t1
+    # and in its direct FP64 sum (every object point at every pixel), on 64 seeded pixels
+    import numpy as np
+    rng = np.random.default_rng(2000)
+    pix = (rng.integers(0, HOLO, 64), rng.integers(0, HOLO, 64))
+    t2 = time.perf_counter()
+    O.plain_pointwise_hologram(sc["intensity"], sc["layer"], g, pixels=pix)
+    dt_dir = time.perf_counter() - t2
     return {"value": UNITS_PER_STEP * n / dt / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"{n} whole paper-scale scene(s), selection + residual-map hologram, {dt:.1f} s",
             "other_forms": {"pointwise_separable_fp64_ms": dt_sep * 1e3,
-                            "pointwise_separable_fp64_value": UNITS_PER_STEP / dt_sep / 1e9}}, H
+                            "pointwise_separable_fp64_value": UNITS_PER_STEP / dt_sep / 1e9,
+                            "pointwise_direct_fp64_value": OBJ * OBJ * 64 / dt_dir / 1e9,
+                            "pointwise_direct_fp64_sample": f"64 seeded hologram pixels, {dt_dir:.1f} s"}}, H
 
 
 # ---------------------------------------------------------------------------------------
