@@ -225,8 +225,7 @@ int cgh_select_progressive(const cgh_plan* plan, const uint8_t* saliency, const 
  *            + sum_{l=1..3} sum_{level-l list} 4^-l (X b_l(m-u) w_l(n-v)
  *                                               + Y w_l(m-u) b_l(n-v) + D w_l(m-u) w_l(n-v)) ]
  *   with u = s*2^l*by, v = s*2^l*bx for a block (z, by, bx) of level l.
- *   coeffs    int32 [Z][obj_h][obj_w] from cgh_haar_decompose (16-byte aligned for the
- *             tensor-core forms, which read the level-1 cells as 16-byte vectors)
+ *   coeffs    int32 [Z][obj_h][obj_w] from cgh_haar_decompose
  *   lists     HOST array of 4 device pointers: lists[0] = LLL list (level-3 blocks),
  *             lists[l] = level-l detail list, l = 1..3 (format of cgh_select_blocks)
  *   d_counts  int32 [4][2] device array, d_counts[2k] = entries in lists[k] (the

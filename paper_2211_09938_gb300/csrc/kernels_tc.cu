@@ -142,58 +142,72 @@ __global__ void __launch_bounds__(1024) k_tc_compact(TcFlags fl, int H, int W, i
   }
 }
 
-// Stage-1 B operand, one thread per 8 x 8 pixel block of one layer: 64 x A^_z, the inverse
-// Haar DWT of the block's LLL value and selected details,
-//   V = LLL + sum_{l=3,2,1} 4^(3-l) [selected] (sx X + sy Y + sx sy D),
-// with sx = -1 for the right child column and sy = -1 for the lower child row of the level-l
-// cell.  All 64 coefficients of the block (LLL, the level-3 X, Y, D, their 2 x 2 level-2 and
-// 4 x 4 level-1 cells) and its flags are fetched in one round of independent vector loads
-// (unselected cells are loaded and masked), then the block is formed in registers and written
-// as 8 compacted rows of 8 compacted columns: rows[k] x cols[c], or, in the transposed order,
-// the block's columns as rows (the "rows" then hold object columns).  Blocks never straddle a
-// kept 32-pixel band, so 8 consecutive compacted rows (columns) are 8 consecutive object rows
-// (columns), or padding (-1) past the object edge.
-template <bool F16, bool TR>
-__device__ __forceinline__ void idwt_block_store(const int (&LL)[1], const int (&d3)[3], const int (&d2)[2][2][3],
-                                                 const int (&d1)[4][4][3], uint16_t* dst, long long b1_plane,
-                                                 int ldb1) {
+// 64 x A^_z at eight consecutive pixels of one object row (ALONG_Y = false: (y0, x0 + q))
+// or one object column (ALONG_Y = true: (y0 + q, x0)), the run starting on a multiple of 8,
+// from the Haar coefficients and the selection flags:
+// V = LLL + sum_{l=3,2,1} 4^(3-l) [selected] (sx X + sy Y + sx sy D), with sx = -1 for the
+// right child column and sy = -1 for the lower child row of the level-l cell.  The run
+// shares one LLL block and one level-3 block, and spans two level-2 and four level-1 blocks.
+template <bool ALONG_Y>
+__device__ __forceinline__ void idwt_run8(const int32_t* __restrict__ P, const TcFlags& fl, int z, int H, int W,
+                                          int y0, int x0, int* V) {
+  const int h3 = H >> 3, w3 = W >> 3, by3 = y0 >> 3, bx3 = x0 >> 3;
+  const size_t f3 = ((size_t)z * h3 + by3) * w3 + bx3;
+  if (fl.occ3[f3]) {
+    const int LL = P[(size_t)by3 * W + bx3];
 #pragma unroll
-  for (int o = 0; o < 8; ++o) {
-    uint32_t hi[4], lo[4];
+    for (int q = 0; q < 8; ++q) V[q] = LL;
+  }
+  if (fl.sel[3][f3]) {
+    const int X = P[(size_t)by3 * W + w3 + bx3], Y = P[(size_t)(h3 + by3) * W + bx3],
+              D = P[(size_t)(h3 + by3) * W + w3 + bx3];
 #pragma unroll
-    for (int p = 0; p < 8; p += 2) {
-      uint16_t h[2], l[2];
-#pragma unroll
-      for (int e = 0; e < 2; ++e) {
-        const int yy = TR ? p + e : o, xx = TR ? o : p + e;
-        const int s3x = (xx & 4) ? -1 : 1, s3y = (yy & 4) ? -1 : 1;
-        const int s2x = (xx & 2) ? -1 : 1, s2y = (yy & 2) ? -1 : 1;
-        const int s1x = (xx & 1) ? -1 : 1, s1y = (yy & 1) ? -1 : 1;
-        const int* c2 = d2[yy >> 2][xx >> 2];
-        const int* c1 = d1[yy >> 1][xx >> 1];
-        const int v = LL[0] + s3x * d3[0] + s3y * d3[1] + s3x * s3y * d3[2] +
-                      4 * (s2x * c2[0] + s2y * c2[1] + s2x * s2y * c2[2]) +
-                      16 * (s1x * c1[0] + s1y * c1[1] + s1x * s1y * c1[2]);
-        split_hi_lo<F16>((float)v, h[e], l[e]);
-      }
-      hi[p / 2] = (uint32_t)h[0] | ((uint32_t)h[1] << 16);
-      lo[p / 2] = (uint32_t)l[0] | ((uint32_t)l[1] << 16);
+    for (int q = 0; q < 8; ++q) {
+      const int y = ALONG_Y ? y0 + q : y0, x = ALONG_Y ? x0 : x0 + q;
+      const int sx = ((x >> 2) & 1) ? -1 : 1, sy = ((y >> 2) & 1) ? -1 : 1;
+      V[q] += sx * X + sy * Y + sx * sy * D;
     }
-    uint16_t* row = dst + (size_t)o * ldb1;
-    *reinterpret_cast<uint4*>(row) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
-    *reinterpret_cast<uint4*>(row + b1_plane) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+  }
+  const int h2 = H >> 2, w2 = W >> 2;
+#pragma unroll
+  for (int g = 0; g < 2; ++g) {
+    const int by2 = ALONG_Y ? (y0 >> 2) + g : y0 >> 2, bx2 = ALONG_Y ? x0 >> 2 : (x0 >> 2) + g;
+    if (fl.sel[2][((size_t)z * h2 + by2) * w2 + bx2]) {
+      const int X = P[(size_t)by2 * W + w2 + bx2], Y = P[(size_t)(h2 + by2) * W + bx2],
+                D = P[(size_t)(h2 + by2) * W + w2 + bx2];
+#pragma unroll
+      for (int q = 4 * g; q < 4 * g + 4; ++q) {
+        const int y = ALONG_Y ? y0 + q : y0, x = ALONG_Y ? x0 : x0 + q;
+        const int sx = ((x >> 1) & 1) ? -1 : 1, sy = ((y >> 1) & 1) ? -1 : 1;
+        V[q] += 4 * (sx * X + sy * Y + sx * sy * D);
+      }
+    }
+  }
+  const int h1 = H >> 1, w1 = W >> 1;
+#pragma unroll
+  for (int g = 0; g < 4; ++g) {
+    const int by1 = ALONG_Y ? (y0 >> 1) + g : y0 >> 1, bx1 = ALONG_Y ? x0 >> 1 : (x0 >> 1) + g;
+    if (fl.sel[1][((size_t)z * h1 + by1) * w1 + bx1]) {
+      const int X = P[(size_t)by1 * W + w1 + bx1], Y = P[(size_t)(h1 + by1) * W + bx1],
+                D = P[(size_t)(h1 + by1) * W + w1 + bx1];
+#pragma unroll
+      for (int q = 2 * g; q < 2 * g + 2; ++q) {
+        const int y = ALONG_Y ? y0 + q : y0, x = ALONG_Y ? x0 : x0 + q;
+        const int sx = (x & 1) ? -1 : 1, sy = (y & 1) ? -1 : 1;
+        V[q] += 16 * (sx * X + sy * Y + sx * sy * D);
+      }
+    }
   }
 }
 
-// Threads (32, 4): x = 8-column group of the compacted columns, y = 8-row group of the
-// compacted rows; grid z = layer.
+// Stage-1 B operand: 64 x A^_z at (rows[k], cols[c .. c+7]), or, in the transposed order,
+// at (cols[c .. c+7], rows[k]) (the "rows" then hold object columns).  One thread builds the
+// eight compacted columns of one 8-pixel band (or of padding).
 template <bool F16>
-__global__ void __launch_bounds__(128) k_tc_idwt(const int32_t* __restrict__ coef, TcFlags fl,
-                                                 const int* __restrict__ rows, const int* __restrict__ cols,
-                                                 const int* __restrict__ kr_pad, const int* __restrict__ kc_pad,
-                                                 const int* __restrict__ orient, int H, int W, int ld_rows,
-                                                 int ld_cols, uint16_t* __restrict__ B1, long long b1_plane,
-                                                 int ldb1) {
+__global__ void k_tc_idwt(const int32_t* __restrict__ coef, TcFlags fl, const int* __restrict__ rows,
+                          const int* __restrict__ cols, const int* __restrict__ kr_pad,
+                          const int* __restrict__ kc_pad, const int* __restrict__ orient, int H, int W,
+                          int ld_rows, int ld_cols, uint16_t* __restrict__ B1, long long b1_plane, int ldb1) {
   __shared__ int s_kr[CGH_MAX_LAYERS];
   pdl_wait();
   pdl_trigger();
@@ -203,91 +217,34 @@ __global__ void __launch_bounds__(128) k_tc_idwt(const int32_t* __restrict__ coe
   const int tid = threadIdx.y * blockDim.x + threadIdx.x;
   if (tid <= z) s_kr[tid] = kr_pad[tid];
   __syncthreads();
-  const int c8 = blockIdx.x * blockDim.x + threadIdx.x, k8 = blockIdx.y * blockDim.y + threadIdx.y;
-  if (8 * k8 >= s_kr[z] || 8 * c8 >= kc_pad[z]) return;
+  const int c = 8 * (blockIdx.x * blockDim.x + threadIdx.x);
+  const int k = blockIdx.y * blockDim.y + threadIdx.y;
+  if (k >= s_kr[z] || c >= kc_pad[z]) return;
   int off = 0;
   for (int q = 0; q < z; ++q) off += s_kr[q];
-  const int tr = *orient;
-  const int r0 = rows[(size_t)z * ld_rows + 8 * k8], q0 = cols[(size_t)z * ld_cols + 8 * c8];
-  int LL[1] = {0}, d3[3] = {0, 0, 0}, d2[2][2][3], d1[4][4][3];
+  const int i = rows[(size_t)z * ld_rows + k], j0 = cols[(size_t)z * ld_cols + c];
+  int V[8];
 #pragma unroll
-  for (int a = 0; a < 2; ++a)
-#pragma unroll
-    for (int b = 0; b < 2; ++b) d2[a][b][0] = d2[a][b][1] = d2[a][b][2] = 0;
-#pragma unroll
-  for (int a = 0; a < 4; ++a)
-#pragma unroll
-    for (int b = 0; b < 4; ++b) d1[a][b][0] = d1[a][b][1] = d1[a][b][2] = 0;
-  if (r0 >= 0 && q0 >= 0) {
-    const int y0 = tr ? q0 : r0, x0 = tr ? r0 : q0;  // the block's object origin
-    const int h3 = H >> 3, w3 = W >> 3, h2 = H >> 2, w2 = W >> 2, h1 = H >> 1, w1 = W >> 1;
-    const int by3 = y0 >> 3, bx3 = x0 >> 3;
+  for (int q = 0; q < 8; ++q) V[q] = 0;
+  if (i >= 0 && j0 >= 0) {
     const int32_t* P = coef + (size_t)z * H * W;
-    // flags: bytes for the level-3 cell, 2 bytes per level-2 row, 4 per level-1 row (the
-    // flag sections start on 16 bytes and the rows' offsets are multiples of 2 and 4)
-    const size_t f3 = ((size_t)z * h3 + by3) * w3 + bx3;
-    const int o3 = fl.occ3[f3], s3 = fl.sel[3][f3];
-    unsigned short f2[2];
-    unsigned int f1[4];
-#pragma unroll
-    for (int g = 0; g < 2; ++g)
-      f2[g] = *reinterpret_cast<const unsigned short*>(fl.sel[2] + ((size_t)z * h2 + 2 * by3 + g) * w2 + 2 * bx3);
-#pragma unroll
-    for (int g = 0; g < 4; ++g)
-      f1[g] = *reinterpret_cast<const unsigned int*>(fl.sel[1] + ((size_t)z * h1 + 4 * by3 + g) * w1 + 4 * bx3);
-    // coefficients: scalars at level 3, pairs at level 2, quadruples at level 1 (row starts
-    // on multiples of 8 elements, Mallat quadrants at multiples of W / 4 and W / 2)
-    const int ll = P[(size_t)by3 * W + bx3];
-    const int x3 = P[(size_t)by3 * W + w3 + bx3], y3 = P[(size_t)(h3 + by3) * W + bx3],
-              dd3 = P[(size_t)(h3 + by3) * W + w3 + bx3];
-    int2 c2[2][3];
-#pragma unroll
-    for (int g = 0; g < 2; ++g) {
-      const size_t r = (size_t)(2 * by3 + g) * W, rh = (size_t)(h2 + 2 * by3 + g) * W;
-      c2[g][0] = *reinterpret_cast<const int2*>(P + r + w2 + 2 * bx3);
-      c2[g][1] = *reinterpret_cast<const int2*>(P + rh + 2 * bx3);
-      c2[g][2] = *reinterpret_cast<const int2*>(P + rh + w2 + 2 * bx3);
-    }
-    int4 c1[4][3];
-#pragma unroll
-    for (int g = 0; g < 4; ++g) {
-      const size_t r = (size_t)(4 * by3 + g) * W, rh = (size_t)(h1 + 4 * by3 + g) * W;
-      c1[g][0] = *reinterpret_cast<const int4*>(P + r + w1 + 4 * bx3);
-      c1[g][1] = *reinterpret_cast<const int4*>(P + rh + 4 * bx3);
-      c1[g][2] = *reinterpret_cast<const int4*>(P + rh + w1 + 4 * bx3);
-    }
-    LL[0] = o3 ? ll : 0;
-    if (s3) {
-      d3[0] = x3;
-      d3[1] = y3;
-      d3[2] = dd3;
-    }
-#pragma unroll
-    for (int g = 0; g < 2; ++g)
-#pragma unroll
-      for (int e = 0; e < 2; ++e)
-        if ((f2[g] >> (8 * e)) & 0xff) {
-          d2[g][e][0] = e ? c2[g][0].y : c2[g][0].x;
-          d2[g][e][1] = e ? c2[g][1].y : c2[g][1].x;
-          d2[g][e][2] = e ? c2[g][2].y : c2[g][2].x;
-        }
-#pragma unroll
-    for (int g = 0; g < 4; ++g)
-#pragma unroll
-      for (int e = 0; e < 4; ++e)
-        if ((f1[g] >> (8 * e)) & 0xff) {
-#pragma unroll
-          for (int q = 0; q < 3; ++q) {
-            const int4 v = c1[g][q];
-            d1[g][e][q] = e == 0 ? v.x : e == 1 ? v.y : e == 2 ? v.z : v.w;
-          }
-        }
+    if (*orient)
+      idwt_run8<true>(P, fl, z, H, W, j0, i, V);
+    else
+      idwt_run8<false>(P, fl, z, H, W, i, j0, V);
   }
-  uint16_t* dst = B1 + (size_t)(off + 8 * k8) * ldb1 + 8 * c8;
-  if (tr)
-    idwt_block_store<F16, true>(LL, d3, d2, d1, dst, b1_plane, ldb1);
-  else
-    idwt_block_store<F16, false>(LL, d3, d2, d1, dst, b1_plane, ldb1);
+  uint32_t hi[4], lo[4];
+#pragma unroll
+  for (int q = 0; q < 8; q += 2) {
+    uint16_t h0, l0, h1v, l1v;
+    split_hi_lo<F16>((float)V[q], h0, l0);
+    split_hi_lo<F16>((float)V[q + 1], h1v, l1v);
+    hi[q / 2] = (uint32_t)h0 | ((uint32_t)h1v << 16);
+    lo[q / 2] = (uint32_t)l0 | ((uint32_t)l1v << 16);
+  }
+  uint16_t* dst = B1 + (size_t)(off + k) * ldb1 + c;
+  *reinterpret_cast<uint4*>(dst) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+  *reinterpret_cast<uint4*>(dst + b1_plane) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
 }
 
 // Shared-memory opt-in of every GEMM instantiation on the current device; called outside
@@ -330,11 +287,7 @@ static int tc_ensure(const cgh_plan* pc) {
   t->ktot_alloc = Z * t->kr_alloc;
   const size_t n3 = (size_t)Z * (H >> 3) * (W >> 3);
   const size_t sz_sel[4] = {0, (size_t)Z * (H >> 1) * (W >> 1), (size_t)Z * (H >> 2) * (W >> 2), n3};
-  // every section starts on 16 bytes (the operand kernel reads the detail flags as vectors)
-  auto a16 = [](size_t x) { return (x + 15) & ~(size_t)15; };
-  const size_t o_row = a16(n3), o_col = o_row + a16((size_t)Z * (H >> 3)), o_s1 = o_col + a16((size_t)Z * (W >> 3));
-  const size_t o_s2 = o_s1 + a16(sz_sel[1]), o_s3 = o_s2 + a16(sz_sel[2]);
-  t->flags_bytes = o_s3 + sz_sel[3];
+  t->flags_bytes = n3 + (size_t)Z * (H >> 3) + (size_t)Z * (W >> 3) + sz_sel[1] + sz_sel[2] + sz_sel[3];
   int rc = CGH_OK;
 #define TC_TRY(expr, what)                  \
   do {                                      \
@@ -345,12 +298,12 @@ static int tc_ensure(const cgh_plan* pc) {
   TC_TRY(cudaMalloc(&t->flags, t->flags_alloc), "tensor-core scratch: flags");
   TC_TRY(cudaMemset(t->flags, 0, t->flags_alloc), "tensor-core scratch: flags");
   t->fl.occ3 = t->flags;
-  t->fl.rowband = t->flags + o_row;
-  t->fl.colband = t->flags + o_col;
+  t->fl.rowband = t->fl.occ3 + n3;
+  t->fl.colband = t->fl.rowband + (size_t)Z * (H >> 3);
   t->fl.sel[0] = nullptr;
-  t->fl.sel[1] = t->flags + o_s1;
-  t->fl.sel[2] = t->flags + o_s2;
-  t->fl.sel[3] = t->flags + o_s3;
+  t->fl.sel[1] = t->fl.colband + (size_t)Z * (W >> 3);
+  t->fl.sel[2] = t->fl.sel[1] + sz_sel[1];
+  t->fl.sel[3] = t->fl.sel[2] + sz_sel[2];
   TC_TRY(cudaMalloc(&t->rows, (size_t)Z * t->kr_alloc * sizeof(int)), "tensor-core scratch: rows");
   TC_TRY(cudaMalloc(&t->cols, (size_t)Z * t->kc_alloc * sizeof(int)), "tensor-core scratch: cols");
   TC_TRY(cudaMalloc(&t->kr_pad, CGH_MAX_LAYERS * sizeof(int)), "tensor-core scratch: kr");
@@ -440,7 +393,7 @@ static int tc_prep(const cgh_plan* p, const int32_t* coef, const int32_t* const*
         "tc: compact");
   if (coef_ready) TC_CK(cudaStreamWaitEvent(st, coef_ready, 0), "tc: wait for the coefficients");
   {
-    dim3 blk(32, 4), grid((t->kc_alloc / 8 + 31) / 32, (t->kr_alloc / 8 + 3) / 4, Z);
+    dim3 blk(8, 32), grid((t->kc_alloc / 8 + 7) / 8, (t->kr_alloc + 31) / 32, Z);
     TC_CK(launch_pdl(k_tc_idwt<F16>, grid, blk, 0, st, coef, t->fl, (const int*)t->rows, (const int*)t->cols,
                      (const int*)t->kr_pad, (const int*)t->kc_pad, (const int*)t->orient, H, W, t->kr_alloc,
                      t->kc_alloc, t->B1, t->b1_plane, t->kc_alloc),
