@@ -63,5 +63,7 @@ def test_host_argument_checks_without_gpu(L):
     assert L.cgh_haar_decompose(None, None, None, None, None) == 1
     assert L.cgh_select_blocks(None, None, None, -1, 1, None, None, 0, None) == 1
     assert L.cgh_progressive_hologram(None, None, None, None, None, 0, 0, None) == 1
+    assert L.cgh_progressive_step(None, None, None, None, None, None, None, None, None, None, 0, 1, None) == 1
+    assert b"cgh_progressive_step" in L.cgh_last_error()
     assert L.cgh_plan_destroy(None) == 0
     assert L.cgh_version() >= 10000
