@@ -303,6 +303,30 @@ def test_arbitrary_mask_residual_form_equals_pointwise_of_progressive_object():
     assert O.rel_l2(H, Href) < 1e-11
 
 
+def test_lists_that_are_not_nested():
+    """P5 for lists that are not nested (detail blocks without their LLL block, e.g. a
+    truncated LLL list): the residual-map form still equals the point-wise hologram of the
+    progressive object, and the hologram is additive over any split of the entries.
+    Catches a superposition that drops (or needs) the LLL block under a detail block."""
+    n = 32
+    sc = scenes.random_scene(14, n, 2 * n, 3, graded=True)
+    g = O.geometry_of(sc)
+    full = O.progressive_lists(sc["saliency"], sc["layer"], 3, scenes.THRESHOLDS_U8)
+    assert all(len(x) for x in full)
+    part_a = [full[0][: len(full[0]) // 3], full[1][::2], full[2][1::2], full[3]]
+    part_b = [full[0][len(full[0]) // 3:], full[1][1::2], full[2][::2], np.zeros(0, np.int32)]
+    Ha = O.progressive_hologram(sc["intensity"], sc["layer"], part_a, g)
+    Ahat = O.progressive_object(sc["intensity"], sc["layer"], part_a, 3) / 64.0
+    assert O.rel_l2(Ha, O.pointwise_hologram_separable(Ahat, g)) < 1e-11
+    Hb = O.progressive_hologram(sc["intensity"], sc["layer"], part_b, g)
+    H = O.progressive_hologram(sc["intensity"], sc["layer"], full, g)
+    assert O.rel_l2(Ha + Hb, H) < 1e-12
+    # detail blocks alone: the object is their residual only (zero block mean)
+    details = [np.zeros(0, np.int32), full[1], full[2], full[3]]
+    Ad = O.progressive_object(sc["intensity"], sc["layer"], details, 3)
+    assert np.all(Ad.reshape(3, n // 8, 8, n // 8, 8).sum(axis=(2, 4)) == 0)
+
+
 def test_progressive_object_extremes():
     rng = np.random.default_rng(2)
     I = rng.integers(0, 256, size=(16, 16))
