@@ -206,7 +206,8 @@ def cpu_baseline(budget_s=12.0):
     O.plain_pointwise_hologram(sc["intensity"], sc["layer"], g, pixels=pix)
     dt_dir = time.perf_counter() - t2
     return {"value": UNITS_PER_STEP * n / dt / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{n} whole paper-scale scene(s), selection + residual-map hologram, {dt:.1f} s",
+            "sample": f"{n} whole paper-scale scene(s), selection + residual-map hologram, {dt:.1f} s "
+                      f"(numpy: matrix products on the BLAS pool of {cores} threads, fringe evaluation on one)",
             "other_forms": {"pointwise_separable_fp64_ms": dt_sep * 1e3,
                             "pointwise_separable_fp64_value": UNITS_PER_STEP / dt_sep / 1e9,
                             "pointwise_direct_fp64_value": OBJ * OBJ * 64 / dt_dir / 1e9,
