@@ -253,11 +253,10 @@ int cgh_progressive_hologram(const cgh_plan* plan, const int32_t* coeffs,
  *   coeffs_ready  a cudaEvent_t or NULL: when given, `stream` waits for it after the
  *                 selection and before coeffs is first read, so that a DWT running on
  *                 another stream overlaps the selection
- * For the tensor-core forms,
- * when the selection's count tables are small (at most 8192 per-layer chunk counts per
- * list and a grid the device holds at once, e.g. a 512x512 object with 16 layers), the
- * selection runs as one cooperative launch with a single grid barrier and marks the
- * operands' selection flags itself, so the lists are not read back.  Its wait is bounded:
+ * For the tensor-core forms, when the selection's count tables are small (at most 8192
+ * per-layer chunk counts per list and a grid the device holds at once, e.g. a 512x512
+ * object with 16 layers), the selection runs as one cooperative launch with a single grid
+ * barrier and marks the operands' selection flags itself, so the lists are not read back.  Its wait is bounded:
  * on timeout it records CGH_ERR_TIMEOUT in the status word (cgh_status); the plan's
  * barrier state is then undefined and the plan must be destroyed.  Uses plan scratch.
  * Errors: CGH_ERR_ARG, CGH_ERR_UNSUPPORTED (form), CGH_ERR_CUDA.
