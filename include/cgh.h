@@ -54,6 +54,12 @@ extern "C" {
  * FP32 accumulation in tensor memory.                                                */
 #define CGH_FORM_TC_BF16X3 1   /* bf16 hi+lo                                            */
 #define CGH_FORM_TC_FP16X3 2   /* fp16 hi+lo                                            */
+/* The same separable form with the fringe operand rounded once to fp16 (its hi planes
+ * only) and the data operand fp16 hi+lo: two products per real product instead of three,
+ * a third fewer MMAs and operand bytes.  The fringe's own fp16 rounding (2^-12) then bounds
+ * the error (a few 1e-4 rel-L2, against 1e-3 for the split paths).  Single scenes only
+ * (cgh_batch_* take the two forms above).                                              */
+#define CGH_FORM_TC_FP16X2 3
 
 /* ---- plan --------------------------------------------------------------------------- */
 /* Plan flag: every output element is written by one CTA in a fixed order (no split-K

@@ -26,7 +26,9 @@ CGH_ERR_NOMEM = 5
 FORM_DIRECT_LUT = 0
 FORM_TC_BF16X3 = 1
 FORM_TC_FP16X3 = 2
-FORMS = {"direct_lut": FORM_DIRECT_LUT, "tc_bf16x3": FORM_TC_BF16X3, "tc_fp16x3": FORM_TC_FP16X3}
+FORM_TC_FP16X2 = 3
+FORMS = {"direct_lut": FORM_DIRECT_LUT, "tc_bf16x3": FORM_TC_BF16X3, "tc_fp16x3": FORM_TC_FP16X3,
+         "tc_fp16x2": FORM_TC_FP16X2}
 
 # Every symbol include/cgh.h declares, with (restype, argtypes).
 _P = ctypes.c_void_p

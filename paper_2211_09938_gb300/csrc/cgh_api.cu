@@ -290,7 +290,7 @@ int cgh_progressive_step(const cgh_plan* p, const uint8_t* saliency, const uint8
   int rc = progressive_tasks(thresholds, lists, capacities, d_counts, &T, "cgh_progressive_step");
   if (rc != CGH_OK) return rc;
   cudaStream_t st = (cudaStream_t)stream;
-  if (form == CGH_FORM_TC_BF16X3 || form == CGH_FORM_TC_FP16X3)
+  if (form == CGH_FORM_TC_BF16X3 || form == CGH_FORM_TC_FP16X3 || form == CGH_FORM_TC_FP16X2)
     return tc_progressive_step(p, saliency, layer_idx, coeffs, (cudaEvent_t)coeffs_ready, T, lists, d_counts,
                                (float2*)holo, accumulate, form, st);
   if (form != CGH_FORM_DIRECT_LUT) return cgh_fail(CGH_ERR_UNSUPPORTED, "cgh_progressive_step: unknown form %d", form);
@@ -319,7 +319,7 @@ int cgh_progressive_hologram(const cgh_plan* p, const int32_t* coeffs, const int
     prof_mark(p, CGH_PROF_DIRECT_LUT, 1, st);
     return CGH_OK;
   }
-  if (form == CGH_FORM_TC_BF16X3 || form == CGH_FORM_TC_FP16X3)
+  if (form == CGH_FORM_TC_BF16X3 || form == CGH_FORM_TC_FP16X3 || form == CGH_FORM_TC_FP16X2)
     return tc_progressive(p, coeffs, lists, d_counts, (float2*)holo, accumulate, form, st);
   return cgh_fail(CGH_ERR_UNSUPPORTED, "cgh_progressive_hologram: unknown form %d", form);
 }

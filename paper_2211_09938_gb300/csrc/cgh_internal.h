@@ -183,6 +183,9 @@ void field_destroy(cgh_plan* p);
 struct CUtensorMap_st;
 int eops_get(const cgh_plan* p, int f16, const struct CUtensorMap_st** mEZ, const struct CUtensorMap_st** mEZt,
              cudaStream_t st);
+// The fringe planes' hi parts only (re_hi, im_hi), as maps over the same memory.
+int eops_get_hi(const cgh_plan* p, int f16, const struct CUtensorMap_st** mEZh,
+                const struct CUtensorMap_st** mEZth, cudaStream_t st);
 void eops_destroy(cgh_plan* p);
 
 // Angular-spectrum reconstruction (kernels_asm.cu).

@@ -241,6 +241,7 @@ struct cgh_eops {
   uint16_t* EZt[2];
   long long ez_plane, ezt_plane;
   CUtensorMap mEZ[2], mEZt[2];
+  CUtensorMap mEZh[2], mEZth[2];  // the hi planes only (re_hi, im_hi) of the same memory
 };
 
 void eops_destroy(cgh_plan* p) {
@@ -270,6 +271,8 @@ int eops_get(const cgh_plan* pc, int f16, const CUtensorMap** mEZ, const CUtenso
     if (rc == CGH_OK) rc = cgh_cuda_check(cudaMalloc(&e->EZt[k], 4 * e->ezt_plane * 2), "fringe operands: EZt");
     if (rc == CGH_OK) rc = make_plane_map(&e->mEZ[k], e->EZ[k], 4, p->holo_h, (long long)Z * p->obj_h);
     if (rc == CGH_OK) rc = make_plane_map(&e->mEZt[k], e->EZt[k], 4, (long long)Z * p->holo_w, p->obj_w);
+    if (rc == CGH_OK) rc = make_hi_plane_map(&e->mEZh[k], e->EZ[k], p->holo_h, (long long)Z * p->obj_h);
+    if (rc == CGH_OK) rc = make_hi_plane_map(&e->mEZth[k], e->EZt[k], (long long)Z * p->holo_w, p->obj_w);
     if (rc != CGH_OK) {
       cudaFree(e->EZ[k]);
       cudaFree(e->EZt[k]);
@@ -295,6 +298,15 @@ int eops_get(const cgh_plan* pc, int f16, const CUtensorMap** mEZ, const CUtenso
   }
   if (mEZ) *mEZ = &e->mEZ[k];
   if (mEZt) *mEZt = &e->mEZt[k];
+  return CGH_OK;
+}
+
+int eops_get_hi(const cgh_plan* p, int f16, const CUtensorMap** mEZh, const CUtensorMap** mEZth, cudaStream_t st) {
+  const int rc = eops_get(p, f16, nullptr, nullptr, st);
+  if (rc != CGH_OK) return rc;
+  const int k = f16 ? 1 : 0;
+  *mEZh = &p->eops->mEZh[k];
+  *mEZth = &p->eops->mEZth[k];
   return CGH_OK;
 }
 

@@ -257,7 +257,9 @@ int tc_init_attributes() {
       (e = set_gemm_attr<KIND_CR, EPI_Y, false>()) != cudaSuccess ||
       (e = set_gemm_attr<KIND_CR, EPI_Y, true>()) != cudaSuccess ||
       (e = set_gemm_attr<KIND_CC, EPI_H, false>()) != cudaSuccess ||
-      (e = set_gemm_attr<KIND_CC, EPI_H, true>()) != cudaSuccess)
+      (e = set_gemm_attr<KIND_CC, EPI_H, true>()) != cudaSuccess ||
+      (e = set_gemm_attr<KIND_CR2, EPI_Y, true>()) != cudaSuccess ||
+      (e = set_gemm_attr<KIND_CC2, EPI_H, true>()) != cudaSuccess)
     return cgh_cuda_check(e, "tensor-core kernel attributes");
   return CGH_OK;
 }
@@ -453,13 +455,17 @@ static void stage2_args(const cgh_plan* p, bool f16, float2* holo, int S, TcGemm
   a.tz = tiles.z;
 }
 
-template <bool F16>
+// X2 (fp16 only): the fringe operand as its hi planes, two products per real product
+// (CGH_FORM_TC_FP16X2).
+template <bool F16, bool X2 = false>
 static int tc_run(const cgh_plan* p, const int32_t* coef, const int32_t* const* lists, const int32_t* d_counts,
                   float2* holo, int accumulate, cudaStream_t st, bool flags_ready = false,
                   cudaEvent_t coef_ready = nullptr) {
+  static_assert(F16 || !X2, "the hi-only fringe form is fp16");
+  constexpr int K1 = X2 ? KIND_CR2 : KIND_CR, K2 = X2 ? KIND_CC2 : KIND_CC;
   cgh_tc_state* t = p->tc;
   const CUtensorMap *mEZ, *mEZt;
-  int rc = eops_get(p, F16 ? 1 : 0, &mEZ, &mEZt, st);
+  int rc = X2 ? eops_get_hi(p, 1, &mEZ, &mEZt, st) : eops_get(p, F16 ? 1 : 0, &mEZ, &mEZt, st);
   if (rc != CGH_OK) return rc;
   // H is cleared by the stage-1 kernel's idle warps when it can be cleared in float4 units
   const size_t hpix = (size_t)p->holo_h * p->holo_w;
@@ -479,7 +485,7 @@ static int tc_run(const cgh_plan* p, const int32_t* coef, const int32_t* const* 
     a.zero_n[1] = (long long)(hpix / 2);
   }
   prof_mark(p, CGH_PROF_TC_STAGE1, 0, st);
-  cudaError_t e = launch_gemm<KIND_CR, EPI_Y, F16>(*mEZt, t->mB1, t->mY, a, tiles, st);
+  cudaError_t e = launch_gemm<K1, EPI_Y, F16>(*mEZt, t->mB1, t->mY, a, tiles, st);
   prof_mark(p, CGH_PROF_TC_STAGE1, 1, st);
   TC_CK(e, "tc: stage-1 GEMM");
   t->flags_dirty = 0;
@@ -489,7 +495,7 @@ static int tc_run(const cgh_plan* p, const int32_t* coef, const int32_t* const* 
   // (whose 1e-5 bar the tensor pipe's chain-length error would otherwise approach) and 128
   // for bf16 hi+lo (whose error is its operand split, far above that of the chains), which
   // halves the partial-sum atomics.
-  const int streamk = p->deterministic ? 0 : (p->max_ksteps > 0 ? p->max_ksteps : (F16 ? 32 : 128));
+  const int streamk = p->deterministic ? 0 : (p->max_ksteps > 0 ? p->max_ksteps : (F16 && !X2 ? 32 : 128));
   int S = p->deterministic ? 1 : stage2_splits(tm * tn, t->ktot_alloc / TC_BK);
   if (!p->deterministic && p->max_ksteps > 0) {
     // cap the chain length on the actual K: sum of the layers' compacted rows is at most
@@ -501,7 +507,7 @@ static int tc_run(const cgh_plan* p, const int32_t* coef, const int32_t* const* 
   stage2_args(p, F16, holo, S, a, tiles);
   a.streamk = streamk;
   prof_mark(p, CGH_PROF_TC_STAGE2, 0, st);
-  e = launch_gemm<KIND_CC, EPI_H, F16>(*mEZ, t->mY, t->mY, a, tiles, st);
+  e = launch_gemm<K2, EPI_H, F16>(*mEZ, t->mY, t->mY, a, tiles, st);
   prof_mark(p, CGH_PROF_TC_STAGE2, 1, st);
   TC_CK(e, "tc: stage-2 GEMM");
   return CGH_OK;
@@ -749,6 +755,7 @@ int tc_progressive(const cgh_plan* p, const int32_t* coef, const int32_t* const*
   int rc = tc_ensure(p);
   if (rc != CGH_OK) return rc;
   if (form == CGH_FORM_TC_FP16X3) return tc_run<true>(p, coef, lists, d_counts, holo, accumulate, st);
+  if (form == CGH_FORM_TC_FP16X2) return tc_run<true, true>(p, coef, lists, d_counts, holo, accumulate, st);
   return tc_run<false>(p, coef, lists, d_counts, holo, accumulate, st);
 }
 
@@ -777,6 +784,8 @@ int tc_progressive_step(const cgh_plan* p, const uint8_t* sal, const uint8_t* L,
                      t->fl, p->obj_h, p->obj_w, p->n_layers),
           "tc: scatter");
   if (form == CGH_FORM_TC_FP16X3) return tc_run<true>(p, coef, lists, d_counts, holo, accumulate, st, true, coef_ready);
+  if (form == CGH_FORM_TC_FP16X2)
+    return tc_run<true, true>(p, coef, lists, d_counts, holo, accumulate, st, true, coef_ready);
   return tc_run<false>(p, coef, lists, d_counts, holo, accumulate, st, true, coef_ready);
 }
 

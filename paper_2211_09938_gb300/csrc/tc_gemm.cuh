@@ -20,7 +20,12 @@
 #define TC_PLANE_BYTES (128 * TC_BK * 2)    // one 128-row plane tile: 8 KiB
 #define TC_WAIT_NS 2000000000ull            // bounded waits: 2 s, then CGH_ERR_TIMEOUT
 
-enum { KIND_TEST = 0, KIND_CR = 1, KIND_CC = 2 };
+// Operand kinds.  CR: complex fringe x real data (stage 1), CC: complex x complex (stage 2),
+// both with every operand split hi + lo (three products per real product).  CR2 / CC2: the
+// same with the fringe operand as its hi planes only (re_hi, im_hi) and the data operand
+// hi + lo, two products per real product (fringe_hi x data_hi + fringe_hi x data_lo); the
+// fringe's own rounding then bounds the error.
+enum { KIND_TEST = 0, KIND_CR = 1, KIND_CC = 2, KIND_CR2 = 3, KIND_CC2 = 4 };
 enum { EPI_H = 0, EPI_Y = 1, EPI_C = 2, EPI_F = 3 };
 
 // ------------------------------------------------------------------------------------
@@ -186,6 +191,14 @@ template <>
 struct TcCfg<KIND_CC> {
   static constexpr int NA = 4, NB = 4;
 };
+template <>
+struct TcCfg<KIND_CR2> {
+  static constexpr int NA = 2, NB = 2;
+};
+template <>
+struct TcCfg<KIND_CC2> {
+  static constexpr int NA = 2, NB = 4;
+};
 
 // Epilogue staging for EPI_Y: 32-column chunks of the four output planes (128 rows x
 // 64 bytes x 4 planes each), written by the epilogue warps and stored by TMA.  KIND_CR keeps
@@ -194,14 +207,16 @@ struct TcCfg<KIND_CC> {
 #define TC_STAGE_Y_BYTES (4 * TC_PLANE_BYTES)
 template <int KIND>
 constexpr int tc_stage_y_bufs() {
-  return KIND == KIND_CR ? 1 : 2;
+  return KIND == KIND_CR || KIND == KIND_CR2 ? 1 : 2;
 }
 
 // Pipeline depth per kind and epilogue, sized so that one CTA per SM fits in shared memory
 // (and owns the tensor memory): > 114 KiB, <= 227 KiB.
 template <int KIND, int EPI>
 constexpr int tc_nst() {
-  return KIND == KIND_TEST ? 8 : (EPI == EPI_Y ? (KIND == KIND_CR ? 4 : 2) : (KIND == KIND_CR ? 4 : 3));
+  return KIND == KIND_TEST ? 8
+                           : (EPI == EPI_Y ? (KIND == KIND_CR ? 4 : KIND == KIND_CR2 ? 6 : 2)
+                                           : (KIND == KIND_CR || KIND == KIND_CC2 ? 4 : 3));
 }
 
 template <int KIND, int EPI>
@@ -253,6 +268,22 @@ __device__ __forceinline__ void issue_products(uint32_t tmem, uint64_t a_desc, u
   const uint32_t f = first ? 0u : 1u;
   if (KIND == KIND_TEST) {
     mma_f16(d0, A(0), B(0), id_pos, f);
+  } else if (KIND == KIND_CR2) {
+    // A: re_hi, im_hi; B: hi, lo
+    mma_f16(d0, A(0), B(0), id_pos, f);
+    mma_f16(d0, A(0), B(1), id_pos, 1);
+    mma_f16(d1, A(1), B(0), id_pos, f);
+    mma_f16(d1, A(1), B(1), id_pos, 1);
+  } else if (KIND == KIND_CC2) {
+    // A: re_hi, im_hi; B: re_hi, re_lo, im_hi, im_lo
+    mma_f16(d0, A(0), B(0), id_pos, f);
+    mma_f16(d0, A(0), B(1), id_pos, 1);
+    mma_f16(d0, A(1), B(2), id_neg, 1);
+    mma_f16(d0, A(1), B(3), id_neg, 1);
+    mma_f16(d1, A(0), B(2), id_pos, f);
+    mma_f16(d1, A(0), B(3), id_pos, 1);
+    mma_f16(d1, A(1), B(0), id_pos, 1);
+    mma_f16(d1, A(1), B(1), id_pos, 1);
   } else if (KIND == KIND_CR) {
     mma_f16(d0, A(0), B(0), id_pos, f);
     mma_f16(d0, A(0), B(1), id_pos, 1);
@@ -856,6 +887,23 @@ static int make_plane_map(CUtensorMap* map, const void* base, int planes, long l
   cuuint64_t dims[3] = {(cuuint64_t)k_alloc, (cuuint64_t)rows, (cuuint64_t)planes};
   cuuint64_t strides[2] = {(cuuint64_t)(k_alloc * 2), (cuuint64_t)(rows * k_alloc * 2)};
   cuuint32_t box[3] = {TC_BK, 128, (cuuint32_t)planes};
+  cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_UINT16, 3, const_cast<void*>(base), dims, strides, box, estr,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return cgh_fail(CGH_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+  return CGH_OK;
+}
+
+// The hi planes (0 and 2: re_hi, im_hi) of a 4-plane hi+lo operand as a 2-plane map over
+// the same memory.
+static int make_hi_plane_map(CUtensorMap* map, const void* base, long long rows, long long k_alloc) {
+  if (get_encoder() != CGH_OK) return CGH_ERR_CUDA;
+  if (((uintptr_t)base & 15) || (k_alloc * 2) % 16)
+    return cgh_fail(CGH_ERR_ARG, "tensor map: base must be 16-byte aligned and rows a multiple of 16 bytes");
+  cuuint64_t dims[3] = {(cuuint64_t)k_alloc, (cuuint64_t)rows, 2};
+  cuuint64_t strides[2] = {(cuuint64_t)(k_alloc * 2), (cuuint64_t)(2 * rows * k_alloc * 2)};
+  cuuint32_t box[3] = {TC_BK, 128, 2};
   cuuint32_t estr[3] = {1, 1, 1};
   CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_UINT16, 3, const_cast<void*>(base), dims, strides, box, estr,
                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,

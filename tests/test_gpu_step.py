@@ -56,7 +56,7 @@ SCENES = {
 
 
 @pytest.mark.parametrize("name", list(SCENES))
-@pytest.mark.parametrize("form,tol", [("tc_bf16x3", BF16X3_TOL), ("tc_fp16x3", FP16X3_TOL)])
+@pytest.mark.parametrize("form,tol", [("tc_bf16x3", BF16X3_TOL), ("tc_fp16x3", FP16X3_TOL), ("tc_fp16x2", 1e-3)])
 def test_step_matches_oracle_and_two_calls(torch_cuda, name, form, tol):
     """Default plan: lists bit-exact and hologram within the form's bar against the oracle.
     Deterministic plan: the step's hologram equals the two calls' bit for bit."""
