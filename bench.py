@@ -361,9 +361,8 @@ def run_level_sweep(plan, coeffs, lists, counts, I, L, stream, form, flush):
             ev[1].record(stream)
             _, A = plan.reconstruct(H, L, fields=False, stream=stream)
             s = ssim(A, ref, stream=stream)
-            n = c[:, 0].cpu().numpy()
             stream.synchronize()
-            out.append({"stage": name, "operators": int(n[0] + 4 * n[1:].sum()),
+            out.append({"stage": name, "operators": Plan.operator_count(c),
                         "ssim_vs_pointwise": s.item(), "superposition_ms": ev[0].elapsed_time(ev[1])})
     return {"form": form, "pointwise_operators": int(I.numel()), "stages": out}
 
@@ -645,7 +644,7 @@ def run_ours(args):
     # the detail-basis terms (an LLL block, or one of X, Y, D of a selected block) and the
     # paper's operators (an LLL block, or one residual cell: 4 per selected block)
     t_terms = n_lll + 3 * (n1 + n2 + n3)
-    operators = n_lll + 4 * (n1 + n2 + n3)
+    operators = Plan.operator_count(counts)
     step_ms = sorted(a.elapsed_time(b) for a, b in evs)
     from paper_2211_09938_gb300.cgh import probe_peaks
     unit_peaks = probe_peaks(stream=stream)

@@ -236,6 +236,15 @@ class Plan:
                 c[k].zero_()
         return c
 
+    @staticmethod
+    def operator_count(counts):
+        """Section 3's operator count of the lists whose device counts are given: one LUT
+        block multiplied, shifted and added per LLL block, and one per residual-map cell,
+        i.e. four per selected detail block (the one-level inverse DWT of a selected block
+        is a 2x2 grid of cells).  Reads the counts back to the host."""
+        n = [int(v) for v in counts[:, 0].cpu().tolist()]
+        return n[0] + 4 * sum(n[1:])
+
     def progressive_hologram(self, coeffs, lists, counts, holo=None, accumulate=False,
                              form="direct_lut", stream=None):
         import torch

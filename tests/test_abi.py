@@ -67,3 +67,20 @@ def test_host_argument_checks_without_gpu(L):
     assert b"cgh_progressive_step" in L.cgh_last_error()
     assert L.cgh_plan_destroy(None) == 0
     assert L.cgh_version() >= 10000
+
+
+def test_operator_count_of_device_counts_matches_oracle():
+    """Plan.operator_count (host arithmetic on the counts the selection writes) agrees with
+    the pinned oracle's operator_count on the same lists, stage by stage."""
+    import numpy as np
+    import torch
+    from oracle import cgh_oracle as O
+    from paper_2211_09938_gb300 import Plan
+    from synth import scenes
+    sc = scenes.random_scene(55, 64, 128, 3, graded=True)
+    lists = O.progressive_lists(sc["saliency"], sc["layer"], 3, scenes.THRESHOLDS_U8)
+    counts = torch.tensor([[len(x), len(x)] for x in lists], dtype=torch.int32)
+    e = np.zeros(0, np.int32)
+    for stage, keep in enumerate(Plan._STAGE_LISTS):
+        st = [lists[k] if k in keep else e for k in range(4)]
+        assert Plan.operator_count(Plan.level_counts(counts, stage)) == O.operator_count(st)

@@ -90,8 +90,11 @@ def _gpu_sweep(torch, sc, form):
         H = plan.progressive_hologram(coeffs, lists, c, form=form)
         _, A = plan.reconstruct(H, L, fields=False)
         n = c[:, 0].cpu().numpy()
-        ops = int(n[0] + 4 * n[1:].sum())
-        out.append((ops, ssim(A, ref).item()))
+        # the count as the product reports it, and the pinned oracle's count of the lists
+        # the GPU wrote (truncated at the GPU's own counts)
+        ops = Plan.operator_count(c)
+        gl = [lists[k][:int(n[k])].cpu().numpy() for k in range(4)]
+        out.append((ops, ssim(A, ref).item(), O.operator_count(gl)))
     torch.cuda.synchronize()
     return out
 
@@ -111,9 +114,9 @@ def test_level_sweep_matches_oracle(torch_cuda, form):
             sc["intensity"], sc["layer"], st, g), g), sc["layer"])
         want.append((O.operator_count(st), O.ssim(a / a.max(), ref / ref.max())))
     got = _gpu_sweep(torch, sc, form)
-    for stage, ((og, sg), (ow, sw)) in enumerate(zip(got, want)):
+    for stage, ((og, sg, ol), (ow, sw)) in enumerate(zip(got, want)):
         print(f"{form} {STAGE_NAMES[stage]}: operators {og} (oracle {ow}) ssim {sg:.6f} (oracle {sw:.6f})")
-        assert og == ow
+        assert og == ow and ol == ow
         assert abs(sg - sw) <= TOL_SWEEP
     assert all(got[k][1] < got[k + 1][1] for k in range(3))
 
@@ -124,10 +127,11 @@ def test_level_sweep_paper_scale_shape(torch_cuda):
     torch = torch_cuda
     sc = scenes.paper_scene()
     got = _gpu_sweep(torch, sc, "tc_bf16x3")
-    for stage, (ops, s) in enumerate(got):
+    for stage, (ops, s, ol) in enumerate(got):
         print(f"paper scale {STAGE_NAMES[stage]}: operators {ops} ssim {s:.5f}")
-    ops = [o for o, _ in got]
-    ss = [s for _, s in got]
+        assert ops == ol
+    ops = [o for o, _, _ in got]
+    ss = [s for _, s, _ in got]
     assert ops == sorted(ops) and ops[-1] < sc["intensity"].size // 2
     assert all(ss[k] < ss[k + 1] for k in range(3))
     assert 0.0 < ss[0] and ss[-1] <= 1.0

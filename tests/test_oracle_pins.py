@@ -205,6 +205,105 @@ def test_operator_counts_of_section_3():
     assert O.detail_term_count(lists) == vals["pointwise_operators"]
 
 
+def _hand_scene_16():
+    layer = np.zeros((16, 16), np.uint8)
+    layer[:, 6:] = 1
+    sal = np.zeros((16, 16), np.uint8)
+    sal[5, 5] = 240
+    return layer, sal
+
+
+def test_operator_count_hand_counted_16x16():
+    """operator_count (reading R20: 1 per LLL block, 1 per residual-map cell) against a
+    count done by hand on a 16x16 two-layer object with one salient pixel
+    (tests/golden/operator_counts_16x16.txt).  Also pins the four lists entry by entry.
+    A weight of 3 per detail block (the detail-coefficient count) gives 21, not 26."""
+    want, vals = {0: [], 1: [], 2: [], 3: []}, {}
+    for line in open(os.path.join(GOLDEN, "operator_counts_16x16.txt")):
+        f = line.split()
+        if not f or f[0].startswith("#"):
+            continue
+        if f[0] == "entry":
+            want[int(f[1])].append(O.pack_entry(int(f[2]), int(f[3]), int(f[4])))
+        else:
+            vals[f[0]] = int(f[1])
+    layer, sal = _hand_scene_16()
+    lists = O.progressive_lists(sal, layer, 2, scenes.THRESHOLDS_U8)
+    for k in range(4):
+        assert lists[k].tolist() == want[k], k
+    assert O.operator_count(lists) == vals["operators"]
+    assert layer.size == vals["pointwise_operators"]
+
+
+def _residual_cells_superposed(lists, n_layers, obj_shape, levels=3):
+    """Walks the loop of the residual-map form (Section 2 steps 2-5) and counts the cells
+    it superposes with a LUT block: one per listed LLL block, and at each level every
+    cell of the residual grid that the strided 2x2 synthesis of a selected block
+    writes to.  No weight is written down: the cells are counted where they land."""
+    masks = O.masks_from_lists(lists, n_layers, obj_shape, levels)
+    Ho, Wo = obj_shape
+    total = 0
+    for z in range(n_layers):
+        total += int(masks[0][z].sum())
+        for l in range(levels, 0, -1):
+            h, w = Ho >> l, Wo >> l
+            cells = np.zeros((2 * h, 2 * w), dtype=bool)
+            for r in (0, 1):
+                for c in (0, 1):
+                    cells[r::2, c::2] |= masks[l][z]
+            total += int(cells.sum())
+    return total
+
+
+@pytest.mark.parametrize("seed,n,n_layers", [(51, 32, 3), (52, 64, 5), (53, 16, 1)])
+def test_operator_count_equals_superposed_residual_cells(seed, n, n_layers):
+    """operator_count equals the number of LUT-block superpositions the residual-map
+    loop performs, on graded scenes where every level selects a different subset."""
+    sc = scenes.random_scene(seed, n, 2 * n, n_layers, graded=True)
+    lists = O.progressive_lists(sc["saliency"], sc["layer"], n_layers, scenes.THRESHOLDS_U8)
+    assert all(len(x) > 0 for x in lists)
+    assert O.operator_count(lists) == _residual_cells_superposed(lists, n_layers, (n, n))
+    # each cumulative stage of the level sweep as well
+    e = np.zeros(0, np.int32)
+    for keep in ((0,), (0, 3), (0, 3, 2)):
+        st = [lists[k] if k in keep else e for k in range(4)]
+        assert O.operator_count(st) == _residual_cells_superposed(st, n_layers, (n, n))
+
+
+# ---------------------------------------------------------------- the comparator
+
+
+def test_rel_l2_hand_values():
+    """rel_l2 = ||x - ref||_2 / ||ref||_2 over all elements (Frobenius for 2-D), complex
+    moduli, ||x|| when ref is zero.  Each value is worked out by hand; the comment names
+    the plausible slip each one catches."""
+    # ||[3,-4]|| / ||[0,4]|| = 5/4; dividing by the squared norm gives 5/16, squaring both 25/16
+    assert O.rel_l2(np.array([3.0, 0.0]), np.array([0.0, 4.0])) == pytest.approx(1.25, rel=1e-15)
+    # orthogonal perturbation of [3,4] by 0.1*[-4,3]: |d| = 0.5, |ref| = 5
+    assert O.rel_l2(np.array([3.0 - 0.4, 4.0 + 0.3]), np.array([3.0, 4.0])) == pytest.approx(0.1, rel=1e-14)
+    # conj(j) - j = -2j: a comparator that drops imaginary parts reads 0
+    assert O.rel_l2(np.array([-1j]), np.array([1j])) == pytest.approx(2.0, rel=1e-15)
+    # purely imaginary error on a real reference: |0.25j| / |2| = 0.125
+    assert O.rel_l2(np.array([2.0 + 0.25j]), np.array([2.0])) == pytest.approx(0.125, rel=1e-15)
+    # 2-D: difference = identity (Frobenius sqrt 2, spectral 1) over ref = diag(2, 0) (both 2)
+    ref = np.array([[2.0, 0.0], [0.0, 0.0]])
+    assert O.rel_l2(ref + np.eye(2), ref) == pytest.approx(np.sqrt(2.0) / 2.0, rel=1e-15)
+    # zero reference: the absolute norm, |[3, 4j]| = 5
+    assert O.rel_l2(np.array([3.0, 4j]), np.zeros(2)) == pytest.approx(5.0, rel=1e-15)
+    assert O.rel_l2(np.zeros(3), np.zeros(3)) == 0.0
+
+
+def test_rel_l2_scaling_and_symmetry_of_scale():
+    """rel_l2(ref (1 + e), ref) = |e| for any complex ref and complex e, and the result
+    does not change when both arrays are scaled by the same complex factor."""
+    rng = np.random.default_rng(7)
+    ref = rng.standard_normal((5, 7)) + 1j * rng.standard_normal((5, 7))
+    for e in (1e-6, -3e-3, 0.5j, 0.2 - 0.1j):
+        assert O.rel_l2(ref * (1 + e), ref) == pytest.approx(abs(e), rel=1e-9)
+    x = ref + 1e-3 * rng.standard_normal(ref.shape)
+    assert O.rel_l2(x * (3 - 4j), ref * (3 - 4j)) == pytest.approx(O.rel_l2(x, ref), rel=1e-12)
+
+
 # ---------------------------------------------------------------- holograms
 
 def tiny_geom(n=8, s=4, n_layers=1, a=None, z=None):
