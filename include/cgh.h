@@ -182,8 +182,10 @@ int cgh_select_blocks(const cgh_plan* plan, const uint8_t* saliency, const uint8
 /*
  * cgh_select_blocks_noalloc - cgh_select_blocks without a plan and without allocating.
  * The paper has no counterpart: this entry point exists for callers that cannot call
- * cudaMalloc (for example code running inside a host callback, or an embedder whose
- * device memory budget is fixed at start-up) and so cannot create a plan.
+ * cudaMalloc (for example an embedder whose device memory budget is fixed and reserved
+ * at start-up and must not grow afterwards) and so cannot create a plan.  Like every
+ * entry point here it calls the CUDA runtime, so it must not be called from inside a
+ * stream host function (cudaLaunchHostFunc), where CUDA calls are not allowed.
  * Same selection, order, output format, d_count[2] semantics and bit-exact results as
  * cgh_select_blocks for the same inputs.
  *   obj_h, obj_w  object size (multiples of 8, 8..8192);  n_layers  Z, 1..64
@@ -193,9 +195,13 @@ int cgh_select_blocks(const cgh_plan* plan, const uint8_t* saliency, const uint8
  * 256) <= 262144, e.g. 64 layers of a 2048x2048 object at level 1; larger requests
  * return CGH_ERR_ARG with a message and enqueue nothing.
  * Allocates nothing: no cudaMalloc, no cudaFree, no allocating library routine.  The
- * first call on each device looks up the array's device address with
- * cudaGetSymbolAddress (with that device current), so make that first call before any
- * stream capture.  All calls on a device share the one array: calls that may overlap on
+ * array is placed when the library's module is first loaded on a device, which under
+ * lazy module loading (the CUDA default) can be this entry point's first call there.
+ * That first call on each device also looks up the array's device address with
+ * cudaGetSymbolAddress (with that device current).  So make one call per device at
+ * start-up, before any stream capture and before the memory budget is fixed.  The
+ * looked-up address is cached for the life of the process and does not survive
+ * cudaDeviceReset: do not call this entry point after resetting its device.  All calls on a device share the one array: calls that may overlap on
  * the GPU (different streams, or different host threads) race and must be serialised
  * by the caller.
  * Errors: CGH_ERR_ARG, CGH_ERR_UNSUPPORTED (device ordinal >= 64), CGH_ERR_CUDA.

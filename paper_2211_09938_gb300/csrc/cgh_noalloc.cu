@@ -1,13 +1,15 @@
 // Allocation-free variant of the block selection (cgh_select_blocks_noalloc).
 //
-// Some callers cannot call cudaMalloc: code that runs where the allocator is off
-// limits, such as a host callback or an embedder with a fixed, pre-reserved memory
-// budget that must not grow after start-up.  They cannot create a plan, because a plan
-// allocates its tables and scratch.  This entry point needs no plan.  Its only scratch,
-// the per-(layer, chunk) counts and offsets of the ordered compaction, lives in the
-// file-scope device array below.  The module loader places that array in device memory
-// when the library is loaded, and every GPU that loads the library keeps it until the
-// process exits.
+// Some callers cannot call cudaMalloc: an embedder whose device memory budget is fixed
+// and reserved at start-up, and which must not see device memory grow afterwards, or a
+// caller that shares the device with an allocator it does not own.  They cannot create
+// a plan, because a plan allocates its tables and scratch.  This entry point needs no
+// plan.  Its only scratch, the per-(layer, chunk) counts and offsets of the ordered
+// compaction, lives in the file-scope device array below.  The array is placed in
+// device memory when this module is first loaded on a device; with lazy module loading
+// (the CUDA default) that can be this entry point's first call on the device, so a
+// caller with a fixed budget makes one call per device at start-up.  Every GPU that has
+// loaded the module keeps the array until the process exits.
 #include <mutex>
 
 #include "cgh_internal.h"
@@ -20,7 +22,10 @@ static __device__ __align__(256) int g_noalloc_scratch[2 * CGH_NOALLOC_HALF];
 
 // Host-side device addresses of g_noalloc_scratch, one per device ordinal, filled by
 // the first call on that device.  The array's name in host code is only a stand-in for
-// the symbol and must never be handed to a kernel.
+// the symbol and must never be handed to a kernel.  The cached address belongs to the
+// device's primary context: after cudaDeviceReset the module is loaded again and the
+// address may change, so the entry point must not be used after a reset in the same
+// process.
 #define CGH_NOALLOC_MAX_DEVICES 64
 static int* g_scratch_ptr[CGH_NOALLOC_MAX_DEVICES];
 static std::mutex g_scratch_mu;
@@ -68,7 +73,8 @@ extern "C" int cgh_select_blocks_noalloc(const uint8_t* saliency, const uint8_t*
   if (need > CGH_NOALLOC_HALF)
     return cgh_fail(CGH_ERR_ARG,
                     "cgh_select_blocks_noalloc: n_layers * ceil(blocks/256) = %lld exceeds the static "
-                    "scratch limit of %d (e.g. 64 layers at 2048x2048, level 1); use cgh_select_blocks",
+                    "scratch limit of %d (64 layers of a 2048x2048 object at level 1 just fit); use "
+                    "cgh_select_blocks",
                     need, CGH_NOALLOC_HALF);
   int* scratch = nullptr;
   int rc = noalloc_scratch(&scratch);
