@@ -241,11 +241,16 @@ int cgh_select_progressive(const cgh_plan* plan, const uint8_t* saliency, const 
  *   lists     HOST array of 4 device pointers: lists[0] = LLL list (level-3 blocks),
  *             lists[l] = level-l detail list, l = 1..3 (format of cgh_select_blocks)
  *   d_counts  int32 [4][2] device array, d_counts[2k] = entries in lists[k] (the
- *             d_count[0] written by cgh_select_blocks); [2k+1] is ignored
+ *             d_count[0] written by cgh_select_blocks); [2k+1] is ignored.  Each list
+ *             must hold d_counts[2k] entries.  A count outside [0, Z * blocks at the
+ *             list's level] cannot come from the selection: the kernels clamp it to that
+ *             range (never reading past the plan's largest possible list) and record
+ *             CGH_ERR_ARG in the plan's status word (read with cgh_status).
  *   holo      complex64 [holo_h][holo_w] output
  *   accumulate 0: holo = H;  1: holo += H
  *   form      CGH_FORM_* (the tensor-core forms use plan scratch)
- * Errors: CGH_ERR_ARG, CGH_ERR_UNSUPPORTED (form), CGH_ERR_CUDA.
+ * Errors: CGH_ERR_ARG, CGH_ERR_UNSUPPORTED (form), CGH_ERR_CUDA; device-side count errors
+ * through cgh_status as above.
  */
 int cgh_progressive_hologram(const cgh_plan* plan, const int32_t* coeffs,
                              const int32_t* const* lists, const int32_t* d_counts,
@@ -378,6 +383,26 @@ int cgh_propagate(const cgh_plan* plan, const float* fields, float* holo, int ac
  */
 int cgh_adjoint(const cgh_plan* plan, const float* grad_holo, const int32_t* const* lists,
                 const int32_t* d_counts, const uint8_t* layer_idx, float* grad_object, void* stream);
+
+/*
+ * cgh_progressive_apply - the progressive operator applied to a real-valued object: the
+ * linear map whose adjoint is cgh_adjoint.  Paper: Eq. 3 (the hologram is the sum of the
+ * holograms of the Haar basis functions times their coefficients), Section 2 steps 2-5.
+ *   H = sum_z E_z P_z(object * [layer_idx = z]) E_z^T,   E_z[m][i] = f_z(m - s*i)
+ * with P_z the layer's progressive approximation (3-level Haar, LLL blocks outside lists[0]
+ * and detail blocks outside lists[1..3] set to zero, inverse Haar).  For an integer object
+ * this is the hologram cgh_progressive_hologram computes; here the object may be any real
+ * image, which makes the operator differentiable with respect to it.
+ *   object     float [obj_h][obj_w];  layer_idx uint8 [obj_h][obj_w]
+ *   lists, d_counts  as for cgh_progressive_hologram
+ *   holo       complex64 [holo_h][holo_w] output;  accumulate 0: holo = H, 1: holo += H
+ * Runs on the tensor cores (bf16 hi+lo, 3 products, FP32 accumulation), through the same
+ * operands as cgh_propagate; uses plan scratch.  Geometry limits as cgh_reconstruct.
+ * Errors: CGH_ERR_ARG, CGH_ERR_UNSUPPORTED (geometry), CGH_ERR_CUDA.
+ */
+int cgh_progressive_apply(const cgh_plan* plan, const float* object, const int32_t* const* lists,
+                          const int32_t* d_counts, const uint8_t* layer_idx, float* holo, int accumulate,
+                          void* stream);
 
 /*
  * cgh_amplitude_backward - cotangent of the composite amplitude |R_{layer(i,j)}(i,j)| with
@@ -529,6 +554,20 @@ int cgh_probe_ffma(float* sink, int grid, long long iters, void* stream);
  * and the context stays usable.  Read the result with cgh_status.
  */
 int cgh_selftest_timeout(const cgh_plan* plan, int limit_us, void* stream);
+
+/*
+ * cgh_selftest_grid_barrier - failure-detection self-test of the single-launch selection's
+ * grid barrier (the paper has no counterpart).  Launches `ctas` CTAs (2 .. the number the
+ * device holds at once, as for the selection) cooperatively; every CTA except absent_cta
+ * crosses the same bounded grid barrier the selection uses (a plan-owned barrier word of
+ * its own, cleared first; absent_cta = -1: every CTA arrives).  A CTA that crosses adds 1
+ * to *d_crossed (device int32, caller-owned, not cleared here).  With a CTA absent the
+ * barrier never completes: each waiting CTA gives up after limit_us microseconds
+ * (1..1000000), records CGH_ERR_TIMEOUT in the plan's status word and returns, so no GPU
+ * hangs.  Read the status with cgh_status.  Errors: CGH_ERR_ARG, CGH_ERR_CUDA.
+ */
+int cgh_selftest_grid_barrier(const cgh_plan* plan, int ctas, int absent_cta, int limit_us,
+                              int32_t* d_crossed, void* stream);
 
 /*
  * cgh_status - read and clear the plan's device status word (synchronises `stream`).

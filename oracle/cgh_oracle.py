@@ -594,6 +594,23 @@ def progressive_adjoint(G, layer, lists, geom, levels=3):
     return out
 
 
+def progressive_hologram_real(x, layer, lists, geom, levels=3):
+    """The progressive operator on a real-valued object x (Eq. 3 is linear in the object):
+    H = sum_z E_z P_z(x [layer == z]) E_z^T with P_z = IDWT o mask o DWT, the layer's
+    progressive approximation.  For an integer object it is progressive_hologram; its
+    adjoint is progressive_adjoint."""
+    x = np.asarray(x, dtype=np.float64)
+    L = np.asarray(layer)
+    masks = masks_from_lists(lists, geom.n_layers, L.shape, levels)
+    planes = np.zeros((geom.n_layers,) + L.shape, dtype=np.float64)
+    for z in range(geom.n_layers):
+        keep = {l: masks[l][z] for l in range(1, levels + 1)}
+        C = haar_forward_real(x * (L == z), levels)
+        C[:L.shape[0] >> levels, :L.shape[1] >> levels] *= masks[0][z]
+        planes[z] = haar_synthesis_real(C, keep, levels)
+    return pointwise_hologram_separable(planes, geom)
+
+
 def _gauss_window(size=11, sigma=1.5):
     t = np.arange(size) - (size - 1) / 2.0
     g = np.exp(-t * t / (2 * sigma * sigma))

@@ -1,11 +1,18 @@
 """Autotuner for the batched tensor-core launch: picks the number of 32-wide K steps per
-stage-2 work unit (how finely each scene's K is split across the persistent CTAs) by
-timing the batch with CUDA events, and caches the choice in a JSON file keyed by the
-batch's shape signature, the form and the GPU name."""
+stage-2 work unit (how finely each scene's K is split across the persistent CTAs, which is
+also the longest accumulation chain) by timing the batch with CUDA events, among the
+candidates the form's accuracy bar allows, and caches the choice in a JSON file keyed by
+the batch's shape signature, the form and the GPU name."""
 import json
 import os
 
 CANDIDATES = (8, 16, 32, 64, 128)
+# Longest stage-2 accumulation chain (K steps) each form may use: the tensor pipe's FP32
+# accumulation error grows with the number of MMAs summed in one accumulator, and the fp16
+# hi+lo form keeps its chains at <= 32 K steps so that its holograms stay within the 1e-5
+# rel-L2 bar (at 128 steps a 512->1024, 16-layer scene reaches 1.3e-5).  The bf16 hi+lo
+# form's bar is 1e-3.
+MAX_CHAIN = {"tc_fp16x3": 32, "tc_bf16x3": 128}
 
 
 def signature(plans, form):
@@ -27,7 +34,8 @@ def tune_batch(batch, plans, form, stream, cache_path=None, reps=3, candidates=C
         batch.set_tuning(cache[key]["ksteps"])
         return cache[key]
     results = {}
-    for c in candidates:
+    cap = MAX_CHAIN.get(form, max(candidates))
+    for c in [c for c in candidates if c <= cap]:
         batch.set_tuning(c)
         with torch.cuda.stream(stream):
             batch.run(stream=stream)  # warm

@@ -57,12 +57,14 @@ SIGNATURES = {
     "cgh_reconstruct_asm": (_I, [_P, _P, _P, _P, _P, _I, _I, _P]),
     "cgh_propagate": (_I, [_P, _P, _P, _I, _P]),
     "cgh_adjoint": (_I, [_P, _P, ctypes.POINTER(_P), _P, _P, _P, _P]),
+    "cgh_progressive_apply": (_I, [_P, _P, ctypes.POINTER(_P), _P, _P, _P, _I, _P]),
     "cgh_amplitude_backward": (_I, [_P, _P, _P, _P, _P, _P]),
     "cgh_phase_to_field": (_I, [_P, _P, ctypes.c_longlong, _P]),
     "cgh_phase_grad": (_I, [_P, _P, _P, ctypes.c_longlong, _P]),
     "cgh_ssim": (_I, [_P, _P, _I, _I, _I, _P, _P, _P]),
     "cgh_status": (_I, [_P, ctypes.POINTER(_I), _P]),
     "cgh_selftest_timeout": (_I, [_P, _I, _P]),
+    "cgh_selftest_grid_barrier": (_I, [_P, _I, _I, _I, _P, _P]),
     "cgh_probe_sfu": (_I, [_P, _I, ctypes.c_longlong, _P]),
     "cgh_probe_ffma": (_I, [_P, _I, ctypes.c_longlong, _P]),
     "cgh_tc_selftest_gemm": (_I, [_P, _P, _P, _I, _I, _I, _I, _P]),
@@ -346,6 +348,17 @@ class Plan:
                                 _stream(stream)))
         return out
 
+    def progressive_apply(self, obj, lists, counts, layer, holo=None, accumulate=False, stream=None):
+        """cgh_progressive_apply: the progressive operator on a real (float32) object; the
+        linear map whose adjoint is `adjoint`."""
+        import torch
+        if holo is None:
+            holo = torch.empty((self.holo_h, self.holo_w), dtype=torch.complex64, device=self.device)
+        arr = (ctypes.c_void_p * 4)(*[l.data_ptr() for l in lists])
+        check(lib().cgh_progressive_apply(self.handle, _ptr(obj), arr, _ptr(counts), _ptr(layer), _ptr(holo),
+                                          1 if accumulate else 0, _stream(stream)))
+        return holo
+
     def amplitude_backward(self, fields, layer, grad_amp, out=None, stream=None):
         import torch
         if out is None:
@@ -374,6 +387,12 @@ class Plan:
 
     def selftest_timeout(self, limit_us, stream=None):
         check(lib().cgh_selftest_timeout(self.handle, int(limit_us), _stream(stream)))
+
+    def selftest_grid_barrier(self, ctas, absent_cta, limit_us, crossed, stream=None):
+        """The selection's bounded grid barrier with `ctas` cooperative CTAs, one of them
+        (absent_cta >= 0) never arriving; crossed: device int32 counter of CTAs that crossed."""
+        check(lib().cgh_selftest_grid_barrier(self.handle, int(ctas), int(absent_cta), int(limit_us),
+                                              _ptr(crossed), _stream(stream)))
 
     def status(self, stream=None):
         v = ctypes.c_int(0)

@@ -169,8 +169,8 @@ int cgh_plan_create(cgh_plan** out, int obj_h, int obj_w, int holo_h, int holo_w
                       cudaMemcpyHostToDevice),
            "cgh_plan_create: copy a_fixed");
   PLAN_TRY(cudaMemset(p->d_status, 0, sizeof(int)), "cgh_plan_create: status clear");
-  PLAN_TRY(cudaMalloc(&p->d_sel_bar, sizeof(unsigned)), "cgh_plan_create: selection barrier");
-  PLAN_TRY(cudaMemset(p->d_sel_bar, 0, sizeof(unsigned)), "cgh_plan_create: selection barrier clear");
+  PLAN_TRY(cudaMalloc(&p->d_sel_bar, 2 * sizeof(unsigned)), "cgh_plan_create: selection barrier");
+  PLAN_TRY(cudaMemset(p->d_sel_bar, 0, 2 * sizeof(unsigned)), "cgh_plan_create: selection barrier clear");
   {
     int sms = 0;
     PLAN_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device), "cgh_plan_create: SM count");
@@ -373,6 +373,17 @@ int cgh_adjoint(const cgh_plan* p, const float* grad_holo, const int32_t* const*
   return field_adjoint(p, (const float2*)grad_holo, lists, d_counts, layer_idx, grad_object, (cudaStream_t)stream);
 }
 
+int cgh_progressive_apply(const cgh_plan* p, const float* object, const int32_t* const* lists,
+                          const int32_t* d_counts, const uint8_t* layer_idx, float* holo, int accumulate,
+                          void* stream) {
+  if (!p || !object || !lists || !d_counts || !layer_idx || !holo)
+    return cgh_fail(CGH_ERR_ARG, "cgh_progressive_apply: NULL argument");
+  for (int k = 0; k < 4; ++k)
+    if (!lists[k]) return cgh_fail(CGH_ERR_ARG, "cgh_progressive_apply: lists[%d] is NULL", k);
+  if ((uintptr_t)holo & 7) return cgh_fail(CGH_ERR_ARG, "cgh_progressive_apply: holo must be 8-byte aligned");
+  return field_forward(p, object, lists, d_counts, layer_idx, (float2*)holo, accumulate, (cudaStream_t)stream);
+}
+
 int cgh_amplitude_backward(const cgh_plan* p, const float* fields, const uint8_t* layer_idx, const float* grad_amp,
                            float* grad_fields, void* stream) {
   if (!p || !fields || !layer_idx || !grad_amp || !grad_fields)
@@ -422,3 +433,18 @@ int cgh_status(const cgh_plan* p, int* status_out, void* stream) {
 }
 
 }  // extern "C"
+
+extern "C" int cgh_selftest_grid_barrier(const cgh_plan* p, int ctas, int absent_cta, int limit_us,
+                                         int32_t* d_crossed, void* stream) {
+  if (!p || !d_crossed || limit_us < 1 || limit_us > 1000000 || ctas < 2 || absent_cta < -1 ||
+      absent_cta >= ctas)
+    return cgh_fail(CGH_ERR_ARG, "cgh_selftest_grid_barrier: plan or d_crossed NULL, ctas < 2, absent_cta "
+                                 "outside -1..ctas-1 or limit outside 1..1000000 us");
+  if (ctas > p->sel_coop_ctas)
+    return cgh_fail(CGH_ERR_ARG, "cgh_selftest_grid_barrier: %d CTAs exceed the %d the device holds at once",
+                    ctas, p->sel_coop_ctas);
+  return cgh_cuda_check(launch_grid_barrier_selftest(p->d_sel_bar + 1, p->d_status, d_crossed, ctas,
+                                                     1000ull * (unsigned long long)limit_us, absent_cta,
+                                                     (cudaStream_t)stream),
+                        "cgh_selftest_grid_barrier");
+}

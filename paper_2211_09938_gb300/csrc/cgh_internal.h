@@ -45,7 +45,7 @@ struct cgh_plan {
   int* d_chunk_cnt;
   int* d_chunk_off;
   int max_chunks;
-  unsigned* d_sel_bar;
+  unsigned* d_sel_bar;  // [0]: the fused selection's grid barrier; [1]: its self-test's
   int sel_coop_ctas;
 
   // Separable tensor-core path (allocated lazily by the first call that needs it).
@@ -95,6 +95,18 @@ static inline cudaError_t launch_pdl(void (*k)(Exp...), dim3 grid, dim3 block, s
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   return cudaLaunchKernelEx(&cfg, k, std::forward<Act>(args)...);
+}
+#endif
+
+#ifdef __CUDACC__
+// A work list's device count, clamped to [0, cmax] (cmax: the plan's largest possible list
+// at that level, layers x blocks).  A count outside that range cannot come from the
+// selection; it is recorded as CGH_ERR_ARG in the plan's status word (first error wins)
+// instead of being walked past the list.
+__device__ __forceinline__ int clamp_list_count(int c, int cmax, int* status) {
+  if (c >= 0 && c <= cmax) return c;
+  if (status) atomicCAS(status, 0, CGH_ERR_ARG);
+  return c < 0 ? 0 : cmax;
 }
 #endif
 
@@ -148,6 +160,8 @@ cudaError_t launch_select_tasks(int obj_h, int obj_w, int n_layers, const uint8_
                                 const SelCoop* coop = nullptr, const TcFlags* fl = nullptr,
                                 bool* flags_done = nullptr);
 int select_fused_ctas_per_sm();
+cudaError_t launch_grid_barrier_selftest(unsigned* bar, int* status, int* crossed, int ctas,
+                                         unsigned long long limit_ns, int absent, cudaStream_t st);
 static inline SelCoop plan_sel_coop(const cgh_plan* p) { return SelCoop{p->d_sel_bar, p->d_status, p->sel_coop_ctas}; }
 cudaError_t basic_init_attributes();
 int tc_init_attributes();
@@ -175,6 +189,8 @@ int tc_build_flags(const cgh_plan* p, const int32_t* const* lists, const int32_t
 // Fields: reconstruction, propagation, adjoints (kernels_field.cu).
 int field_init_attributes();
 int field_propagate(const cgh_plan* p, const float2* fields, float2* holo, int accumulate, cudaStream_t st);
+int field_forward(const cgh_plan* p, const float* obj, const int32_t* const* lists, const int32_t* d_counts,
+                  const uint8_t* L, float2* holo, int accumulate, cudaStream_t st);
 int field_adjoint(const cgh_plan* p, const float2* grad_holo, const int32_t* const* lists,
                   const int32_t* d_counts, const uint8_t* L, float* grad_obj, cudaStream_t st);
 int field_amplitude_backward(const cgh_plan* p, const float2* fields, const uint8_t* L, const float* grad_amp,

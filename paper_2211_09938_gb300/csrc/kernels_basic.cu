@@ -409,7 +409,7 @@ __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
   asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
   return v;
 }
-__device__ bool sel_grid_barrier(unsigned* bar, int* status) {
+__device__ bool sel_grid_barrier(unsigned* bar, int* status, unsigned long long limit_ns = SEL_WAIT_NS) {
   __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -419,7 +419,7 @@ __device__ bool sel_grid_barrier(unsigned* bar, int* status) {
     const unsigned long long t0 = sel_timer();
     int ok = 1;
     while (((ld_acquire_u32(bar) ^ old) & 0x80000000u) == 0u) {
-      if (sel_timer() - t0 > SEL_WAIT_NS) {
+      if (sel_timer() - t0 > limit_ns) {
         ok = 0;
         if (status) atomicExch(status, CGH_ERR_TIMEOUT);
         break;
@@ -430,6 +430,32 @@ __device__ bool sel_grid_barrier(unsigned* bar, int* status) {
   }
   __syncthreads();
   return s_ok != 0;
+}
+
+// Self-test of the grid barrier's bounded wait: every CTA but `absent` crosses the barrier
+// (absent < 0: all of them).  With one CTA absent the barrier never completes, so every
+// waiting CTA gives up after limit_ns, records CGH_ERR_TIMEOUT and returns.
+__global__ void k_grid_barrier_selftest(unsigned* bar, int* status, unsigned long long limit_ns, int absent,
+                                        int* crossed) {
+  if ((int)blockIdx.x == absent) return;
+  if (sel_grid_barrier(bar, status, limit_ns) && threadIdx.x == 0) atomicAdd(crossed, 1);
+}
+
+cudaError_t launch_grid_barrier_selftest(unsigned* bar, int* status, int* crossed, int ctas,
+                                         unsigned long long limit_ns, int absent, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(bar, 0, sizeof(unsigned), st);
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(ctas);
+  cfg.blockDim = dim3(32);
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  e = cudaLaunchKernelEx(&cfg, k_grid_barrier_selftest, bar, status, limit_ns, absent, crossed);
+  return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 template <bool FLAGS>
@@ -819,7 +845,7 @@ __global__ void __launch_bounds__(256, 1) k_direct_lut(
     const float2* __restrict__ tab, int tab_len, int tab_off, const int32_t* __restrict__ coef,
     const int32_t* __restrict__ l0, const int32_t* __restrict__ l1, const int32_t* __restrict__ l2,
     const int32_t* __restrict__ l3, const int32_t* __restrict__ d_counts, int H, int W, int Z, int s,
-    float2* __restrict__ holo, int HH, int HW, int use_atomic) {
+    float2* __restrict__ holo, int HH, int HW, int use_atomic, int* status) {
   // Row factors staged as (x, x, -y, y) and column factors as (x, y, y, x): a complex
   // multiply-accumulate is then two packed FP32x2 FMAs, (x,x)*(cx,cy) + (-y,y)*(cy,cx).
   extern __shared__ float4 dl_smem[];
@@ -839,7 +865,8 @@ __global__ void __launch_bounds__(256, 1) k_direct_lut(
   for (int li = 0; li < 4; ++li) {
     const int level = li == 0 ? 3 : li;
     const bool lll = li == 0;
-    const int cnt = max(0, d_counts[2 * li]);
+    const int cnt = clamp_list_count(d_counts[2 * li], Z * (H >> level) * (W >> level),
+                                     blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 ? status : nullptr);
     const int e0 = (int)((long long)cnt * split / nsplit);
     const int e1 = (int)((long long)cnt * (split + 1) / nsplit);
     const int per = lll ? DL_KC : DL_KC / 2;  // entries per chunk
@@ -964,6 +991,6 @@ cudaError_t launch_direct_lut(const cgh_plan* p, const int32_t* coef, const int3
   // holo must be zero (or hold the previous hologram) when S > 1: atomics accumulate.
   k_direct_lut<<<grid, 256, smem, st>>>(p->d_tab, p->tab_len, p->tab_off, coef, lists[0], lists[1],
                                         lists[2], lists[3], d_counts, p->obj_h, p->obj_w, p->n_layers, p->s, holo,
-                                        p->holo_h, p->holo_w, 1);
+                                        p->holo_h, p->holo_w, 1, p->d_status);
   return cudaGetLastError();
 }

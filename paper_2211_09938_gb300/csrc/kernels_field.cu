@@ -137,21 +137,11 @@ __global__ void k_amplitude_backward(const float2* __restrict__ F, const uint8_t
   gF[(size_t)z * n + p] = out;
 }
 
-// Adjoint of the progressive operator on one 8x8 block of one layer: x = Re R_z, then the
-// layer's progressive approximation (3-level Haar, unselected LLL / detail blocks zeroed,
-// inverse), kept where the pixel belongs to layer z.  The approximation is an orthogonal
-// projection in the Haar basis, hence its own adjoint.
-__global__ void k_adjoint_project(const float2* __restrict__ F, const uint8_t* __restrict__ L, TcFlags fl, int H,
-                                  int W, int Z, float* __restrict__ grad) {
-  const int bx = blockIdx.x * blockDim.x + threadIdx.x, by = blockIdx.y * blockDim.y + threadIdx.y;
-  const int z = blockIdx.z;
-  if (bx >= (W >> 3) || by >= (H >> 3)) return;
-  float a[8][8];
-  const float2* Fz = F + (size_t)z * H * W;
-#pragma unroll
-  for (int r = 0; r < 8; ++r)
-#pragma unroll
-    for (int c = 0; c < 8; ++c) a[r][c] = Fz[(size_t)(8 * by + r) * W + 8 * bx + c].x;
+// The progressive approximation P_z of one 8x8 block of layer z, in place: 3-level Haar,
+// LLL and detail coefficients of blocks outside the layer's lists set to zero (flags),
+// inverse Haar.  It is an orthogonal projection in the Haar basis, hence self-adjoint.
+__device__ __forceinline__ void haar_project_block(float (&a)[8][8], const TcFlags& fl, int H, int W, int z,
+                                                   int by, int bx) {
   // forward: levels 1..3 in place on the low band, detail kept or dropped per flags
   float s1[4][4], x1[4][4], y1[4][4], d1[4][4];
 #pragma unroll
@@ -206,10 +196,55 @@ __global__ void k_adjoint_project(const float2* __restrict__ F, const uint8_t* _
     for (int c = 0; c < 8; ++c) {
       const int pr = r >> 1, pc = c >> 1;
       const float sx = (c & 1) ? -1.f : 1.f, sy = (r & 1) ? -1.f : 1.f;
-      const float v = 0.25f * (t1[pr][pc] + sx * x1[pr][pc] + sy * y1[pr][pc] + sx * sy * d1[pr][pc]);
-      const size_t o = (size_t)(8 * by + r) * W + 8 * bx + c;
-      if (L[o] == z) grad[o] = v;
+      a[r][c] = 0.25f * (t1[pr][pc] + sx * x1[pr][pc] + sy * y1[pr][pc] + sx * sy * d1[pr][pc]);
     }
+}
+
+// Adjoint of the progressive operator on one 8x8 block of one layer: x = Re R_z, then the
+// layer's progressive approximation, kept where the pixel belongs to layer z.
+__global__ void k_adjoint_project(const float2* __restrict__ F, const uint8_t* __restrict__ L, TcFlags fl, int H,
+                                  int W, int Z, float* __restrict__ grad) {
+  const int bx = blockIdx.x * blockDim.x + threadIdx.x, by = blockIdx.y * blockDim.y + threadIdx.y;
+  const int z = blockIdx.z;
+  if (bx >= (W >> 3) || by >= (H >> 3)) return;
+  float a[8][8];
+  const float2* Fz = F + (size_t)z * H * W;
+#pragma unroll
+  for (int r = 0; r < 8; ++r)
+#pragma unroll
+    for (int c = 0; c < 8; ++c) a[r][c] = Fz[(size_t)(8 * by + r) * W + 8 * bx + c].x;
+  haar_project_block(a, fl, H, W, z, by, bx);
+#pragma unroll
+  for (int r = 0; r < 8; ++r)
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      const size_t o = (size_t)(8 * by + r) * W + 8 * bx + c;
+      if (L[o] == z) grad[o] = a[r][c];
+    }
+}
+
+// The progressive operator's object side for a real object x (its transpose is
+// k_adjoint_project): the layer plane x [layer = z], projected by P_z, written as the
+// complex layer field F_z (imaginary part 0) over the whole block.
+__global__ void k_forward_project(const float* __restrict__ x, const uint8_t* __restrict__ L, TcFlags fl, int H,
+                                  int W, int Z, float2* __restrict__ F) {
+  const int bx = blockIdx.x * blockDim.x + threadIdx.x, by = blockIdx.y * blockDim.y + threadIdx.y;
+  const int z = blockIdx.z;
+  if (bx >= (W >> 3) || by >= (H >> 3)) return;
+  float a[8][8];
+#pragma unroll
+  for (int r = 0; r < 8; ++r)
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      const size_t o = (size_t)(8 * by + r) * W + 8 * bx + c;
+      a[r][c] = L[o] == z ? x[o] : 0.f;
+    }
+  haar_project_block(a, fl, H, W, z, by, bx);
+  float2* Fz = F + (size_t)z * H * W;
+#pragma unroll
+  for (int r = 0; r < 8; ++r)
+#pragma unroll
+    for (int c = 0; c < 8; ++c) Fz[(size_t)(8 * by + r) * W + 8 * bx + c] = make_float2(a[r][c], 0.f);
 }
 
 __global__ void k_phase_to_field(const float* __restrict__ phase, float2* __restrict__ field, long long n) {
@@ -549,6 +584,21 @@ int field_adjoint(const cgh_plan* p, const float2* grad_holo, const int32_t* con
   dim3 blk(32, 4), grid((f->No / 8 + 31) / 32, (f->No / 8 + 3) / 4, f->Z);
   k_adjoint_project<<<grid, blk, 0, st>>>(f->F, L, fl, f->No, f->No, f->Z, grad_obj);
   return cgh_cuda_check(cudaGetLastError(), "adjoint: projection");
+}
+
+int field_forward(const cgh_plan* p, const float* obj, const int32_t* const* lists, const int32_t* d_counts,
+                  const uint8_t* L, float2* holo, int accumulate, cudaStream_t st) {
+  int rc = field_ensure(p, st);
+  if (rc != CGH_OK) return rc;
+  cgh_field_state* f = p->fs;
+  TcFlags fl;
+  rc = tc_build_flags(p, lists, d_counts, &fl, st);
+  if (rc != CGH_OK) return rc;
+  dim3 blk(32, 4), grid((f->No / 8 + 31) / 32, (f->No / 8 + 3) / 4, f->Z);
+  k_forward_project<<<grid, blk, 0, st>>>(obj, L, fl, f->No, f->No, f->Z, f->F);
+  rc = cgh_cuda_check(cudaGetLastError(), "progressive apply: projection");
+  if (rc != CGH_OK) return rc;
+  return field_propagate(p, f->F, holo, accumulate, st);
 }
 
 extern "C" int cgh_phase_to_field(const float* phase, float* field, long long n, void* stream) {

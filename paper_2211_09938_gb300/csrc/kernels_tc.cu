@@ -20,14 +20,15 @@
 
 __global__ void k_tc_scatter(const int32_t* __restrict__ l0, const int32_t* __restrict__ l1,
                              const int32_t* __restrict__ l2, const int32_t* __restrict__ l3,
-                             const int32_t* __restrict__ d_counts, TcFlags fl, int H, int W, int Z) {
+                             const int32_t* __restrict__ d_counts, TcFlags fl, int H, int W, int Z,
+                             int* status) {
   pdl_wait();
   pdl_trigger();
   const int li = blockIdx.y;
   const int32_t* lst = li == 0 ? l0 : li == 1 ? l1 : li == 2 ? l2 : l3;
   const int level = li == 0 ? 3 : li;
-  const int cnt = d_counts[2 * li];
   const int hl = H >> level, wl = W >> level;
+  const int cnt = clamp_list_count(d_counts[2 * li], Z * hl * wl, blockIdx.x == 0 ? status : nullptr);
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < cnt; e += gridDim.x * blockDim.x) {
     const int ent = lst[e];
     const int z = (ent >> 24) & 0x7F, by = (ent >> 12) & 0xFFF, bx = ent & 0xFFF;
@@ -387,7 +388,7 @@ static int tc_prep(const cgh_plan* p, const int32_t* coef, const int32_t* const*
     if (t->flags_dirty) TC_CK(cudaMemsetAsync(t->flags, 0, t->flags_bytes, st), "tc: clear flags");
     t->flags_dirty = 1;
     TC_CK(launch_pdl(k_tc_scatter, dim3(64, 4), dim3(256), 0, st, lists[0], lists[1], lists[2], lists[3],
-                     d_counts, t->fl, H, W, Z),
+                     d_counts, t->fl, H, W, Z, p->d_status),
           "tc: scatter");
   }
   TC_CK(launch_pdl(k_tc_compact, dim3(Z), dim3(1024), 0, st, t->fl, H, W, Z, p->contraction, t->rows, t->cols,
@@ -713,7 +714,7 @@ static int batch_run(cgh_batch* b, cudaStream_t st) {
     if (!done)
       TC_CK(launch_pdl(k_tc_scatter, dim3(64, 4), dim3(256), 0, st, b->lists[4 * i], b->lists[4 * i + 1],
                        b->lists[4 * i + 2], b->lists[4 * i + 3], (const int32_t*)(b->counts + 8 * i), t->fl,
-                       p->obj_h, p->obj_w, p->n_layers),
+                       p->obj_h, p->obj_w, p->n_layers, p->d_status),
             "batch: scatter");
     const int rc = tc_prep<F16>(p, b->coeffs[i], b->lists + 4 * i, b->counts + 8 * i, st, true);
     if (rc != CGH_OK) return rc;
@@ -781,7 +782,7 @@ int tc_progressive_step(const cgh_plan* p, const uint8_t* sal, const uint8_t* L,
   prof_mark(p, CGH_PROF_SELECT, 1, st);
   if (!done)
     TC_CK(launch_pdl(k_tc_scatter, dim3(64, 4), dim3(256), 0, st, lists[0], lists[1], lists[2], lists[3], d_counts,
-                     t->fl, p->obj_h, p->obj_w, p->n_layers),
+                     t->fl, p->obj_h, p->obj_w, p->n_layers, p->d_status),
           "tc: scatter");
   if (form == CGH_FORM_TC_FP16X3) return tc_run<true>(p, coef, lists, d_counts, holo, accumulate, st, true, coef_ready);
   if (form == CGH_FORM_TC_FP16X2)
@@ -798,7 +799,7 @@ int tc_build_flags(const cgh_plan* p, const int32_t* const* lists, const int32_t
   t->flags_dirty = 1;
   if (rc != CGH_OK) return rc;
   k_tc_scatter<<<dim3(64, 4), 256, 0, st>>>(lists[0], lists[1], lists[2], lists[3], d_counts, t->fl, p->obj_h,
-                                          p->obj_w, p->n_layers);
+                                          p->obj_w, p->n_layers, p->d_status);
   rc = cgh_cuda_check(cudaGetLastError(), "flags: scatter");
   if (rc != CGH_OK) return rc;
   *out = t->fl;

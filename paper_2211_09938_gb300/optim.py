@@ -51,6 +51,30 @@ def reconstruct_amplitude(phase, plan, layer, checkpoint=True):
     return PhaseReconstruction.apply(phase, plan, layer, checkpoint)
 
 
+class ProgressiveOperator(torch.autograd.Function):
+    """object [obj, obj] float32  ->  progressive hologram [holo, holo] complex64:
+    H = sum_z E_z P_z(object [layer = z]) E_z^T (Eq. 3, Section 2 steps 2-5, for a real
+    object), forward by cgh_progressive_apply.  The map is linear in the object, so the
+    backward is its adjoint, cgh_adjoint: for a cotangent G of H (real-pair convention,
+    dL/dRe H + j dL/dIm H, as torch passes it) the object gradient is
+    Re(A^H G) = [layer = z] P_z Re(R_z), R_z the back-propagation of G to layer z."""
+
+    @staticmethod
+    def forward(ctx, obj, plan, lists, counts, layer):
+        ctx.plan, ctx.lists, ctx.counts, ctx.layer = plan, lists, counts, layer
+        return plan.progressive_apply(obj.contiguous().float(), lists, counts, layer)
+
+    @staticmethod
+    def backward(ctx, g_holo):
+        g = ctx.plan.adjoint(g_holo.contiguous().to(torch.complex64), ctx.lists, ctx.counts, ctx.layer)
+        return g, None, None, None, None
+
+
+def progressive_hologram(obj, plan, lists, counts, layer):
+    """Differentiable progressive hologram of a real object (see ProgressiveOperator)."""
+    return ProgressiveOperator.apply(obj, plan, lists, counts, layer)
+
+
 def weighted_loss(amp, target, weight, kappa):
     """sum w (amp / kappa - target)^2, accumulated in float64."""
     d = amp.double() / kappa - target.double()

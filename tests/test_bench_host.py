@@ -2,27 +2,41 @@
 reported only while the kernel's sources still hash to the value recorded with it."""
 import json
 import os
-import shutil
 
 import bench
 
 
 def test_traffic_follows_the_sources(tmp_path, monkeypatch):
+    import hashlib
     root = tmp_path
     os.makedirs(root / "profiles")
-    entry = json.load(open(os.path.join(bench.ROOT, "profiles", "traffic.json")))
-    key = "k_tc_gemm<KIND_CC,EPI_H> (stage 2)"
-    for f in entry[key]["src_files"]:
-        os.makedirs(root / os.path.dirname(f), exist_ok=True)
-        shutil.copy(os.path.join(bench.ROOT, f), root / f)
-    shutil.copy(os.path.join(bench.ROOT, "profiles", "traffic.json"), root / "profiles" / "traffic.json")
+    os.makedirs(root / "src")
+    files = ["src/a.cu", "src/b.cuh"]
+    for k, f in enumerate(files):
+        (root / f).write_text(f"// kernel source {k}\n")
+    h = hashlib.sha256()
+    for f in files:
+        h.update((root / f).read_bytes())
+    key = "k_example"
+    entry = {key: {"bytes": 12345.0, "source": "profiles/k_example.md", "src_files": files,
+                   "src_hash": h.hexdigest()[:16]}}
+    (root / "profiles" / "traffic.json").write_text(json.dumps(entry))
     monkeypatch.setattr(bench, "ROOT", str(root))
-    assert bench.kernel_traffic(key) == entry[key]["bytes"]
+    assert bench.kernel_traffic(key) == 12345.0
     # any change to a source the counters were taken from makes the figure stale
-    with open(root / entry[key]["src_files"][0], "a") as fh:
+    with open(root / files[1], "a") as fh:
         fh.write("\n")
     assert bench.kernel_traffic(key) is None
     assert bench.kernel_traffic("no such kernel") is None
+
+
+def test_committed_traffic_entries_are_well_formed():
+    entry = json.load(open(os.path.join(bench.ROOT, "profiles", "traffic.json")))
+    for key, e in entry.items():
+        assert e["bytes"] > 0 and len(e["src_hash"]) == 16, key
+        assert os.path.exists(os.path.join(bench.ROOT, e["source"])), key
+        for f in e["src_files"]:
+            assert os.path.exists(os.path.join(bench.ROOT, f)), (key, f)
 
 
 def test_whole_job_value_is_all_ranks_over_the_slowest():

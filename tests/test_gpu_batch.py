@@ -43,7 +43,8 @@ def test_batch_matches_single_scene_and_oracle(form):
         Href = O.progressive_hologram(sc["intensity"], sc["layer"], ref_lists, g)
         err = O.rel_l2(got[k], Href)
         print(f"batch {form} scene {k} ({sc['intensity'].shape[0]}->{sc['holo'][0]}, Z={g.n_layers}): {err:.2e}")
-        assert err <= 1e-5
+        # measured max: bf16x3 4.4e-6, fp16x3 2.3e-6 (the benchmark spec bars 1e-3 / 1e-5)
+        assert err <= (1.5e-5 if form == "tc_bf16x3" else 7e-6)
         with torch.cuda.stream(st):
             coeffs = plans[k].haar_decompose(I[k], L[k], stream=st)
             lists, counts = plans[k].progressive_lists(S[k], L[k], scenes.THRESHOLDS_U8, stream=st)
@@ -64,3 +65,56 @@ def test_batch_matches_single_scene_and_oracle(form):
     for k in range(len(scs)):
         assert O.rel_l2(Hs[k].cpu().numpy(), got[k]) <= 1e-5
     batch.close()
+
+
+def _oracle_progressive_separable(sc):
+    """The FP64 progressive hologram as the point-wise hologram of the progressively
+    reconstructed object (pinned equal to the residual-map form), computed separably:
+    fast enough for 1024x1024 objects at 2048x2048 holograms."""
+    g = O.geometry_of(sc)
+    lists = O.progressive_lists(sc["saliency"], sc["layer"], g.n_layers, scenes.THRESHOLDS_U8)
+    A = O.progressive_object(sc["intensity"], sc["layer"], lists, g.n_layers)
+    return O.pointwise_hologram_separable(A / 64.0, g)
+
+
+@pytest.mark.parametrize("form,bar", [("tc_fp16x3", 1e-5), ("tc_bf16x3", 5e-5)])
+def test_batch_at_bench_sizes(form, bar):
+    """The sizes the 64-scene batch benchmark runs: a 512->1024 scene with 16 layers and a
+    1024->2048 scene with 28 layers, beside small and mid scenes of very different K, in one
+    batch with the autotuned stage-2 split.  Stage-2 work units then span scenes of very
+    different K.  Every hologram is checked against the FP64 oracle."""
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2211_09938_gb300 import Plan, autotune
+    from paper_2211_09938_gb300.cgh import Batch
+    scs = [scenes.random_scene(611, 512, 1024, 16, sal_fraction=0.3),
+           scenes.random_scene(612, 1024, 2048, 28, sal_fraction=0.45),
+           scenes.random_scene(613, 128, 256, 4, sal_fraction=0.05),
+           scenes.random_scene(614, 256, 512, 32, sal_fraction=0.6)]
+    st = torch.cuda.Stream()
+    with torch.cuda.stream(st):
+        plans = [Plan.for_scene(sc, stream=st) for sc in scs]
+        I = [torch.from_numpy(sc["intensity"]).cuda() for sc in scs]
+        L = [torch.from_numpy(sc["layer"]).cuda() for sc in scs]
+        S = [torch.from_numpy(sc["saliency"]).cuda() for sc in scs]
+        Hs = [torch.empty(sc["holo"], dtype=torch.complex64, device="cuda") for sc in scs]
+        batch = Batch(plans, I, L, S, scenes.THRESHOLDS_U8, Hs, form=form, stream=st)
+    tuned = autotune.tune_batch(batch, plans, form, st)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=st):
+        batch.run(stream=st)
+    for h in Hs:
+        h.fill_(float("nan"))
+    with torch.cuda.stream(st):
+        g.replay()
+    st.synchronize()
+    for k, sc in enumerate(scs):
+        err = O.rel_l2(Hs[k].cpu().numpy(), _oracle_progressive_separable(sc))
+        print(f"batch {form} ({tuned}) scene {k} ({sc['intensity'].shape[0]}->{sc['holo'][0]}, "
+              f"Z={len(sc['z'])}): rel-L2 {err:.2e}")
+        assert err <= bar, (k, err)
+    assert all(p.status() == 0 for p in plans)
+    batch.close()
+    for p in plans:
+        p.close()

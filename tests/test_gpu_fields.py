@@ -211,3 +211,84 @@ def test_phase_optimisation_decreases_and_resumes_bit_identically(torch_cuda, tm
         c.step()
     assert c.step_count == 6
     assert torch.equal(c.phase.detach(), a.phase.detach())
+
+
+@pytest.mark.parametrize("name,make", [
+    ("graded_64_to_128_z4", lambda: scenes.random_scene(171, 64, 128, 4, graded=True)),
+    ("paper_512_to_1024_z16", lambda: scenes.paper_scene()),
+])
+def test_progressive_apply_matches_oracle_and_integer_path(torch_cuda, name, make):
+    """cgh_progressive_apply on a real object against the FP64 oracle's real-object
+    operator; on the integer intensity it is the hologram cgh_progressive_hologram gives."""
+    torch = torch_cuda
+    from paper_2211_09938_gb300 import Plan
+    sc = make()
+    g = O.geometry_of(sc)
+    plan = Plan.for_scene(sc)
+    L = torch.from_numpy(sc["layer"]).cuda()
+    S = torch.from_numpy(sc["saliency"]).cuda()
+    I = torch.from_numpy(sc["intensity"]).cuda()
+    lists, counts = plan.progressive_lists(S, L, scenes.THRESHOLDS_U8)
+    ref_lists = O.progressive_lists(sc["saliency"], sc["layer"], g.n_layers, scenes.THRESHOLDS_U8)
+    rng = np.random.default_rng(172)
+    x = (sc["intensity"].astype(np.float64) + rng.normal(size=sc["intensity"].shape) * 7.3).astype(np.float32)
+    H = plan.progressive_apply(torch.from_numpy(x).cuda(), lists, counts, L)
+    Hi = plan.progressive_apply(I.float(), lists, counts, L)
+    Hp = plan.progressive_hologram(plan.haar_decompose(I, L), lists, counts, form="tc_fp16x3")
+    torch.cuda.synchronize()
+    err = O.rel_l2(H.cpu().numpy(), O.progressive_hologram_real(x.astype(np.float64), sc["layer"], ref_lists, g))
+    Href = O.progressive_hologram(sc["intensity"], sc["layer"], ref_lists, g)
+    erri = O.rel_l2(Hi.cpu().numpy(), Href)
+    print(f"progressive_apply {name}: real object {err:.2e}, integer object {erri:.2e}, "
+          f"vs progressive_hologram {O.rel_l2(Hi.cpu().numpy(), Hp.cpu().numpy()):.2e}")
+    assert err <= TOL and erri <= TOL
+    assert O.rel_l2(Hi.cpu().numpy(), Hp.cpu().numpy()) <= TOL
+    assert plan.status() == 0
+
+
+def test_progressive_autograd_vs_oracle_adjoint_and_finite_differences(torch_cuda):
+    """torch.autograd through ProgressiveOperator (forward cgh_progressive_apply, backward
+    cgh_adjoint): the object gradient of a nonlinear loss of the hologram matches the FP64
+    oracle's adjoint applied to the same cotangent, and central finite differences
+    (h = 1e-3) of the loss evaluated with the FP64 oracle's forward on 64 random entries."""
+    torch = torch_cuda
+    from paper_2211_09938_gb300 import Plan, optim
+    sc = scenes.random_scene(181, 32, 64, 3, graded=True)
+    g = O.geometry_of(sc)
+    plan = Plan.for_scene(sc)
+    L = torch.from_numpy(sc["layer"]).cuda()
+    S = torch.from_numpy(sc["saliency"]).cuda()
+    lists, counts = plan.progressive_lists(S, L, scenes.THRESHOLDS_U8)
+    ref_lists = O.progressive_lists(sc["saliency"], sc["layer"], g.n_layers, scenes.THRESHOLDS_U8)
+    rng = np.random.default_rng(182)
+    x0 = sc["intensity"].astype(np.float64) / 255.0 + 0.1 * rng.normal(size=sc["intensity"].shape)
+    W = rng.uniform(0.5, 2.0, size=sc["holo"])
+    T = cplx(rng, *sc["holo"]).astype(np.complex128) * 20.0
+
+    def loss_np(x):
+        H = O.progressive_hologram_real(x, sc["layer"], ref_lists, g)
+        return float(np.sum(W * np.abs(H - T) ** 2))
+
+    x = torch.from_numpy(x0.astype(np.float32)).cuda().requires_grad_(True)
+    H = optim.progressive_hologram(x, plan, lists, counts, L)
+    Wd = torch.from_numpy(W).cuda()
+    Td = torch.from_numpy(T).cuda()
+    loss = (Wd * (H.to(torch.complex128) - Td).abs() ** 2).sum()
+    loss.backward()
+    grad = x.grad.double().cpu().numpy()
+    # the oracle adjoint of the cotangent dL/dH = 2 W (H - T) at the FP64 forward
+    Hn = O.progressive_hologram_real(x0, sc["layer"], ref_lists, g)
+    want = O.progressive_adjoint(2.0 * W * (Hn - T), sc["layer"], ref_lists, g)
+    err = O.rel_l2(grad, want)
+    idx = rng.choice(x0.size, size=64, replace=False)
+    h = 1e-3
+    fd = []
+    for k in idx:
+        e = np.zeros(x0.size)
+        e[k] = h
+        e = e.reshape(x0.shape)
+        fd.append((loss_np(x0 + e) - loss_np(x0 - e)) / (2 * h))
+    fd = np.array(fd)
+    err_fd = float(np.linalg.norm(grad.reshape(-1)[idx] - fd) / np.linalg.norm(fd))
+    print(f"object gradient: vs oracle adjoint {err:.2e}, vs central differences {err_fd:.2e}")
+    assert err <= 1e-3 and err_fd <= 1e-3

@@ -2,8 +2,9 @@
 32 layers.  Every form against the FP64 oracle, for the full hologram and layer by layer
 (each layer's own work lists), with rel-L2 and max-abs error printed.
 Bars: direct FP32 <= 1e-5 rel-L2; per layer every form <= 1e-5 (fp16/bf16 hi+lo: 1e-5 /
-1e-3); the full 32-layer hologram with short tensor-memory accumulation chains <= 1e-5 for
-both split forms, with the default long chains <= 1e-4 (fp16) and <= 1e-3 (bf16)."""
+1e-3); the full 32-layer hologram with the default chains <= 1e-5 for fp16 hi+lo (chains of
+at most 32 K steps; measured 6.7e-6) and <= 7e-5 for bf16 hi+lo (chains up to 128; measured
+2.2e-5, the benchmark spec bar 1e-3); with 8-step chains <= 1e-5 for both."""
 import numpy as np
 import pytest
 
@@ -12,7 +13,7 @@ from synth import scenes
 
 pytestmark = pytest.mark.gpu
 
-BARS = {"direct_lut": 1e-5, "tc_fp16x3": 1e-5, "tc_bf16x3": 1e-3}
+BARS = {"direct_lut": 3e-6, "tc_fp16x3": 8e-6, "tc_bf16x3": 1.6e-5}  # per layer, ~3x achieved
 
 
 @pytest.fixture(scope="module")
@@ -80,6 +81,7 @@ def test_precision_full_and_per_layer(setup):
     for form, bar in BARS.items():
         assert worst[form] <= bar, (form, worst[form])
     assert full["direct_lut"] <= 1e-5
-    # default chains (up to ~110 K steps here): the split forms stay well inside the 1e-3 bar
-    assert full["tc_fp16x3"] <= 1e-4 and full["tc_bf16x3"] <= 1e-3
+    # default chains: fp16 hi+lo caps them at 32 K steps and meets the FP32 bar; bf16 hi+lo
+    # runs up to 128 K steps (bar 1e-3, regression margin 3x)
+    assert full["tc_fp16x3"] <= 1e-5 and full["tc_bf16x3"] <= 7e-5
     assert short["tc_fp16x3"] <= 1e-5 and short["tc_bf16x3"] <= 1e-5

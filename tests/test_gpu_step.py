@@ -13,8 +13,16 @@ from synth import scenes
 
 pytestmark = pytest.mark.gpu
 
+# the benchmark spec bars: 1e-5 (fp16 hi+lo, the FP32 bar) and 1e-3 (bf16 hi+lo); the per-scene
+# regression bars sit at about 3x what each form achieves (never above its benchmark spec bar).
 BF16X3_TOL = 1e-3
 FP16X3_TOL = 1e-5
+SCENE_TOL = {  # scene: (bf16x3, fp16x3, fp16x2); achieved bf16x3 1.07e-5 / 2.1e-6 / 2.2e-6 / 2.35e-5
+    "paper_512_z16": (3.5e-5, 1e-5, 1e-3),
+    "graded_64_s2_z5": (7e-6, 2e-6, 5e-4),
+    "single_layer_32_s2": (7e-6, 2e-6, 6e-4),
+    "large_table_512_z40": (7e-5, 1e-5, 8e-4),
+}
 
 
 @pytest.fixture(scope="module")
@@ -75,7 +83,7 @@ def test_step_matches_oracle_and_two_calls(torch_cuda, name, form, tol):
     Href = O.progressive_hologram(sc["intensity"], sc["layer"], ref_lists, O.geometry_of(sc))
     err = O.rel_l2(H.cpu().numpy(), Href)
     print(f"{form} {name}: rel-L2 {err:.3e}")
-    assert err <= tol
+    assert err <= min(tol, SCENE_TOL[name][("tc_bf16x3", "tc_fp16x3", "tc_fp16x2").index(form)])
 
     dplan, I, L, S, coeffs = _inputs(torch, sc, flags=Plan.DETERMINISTIC)
     H, lists, counts = dplan.progressive_step(S, L, coeffs, scenes.THRESHOLDS_U8, form=form)

@@ -2,8 +2,9 @@
 progressive hologram against the FP64 oracle.
 
 Bars: the diagnostic GEMM is exact up to FP32 accumulation order (operands are exact
-bf16/fp16 values); the progressive hologram meets rel-L2 <= 1e-3 for the bf16 hi+lo
-path and <= 1e-5 for the fp16 hi+lo path."""
+bf16/fp16 values); the progressive hologram meets the benchmark spec bars (rel-L2 <= 1e-3 for
+the bf16 hi+lo path, <= 1e-5 for the fp16 hi+lo path) with regression margins of about 3x
+what each form achieves."""
 import numpy as np
 import pytest
 
@@ -12,9 +13,14 @@ from synth import scenes
 
 pytestmark = pytest.mark.gpu
 
-BF16X3_TOL = 1e-3
+# The benchmark spec bars are 1e-5 rel-L2 (FP32) and 1e-3 (bf16 split); the regression bars
+# below sit at about 3x what each form achieves (never above its benchmark spec bar), so a loss
+# of accuracy fails a test long before a bar is crossed.  Paper scale: bf16x3 1.07e-5,
+# fp16x3 6.5e-6, fp16x2 2.9e-4; small scenes: bf16x3 <= 4.5e-6, fp16x3 <= 5.6e-7.
+BF16X3_TOL = 3.5e-5
 FP16X3_TOL = 1e-5
 FP16X2_TOL = 1e-3  # fringe rounded once to fp16 (unit roundoff 2^-11), data hi+lo
+SMALL_TOL = {"tc_bf16x3": 1.5e-5, "tc_fp16x3": 2e-6, "tc_fp16x2": 8e-4}
 
 
 @pytest.fixture(scope="module")
@@ -86,7 +92,7 @@ def test_progressive_tc(torch_cuda, name, form, tol):
     Href = O.progressive_hologram(sc["intensity"], sc["layer"], ref_lists, O.geometry_of(sc))
     err = O.rel_l2(H, Href)
     print(f"{form} {name}: rel-L2 {err:.3e}")
-    assert err <= tol
+    assert err <= min(tol, SMALL_TOL[form])
 
 
 @pytest.mark.parametrize("form,tol", [("tc_bf16x3", BF16X3_TOL), ("tc_fp16x3", FP16X3_TOL),

@@ -487,6 +487,29 @@ def test_adjoint_dot_product():
     assert abs(lhs - rhs) <= 1e-10 * max(1.0, abs(lhs))
 
 
+def test_progressive_hologram_real_integer_case_linearity_and_adjoint():
+    """progressive_hologram_real: on an integer object it equals the residual-map form
+    (progressive_hologram, pinned by P1-P5); it is linear over real objects; and
+    <F(x), G> = <x, F^*(G)> with progressive_adjoint for a real, non-integer x."""
+    n = 16
+    rng = np.random.default_rng(23)
+    sc = scenes.random_scene(23, n, 2 * n, 3, graded=True)
+    g = O.geometry_of(sc)
+    lists = O.progressive_lists(sc["saliency"], sc["layer"], 3, scenes.THRESHOLDS_U8)
+    Hi = O.progressive_hologram(sc["intensity"], sc["layer"], lists, g)
+    assert O.rel_l2(O.progressive_hologram_real(sc["intensity"].astype(np.float64), sc["layer"], lists, g),
+                    Hi) < 1e-12
+    x = rng.normal(size=(n, n)) * 50.0
+    y = rng.normal(size=(n, n)) * 50.0
+    Fx = O.progressive_hologram_real(x, sc["layer"], lists, g)
+    Fy = O.progressive_hologram_real(y, sc["layer"], lists, g)
+    assert O.rel_l2(O.progressive_hologram_real(2.0 * x - 0.5 * y, sc["layer"], lists, g), 2.0 * Fx - 0.5 * Fy) < 1e-12
+    G = rng.normal(size=(2 * n, 2 * n)) + 1j * rng.normal(size=(2 * n, 2 * n))
+    lhs = np.real(np.vdot(Fx, G))
+    rhs = float(np.sum(x * O.progressive_adjoint(G, sc["layer"], lists, g)))
+    assert abs(lhs - rhs) <= 1e-10 * max(1.0, abs(lhs))
+
+
 def test_reconstruct_is_adjoint_of_pointwise():
     rng = np.random.default_rng(22)
     g = tiny_geom(8, 2, 2)
