@@ -329,8 +329,19 @@ def run_phase_opt_workload(stream, steps):
     torch.cuda.synchronize()
     ms = a.elapsed_time(b) / steps
     plan.close()
+    # tensor-core work of one Adam step: per hologram and layer, the reconstruction
+    # (8 Nh^2 No + 8 Nh No^2 flop for the two complex products), its recomputation in the
+    # backward (checkpointing) and the propagation of the field cotangents (the same sizes),
+    # each as 3 bf16 hi+lo products
+    nh, no, nz, nb = 1024, 512, 8, 4
+    flop = 3 * nb * nz * 3 * 8.0 * (nh * nh * no + nh * no * no)
+    pk = peaks() or {}
+    peak_tf = pk.get("bf16_tflops_sustained", pk.get("bf16_tflops", 1700.0))
+    roof = {"bound": "tensor", "flop_per_adam_step": flop, "achieved": flop / (ms / 1e3) / 1e12,
+            "peak": peak_tf, "unit": "TFLOP/s", "frac": flop / (ms / 1e3) / 1e12 / peak_tf,
+            "peak_note": "measured cuBLAS bf16 dense, sustained (a seconds-long loop)"}
     return {"batch": 4, "holo": 1024, "layers": 8, "adam_steps": steps + 1, "adam_steps_timed": steps,
-            "ms_per_adam_step": ms,
+            "ms_per_adam_step": ms, "roofline": roof,
             "adam_steps_per_s": 1e3 / ms, "loss_first": l0, "loss_last": l1,
             "note": "forward reconstruction + amplitude backward + propagation per hologram, fields recomputed "
                     "in backward (checkpointing)"}
@@ -436,6 +447,99 @@ def run_rgb_workload(stream, form, flush, reps=10):
     rgb.close()
     return {"form": form, "wavelengths_nm": [w * 1e9 for w in WAVELENGTHS_RGB], "ms_per_colour_frame": ms,
             "value": 3 * UNITS_PER_STEP / (ms / 1e3) / 1e9, "unit": UNIT}
+
+
+def run_precision_workload(stream, flush, forms=("tc_fp16x3", "tc_bf16x3", "tc_fp16x2", "direct_lut"), reps=5):
+    """The precision configuration: the paper-scale 512x512 scene at a 2048x2048 hologram
+    with 32 layers.  Per superposition form: device time of the superposition call (L2
+    flushed before each), Gpoint*px/s, the stage-2 GEMM's roofline fraction (tensor forms),
+    and rel-L2 / max-abs against the FP64 oracle for the full hologram and for every layer
+    (each layer's own work lists).  The oracle's per-layer holograms sum to the full one."""
+    import numpy as np
+    import torch
+    from oracle import cgh_oracle as O
+    from paper_2211_09938_gb300 import Plan
+    from synth import scenes
+    obj, holo, nl = 512, 2048, 32
+    sc = scenes.paper_scene(n_layers=nl, holo=holo)
+    g = O.geometry_of(sc)
+    pk = peaks() or {}
+    peak_tf = pk.get("bf16_tflops", 1900.0)
+    with torch.cuda.stream(stream):
+        plan = Plan.for_scene(sc, stream=stream)
+        I = torch.from_numpy(sc["intensity"]).cuda()
+        L = torch.from_numpy(sc["layer"]).cuda()
+        S = torch.from_numpy(sc["saliency"]).cuda()
+        coeffs = plan.haar_decompose(I, L, stream=stream)
+        lists, counts = plan.progressive_lists(S, L, scenes.THRESHOLDS_U8, stream=stream)
+        H = torch.empty((holo, holo), dtype=torch.complex64, device="cuda")
+    stream.synchronize()
+    c = counts.cpu().numpy()
+    host = [lists[k][:int(c[k, 0])].cpu().numpy() for k in range(4)]
+    per_layer_lists = []
+    for z in range(nl):
+        sel = [x[(x >> 24) == z] for x in host]
+        dl = [torch.from_numpy(np.concatenate([x, np.zeros(1, np.int32)]).astype(np.int32)).cuda() for x in sel]
+        cnt = torch.tensor([[len(x), len(x)] for x in sel], dtype=torch.int32, device="cuda")
+        per_layer_lists.append((sel, dl, cnt))
+    out = {"workload": f"paper-scale scene {obj}x{obj}, {nl} layers z in [0.08,0.20] m, hologram {holo}x{holo}",
+           "forms": {}}
+    got = {}
+    for form in forms:
+        times, st2 = [], []
+        for k in range(reps + 1):
+            plan.profile(True)
+            with torch.cuda.stream(stream):
+                flush.fill_(float(k))
+                e = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+                e[0].record(stream)
+                plan.progressive_hologram(coeffs, lists, counts, holo=H, form=form, stream=stream)
+                e[1].record(stream)
+            prof = plan.profile_read(stream=stream)
+            plan.profile(False)
+            if k:
+                times.append(e[0].elapsed_time(e[1]))
+                st2.append(prof.get("tc_stage2", 0.0))
+        ms = sorted(times)[len(times) // 2]
+        ent = {"superposition_ms": ms, "value": obj * obj * holo * holo / (ms / 1e3) / 1e9, "unit": UNIT}
+        if form != "direct_lut":
+            kr, _ = plan.tc_layer_dims(stream=stream)
+            prods = 2 if form == "tc_fp16x2" else 3
+            flop = prods * 8.0 * holo * holo * sum(kr)
+            k_ms = sorted(st2)[len(st2) // 2]
+            ent["stage2"] = {"ms": k_ms, "achieved_tflops": flop / (k_ms / 1e3) / 1e12,
+                             "frac_of_measured_bf16_peak": flop / (k_ms / 1e3) / 1e12 / peak_tf,
+                             "k_contracted": sum(kr)}
+        got[form] = H.cpu().numpy()
+        layer_h = []
+        for z in range(nl):
+            _, dl, cnt = per_layer_lists[z]
+            with torch.cuda.stream(stream):
+                Hz = plan.progressive_hologram(coeffs, dl, cnt, form=form, stream=stream)
+            stream.synchronize()
+            layer_h.append(Hz.cpu().numpy())
+        ent["_layers"] = layer_h
+        out["forms"][form] = ent
+    plan.close()
+    # the FP64 oracle, layer by layer (its per-layer holograms sum to the full hologram)
+    Href = np.zeros((holo, holo), np.complex128)
+    for z in range(nl):
+        Hz_ref = O.progressive_hologram(sc["intensity"], sc["layer"], per_layer_lists[z][0], g)
+        Href += Hz_ref
+        for form in forms:
+            ent = out["forms"][form]
+            Hz = ent["_layers"][z]
+            ent.setdefault("per_layer_rel_l2", []).append(O.rel_l2(Hz, Hz_ref))
+            ent.setdefault("per_layer_max_abs", []).append(float(np.max(np.abs(Hz - Hz_ref))))
+    for form in forms:
+        ent = out["forms"][form]
+        del ent["_layers"]
+        ent["rel_l2_vs_fp64_oracle"] = O.rel_l2(got[form], Href)
+        ent["max_abs_vs_fp64_oracle"] = float(np.max(np.abs(got[form] - Href)))
+        ent["per_layer_rel_l2_max"] = max(ent["per_layer_rel_l2"])
+    out["max_abs_reference"] = float(np.max(np.abs(Href)))
+    out["bars"] = {"fp32": 1e-5, "bf16_split": 1e-3}
+    return out
 
 
 def run_hbm_paths(stream, flush, reps=5):
@@ -594,7 +698,7 @@ def run_ours(args):
     # two products per real product), timed the same way; its accuracy is reported beside the
     # other forms'
     fast = None
-    if form == "tc_bf16x3" and graph is not None and not args.skip_forms:
+    if form != "direct_lut" and graph is not None and not args.skip_forms:
         with torch.cuda.stream(stream):
             for _ in range(args.warmup):
                 step("tc_fp16x2")
@@ -660,12 +764,16 @@ def run_ours(args):
         roof = {"bound": "tensor", "kernel": "k_tc_gemm<KIND_CC,EPI_H> (stage 2)",
                 "achieved": algo_flop / (k_ms / 1e3) / 1e12, "peak": peak_tf, "unit": "TFLOP/s",
                 "frac": algo_flop / (k_ms / 1e3) / 1e12 / peak_tf,
-                "traffic": kernel_traffic("k_tc_gemm<KIND_CC,EPI_H> (stage 2)") if form == "tc_bf16x3" else None,
-                "traffic_note": "ncu dram__bytes_read.sum + dram__bytes_write.sum per launch "
-                                "(profiles/k_tc_gemm_stage2_paper_scale.md); null if the kernel changed since",
+                "traffic": kernel_traffic(f"k_tc_gemm<KIND_CC,EPI_H> (stage 2, {form})"),
+                "traffic_note": "ncu dram__bytes_read.sum + dram__bytes_write.sum per launch, from "
+                                "profiles/traffic.json (the ncu summary it names); null if the kernel changed "
+                                "since the counters were taken",
                 "peak_note": "measured cuBLAS bf16 dense burst (MEASURED_PEAKS.json); fp16 has the same "
                              "nominal dense rate" if "bf16_tflops" in pk else "fallback 1.9 PFLOP/s",
-                "kernel_ms": k_ms, "k_rows_total": ksum, "k_cols_total": sum(kc)}
+                "kernel_ms": k_ms, "k_contracted": ksum, "k_other_axis": sum(kc),
+                "k_note": "k_contracted: the sum over the layers of the compacted object rows or columns "
+                          "that stage 2 contracts over (the smaller, chosen on the device); k_other_axis: "
+                          "the other one"}
     if form == "direct_lut":
         # FP32 FFMA bound: 8 flop (4 FFMA) per rank-1 term and hologram pixel
         algo_flop = 8.0 * rank1_terms * HOLO * HOLO
@@ -785,6 +893,8 @@ def run_ours(args):
         line["pointcloud_direct"] = pointcloud
     if rank == 0 and not args.skip_hbm_paths:
         line["hbm_paths_8192"] = run_hbm_paths(stream, flush)
+    if rank == 0 and ws == 1 and not args.skip_precision:
+        line["precision"] = run_precision_workload(stream, flush)
     if rank == 0 and not args.skip_rgb:
         line["rgb"] = run_rgb_workload(stream, form if form != "direct_lut" else "tc_bf16x3", flush)
     if rank == 0 and not args.skip_asm:
@@ -865,7 +975,7 @@ def main():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--form", default="tc_bf16x3", choices=["direct_lut", "tc_bf16x3", "tc_fp16x3"])
+    ap.add_argument("--form", default="tc_fp16x3", choices=["direct_lut", "tc_bf16x3", "tc_fp16x3"])
     ap.add_argument("--skip-forms", action="store_true")
     ap.add_argument("--no-graph", action="store_true", help="launch the step eagerly instead of as a CUDA graph")
     ap.add_argument("--skip-batch", action="store_true", help="skip the 64-scene batch measurement")
@@ -878,6 +988,8 @@ def main():
     ap.add_argument("--skip-asm", action="store_true", help="skip the angular-spectrum reconstruction timing")
     ap.add_argument("--skip-rgb", action="store_true", help="skip the three-channel colour frame timing")
     ap.add_argument("--skip-hbm-paths", action="store_true", help="skip the DWT and selection at an 8192^2 object")
+    ap.add_argument("--skip-precision", action="store_true",
+                    help="skip the 2048^2-hologram, 32-layer precision workload")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
