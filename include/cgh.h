@@ -121,6 +121,23 @@ int cgh_plan_set_tuning(cgh_plan* plan, int max_ksteps_per_chain);
  * Results agree to rounding.  Applies to later calls of the plan.  The paper has no
  * counterpart (it superposes block fringes directly).
  */
+/*
+ * cgh_plan_set_stage2_tiles - tile shape of the separable form's stage-2 GEMM.
+ *   CGH_TILES_AUTO  (default) CTA pairs whenever the call splits K stream-K style (not
+ *                   with CGH_PLAN_DETERMINISTIC) and the device holds CTA pairs
+ *   CGH_TILES_CTA   one CTA per 128 x 128 output tile
+ *   CGH_TILES_PAIR  two CTAs of a cluster per 256 x 128 output tile (tcgen05 cta_group::2:
+ *                   each CTA stages its 128 rows of the fringe operand and half of the data
+ *                   operand, so the data operand is staged once per pair); falls back to
+ *                   one CTA per tile where pairs do not apply
+ * Results agree to rounding.  Applies to later calls of the plan.  The paper has no
+ * counterpart (a tuning knob of the GPU contraction).
+ */
+#define CGH_TILES_AUTO 0
+#define CGH_TILES_CTA 1
+#define CGH_TILES_PAIR 2
+int cgh_plan_set_stage2_tiles(cgh_plan* plan, int tiles);
+
 #define CGH_CONTRACT_AUTO 0
 #define CGH_CONTRACT_ROWS 1
 #define CGH_CONTRACT_COLS 2

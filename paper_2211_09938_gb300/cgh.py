@@ -41,6 +41,7 @@ SIGNATURES = {
                              ctypes.POINTER(_D), _I, _I, _P]),
     "cgh_plan_destroy": (_I, [_P]),
     "cgh_plan_set_tuning": (_I, [_P, _I]),
+    "cgh_plan_set_stage2_tiles": (_I, [_P, _I]),
     "cgh_plan_set_contraction": (_I, [_P, _I]),
     "cgh_build_tables": (_I, [_P, _P]),
     "cgh_haar_decompose": (_I, [_P, _P, _P, _P, _P]),
@@ -174,6 +175,13 @@ class Plan:
         """Contraction order of the tensor form (cgh_plan_set_contraction): CONTRACT_AUTO,
         CONTRACT_ROWS or CONTRACT_COLS."""
         check(lib().cgh_plan_set_contraction(self.handle, int(order)))
+
+    TILES_AUTO, TILES_CTA, TILES_PAIR = 0, 1, 2
+
+    def set_stage2_tiles(self, tiles):
+        """cgh_plan_set_stage2_tiles: TILES_AUTO, TILES_CTA (128x128 per CTA) or TILES_PAIR
+        (256x128 per CTA pair, tcgen05 cta_group::2)."""
+        check(lib().cgh_plan_set_stage2_tiles(self.handle, int(tiles)))
 
     def set_tuning(self, max_ksteps_per_chain):
         check(lib().cgh_plan_set_tuning(self.handle, int(max_ksteps_per_chain)))

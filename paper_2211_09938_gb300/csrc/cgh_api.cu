@@ -68,6 +68,13 @@ int cgh_plan_set_tuning(cgh_plan* p, int max_ksteps) {
   return CGH_OK;
 }
 
+int cgh_plan_set_stage2_tiles(cgh_plan* p, int tiles) {
+  if (!p || tiles < CGH_TILES_AUTO || tiles > CGH_TILES_PAIR)
+    return cgh_fail(CGH_ERR_ARG, "cgh_plan_set_stage2_tiles: bad argument");
+  p->stage2_tiles = tiles;
+  return CGH_OK;
+}
+
 int cgh_plan_set_contraction(cgh_plan* p, int order) {
   if (!p || order < CGH_CONTRACT_AUTO || order > CGH_CONTRACT_COLS)
     return cgh_fail(CGH_ERR_ARG, "cgh_plan_set_contraction: bad argument");

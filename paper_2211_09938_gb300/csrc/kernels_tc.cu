@@ -12,7 +12,7 @@
 // hi*hi + hi*lo + lo*hi (three MMAs) with FP32 accumulation in tensor memory; a complex
 // product is four real ones (the imaginary-times-imaginary term negated through the
 // instruction descriptor).  A^_z is 64x an integer <= 16320, exact in hi + lo.
-#include "tc_gemm.cuh"
+#include "tc_gemm_pair.cuh"
 
 // ------------------------------------------------------------------------------------
 // operand preparation kernels
@@ -260,8 +260,15 @@ int tc_init_attributes() {
       (e = set_gemm_attr<KIND_CC, EPI_H, false>()) != cudaSuccess ||
       (e = set_gemm_attr<KIND_CC, EPI_H, true>()) != cudaSuccess ||
       (e = set_gemm_attr<KIND_CR2, EPI_Y, true>()) != cudaSuccess ||
-      (e = set_gemm_attr<KIND_CC2, EPI_H, true>()) != cudaSuccess)
+      (e = set_gemm_attr<KIND_CC2, EPI_H, true>()) != cudaSuccess ||
+      (e = set_gemm_pair_attr<KIND_CC, false>()) != cudaSuccess ||
+      (e = set_gemm_pair_attr<KIND_CC, true>()) != cudaSuccess ||
+      (e = set_gemm_pair_attr<KIND_CC2, true>()) != cudaSuccess)
     return cgh_cuda_check(e, "tensor-core kernel attributes");
+  // how many CTA pairs the device holds, looked up once here (outside any capture)
+  gemm_pair_clusters<KIND_CC, false>();
+  gemm_pair_clusters<KIND_CC, true>();
+  gemm_pair_clusters<KIND_CC2, true>();
   return CGH_OK;
 }
 
@@ -277,6 +284,7 @@ struct cgh_tc_state {
   uint16_t *B1, *Y;
   long long b1_plane, y_plane;
   CUtensorMap mB1, mY;
+  CUtensorMap mY64;  // the stage-1 output with 64-row boxes (stage 2 on CTA pairs)
 };
 
 static int tc_ensure(const cgh_plan* pc) {
@@ -322,6 +330,7 @@ static int tc_ensure(const cgh_plan* pc) {
   TC_TRY(cudaMalloc(&t->Y, 4 * t->y_plane * sizeof(uint16_t)), "tensor-core scratch: Y");
   if ((rc = make_plane_map(&t->mB1, t->B1, 2, t->ktot_alloc, t->kc_alloc)) != CGH_OK) goto fail;
   if ((rc = make_plane_map(&t->mY, t->Y, 4, p->holo_w, t->ktot_alloc)) != CGH_OK) goto fail;
+  if ((rc = make_plane_map(&t->mY64, t->Y, 4, p->holo_w, t->ktot_alloc, 64)) != CGH_OK) goto fail;
 #undef TC_TRY
   p->tc = t;
   return CGH_OK;
@@ -508,7 +517,9 @@ static int tc_run(const cgh_plan* p, const int32_t* coef, const int32_t* const* 
   stage2_args(p, F16, holo, S, a, tiles);
   a.streamk = streamk;
   prof_mark(p, CGH_PROF_TC_STAGE2, 0, st);
-  e = launch_gemm<K2, EPI_H, F16>(*mEZ, t->mY, t->mY, a, tiles, st);
+  e = cudaErrorNotSupported;
+  if (streamk > 0 && p->stage2_tiles != CGH_TILES_CTA) e = launch_gemm_pair<K2, F16>(*mEZ, t->mY64, a, tiles, st);
+  if (e == cudaErrorNotSupported) e = launch_gemm<K2, EPI_H, F16>(*mEZ, t->mY, t->mY, a, tiles, st);
   prof_mark(p, CGH_PROF_TC_STAGE2, 1, st);
   TC_CK(e, "tc: stage-2 GEMM");
   return CGH_OK;

@@ -878,15 +878,16 @@ static int get_encoder() {
   return CGH_OK;
 }
 
-// 3-D map over `planes` planes of a [rows][k_alloc] 16-bit matrix; box 32 x 128 x planes,
-// 64-byte swizzle (matches sdesc_sw64).
-static int make_plane_map(CUtensorMap* map, const void* base, int planes, long long rows, long long k_alloc) {
+// 3-D map over `planes` planes of a [rows][k_alloc] 16-bit matrix; box 32 x box_rows x
+// planes, 64-byte swizzle (matches sdesc_sw64).
+static int make_plane_map(CUtensorMap* map, const void* base, int planes, long long rows, long long k_alloc,
+                          int box_rows = 128) {
   if (get_encoder() != CGH_OK) return CGH_ERR_CUDA;
   if (((uintptr_t)base & 15) || (k_alloc * 2) % 16)
     return cgh_fail(CGH_ERR_ARG, "tensor map: base must be 16-byte aligned and rows a multiple of 16 bytes");
   cuuint64_t dims[3] = {(cuuint64_t)k_alloc, (cuuint64_t)rows, (cuuint64_t)planes};
   cuuint64_t strides[2] = {(cuuint64_t)(k_alloc * 2), (cuuint64_t)(rows * k_alloc * 2)};
-  cuuint32_t box[3] = {TC_BK, 128, (cuuint32_t)planes};
+  cuuint32_t box[3] = {TC_BK, (cuuint32_t)box_rows, (cuuint32_t)planes};
   cuuint32_t estr[3] = {1, 1, 1};
   CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_UINT16, 3, const_cast<void*>(base), dims, strides, box, estr,
                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,

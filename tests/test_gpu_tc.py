@@ -147,3 +147,48 @@ def test_contraction_orders(torch_cuda):
     H, ref_lists = run(torch, rect, "tc_fp16x3", order=Plan.CONTRACT_COLS)
     Hr = O.progressive_hologram(rect["intensity"], rect["layer"], ref_lists, O.geometry_of(rect))
     assert O.rel_l2(H, Hr) <= FP16X3_TOL
+
+
+PAIR_SCENES = {
+    "paper_512_to_1024_z16": lambda: scenes.paper_scene(),
+    "tiny_64_to_256_z4": lambda: scenes.tiny_scene(),
+    # 3 row tiles (the last CTA pair has one CTA past the hologram) and ragged columns
+    "s3_48_z3": lambda: scenes.random_scene(80, 48, 144, 3, graded=True),
+    "odd_tiles_96_to_384_z5": lambda: scenes.random_scene(84, 96, 384, 5, graded=True),
+}
+
+
+@pytest.mark.parametrize("name", list(PAIR_SCENES))
+@pytest.mark.parametrize("form", ["tc_fp16x3", "tc_bf16x3", "tc_fp16x2"])
+def test_stage2_cta_pairs_match_single_cta_and_oracle(torch_cuda, name, form):
+    """Stage 2 on CTA pairs (256 x 128 tiles, tcgen05 cta_group::2) against one CTA per
+    128 x 128 tile and the FP64 oracle: both within the form's bar, and close to each other
+    (they sum the same products in a different order)."""
+    torch = torch_cuda
+    from paper_2211_09938_gb300 import Plan
+    sc = PAIR_SCENES[name]()
+    plan = Plan.for_scene(sc)
+    I = torch.from_numpy(sc["intensity"]).cuda()
+    L = torch.from_numpy(sc["layer"]).cuda()
+    S = torch.from_numpy(sc["saliency"]).cuda()
+    coeffs = plan.haar_decompose(I, L)
+    lists, counts = plan.progressive_lists(S, L, scenes.THRESHOLDS_U8)
+    got = {}
+    for tiles in (Plan.TILES_CTA, Plan.TILES_PAIR):
+        plan.set_stage2_tiles(tiles)
+        H = plan.progressive_hologram(coeffs, lists, counts, form=form)
+        H2 = plan.progressive_hologram(coeffs, lists, counts, form=form)  # a second call, same plan
+        torch.cuda.synchronize()
+        assert plan.status() == 0
+        got[tiles] = (H.cpu().numpy(), H2.cpu().numpy())
+    ref_lists = O.progressive_lists(sc["saliency"], sc["layer"], plan.n_layers, scenes.THRESHOLDS_U8)
+    Href = O.progressive_hologram(sc["intensity"], sc["layer"], ref_lists, O.geometry_of(sc))
+    bar = {"tc_fp16x3": FP16X3_TOL, "tc_bf16x3": BF16X3_TOL, "tc_fp16x2": FP16X2_TOL}[form]
+    e_cta = O.rel_l2(got[Plan.TILES_CTA][0], Href)
+    e_pair = O.rel_l2(got[Plan.TILES_PAIR][0], Href)
+    d = O.rel_l2(got[Plan.TILES_PAIR][0], got[Plan.TILES_CTA][0])
+    print(f"{form} {name}: one CTA {e_cta:.3e}, CTA pairs {e_pair:.3e}, pairs vs one CTA {d:.3e}")
+    assert e_cta <= bar and e_pair <= bar
+    assert e_pair <= 1.5 * e_cta + 1e-7
+    assert O.rel_l2(got[Plan.TILES_PAIR][1], got[Plan.TILES_PAIR][0]) <= 2 * e_pair + 1e-7
+    plan.close()
