@@ -138,6 +138,17 @@ int cgh_plan_set_tuning(cgh_plan* plan, int max_ksteps_per_chain);
 #define CGH_TILES_PAIR 2
 int cgh_plan_set_stage2_tiles(cgh_plan* plan, int tiles);
 
+/*
+ * cgh_plan_set_fusion - 1 (default): the separable form's two GEMM stages run as one
+ * cooperative persistent launch in which each CTA does its share of stage 1 and then its
+ * stream-K share of stage 2, each stage-2 K step waiting (bounded) until every stage-1
+ * tile of its layer is stored; used when the call splits K stream-K style (not with
+ * CGH_PLAN_DETERMINISTIC), the stage-2 tiles are not forced to CTA pairs, and the grid fits
+ * on the device at once.  0: two launches.  Results agree to rounding.  Applies to later
+ * calls of the plan.  The paper has no counterpart (a scheduling choice of the GPU path).
+ */
+int cgh_plan_set_fusion(cgh_plan* plan, int fused);
+
 #define CGH_CONTRACT_AUTO 0
 #define CGH_CONTRACT_ROWS 1
 #define CGH_CONTRACT_COLS 2
@@ -525,7 +536,8 @@ int cgh_batch_destroy(cgh_batch* batch);
 #define CGH_PROF_ASM_FFT 10    /* angular spectrum: forward 2-D FFT      */
 #define CGH_PROF_ASM_INV 11    /* angular spectrum: transfer + inverse FFTs */
 #define CGH_PROF_POINTCLOUD 12 /* per-point depth direct kernel          */
-#define CGH_PROF_SLOTS 13
+#define CGH_PROF_TC_FUSED 13   /* tensor form: both GEMM stages in one launch */
+#define CGH_PROF_SLOTS 14
 
 /*
  * cgh_profile - enable (1) or disable (0) CUDA-event timing around the plan's internal

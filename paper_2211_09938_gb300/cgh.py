@@ -42,6 +42,7 @@ SIGNATURES = {
     "cgh_plan_destroy": (_I, [_P]),
     "cgh_plan_set_tuning": (_I, [_P, _I]),
     "cgh_plan_set_stage2_tiles": (_I, [_P, _I]),
+    "cgh_plan_set_fusion": (_I, [_P, _I]),
     "cgh_plan_set_contraction": (_I, [_P, _I]),
     "cgh_build_tables": (_I, [_P, _P]),
     "cgh_haar_decompose": (_I, [_P, _P, _P, _P, _P]),
@@ -182,6 +183,11 @@ class Plan:
         """cgh_plan_set_stage2_tiles: TILES_AUTO, TILES_CTA (128x128 per CTA) or TILES_PAIR
         (256x128 per CTA pair, tcgen05 cta_group::2)."""
         check(lib().cgh_plan_set_stage2_tiles(self.handle, int(tiles)))
+
+    def set_fusion(self, fused):
+        """cgh_plan_set_fusion: both GEMM stages in one cooperative launch (True, default)
+        or two launches (False)."""
+        check(lib().cgh_plan_set_fusion(self.handle, 1 if fused else 0))
 
     def set_tuning(self, max_ksteps_per_chain):
         check(lib().cgh_plan_set_tuning(self.handle, int(max_ksteps_per_chain)))
@@ -376,7 +382,7 @@ class Plan:
         return out
 
     PROF_SLOTS = ["tables", "haar", "select", "direct_lut", "tc_prep", "tc_stage1", "tc_stage2",
-                  "plain", "recon", "propagate", "asm_fft", "asm_inv", "pointcloud"]
+                  "plain", "recon", "propagate", "asm_fft", "asm_inv", "pointcloud", "tc_fused"]
 
     def profile(self, enable=True):
         check(lib().cgh_profile(self.handle, 1 if enable else 0))

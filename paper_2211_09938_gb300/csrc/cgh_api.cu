@@ -75,6 +75,12 @@ int cgh_plan_set_stage2_tiles(cgh_plan* p, int tiles) {
   return CGH_OK;
 }
 
+int cgh_plan_set_fusion(cgh_plan* p, int fused) {
+  if (!p || fused < 0 || fused > 1) return cgh_fail(CGH_ERR_ARG, "cgh_plan_set_fusion: bad argument");
+  p->no_fusion = !fused;
+  return CGH_OK;
+}
+
 int cgh_plan_set_contraction(cgh_plan* p, int order) {
   if (!p || order < CGH_CONTRACT_AUTO || order > CGH_CONTRACT_COLS)
     return cgh_fail(CGH_ERR_ARG, "cgh_plan_set_contraction: bad argument");

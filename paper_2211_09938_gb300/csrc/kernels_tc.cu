@@ -12,6 +12,7 @@
 // hi*hi + hi*lo + lo*hi (three MMAs) with FP32 accumulation in tensor memory; a complex
 // product is four real ones (the imaginary-times-imaginary term negated through the
 // instruction descriptor).  A^_z is 64x an integer <= 16320, exact in hi + lo.
+#include "tc_fused.cuh"
 #include "tc_gemm_pair.cuh"
 
 // ------------------------------------------------------------------------------------
@@ -87,7 +88,8 @@ __global__ void __launch_bounds__(1024) k_tc_compact(TcFlags fl, int H, int W, i
                                                      int* __restrict__ rows, int* __restrict__ cols,
                                                      int* __restrict__ kr_pad, int* __restrict__ kc_pad, int ld_rows,
                                                      int ld_cols, int* __restrict__ rband, int* __restrict__ cband,
-                                                     int* __restrict__ kmap2, int* __restrict__ orient) {
+                                                     int* __restrict__ kmap2, int* __restrict__ orient,
+                                                     int* __restrict__ fused_sync) {
   __shared__ int s_warp[33];
   __shared__ int s_cnt[2][CGH_MAX_LAYERS];  // kept bands per layer: object rows, object columns
   pdl_wait();
@@ -115,6 +117,9 @@ __global__ void __launch_bounds__(1024) k_tc_compact(TcFlags fl, int H, int W, i
     tr = sc < sr ? 1 : 0;
   }
   if (z == 0 && t == 0) *orient = tr;
+  // the fused GEMM launch's counters (per-layer stage-1 tiles, cleared CTAs) start at zero
+  if (z == 0 && fused_sync)
+    for (int e = t; e <= CGH_MAX_LAYERS; e += blockDim.x) fused_sync[e] = 0;
   int koff = 0;  // this layer's first K step in the concatenated stage-2 K
   for (int q = 0; q < z; ++q) koff += s_cnt[tr][q];
   for (int axis = 0; axis < 2; ++axis) {
@@ -263,12 +268,18 @@ int tc_init_attributes() {
       (e = set_gemm_attr<KIND_CC2, EPI_H, true>()) != cudaSuccess ||
       (e = set_gemm_pair_attr<KIND_CC, false>()) != cudaSuccess ||
       (e = set_gemm_pair_attr<KIND_CC, true>()) != cudaSuccess ||
-      (e = set_gemm_pair_attr<KIND_CC2, true>()) != cudaSuccess)
+      (e = set_gemm_pair_attr<KIND_CC2, true>()) != cudaSuccess ||
+      (e = set_fused_attr<KIND_CR, KIND_CC, false>()) != cudaSuccess ||
+      (e = set_fused_attr<KIND_CR, KIND_CC, true>()) != cudaSuccess ||
+      (e = set_fused_attr<KIND_CR2, KIND_CC2, true>()) != cudaSuccess)
     return cgh_cuda_check(e, "tensor-core kernel attributes");
   // how many CTA pairs the device holds, looked up once here (outside any capture)
   gemm_pair_clusters<KIND_CC, false>();
   gemm_pair_clusters<KIND_CC, true>();
   gemm_pair_clusters<KIND_CC2, true>();
+  fused_max_ctas<KIND_CR, KIND_CC, false>();
+  fused_max_ctas<KIND_CR, KIND_CC, true>();
+  fused_max_ctas<KIND_CR2, KIND_CC2, true>();
   return CGH_OK;
 }
 
@@ -285,6 +296,7 @@ struct cgh_tc_state {
   long long b1_plane, y_plane;
   CUtensorMap mB1, mY;
   CUtensorMap mY64;  // the stage-1 output with 64-row boxes (stage 2 on CTA pairs)
+  int* fused_sync;   // [CGH_MAX_LAYERS + 1] counters of the fused GEMM launch
 };
 
 static int tc_ensure(const cgh_plan* pc) {
@@ -322,6 +334,8 @@ static int tc_ensure(const cgh_plan* pc) {
   TC_TRY(cudaMalloc(&t->rband, (size_t)Z * (t->kr_alloc / 32) * sizeof(int)), "tensor-core scratch: bands");
   TC_TRY(cudaMalloc(&t->cband, (size_t)Z * (t->kc_alloc / 32) * sizeof(int)), "tensor-core scratch: bands");
   TC_TRY(cudaMalloc(&t->kmap2, (size_t)(t->ktot_alloc / 32) * sizeof(int)), "tensor-core scratch: K map");
+  TC_TRY(cudaMalloc(&t->fused_sync, (CGH_MAX_LAYERS + 1) * sizeof(int)), "tensor-core scratch: counters");
+  TC_TRY(cudaMemset(t->fused_sync, 0, (CGH_MAX_LAYERS + 1) * sizeof(int)), "tensor-core scratch: counters");
   TC_TRY(cudaMalloc(&t->orient, sizeof(int)), "tensor-core scratch: order");
   TC_TRY(cudaMemset(t->orient, 0, sizeof(int)), "tensor-core scratch: order");
   t->b1_plane = (long long)t->ktot_alloc * t->kc_alloc;
@@ -352,6 +366,7 @@ void tc_destroy(cgh_plan* p) {
   cudaFree(t->cband);
   cudaFree(t->kmap2);
   cudaFree(t->orient);
+  cudaFree(t->fused_sync);
   cudaFree(t->B1);
   cudaFree(t->Y);
   free(t);
@@ -401,7 +416,8 @@ static int tc_prep(const cgh_plan* p, const int32_t* coef, const int32_t* const*
           "tc: scatter");
   }
   TC_CK(launch_pdl(k_tc_compact, dim3(Z), dim3(1024), 0, st, t->fl, H, W, Z, p->contraction, t->rows, t->cols,
-                   t->kr_pad, t->kc_pad, t->kr_alloc, t->kc_alloc, t->rband, t->cband, t->kmap2, t->orient),
+                   t->kr_pad, t->kc_pad, t->kr_alloc, t->kc_alloc, t->rband, t->cband, t->kmap2, t->orient,
+                   t->fused_sync),
         "tc: compact");
   if (coef_ready) TC_CK(cudaStreamWaitEvent(st, coef_ready, 0), "tc: wait for the coefficients");
   {
@@ -485,20 +501,15 @@ static int tc_run(const cgh_plan* p, const int32_t* coef, const int32_t* const* 
   rc = tc_prep<F16>(p, coef, lists, d_counts, st, flags_ready, coef_ready);
   if (rc != CGH_OK) return rc;
   prof_mark(p, CGH_PROF_TC_PREP, 1, st);
-  TcGemmArgs a;
-  dim3 tiles;
-  stage1_args(p, F16, a, tiles);
-  a.zero_ptr[0] = reinterpret_cast<float4*>(t->flags);  // marks of this call, for the next one
-  a.zero_n[0] = (long long)(t->flags_alloc / 16);
+  TcGemmArgs a1, a2;
+  dim3 tiles1, tiles2;
+  stage1_args(p, F16, a1, tiles1);
+  a1.zero_ptr[0] = reinterpret_cast<float4*>(t->flags);  // marks of this call, for the next one
+  a1.zero_n[0] = (long long)(t->flags_alloc / 16);
   if (h_zero_in_stage1) {
-    a.zero_ptr[1] = reinterpret_cast<float4*>(holo);
-    a.zero_n[1] = (long long)(hpix / 2);
+    a1.zero_ptr[1] = reinterpret_cast<float4*>(holo);
+    a1.zero_n[1] = (long long)(hpix / 2);
   }
-  prof_mark(p, CGH_PROF_TC_STAGE1, 0, st);
-  cudaError_t e = launch_gemm<K1, EPI_Y, F16>(*mEZt, t->mB1, t->mY, a, tiles, st);
-  prof_mark(p, CGH_PROF_TC_STAGE1, 1, st);
-  TC_CK(e, "tc: stage-1 GEMM");
-  t->flags_dirty = 0;
   const int tm = (p->holo_h + TC_BM - 1) / TC_BM, tn = (p->holo_w + TC_BN - 1) / TC_BN;
   // Stream-K over the (tile, K step) space unless the plan asks for single-writer tiles
   // (deterministic).  Chains of at most the plan's cap, else 32 K steps for fp16 hi+lo
@@ -514,12 +525,29 @@ static int tc_run(const cgh_plan* p, const int32_t* coef, const int32_t* const* 
     const int need = (kst + p->max_ksteps - 1) / p->max_ksteps;
     if (need > S) S = need;
   }
-  stage2_args(p, F16, holo, S, a, tiles);
-  a.streamk = streamk;
+  stage2_args(p, F16, holo, S, a2, tiles2);
+  a2.streamk = streamk;
+  cudaError_t e = cudaErrorNotSupported;
+  if (streamk > 0 && !p->no_fusion && p->stage2_tiles != CGH_TILES_PAIR) {
+    // both stages in one cooperative launch (stage 2 starts on finished layers)
+    prof_mark(p, CGH_PROF_TC_FUSED, 0, st);
+    e = launch_fused<K1, K2, F16>(*mEZt, t->mB1, t->mY, *mEZ, a1, tiles1, a2, tiles2, t->fused_sync, st);
+    prof_mark(p, CGH_PROF_TC_FUSED, 1, st);
+    if (e != cudaErrorNotSupported) {
+      TC_CK(e, "tc: fused GEMMs");
+      t->flags_dirty = 0;
+      return CGH_OK;
+    }
+  }
+  prof_mark(p, CGH_PROF_TC_STAGE1, 0, st);
+  e = launch_gemm<K1, EPI_Y, F16>(*mEZt, t->mB1, t->mY, a1, tiles1, st);
+  prof_mark(p, CGH_PROF_TC_STAGE1, 1, st);
+  TC_CK(e, "tc: stage-1 GEMM");
+  t->flags_dirty = 0;
   prof_mark(p, CGH_PROF_TC_STAGE2, 0, st);
   e = cudaErrorNotSupported;
-  if (streamk > 0 && p->stage2_tiles != CGH_TILES_CTA) e = launch_gemm_pair<K2, F16>(*mEZ, t->mY64, a, tiles, st);
-  if (e == cudaErrorNotSupported) e = launch_gemm<K2, EPI_H, F16>(*mEZ, t->mY, t->mY, a, tiles, st);
+  if (streamk > 0 && p->stage2_tiles != CGH_TILES_CTA) e = launch_gemm_pair<K2, F16>(*mEZ, t->mY64, a2, tiles2, st);
+  if (e == cudaErrorNotSupported) e = launch_gemm<K2, EPI_H, F16>(*mEZ, t->mY, t->mY, a2, tiles2, st);
   prof_mark(p, CGH_PROF_TC_STAGE2, 1, st);
   TC_CK(e, "tc: stage-2 GEMM");
   return CGH_OK;

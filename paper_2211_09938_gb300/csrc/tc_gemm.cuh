@@ -328,6 +328,7 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
 
 struct TileInfo {
   int a_row, b_row, k_lo, nk, out_row0, out_col0, n_valid, row_lim, col_lim, item;
+  int layer;       // mode 1: the tile's layer
   const int* akm;  // A's K coordinate per K step of this tile, or null (= k_lo + 32 kt)
 };
 
@@ -339,6 +340,7 @@ __device__ __forceinline__ bool decode_stage1(const TcGemmArgs& a, int mt, int n
   const int krz = s_off[zz + 1] - s_off[zz];
   ti.n_valid = min(TC_BN, krz - nt * TC_BN);
   if (ti.n_valid <= 0) return false;
+  ti.layer = zz;
   ti.a_row = zz * a.a_rows_per_z + mt * TC_BM;
   ti.b_row = s_off[zz] + nt * TC_BN;
   ti.k_lo = 0;
@@ -394,7 +396,13 @@ __device__ __forceinline__ bool decode_tile(const TcGemmArgs& a, int t, const in
 // two accumulator buffers of Re | Im) and one lane issues the MMAs; warps 2-5 drain a
 // finished buffer (TMEM -> registers -> global) while the next tile accumulates in the
 // other buffer.
-template <int KIND, int EPI, bool F16, class Src>
+// TMEM: ALLOC allocates the 512 columns at the start (else *s_tmem_p holds an allocation
+// made earlier in the kernel), DEALLOC frees them at the end (else they stay allocated for
+// a later body in the same kernel).  Hooks of the source: before_load(ti, kt) runs in the
+// producer before the loads of K step kt (it may wait, bounded, for inputs that other CTAs
+// produce; false aborts), before_epilogue() before a tile's output is written (false
+// aborts), tile_stored(ti) after a tile's EPI_Y stores are complete and visible.
+template <int KIND, int EPI, bool F16, class Src, bool ALLOC = true, bool DEALLOC = true>
 __device__ __forceinline__ void tc_gemm_body(const Src& src, uint8_t* smem, uint64_t* full_bar, uint64_t* empty_bar,
                                              uint64_t* tfull_bar, uint64_t* tempty_bar, uint64_t* done_bar,
                                              uint32_t* s_tmem_p, volatile int* s_abort_p) {
@@ -420,7 +428,7 @@ __device__ __forceinline__ void tc_gemm_body(const Src& src, uint8_t* smem, uint
     s_abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == 1) {
+  if (ALLOC && warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(smem_u32(s_tmem_p))
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
@@ -448,7 +456,7 @@ __device__ __forceinline__ void tc_gemm_body(const Src& src, uint8_t* smem, uint
         for (int kt = 0; kt < ti.nk; ++kt, ++it) {
           const int s = it % NST;
           const uint32_t ph = (uint32_t)(it / NST) & 1u;
-          if (!mbar_wait_bounded(&empty_bar[s], ph ^ 1u, &s_abort, status)) {
+          if (!mbar_wait_bounded(&empty_bar[s], ph ^ 1u, &s_abort, status) || !src.before_load(ti, kt, &s_abort)) {
             ok = false;
             break;
           }
@@ -519,7 +527,7 @@ __device__ __forceinline__ void tc_gemm_body(const Src& src, uint8_t* smem, uint
       const TcGemmArgs& args = src.args(ti);
       const int buf = local & 1;
       const uint32_t ph = (uint32_t)(local >> 1) & 1u;
-      bool have = mbar_wait_bounded(&tfull_bar[buf], ph, &s_abort, status);
+      bool have = mbar_wait_bounded(&tfull_bar[buf], ph, &s_abort, status) && src.before_epilogue(&s_abort);
       // one decision for all four epilogue warps: tcgen05.ld is warp-collective and the
       // staged stores meet at named barriers
       have = epi_all(have && !s_abort);
@@ -646,12 +654,20 @@ __device__ __forceinline__ void tc_gemm_body(const Src& src, uint8_t* smem, uint
       __syncwarp();
       if (lane == 0) mbar_arrive(&tempty_bar[buf]);
       ++local;
+      if (EPI == EPI_Y && src.publishes()) {
+        // the tile's stores (staged TMA stores and direct stores) complete and visible, then
+        // published once
+        if (lane == 0 && quarter == 0) bulk_wait_all();
+        __threadfence();
+        epi_barrier();
+        if (lane == 0 && quarter == 0) src.tile_stored(ti);
+      }
     }
     if (EPI == EPI_Y && lane == 0 && quarter == 0) bulk_wait_all();  // staged stores complete
   }
   tc_fence_before();
   __syncthreads();
-  if (warp == 1) {
+  if (DEALLOC && warp == 1) {
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem) : "memory");
   }
@@ -728,6 +744,10 @@ struct TcSingleSrc {
   __device__ void acquire_maps(const CUtensorMap*, const CUtensorMap*) const {}
   __device__ const TcGemmArgs& args(const TileInfo&) const { return *a; }
   __device__ int* status() const { return a->status; }
+  __device__ bool before_load(const TileInfo&, int, volatile int*) const { return true; }
+  __device__ bool before_epilogue(volatile int*) const { return true; }
+  __device__ bool publishes() const { return false; }
+  __device__ void tile_stored(const TileInfo&) const {}
 };
 
 template <int KIND, int EPI, bool F16>
@@ -829,6 +849,10 @@ struct TcBatchSrc {
   }
   __device__ const TcGemmArgs& args(const TileInfo& ti) const { return items[ti.item].a; }
   __device__ int* status() const { return st; }
+  __device__ bool before_load(const TileInfo&, int, volatile int*) const { return true; }
+  __device__ bool before_epilogue(volatile int*) const { return true; }
+  __device__ bool publishes() const { return false; }
+  __device__ void tile_stored(const TileInfo&) const {}
 };
 
 #define TC_BATCH_MAX 1024

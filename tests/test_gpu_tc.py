@@ -192,3 +192,46 @@ def test_stage2_cta_pairs_match_single_cta_and_oracle(torch_cuda, name, form):
     assert e_pair <= 1.5 * e_cta + 1e-7
     assert O.rel_l2(got[Plan.TILES_PAIR][1], got[Plan.TILES_PAIR][0]) <= 2 * e_pair + 1e-7
     plan.close()
+
+
+@pytest.mark.parametrize("name", list(PAIR_SCENES))
+@pytest.mark.parametrize("form", ["tc_fp16x3", "tc_bf16x3", "tc_fp16x2"])
+def test_fused_stages_match_two_launches_and_oracle(torch_cuda, name, form):
+    """Both GEMM stages in one cooperative launch (stage 2 waiting per layer for stage 1's
+    stored tiles) against two launches and the FP64 oracle, over two calls in a row (the
+    per-layer counters are reset by the compaction of the next call)."""
+    torch = torch_cuda
+    from paper_2211_09938_gb300 import Plan
+    sc = PAIR_SCENES[name]()
+    plan = Plan.for_scene(sc)
+    I = torch.from_numpy(sc["intensity"]).cuda()
+    L = torch.from_numpy(sc["layer"]).cuda()
+    S = torch.from_numpy(sc["saliency"]).cuda()
+    coeffs = plan.haar_decompose(I, L)
+    lists, counts = plan.progressive_lists(S, L, scenes.THRESHOLDS_U8)
+    got = {}
+    for fused in (False, True):
+        plan.set_fusion(fused)
+        plan.set_stage2_tiles(Plan.TILES_CTA)
+        plan.profile(True)
+        H = plan.progressive_hologram(coeffs, lists, counts, form=form)
+        prof = plan.profile_read()
+        plan.profile(False)
+        H2 = plan.progressive_hologram(coeffs, lists, counts, form=form)
+        torch.cuda.synchronize()
+        assert plan.status() == 0
+        # the fused path ran as one launch, the other as two
+        assert (prof["tc_fused"] > 0) == fused and (prof["tc_stage2"] > 0) == (not fused)
+        got[fused] = (H.cpu().numpy(), H2.cpu().numpy())
+    ref_lists = O.progressive_lists(sc["saliency"], sc["layer"], plan.n_layers, scenes.THRESHOLDS_U8)
+    Href = O.progressive_hologram(sc["intensity"], sc["layer"], ref_lists, O.geometry_of(sc))
+    bar = {"tc_fp16x3": FP16X3_TOL, "tc_bf16x3": BF16X3_TOL, "tc_fp16x2": FP16X2_TOL}[form]
+    e2 = O.rel_l2(got[False][0], Href)
+    e1 = O.rel_l2(got[True][0], Href)
+    print(f"{form} {name}: two launches {e2:.3e}, fused {e1:.3e}, "
+          f"fused vs two {O.rel_l2(got[True][0], got[False][0]):.3e}")
+    assert e2 <= bar and e1 <= bar
+    # same chains, same order of products: only the split of the partial sums may differ
+    assert O.rel_l2(got[True][0], got[False][0]) <= 1e-6
+    assert O.rel_l2(got[True][1], got[True][0]) <= 1e-6
+    plan.close()
