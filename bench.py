@@ -624,7 +624,7 @@ def run_ours(args):
     # cgh_progressive_step (the single-launch selection, which also marks the operand flags,
     # compaction, inverse DWT, the two GEMMs); direct form, the three selection passes and
     # the direct kernel
-    launches_per_step = 2 + 1 + (1 + 4 if tensor_form else 3 + 1)
+    launches_per_step = 2 + 1 + (1 + 4 if tensor_form else 3 + 1)  # one fewer when the GEMMs are fused
 
     # The fringe-table build, the DWT and the block selection are independent: the first two
     # run on side streams forked from (and joined back into) the step's stream, which the
@@ -772,10 +772,10 @@ def run_ours(args):
         peak_tf = pk.get("bf16_tflops", 1900.0)
         roof = {"bound": "tensor",
                 "kernel": "k_tc_fused (both GEMM stages, one cooperative launch)" if fused
-                else "k_tc_gemm<KIND_CC,EPI_H> (stage 2)",
+                else "k_tc_gemm_pair<KIND_CC> (stage 2 on CTA pairs, tcgen05 cta_group::2)",
                 "achieved": algo_flop / (k_ms / 1e3) / 1e12, "peak": peak_tf, "unit": "TFLOP/s",
                 "frac": algo_flop / (k_ms / 1e3) / 1e12 / peak_tf,
-                "traffic": kernel_traffic(("k_tc_fused" if fused else "k_tc_gemm stage 2") + f" ({form})"),
+                "traffic": kernel_traffic(("k_tc_fused" if fused else "k_tc_gemm_pair stage 2") + f" ({form})"),
                 "traffic_note": "ncu dram__bytes_read.sum + dram__bytes_write.sum per launch, from "
                                 "profiles/traffic.json (the ncu summary it names); null if the kernel changed "
                                 "since the counters were taken",
@@ -884,7 +884,7 @@ def run_ours(args):
                    "parallelism": f"replicas{ws}" if ws > 1 else "single GPU",
                    "work_lists": [n_lll, n1, n2, n3], "rank1_terms": rank1_terms},
         "roofline": roof, "clocks": clocks, "e2e": e2e,
-        "gpu_launches": launches_per_step * args.steps, "wall_s_timed_region": wall,
+        "gpu_launches": (launches_per_step - (1 if fused else 0)) * args.steps, "wall_s_timed_region": wall,
         "ms_per_step_p50": step_ms[len(step_ms) // 2], "ms_per_step_p99": step_ms[min(len(step_ms) - 1,
                                                                                      int(0.99 * len(step_ms)))],
         "algorithmic": {"terms": t_terms, "terms_px_per_s": t_terms * HOLO * HOLO / (dev_ms / args.steps / 1e3),
@@ -894,6 +894,28 @@ def run_ours(args):
         "unit_peaks_measured": unit_peaks,
     }
     line["stages_ms"] = stages
+    if form != "direct_lut" and not args.skip_forms:
+        # the same superposition with both stages in one cooperative launch (plan option)
+        plan.set_fusion(True)
+        s1, s2 = [], []
+        for k in range(R):
+            plan.profile(True)
+            with torch.cuda.stream(stream):
+                flush.fill_(float(k))
+                plan.progressive_hologram(coeffs, lists, counts, holo=holo, form=form, stream=stream)
+            pr = plan.profile_read(stream=stream)
+            plan.profile(False)
+            s1.append(pr.get("tc_fused", 0.0))
+        plan.set_fusion(False)
+        m1 = sorted(s1)[len(s1) // 2]
+        fl = stage1_flop + stage2_flop
+        line["fused_gemms"] = {
+            "kernel": "k_tc_fused (both GEMM stages, one cooperative launch)", "ms": m1,
+            "two_launches_ms": stages.get("tc_stage1", 0.0) + stages.get("tc_stage2", 0.0),
+            "achieved_tflops": fl / (m1 / 1e3) / 1e12, "frac_of_measured_bf16_peak": fl / (m1 / 1e3) / 1e12 / peak_tf,
+            "note": "plan option (cgh_plan_set_fusion); the step runs the two launches, because the cooperative "
+                    "launch needs every SM and so gains nothing in the captured step and slows concurrent "
+                    "pipelines; L2 flushed before each"}
     if rank == 0 and ws == 1 and not args.skip_batch:
         line["batch"] = run_batch_workload(stream, form if form != "direct_lut" else "tc_bf16x3",
                                            args.batch_scenes, 10)

@@ -185,8 +185,8 @@ class Plan:
         check(lib().cgh_plan_set_stage2_tiles(self.handle, int(tiles)))
 
     def set_fusion(self, fused):
-        """cgh_plan_set_fusion: both GEMM stages in one cooperative launch (True, default)
-        or two launches (False)."""
+        """cgh_plan_set_fusion: both GEMM stages in one cooperative launch (True) or two
+        launches (False, default)."""
         check(lib().cgh_plan_set_fusion(self.handle, 1 if fused else 0))
 
     def set_tuning(self, max_ksteps_per_chain):

@@ -77,7 +77,7 @@ int cgh_plan_set_stage2_tiles(cgh_plan* p, int tiles) {
 
 int cgh_plan_set_fusion(cgh_plan* p, int fused) {
   if (!p || fused < 0 || fused > 1) return cgh_fail(CGH_ERR_ARG, "cgh_plan_set_fusion: bad argument");
-  p->no_fusion = !fused;
+  p->fusion = fused;
   return CGH_OK;
 }
 

@@ -528,7 +528,7 @@ static int tc_run(const cgh_plan* p, const int32_t* coef, const int32_t* const* 
   stage2_args(p, F16, holo, S, a2, tiles2);
   a2.streamk = streamk;
   cudaError_t e = cudaErrorNotSupported;
-  if (streamk > 0 && !p->no_fusion && p->stage2_tiles != CGH_TILES_PAIR) {
+  if (streamk > 0 && p->fusion && p->stage2_tiles != CGH_TILES_PAIR) {
     // both stages in one cooperative launch (stage 2 starts on finished layers)
     prof_mark(p, CGH_PROF_TC_FUSED, 0, st);
     e = launch_fused<K1, K2, F16>(*mEZt, t->mB1, t->mY, *mEZ, a1, tiles1, a2, tiles2, t->fused_sync, st);

@@ -7,7 +7,8 @@
 // the producer waits (bounded) until every stage-1 tile of layer z has been published.
 // So stage 2 starts on a CTA as soon as that CTA's stage-1 tiles are done and the layers
 // it needs are complete, instead of after the last stage-1 tile of the grid, and the
-// second launch, its prologue and pipeline fill disappear.  The launch is cooperative, so
+// second launch, its prologue and pipeline fill disappear (an option of the plan: the
+// cooperative launch occupies every SM, so it cannot overlap other streams' kernels).  The launch is cooperative, so
 // all CTAs are resident and the waits always end (every stage-1 tile is owned by a running
 // CTA that waits for nothing in stage 1).  The hologram is cleared by every CTA at the
 // start; stage 2 adds into it only after every CTA has cleared its share (a second counter).
