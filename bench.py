@@ -218,6 +218,11 @@ def cpu_baseline(budget_s=12.0):
 # secondary workloads (reported as fields of the same JSON line)
 
 
+def progress(msg):
+    """One line on stderr per bench phase (the JSON line goes to stdout)."""
+    print(f"[bench {time.strftime('%H:%M:%S')}] {msg}", file=sys.stderr, flush=True)
+
+
 def run_batch_workload(stream, form, count, reps):
     """64 scenes of uneven size (object edge in {128,256,512,1024}, hologram 2x, 4..32
     layers, ellipse saliency covering 5-60%) as one graph-captured batch."""
@@ -235,7 +240,9 @@ def run_batch_workload(stream, form, count, reps):
         batch = Batch(plans, I, L, S, scenes.THRESHOLDS_U8, Hs, form=form, stream=stream)
     cache = os.path.join(ROOT, "paper_2211_09938_gb300", "_build", "autotune.json")
     os.makedirs(os.path.dirname(cache), exist_ok=True)
+    progress("batch: created, autotuning")
     tuned = autotune.tune_batch(batch, plans, form, stream, cache_path=cache)
+    progress(f"batch: tuned {tuned.get('tiles')}/{tuned['ksteps']}")
     g = torch.cuda.CUDAGraph()
     with torch.cuda.graph(g, stream=stream):
         batch.run(stream=stream)
@@ -252,6 +259,7 @@ def run_batch_workload(stream, form, count, reps):
     torch.cuda.synchronize()
     ms = sorted(a.elapsed_time(b) for a, b in evs)[reps // 2]
     work = sum(sc["intensity"].size * sc["holo"][0] * sc["holo"][1] for sc in scs)
+    progress("batch: timed; per-scene latency")
     # per-scene latency: each scene alone as its own captured graph
     lat = []
     for k, sc in enumerate(scs):
@@ -290,7 +298,8 @@ def run_batch_workload(stream, form, count, reps):
             "gpoint_px_per_s": work / (ms / 1e3) / 1e9,
             "latency_ms_p50": lat[len(lat) // 2], "latency_ms_p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
             "latency_note": "each scene alone as a captured graph (DWT, selection, superposition)",
-            "autotuned_ksteps_per_unit": tuned["ksteps"],
+            "autotuned_ksteps_per_unit": tuned["ksteps"], "autotuned_stage2_tiles": tuned.get("tiles"),
+            "autotune_tried_ms": tuned.get("tried"),
             "sizes": sorted(set(sc["intensity"].shape[0] for sc in scs))}
 
 
@@ -800,6 +809,7 @@ def run_ours(args):
                              f"{sms * 256 * pk.get('sm_max_mhz', 2070.0) * 1e6 / 1e12:.1f} TFLOP/s",
                 "kernel_ms": k_ms}
 
+    progress("step timed; end to end")
     # ---- end to end from pinned host inputs to the host hologram, every step: the library's
     # streaming pipeline (copies in and out on their own streams, overlapping the neighbouring
     # scenes' compute; two device slots, each step a captured graph)
@@ -916,23 +926,30 @@ def run_ours(args):
             "note": "plan option (cgh_plan_set_fusion); the step runs the two launches, because the cooperative "
                     "launch needs every SM and so gains nothing in the captured step and slows concurrent "
                     "pipelines; L2 flushed before each"}
+    progress("e2e done; batch")
     if rank == 0 and ws == 1 and not args.skip_batch:
         line["batch"] = run_batch_workload(stream, form if form != "direct_lut" else "tc_bf16x3",
                                            args.batch_scenes, 10)
+    progress("phase optimisation")
     if rank == 0 and ws == 1 and not args.skip_phase_opt:
         line["phase_opt"] = run_phase_opt_workload(stream, args.phase_opt_steps)
     if plain is not None:
         line["plain_direct"] = plain
     if pointcloud is not None:
         line["pointcloud_direct"] = pointcloud
+    progress("HBM paths")
     if rank == 0 and not args.skip_hbm_paths:
         line["hbm_paths_8192"] = run_hbm_paths(stream, flush)
+    progress("precision")
     if rank == 0 and ws == 1 and not args.skip_precision:
         line["precision"] = run_precision_workload(stream, flush)
+    progress("rgb")
     if rank == 0 and not args.skip_rgb:
         line["rgb"] = run_rgb_workload(stream, form if form != "direct_lut" else "tc_bf16x3", flush)
+    progress("angular spectrum")
     if rank == 0 and not args.skip_asm:
         line["asm_reconstruct"] = run_asm_workload(plan, holo, L, stream, flush)
+    progress("level sweep")
     if rank == 0 and not args.skip_level_sweep:
         line["level_sweep"] = run_level_sweep(plan, coeffs, lists, counts, I, L, stream, form, flush)
     # the other superposition forms on the same scene (device ms of the superposition call)
@@ -954,6 +971,7 @@ def run_ours(args):
         line["other_forms_superposition_ms"] = others
     if fast is not None:
         line["fp16x2_step"] = fast
+    progress("cpu baseline")
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cb, Href = cpu_baseline()
         line["cpu_baseline"] = cb
@@ -1004,6 +1022,9 @@ def per_layer_accuracy(plan, sc, coeffs, lists, counts, form, stream):
 
 
 def main():
+    import faulthandler
+    # should a phase ever stall, say where (stderr, every 4 minutes); the JSON line is unaffected
+    faulthandler.dump_traceback_later(240, repeat=True, file=sys.stderr)
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=50)

@@ -497,7 +497,9 @@ typedef struct cgh_batch cgh_batch;
  * thresholds (HOST int[3], levels 1, 2, 3).  The buffers are bound at creation and reused by
  * every cgh_batch_run (fill the inputs, run, read the outputs), so a run can be captured in
  * a CUDA graph.  form: CGH_FORM_TC_BF16X3 or CGH_FORM_TC_FP16X3.  The batch allocates the
- * per-scene coefficients and work lists; it does not own the plans.  1 <= n <= 1024.
+ * per-scene coefficients and work lists and its launch tables (which take each plan's
+ * contraction order as set at creation); it does not own the plans.  1 <= n <= 1024, at most
+ * 65535 scene layers in all.  Holograms 16-byte aligned with an even pixel count.
  * Errors: CGH_ERR_ARG, CGH_ERR_UNSUPPORTED (form), CGH_ERR_NOMEM, CGH_ERR_CUDA.
  */
 int cgh_batch_create(cgh_batch** out, cgh_plan* const* plans, int n, const uint8_t* const* intensity,
@@ -505,9 +507,12 @@ int cgh_batch_create(cgh_batch** out, cgh_plan* const* plans, int n, const uint8
                      float* const* holos, int form, void* stream);
 
 /*
- * cgh_batch_run - enqueue one progressive hologram per scene: per scene the DWT, the fused
- * selection and the operand build; then ONE persistent stage-1 launch and ONE persistent
- * stage-2 launch whose work units span every scene (uneven sizes and work lists included).
+ * cgh_batch_run - enqueue one progressive hologram per scene, with a fixed number of
+ * launches whatever the number of scenes: one clear of the selection flags and holograms,
+ * one DWT, the three selection passes (counts, scan, ordered scatter, which also marks the
+ * tensor-core flags), one compaction and one inverse-DWT operand build, each walking all
+ * scenes; then ONE persistent stage-1 launch and ONE persistent stage-2 launch whose work
+ * units span every scene (uneven sizes and work lists included).
  */
 int cgh_batch_run(cgh_batch* batch, void* stream);
 
@@ -517,6 +522,15 @@ int cgh_batch_run(cgh_batch* batch, void* stream);
  * the autotuner of the Python package; default 32.
  */
 int cgh_batch_set_tuning(cgh_batch* batch, int ksteps_per_unit);
+
+/*
+ * cgh_batch_set_stage2_tiles - tile shape of the batch's stage-2 launch: CGH_TILES_CTA (or
+ * CGH_TILES_AUTO, the default) one CTA per 128 x 128 tile, CGH_TILES_PAIR two CTAs of a
+ * cluster per 256 x 128 tile (tcgen05 cta_group::2; one CTA per tile where the device holds
+ * no pair).  Chosen by the autotuner of the Python package with the K steps per unit.
+ * Applies to later runs (no synchronisation needed).  The paper has no counterpart.
+ */
+int cgh_batch_set_stage2_tiles(cgh_batch* batch, int tiles);
 
 /* cgh_batch_lists - device pointers of scene k's work lists [4], counts int32[4][2] and
  * coefficients (owned by the batch; valid after a run has completed). */

@@ -1,12 +1,14 @@
-"""Autotuner for the batched tensor-core launch: picks the number of 32-wide K steps per
-stage-2 work unit (how finely each scene's K is split across the persistent CTAs, which is
-also the longest accumulation chain) by timing the batch with CUDA events, among the
-candidates the form's accuracy bar allows, and caches the choice in a JSON file keyed by
-the batch's shape signature, the form and the GPU name."""
+"""Autotuner for the batched tensor-core launch.  It picks the stage-2 tile shape (one CTA
+per 128x128 tile, or a CTA pair per 256x128 tile on tcgen05 cta_group::2) and the number of
+32-wide K steps per stage-2 work unit (how finely each scene's K is split across the
+persistent CTAs, which is also the longest accumulation chain) by timing the batch with
+CUDA events, among the candidates the form's accuracy bar allows, and caches the choice in a
+JSON file keyed by the batch's shape signature, the form and the GPU name."""
 import json
 import os
 
 CANDIDATES = (8, 16, 32, 64, 128)
+TILES = {"cta": 1, "pair": 2}  # Plan.TILES_CTA, Plan.TILES_PAIR
 # Longest stage-2 accumulation chain (K steps) each form may use: the tensor pipe's FP32
 # accumulation error grows with the number of MMAs summed in one accumulator, and the fp16
 # hi+lo form keeps its chains at <= 32 K steps so that its holograms stay within the 1e-5
@@ -30,28 +32,33 @@ def tune_batch(batch, plans, form, stream, cache_path=None, reps=3, candidates=C
             cache = json.load(open(cache_path))
         except Exception:
             cache = {}
-    if key in cache:
+    if key in cache and "tiles" in cache[key]:
+        batch.set_stage2_tiles(TILES[cache[key]["tiles"]])
         batch.set_tuning(cache[key]["ksteps"])
         return cache[key]
     results = {}
     cap = MAX_CHAIN.get(form, max(candidates))
-    for c in [c for c in candidates if c <= cap]:
-        batch.set_tuning(c)
-        with torch.cuda.stream(stream):
-            batch.run(stream=stream)  # warm
-        times = []
-        for _ in range(reps):
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for tname, tval in TILES.items():
+        batch.set_stage2_tiles(tval)
+        for c in [c for c in candidates if c <= cap]:
+            batch.set_tuning(c)
             with torch.cuda.stream(stream):
-                e0.record(stream)
-                batch.run(stream=stream)
-                e1.record(stream)
-            torch.cuda.synchronize()
-            times.append(e0.elapsed_time(e1))
-        results[c] = sorted(times)[len(times) // 2]
+                batch.run(stream=stream)  # warm
+            times = []
+            for _ in range(reps):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                with torch.cuda.stream(stream):
+                    e0.record(stream)
+                    batch.run(stream=stream)
+                    e1.record(stream)
+                torch.cuda.synchronize()
+                times.append(e0.elapsed_time(e1))
+            results[(tname, c)] = sorted(times)[len(times) // 2]
     best = min(results, key=results.get)
-    batch.set_tuning(best)
-    entry = {"ksteps": best, "ms": results[best], "tried": {str(k): v for k, v in results.items()}}
+    batch.set_stage2_tiles(TILES[best[0]])
+    batch.set_tuning(best[1])
+    entry = {"tiles": best[0], "ksteps": best[1], "ms": results[best],
+             "tried": {f"{t}/{k}": v for (t, k), v in results.items()}}
     if cache_path:
         cache[key] = entry
         tmp = cache_path + ".tmp"

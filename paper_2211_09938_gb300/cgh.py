@@ -74,6 +74,7 @@ SIGNATURES = {
                               ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_I),
                               ctypes.POINTER(_P), _I, _P]),
     "cgh_batch_run": (_I, [_P, _P]),
+    "cgh_batch_set_stage2_tiles": (_I, [_P, _I]),
     "cgh_batch_set_tuning": (_I, [_P, _I]),
     "cgh_batch_lists": (_I, [_P, _I, ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_P)]),
     "cgh_batch_destroy": (_I, [_P]),
@@ -503,6 +504,10 @@ class Batch:
 
     def set_tuning(self, ksteps_per_unit):
         check(lib().cgh_batch_set_tuning(self.handle, int(ksteps_per_unit)))
+
+    def set_stage2_tiles(self, tiles):
+        """Plan.TILES_CTA (128x128 per CTA) or Plan.TILES_PAIR (256x128 per CTA pair)."""
+        check(lib().cgh_batch_set_stage2_tiles(self.handle, int(tiles)))
 
     def lists(self, k):
         """(lists [4] as raw device pointers, counts pointer, coeffs pointer) of scene k."""

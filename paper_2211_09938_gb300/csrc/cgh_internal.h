@@ -174,6 +174,25 @@ struct TcFlags {
   uint8_t *occ3, *rowband, *colband, *sel[4];
 };
 
+// Batches (one launch per preparation kernel across scenes).
+struct HaarItem {  // one (scene, layer) plane of the batched DWT
+  const uint8_t* I;
+  const uint8_t* L;
+  int32_t* coef;
+  int H, W, z;
+};
+struct SelTaskB {  // one selection of one scene of the batched selection
+  SelTask t;       // chunk0 and cnt_off over the whole batch
+  const uint8_t* sal;
+  const uint8_t* L;
+  int H, W, Z;
+  TcFlags fl;
+};
+cudaError_t launch_haar_batch(const HaarItem* d_items, int n_items, int max_h, int max_w, cudaStream_t st);
+cudaError_t launch_select_batch(const SelTaskB* d_tasks, int n_tasks, int total_chunks, int max_scan_blocks,
+                                int* chunk_cnt, int* chunk_off, cudaStream_t st);
+int select_scan_blocks(int n_layers, int nchunks);
+
 // Separable tensor-core path (kernels_tc.cu).
 int tc_progressive(const cgh_plan* p, const int32_t* coef, const int32_t* const* lists,
                    const int32_t* d_counts, float2* holo, int accumulate, int form, cudaStream_t st);

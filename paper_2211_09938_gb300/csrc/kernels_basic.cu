@@ -81,13 +81,8 @@ cudaError_t launch_build_tables(const cgh_plan* p, cudaStream_t st) {
 // (A2) three-level integer Haar DWT of every layer plane (Eq. 2, Section 2 step 1).
 // One thread per (8x8 block, layer).  The 2x2 cell [a b; c d] gives
 // S = a+b+c+d, X = a-b+c-d, Y = a+b-c-d, D = a-b-c+d; Mallat output.
-__global__ void __launch_bounds__(128) k_haar3(const uint8_t* __restrict__ I,
-                                               const uint8_t* __restrict__ L,
-                                               int32_t* __restrict__ coef, int H, int W) {
-  const int bx = blockIdx.x * blockDim.x + threadIdx.x;
-  const int by = blockIdx.y * blockDim.y + threadIdx.y;
-  const int z = blockIdx.z;
-  if (bx >= (W >> 3) || by >= (H >> 3)) return;
+__device__ __forceinline__ void haar3_block(const uint8_t* __restrict__ I, const uint8_t* __restrict__ L,
+                                            int32_t* __restrict__ coef, int H, int W, int z, int bx, int by) {
   int a[8][8];
 #pragma unroll
   for (int r = 0; r < 8; ++r) {
@@ -148,6 +143,32 @@ __global__ void __launch_bounds__(128) k_haar3(const uint8_t* __restrict__ I,
   P[(size_t)by * W + w3 + bx] = A - B + C - D;
   P[(size_t)(h3 + by) * W + bx] = A + B - C - D;
   P[(size_t)(h3 + by) * W + w3 + bx] = A - B - C + D;
+}
+
+__global__ void __launch_bounds__(128) k_haar3(const uint8_t* __restrict__ I,
+                                               const uint8_t* __restrict__ L,
+                                               int32_t* __restrict__ coef, int H, int W) {
+  const int bx = blockIdx.x * blockDim.x + threadIdx.x;
+  const int by = blockIdx.y * blockDim.y + threadIdx.y;
+  if (bx >= (W >> 3) || by >= (H >> 3)) return;
+  haar3_block(I, L, coef, H, W, blockIdx.z, bx, by);
+}
+
+// Batched DWT: grid.z walks the (scene, layer) items; x and y cover the largest scene.
+__global__ void __launch_bounds__(128) k_haar3_batch(const HaarItem* __restrict__ items) {
+  const HaarItem it = items[blockIdx.z];
+  const int bx = blockIdx.x * blockDim.x + threadIdx.x;
+  const int by = blockIdx.y * blockDim.y + threadIdx.y;
+  if (bx >= (it.W >> 3) || by >= (it.H >> 3)) return;
+  haar3_block(it.I, it.L, it.coef, it.H, it.W, it.z, bx, by);
+}
+
+cudaError_t launch_haar_batch(const HaarItem* d_items, int n_items, int max_h, int max_w, cudaStream_t st) {
+  if (n_items <= 0) return cudaSuccess;
+  dim3 block(32, 4);
+  dim3 grid(((max_w >> 3) + 31) / 32, ((max_h >> 3) + 3) / 4, n_items);
+  k_haar3_batch<<<grid, block, 0, st>>>(d_items);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_haar(const cgh_plan* p, const uint8_t* I, const uint8_t* L, int32_t* coef,
@@ -222,15 +243,10 @@ __device__ __forceinline__ int sel_task_of(const SelTasks& T, int chunk) {
 }
 
 // Pass 1: per (task, layer, chunk) counts; one thread per block of the chunk.
-__global__ void __launch_bounds__(CGH_SEL_CHUNK) k_select_count(const uint8_t* __restrict__ sal,
-                                                                const uint8_t* __restrict__ L, int H, int W,
-                                                                int Z, const SelTasks T,
-                                                                int* __restrict__ chunk_cnt) {
+__device__ __forceinline__ void select_count_body(const uint8_t* __restrict__ sal, const uint8_t* __restrict__ L,
+                                                  int H, int W, int Z, const SelTask& tk, int chunk,
+                                                  int* __restrict__ chunk_cnt) {
   __shared__ int s_cnt[CGH_MAX_LAYERS];
-  pdl_wait();
-  pdl_trigger();
-  const SelTask& tk = T.t[sel_task_of(T, blockIdx.x)];
-  const int chunk = blockIdx.x - tk.chunk0;
   const int level = tk.level, nbx = W >> level, nb = (H >> level) * nbx;
   for (int t = threadIdx.x; t < Z; t += blockDim.x) s_cnt[t] = 0;
   if (chunk == 0 && threadIdx.x == 0) tk.count[1] = 0;  // the scan's CTA counter
@@ -244,6 +260,16 @@ __global__ void __launch_bounds__(CGH_SEL_CHUNK) k_select_count(const uint8_t* _
   }
   __syncthreads();
   for (int z = threadIdx.x; z < Z; z += blockDim.x) chunk_cnt[tk.cnt_off + z * tk.nchunks + chunk] = s_cnt[z];
+}
+
+__global__ void __launch_bounds__(CGH_SEL_CHUNK) k_select_count(const uint8_t* __restrict__ sal,
+                                                                const uint8_t* __restrict__ L, int H, int W,
+                                                                int Z, const SelTasks T,
+                                                                int* __restrict__ chunk_cnt) {
+  pdl_wait();
+  pdl_trigger();
+  const SelTask& tk = T.t[sel_task_of(T, blockIdx.x)];
+  select_count_body(sal, L, H, W, Z, tk, blockIdx.x - tk.chunk0, chunk_cnt);
 }
 
 // Pass 2: per task, exclusive scan of its counts in (layer, chunk) order, in blocks of
@@ -283,15 +309,12 @@ __device__ __forceinline__ int cta_exclusive_scan(int x, int* s_warp, int& total
   return r;
 }
 
-__global__ void __launch_bounds__(1024) k_select_scan(int* chunk_cnt, int* __restrict__ chunk_off,
-                                                      int Z, const SelTasks T) {
+__device__ __forceinline__ void select_scan_body(int* chunk_cnt, int* __restrict__ chunk_off, int Z,
+                                                 const SelTask& tk, int blk) {
   __shared__ int s_warp[33];
   __shared__ int s_last;
-  pdl_wait();
-  pdl_trigger();
-  const SelTask& tk = T.t[blockIdx.y];
   const int n = Z * tk.nchunks, nblk = (n + SEL_SCAN_BLOCK - 1) / SEL_SCAN_BLOCK;
-  const int b0 = blockIdx.x * SEL_SCAN_BLOCK;
+  const int b0 = blk * SEL_SCAN_BLOCK;
   if (b0 >= n) return;
   int* cnt = chunk_cnt + tk.cnt_off;
   int* off = chunk_off + tk.cnt_off;
@@ -333,19 +356,26 @@ __global__ void __launch_bounds__(1024) k_select_scan(int* chunk_cnt, int* __res
   }
 }
 
+__global__ void __launch_bounds__(1024) k_select_scan(int* chunk_cnt, int* __restrict__ chunk_off,
+                                                      int Z, const SelTasks T) {
+  pdl_wait();
+  pdl_trigger();
+  select_scan_body(chunk_cnt, chunk_off, Z, T.t[blockIdx.y], blockIdx.x);
+}
+
 // Pass 3: ordered scatter.  Per layer, warp ballots give every warp's count and every
 // thread's rank inside its warp; one shared exclusive scan over the warps (per layer) gives
 // the warp offsets.  Two barriers per CTA whatever the number of layers.
-__global__ void __launch_bounds__(CGH_SEL_CHUNK) k_select_scatter(
-    const uint8_t* __restrict__ sal, const uint8_t* __restrict__ L, int H, int W, int Z, const SelTasks T,
-    const int* __restrict__ chunk_cnt, const int* __restrict__ chunk_off) {
+// FLAGS: also mark the tensor-core selection flags of every written entry (as the fused
+// selection does; fl is then the scene's flag block).
+template <bool FLAGS>
+__device__ __forceinline__ void select_scatter_body(const uint8_t* __restrict__ sal, const uint8_t* __restrict__ L,
+                                                    int H, int W, int Z, const SelTask& tk, int chunk,
+                                                    const int* __restrict__ chunk_cnt,
+                                                    const int* __restrict__ chunk_off, const TcFlags& fl) {
   constexpr int NW = CGH_SEL_CHUNK / 32;
   __shared__ int s_wcnt[NW][CGH_MAX_LAYERS];
   __shared__ int s_pre[CGH_MAX_LAYERS];
-  pdl_wait();
-  pdl_trigger();
-  const SelTask& tk = T.t[sel_task_of(T, blockIdx.x)];
-  const int chunk = blockIdx.x - tk.chunk0;
   const int level = tk.level, nbx = W >> level, nb = (H >> level) * nbx;
   const int b = chunk * CGH_SEL_CHUNK + threadIdx.x;
   const int by = b / nbx, bx = b - by * nbx;
@@ -372,14 +402,98 @@ __global__ void __launch_bounds__(CGH_SEL_CHUNK) k_select_scatter(
     s_pre[threadIdx.x] = chunk_cnt[tk.cnt_off + (e / SEL_SCAN_BLOCK) * SEL_SCAN_BLOCK] + chunk_off[tk.cnt_off + e];
   }
   __syncthreads();
+  const int hl = H >> level, wl = W >> level;
   for (int z = 0; z < Z; ++z) {
     const bool f = (m >> z) & 1ull;
     const unsigned bal = __ballot_sync(0xffffffffu, f);
     if (f) {
       const int pos = s_pre[z] + s_wcnt[warp][z] + __popc(bal & below);
-      if (pos < tk.capacity) tk.list[pos] = (z << 24) | (by << 12) | bx;
+      if (pos < tk.capacity) {
+        tk.list[pos] = (z << 24) | (by << 12) | bx;
+        if (FLAGS) {
+          if (tk.flag_kind == SEL_FLAGS_LLL) {
+            fl.occ3[((size_t)z * hl + by) * wl + bx] = 1;
+            fl.rowband[(size_t)z * hl + by] = 1;
+            fl.colband[(size_t)z * wl + bx] = 1;
+          } else if (tk.flag_kind == SEL_FLAGS_DETAIL) {
+            uint8_t* sel = level == 1 ? fl.sel[1] : level == 2 ? fl.sel[2] : fl.sel[3];
+            sel[((size_t)z * hl + by) * wl + bx] = 1;
+            fl.rowband[(size_t)z * (H >> 3) + (by >> (3 - level))] = 1;
+            fl.colband[(size_t)z * (W >> 3) + (bx >> (3 - level))] = 1;
+          }
+        }
+      }
     }
   }
+}
+
+__global__ void __launch_bounds__(CGH_SEL_CHUNK) k_select_scatter(
+    const uint8_t* __restrict__ sal, const uint8_t* __restrict__ L, int H, int W, int Z, const SelTasks T,
+    const int* __restrict__ chunk_cnt, const int* __restrict__ chunk_off) {
+  pdl_wait();
+  pdl_trigger();
+  const SelTask& tk = T.t[sel_task_of(T, blockIdx.x)];
+  select_scatter_body<false>(sal, L, H, W, Z, tk, blockIdx.x - tk.chunk0, chunk_cnt, chunk_off, TcFlags{});
+}
+
+// Batched three-pass selection: every task carries its scene; chunks of all tasks form one
+// grid (a task's chunk0 and cnt_off are global), found by binary search.
+__device__ __forceinline__ int sel_task_of_batch(const SelTaskB* __restrict__ tasks, int n, int chunk) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (tasks[mid].t.chunk0 <= chunk)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  return lo;
+}
+
+__global__ void __launch_bounds__(CGH_SEL_CHUNK) k_select_count_batch(const SelTaskB* __restrict__ tasks, int n,
+                                                                      int* __restrict__ chunk_cnt) {
+  pdl_wait();
+  pdl_trigger();
+  const SelTaskB& tb = tasks[sel_task_of_batch(tasks, n, blockIdx.x)];
+  select_count_body(tb.sal, tb.L, tb.H, tb.W, tb.Z, tb.t, blockIdx.x - tb.t.chunk0, chunk_cnt);
+}
+
+__global__ void __launch_bounds__(1024) k_select_scan_batch(const SelTaskB* __restrict__ tasks, int* chunk_cnt,
+                                                            int* __restrict__ chunk_off) {
+  pdl_wait();
+  pdl_trigger();
+  const SelTaskB& tb = tasks[blockIdx.y];
+  select_scan_body(chunk_cnt, chunk_off, tb.Z, tb.t, blockIdx.x);
+}
+
+__global__ void __launch_bounds__(CGH_SEL_CHUNK) k_select_scatter_batch(const SelTaskB* __restrict__ tasks, int n,
+                                                                        const int* __restrict__ chunk_cnt,
+                                                                        const int* __restrict__ chunk_off) {
+  pdl_wait();
+  pdl_trigger();
+  const SelTaskB& tb = tasks[sel_task_of_batch(tasks, n, blockIdx.x)];
+  select_scatter_body<true>(tb.sal, tb.L, tb.H, tb.W, tb.Z, tb.t, blockIdx.x - tb.t.chunk0, chunk_cnt, chunk_off,
+                            tb.fl);
+}
+
+// The three passes over all tasks of a batch (the tasks' chunk0 / cnt_off / nchunks set by
+// the caller): lists, counts and, for tasks with a flag kind, the tensor-core flags.
+cudaError_t launch_select_batch(const SelTaskB* d_tasks, int n_tasks, int total_chunks, int max_scan_blocks,
+                                int* chunk_cnt, int* chunk_off, cudaStream_t st) {
+  if (n_tasks <= 0) return cudaSuccess;
+  cudaError_t e = launch_pdl(k_select_count_batch, dim3(total_chunks), dim3(CGH_SEL_CHUNK), 0, st, d_tasks, n_tasks,
+                             chunk_cnt);
+  if (e == cudaSuccess)
+    e = launch_pdl(k_select_scan_batch, dim3(max_scan_blocks, n_tasks), dim3(1024), 0, st, d_tasks, chunk_cnt,
+                   chunk_off);
+  if (e == cudaSuccess)
+    e = launch_pdl(k_select_scatter_batch, dim3(total_chunks), dim3(CGH_SEL_CHUNK), 0, st, d_tasks, n_tasks,
+                   (const int*)chunk_cnt, (const int*)chunk_off);
+  return e != cudaSuccess ? e : cudaGetLastError();
+}
+
+int select_scan_blocks(int n_layers, int nchunks) {
+  return (n_layers * nchunks + SEL_SCAN_BLOCK - 1) / SEL_SCAN_BLOCK;
 }
 
 // ---------------------------------------------------------------------------

@@ -12,6 +12,8 @@
 // hi*hi + hi*lo + lo*hi (three MMAs) with FP32 accumulation in tensor memory; a complex
 // product is four real ones (the imaginary-times-imaginary term negated through the
 // instruction descriptor).  A^_z is 64x an integer <= 16320, exact in hi + lo.
+#include <vector>
+
 #include "tc_fused.cuh"
 #include "tc_gemm_pair.cuh"
 
@@ -84,17 +86,29 @@ __device__ int block_scan_flags(int f, int* s_warp, int* total) {
 // asks for columns): H^T = sum_z E_z A^_z^T E_z^T is then computed and written transposed.
 // Every CTA counts the kept bands of all layers (for the decision and for its layer's
 // offset in the concatenated K); CTA 0 records the decision.
-__global__ void __launch_bounds__(1024) k_tc_compact(TcFlags fl, int H, int W, int Z, int order,
-                                                     int* __restrict__ rows, int* __restrict__ cols,
-                                                     int* __restrict__ kr_pad, int* __restrict__ kc_pad, int ld_rows,
-                                                     int ld_cols, int* __restrict__ rband, int* __restrict__ cband,
-                                                     int* __restrict__ kmap2, int* __restrict__ orient,
-                                                     int* __restrict__ fused_sync) {
+struct CompactArgs {
+  TcFlags fl;
+  int H, W, Z, order;
+  int *rows, *cols, *kr_pad, *kc_pad;
+  int ld_rows, ld_cols;
+  int *rband, *cband, *kmap2, *orient, *fused_sync;
+};
+
+__device__ __forceinline__ void compact_body(const CompactArgs& A, int z) {
+  const TcFlags& fl = A.fl;
+  const int H = A.H, W = A.W, Z = A.Z, order = A.order, ld_rows = A.ld_rows, ld_cols = A.ld_cols;
+  int* const rows = A.rows;
+  int* const cols = A.cols;
+  int* const kr_pad = A.kr_pad;
+  int* const kc_pad = A.kc_pad;
+  int* const rband = A.rband;
+  int* const cband = A.cband;
+  int* const kmap2 = A.kmap2;
+  int* const orient = A.orient;
+  int* const fused_sync = A.fused_sync;
   __shared__ int s_warp[33];
   __shared__ int s_cnt[2][CGH_MAX_LAYERS];  // kept bands per layer: object rows, object columns
-  pdl_wait();
-  pdl_trigger();
-  const int z = blockIdx.x, t = threadIdx.x;
+  const int t = threadIdx.x;
   for (int e = t; e < 2 * CGH_MAX_LAYERS; e += blockDim.x) s_cnt[e / CGH_MAX_LAYERS][e % CGH_MAX_LAYERS] = 0;
   __syncthreads();
   for (int axis = 0; axis < 2; ++axis) {
@@ -146,6 +160,21 @@ __global__ void __launch_bounds__(1024) k_tc_compact(TcFlags fl, int H, int W, i
     if (t == 0) (role == 0 ? kr_pad : kc_pad)[z] = 32 * total;
     __syncthreads();
   }
+}
+
+__global__ void __launch_bounds__(1024) k_tc_compact(const CompactArgs A) {
+  pdl_wait();
+  pdl_trigger();
+  compact_body(A, blockIdx.x);
+}
+
+// Batched compaction: blockIdx.y is the scene, blockIdx.x its layer.
+__global__ void __launch_bounds__(1024) k_tc_compact_batch(const CompactArgs* __restrict__ scenes) {
+  pdl_wait();
+  pdl_trigger();
+  const CompactArgs& A = scenes[blockIdx.y];
+  if ((int)blockIdx.x >= A.Z) return;
+  compact_body(A, blockIdx.x);
 }
 
 // 64 x A^_z at eight consecutive pixels of one object row (ALONG_Y = false: (y0, x0 + q))
@@ -209,22 +238,36 @@ __device__ __forceinline__ void idwt_run8(const int32_t* __restrict__ P, const T
 // Stage-1 B operand: 64 x A^_z at (rows[k], cols[c .. c+7]), or, in the transposed order,
 // at (cols[c .. c+7], rows[k]) (the "rows" then hold object columns).  One thread builds the
 // eight compacted columns of one 8-pixel band (or of padding).
+struct IdwtArgs {
+  const int32_t* coef;
+  TcFlags fl;
+  const int *rows, *cols, *kr_pad, *kc_pad, *orient;
+  int H, W, ld_rows, ld_cols;
+  uint16_t* B1;
+  long long b1_plane;
+  int ldb1;
+};
+
 template <bool F16>
-__global__ void k_tc_idwt(const int32_t* __restrict__ coef, TcFlags fl, const int* __restrict__ rows,
-                          const int* __restrict__ cols, const int* __restrict__ kr_pad,
-                          const int* __restrict__ kc_pad, const int* __restrict__ orient, int H, int W,
-                          int ld_rows, int ld_cols, uint16_t* __restrict__ B1, long long b1_plane, int ldb1) {
+__device__ __forceinline__ void idwt_body(const IdwtArgs& A, int z, int bxi, int byi) {
+  const int32_t* __restrict__ coef = A.coef;
+  const TcFlags& fl = A.fl;
+  const int* __restrict__ rows = A.rows;
+  const int* __restrict__ cols = A.cols;
+  const int* __restrict__ kr_pad = A.kr_pad;
+  const int* __restrict__ kc_pad = A.kc_pad;
+  const int* __restrict__ orient = A.orient;
+  const int H = A.H, W = A.W, ld_rows = A.ld_rows, ld_cols = A.ld_cols, ldb1 = A.ldb1;
+  uint16_t* __restrict__ B1 = A.B1;
+  const long long b1_plane = A.b1_plane;
   __shared__ int s_kr[CGH_MAX_LAYERS];
-  pdl_wait();
-  pdl_trigger();
-  const int z = blockIdx.z;
   // the layers' row counts, loaded in parallel (a per-thread loop of loads would cost a memory
   // latency per earlier layer)
   const int tid = threadIdx.y * blockDim.x + threadIdx.x;
   if (tid <= z) s_kr[tid] = kr_pad[tid];
   __syncthreads();
-  const int c = 8 * (blockIdx.x * blockDim.x + threadIdx.x);
-  const int k = blockIdx.y * blockDim.y + threadIdx.y;
+  const int c = 8 * (bxi * blockDim.x + threadIdx.x);
+  const int k = byi * blockDim.y + threadIdx.y;
   if (k >= s_kr[z] || c >= kc_pad[z]) return;
   int off = 0;
   for (int q = 0; q < z; ++q) off += s_kr[q];
@@ -251,6 +294,25 @@ __global__ void k_tc_idwt(const int32_t* __restrict__ coef, TcFlags fl, const in
   uint16_t* dst = B1 + (size_t)(off + k) * ldb1 + c;
   *reinterpret_cast<uint4*>(dst) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
   *reinterpret_cast<uint4*>(dst + b1_plane) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+}
+
+template <bool F16>
+__global__ void k_tc_idwt(const IdwtArgs A) {
+  pdl_wait();
+  pdl_trigger();
+  idwt_body<F16>(A, blockIdx.z, blockIdx.x, blockIdx.y);
+}
+
+// Batched inverse DWT: blockIdx.z walks the (scene, layer) items (item.x scene, item.y
+// layer); x and y cover the largest scene.
+template <bool F16>
+__global__ void k_tc_idwt_batch(const IdwtArgs* __restrict__ scenes, const int2* __restrict__ items) {
+  pdl_wait();
+  pdl_trigger();
+  const int2 it = items[blockIdx.z];
+  const IdwtArgs& A = scenes[it.x];
+  if ((int)blockIdx.x * (int)blockDim.x * 8 >= A.ld_cols || (int)blockIdx.y * (int)blockDim.y >= A.ld_rows) return;
+  idwt_body<F16>(A, it.y, blockIdx.x, blockIdx.y);
 }
 
 // Shared-memory opt-in of every GEMM instantiation on the current device; called outside
@@ -396,6 +458,19 @@ static int stage2_splits(int tiles, int kmax_steps) {
     if (_rc != CGH_OK) return _rc;                          \
   } while (0)
 
+static CompactArgs compact_args(const cgh_plan* p) {
+  cgh_tc_state* t = p->tc;
+  return CompactArgs{t->fl,       p->obj_h,    p->obj_w,     p->n_layers, p->contraction, t->rows,
+                     t->cols,     t->kr_pad,   t->kc_pad,    t->kr_alloc, t->kc_alloc,    t->rband,
+                     t->cband,    t->kmap2,    t->orient,    t->fused_sync};
+}
+
+static IdwtArgs idwt_args(const cgh_plan* p, const int32_t* coef) {
+  cgh_tc_state* t = p->tc;
+  return IdwtArgs{coef,     t->fl,       t->rows,     t->cols,     t->kr_pad,   t->kc_pad,   t->orient,
+                  p->obj_h, p->obj_w,    t->kr_alloc, t->kc_alloc, t->B1,       t->b1_plane, t->kc_alloc};
+}
+
 // Operands of both GEMM stages for one scene: selection flags, per-layer band compaction,
 // the stage-2 K-step map and the inverse-DWT operand (stage-1 B).  The A operands of both
 // stages are the plan's fringe planes (eops_get), read band by band through the K maps.
@@ -415,17 +490,11 @@ static int tc_prep(const cgh_plan* p, const int32_t* coef, const int32_t* const*
                      d_counts, t->fl, H, W, Z, p->d_status),
           "tc: scatter");
   }
-  TC_CK(launch_pdl(k_tc_compact, dim3(Z), dim3(1024), 0, st, t->fl, H, W, Z, p->contraction, t->rows, t->cols,
-                   t->kr_pad, t->kc_pad, t->kr_alloc, t->kc_alloc, t->rband, t->cband, t->kmap2, t->orient,
-                   t->fused_sync),
-        "tc: compact");
+  TC_CK(launch_pdl(k_tc_compact, dim3(Z), dim3(1024), 0, st, compact_args(p)), "tc: compact");
   if (coef_ready) TC_CK(cudaStreamWaitEvent(st, coef_ready, 0), "tc: wait for the coefficients");
   {
     dim3 blk(8, 32), grid((t->kc_alloc / 8 + 7) / 8, (t->kr_alloc + 31) / 32, Z);
-    TC_CK(launch_pdl(k_tc_idwt<F16>, grid, blk, 0, st, coef, t->fl, (const int*)t->rows, (const int*)t->cols,
-                     (const int*)t->kr_pad, (const int*)t->kc_pad, (const int*)t->orient, H, W, t->kr_alloc,
-                     t->kc_alloc, t->B1, t->b1_plane, t->kc_alloc),
-          "tc: idwt");
+    TC_CK(launch_pdl(k_tc_idwt<F16>, grid, blk, 0, st, idwt_args(p, coef)), "tc: idwt");
   }
 
   return CGH_OK;
@@ -567,6 +636,18 @@ __global__ void k_batch_koff(TcBatchItem* __restrict__ a, TcBatchItem* __restric
   }
 }
 
+// A region the batch clears before its preparation (selection flags, holograms).
+struct ZeroRegion {
+  float4* p;
+  long long n;  // float4 units
+};
+
+__global__ void k_zero_regions(const ZeroRegion* __restrict__ regs) {
+  const ZeroRegion r = regs[blockIdx.y];
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < r.n; i += (long long)gridDim.x * blockDim.x)
+    r.p[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
 struct cgh_batch {
   int n, form, ksteps;
   cgh_plan** plans;
@@ -577,12 +658,114 @@ struct cgh_batch {
   int32_t** lists;  // [n][4]
   int32_t* counts;  // device [n][4][2]
   TcBatchItem *h1, *h2, *d1, *d2;
-  int units1, units2;
+  int units1, units2, units2p;
+  int stage2_tiles;  // CGH_TILES_*: stage 2 on one CTA per tile or on CTA pairs
+  // one launch per preparation kernel across the scenes: device tables and scratch
+  ZeroRegion* d_zero;
+  int n_zero;
+  HaarItem* d_haar;
+  int n_haar, max_h, max_w;
+  SelTaskB* d_sel;
+  int n_sel, sel_chunks, sel_scan_blocks;
+  int *sel_cnt, *sel_off;
+  CompactArgs* d_compact;
+  int max_z;
+  IdwtArgs* d_idwt;
+  int2* d_idwt_items;
+  int max_kr, max_kc;
 };
+
+// Device tables of the batched preparation (built once per batch: every pointer is fixed).
+static int batch_prep_tables(cgh_batch* b) {
+  const int n = b->n;
+  std::vector<ZeroRegion> zero;
+  std::vector<HaarItem> haar;
+  std::vector<SelTaskB> sel;
+  std::vector<CompactArgs> comp;
+  std::vector<IdwtArgs> idw;
+  std::vector<int2> items;
+  int chunk0 = 0, cnt_off = 0, scan_blocks = 1;
+  b->max_h = b->max_w = b->max_z = b->max_kr = b->max_kc = 0;
+  for (int i = 0; i < n; ++i) {
+    const cgh_plan* p = b->plans[i];
+    cgh_tc_state* t = p->tc;
+    const int H = p->obj_h, W = p->obj_w, Z = p->n_layers;
+    zero.push_back(ZeroRegion{reinterpret_cast<float4*>(t->flags), (long long)(t->flags_alloc / 16)});
+    const size_t hb = (size_t)p->holo_h * p->holo_w * sizeof(float2);
+    if (hb % 16 || ((uintptr_t)b->H[i] & 15))
+      return cgh_fail(CGH_ERR_ARG, "cgh_batch: hologram %d must be 16-byte aligned with an even pixel count", i);
+    zero.push_back(ZeroRegion{reinterpret_cast<float4*>(b->H[i]), (long long)(hb / 16)});
+    for (int z = 0; z < Z; ++z) {
+      haar.push_back(HaarItem{b->I[i], b->L[i], b->coeffs[i], H, W, z});
+      items.push_back(make_int2(i, z));
+    }
+    for (int k = 0; k < 4; ++k) {
+      SelTaskB tb;
+      memset(&tb, 0, sizeof(tb));
+      const int lvl = k == 0 ? CGH_LEVELS : k;
+      tb.t.level = lvl;
+      tb.t.threshold = k == 0 ? -1 : b->thr[k - 1];
+      tb.t.capacity = Z * (H >> lvl) * (W >> lvl);
+      tb.t.nchunks = select_num_chunks(H, W, lvl);
+      tb.t.chunk0 = chunk0;
+      tb.t.cnt_off = cnt_off;
+      tb.t.flag_kind = k == 0 ? SEL_FLAGS_LLL : SEL_FLAGS_DETAIL;
+      tb.t.list = b->lists[4 * i + k];
+      tb.t.count = b->counts + 8 * i + 2 * k;
+      tb.sal = k == 0 ? nullptr : b->S[i];
+      tb.L = b->L[i];
+      tb.H = H;
+      tb.W = W;
+      tb.Z = Z;
+      tb.fl = t->fl;
+      chunk0 += tb.t.nchunks;
+      cnt_off += Z * tb.t.nchunks;
+      const int sb = select_scan_blocks(Z, tb.t.nchunks);
+      scan_blocks = sb > scan_blocks ? sb : scan_blocks;
+      sel.push_back(tb);
+    }
+    comp.push_back(compact_args(p));
+    idw.push_back(idwt_args(p, b->coeffs[i]));
+    b->max_h = H > b->max_h ? H : b->max_h;
+    b->max_w = W > b->max_w ? W : b->max_w;
+    b->max_z = Z > b->max_z ? Z : b->max_z;
+    b->max_kr = t->kr_alloc > b->max_kr ? t->kr_alloc : b->max_kr;
+    b->max_kc = t->kc_alloc > b->max_kc ? t->kc_alloc : b->max_kc;
+  }
+  b->n_zero = (int)zero.size();
+  b->n_haar = (int)haar.size();
+  b->n_sel = (int)sel.size();
+  b->sel_chunks = chunk0;
+  b->sel_scan_blocks = scan_blocks;
+  if (b->n_haar > 65535) return cgh_fail(CGH_ERR_ARG, "cgh_batch: more than 65535 scene layers");
+#define BP_TRY(expr, what)                            \
+  do {                                                \
+    int _rc = cgh_cuda_check((expr), (what));         \
+    if (_rc != CGH_OK) return _rc;                    \
+  } while (0)
+  BP_TRY(cudaMalloc(&b->d_zero, zero.size() * sizeof(ZeroRegion)), "cgh_batch: tables");
+  BP_TRY(cudaMalloc(&b->d_haar, haar.size() * sizeof(HaarItem)), "cgh_batch: tables");
+  BP_TRY(cudaMalloc(&b->d_sel, sel.size() * sizeof(SelTaskB)), "cgh_batch: tables");
+  BP_TRY(cudaMalloc(&b->d_compact, comp.size() * sizeof(CompactArgs)), "cgh_batch: tables");
+  BP_TRY(cudaMalloc(&b->d_idwt, idw.size() * sizeof(IdwtArgs)), "cgh_batch: tables");
+  BP_TRY(cudaMalloc(&b->d_idwt_items, items.size() * sizeof(int2)), "cgh_batch: tables");
+  BP_TRY(cudaMalloc(&b->sel_cnt, (size_t)cnt_off * sizeof(int)), "cgh_batch: selection scratch");
+  BP_TRY(cudaMalloc(&b->sel_off, (size_t)cnt_off * sizeof(int)), "cgh_batch: selection scratch");
+  BP_TRY(cudaMemcpy(b->d_zero, zero.data(), zero.size() * sizeof(ZeroRegion), cudaMemcpyHostToDevice), "cgh_batch: tables");
+  BP_TRY(cudaMemcpy(b->d_haar, haar.data(), haar.size() * sizeof(HaarItem), cudaMemcpyHostToDevice), "cgh_batch: tables");
+  BP_TRY(cudaMemcpy(b->d_sel, sel.data(), sel.size() * sizeof(SelTaskB), cudaMemcpyHostToDevice), "cgh_batch: tables");
+  BP_TRY(cudaMemcpy(b->d_compact, comp.data(), comp.size() * sizeof(CompactArgs), cudaMemcpyHostToDevice),
+         "cgh_batch: tables");
+  BP_TRY(cudaMemcpy(b->d_idwt, idw.data(), idw.size() * sizeof(IdwtArgs), cudaMemcpyHostToDevice), "cgh_batch: tables");
+  BP_TRY(cudaMemcpy(b->d_idwt_items, items.data(), items.size() * sizeof(int2), cudaMemcpyHostToDevice),
+         "cgh_batch: tables");
+#undef BP_TRY
+  return CGH_OK;
+}
 
 static int batch_upload(cgh_batch* b) {
   const bool f16 = b->form == CGH_FORM_TC_FP16X3;
-  int u1 = 0, u2 = 0;
+  int u1 = 0, u2 = 0, u2p = 0;
   for (int i = 0; i < b->n; ++i) {
     const cgh_plan* p = b->plans[i];
     cgh_tc_state* t = p->tc;
@@ -603,12 +786,16 @@ static int batch_upload(cgh_batch* b) {
     b->h2[i].ma = *mEZ;
     b->h2[i].mb = t->mY;
     b->h2[i].mc = t->mY;
+    b->h2[i].mb64 = t->mY64;
     stage2_args(p, f16, b->H[i], S, b->h2[i].a, tiles);
     b->h2[i].unit0 = u2;
+    b->h2[i].unit0p = u2p;
     u2 += tiles.x * tiles.y * tiles.z;
+    u2p += ((tiles.x + 1) / 2) * tiles.y * tiles.z;
   }
   b->units1 = u1;
   b->units2 = u2;
+  b->units2p = u2p;
   TC_CK(cudaMemcpy(b->d1, b->h1, b->n * sizeof(TcBatchItem), cudaMemcpyHostToDevice), "batch: upload");
   TC_CK(cudaMemcpy(b->d2, b->h2, b->n * sizeof(TcBatchItem), cudaMemcpyHostToDevice), "batch: upload");
   return CGH_OK;
@@ -625,6 +812,14 @@ extern "C" int cgh_batch_destroy(cgh_batch* b) {
   cudaFree(b->counts);
   cudaFree(b->d1);
   cudaFree(b->d2);
+  cudaFree(b->d_zero);
+  cudaFree(b->d_haar);
+  cudaFree(b->d_sel);
+  cudaFree(b->sel_cnt);
+  cudaFree(b->sel_off);
+  cudaFree(b->d_compact);
+  cudaFree(b->d_idwt);
+  cudaFree(b->d_idwt_items);
   free(b->h1);
   free(b->h2);
   free(b->coeffs);
@@ -709,12 +904,19 @@ extern "C" int cgh_batch_create(cgh_batch** out, cgh_plan* const* plans, int n, 
     }
   }
 #undef B_TRY
-  if ((rc = batch_upload(b)) != CGH_OK) {
+  if ((rc = batch_upload(b)) != CGH_OK || (rc = batch_prep_tables(b)) != CGH_OK) {
     cgh_batch_destroy(b);
     return rc;
   }
   (void)stream;
   *out = b;
+  return CGH_OK;
+}
+
+extern "C" int cgh_batch_set_stage2_tiles(cgh_batch* b, int tiles) {
+  if (!b || (tiles != CGH_TILES_CTA && tiles != CGH_TILES_PAIR && tiles != CGH_TILES_AUTO))
+    return cgh_fail(CGH_ERR_ARG, "cgh_batch_set_stage2_tiles: bad argument");
+  b->stage2_tiles = tiles == CGH_TILES_AUTO ? CGH_TILES_CTA : tiles;
   return CGH_OK;
 }
 
@@ -725,40 +927,25 @@ extern "C" int cgh_batch_set_tuning(cgh_batch* b, int ksteps_per_unit) {
   return batch_upload(b);
 }
 
+// One launch per preparation kernel across all scenes: clear flags and holograms, DWT,
+// the three selection passes (which also mark the tensor-core flags), compaction, inverse
+// DWT; then the per-scene K offsets and one persistent launch per GEMM stage.
 template <bool F16>
 static int batch_run(cgh_batch* b, cudaStream_t st) {
-  for (int i = 0; i < b->n; ++i) {
-    cgh_plan* p = b->plans[i];
-    TC_CK(launch_haar(p, b->I[i], b->L[i], b->coeffs[i], st), "batch: DWT");
-    SelTasks T;
-    memset(&T, 0, sizeof(T));
-    T.n = 4;
-    for (int k = 0; k < 4; ++k) {
-      const int lvl = k == 0 ? CGH_LEVELS : k;
-      T.t[k].level = lvl;
-      T.t[k].threshold = k == 0 ? -1 : b->thr[k - 1];
-      T.t[k].capacity = p->n_layers * (p->obj_h >> lvl) * (p->obj_w >> lvl);
-      T.t[k].list = b->lists[4 * i + k];
-      T.t[k].count = b->counts + 8 * i + 2 * k;
-    }
-    cgh_tc_state* t = p->tc;
-    if (t->flags_dirty) TC_CK(cudaMemsetAsync(t->flags, 0, t->flags_bytes, st), "batch: clear flags");
-    t->flags_dirty = 1;
-    for (int k = 0; k < 4; ++k) T.t[k].flag_kind = k == 0 ? SEL_FLAGS_LLL : SEL_FLAGS_DETAIL;
-    const SelCoop coop = plan_sel_coop(p);
-    bool done = false;
-    TC_CK(launch_select_tasks(p->obj_h, p->obj_w, p->n_layers, b->S[i], b->L[i], T, p->d_chunk_cnt, p->d_chunk_off,
-                              st, &coop, &t->fl, &done),
-          "batch: selection");
-    if (!done)
-      TC_CK(launch_pdl(k_tc_scatter, dim3(64, 4), dim3(256), 0, st, b->lists[4 * i], b->lists[4 * i + 1],
-                       b->lists[4 * i + 2], b->lists[4 * i + 3], (const int32_t*)(b->counts + 8 * i), t->fl,
-                       p->obj_h, p->obj_w, p->n_layers, p->d_status),
-            "batch: scatter");
-    const int rc = tc_prep<F16>(p, b->coeffs[i], b->lists + 4 * i, b->counts + 8 * i, st, true);
-    if (rc != CGH_OK) return rc;
-    TC_CK(cudaMemsetAsync(b->H[i], 0, (size_t)p->holo_h * p->holo_w * sizeof(float2), st), "batch: clear");
+  k_zero_regions<<<dim3(64, b->n_zero), 256, 0, st>>>(b->d_zero);
+  TC_CK(cudaGetLastError(), "batch: clear");
+  TC_CK(launch_haar_batch(b->d_haar, b->n_haar, b->max_h, b->max_w, st), "batch: DWT");
+  TC_CK(launch_select_batch(b->d_sel, b->n_sel, b->sel_chunks, b->sel_scan_blocks, b->sel_cnt, b->sel_off, st),
+        "batch: selection");
+  TC_CK(launch_pdl(k_tc_compact_batch, dim3(b->max_z, b->n), dim3(1024), 0, st, (const CompactArgs*)b->d_compact),
+        "batch: compact");
+  {
+    dim3 blk(8, 32), grid((b->max_kc / 8 + 7) / 8, (b->max_kr + 31) / 32, b->n_haar);
+    TC_CK(launch_pdl(k_tc_idwt_batch<F16>, grid, blk, 0, st, (const IdwtArgs*)b->d_idwt,
+                     (const int2*)b->d_idwt_items),
+          "batch: idwt");
   }
+  for (int i = 0; i < b->n; ++i) b->plans[i]->tc->flags_dirty = 1;
   k_batch_koff<<<(b->n + 127) / 128, 128, 0, st>>>(b->d1, b->d2, b->n);
   TC_CK(cudaGetLastError(), "batch: offsets");
   const int sms = tc_num_sms();
@@ -766,9 +953,14 @@ static int batch_run(cgh_batch* b, cudaStream_t st) {
   k_tc_gemm_batch<KIND_CR, EPI_Y, F16><<<b->units1 < sms ? b->units1 : sms, 192, tc_smem_bytes<KIND_CR, EPI_Y>(), st>>>(
       b->d1, b->n, b->units1, status);
   TC_CK(cudaGetLastError(), "batch: stage 1");
-  k_tc_gemm_batch<KIND_CC, EPI_H, F16><<<b->units2 < sms ? b->units2 : sms, 192, tc_smem_bytes<KIND_CC, EPI_H>(), st>>>(
-      b->d2, b->n, b->units2, status);
-  TC_CK(cudaGetLastError(), "batch: stage 2");
+  cudaError_t e = cudaErrorNotSupported;
+  if (b->stage2_tiles == CGH_TILES_PAIR) e = launch_gemm_pair_batch<KIND_CC, F16>(b->d2, b->n, b->units2p, status, st);
+  if (e == cudaErrorNotSupported) {
+    k_tc_gemm_batch<KIND_CC, EPI_H, F16><<<b->units2 < sms ? b->units2 : sms, 192, tc_smem_bytes<KIND_CC, EPI_H>(),
+                                           st>>>(b->d2, b->n, b->units2, status);
+    e = cudaGetLastError();
+  }
+  TC_CK(e, "batch: stage 2");
   return CGH_OK;
 }
 

@@ -799,8 +799,10 @@ struct alignas(128) TcBatchItem {
   CUtensorMap ma;
   CUtensorMap mb;
   CUtensorMap mc;
+  CUtensorMap mb64;  // stage 2 on CTA pairs: B with 64-row boxes
   TcGemmArgs a;
   int unit0;
+  int unit0p;        // stage 2 on CTA pairs: first pair unit
   int koff[CGH_MAX_LAYERS + 1];
 };
 

@@ -121,9 +121,11 @@ constexpr size_t pair_smem_bytes() {
 // a.streamk K steps at tile boundaries.  Both CTAs of the pair decode the same sequence;
 // `rank` selects the CTA's 128 rows of A and 64 rows of B.
 struct PairSlice {
+  const TcGemmArgs* a;
   long long cur, end;
   int nkt, tmp;
-  __device__ bool next(const TcGemmArgs& a, uint32_t rank, TileInfo& ti) {
+  __device__ bool next(uint32_t rank, TileInfo& ti) {
+    const TcGemmArgs& a = *this->a;
     if (nkt <= 0 || cur >= end) return false;
     const long long tile = cur / nkt;
     const int kk = (int)(cur - tile * nkt);
@@ -145,12 +147,11 @@ struct PairSlice {
   }
 };
 
-// Stage 2 (mode 2, stream-K, EPI_H) on CTA pairs.  mapA: A planes, 128-row boxes; mapB:
-// B planes, 64-row boxes.  Launched with cluster dimension 2 and an even grid.
-template <int KIND, bool F16>
-__global__ void __launch_bounds__(192, 1) k_tc_gemm_pair(const __grid_constant__ CUtensorMap mapA,
-                                                          const __grid_constant__ CUtensorMap mapB,
-                                                          const TcGemmArgs args) {
+// The body of stage 2 on CTA pairs over a source of work units (PairSingleSrc: one problem,
+// stream-K; PairBatchSrc: the units of a batch of problems).  Each role iterates its own
+// copy of src.iter(); both CTAs of a pair decode the same sequence.
+template <int KIND, bool F16, class PSrc>
+__device__ __forceinline__ void tc_gemm_pair_body(const PSrc& src) {
   using Cfg = TcCfg<KIND>;
   constexpr int NA = Cfg::NA, NST = pair_nst<KIND>();
   constexpr uint32_t STAGE = pair_stage_bytes<KIND>();
@@ -159,12 +160,10 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm_pair(const __grid_constant__
   __shared__ __align__(8) uint64_t full_bar[NST], empty_bar[NST], tfull_bar[2], tempty_bar[2], done_bar;
   __shared__ uint32_t s_tmem;
   __shared__ volatile int s_abort_v;
-  __shared__ int s_kr[CGH_MAX_LAYERS];
-  __shared__ int s_ktot;
   volatile int& s_abort = s_abort_v;
   const uint32_t rank = cluster_ctarank();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  int* const status = args.status;
+  int* const status = src.status();
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < NST; ++s) {
@@ -189,25 +188,8 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm_pair(const __grid_constant__
   cluster_sync_all();  // both CTAs' barriers exist before any remote signal
   tc_fence_after();
   pdl_wait();  // the K sizes and the stage-1 output come from earlier kernels
-  if (threadIdx.x < args.n_layers) s_kr[threadIdx.x] = args.kr_pad[threadIdx.x];
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    int o = 0;
-    for (int q = 0; q < args.n_layers; ++q) o += s_kr[q];
-    s_ktot = o;
-  }
-  __syncthreads();
   const uint32_t tmem = s_tmem;
   const uint32_t smem_base = smem_u32(smem);
-  PairSlice slice;
-  {
-    const int npairs = gridDim.x >> 1, pair = blockIdx.x >> 1;
-    slice.nkt = s_ktot / TC_BK;
-    slice.tmp = (args.tm + 1) >> 1;
-    const long long W = (long long)slice.tmp * args.tn * slice.nkt;
-    slice.cur = W * pair / npairs;
-    slice.end = W * (pair + 1) / npairs;
-  }
 
   if (warp == 0) {
     if (lane == 0) {
@@ -219,8 +201,11 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm_pair(const __grid_constant__
       for (int s = 0; s < NST; ++s) issued[s] = false, issued_ph[s] = 0;
       bool ok = true;
       TileInfo ti;
-      PairSlice sl = slice;
-      while (ok && sl.next(args, rank, ti)) {
+      auto sl = src.iter();
+      while (ok && sl.next(rank, ti)) {
+        const CUtensorMap* mA = src.mapA(ti);
+        const CUtensorMap* mB = src.mapB(ti);
+        src.acquire_maps(mA, mB);
         for (int kt = 0; kt < ti.nk; ++kt, ++it) {
           const int s = it % NST;
           const uint32_t ph = (uint32_t)(it / NST) & 1u;
@@ -230,8 +215,8 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm_pair(const __grid_constant__
           }
           uint8_t* st = smem + s * STAGE;
           if (rank == 0) mbar_arrive_expect_tx(&full_bar[s], 2 * STAGE);
-          tma_load_3d_pair(st, &mapA, full0 + 8u * s, ti.akm ? ti.akm[kt] : ti.k_lo + kt * TC_BK, ti.a_row, 0);
-          tma_load_3d_pair(st + NA * TC_PAIR_A_PLANE, &mapB, full0 + 8u * s, ti.k_lo + kt * TC_BK, ti.b_row, 0);
+          tma_load_3d_pair(st, mA, full0 + 8u * s, ti.akm ? ti.akm[kt] : ti.k_lo + kt * TC_BK, ti.a_row, 0);
+          tma_load_3d_pair(st + NA * TC_PAIR_A_PLANE, mB, full0 + 8u * s, ti.k_lo + kt * TC_BK, ti.b_row, 0);
           issued[s] = true;
           issued_ph[s] = ph;
         }
@@ -254,8 +239,8 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm_pair(const __grid_constant__
       int it = 0, local = 0;
       bool ok = true;
       TileInfo ti;
-      PairSlice sl = slice;
-      while (ok && sl.next(args, rank, ti)) {
+      auto sl = src.iter();
+      while (ok && sl.next(rank, ti)) {
         const int buf = local & 1;
         const uint32_t use_ph = (uint32_t)(local >> 1) & 1u;
         if (!mbar_wait_bounded(&tempty_bar[buf], use_ph ^ 1u, &s_abort, status)) break;
@@ -292,8 +277,9 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm_pair(const __grid_constant__
     const uint32_t tempty0 = mapa_rank(smem_u32(&tempty_bar[0]), 0);
     int local = 0;
     TileInfo ti;
-    PairSlice sl = slice;
-    while (sl.next(args, rank, ti)) {
+    auto sl = src.iter();
+    while (sl.next(rank, ti)) {
+      const TcGemmArgs& args = src.args(ti);
       const int buf = local & 1;
       const uint32_t ph = (uint32_t)(local >> 1) & 1u;
       bool have = mbar_wait_bounded(&tfull_bar[buf], ph, &s_abort, status);
@@ -357,12 +343,126 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm_pair(const __grid_constant__
   }
 }
 
+// One problem: stream-K slices of the (pair tile, K step) space.
+struct PairSingleSrc {
+  const CUtensorMap* ma;
+  const CUtensorMap* mb;
+  const TcGemmArgs* a;
+  PairSlice slice;
+  __device__ PairSlice iter() const { return slice; }
+  __device__ const CUtensorMap* mapA(const TileInfo&) const { return ma; }
+  __device__ const CUtensorMap* mapB(const TileInfo&) const { return mb; }
+  __device__ void acquire_maps(const CUtensorMap*, const CUtensorMap*) const {}
+  __device__ const TcGemmArgs& args(const TileInfo&) const { return *a; }
+  __device__ int* status() const { return a->status; }
+};
+
+template <int KIND, bool F16>
+__global__ void __launch_bounds__(192, 1) k_tc_gemm_pair(const __grid_constant__ CUtensorMap mapA,
+                                                          const __grid_constant__ CUtensorMap mapB,
+                                                          const TcGemmArgs args) {
+  __shared__ int s_kr[CGH_MAX_LAYERS];
+  __shared__ int s_ktot;
+  pdl_wait();
+  if (threadIdx.x < args.n_layers) s_kr[threadIdx.x] = args.kr_pad[threadIdx.x];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int o = 0;
+    for (int q = 0; q < args.n_layers; ++q) o += s_kr[q];
+    s_ktot = o;
+  }
+  __syncthreads();
+  PairSingleSrc src{&mapA, &mapB, &args, {}};
+  {
+    const int npairs = gridDim.x >> 1, pair = blockIdx.x >> 1;
+    src.slice.a = &args;
+    src.slice.nkt = s_ktot / TC_BK;
+    src.slice.tmp = (args.tm + 1) >> 1;
+    const long long W = (long long)src.slice.tmp * args.tn * src.slice.nkt;
+    src.slice.cur = W * pair / npairs;
+    src.slice.end = W * (pair + 1) / npairs;
+  }
+  tc_gemm_pair_body<KIND, F16>(src);
+}
+
+// The stage-2 units of a batch on CTA pairs: per item (pair tiles along M) x (tiles along
+// N) x (K splits), found by binary search over the items' first pair units.
+struct PairBatchSrc {
+  const TcBatchItem* items;
+  int n, tot;
+  int* st;
+  struct Iter {
+    const PairBatchSrc* s;
+    int cur;
+    __device__ bool next(uint32_t rank, TileInfo& ti) {
+      const int npairs = gridDim.x >> 1;
+      for (; cur < s->tot; cur += npairs)
+        if (s->decode(cur, rank, ti)) {
+          cur += npairs;
+          return true;
+        }
+      return false;
+    }
+  };
+  __device__ Iter iter() const { return Iter{this, (int)(blockIdx.x >> 1)}; }
+  __device__ bool decode(int t, uint32_t rank, TileInfo& ti) const {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (items[mid].unit0p <= t)
+        lo = mid;
+      else
+        hi = mid - 1;
+    }
+    const TcBatchItem& it = items[lo];
+    const TcGemmArgs& a = it.a;
+    const int local = t - it.unit0p, tmp = (a.tm + 1) >> 1;
+    const int mtp = local % tmp, r = local / tmp, nt = r % a.tn, split = r / a.tn;
+    const int nkt = it.koff[a.n_layers] / TC_BK, S = a.tz;
+    const int k0 = (int)((long long)nkt * split / S), k1 = (int)((long long)nkt * (split + 1) / S);
+    ti.item = lo;
+    ti.akm = a.a_kmap ? a.a_kmap + k0 : nullptr;
+    ti.a_row = (2 * mtp + (int)rank) * TC_BM;
+    ti.b_row = nt * TC_BN + 64 * (int)rank;
+    ti.k_lo = k0 * TC_BK;
+    ti.nk = k1 - k0;
+    ti.out_row0 = ti.a_row;
+    ti.out_col0 = nt * TC_BN;
+    ti.n_valid = TC_BN;
+    ti.row_lim = a.M;
+    ti.col_lim = a.N;
+    return ti.nk > 0;
+  }
+  __device__ const CUtensorMap* mapA(const TileInfo& ti) const { return &items[ti.item].ma; }
+  __device__ const CUtensorMap* mapB(const TileInfo& ti) const { return &items[ti.item].mb64; }
+  __device__ void acquire_maps(const CUtensorMap* a, const CUtensorMap* b) const {
+    // tensor maps written to global memory by a copy before the launch
+    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(reinterpret_cast<uint64_t>(a))
+                 : "memory");
+    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(reinterpret_cast<uint64_t>(b))
+                 : "memory");
+  }
+  __device__ const TcGemmArgs& args(const TileInfo& ti) const { return items[ti.item].a; }
+  __device__ int* status() const { return st; }
+};
+
+template <int KIND, bool F16>
+__global__ void __launch_bounds__(192, 1) k_tc_gemm_pair_batch(const TcBatchItem* __restrict__ items, int n,
+                                                                int total, int* status) {
+  pdl_wait();
+  PairBatchSrc src{items, n, total, status};
+  tc_gemm_pair_body<KIND, F16>(src);
+}
+
 // ------------------------------------------------------------------------------------
 // host side
 
 template <int KIND, bool F16>
 static cudaError_t set_gemm_pair_attr() {
-  return cudaFuncSetAttribute(k_tc_gemm_pair<KIND, F16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaError_t e = cudaFuncSetAttribute(k_tc_gemm_pair<KIND, F16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)pair_smem_bytes<KIND>());
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_tc_gemm_pair_batch<KIND, F16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)pair_smem_bytes<KIND>());
 }
 
@@ -417,4 +517,28 @@ static cudaError_t launch_gemm_pair(const CUtensorMap& ma, const CUtensorMap& mb
   cfg.attrs = attr;
   cfg.numAttrs = 2;
   return cudaLaunchKernelEx(&cfg, k_tc_gemm_pair<KIND, F16>, ma, mb64, a);
+}
+
+// The batch's stage 2 on CTA pairs over `total` pair units; cudaErrorNotSupported when the
+// device holds no CTA pair of this kernel.
+template <int KIND, bool F16>
+static cudaError_t launch_gemm_pair_batch(const TcBatchItem* d_items, int n, int total, int* status,
+                                          cudaStream_t st) {
+  int pairs = gemm_pair_clusters<KIND, F16>();
+  if (pairs <= 0) return cudaErrorNotSupported;
+  if (pairs > total) pairs = total;
+  if (pairs <= 0) return cudaSuccess;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(2 * pairs);
+  cfg.blockDim = dim3(192);
+  cfg.dynamicSmemBytes = pair_smem_bytes<KIND>();
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = 2;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_tc_gemm_pair_batch<KIND, F16>, d_items, n, total, status);
 }

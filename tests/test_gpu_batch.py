@@ -64,6 +64,17 @@ def test_batch_matches_single_scene_and_oracle(form):
     st.synchronize()
     for k in range(len(scs)):
         assert O.rel_l2(Hs[k].cpu().numpy(), got[k]) <= 1e-5
+    # stage 2 on CTA pairs (256x128 tiles), twice in a row
+    batch.set_stage2_tiles(Plan.TILES_PAIR)
+    for _ in range(2):
+        for h in Hs:
+            h.fill_(float("nan"))
+        with torch.cuda.stream(st):
+            batch.run(stream=st)
+        st.synchronize()
+        for k in range(len(scs)):
+            assert O.rel_l2(Hs[k].cpu().numpy(), got[k]) <= 1e-5, k
+    assert all(p.status() == 0 for p in plans)
     batch.close()
 
 
