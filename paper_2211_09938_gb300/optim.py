@@ -94,7 +94,7 @@ class PhaseOptimiser:
     torch.save/torch.load) checkpoint and resume the run; with a plan created with
     Plan.DETERMINISTIC a resumed run reproduces an uninterrupted one bit for bit."""
 
-    def __init__(self, plan, layer, targets, weights, phase0, lr=0.05, checkpoint=True):
+    def __init__(self, plan, layer, targets, weights, phase0, lr=0.05, checkpoint=True, concurrent=True):
         self.plan = plan
         self.layer = layer
         self.targets = targets
@@ -103,16 +103,35 @@ class PhaseOptimiser:
         self.phase = phase0.detach().clone().float().contiguous().requires_grad_(True)
         self.opt = torch.optim.Adam([self.phase], lr=lr)
         self.step_count = 0
+        nb = self.phase.shape[0]
+        # concurrent: the holograms of the batch run on their own streams, each with its own
+        # plan (plan scratch is per plan), so that their GEMMs and small kernels overlap on the
+        # GPU; autograd runs every hologram's backward on the stream of its forward
+        self.plans = [plan] + ([plan.clone() for _ in range(nb - 1)] if concurrent else [plan] * (nb - 1))
+        self.streams = [torch.cuda.Stream() for _ in range(nb)] if concurrent else None
         with torch.no_grad():
             self.kappa = [fit_kappa(reconstruct_amplitude(self.phase[b], plan, layer, False), targets[b])
-                          for b in range(self.phase.shape[0])]
+                          for b in range(nb)]
 
     def loss(self):
-        total = 0.0
-        for b in range(self.phase.shape[0]):
-            amp = reconstruct_amplitude(self.phase[b], self.plan, self.layer, self.checkpoint)
-            total = total + weighted_loss(amp, self.targets[b], self.weights, self.kappa[b])
-        return total
+        nb = self.phase.shape[0]
+        if self.streams is None:
+            total = 0.0
+            for b in range(nb):
+                amp = reconstruct_amplitude(self.phase[b], self.plans[b], self.layer, self.checkpoint)
+                total = total + weighted_loss(amp, self.targets[b], self.weights, self.kappa[b])
+            return total
+        cur = torch.cuda.current_stream()
+        parts = []
+        for b in range(nb):
+            s = self.streams[b]
+            s.wait_stream(cur)
+            with torch.cuda.stream(s):
+                amp = reconstruct_amplitude(self.phase[b], self.plans[b], self.layer, self.checkpoint)
+                parts.append(weighted_loss(amp, self.targets[b], self.weights, self.kappa[b]))
+        for s in self.streams:
+            cur.wait_stream(s)
+        return torch.stack(parts).sum()
 
     def step(self):
         self.opt.zero_grad(set_to_none=True)

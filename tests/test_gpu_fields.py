@@ -211,6 +211,11 @@ def test_phase_optimisation_decreases_and_resumes_bit_identically(torch_cuda, tm
         c.step()
     assert c.step_count == 6
     assert torch.equal(c.phase.detach(), a.phase.detach())
+    # the holograms one after another on one stream and plan give the same phases bit for bit
+    d = optim.PhaseOptimiser(plan, L, T, W, ph0, lr=0.05, concurrent=False)
+    for _ in range(6):
+        d.step()
+    assert torch.equal(d.phase.detach(), a.phase.detach())
 
 
 @pytest.mark.parametrize("name,make", [
