@@ -94,7 +94,7 @@ class PhaseOptimiser:
     torch.save/torch.load) checkpoint and resume the run; with a plan created with
     Plan.DETERMINISTIC a resumed run reproduces an uninterrupted one bit for bit."""
 
-    def __init__(self, plan, layer, targets, weights, phase0, lr=0.05, checkpoint=True, concurrent=True):
+    def __init__(self, plan, layer, targets, weights, phase0, lr=0.05, checkpoint=True, concurrent=False):
         self.plan = plan
         self.layer = layer
         self.targets = targets
@@ -106,7 +106,9 @@ class PhaseOptimiser:
         nb = self.phase.shape[0]
         # concurrent: the holograms of the batch run on their own streams, each with its own
         # plan (plan scratch is per plan), so that their GEMMs and small kernels overlap on the
-        # GPU; autograd runs every hologram's backward on the stream of its forward
+        # GPU; autograd runs every hologram's backward on the stream of its forward.  Measured
+        # at batch 4, 1024^2, 8 layers: 2.96 ms per Adam step against 2.66 ms in order (the
+        # four plans' operands compete for L2), so it is off by default.
         self.plans = [plan] + ([plan.clone() for _ in range(nb - 1)] if concurrent else [plan] * (nb - 1))
         self.streams = [torch.cuda.Stream() for _ in range(nb)] if concurrent else None
         with torch.no_grad():

@@ -189,6 +189,41 @@ def test_phase_gradient_vs_oracle_and_finite_differences(torch_cuda):
     assert err_fd <= 1e-2
 
 
+def test_phase_gradient_at_bench_size(torch_cuda):
+    """The phase-optimisation benchmark's size: 512x512 object, 1024x1024 hologram, 8 layers.
+    The autograd gradient (checkpointed reconstruction, propagation backward) against the
+    FP64 oracle's analytic gradient over every entry, and against central differences
+    (h = 1e-3) of the FP64 oracle loss on 64 random entries."""
+    torch = torch_cuda
+    from paper_2211_09938_gb300 import optim
+    sc, plan, target, weight, phase = _opt_case(torch, n=512, holo=1024, nl=8, seed=5000)
+    g = O.geometry_of(sc)
+    L = torch.from_numpy(sc["layer"]).cuda()
+    T = torch.from_numpy(target).cuda()
+    W = torch.from_numpy(weight).cuda()
+    with torch.no_grad():
+        kappa = optim.fit_kappa(optim.reconstruct_amplitude(torch.from_numpy(phase).cuda(), plan, L), T)
+    ph = torch.from_numpy(phase).cuda().requires_grad_(True)
+    optim.weighted_loss(optim.reconstruct_amplitude(ph, plan, L, True), T, W, kappa).backward()
+    grad = ph.grad.cpu().numpy().astype(np.float64)
+    ref = O.phase_opt_grad(phase.astype(np.float64), target, weight, sc["layer"], g, kappa)
+    err = O.rel_l2(grad, ref)
+    rng = np.random.default_rng(5001)
+    idx = rng.choice(phase.size, size=64, replace=False)
+    h = 1e-3
+    fd = []
+    for k in idx:
+        e = np.zeros(phase.size)
+        e[k] = h
+        e = e.reshape(phase.shape)
+        fd.append((O.phase_opt_loss(phase + e, target, weight, sc["layer"], g, kappa)
+                   - O.phase_opt_loss(phase - e, target, weight, sc["layer"], g, kappa)) / (2 * h))
+    fd = np.array(fd)
+    err_fd = float(np.linalg.norm(grad.reshape(-1)[idx] - fd) / np.linalg.norm(fd))
+    print(f"bench-size phase gradient: vs FP64 oracle {err:.2e}, vs central differences (64 entries) {err_fd:.2e}")
+    assert err <= 1e-3 and err_fd <= 1e-2
+
+
 def test_phase_optimisation_decreases_and_resumes_bit_identically(torch_cuda, tmp_path):
     torch = torch_cuda
     from paper_2211_09938_gb300 import Plan, optim
@@ -211,8 +246,8 @@ def test_phase_optimisation_decreases_and_resumes_bit_identically(torch_cuda, tm
         c.step()
     assert c.step_count == 6
     assert torch.equal(c.phase.detach(), a.phase.detach())
-    # the holograms one after another on one stream and plan give the same phases bit for bit
-    d = optim.PhaseOptimiser(plan, L, T, W, ph0, lr=0.05, concurrent=False)
+    # the holograms on their own streams and plans give the same phases bit for bit
+    d = optim.PhaseOptimiser(plan, L, T, W, ph0, lr=0.05, concurrent=True)
     for _ in range(6):
         d.step()
     assert torch.equal(d.phase.detach(), a.phase.detach())
