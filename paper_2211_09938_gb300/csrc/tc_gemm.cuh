@@ -285,24 +285,26 @@ __device__ __forceinline__ void issue_products(uint32_t tmem, uint64_t a_desc, u
     mma_f16(d1, A(1), B(0), id_pos, 1);
     mma_f16(d1, A(1), B(1), id_pos, 1);
   } else if (KIND == KIND_CR) {
+    // the two accumulators' products interleaved (each accumulator's own order unchanged),
+    // so that consecutive MMAs never depend on each other's result
     mma_f16(d0, A(0), B(0), id_pos, f);
-    mma_f16(d0, A(0), B(1), id_pos, 1);
-    mma_f16(d0, A(1), B(0), id_pos, 1);
     mma_f16(d1, A(2), B(0), id_pos, f);
+    mma_f16(d0, A(0), B(1), id_pos, 1);
     mma_f16(d1, A(2), B(1), id_pos, 1);
+    mma_f16(d0, A(1), B(0), id_pos, 1);
     mma_f16(d1, A(3), B(0), id_pos, 1);
   } else {
     mma_f16(d0, A(0), B(0), id_pos, f);
-    mma_f16(d0, A(0), B(1), id_pos, 1);
-    mma_f16(d0, A(1), B(0), id_pos, 1);
-    mma_f16(d0, A(2), B(2), id_neg, 1);
-    mma_f16(d0, A(2), B(3), id_neg, 1);
-    mma_f16(d0, A(3), B(2), id_neg, 1);
     mma_f16(d1, A(0), B(2), id_pos, f);
+    mma_f16(d0, A(0), B(1), id_pos, 1);
     mma_f16(d1, A(0), B(3), id_pos, 1);
+    mma_f16(d0, A(1), B(0), id_pos, 1);
     mma_f16(d1, A(1), B(2), id_pos, 1);
+    mma_f16(d0, A(2), B(2), id_neg, 1);
     mma_f16(d1, A(2), B(0), id_pos, 1);
+    mma_f16(d0, A(2), B(3), id_neg, 1);
     mma_f16(d1, A(2), B(1), id_pos, 1);
+    mma_f16(d0, A(3), B(2), id_neg, 1);
     mma_f16(d1, A(3), B(0), id_pos, 1);
   }
 }
