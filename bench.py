@@ -781,10 +781,10 @@ def run_ours(args):
         peak_tf = pk.get("bf16_tflops", 1900.0)
         roof = {"bound": "tensor",
                 "kernel": "k_tc_fused (both GEMM stages, one cooperative launch)" if fused
-                else "k_tc_gemm_pair<KIND_CC> (stage 2 on CTA pairs, tcgen05 cta_group::2)",
+                else "k_tc_gemm<KIND_CC,EPI_H> (stage 2, one CTA per 128x128 tile)",
                 "achieved": algo_flop / (k_ms / 1e3) / 1e12, "peak": peak_tf, "unit": "TFLOP/s",
                 "frac": algo_flop / (k_ms / 1e3) / 1e12 / peak_tf,
-                "traffic": kernel_traffic(("k_tc_fused" if fused else "k_tc_gemm_pair stage 2") + f" ({form})"),
+                "traffic": kernel_traffic(("k_tc_fused" if fused else "k_tc_gemm stage 2") + f" ({form})"),
                 "traffic_note": "ncu dram__bytes_read.sum + dram__bytes_write.sum per launch, from "
                                 "profiles/traffic.json (the ncu summary it names); null if the kernel changed "
                                 "since the counters were taken",

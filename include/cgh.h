@@ -123,8 +123,9 @@ int cgh_plan_set_tuning(cgh_plan* plan, int max_ksteps_per_chain);
  */
 /*
  * cgh_plan_set_stage2_tiles - tile shape of the separable form's stage-2 GEMM.
- *   CGH_TILES_AUTO  (default) CTA pairs whenever the call splits K stream-K style (not
- *                   with CGH_PLAN_DETERMINISTIC) and the device holds CTA pairs
+ *   CGH_TILES_AUTO  (default) CTA pairs when the call splits K stream-K style (not with
+ *                   CGH_PLAN_DETERMINISTIC), the device holds CTA pairs and the hologram
+ *                   has at least as many 128 x 128 tiles as the device has SMs
  *   CGH_TILES_CTA   one CTA per 128 x 128 output tile
  *   CGH_TILES_PAIR  two CTAs of a cluster per 256 x 128 output tile (tcgen05 cta_group::2:
  *                   each CTA stages its 128 rows of the fringe operand and half of the data
