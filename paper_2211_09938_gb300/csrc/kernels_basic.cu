@@ -497,6 +497,256 @@ int select_scan_blocks(int n_layers, int nchunks) {
 }
 
 // ---------------------------------------------------------------------------
+// Multi-level selection for large objects (width a multiple of 2048): the four lists of a
+// progressive hologram (LLL = every occupied 8x8 block, and the detail blocks of levels 3,
+// 2, 1 above their thresholds) from ONE read of the inputs per pass.  One thread owns one
+// 8x8 block and derives the masks of its 2x2, 4x4 and 8x8 blocks in registers; one CTA
+// owns a segment of 256 consecutive 8x8 blocks of one row of them.  The count table of a
+// list holds, per layer, one entry per (row of that level's blocks, segment): 1 row of
+// level-3 blocks, 2 rows of level-2 and 4 rows of level-1 blocks per segment.  In the
+// order (layer, row, segment) these are the list's own order (layer, block row, block
+// column), so the blocked exclusive scan of the three-pass selection gives every segment
+// row its first position, and the scatter ranks the blocks inside it.  Bit-exact with the
+// per-level selection.
+#define SEL_ML_SEG 256
+
+struct MlMasks {
+  unsigned long long lll, m3, m2[4], m1[16];  // m2[2r+c], m1[4r+c]: rows r, columns c
+};
+
+// Masks of the 8x8 block (by3, bx3): layers present (and, for the detail levels, the block
+// maximum of the saliency above that level's threshold, -1 = no threshold).
+__device__ __forceinline__ void ml_masks(const uint8_t* __restrict__ sal, const uint8_t* __restrict__ L, int W,
+                                         int by3, int bx3, int Z, int t3, int t2, int t1, MlMasks& m) {
+  uint2 lv[8], sv[8];
+#pragma unroll
+  for (int r = 0; r < 8; ++r) {
+    const size_t o = (size_t)(8 * by3 + r) * W + 8 * bx3;
+    lv[r] = *reinterpret_cast<const uint2*>(L + o);
+    sv[r] = *reinterpret_cast<const uint2*>(sal + o);
+  }
+  unsigned long long occ1[16];
+  int mx1[16];
+#pragma unroll
+  for (int q = 0; q < 16; ++q) occ1[q] = 0ull, mx1[q] = 0;
+#pragma unroll
+  for (int r = 0; r < 8; ++r)
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      const unsigned lw = c < 4 ? lv[r].x : lv[r].y, sw = c < 4 ? sv[r].x : sv[r].y;
+      const int sh = 8 * (c & 3);
+      const int lz = (lw >> sh) & 0xFF, sz = (sw >> sh) & 0xFF;
+      const int q = (r >> 1) * 4 + (c >> 1);
+      if (lz < Z) occ1[q] |= 1ull << lz;
+      mx1[q] = max(mx1[q], sz);
+    }
+  unsigned long long occ3 = 0ull;
+  int mx3 = 0;
+#pragma unroll
+  for (int r2 = 0; r2 < 2; ++r2)
+#pragma unroll
+    for (int c2 = 0; c2 < 2; ++c2) {
+      unsigned long long o2 = 0ull;
+      int x2 = 0;
+#pragma unroll
+      for (int r = 0; r < 2; ++r)
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+          const int q = (2 * r2 + r) * 4 + 2 * c2 + c;
+          o2 |= occ1[q];
+          x2 = max(x2, mx1[q]);
+          m.m1[q] = (t1 < 0 || mx1[q] > t1) ? occ1[q] : 0ull;
+        }
+      m.m2[2 * r2 + c2] = (t2 < 0 || x2 > t2) ? o2 : 0ull;
+      occ3 |= o2;
+      mx3 = max(mx3, x2);
+    }
+  m.lll = occ3;
+  m.m3 = (t3 < 0 || mx3 > t3) ? occ3 : 0ull;
+}
+
+// Layer-z bits of this thread's blocks in row q of list k (k: 0 LLL, 1 level 1, 2 level 2,
+// 3 level 3; rows per segment 1, 4, 2, 1), left to right.
+__device__ __forceinline__ int ml_row_bits(const MlMasks& m, int k, int q, int z) {
+  if (k == 0) return (int)((m.lll >> z) & 1ull);
+  if (k == 3) return (int)((m.m3 >> z) & 1ull);
+  if (k == 2) return (int)((m.m2[2 * q] >> z) & 1ull) | ((int)((m.m2[2 * q + 1] >> z) & 1ull) << 1);
+  int b = 0;
+#pragma unroll
+  for (int c = 0; c < 4; ++c) b |= (int)((m.m1[4 * q + c] >> z) & 1ull) << c;
+  return b;
+}
+__device__ __forceinline__ unsigned long long ml_row_union(const MlMasks& m, int k, int q) {
+  if (k == 0) return m.lll;
+  if (k == 3) return m.m3;
+  if (k == 2) return m.m2[2 * q] | m.m2[2 * q + 1];
+  return m.m1[4 * q] | m.m1[4 * q + 1] | m.m1[4 * q + 2] | m.m1[4 * q + 3];
+}
+__host__ __device__ __forceinline__ int ml_rows(int k) { return k == 1 ? 4 : k == 2 ? 2 : 1; }
+
+// OR of a 64-bit mask over the CTA (s_or: 2 x 32-bit words per warp, all threads call).
+__device__ __forceinline__ unsigned long long ml_cta_or(unsigned long long v, unsigned* s_or) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const unsigned lo = __reduce_or_sync(0xffffffffu, (unsigned)v), hi = __reduce_or_sync(0xffffffffu, (unsigned)(v >> 32));
+  __syncthreads();
+  if (lane == 0) {
+    s_or[2 * warp] = lo;
+    s_or[2 * warp + 1] = hi;
+  }
+  __syncthreads();
+  unsigned a = 0, b = 0;
+#pragma unroll
+  for (int w = 0; w < SEL_ML_SEG / 32; ++w) a |= s_or[2 * w], b |= s_or[2 * w + 1];
+  return ((unsigned long long)b << 32) | a;
+}
+
+// Pass 1: per (list, layer, segment row) counts.  CTA = (row of 8x8 blocks, segment).
+__global__ void __launch_bounds__(SEL_ML_SEG) k_select_ml_count(const uint8_t* __restrict__ sal,
+                                                                const uint8_t* __restrict__ L, int H, int W, int Z,
+                                                                const SelTasks T, int* __restrict__ chunk_cnt) {
+  __shared__ unsigned s_or[2 * (SEL_ML_SEG / 32)];
+  __shared__ int s_cnt[4][CGH_MAX_LAYERS];
+  pdl_wait();
+  pdl_trigger();
+  const int nseg = (W >> 3) / SEL_ML_SEG, R = blockIdx.x / nseg, sg = blockIdx.x - R * nseg;
+  const int bx3 = sg * SEL_ML_SEG + threadIdx.x;
+  MlMasks m;
+  ml_masks(sal, L, W, R, bx3, Z, T.t[3].threshold, T.t[2].threshold, T.t[1].threshold, m);
+  if (blockIdx.x == 0 && threadIdx.x < 4) T.t[threadIdx.x].count[1] = 0;  // the scan's CTA counters
+  for (int k = 0; k < 4; ++k) {
+    const SelTask& tk = T.t[k];
+    for (int q = 0; q < ml_rows(k); ++q) {
+      for (int e = threadIdx.x; e < Z; e += blockDim.x) s_cnt[0][e] = 0;
+      unsigned long long u = ml_cta_or(ml_row_union(m, k, q), s_or);  // also orders the clear above
+      while (u) {
+        const int z = __ffsll((long long)u) - 1;
+        u &= u - 1ull;
+        const int c = __reduce_add_sync(0xffffffffu, __popc(ml_row_bits(m, k, q, z)));
+        if ((threadIdx.x & 31) == 0 && c) atomicAdd(&s_cnt[0][z], c);
+      }
+      __syncthreads();
+      const int row = R * ml_rows(k) + q;  // row of this level's blocks
+      for (int z = threadIdx.x; z < Z; z += blockDim.x)
+        chunk_cnt[tk.cnt_off + z * tk.nchunks + row * nseg + sg] = s_cnt[0][z];
+      __syncthreads();
+    }
+  }
+}
+// Exclusive prefix of x over the SEL_ML_SEG threads of the CTA (s_w: one int per warp).
+__device__ __forceinline__ int ml_cta_exclusive(int x, int* s_w) {
+  constexpr int NW = SEL_ML_SEG / 32;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int inc = x;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int t = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += t;
+  }
+  __syncthreads();  // s_w of the previous call has been read
+  if (lane == 31) s_w[warp] = inc;
+  __syncthreads();
+  int before = 0;
+#pragma unroll
+  for (int w = 0; w < NW; ++w) before += w < warp ? s_w[w] : 0;
+  return before + inc - x;
+}
+
+// Pass 3: ordered scatter of all four lists (FLAGS: also the tensor-core flags).
+template <bool FLAGS>
+__global__ void __launch_bounds__(SEL_ML_SEG) k_select_ml_scatter(const uint8_t* __restrict__ sal,
+                                                                  const uint8_t* __restrict__ L, int H, int W, int Z,
+                                                                  const SelTasks T, const int* __restrict__ chunk_cnt,
+                                                                  const int* __restrict__ chunk_off, TcFlags fl) {
+  __shared__ unsigned s_or[2 * (SEL_ML_SEG / 32)];
+  __shared__ int s_w[SEL_ML_SEG / 32];
+  __shared__ int s_base[CGH_MAX_LAYERS];
+  pdl_wait();
+  pdl_trigger();
+  const int nseg = (W >> 3) / SEL_ML_SEG, R = blockIdx.x / nseg, sg = blockIdx.x - R * nseg;
+  const int bx3 = sg * SEL_ML_SEG + threadIdx.x;
+  MlMasks m;
+  ml_masks(sal, L, W, R, bx3, Z, T.t[3].threshold, T.t[2].threshold, T.t[1].threshold, m);
+  for (int k = 0; k < 4; ++k) {
+    const SelTask& tk = T.t[k];
+    const int level = tk.level, hl = H >> level, wl = W >> level, rows = ml_rows(k), cols = k == 1 ? 4 : k == 2 ? 2 : 1;
+    for (int q = 0; q < rows; ++q) {
+      const int row = R * rows + q;
+      __syncthreads();  // s_base of the previous row has been read
+      for (int z = threadIdx.x; z < Z; z += blockDim.x) {
+        const int e = z * tk.nchunks + row * nseg + sg;
+        s_base[z] = chunk_cnt[tk.cnt_off + (e / SEL_SCAN_BLOCK) * SEL_SCAN_BLOCK] + chunk_off[tk.cnt_off + e];
+      }
+      unsigned long long u = ml_cta_or(ml_row_union(m, k, q), s_or);  // its barriers publish s_base
+      while (u) {
+        const int z = __ffsll((long long)u) - 1;
+        u &= u - 1ull;
+        const int bits = ml_row_bits(m, k, q, z);
+        int pos = s_base[z] + ml_cta_exclusive(__popc(bits), s_w);
+        for (int c = 0; c < cols; ++c) {
+          if (!((bits >> c) & 1)) continue;
+          const int by = row, bx = bx3 * cols + c;
+          if (pos < tk.capacity) {
+            tk.list[pos] = (z << 24) | (by << 12) | bx;
+            if (FLAGS) {
+              if (k == 0) {
+                fl.occ3[((size_t)z * hl + by) * wl + bx] = 1;
+                fl.rowband[(size_t)z * hl + by] = 1;
+                fl.colband[(size_t)z * wl + bx] = 1;
+              } else {
+                uint8_t* sel = level == 1 ? fl.sel[1] : level == 2 ? fl.sel[2] : fl.sel[3];
+                sel[((size_t)z * hl + by) * wl + bx] = 1;
+                fl.rowband[(size_t)z * (H >> 3) + (by >> (3 - level))] = 1;
+                fl.colband[(size_t)z * (W >> 3) + (bx >> (3 - level))] = 1;
+              }
+            }
+          }
+          ++pos;
+        }
+      }
+    }
+  }
+}
+
+// The four lists of a progressive hologram through the multi-level passes, when the tasks
+// are exactly that set (T.t[0]: level 3, no threshold; T.t[l]: level l) and the object
+// width is a multiple of 8 x SEL_ML_SEG.  Returns false (nothing launched) otherwise.
+static bool select_ml_applies(int obj_h, int obj_w, const SelTasks& T) {
+  if (T.n != 4 || (obj_w >> 3) % SEL_ML_SEG || obj_h % 8 || obj_w % 8) return false;
+  if (T.t[0].level != 3 || T.t[0].threshold >= 0) return false;
+  for (int l = 1; l <= 3; ++l)
+    if (T.t[l].level != l) return false;
+  return true;
+}
+
+static cudaError_t launch_select_ml(int obj_h, int obj_w, int n_layers, const uint8_t* sal, const uint8_t* L,
+                                    SelTasks T, int* chunk_cnt, int* chunk_off, cudaStream_t st, const TcFlags* fl) {
+  const int nseg = (obj_w >> 3) / SEL_ML_SEG, h3 = obj_h >> 3;
+  int off = 0, nblk = 1;
+  for (int k = 0; k < 4; ++k) {
+    const int rows = ml_rows(k) * h3;
+    T.t[k].nchunks = rows * nseg;
+    T.t[k].chunk0 = 0;
+    T.t[k].cnt_off = off;
+    off += n_layers * T.t[k].nchunks;
+    const int b = (n_layers * T.t[k].nchunks + SEL_SCAN_BLOCK - 1) / SEL_SCAN_BLOCK;
+    nblk = b > nblk ? b : nblk;
+  }
+  const int grid = h3 * nseg;
+  cudaError_t e = launch_pdl(k_select_ml_count, dim3(grid), dim3(SEL_ML_SEG), 0, st, sal, L, obj_h, obj_w, n_layers,
+                             T, chunk_cnt);
+  if (e == cudaSuccess)
+    e = launch_pdl(k_select_scan, dim3(nblk, T.n), dim3(1024), 0, st, chunk_cnt, chunk_off, n_layers, T);
+  if (e == cudaSuccess) {
+    const TcFlags f = fl ? *fl : TcFlags{};
+    e = fl ? launch_pdl(k_select_ml_scatter<true>, dim3(grid), dim3(SEL_ML_SEG), 0, st, sal, L, obj_h, obj_w,
+                        n_layers, T, (const int*)chunk_cnt, (const int*)chunk_off, f)
+           : launch_pdl(k_select_ml_scatter<false>, dim3(grid), dim3(SEL_ML_SEG), 0, st, sal, L, obj_h, obj_w,
+                        n_layers, T, (const int*)chunk_cnt, (const int*)chunk_off, f);
+  }
+  return e != cudaSuccess ? e : cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
 // Single-launch selection for small count tables: one CTA per chunk, all co-resident
 // (cooperative launch), one grid barrier between the counts and the scatter.
 //   1. each CTA computes its blocks' layer masks (kept in registers), its per-layer warp
@@ -718,6 +968,12 @@ cudaError_t launch_select_tasks(int obj_h, int obj_w, int n_layers, const uint8_
                                             coop->bar, coop->status, f);
     if (e == cudaSuccess && flags_done) *flags_done = fl != nullptr;
     return e != cudaSuccess ? e : cudaGetLastError();
+  }
+  if (sal && select_ml_applies(obj_h, obj_w, T)) {
+    // the four lists of a large object: one read of the inputs per pass for all levels
+    const cudaError_t e = launch_select_ml(obj_h, obj_w, n_layers, sal, L, T, chunk_cnt, chunk_off, st, fl);
+    if (e == cudaSuccess && flags_done) *flags_done = fl != nullptr;
+    return e;
   }
   cudaError_t e = launch_pdl(k_select_count, dim3(c0), dim3(CGH_SEL_CHUNK), 0, st, sal, L, obj_h, obj_w, n_layers,
                              T, chunk_cnt);

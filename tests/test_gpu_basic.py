@@ -332,3 +332,64 @@ def test_select_max_object(torch_cuda):
         assert c[k, 0] == c[k, 1] == len(ref[k]), k
         assert np.array_equal(lists[k][:c[k, 0]].cpu().numpy(), ref[k]), k
     assert plan.status() == 0
+
+
+def _lists_vectorised(sal, layer, n_layers, thresholds):
+    """The four work lists from the pinned oracle's per-layer selection masks, vectorised
+    per layer (the oracle's own list builder loops in Python, too slow at 8192^2)."""
+    out = []
+    for k, level in enumerate((3, 1, 2, 3)):
+        thr = -1 if k == 0 else thresholds[level]
+        parts = []
+        for z in range(n_layers):
+            by, bx = np.nonzero(O.selected_mask(sal, layer, z, thr, level))
+            parts.append((z << 24) | (by.astype(np.int64) << 12) | bx)
+        out.append(np.concatenate(parts).astype(np.int32))
+    return out
+
+
+@pytest.mark.parametrize("n,n_layers", [(2048, 6), (4096, 3), (8192, 4)])
+def test_select_multilevel_large_objects(torch_cuda, n, n_layers):
+    """Objects whose width is a multiple of 2048 take the multi-level selection (one read
+    of the inputs per pass for all four lists): bit-exact against the oracle's selection
+    masks, with a truncating capacity on the level-1 list, and through the tensor-form step
+    (which marks the operand flags in the same pass) equal to the two-call path bit for bit
+    on a deterministic plan."""
+    torch = torch_cuda
+    from paper_2211_09938_gb300 import Plan
+    rng = np.random.default_rng(n + n_layers)
+    yy, xx = np.mgrid[0:n, 0:n] / n
+    sal = np.clip(255 * np.exp(-((yy - 0.4) ** 2 + (xx - 0.6) ** 2) / 0.05) + rng.normal(0, 8, (n, n)),
+                  0, 255).astype(np.uint8)
+    layer = (np.floor((0.5 + 0.5 * np.sin(6 * yy + 3 * xx)) * n_layers).clip(0, n_layers - 1)).astype(np.uint8)
+    layer[rng.random((n, n)) < 0.002] = 255  # a few pixels on no layer
+    want = _lists_vectorised(sal, layer, n_layers, scenes.THRESHOLDS_U8)
+    sc = dict(intensity=np.zeros((n, n), np.uint8), layer=layer, saliency=sal,
+              z=np.linspace(0.08, 0.2, n_layers), holo=(n, n), pitch=8e-6, wavelength=532e-9)
+    plan = Plan.for_scene(sc)
+    S = torch.from_numpy(sal).cuda()
+    L = torch.from_numpy(layer).cuda()
+    lists, counts = plan.progressive_lists(S, L, scenes.THRESHOLDS_U8)
+    c = counts.cpu().numpy()
+    for k in range(4):
+        assert c[k, 0] == c[k, 1] == len(want[k]), (k, c[k], len(want[k]))
+        assert np.array_equal(lists[k][:c[k, 0]].cpu().numpy(), want[k]), k
+    cap = len(want[1]) // 3
+    short = [l.clone() for l in lists]
+    short[1] = torch.full((cap,), -1, dtype=torch.int32, device="cuda")
+    l2, c2 = plan.progressive_lists(S, L, scenes.THRESHOLDS_U8, lists=short)
+    c2 = c2.cpu().numpy()
+    assert c2[1].tolist() == [cap, len(want[1])]
+    assert np.array_equal(l2[1].cpu().numpy(), want[1][:cap])
+    plan.close()
+    if n == 2048:
+        I = torch.from_numpy(rng.integers(0, 256, (n, n), dtype=np.uint8)).cuda()
+        dplan = Plan.for_scene(sc, flags=Plan.DETERMINISTIC)
+        coeffs = dplan.haar_decompose(I, L)
+        H1, ls, cs = dplan.progressive_step(S, L, coeffs, scenes.THRESHOLDS_U8, form="tc_fp16x3")
+        lo, co = dplan.progressive_lists(S, L, scenes.THRESHOLDS_U8)
+        H2 = dplan.progressive_hologram(coeffs, lo, co, form="tc_fp16x3")
+        torch.cuda.synchronize()
+        assert dplan.status() == 0
+        assert torch.equal(H1, H2)
+        dplan.close()
