@@ -576,13 +576,56 @@ __device__ __forceinline__ int ml_row_bits(const MlMasks& m, int k, int q, int z
   for (int c = 0; c < 4; ++c) b |= (int)((m.m1[4 * q + c] >> z) & 1ull) << c;
   return b;
 }
-__device__ __forceinline__ unsigned long long ml_row_union(const MlMasks& m, int k, int q) {
-  if (k == 0) return m.lll;
-  if (k == 3) return m.m3;
-  if (k == 2) return m.m2[2 * q] | m.m2[2 * q + 1];
-  return m.m1[4 * q] | m.m1[4 * q + 1] | m.m1[4 * q + 2] | m.m1[4 * q + 3];
-}
 __host__ __device__ __forceinline__ int ml_rows(int k) { return k == 1 ? 4 : k == 2 ? 2 : 1; }
+
+// The eight rows of a segment (list k, row q): 0 LLL, 1 level 3, 2-3 level 2, 4-7 level 1.
+// Each thread's count of layer-z blocks in every row, packed as 16-bit fields: lo holds rows
+// 0-3, hi rows 4-7 (a row of a segment has at most 1024 blocks, so no field overflows even
+// after the CTA-wide sums).
+__device__ __forceinline__ void ml_packed_counts(const MlMasks& m, int z, unsigned long long& lo,
+                                                 unsigned long long& hi) {
+  const unsigned long long c0 = (m.lll >> z) & 1ull, c1 = (m.m3 >> z) & 1ull;
+  const unsigned long long c2 = ((m.m2[0] >> z) & 1ull) + ((m.m2[1] >> z) & 1ull);
+  const unsigned long long c3 = ((m.m2[2] >> z) & 1ull) + ((m.m2[3] >> z) & 1ull);
+  lo = c0 | (c1 << 16) | (c2 << 32) | (c3 << 48);
+  hi = 0ull;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const unsigned long long c = ((m.m1[4 * q] >> z) & 1ull) + ((m.m1[4 * q + 1] >> z) & 1ull) +
+                                 ((m.m1[4 * q + 2] >> z) & 1ull) + ((m.m1[4 * q + 3] >> z) & 1ull);
+    hi |= c << (16 * q);
+  }
+}
+// Row r of the eight (see ml_packed_counts) -> (list k, row q within the segment).
+__host__ __device__ __forceinline__ int ml_row_list(int r) { return r == 0 ? 0 : r == 1 ? 3 : r < 4 ? 2 : 1; }
+__host__ __device__ __forceinline__ int ml_row_q(int r) { return r < 2 ? 0 : r < 4 ? r - 2 : r - 4; }
+
+// Exclusive prefix (and CTA total) of two packed 64-bit values over the CTA.
+__device__ __forceinline__ void ml_cta_exclusive2(unsigned long long& a, unsigned long long& b,
+                                                  unsigned long long* s_w, unsigned long long& ta,
+                                                  unsigned long long& tb) {
+  constexpr int NW = SEL_ML_SEG / 32;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  unsigned long long ia = a, ib = b;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned long long xa = __shfl_up_sync(0xffffffffu, ia, o), xb = __shfl_up_sync(0xffffffffu, ib, o);
+    if (lane >= o) ia += xa, ib += xb;
+  }
+  __syncthreads();  // s_w of the previous call has been read
+  if (lane == 31) s_w[2 * warp] = ia, s_w[2 * warp + 1] = ib;
+  __syncthreads();
+  unsigned long long pa = 0ull, pb = 0ull;
+  ta = tb = 0ull;
+#pragma unroll
+  for (int w = 0; w < NW; ++w) {
+    const unsigned long long wa = s_w[2 * w], wb = s_w[2 * w + 1];
+    if (w < warp) pa += wa, pb += wb;
+    ta += wa, tb += wb;
+  }
+  a = pa + ia - a;
+  b = pb + ib - b;
+}
 
 // OR of a 64-bit mask over the CTA (s_or: 2 x 32-bit words per warp, all threads call).
 __device__ __forceinline__ unsigned long long ml_cta_or(unsigned long long v, unsigned* s_or) {
@@ -605,7 +648,8 @@ __global__ void __launch_bounds__(SEL_ML_SEG) k_select_ml_count(const uint8_t* _
                                                                 const uint8_t* __restrict__ L, int H, int W, int Z,
                                                                 const SelTasks T, int* __restrict__ chunk_cnt) {
   __shared__ unsigned s_or[2 * (SEL_ML_SEG / 32)];
-  __shared__ int s_cnt[4][CGH_MAX_LAYERS];
+  __shared__ unsigned long long s_w[2 * (SEL_ML_SEG / 32)];
+  __shared__ int s_cnt[8][CGH_MAX_LAYERS];
   pdl_wait();
   pdl_trigger();
   const int nseg = (W >> 3) / SEL_ML_SEG, R = blockIdx.x / nseg, sg = blockIdx.x - R * nseg;
@@ -613,42 +657,31 @@ __global__ void __launch_bounds__(SEL_ML_SEG) k_select_ml_count(const uint8_t* _
   MlMasks m;
   ml_masks(sal, L, W, R, bx3, Z, T.t[3].threshold, T.t[2].threshold, T.t[1].threshold, m);
   if (blockIdx.x == 0 && threadIdx.x < 4) T.t[threadIdx.x].count[1] = 0;  // the scan's CTA counters
-  for (int k = 0; k < 4; ++k) {
-    const SelTask& tk = T.t[k];
-    for (int q = 0; q < ml_rows(k); ++q) {
-      for (int e = threadIdx.x; e < Z; e += blockDim.x) s_cnt[0][e] = 0;
-      unsigned long long u = ml_cta_or(ml_row_union(m, k, q), s_or);  // also orders the clear above
-      while (u) {
-        const int z = __ffsll((long long)u) - 1;
-        u &= u - 1ull;
-        const int c = __reduce_add_sync(0xffffffffu, __popc(ml_row_bits(m, k, q, z)));
-        if ((threadIdx.x & 31) == 0 && c) atomicAdd(&s_cnt[0][z], c);
-      }
-      __syncthreads();
-      const int row = R * ml_rows(k) + q;  // row of this level's blocks
-      for (int z = threadIdx.x; z < Z; z += blockDim.x)
-        chunk_cnt[tk.cnt_off + z * tk.nchunks + row * nseg + sg] = s_cnt[0][z];
-      __syncthreads();
+  for (int e = threadIdx.x; e < 8 * Z; e += blockDim.x) s_cnt[e / Z][e % Z] = 0;
+  unsigned long long all = m.lll | m.m3;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) all |= m.m2[q];
+#pragma unroll
+  for (int q = 0; q < 16; ++q) all |= m.m1[q];
+  unsigned long long u = ml_cta_or(all, s_or);  // its barriers also order the clear above
+  while (u) {
+    const int z = __ffsll((long long)u) - 1;
+    u &= u - 1ull;
+    unsigned long long lo, hi, tlo, thi;
+    ml_packed_counts(m, z, lo, hi);
+    ml_cta_exclusive2(lo, hi, s_w, tlo, thi);
+    if (threadIdx.x < 8) {
+      const unsigned long long t = threadIdx.x < 4 ? tlo : thi;
+      s_cnt[threadIdx.x][z] = (int)((t >> (16 * (threadIdx.x & 3))) & 0xFFFFull);
     }
   }
-}
-// Exclusive prefix of x over the SEL_ML_SEG threads of the CTA (s_w: one int per warp).
-__device__ __forceinline__ int ml_cta_exclusive(int x, int* s_w) {
-  constexpr int NW = SEL_ML_SEG / 32;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  int inc = x;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const int t = __shfl_up_sync(0xffffffffu, inc, o);
-    if (lane >= o) inc += t;
-  }
-  __syncthreads();  // s_w of the previous call has been read
-  if (lane == 31) s_w[warp] = inc;
   __syncthreads();
-  int before = 0;
-#pragma unroll
-  for (int w = 0; w < NW; ++w) before += w < warp ? s_w[w] : 0;
-  return before + inc - x;
+  for (int e = threadIdx.x; e < 8 * Z; e += blockDim.x) {
+    const int r = e / Z, z = e - r * Z, k = ml_row_list(r);
+    const SelTask& tk = T.t[k];
+    const int row = R * ml_rows(k) + ml_row_q(r);
+    chunk_cnt[tk.cnt_off + z * tk.nchunks + row * nseg + sg] = s_cnt[r][z];
+  }
 }
 
 // Pass 3: ordered scatter of all four lists (FLAGS: also the tensor-core flags).
@@ -658,50 +691,62 @@ __global__ void __launch_bounds__(SEL_ML_SEG) k_select_ml_scatter(const uint8_t*
                                                                   const SelTasks T, const int* __restrict__ chunk_cnt,
                                                                   const int* __restrict__ chunk_off, TcFlags fl) {
   __shared__ unsigned s_or[2 * (SEL_ML_SEG / 32)];
-  __shared__ int s_w[SEL_ML_SEG / 32];
-  __shared__ int s_base[CGH_MAX_LAYERS];
+  __shared__ unsigned long long s_w[2 * (SEL_ML_SEG / 32)];
+  __shared__ int s_base[8][CGH_MAX_LAYERS];
   pdl_wait();
   pdl_trigger();
   const int nseg = (W >> 3) / SEL_ML_SEG, R = blockIdx.x / nseg, sg = blockIdx.x - R * nseg;
   const int bx3 = sg * SEL_ML_SEG + threadIdx.x;
   MlMasks m;
   ml_masks(sal, L, W, R, bx3, Z, T.t[3].threshold, T.t[2].threshold, T.t[1].threshold, m);
-  for (int k = 0; k < 4; ++k) {
+  // every row's first position per layer: the prefix of its scan block plus its offset
+  for (int e = threadIdx.x; e < 8 * Z; e += blockDim.x) {
+    const int r = e / Z, z = e - r * Z, k = ml_row_list(r);
     const SelTask& tk = T.t[k];
-    const int level = tk.level, hl = H >> level, wl = W >> level, rows = ml_rows(k), cols = k == 1 ? 4 : k == 2 ? 2 : 1;
-    for (int q = 0; q < rows; ++q) {
-      const int row = R * rows + q;
-      __syncthreads();  // s_base of the previous row has been read
-      for (int z = threadIdx.x; z < Z; z += blockDim.x) {
-        const int e = z * tk.nchunks + row * nseg + sg;
-        s_base[z] = chunk_cnt[tk.cnt_off + (e / SEL_SCAN_BLOCK) * SEL_SCAN_BLOCK] + chunk_off[tk.cnt_off + e];
-      }
-      unsigned long long u = ml_cta_or(ml_row_union(m, k, q), s_or);  // its barriers publish s_base
-      while (u) {
-        const int z = __ffsll((long long)u) - 1;
-        u &= u - 1ull;
-        const int bits = ml_row_bits(m, k, q, z);
-        int pos = s_base[z] + ml_cta_exclusive(__popc(bits), s_w);
-        for (int c = 0; c < cols; ++c) {
-          if (!((bits >> c) & 1)) continue;
-          const int by = row, bx = bx3 * cols + c;
-          if (pos < tk.capacity) {
-            tk.list[pos] = (z << 24) | (by << 12) | bx;
-            if (FLAGS) {
-              if (k == 0) {
-                fl.occ3[((size_t)z * hl + by) * wl + bx] = 1;
-                fl.rowband[(size_t)z * hl + by] = 1;
-                fl.colband[(size_t)z * wl + bx] = 1;
-              } else {
-                uint8_t* sel = level == 1 ? fl.sel[1] : level == 2 ? fl.sel[2] : fl.sel[3];
-                sel[((size_t)z * hl + by) * wl + bx] = 1;
-                fl.rowband[(size_t)z * (H >> 3) + (by >> (3 - level))] = 1;
-                fl.colband[(size_t)z * (W >> 3) + (bx >> (3 - level))] = 1;
-              }
+    const int row = R * ml_rows(k) + ml_row_q(r);
+    const int idx = z * tk.nchunks + row * nseg + sg;
+    s_base[r][z] = chunk_cnt[tk.cnt_off + (idx / SEL_SCAN_BLOCK) * SEL_SCAN_BLOCK] + chunk_off[tk.cnt_off + idx];
+  }
+  unsigned long long all = m.lll | m.m3;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) all |= m.m2[q];
+#pragma unroll
+  for (int q = 0; q < 16; ++q) all |= m.m1[q];
+  unsigned long long u = ml_cta_or(all, s_or);  // its barriers publish s_base
+  while (u) {
+    const int z = __ffsll((long long)u) - 1;
+    u &= u - 1ull;
+    unsigned long long lo, hi, tlo, thi;
+    ml_packed_counts(m, z, lo, hi);
+    ml_cta_exclusive2(lo, hi, s_w, tlo, thi);
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      const int k = ml_row_list(r), q = ml_row_q(r);
+      const SelTask& tk = T.t[k];
+      const int bits = ml_row_bits(m, k, q, z);
+      if (!bits) continue;
+      const int level = tk.level, hl = H >> level, wl = W >> level, cols = k == 1 ? 4 : k == 2 ? 2 : 1;
+      int pos = s_base[r][z] + (int)(((r < 4 ? lo : hi) >> (16 * (r & 3))) & 0xFFFFull);
+      const int by = R * ml_rows(k) + q;
+      for (int c = 0; c < cols; ++c) {
+        if (!((bits >> c) & 1)) continue;
+        const int bx = bx3 * cols + c;
+        if (pos < tk.capacity) {
+          tk.list[pos] = (z << 24) | (by << 12) | bx;
+          if (FLAGS) {
+            if (k == 0) {
+              fl.occ3[((size_t)z * hl + by) * wl + bx] = 1;
+              fl.rowband[(size_t)z * hl + by] = 1;
+              fl.colband[(size_t)z * wl + bx] = 1;
+            } else {
+              uint8_t* sel = level == 1 ? fl.sel[1] : level == 2 ? fl.sel[2] : fl.sel[3];
+              sel[((size_t)z * hl + by) * wl + bx] = 1;
+              fl.rowband[(size_t)z * (H >> 3) + (by >> (3 - level))] = 1;
+              fl.colband[(size_t)z * (W >> 3) + (bx >> (3 - level))] = 1;
             }
           }
-          ++pos;
         }
+        ++pos;
       }
     }
   }
