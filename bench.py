@@ -740,6 +740,31 @@ def run_ours(args):
                         "products per real product; rel-L2 in other_forms_rel_l2_vs_fp64_oracle (bar 1e-3)"}
         del g2
 
+    # ---- a long steady run of the same captured step (L2 flushed before each), with the SM
+    # clock sampled throughout: thousands of steps instead of the K of the timed region above
+    steady = None
+    if graph is not None and rank == 0 and args.steady_steps > 0:
+        n_st = args.steady_steps
+        sam = ClockSampler(devn)
+        sam.start()
+        time.sleep(0.3)
+        ev_st = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n_st)]
+        with torch.cuda.stream(stream):
+            for k in range(n_st):
+                flush.fill_(float(k))
+                ev_st[k][0].record(stream)
+                graph.replay()
+                ev_st[k][1].record(stream)
+        torch.cuda.synchronize()
+        sam.stop()
+        t_st = sorted(a.elapsed_time(b) for a, b in ev_st)
+        steady = {"steps": n_st, "ms_per_step_median": t_st[n_st // 2], "ms_per_step_p10": t_st[n_st // 10],
+                  "ms_per_step_p99": t_st[min(n_st - 1, int(0.99 * n_st))],
+                  "value_median": UNITS_PER_STEP / (t_st[n_st // 2] / 1e3) / 1e9, "unit": UNIT,
+                  "clocks": sam.summary(),
+                  "note": "the captured step replayed back to back, a 512 MiB L2 flush before each, SM clock "
+                          "sampled every 100 ms over the run"}
+
     # ---- per-stage device times (CUDA events recorded by the library on `stream`),
     # L2 flushed before every repetition; the dominant kernel's average launch duration
     R = max(5, min(50, args.steps))
@@ -904,6 +929,8 @@ def run_ours(args):
         "unit_peaks_measured": unit_peaks,
     }
     line["stages_ms"] = stages
+    if steady is not None:
+        line["steady_state"] = steady
     if form != "direct_lut" and not args.skip_forms:
         # the same superposition with both stages in one cooperative launch (plan option)
         plan.set_fusion(True)
@@ -1043,6 +1070,8 @@ def main():
     ap.add_argument("--skip-asm", action="store_true", help="skip the angular-spectrum reconstruction timing")
     ap.add_argument("--skip-rgb", action="store_true", help="skip the three-channel colour frame timing")
     ap.add_argument("--skip-hbm-paths", action="store_true", help="skip the DWT and selection at an 8192^2 object")
+    ap.add_argument("--steady-steps", type=int, default=5000,
+                    help="captured steps of the steady-state run (0: skip)")
     ap.add_argument("--skip-precision", action="store_true",
                     help="skip the 2048^2-hologram, 32-layer precision workload")
     ap.add_argument("--no-cpu-baseline", action="store_true")
