@@ -48,6 +48,7 @@ struct cgh_plan {
   int* d_chunk_off;
   int max_chunks;
   unsigned* d_sel_bar;  // [0]: the fused selection's grid barrier; [1]: its self-test's
+  uint2* d_ml_rec;      // multi-level selection: one record per 8x8 block (null below 2048-pixel rows)
   int sel_coop_ctas;
 
   // Separable tensor-core path (allocated lazily by the first call that needs it).
@@ -134,12 +135,15 @@ struct SelTasks {
   SelTask t[4];
   int n;
 };
-// The fused single-launch selection: the plan's grid-barrier word, its status word and the
-// largest grid the device holds at once (0: use the three-pass selection).
+// Selection scratch of a plan: the fused single-launch selection's grid-barrier word, its
+// status word and the largest grid the device holds at once (0: use the three-pass
+// selection); the multi-level selection's block records (two words per 8x8 block of the
+// object; null: the multi-level passes are not used).
 struct SelCoop {
   unsigned* bar;
   int* status;
   int max_ctas;
+  uint2* ml_rec;
 };
 
 // Kernel launchers (kernels_basic.cu).  All asynchronous on `st`.
@@ -164,7 +168,9 @@ cudaError_t launch_select_tasks(int obj_h, int obj_w, int n_layers, const uint8_
 int select_fused_ctas_per_sm();
 cudaError_t launch_grid_barrier_selftest(unsigned* bar, int* status, int* crossed, int ctas,
                                          unsigned long long limit_ns, int absent, cudaStream_t st);
-static inline SelCoop plan_sel_coop(const cgh_plan* p) { return SelCoop{p->d_sel_bar, p->d_status, p->sel_coop_ctas}; }
+static inline SelCoop plan_sel_coop(const cgh_plan* p) {
+  return SelCoop{p->d_sel_bar, p->d_status, p->sel_coop_ctas, p->d_ml_rec};
+}
 cudaError_t basic_init_attributes();
 int tc_init_attributes();
 

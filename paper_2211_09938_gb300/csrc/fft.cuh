@@ -2,11 +2,13 @@
 // angular-spectrum reconstruction.
 //
 // Algorithm: Stockham auto-sort FFT (Stockham 1966; the GPU formulation of Govindaraju et
-// al., SC 2008): pass p combines R-point DFTs of the sub-transforms of length Ns = 8^p
+// al., SC 2008): pass p combines R-point DFTs of the sub-transforms of length Ns = 16^p
 // already computed; group j reads the R elements j + r*L/R, multiplies element r by the
 // twiddle W_{Ns*R}^{(j mod Ns)*r}, takes an R-point DFT in registers and writes element r
-// to (j div Ns)*Ns*R + (j mod Ns) + r*Ns.  Radix 8 for every pass but possibly the last
-// (radix 2 or 4), so 1024 = 8*8*8*2 takes four passes.  Output in natural order.
+// to (j div Ns)*Ns*R + (j mod Ns) + r*Ns.  Radix 16 for every pass but possibly the last
+// (radix 2, 4 or 8), so 1024 = 16*16*4 takes three passes and two trips through shared
+// memory, and a thread holding 16 elements takes one whole group per pass.  Output in
+// natural order.
 // Forward: X[k] = sum_n x[n] exp(-2 pi i n k / L); inverse: exp(+...), unnormalised.
 //
 // A CTA transforms B lines of length L at once (a tile of rows or of columns).  Thread
@@ -14,7 +16,7 @@
 // 32/B consecutive elements of each of B lines (coalesced for both row and column tiles).
 // The first pass reads its inputs through a loader functor and the last pass writes its
 // outputs through a storer functor (both see (line, index)); the passes in between work
-// in shared memory, padded by one element every 8 and with a line stride chosen so that
+// in shared memory, padded by one element every 16 and with a line stride chosen so that
 // the strided accesses of the early passes spread over the banks.
 #pragma once
 
@@ -81,22 +83,58 @@ __host__ __device__ __forceinline__ void dft8(float2* v) {
   v[7] = csub(e3, o3);
 }
 
+// 16-point DFT as 4 x 4: 4-point DFTs over the stride-4 samples, twiddles W_16^(n2 k1),
+// 4-point DFTs across, and the 4 x 4 transpose back to natural order.
+template <bool INV>
+__host__ __device__ __forceinline__ void dft16(float2* v) {
+  constexpr float c = 0.92387953251128675613f;  // cos(pi/8)
+  constexpr float s = 0.38268343236508977173f;  // sin(pi/8)
+  constexpr float h = 0.70710678118654752440f;  // 1/sqrt(2)
+#pragma unroll
+  for (int n2 = 0; n2 < 4; ++n2) dft4<INV>(v[n2], v[4 + n2], v[8 + n2], v[12 + n2]);
+  // slot 4 k1 + n2 times W_16^(n2 k1); forward W_16^m = exp(-2 pi i m / 16), inverse its conjugate
+  const float sg = INV ? 1.f : -1.f;
+  v[5] = cmul(v[5], make_float2(c, sg * s));       // W^1
+  v[6] = cmul(v[6], make_float2(h, sg * h));       // W^2
+  v[7] = cmul(v[7], make_float2(s, sg * c));       // W^3
+  v[9] = cmul(v[9], make_float2(h, sg * h));       // W^2
+  v[10] = rot<INV>(v[10]);                         // W^4
+  v[11] = cmul(v[11], make_float2(-h, sg * h));    // W^6
+  v[13] = cmul(v[13], make_float2(s, sg * c));     // W^3
+  v[14] = cmul(v[14], make_float2(-h, sg * h));    // W^6
+  v[15] = cmul(v[15], make_float2(-c, -sg * s));   // W^9
+#pragma unroll
+  for (int k1 = 0; k1 < 4; ++k1) dft4<INV>(v[4 * k1], v[4 * k1 + 1], v[4 * k1 + 2], v[4 * k1 + 3]);
+  // X[k1 + 4 k2] sits in slot 4 k1 + k2
+  float2 t[16];
+#pragma unroll
+  for (int k = 0; k < 16; ++k) t[k] = v[4 * (k & 3) + (k >> 2)];
+#pragma unroll
+  for (int k = 0; k < 16; ++k) v[k] = t[k];
+}
+
 template <int R, bool INV>
 __host__ __device__ __forceinline__ void dft(float2* v) {
-  if constexpr (R == 8) {
+  if constexpr (R == 16) {
+    dft16<INV>(v);
+  } else if constexpr (R == 8) {
     dft8<INV>(v);
   } else if constexpr (R == 4) {
     dft4<INV>(v[0], v[1], v[2], v[3]);
   } else {
-    static_assert(R == 2, "radix 2, 4 or 8");
+    static_assert(R == 2, "radix 2, 4, 8 or 16");
     dft2<INV>(v);
   }
 }
 
+// Radix 16 for every pass but possibly the last (radix 2, 4 or 8).
+constexpr int LR = 4;  // log2 of the radix
 __host__ __device__ constexpr int ilog2(int x) { return x <= 1 ? 0 : 1 + ilog2(x >> 1); }
-__host__ __device__ constexpr int n_passes(int L) { return ilog2(L) / 3 + (ilog2(L) % 3 ? 1 : 0); }
-__host__ __device__ constexpr int pass_radix(int L, int p) { return p < ilog2(L) / 3 ? 8 : (1 << (ilog2(L) % 3)); }
-__host__ __device__ constexpr int pass_ns(int p) { return 1 << (3 * p); }  // only the last pass may have radix < 8
+__host__ __device__ constexpr int n_passes(int L) { return ilog2(L) / LR + (ilog2(L) % LR ? 1 : 0); }
+__host__ __device__ constexpr int pass_radix(int L, int p) {
+  return p < ilog2(L) / LR ? (1 << LR) : (1 << (ilog2(L) % LR));
+}
+__host__ __device__ constexpr int pass_ns(int p) { return 1 << (LR * p); }  // only the last pass may have a smaller radix
 
 // Twiddle and DFT of one group of pass (R, NS): v[r] *= W_{NS*R}^{(j mod NS) r}.
 template <int R, int NS, bool INV>
@@ -120,14 +158,16 @@ __host__ __device__ __forceinline__ int out_base(int j) {
 }
 
 // Shared-memory layout of B lines of length L: line stride LS floats2, one pad element
-// after every 8.  LS = L + L/8 + 16/min(B,16) (mod 16 adjustments keep it a multiple of 8
-// plus the bank offset that separates the B lines a half-warp touches).
+// after every 16 (the first pass writes each group's 16 outputs contiguously, so padded
+// groups start 17 elements apart and the threads of a half-warp hit distinct banks).
+// LS = L + L/16 + 16/min(B,16): the last term is the bank offset that separates the B lines
+// a half-warp touches.
 template <int L, int B>
 struct Smem {
   static constexpr int bo = 16 / (B < 16 ? B : 16);
-  static constexpr int LS = L + L / 8 + (bo == 16 ? 1 : bo);
+  static constexpr int LS = L + L / 16 + (bo == 16 ? 1 : bo);
   static constexpr int floats2 = B * LS;
-  __host__ __device__ static __forceinline__ int at(int b, int i) { return b * LS + i + (i >> 3); }
+  __host__ __device__ static __forceinline__ int at(int b, int i) { return b * LS + i + (i >> 4); }
 };
 
 #ifdef __CUDACC__
@@ -140,7 +180,7 @@ template <int L, int B, int T, bool INV, bool LD_SMEM = false, class Ld, class S
 __device__ __forceinline__ void fft_tile(float2* s, const float2* __restrict__ tw, Ld&& ld, St&& st) {
   using S = Smem<L, B>;
   constexpr int NP = n_passes(L);
-  static_assert(NP >= 2 && NP <= 4, "L in [64, 4096]");
+  static_assert(NP >= 2 && NP <= 3, "L in [64, 4096]");
   static_assert(L <= LMAX, "L too large");
 
   // pass 0 (radix 8, NS = 1): global -> registers -> shared
@@ -188,7 +228,6 @@ __device__ __forceinline__ void fft_tile(float2* s, const float2* __restrict__ t
     __syncthreads();
   };
   if constexpr (NP > 2) middle(std::integral_constant<int, 1>{});
-  if constexpr (NP > 3) middle(std::integral_constant<int, 2>{});
   // last pass: shared -> registers -> global (NS * R = L, so group j writes j + r * NS)
   {
     constexpr int p = NP - 1;

@@ -6,6 +6,8 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <cuda_fp16.h>
+
 #include "cgh_internal.h"
 
 #include <type_traits>
@@ -499,256 +501,421 @@ int select_scan_blocks(int n_layers, int nchunks) {
 // ---------------------------------------------------------------------------
 // Multi-level selection for large objects (width a multiple of 2048): the four lists of a
 // progressive hologram (LLL = every occupied 8x8 block, and the detail blocks of levels 3,
-// 2, 1 above their thresholds) from ONE read of the inputs per pass.  One thread owns one
-// 8x8 block and derives the masks of its 2x2, 4x4 and 8x8 blocks in registers; one CTA
-// owns a segment of 256 consecutive 8x8 blocks of one row of them.  The count table of a
-// list holds, per layer, one entry per (row of that level's blocks, segment): 1 row of
-// level-3 blocks, 2 rows of level-2 and 4 rows of level-1 blocks per segment.  In the
+// 2, 1 above their thresholds) in two passes over the 8x8 blocks.  One thread owns one 8x8
+// block; one CTA owns a segment of 256 consecutive 8x8 blocks of one row of them.  The count
+// table of a list holds, per layer, one entry per (row of that level's blocks, segment): 1
+// row of level-3 blocks, 2 rows of level-2 and 4 rows of level-1 blocks per segment.  In the
 // order (layer, row, segment) these are the list's own order (layer, block row, block
-// column), so the blocked exclusive scan of the three-pass selection gives every segment
-// row its first position, and the scatter ranks the blocks inside it.  Bit-exact with the
-// per-level selection.
+// column), so the blocked exclusive scan of the three-pass selection gives every segment row
+// its first position, and the scatter ranks the blocks inside it.
+//   count:   reads the block's 64 saliency and layer bytes, writes a 64-bit record of the block
+//            and adds its per-layer row counts into the CTA's table (warp reductions);
+//   scatter: reads the records instead of the inputs (the layer map again only for blocks
+//            with points in three or more layers), ranks the blocks and writes the entries.
+// Byte-wise work uses 32-bit integer and paired fp16 operations: the block maxima of the
+// saliency as fp16 pairs 1024 + s (exact: integers up to 2048 are fp16 numbers), layer
+// equality and range tests as carry-free byte arithmetic.  Bit-exact with the per-level
+// selection.
 #define SEL_ML_SEG 256
 
-struct MlMasks {
-  unsigned long long lll, m3, m2[4], m1[16];  // m2[2r+c], m1[4r+c]: rows r, columns c
-};
+// Record of one 8x8 block, two words.  Each word describes one layer of the block: bits 0-15
+// its level-1 entries (the 2x2 blocks, 4r+c), bits 16-19 its level-2 entries (the 4x4 blocks,
+// 2r+c), bit 20 its level-3 entry, bit 21 its LLL entry (the block holds a point of that
+// layer), bits 22-27 the layer; 0 = no layer.  A block with points in three or more layers
+// sets ML_MULTI in word 1 and keeps its threshold tests in word 0 (bits 0-20 as above: a
+// sub-block passes when the maximum of its saliency is above its level's threshold, or the
+// level has none); the scatter reads its layer map again.
+#define ML_MULTI 0x80000000u
+#define ML_BITS 0x3FFFFFu
+#define ML_B7 0x80808080u
+#define ML_LO7 0x7F7F7F7Fu
 
-// Masks of the 8x8 block (by3, bx3): layers present (and, for the detail levels, the block
-// maximum of the saliency above that level's threshold, -1 = no threshold).
-__device__ __forceinline__ void ml_masks(const uint8_t* __restrict__ sal, const uint8_t* __restrict__ L, int W,
-                                         int by3, int bx3, int Z, int t3, int t2, int t1, MlMasks& m) {
-  uint2 lv[8], sv[8];
+__device__ __forceinline__ __half2 ml_as_h2(unsigned u) { return *reinterpret_cast<const __half2*>(&u); }
+__device__ __forceinline__ unsigned ml_as_u(__half2 h) { return *reinterpret_cast<const unsigned*>(&h); }
+// Bytes 0 and 2 (SEL 0x4240) or 1 and 3 (0x4341) of w as the fp16 pair (1024 + b, 1024 + b').
+__device__ __forceinline__ __half2 ml_pair(unsigned w, unsigned sel) { return ml_as_h2(__byte_perm(w, 0x64u, sel)); }
+// A level's threshold t as the fp16 pair 1024 + t, clamped so that "above" stays exact: no
+// threshold (t < 0) passes every block, t >= 255 none.
+__device__ __forceinline__ __half2 ml_threshold(int t) {
+  return __float2half2_rn(1024.f + (float)(t < 0 ? -1 : t > 255 ? 255 : t));
+}
+// Bits of the low and high halves of a paired mask (0xFFFF per true half).
+__device__ __forceinline__ unsigned ml_two(unsigned g) { return (g & 1u) | ((g >> 15) & 2u); }
+
+// Threshold tests of the block (record bits 0-20) from its saliency rows.
+__device__ __forceinline__ unsigned ml_tests(const uint2 (&sv)[8], __half2 t1, __half2 t2, __half2 t3) {
+  __half2 m[4][2];  // [row pair][half]: maxima of the 2x2 blocks 4p + 2h (low) and 4p + 2h + 1 (high)
+  unsigned tests = 0u;
 #pragma unroll
-  for (int r = 0; r < 8; ++r) {
-    const size_t o = (size_t)(8 * by3 + r) * W + 8 * bx3;
-    lv[r] = *reinterpret_cast<const uint2*>(L + o);
-    sv[r] = *reinterpret_cast<const uint2*>(sal + o);
+  for (int p = 0; p < 4; ++p)
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const unsigned a = h ? sv[2 * p].y : sv[2 * p].x, b = h ? sv[2 * p + 1].y : sv[2 * p + 1].x;
+      m[p][h] = __hmax2(__hmax2(ml_pair(a, 0x4240u), ml_pair(a, 0x4341u)),
+                        __hmax2(ml_pair(b, 0x4240u), ml_pair(b, 0x4341u)));
+      tests |= ml_two(__hgt2_mask(m[p][h], t1)) << (4 * p + 2 * h);
+    }
+  // 4x4 blocks of row r2: low = column 0, high = column 1
+  __half2 x[2];
+#pragma unroll
+  for (int r2 = 0; r2 < 2; ++r2) {
+    const unsigned c0 = ml_as_u(__hmax2(m[2 * r2][0], m[2 * r2 + 1][0]));
+    const unsigned c1 = ml_as_u(__hmax2(m[2 * r2][1], m[2 * r2 + 1][1]));
+    x[r2] = __hmax2(ml_as_h2(__byte_perm(c0, c1, 0x5410u)), ml_as_h2(__byte_perm(c0, c1, 0x7632u)));
+    tests |= ml_two(__hgt2_mask(x[r2], t2)) << (16 + 2 * r2);
   }
-  unsigned long long occ1[16];
-  int mx1[16];
+  const __half2 y = __hmax2(x[0], x[1]);
+  const unsigned yu = ml_as_u(y);
+  tests |= (__hgt2_mask(__hmax2(y, ml_as_h2(__byte_perm(yu, yu, 0x1032u))), t3) & 1u) << 20;
+  return tests;
+}
+
+// Carry-free byte tests (bit 7 of every byte): byte == 0, and byte >= Z (Z <= 128).
+__device__ __forceinline__ unsigned ml_zero_bytes(unsigned x) { return ~(((x & ML_LO7) + ML_LO7) | x) & ML_B7; }
+__device__ __forceinline__ unsigned ml_absent_bytes(unsigned w, unsigned kz) { return (((w & ML_LO7) + kz) | w) & ML_B7; }
+
+// The 2x2 blocks (4r+c) holding a marked pixel, from per-row byte marks (bit 7 of every byte).
+__device__ __forceinline__ unsigned ml_gather(const uint2 (&mk)[8]) {
+  unsigned bits = 0u;
 #pragma unroll
-  for (int q = 0; q < 16; ++q) occ1[q] = 0ull, mx1[q] = 0;
+  for (int p = 0; p < 4; ++p)
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      unsigned t = h ? (mk[2 * p].y | mk[2 * p + 1].y) : (mk[2 * p].x | mk[2 * p + 1].x);
+      t |= t << 8;  // bit 15: columns 0-1, bit 31: columns 2-3
+      bits |= (((t >> 15) & 1u) | ((t >> 30) & 2u)) << (4 * p + 2 * h);
+    }
+  return bits;
+}
+// The 2x2 blocks holding a pixel of layer z.
+__device__ __forceinline__ unsigned ml_pres_layer(const uint2 (&lv)[8], unsigned z) {
+  const unsigned zz = 0x01010101u * z;
+  uint2 mk[8];
+#pragma unroll
+  for (int r = 0; r < 8; ++r) mk[r] = make_uint2(ml_zero_bytes(lv[r].x ^ zz), ml_zero_bytes(lv[r].y ^ zz));
+  return ml_gather(mk);
+}
+
+// Record bits 0-21 of one layer from the 2x2 blocks holding its points (pres, 4r+c) and the
+// threshold tests: a block of any level is an entry when it holds a point and passes.
+__device__ __forceinline__ unsigned ml_layer_bits(unsigned pres, unsigned tests) {
+  if (!pres) return 0u;
+  const unsigned p2 = ((pres & 0x0033u) ? 1u : 0u) | ((pres & 0x00CCu) ? 2u : 0u) | ((pres & 0x3300u) ? 4u : 0u) |
+                      ((pres & 0xCC00u) ? 8u : 0u);
+  return (pres & tests & 0xFFFFu) | ((p2 & (tests >> 16) & 0xFu) << 16) | (tests & (1u << 20)) | (1u << 21);
+}
+
+// The layers present in a block (bit z: a pixel of layer z < Z).
+__device__ __forceinline__ unsigned long long ml_layer_mask(const uint2 (&lv)[8], int Z) {
+  unsigned long long m = 0ull;
 #pragma unroll
   for (int r = 0; r < 8; ++r)
 #pragma unroll
-    for (int c = 0; c < 8; ++c) {
-      const unsigned lw = c < 4 ? lv[r].x : lv[r].y, sw = c < 4 ? sv[r].x : sv[r].y;
-      const int sh = 8 * (c & 3);
-      const int lz = (lw >> sh) & 0xFF, sz = (sw >> sh) & 0xFF;
-      const int q = (r >> 1) * 4 + (c >> 1);
-      if (lz < Z) occ1[q] |= 1ull << lz;
-      mx1[q] = max(mx1[q], sz);
+    for (int h = 0; h < 2; ++h) {
+      const unsigned w = h ? lv[r].y : lv[r].x;
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const int lz = (w >> (8 * c)) & 0xFF;
+        if (lz < Z) m |= 1ull << lz;
+      }
     }
-  unsigned long long occ3 = 0ull;
-  int mx3 = 0;
-#pragma unroll
-  for (int r2 = 0; r2 < 2; ++r2)
-#pragma unroll
-    for (int c2 = 0; c2 < 2; ++c2) {
-      unsigned long long o2 = 0ull;
-      int x2 = 0;
-#pragma unroll
-      for (int r = 0; r < 2; ++r)
-#pragma unroll
-        for (int c = 0; c < 2; ++c) {
-          const int q = (2 * r2 + r) * 4 + 2 * c2 + c;
-          o2 |= occ1[q];
-          x2 = max(x2, mx1[q]);
-          m.m1[q] = (t1 < 0 || mx1[q] > t1) ? occ1[q] : 0ull;
-        }
-      m.m2[2 * r2 + c2] = (t2 < 0 || x2 > t2) ? o2 : 0ull;
-      occ3 |= o2;
-      mx3 = max(mx3, x2);
-    }
-  m.lll = occ3;
-  m.m3 = (t3 < 0 || mx3 > t3) ? occ3 : 0ull;
+  return m;
 }
 
-// Layer-z bits of this thread's blocks in row q of list k (k: 0 LLL, 1 level 1, 2 level 2,
-// 3 level 3; rows per segment 1, 4, 2, 1), left to right.
-__device__ __forceinline__ int ml_row_bits(const MlMasks& m, int k, int q, int z) {
-  if (k == 0) return (int)((m.lll >> z) & 1ull);
-  if (k == 3) return (int)((m.m3 >> z) & 1ull);
-  if (k == 2) return (int)((m.m2[2 * q] >> z) & 1ull) | ((int)((m.m2[2 * q + 1] >> z) & 1ull) << 1);
-  int b = 0;
+__device__ __forceinline__ unsigned ml_layer_of(unsigned w) { return (w >> 22) & 63u; }
+// Layers of a record (bit z), for blocks with at most two layers.
+__device__ __forceinline__ unsigned long long ml_rec_layers(uint2 r) {
+  return ((r.x >> 21) & 1u ? 1ull << ml_layer_of(r.x) : 0ull) | ((r.y >> 21) & 1u ? 1ull << ml_layer_of(r.y) : 0ull);
+}
+// Bits 0-21 of layer z for a thread's block: from its record, or, for a block with points in
+// three or more layers, from its layer rows (lv) and the tests kept in the record.
+__device__ __forceinline__ unsigned ml_bits_of(uint2 r, const uint2 (&lv)[8], unsigned long long lmask, int z) {
+  if (!(r.y & ML_MULTI))
+    return ((int)ml_layer_of(r.x) == z ? (r.x & ML_BITS) : 0u) | ((int)ml_layer_of(r.y) == z ? (r.y & ML_BITS) : 0u);
+  if (!((lmask >> z) & 1ull)) return 0u;
+  return ml_layer_bits(ml_pres_layer(lv, (unsigned)z), r.x);
+}
+
+// Record of the block from its rows of layers (lv) and its threshold tests.
+__device__ __forceinline__ uint2 ml_record(const uint2 (&lv)[8], int Z, unsigned tests) {
+  const unsigned l0 = 0x01010101u * (lv[0].x & 0xFFu);
+  unsigned d = 0u;
 #pragma unroll
-  for (int c = 0; c < 4; ++c) b |= (int)((m.m1[4 * q + c] >> z) & 1ull) << c;
-  return b;
+  for (int r = 0; r < 8; ++r) d |= (lv[r].x ^ l0) | (lv[r].y ^ l0);
+  if (!d) {  // one value throughout: one layer, or no point
+    const unsigned z = l0 & 0xFFu;
+    return make_uint2((int)z < Z ? (z << 22) | ml_layer_bits(0xFFFFu, tests) : 0u, 0u);
+  }
+  const unsigned kz = 0x01010101u * (unsigned)(128 - Z);
+  // a layer of the block: its first pixel's, or else the first point's
+  unsigned za = l0 & 0xFFu;
+  if ((int)za >= Z) {
+    za = 0xFFu;
+#pragma unroll
+    for (int r = 0; r < 8; ++r)
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const unsigned w = h ? lv[r].y : lv[r].x, pr = ~ml_absent_bytes(w, kz) & ML_B7;
+        if (za == 0xFFu && pr) za = (w >> (__ffs(pr) - 8)) & 0xFFu;
+      }
+    if (za == 0xFFu) return make_uint2(0u, 0u);
+  }
+  // pixels of layer za, and points of other layers
+  uint2 ea[8];
+  unsigned rest = 0u, zb = 0xFFu;
+  const unsigned zza = 0x01010101u * za;
+#pragma unroll
+  for (int r = 0; r < 8; ++r) {
+    ea[r] = make_uint2(ml_zero_bytes(lv[r].x ^ zza), ml_zero_bytes(lv[r].y ^ zza));
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const unsigned w = h ? lv[r].y : lv[r].x;
+      const unsigned o = ~ml_absent_bytes(w, kz) & ML_B7 & ~(h ? ea[r].y : ea[r].x);
+      if (zb == 0xFFu && o) zb = (w >> (__ffs(o) - 8)) & 0xFFu;
+      rest |= o;
+    }
+  }
+  const unsigned wa = (za << 22) | ml_layer_bits(ml_gather(ea), tests);
+  if (!rest) return make_uint2(wa, 0u);
+  // a second layer: the block is described when no point lies in a third
+  const unsigned zzb = 0x01010101u * zb;
+  uint2 eb[8];
+  unsigned third = 0u;
+#pragma unroll
+  for (int r = 0; r < 8; ++r) {
+    eb[r] = make_uint2(ml_zero_bytes(lv[r].x ^ zzb), ml_zero_bytes(lv[r].y ^ zzb));
+    third |= (~ml_absent_bytes(lv[r].x, kz) & ~(ea[r].x | eb[r].x)) | (~ml_absent_bytes(lv[r].y, kz) & ~(ea[r].y | eb[r].y));
+  }
+  if (third & ML_B7) return make_uint2(tests, ML_MULTI);
+  return make_uint2(wa, (zb << 22) | ml_layer_bits(ml_gather(eb), tests));
+}
+
+// The eight rows of a segment: 0 LLL, 1 level 3, 2-3 level 2, 4-7 level 1.  A thread's count of
+// entries in each row, packed as 16-bit fields, two rows per word (a row of a segment has at
+// most 1024 blocks, so no field overflows in the CTA-wide sums).
+__device__ __forceinline__ void ml_pack(unsigned b, unsigned (&w)[4]) {
+  w[0] = ((b >> 21) & 1u) | (((b >> 20) & 1u) << 16);
+  w[1] = __popc((b >> 16) & 3u) | (__popc((b >> 18) & 3u) << 16);
+  unsigned x = b & 0xFFFFu;
+  x = (x & 0x5555u) + ((x >> 1) & 0x5555u);
+  x = (x & 0x3333u) + ((x >> 2) & 0x3333u);  // nibble q: the count of level-1 row q
+  w[2] = (x & 0xFu) | (((x >> 4) & 0xFu) << 16);
+  w[3] = ((x >> 8) & 0xFu) | (((x >> 12) & 0xFu) << 16);
 }
 __host__ __device__ __forceinline__ int ml_rows(int k) { return k == 1 ? 4 : k == 2 ? 2 : 1; }
-
-// The eight rows of a segment (list k, row q): 0 LLL, 1 level 3, 2-3 level 2, 4-7 level 1.
-// Each thread's count of layer-z blocks in every row, packed as 16-bit fields: lo holds rows
-// 0-3, hi rows 4-7 (a row of a segment has at most 1024 blocks, so no field overflows even
-// after the CTA-wide sums).
-__device__ __forceinline__ void ml_packed_counts(const MlMasks& m, int z, unsigned long long& lo,
-                                                 unsigned long long& hi) {
-  const unsigned long long c0 = (m.lll >> z) & 1ull, c1 = (m.m3 >> z) & 1ull;
-  const unsigned long long c2 = ((m.m2[0] >> z) & 1ull) + ((m.m2[1] >> z) & 1ull);
-  const unsigned long long c3 = ((m.m2[2] >> z) & 1ull) + ((m.m2[3] >> z) & 1ull);
-  lo = c0 | (c1 << 16) | (c2 << 32) | (c3 << 48);
-  hi = 0ull;
-#pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    const unsigned long long c = ((m.m1[4 * q] >> z) & 1ull) + ((m.m1[4 * q + 1] >> z) & 1ull) +
-                                 ((m.m1[4 * q + 2] >> z) & 1ull) + ((m.m1[4 * q + 3] >> z) & 1ull);
-    hi |= c << (16 * q);
-  }
-}
-// Row r of the eight (see ml_packed_counts) -> (list k, row q within the segment).
+// Row r of the eight -> (list k, row q within the segment).
 __host__ __device__ __forceinline__ int ml_row_list(int r) { return r == 0 ? 0 : r == 1 ? 3 : r < 4 ? 2 : 1; }
 __host__ __device__ __forceinline__ int ml_row_q(int r) { return r < 2 ? 0 : r < 4 ? r - 2 : r - 4; }
 
-// Exclusive prefix (and CTA total) of two packed 64-bit values over the CTA.
-__device__ __forceinline__ void ml_cta_exclusive2(unsigned long long& a, unsigned long long& b,
-                                                  unsigned long long* s_w, unsigned long long& ta,
-                                                  unsigned long long& tb) {
-  constexpr int NW = SEL_ML_SEG / 32;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  unsigned long long ia = a, ib = b;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const unsigned long long xa = __shfl_up_sync(0xffffffffu, ia, o), xb = __shfl_up_sync(0xffffffffu, ib, o);
-    if (lane >= o) ia += xa, ib += xb;
-  }
-  __syncthreads();  // s_w of the previous call has been read
-  if (lane == 31) s_w[2 * warp] = ia, s_w[2 * warp + 1] = ib;
-  __syncthreads();
-  unsigned long long pa = 0ull, pb = 0ull;
-  ta = tb = 0ull;
-#pragma unroll
-  for (int w = 0; w < NW; ++w) {
-    const unsigned long long wa = s_w[2 * w], wb = s_w[2 * w + 1];
-    if (w < warp) pa += wa, pb += wb;
-    ta += wa, tb += wb;
-  }
-  a = pa + ia - a;
-  b = pb + ib - b;
+__device__ __forceinline__ unsigned long long ml_warp_or(unsigned long long v) {
+  return ((unsigned long long)__reduce_or_sync(0xffffffffu, (unsigned)(v >> 32)) << 32) |
+         __reduce_or_sync(0xffffffffu, (unsigned)v);
 }
 
-// OR of a 64-bit mask over the CTA (s_or: 2 x 32-bit words per warp, all threads call).
-__device__ __forceinline__ unsigned long long ml_cta_or(unsigned long long v, unsigned* s_or) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const unsigned lo = __reduce_or_sync(0xffffffffu, (unsigned)v), hi = __reduce_or_sync(0xffffffffu, (unsigned)(v >> 32));
-  __syncthreads();
-  if (lane == 0) {
-    s_or[2 * warp] = lo;
-    s_or[2 * warp + 1] = hi;
-  }
-  __syncthreads();
-  unsigned a = 0, b = 0;
-#pragma unroll
-  for (int w = 0; w < SEL_ML_SEG / 32; ++w) a |= s_or[2 * w], b |= s_or[2 * w + 1];
-  return ((unsigned long long)b << 32) | a;
-}
-
-// Pass 1: per (list, layer, segment row) counts.  CTA = (row of 8x8 blocks, segment).
+// Pass 1: the blocks' records and the per (list, layer, segment row) counts.  CTA = (row of
+// 8x8 blocks, segment).
 __global__ void __launch_bounds__(SEL_ML_SEG) k_select_ml_count(const uint8_t* __restrict__ sal,
                                                                 const uint8_t* __restrict__ L, int H, int W, int Z,
-                                                                const SelTasks T, int* __restrict__ chunk_cnt) {
-  __shared__ unsigned s_or[2 * (SEL_ML_SEG / 32)];
-  __shared__ unsigned long long s_w[2 * (SEL_ML_SEG / 32)];
-  __shared__ int s_cnt[8][CGH_MAX_LAYERS];
+                                                                const SelTasks T, int* __restrict__ chunk_cnt,
+                                                                uint2* __restrict__ rec) {
+  __shared__ unsigned s_cnt[CGH_MAX_LAYERS][4];
   pdl_wait();
   pdl_trigger();
   const int nseg = (W >> 3) / SEL_ML_SEG, R = blockIdx.x / nseg, sg = blockIdx.x - R * nseg;
-  const int bx3 = sg * SEL_ML_SEG + threadIdx.x;
-  MlMasks m;
-  ml_masks(sal, L, W, R, bx3, Z, T.t[3].threshold, T.t[2].threshold, T.t[1].threshold, m);
+  const int bx3 = sg * SEL_ML_SEG + threadIdx.x, lane = threadIdx.x & 31;
+  uint2 lv[8], sv[8];
+#pragma unroll
+  for (int r = 0; r < 8; ++r) {
+    const size_t o = (size_t)(8 * R + r) * W + 8 * bx3;
+    lv[r] = *reinterpret_cast<const uint2*>(L + o);
+    sv[r] = *reinterpret_cast<const uint2*>(sal + o);
+  }
   if (blockIdx.x == 0 && threadIdx.x < 4) T.t[threadIdx.x].count[1] = 0;  // the scan's CTA counters
-  for (int e = threadIdx.x; e < 8 * Z; e += blockDim.x) s_cnt[e / Z][e % Z] = 0;
-  unsigned long long all = m.lll | m.m3;
+  for (int e = threadIdx.x; e < 4 * Z; e += blockDim.x) (&s_cnt[0][0])[e] = 0u;
+  // threshold tests; a block of one saliency value (common) takes them directly
+  const int t1 = T.t[1].threshold, t2 = T.t[2].threshold, t3 = T.t[3].threshold;
+  const unsigned s0 = 0x01010101u * (sv[0].x & 0xFFu);
+  unsigned ds = 0u;
 #pragma unroll
-  for (int q = 0; q < 4; ++q) all |= m.m2[q];
-#pragma unroll
-  for (int q = 0; q < 16; ++q) all |= m.m1[q];
-  unsigned long long u = ml_cta_or(all, s_or);  // its barriers also order the clear above
+  for (int r = 0; r < 8; ++r) ds |= (sv[r].x ^ s0) | (sv[r].y ^ s0);
+  unsigned tests;
+  if (!ds) {
+    const int s = (int)(s0 & 0xFFu);
+    tests = (t1 < 0 || s > t1 ? 0xFFFFu : 0u) | (t2 < 0 || s > t2 ? 0xF0000u : 0u) | (t3 < 0 || s > t3 ? 0x100000u : 0u);
+  } else {
+    tests = ml_tests(sv, ml_threshold(t1), ml_threshold(t2), ml_threshold(t3));
+  }
+  const uint2 r = ml_record(lv, Z, tests);
+  rec[(size_t)R * (W >> 3) + bx3] = r;
+  const unsigned long long lmask = (r.y & ML_MULTI) ? ml_layer_mask(lv, Z) : ml_rec_layers(r);
+  __syncthreads();  // s_cnt cleared
+  unsigned long long u = ml_warp_or(lmask);
   while (u) {
     const int z = __ffsll((long long)u) - 1;
     u &= u - 1ull;
-    unsigned long long lo, hi, tlo, thi;
-    ml_packed_counts(m, z, lo, hi);
-    ml_cta_exclusive2(lo, hi, s_w, tlo, thi);
-    if (threadIdx.x < 8) {
-      const unsigned long long t = threadIdx.x < 4 ? tlo : thi;
-      s_cnt[threadIdx.x][z] = (int)((t >> (16 * (threadIdx.x & 3))) & 0xFFFFull);
-    }
+    unsigned w[4];
+    ml_pack(ml_bits_of(r, lv, lmask, z), w);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) w[j] = __reduce_add_sync(0xffffffffu, w[j]);
+    if (lane == 0)
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        if (w[j]) atomicAdd(&s_cnt[z][j], w[j]);
   }
   __syncthreads();
   for (int e = threadIdx.x; e < 8 * Z; e += blockDim.x) {
-    const int r = e / Z, z = e - r * Z, k = ml_row_list(r);
+    const int z = e >> 3, r8 = e & 7, k = ml_row_list(r8);
     const SelTask& tk = T.t[k];
-    const int row = R * ml_rows(k) + ml_row_q(r);
-    chunk_cnt[tk.cnt_off + z * tk.nchunks + row * nseg + sg] = s_cnt[r][z];
+    const int row = R * ml_rows(k) + ml_row_q(r8);
+    chunk_cnt[tk.cnt_off + z * tk.nchunks + row * nseg + sg] = (int)((s_cnt[z][r8 >> 1] >> (16 * (r8 & 1))) & 0xFFFFu);
   }
 }
 
-// Pass 3: ordered scatter of all four lists (FLAGS: also the tensor-core flags).
+// Entries of one block in one layer z (bits b, record layout) from the first positions of the
+// warp's rows (pos0[r8]) and the lane's exclusive counts within the warp (bytes of e[0] for
+// rows 0-3, e[1] for rows 4-7).  FLAGS: also the tensor-core flags.
 template <bool FLAGS>
-__global__ void __launch_bounds__(SEL_ML_SEG) k_select_ml_scatter(const uint8_t* __restrict__ sal,
-                                                                  const uint8_t* __restrict__ L, int H, int W, int Z,
+__device__ __forceinline__ void ml_write(unsigned b, int z, const unsigned (&e)[2], const int* pos0, int R, int bx3,
+                                         int H, int W, const SelTasks& T, const TcFlags& fl) {
+#pragma unroll
+  for (int r8 = 0; r8 < 8; ++r8) {
+    const int k = ml_row_list(r8), q = ml_row_q(r8);
+    const int cols = k == 1 ? 4 : k == 2 ? 2 : 1;
+    const int sh = k == 0 ? 21 : k == 3 ? 20 : k == 2 ? 16 + 2 * q : 4 * q;
+    const int bits = (int)((b >> sh) & ((1u << cols) - 1u));
+    if (!bits) continue;
+    const SelTask& tk = T.t[k];
+    int pos = pos0[r8] + (int)((e[r8 >> 2] >> (8 * (r8 & 3))) & 0xFFu);
+    const int by = R * ml_rows(k) + q, v0 = (z << 24) | (by << 12) | (bx3 * cols);
+    if (!FLAGS && pos + __popc(bits) <= tk.capacity) {  // the whole run fits
+#pragma unroll
+      for (int cc = 0; cc < cols; ++cc)
+        if ((bits >> cc) & 1) tk.list[pos++] = v0 + cc;
+      continue;
+    }
+    const int level = tk.level, hl = H >> level, wl = W >> level;
+    for (int cc = 0; cc < cols; ++cc) {
+      if (!((bits >> cc) & 1)) continue;
+      const int bx = bx3 * cols + cc;
+      if (pos < tk.capacity) {
+        tk.list[pos] = v0 + cc;
+        if (FLAGS) {
+          if (k == 0) {
+            fl.occ3[((size_t)z * hl + by) * wl + bx] = 1;
+            fl.rowband[(size_t)z * hl + by] = 1;
+            fl.colband[(size_t)z * wl + bx] = 1;
+          } else {
+            uint8_t* sel = level == 1 ? fl.sel[1] : level == 2 ? fl.sel[2] : fl.sel[3];
+            sel[((size_t)z * hl + by) * wl + bx] = 1;
+            fl.rowband[(size_t)z * (H >> 3) + (by >> (3 - level))] = 1;
+            fl.colband[(size_t)z * (W >> 3) + (bx >> (3 - level))] = 1;
+          }
+        }
+      }
+      ++pos;
+    }
+  }
+}
+
+// Pass 3: ordered scatter of all four lists from the records (FLAGS: also the tensor-core
+// flags).  Per CTA: the warps' per-layer row totals, their prefix over the warps added to the
+// rows' first positions (one table per warp, layer and row), then per layer of the warp an
+// exclusive scan of the lanes' row counts (bytes: at most 4 a lane, 128 a warp).  A lane keeps
+// the scans of its record's one or two layers and writes its entries once per layer.
+template <bool FLAGS>
+__global__ void __launch_bounds__(SEL_ML_SEG) k_select_ml_scatter(const uint8_t* __restrict__ L, int H, int W, int Z,
                                                                   const SelTasks T, const int* __restrict__ chunk_cnt,
-                                                                  const int* __restrict__ chunk_off, TcFlags fl) {
-  __shared__ unsigned s_or[2 * (SEL_ML_SEG / 32)];
-  __shared__ unsigned long long s_w[2 * (SEL_ML_SEG / 32)];
-  __shared__ int s_base[8][CGH_MAX_LAYERS];
+                                                                  const int* __restrict__ chunk_off,
+                                                                  const uint2* __restrict__ rec, TcFlags fl) {
+  constexpr int NW = SEL_ML_SEG / 32;
+  __shared__ int s_base[CGH_MAX_LAYERS][8];
+  __shared__ unsigned s_wt[NW][CGH_MAX_LAYERS][4];
+  __shared__ int s_pos[NW][CGH_MAX_LAYERS][8];
   pdl_wait();
   pdl_trigger();
   const int nseg = (W >> 3) / SEL_ML_SEG, R = blockIdx.x / nseg, sg = blockIdx.x - R * nseg;
-  const int bx3 = sg * SEL_ML_SEG + threadIdx.x;
-  MlMasks m;
-  ml_masks(sal, L, W, R, bx3, Z, T.t[3].threshold, T.t[2].threshold, T.t[1].threshold, m);
+  const int bx3 = sg * SEL_ML_SEG + threadIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint2 r = rec[(size_t)R * (W >> 3) + bx3];
+  const bool multi = (r.y & ML_MULTI) != 0u;
+  uint2 lv[8];
+  unsigned long long lmask;
+  if (multi) {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) lv[q] = *reinterpret_cast<const uint2*>(L + (size_t)(8 * R + q) * W + 8 * bx3);
+    lmask = ml_layer_mask(lv, Z);
+  } else {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) lv[q] = make_uint2(0u, 0u);
+    lmask = ml_rec_layers(r);
+  }
   // every row's first position per layer: the prefix of its scan block plus its offset
   for (int e = threadIdx.x; e < 8 * Z; e += blockDim.x) {
-    const int r = e / Z, z = e - r * Z, k = ml_row_list(r);
+    const int z = e >> 3, r8 = e & 7, k = ml_row_list(r8);
     const SelTask& tk = T.t[k];
-    const int row = R * ml_rows(k) + ml_row_q(r);
+    const int row = R * ml_rows(k) + ml_row_q(r8);
     const int idx = z * tk.nchunks + row * nseg + sg;
-    s_base[r][z] = chunk_cnt[tk.cnt_off + (idx / SEL_SCAN_BLOCK) * SEL_SCAN_BLOCK] + chunk_off[tk.cnt_off + idx];
+    s_base[z][r8] = chunk_cnt[tk.cnt_off + (idx / SEL_SCAN_BLOCK) * SEL_SCAN_BLOCK] + chunk_off[tk.cnt_off + idx];
   }
-  unsigned long long all = m.lll | m.m3;
-#pragma unroll
-  for (int q = 0; q < 4; ++q) all |= m.m2[q];
-#pragma unroll
-  for (int q = 0; q < 16; ++q) all |= m.m1[q];
-  unsigned long long u = ml_cta_or(all, s_or);  // its barriers publish s_base
-  while (u) {
+  // the warp's totals per layer (zero for the layers it does not hold)
+  const unsigned long long uw = ml_warp_or(lmask);
+  for (unsigned long long u = uw; u; u &= u - 1ull) {
     const int z = __ffsll((long long)u) - 1;
-    u &= u - 1ull;
-    unsigned long long lo, hi, tlo, thi;
-    ml_packed_counts(m, z, lo, hi);
-    ml_cta_exclusive2(lo, hi, s_w, tlo, thi);
+    unsigned w[4];
+    ml_pack(ml_bits_of(r, lv, lmask, z), w);
 #pragma unroll
-    for (int r = 0; r < 8; ++r) {
-      const int k = ml_row_list(r), q = ml_row_q(r);
-      const SelTask& tk = T.t[k];
-      const int bits = ml_row_bits(m, k, q, z);
-      if (!bits) continue;
-      const int level = tk.level, hl = H >> level, wl = W >> level, cols = k == 1 ? 4 : k == 2 ? 2 : 1;
-      int pos = s_base[r][z] + (int)(((r < 4 ? lo : hi) >> (16 * (r & 3))) & 0xFFFFull);
-      const int by = R * ml_rows(k) + q;
-      for (int c = 0; c < cols; ++c) {
-        if (!((bits >> c) & 1)) continue;
-        const int bx = bx3 * cols + c;
-        if (pos < tk.capacity) {
-          tk.list[pos] = (z << 24) | (by << 12) | bx;
-          if (FLAGS) {
-            if (k == 0) {
-              fl.occ3[((size_t)z * hl + by) * wl + bx] = 1;
-              fl.rowband[(size_t)z * hl + by] = 1;
-              fl.colband[(size_t)z * wl + bx] = 1;
-            } else {
-              uint8_t* sel = level == 1 ? fl.sel[1] : level == 2 ? fl.sel[2] : fl.sel[3];
-              sel[((size_t)z * hl + by) * wl + bx] = 1;
-              fl.rowband[(size_t)z * (H >> 3) + (by >> (3 - level))] = 1;
-              fl.colband[(size_t)z * (W >> 3) + (bx >> (3 - level))] = 1;
-            }
-          }
-        }
-        ++pos;
-      }
+    for (int j = 0; j < 4; ++j) w[j] = __reduce_add_sync(0xffffffffu, w[j]);
+    if (lane == 0)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) s_wt[warp][z][j] = w[j];
+  }
+  for (int z = lane; z < Z; z += 32)
+    if (!((uw >> z) & 1ull))
+#pragma unroll
+      for (int j = 0; j < 4; ++j) s_wt[warp][z][j] = 0u;
+  __syncthreads();
+  // first position of every (warp, layer, row)
+  for (int e = threadIdx.x; e < 8 * Z; e += blockDim.x) {
+    const int z = e >> 3, r8 = e & 7;
+    int acc = s_base[z][r8];
+#pragma unroll
+    for (int v = 0; v < NW; ++v) {
+      s_pos[v][z][r8] = acc;
+      acc += (int)((s_wt[v][z][r8 >> 1] >> (16 * (r8 & 1))) & 0xFFFFu);
     }
+  }
+  __syncthreads();
+  const int za = (int)ml_layer_of(r.x), zb = (int)ml_layer_of(r.y);
+  unsigned ea[2] = {0u, 0u}, eb[2] = {0u, 0u};
+  for (unsigned long long u = uw; u; u &= u - 1ull) {
+    const int z = __ffsll((long long)u) - 1;
+    const unsigned b = ml_bits_of(r, lv, lmask, z);
+    // the lane's row counts as bytes, rows 0-3 and 4-7, and the warp's inclusive scan
+    unsigned nb = b & 0xFFFFu;
+    nb = (nb & 0x5555u) + ((nb >> 1) & 0x5555u);
+    nb = (nb & 0x3333u) + ((nb >> 2) & 0x3333u);  // nibble q: level-1 row q
+    nb = ((nb & 0xFF00u) << 8) | (nb & 0xFFu);
+    const unsigned c[2] = {((b >> 21) & 1u) | (((b >> 20) & 1u) << 8) | ((unsigned)__popc((b >> 16) & 3u) << 16) |
+                               ((unsigned)__popc((b >> 18) & 3u) << 24),
+                           (nb | (nb << 4)) & 0x0F0F0F0Fu};
+    unsigned x[2] = {c[0], c[1]};
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1)
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        const unsigned y = __shfl_up_sync(0xffffffffu, x[j], o);
+        if (lane >= o) x[j] += y;
+      }
+    const unsigned ex[2] = {x[0] - c[0], x[1] - c[1]};
+    if (multi) {
+      if (b) ml_write<FLAGS>(b, z, ex, s_pos[warp][z], R, bx3, H, W, T, fl);
+    } else {
+      if (z == za) ea[0] = ex[0], ea[1] = ex[1];
+      if (z == zb) eb[0] = ex[0], eb[1] = ex[1];
+    }
+  }
+  if (!multi) {
+    if ((r.x >> 21) & 1u) ml_write<FLAGS>(r.x & ML_BITS, za, ea, s_pos[warp][za], R, bx3, H, W, T, fl);
+    if ((r.y >> 21) & 1u) ml_write<FLAGS>(r.y & ML_BITS, zb, eb, s_pos[warp][zb], R, bx3, H, W, T, fl);
   }
 }
 
@@ -764,7 +931,8 @@ static bool select_ml_applies(int obj_h, int obj_w, const SelTasks& T) {
 }
 
 static cudaError_t launch_select_ml(int obj_h, int obj_w, int n_layers, const uint8_t* sal, const uint8_t* L,
-                                    SelTasks T, int* chunk_cnt, int* chunk_off, cudaStream_t st, const TcFlags* fl) {
+                                    SelTasks T, int* chunk_cnt, int* chunk_off, uint2* rec, cudaStream_t st,
+                                    const TcFlags* fl) {
   const int nseg = (obj_w >> 3) / SEL_ML_SEG, h3 = obj_h >> 3;
   int off = 0, nblk = 1;
   for (int k = 0; k < 4; ++k) {
@@ -778,15 +946,15 @@ static cudaError_t launch_select_ml(int obj_h, int obj_w, int n_layers, const ui
   }
   const int grid = h3 * nseg;
   cudaError_t e = launch_pdl(k_select_ml_count, dim3(grid), dim3(SEL_ML_SEG), 0, st, sal, L, obj_h, obj_w, n_layers,
-                             T, chunk_cnt);
+                             T, chunk_cnt, rec);
   if (e == cudaSuccess)
     e = launch_pdl(k_select_scan, dim3(nblk, T.n), dim3(1024), 0, st, chunk_cnt, chunk_off, n_layers, T);
   if (e == cudaSuccess) {
     const TcFlags f = fl ? *fl : TcFlags{};
-    e = fl ? launch_pdl(k_select_ml_scatter<true>, dim3(grid), dim3(SEL_ML_SEG), 0, st, sal, L, obj_h, obj_w,
-                        n_layers, T, (const int*)chunk_cnt, (const int*)chunk_off, f)
-           : launch_pdl(k_select_ml_scatter<false>, dim3(grid), dim3(SEL_ML_SEG), 0, st, sal, L, obj_h, obj_w,
-                        n_layers, T, (const int*)chunk_cnt, (const int*)chunk_off, f);
+    e = fl ? launch_pdl(k_select_ml_scatter<true>, dim3(grid), dim3(SEL_ML_SEG), 0, st, L, obj_h, obj_w, n_layers, T,
+                        (const int*)chunk_cnt, (const int*)chunk_off, (const uint2*)rec, f)
+           : launch_pdl(k_select_ml_scatter<false>, dim3(grid), dim3(SEL_ML_SEG), 0, st, L, obj_h, obj_w, n_layers, T,
+                        (const int*)chunk_cnt, (const int*)chunk_off, (const uint2*)rec, f);
   }
   return e != cudaSuccess ? e : cudaGetLastError();
 }
@@ -1014,9 +1182,11 @@ cudaError_t launch_select_tasks(int obj_h, int obj_w, int n_layers, const uint8_
     if (e == cudaSuccess && flags_done) *flags_done = fl != nullptr;
     return e != cudaSuccess ? e : cudaGetLastError();
   }
-  if (sal && select_ml_applies(obj_h, obj_w, T)) {
-    // the four lists of a large object: one read of the inputs per pass for all levels
-    const cudaError_t e = launch_select_ml(obj_h, obj_w, n_layers, sal, L, T, chunk_cnt, chunk_off, st, fl);
+  if (sal && coop && coop->ml_rec && select_ml_applies(obj_h, obj_w, T)) {
+    // the four lists of a large object: one read of the inputs for all levels, then the
+    // blocks' records
+    const cudaError_t e = launch_select_ml(obj_h, obj_w, n_layers, sal, L, T, chunk_cnt, chunk_off, coop->ml_rec,
+                                           st, fl);
     if (e == cudaSuccess && flags_done) *flags_done = fl != nullptr;
     return e;
   }

@@ -348,21 +348,44 @@ def _lists_vectorised(sal, layer, n_layers, thresholds):
     return out
 
 
-@pytest.mark.parametrize("n,n_layers", [(2048, 6), (4096, 3), (8192, 4)])
-def test_select_multilevel_large_objects(torch_cuda, n, n_layers):
+def _ml_inputs(rng, n, n_layers, pattern):
+    """Saliency and layer maps for the multi-level selection.  smooth: a noisy saliency
+    bump over sinusoidal layer bands with a few pixels on no layer (blocks of one, two and
+    rarely more layers); noise: every pixel's layer and saliency at random, 5% on no layer
+    (most blocks hold three or more layers); flat: saliency and layer constant on 8x8 and
+    16x16 tiles, saliency values at and just above each threshold (the one-value paths)."""
+    if pattern == "smooth":
+        yy, xx = np.mgrid[0:n, 0:n] / n
+        sal = np.clip(255 * np.exp(-((yy - 0.4) ** 2 + (xx - 0.6) ** 2) / 0.05) + rng.normal(0, 8, (n, n)),
+                      0, 255).astype(np.uint8)
+        layer = (np.floor((0.5 + 0.5 * np.sin(6 * yy + 3 * xx)) * n_layers).clip(0, n_layers - 1)).astype(np.uint8)
+        layer[rng.random((n, n)) < 0.002] = 255  # a few pixels on no layer
+    elif pattern == "noise":
+        sal = rng.integers(0, 256, (n, n), dtype=np.uint8)
+        layer = rng.integers(0, n_layers, (n, n), dtype=np.uint8)
+        layer[rng.random((n, n)) < 0.05] = 255
+    else:
+        t = list(scenes.THRESHOLDS_U8.values())
+        vals = np.array(sorted({0, 255} | set(t) | {x + 1 for x in t}), np.uint8)
+        sal = np.kron(rng.choice(vals, (n // 8, n // 8)), np.ones((8, 8), np.uint8))
+        tiles = rng.integers(0, n_layers + 1, (n // 16, n // 16)).astype(np.uint8)
+        tiles[tiles == n_layers] = 255  # tiles with no point
+        layer = np.kron(tiles, np.ones((16, 16), np.uint8))
+    return sal, layer
+
+
+@pytest.mark.parametrize("n,n_layers,pattern", [(2048, 6, "smooth"), (4096, 3, "smooth"), (8192, 4, "smooth"),
+                                                (2048, 5, "noise"), (2048, 7, "flat")])
+def test_select_multilevel_large_objects(torch_cuda, n, n_layers, pattern):
     """Objects whose width is a multiple of 2048 take the multi-level selection (one read
-    of the inputs per pass for all four lists): bit-exact against the oracle's selection
-    masks, with a truncating capacity on the level-1 list, and through the tensor-form step
-    (which marks the operand flags in the same pass) equal to the two-call path bit for bit
-    on a deterministic plan."""
+    of the inputs for all four lists, then per-block records): bit-exact against the
+    oracle's selection masks, with a truncating capacity on the level-1 list, and through
+    the tensor-form step (which marks the operand flags in the same pass) equal to the
+    two-call path bit for bit on a deterministic plan."""
     torch = torch_cuda
     from paper_2211_09938_gb300 import Plan
     rng = np.random.default_rng(n + n_layers)
-    yy, xx = np.mgrid[0:n, 0:n] / n
-    sal = np.clip(255 * np.exp(-((yy - 0.4) ** 2 + (xx - 0.6) ** 2) / 0.05) + rng.normal(0, 8, (n, n)),
-                  0, 255).astype(np.uint8)
-    layer = (np.floor((0.5 + 0.5 * np.sin(6 * yy + 3 * xx)) * n_layers).clip(0, n_layers - 1)).astype(np.uint8)
-    layer[rng.random((n, n)) < 0.002] = 255  # a few pixels on no layer
+    sal, layer = _ml_inputs(rng, n, n_layers, pattern)
     want = _lists_vectorised(sal, layer, n_layers, scenes.THRESHOLDS_U8)
     sc = dict(intensity=np.zeros((n, n), np.uint8), layer=layer, saliency=sal,
               z=np.linspace(0.08, 0.2, n_layers), holo=(n, n), pitch=8e-6, wavelength=532e-9)
