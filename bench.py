@@ -54,16 +54,32 @@ def whole_job_value(units_per_step_per_rank, steps, world_size, max_ms):
     return units_per_step_per_rank * steps * world_size / (max_ms / 1e3) / 1e9
 
 
+def kernel_source_hash(src_files, marker=None):
+    """First 16 hex digits of the SHA-256 of the kernel's sources: whole files, or with a
+    marker (text on the kernel's definition line) only the definition in the first file, from
+    that line to the first closing brace at column 0 after it (the other files whole)."""
+    import hashlib
+    h = hashlib.sha256()
+    for n, f in enumerate(src_files):
+        text = open(os.path.join(ROOT, f), "rb").read()
+        if marker and n == 0:
+            i = text.find(marker.encode())
+            if i < 0:
+                raise KeyError(f"{marker} not in {f}")
+            i = text.rfind(b"\n", 0, i) + 1
+            j = text.find(b"\n}\n", i)
+            text = text[i:] if j < 0 else text[i:j + 3]
+        h.update(text)
+    return h.hexdigest()[:16]
+
+
 def kernel_traffic(key):
     """DRAM bytes per launch of `key` from the committed ncu summary (profiles/traffic.json),
     or None when the kernel's sources changed since those counters were taken."""
-    import hashlib
     try:
         entry = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))[key]
-        h = hashlib.sha256()
-        for f in entry["src_files"]:
-            h.update(open(os.path.join(ROOT, f), "rb").read())
-        return entry["bytes"] if h.hexdigest()[:16] == entry["src_hash"] else None
+        ok = kernel_source_hash(entry["src_files"], entry.get("src_marker")) == entry["src_hash"]
+        return entry["bytes"] if ok else None
     except Exception:
         return None
 

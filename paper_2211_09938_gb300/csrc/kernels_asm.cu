@@ -44,6 +44,13 @@
 #define ASM_IC_TILE 16384
 #define ASM_SMALL_T 256
 #define ASM_SMALL_TILE 4096
+// The inverse-row kernel: 2048-element tiles on 128 threads up to a folded edge of 512 (eight
+// CTAs per SM overlap their load, transform and store phases: 41 -> 37 us at 512), 4096 from
+// 1024 (there the smaller tiles measured slower, 44 -> 48 us).
+template <int L>
+constexpr int asm_ir_tile() {
+  return L >= 1024 ? (L > 4096 ? L : 4096) : 2048;
+}
 #define ASM_MINB(T) (1024 / (T))
 
 struct AsmLayer {
@@ -319,8 +326,9 @@ int asm_init_attributes() {
       keep(cudaFuncSetAttribute(k_asm_fwd_rows<Lc, BS, ASM_SMALL_T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 sms));
       keep(cudaFuncSetAttribute(k_asm_fwd_cols<Lc, BB, ASM_BIG_T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smb));
-      keep(cudaFuncSetAttribute(k_asm_inv_rows<Lc, BS, ASM_SMALL_T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)rows_smem<Lc, ASM_SMALL_TILE>()));
+      constexpr int IRT = asm_ir_tile<Lc>();
+      keep(cudaFuncSetAttribute(k_asm_inv_rows<Lc, IRT / Lc, IRT / 16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)rows_smem<Lc, IRT>()));
       constexpr int BI = ASM_IC_TILE / Lc, smi = (int)tile_smem<Lc, ASM_IC_TILE>();
       for (int s = 1; s <= 8; s <<= 1)
         with_stride(s, [&](auto sc) {
@@ -460,7 +468,6 @@ extern "C" int cgh_reconstruct_asm(const cgh_plan* p, const float* holo, float* 
   prof_mark(p, CGH_PROF_ASM_INV, 0, st);
   with_len(L, [&](auto lc) {
     constexpr int Lc = decltype(lc)::value;
-    constexpr int BS = ASM_SMALL_TILE / Lc;
     with_stride(s, [&](auto sc) {
       constexpr int Sc = decltype(sc)::value;
       if constexpr (Lc * Sc <= 4096) {
@@ -473,8 +480,9 @@ extern "C" int cgh_reconstruct_asm(const cgh_plan* p, const float* holo, float* 
           k_asm_inv_cols<Lc, BI, ASM_IC_T, Sc, false><<<grid, ASM_IC_T, smi, st>>>(a->X, No, a->layers, a->Y, a->tw);
       }
     });
-    k_asm_inv_rows<Lc, BS, ASM_SMALL_T><<<dim3((No + BS - 1) / BS, Z), ASM_SMALL_T, rows_smem<Lc, ASM_SMALL_TILE>(),
-                                          st>>>(a->Y, No, Z, a->layers, layer_idx, (float2*)fields, amplitude, a->tw);
+    constexpr int IRT = asm_ir_tile<Lc>(), BR = IRT / Lc;
+    k_asm_inv_rows<Lc, BR, IRT / 16><<<dim3((No + BR - 1) / BR, Z), IRT / 16, rows_smem<Lc, IRT>(), st>>>(
+        a->Y, No, Z, a->layers, layer_idx, (float2*)fields, amplitude, a->tw);
   });
   prof_mark(p, CGH_PROF_ASM_INV, 1, st);
   return cgh_cuda_check(cudaGetLastError(), "cgh_reconstruct_asm: inverse transforms");

@@ -83,19 +83,33 @@ cudaError_t launch_build_tables(const cgh_plan* p, cudaStream_t st) {
 // (A2) three-level integer Haar DWT of every layer plane (Eq. 2, Section 2 step 1).
 // One thread per (8x8 block, layer).  The 2x2 cell [a b; c d] gives
 // S = a+b+c+d, X = a-b+c-d, Y = a+b-c-d, D = a-b-c+d; Mallat output.
-__device__ __forceinline__ void haar3_block(const uint8_t* __restrict__ I, const uint8_t* __restrict__ L,
-                                            int32_t* __restrict__ coef, int H, int W, int z, int bx, int by) {
-  int a[8][8];
+// The block's rows of intensity (iv) and layer index (lv).
+__device__ __forceinline__ void haar3_load(const uint8_t* __restrict__ I, const uint8_t* __restrict__ L, int W,
+                                           int bx, int by, uint2 (&iv)[8], uint2 (&lv)[8]) {
 #pragma unroll
   for (int r = 0; r < 8; ++r) {
     const size_t o = (size_t)(8 * by + r) * W + 8 * bx;
-    const uint2 iv = *reinterpret_cast<const uint2*>(I + o);
-    const uint2 lv = *reinterpret_cast<const uint2*>(L + o);
+    iv[r] = *reinterpret_cast<const uint2*>(I + o);
+    lv[r] = *reinterpret_cast<const uint2*>(L + o);
+  }
+}
+
+// The three levels of layer z of one 8x8 block, from its loaded rows.
+__device__ __forceinline__ void haar3_layer(const uint2 (&iv)[8], const uint2 (&lv)[8], int32_t* __restrict__ coef,
+                                            int H, int W, int z, int bx, int by) {
+  // the layer's intensities: bytes of other layers cleared word by word (carry-free test of
+  // byte == z on bit 7 of each byte, widened to a byte mask), then unpacked
+  const unsigned zz = 0x01010101u * (unsigned)z;
+  int a[8][8];
 #pragma unroll
-    for (int c = 0; c < 8; ++c) {
-      const unsigned iw = c < 4 ? iv.x : iv.y, lw = c < 4 ? lv.x : lv.y;
-      const int sh = 8 * (c & 3);
-      a[r][c] = (((lw >> sh) & 0xFF) == (unsigned)z) ? (int)((iw >> sh) & 0xFF) : 0;
+  for (int r = 0; r < 8; ++r) {
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const unsigned x = (h ? lv[r].y : lv[r].x) ^ zz;
+      const unsigned eq = ~(((x & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | x) & 0x80808080u;
+      const unsigned w = (h ? iv[r].y : iv[r].x) & ((eq >> 7) * 0xFFu);
+#pragma unroll
+      for (int c = 0; c < 4; ++c) a[r][4 * h + c] = (int)((w >> (8 * c)) & 0xFFu);
     }
   }
   int s1[4][4], x1[4][4], y1[4][4], d1[4][4];
@@ -147,13 +161,24 @@ __device__ __forceinline__ void haar3_block(const uint8_t* __restrict__ I, const
   P[(size_t)(h3 + by) * W + w3 + bx] = A - B - C + D;
 }
 
+__device__ __forceinline__ void haar3_block(const uint8_t* __restrict__ I, const uint8_t* __restrict__ L,
+                                            int32_t* __restrict__ coef, int H, int W, int z, int bx, int by) {
+  uint2 iv[8], lv[8];
+  haar3_load(I, L, W, bx, by, iv, lv);
+  haar3_layer(iv, lv, coef, H, W, z, bx, by);
+}
+
+// One layer per CTA, the layer fastest in the grid (blockIdx.x): the CTAs of all layers of a
+// tile run next to each other, so the tile's input rows come from HBM once and from L2 for the
+// other layers (with the layer slowest, an 8192^2 object with 4 layers re-read its 128 MB of
+// inputs from HBM for every layer: 537 MB read for 1 GB of coefficients written).
 __global__ void __launch_bounds__(128) k_haar3(const uint8_t* __restrict__ I,
                                                const uint8_t* __restrict__ L,
                                                int32_t* __restrict__ coef, int H, int W) {
-  const int bx = blockIdx.x * blockDim.x + threadIdx.x;
-  const int by = blockIdx.y * blockDim.y + threadIdx.y;
+  const int bx = blockIdx.y * blockDim.x + threadIdx.x;
+  const int by = blockIdx.z * blockDim.y + threadIdx.y;
   if (bx >= (W >> 3) || by >= (H >> 3)) return;
-  haar3_block(I, L, coef, H, W, blockIdx.z, bx, by);
+  haar3_block(I, L, coef, H, W, blockIdx.x, bx, by);
 }
 
 // Batched DWT: grid.z walks the (scene, layer) items; x and y cover the largest scene.
@@ -176,7 +201,7 @@ cudaError_t launch_haar_batch(const HaarItem* d_items, int n_items, int max_h, i
 cudaError_t launch_haar(const cgh_plan* p, const uint8_t* I, const uint8_t* L, int32_t* coef,
                         cudaStream_t st) {
   dim3 block(32, 4);
-  dim3 grid(((p->obj_w >> 3) + 31) / 32, ((p->obj_h >> 3) + 3) / 4, p->n_layers);
+  dim3 grid(p->n_layers, ((p->obj_w >> 3) + 31) / 32, ((p->obj_h >> 3) + 3) / 4);
   k_haar3<<<grid, block, 0, st>>>(I, L, coef, p->obj_h, p->obj_w);
   return cudaGetLastError();
 }
@@ -660,13 +685,36 @@ __device__ __forceinline__ uint2 ml_record(const uint2 (&lv)[8], int Z, unsigned
       }
     if (za == 0xFFu) return make_uint2(0u, 0u);
   }
-  // pixels of layer za, and points of other layers
+  // pixels of layer za, and the first pixel of another value
   uint2 ea[8];
-  unsigned rest = 0u, zb = 0xFFu;
+  unsigned zb = 0xFFu;
   const unsigned zza = 0x01010101u * za;
 #pragma unroll
   for (int r = 0; r < 8; ++r) {
     ea[r] = make_uint2(ml_zero_bytes(lv[r].x ^ zza), ml_zero_bytes(lv[r].y ^ zza));
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const unsigned w = h ? lv[r].y : lv[r].x, o = ~(h ? ea[r].y : ea[r].x) & ML_B7;
+      if (zb == 0xFFu && o) zb = (w >> (__ffs(o) - 8)) & 0xFFu;
+    }
+  }
+  const unsigned wa = (za << 22) | ml_layer_bits(ml_gather(ea), tests);
+  if ((int)zb < Z) {  // the common case: two layers and a point in every pixel
+    const unsigned zzb = 0x01010101u * zb;
+    uint2 eb[8];
+    unsigned other = 0u;
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      eb[r] = make_uint2(ml_zero_bytes(lv[r].x ^ zzb), ml_zero_bytes(lv[r].y ^ zzb));
+      other |= ~(ea[r].x | eb[r].x) | ~(ea[r].y | eb[r].y);
+    }
+    if (!(other & ML_B7)) return make_uint2(wa, (zb << 22) | ml_layer_bits(ml_gather(eb), tests));
+  }
+  // otherwise: points of layers other than za (pixels without a point left out)
+  unsigned rest = 0u;
+  zb = 0xFFu;
+#pragma unroll
+  for (int r = 0; r < 8; ++r)
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       const unsigned w = h ? lv[r].y : lv[r].x;
@@ -674,8 +722,6 @@ __device__ __forceinline__ uint2 ml_record(const uint2 (&lv)[8], int Z, unsigned
       if (zb == 0xFFu && o) zb = (w >> (__ffs(o) - 8)) & 0xFFu;
       rest |= o;
     }
-  }
-  const unsigned wa = (za << 22) | ml_layer_bits(ml_gather(ea), tests);
   if (!rest) return make_uint2(wa, 0u);
   // a second layer: the block is described when no point lies in a third
   const unsigned zzb = 0x01010101u * zb;
@@ -714,7 +760,7 @@ __device__ __forceinline__ unsigned long long ml_warp_or(unsigned long long v) {
 
 // Pass 1: the blocks' records and the per (list, layer, segment row) counts.  CTA = (row of
 // 8x8 blocks, segment).
-__global__ void __launch_bounds__(SEL_ML_SEG) k_select_ml_count(const uint8_t* __restrict__ sal,
+__global__ void __launch_bounds__(SEL_ML_SEG, 4) k_select_ml_count(const uint8_t* __restrict__ sal,
                                                                 const uint8_t* __restrict__ L, int H, int W, int Z,
                                                                 const SelTasks T, int* __restrict__ chunk_cnt,
                                                                 uint2* __restrict__ rec) {

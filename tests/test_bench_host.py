@@ -30,10 +30,34 @@ def test_traffic_follows_the_sources(tmp_path, monkeypatch):
     assert bench.kernel_traffic("no such kernel") is None
 
 
+def test_traffic_of_one_kernel_follows_its_definition_only(tmp_path, monkeypatch):
+    """With a marker the hash covers the kernel's definition (its line to the next closing
+    brace at column 0): edits elsewhere in the file keep the figure, edits inside drop it."""
+    import hashlib
+    root = tmp_path
+    os.makedirs(root / "profiles")
+    src = root / "k.cu"
+    before = "__global__ void k_other() {\n  x = 1;\n}\n"
+    body = "__global__ void k_mine(int* p) {\n  p[0] = 2;\n}\n"
+    after = "int tail() {\n  return 3;\n}\n"
+    src.write_text(before + body + after)
+    entry = {"k_mine": {"bytes": 77.0, "source": "profiles/k.md", "src_files": ["k.cu"], "src_marker": "k_mine(",
+                        "src_hash": hashlib.sha256(body.encode()).hexdigest()[:16]}}
+    (root / "profiles" / "traffic.json").write_text(json.dumps(entry))
+    monkeypatch.setattr(bench, "ROOT", str(root))
+    assert bench.kernel_source_hash(["k.cu"], "k_mine(") == entry["k_mine"]["src_hash"]
+    assert bench.kernel_traffic("k_mine") == 77.0
+    src.write_text(before.replace("1", "5") + body + after + "// more\n")
+    assert bench.kernel_traffic("k_mine") == 77.0
+    src.write_text(before + body.replace("2", "4") + after)
+    assert bench.kernel_traffic("k_mine") is None
+
+
 def test_committed_traffic_entries_are_well_formed():
     entry = json.load(open(os.path.join(bench.ROOT, "profiles", "traffic.json")))
     for key, e in entry.items():
         assert e["bytes"] > 0 and len(e["src_hash"]) == 16, key
+        bench.kernel_source_hash(e["src_files"], e.get("src_marker"))  # the marker is still in the sources
         assert os.path.exists(os.path.join(bench.ROOT, e["source"])), key
         for f in e["src_files"]:
             assert os.path.exists(os.path.join(bench.ROOT, f)), (key, f)
