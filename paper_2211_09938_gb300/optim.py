@@ -92,18 +92,29 @@ class PhaseOptimiser:
     reconstructed composite amplitude matches its target (weights per pixel, e.g. 4
     inside the saliency mask and 1 outside).  state_dict()/load_state_dict() (with
     torch.save/torch.load) checkpoint and resume the run; with a plan created with
-    Plan.DETERMINISTIC a resumed run reproduces an uninterrupted one bit for bit."""
+    Plan.DETERMINISTIC a resumed run reproduces an uninterrupted one bit for bit.
 
-    def __init__(self, plan, layer, targets, weights, phase0, lr=0.05, checkpoint=True, concurrent=False):
+    graph=True captures one whole step (the B reconstructions, the loss, the backward through
+    libcgh's kernels and the fused Adam update) in a CUDA graph on the first step and replays it
+    from then on: the ~130 launches of a step then cost one host call, where the eager loop is
+    bound by the host's launch rate."""
+
+    def __init__(self, plan, layer, targets, weights, phase0, lr=0.05, checkpoint=True, concurrent=False,
+                 graph=False):
         self.plan = plan
         self.layer = layer
         self.targets = targets
         self.weights = weights
         self.checkpoint = checkpoint
         self.phase = phase0.detach().clone().float().contiguous().requires_grad_(True)
-        self.opt = torch.optim.Adam([self.phase], lr=lr)
+        self.use_graph = bool(graph) and not concurrent
+        self.opt = torch.optim.Adam([self.phase], lr=lr, fused=True, capturable=self.use_graph)
+        self.graph = None
         self.step_count = 0
         nb = self.phase.shape[0]
+        # the loss's constants in float64, cast once
+        self._t64 = [targets[b].double() for b in range(nb)]
+        self._w64 = weights.double()
         # concurrent: the holograms of the batch run on their own streams, each with its own
         # plan (plan scratch is per plan), so that their GEMMs and small kernels overlap on the
         # GPU; autograd runs every hologram's backward on the stream of its forward.  Measured
@@ -121,7 +132,7 @@ class PhaseOptimiser:
             total = 0.0
             for b in range(nb):
                 amp = reconstruct_amplitude(self.phase[b], self.plans[b], self.layer, self.checkpoint)
-                total = total + weighted_loss(amp, self.targets[b], self.weights, self.kappa[b])
+                total = total + weighted_loss(amp, self._t64[b], self._w64, self.kappa[b])
             return total
         cur = torch.cuda.current_stream()
         parts = []
@@ -130,18 +141,56 @@ class PhaseOptimiser:
             s.wait_stream(cur)
             with torch.cuda.stream(s):
                 amp = reconstruct_amplitude(self.phase[b], self.plans[b], self.layer, self.checkpoint)
-                parts.append(weighted_loss(amp, self.targets[b], self.weights, self.kappa[b]))
+                parts.append(weighted_loss(amp, self._t64[b], self._w64, self.kappa[b]))
         for s in self.streams:
             cur.wait_stream(s)
         return torch.stack(parts).sum()
 
-    def step(self):
+    def _capture(self):
+        """Warm up on a side stream (output buffers, the plan's lazily built operands, Adam's
+        state), capture one step, then put the phase and Adam's state back as they were, so
+        that the first replay is the next step."""
+        phase0 = self.phase.detach().clone()
+        state0 = [{k: v.clone() for k, v in st.items() if torch.is_tensor(v)} for st in self.opt.state.values()]
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            for _ in range(2):
+                self.opt.zero_grad(set_to_none=True)
+                self.loss().backward()
+                self.opt.step()
+        torch.cuda.current_stream().wait_stream(side)
         self.opt.zero_grad(set_to_none=True)
-        L = self.loss()
-        L.backward()
-        self.opt.step()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            self._static_loss = self.loss()
+            self._static_loss.backward()
+            self.opt.step()
+        with torch.no_grad():
+            self.phase.copy_(phase0)
+            for st, old in zip(self.opt.state.values(), state0 if state0 else [None] * len(self.opt.state)):
+                for k, v in st.items():
+                    if torch.is_tensor(v):
+                        v.copy_(old[k]) if old else v.zero_()
+        self.graph = g
+
+    def step(self, sync=True):
+        """One Adam step; returns the loss as a float, or with sync=False as a device tensor
+        (no host synchronisation, so that the host queues the next steps while the GPU runs)."""
+        if self.use_graph:
+            if self.graph is None:
+                self._capture()
+            self.graph.replay()
+            L = self._static_loss.detach()
+            L = L if sync else L.clone()
+        else:
+            self.opt.zero_grad(set_to_none=True)
+            L = self.loss()
+            L.backward()
+            self.opt.step()
+            L = L.detach()
         self.step_count += 1
-        return float(L.detach())
+        return float(L) if sync else L
 
     def state_dict(self):
         return {"phase": self.phase.detach().clone(), "adam": self.opt.state_dict(),
@@ -153,3 +202,4 @@ class PhaseOptimiser:
         self.opt.load_state_dict(st["adam"])
         self.step_count = int(st["step"])
         self.kappa = list(st["kappa"])
+        self.graph = None  # the captured step holds the old state tensors: capture again

@@ -251,6 +251,15 @@ def test_phase_optimisation_decreases_and_resumes_bit_identically(torch_cuda, tm
     for _ in range(6):
         d.step()
     assert torch.equal(d.phase.detach(), a.phase.detach())
+    # one captured step replayed: the same run (the capture's warm-up steps are undone), to
+    # the rounding of the capturable Adam update
+    e = optim.PhaseOptimiser(plan, L, T, W, ph0, lr=0.05, graph=True)
+    lg = [e.step() for _ in range(6)]
+    assert e.step_count == 6
+    np.testing.assert_allclose(lg, losses, rtol=1e-5)
+    err = float((e.phase.detach() - a.phase.detach()).abs().max())
+    print(f"graph-captured optimiser: max phase difference after 6 steps {err:.2e}")
+    assert err <= 1e-4
 
 
 @pytest.mark.parametrize("name,make", [
