@@ -59,6 +59,7 @@ int cgh_plan_destroy(cgh_plan* p) {
   cudaFree(p->d_chunk_off);
   cudaFree(p->d_sel_bar);
   cudaFree(p->d_ml_rec);
+  cudaFree(p->d_ml_wt);
   free(p);
   return CGH_OK;
 }
@@ -185,9 +186,12 @@ int cgh_plan_create(cgh_plan** out, int obj_h, int obj_w, int holo_h, int holo_w
   PLAN_TRY(cudaMemset(p->d_status, 0, sizeof(int)), "cgh_plan_create: status clear");
   PLAN_TRY(cudaMalloc(&p->d_sel_bar, 2 * sizeof(unsigned)), "cgh_plan_create: selection barrier");
   PLAN_TRY(cudaMemset(p->d_sel_bar, 0, 2 * sizeof(unsigned)), "cgh_plan_create: selection barrier clear");
-  if (obj_h % 8 == 0 && (obj_w / 8) % 256 == 0)
+  if (obj_h % 8 == 0 && (obj_w / 8) % 256 == 0) {  // the multi-level selection's scratch
     PLAN_TRY(cudaMalloc(&p->d_ml_rec, (size_t)(obj_h / 8) * (obj_w / 8) * sizeof(uint2)),
              "cgh_plan_create: selection records");
+    PLAN_TRY(cudaMalloc(&p->d_ml_wt, (size_t)(obj_h / 8) * (obj_w / 8) / 256 * 8 * n_layers * sizeof(uint4)),
+             "cgh_plan_create: selection row totals");
+  }
   {
     int sms = 0;
     PLAN_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device), "cgh_plan_create: SM count");

@@ -49,6 +49,7 @@ struct cgh_plan {
   int max_chunks;
   unsigned* d_sel_bar;  // [0]: the fused selection's grid barrier; [1]: its self-test's
   uint2* d_ml_rec;      // multi-level selection: one record per 8x8 block (null below 2048-pixel rows)
+  uint4* d_ml_wt;       // multi-level selection: row totals per (CTA, warp, layer)
   int sel_coop_ctas;
 
   // Separable tensor-core path (allocated lazily by the first call that needs it).
@@ -138,12 +139,14 @@ struct SelTasks {
 // Selection scratch of a plan: the fused single-launch selection's grid-barrier word, its
 // status word and the largest grid the device holds at once (0: use the three-pass
 // selection); the multi-level selection's block records (two words per 8x8 block of the
-// object; null: the multi-level passes are not used).
+// object) and its per-warp row totals (eight warps x layers x four words per CTA of 256
+// blocks); null: the multi-level passes are not used.
 struct SelCoop {
   unsigned* bar;
   int* status;
   int max_ctas;
   uint2* ml_rec;
+  uint4* ml_wt;
 };
 
 // Kernel launchers (kernels_basic.cu).  All asynchronous on `st`.
@@ -169,7 +172,7 @@ int select_fused_ctas_per_sm();
 cudaError_t launch_grid_barrier_selftest(unsigned* bar, int* status, int* crossed, int ctas,
                                          unsigned long long limit_ns, int absent, cudaStream_t st);
 static inline SelCoop plan_sel_coop(const cgh_plan* p) {
-  return SelCoop{p->d_sel_bar, p->d_status, p->sel_coop_ctas, p->d_ml_rec};
+  return SelCoop{p->d_sel_bar, p->d_status, p->sel_coop_ctas, p->d_ml_rec, p->d_ml_wt};
 }
 cudaError_t basic_init_attributes();
 int tc_init_attributes();

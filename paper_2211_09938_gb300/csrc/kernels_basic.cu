@@ -763,7 +763,7 @@ __device__ __forceinline__ unsigned long long ml_warp_or(unsigned long long v) {
 __global__ void __launch_bounds__(SEL_ML_SEG, 4) k_select_ml_count(const uint8_t* __restrict__ sal,
                                                                 const uint8_t* __restrict__ L, int H, int W, int Z,
                                                                 const SelTasks T, int* __restrict__ chunk_cnt,
-                                                                uint2* __restrict__ rec) {
+                                                                uint2* __restrict__ rec, uint4* __restrict__ wt) {
   __shared__ unsigned s_cnt[CGH_MAX_LAYERS][4];
   pdl_wait();
   pdl_trigger();
@@ -795,19 +795,25 @@ __global__ void __launch_bounds__(SEL_ML_SEG, 4) k_select_ml_count(const uint8_t
   rec[(size_t)R * (W >> 3) + bx3] = r;
   const unsigned long long lmask = (r.y & ML_MULTI) ? ml_layer_mask(lv, Z) : ml_rec_layers(r);
   __syncthreads();  // s_cnt cleared
-  unsigned long long u = ml_warp_or(lmask);
-  while (u) {
+  // per layer of the warp: its row totals, kept for the scatter (zero for the other layers)
+  // and added into the CTA's table
+  const unsigned long long uw = ml_warp_or(lmask);
+  uint4* const wtw = wt + ((size_t)blockIdx.x * (SEL_ML_SEG / 32) + (threadIdx.x >> 5)) * Z;
+  for (unsigned long long u = uw; u; u &= u - 1ull) {
     const int z = __ffsll((long long)u) - 1;
-    u &= u - 1ull;
     unsigned w[4];
     ml_pack(ml_bits_of(r, lv, lmask, z), w);
 #pragma unroll
     for (int j = 0; j < 4; ++j) w[j] = __reduce_add_sync(0xffffffffu, w[j]);
-    if (lane == 0)
+    if (lane == 0) {
+      wtw[z] = make_uint4(w[0], w[1], w[2], w[3]);
 #pragma unroll
       for (int j = 0; j < 4; ++j)
         if (w[j]) atomicAdd(&s_cnt[z][j], w[j]);
+    }
   }
+  for (int z = lane; z < Z; z += 32)
+    if (!((uw >> z) & 1ull)) wtw[z] = make_uint4(0u, 0u, 0u, 0u);
   __syncthreads();
   for (int e = threadIdx.x; e < 8 * Z; e += blockDim.x) {
     const int z = e >> 3, r8 = e & 7, k = ml_row_list(r8);
@@ -872,10 +878,11 @@ template <bool FLAGS>
 __global__ void __launch_bounds__(SEL_ML_SEG) k_select_ml_scatter(const uint8_t* __restrict__ L, int H, int W, int Z,
                                                                   const SelTasks T, const int* __restrict__ chunk_cnt,
                                                                   const int* __restrict__ chunk_off,
-                                                                  const uint2* __restrict__ rec, TcFlags fl) {
+                                                                  const uint2* __restrict__ rec,
+                                                                  const uint4* __restrict__ wt, TcFlags fl) {
   constexpr int NW = SEL_ML_SEG / 32;
   __shared__ int s_base[CGH_MAX_LAYERS][8];
-  __shared__ unsigned s_wt[NW][CGH_MAX_LAYERS][4];
+  __shared__ uint4 s_wt[NW * CGH_MAX_LAYERS];  // the count pass's row totals, [warp][layer]
   __shared__ int s_pos[NW][CGH_MAX_LAYERS][8];
   pdl_wait();
   pdl_trigger();
@@ -902,22 +909,9 @@ __global__ void __launch_bounds__(SEL_ML_SEG) k_select_ml_scatter(const uint8_t*
     const int idx = z * tk.nchunks + row * nseg + sg;
     s_base[z][r8] = chunk_cnt[tk.cnt_off + (idx / SEL_SCAN_BLOCK) * SEL_SCAN_BLOCK] + chunk_off[tk.cnt_off + idx];
   }
-  // the warp's totals per layer (zero for the layers it does not hold)
+  // every warp's row totals per layer, as the count pass left them
+  for (int e = threadIdx.x; e < NW * Z; e += blockDim.x) s_wt[e] = wt[(size_t)blockIdx.x * NW * Z + e];
   const unsigned long long uw = ml_warp_or(lmask);
-  for (unsigned long long u = uw; u; u &= u - 1ull) {
-    const int z = __ffsll((long long)u) - 1;
-    unsigned w[4];
-    ml_pack(ml_bits_of(r, lv, lmask, z), w);
-#pragma unroll
-    for (int j = 0; j < 4; ++j) w[j] = __reduce_add_sync(0xffffffffu, w[j]);
-    if (lane == 0)
-#pragma unroll
-      for (int j = 0; j < 4; ++j) s_wt[warp][z][j] = w[j];
-  }
-  for (int z = lane; z < Z; z += 32)
-    if (!((uw >> z) & 1ull))
-#pragma unroll
-      for (int j = 0; j < 4; ++j) s_wt[warp][z][j] = 0u;
   __syncthreads();
   // first position of every (warp, layer, row)
   for (int e = threadIdx.x; e < 8 * Z; e += blockDim.x) {
@@ -926,7 +920,9 @@ __global__ void __launch_bounds__(SEL_ML_SEG) k_select_ml_scatter(const uint8_t*
 #pragma unroll
     for (int v = 0; v < NW; ++v) {
       s_pos[v][z][r8] = acc;
-      acc += (int)((s_wt[v][z][r8 >> 1] >> (16 * (r8 & 1))) & 0xFFFFu);
+      const uint4 t = s_wt[v * Z + z];
+      const unsigned wj = (r8 >> 1) == 0 ? t.x : (r8 >> 1) == 1 ? t.y : (r8 >> 1) == 2 ? t.z : t.w;
+      acc += (int)((wj >> (16 * (r8 & 1))) & 0xFFFFu);
     }
   }
   __syncthreads();
@@ -977,8 +973,8 @@ static bool select_ml_applies(int obj_h, int obj_w, const SelTasks& T) {
 }
 
 static cudaError_t launch_select_ml(int obj_h, int obj_w, int n_layers, const uint8_t* sal, const uint8_t* L,
-                                    SelTasks T, int* chunk_cnt, int* chunk_off, uint2* rec, cudaStream_t st,
-                                    const TcFlags* fl) {
+                                    SelTasks T, int* chunk_cnt, int* chunk_off, uint2* rec, uint4* wt,
+                                    cudaStream_t st, const TcFlags* fl) {
   const int nseg = (obj_w >> 3) / SEL_ML_SEG, h3 = obj_h >> 3;
   int off = 0, nblk = 1;
   for (int k = 0; k < 4; ++k) {
@@ -992,15 +988,15 @@ static cudaError_t launch_select_ml(int obj_h, int obj_w, int n_layers, const ui
   }
   const int grid = h3 * nseg;
   cudaError_t e = launch_pdl(k_select_ml_count, dim3(grid), dim3(SEL_ML_SEG), 0, st, sal, L, obj_h, obj_w, n_layers,
-                             T, chunk_cnt, rec);
+                             T, chunk_cnt, rec, wt);
   if (e == cudaSuccess)
     e = launch_pdl(k_select_scan, dim3(nblk, T.n), dim3(1024), 0, st, chunk_cnt, chunk_off, n_layers, T);
   if (e == cudaSuccess) {
     const TcFlags f = fl ? *fl : TcFlags{};
     e = fl ? launch_pdl(k_select_ml_scatter<true>, dim3(grid), dim3(SEL_ML_SEG), 0, st, L, obj_h, obj_w, n_layers, T,
-                        (const int*)chunk_cnt, (const int*)chunk_off, (const uint2*)rec, f)
+                        (const int*)chunk_cnt, (const int*)chunk_off, (const uint2*)rec, (const uint4*)wt, f)
            : launch_pdl(k_select_ml_scatter<false>, dim3(grid), dim3(SEL_ML_SEG), 0, st, L, obj_h, obj_w, n_layers, T,
-                        (const int*)chunk_cnt, (const int*)chunk_off, (const uint2*)rec, f);
+                        (const int*)chunk_cnt, (const int*)chunk_off, (const uint2*)rec, (const uint4*)wt, f);
   }
   return e != cudaSuccess ? e : cudaGetLastError();
 }
@@ -1228,11 +1224,11 @@ cudaError_t launch_select_tasks(int obj_h, int obj_w, int n_layers, const uint8_
     if (e == cudaSuccess && flags_done) *flags_done = fl != nullptr;
     return e != cudaSuccess ? e : cudaGetLastError();
   }
-  if (sal && coop && coop->ml_rec && select_ml_applies(obj_h, obj_w, T)) {
+  if (sal && coop && coop->ml_rec && coop->ml_wt && select_ml_applies(obj_h, obj_w, T)) {
     // the four lists of a large object: one read of the inputs for all levels, then the
     // blocks' records
     const cudaError_t e = launch_select_ml(obj_h, obj_w, n_layers, sal, L, T, chunk_cnt, chunk_off, coop->ml_rec,
-                                           st, fl);
+                                           coop->ml_wt, st, fl);
     if (e == cudaSuccess && flags_done) *flags_done = fl != nullptr;
     return e;
   }
