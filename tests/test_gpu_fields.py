@@ -260,6 +260,18 @@ def test_phase_optimisation_decreases_and_resumes_bit_identically(torch_cuda, tm
     err = float((e.phase.detach() - a.phase.detach()).abs().max())
     print(f"graph-captured optimiser: max phase difference after 6 steps {err:.2e}")
     assert err <= 1e-4
+    # save after 3 replayed steps, load into a fresh graph optimiser (which captures again
+    # around the loaded state) and finish: the uninterrupted replayed run, bit for bit
+    f = optim.PhaseOptimiser(plan, L, T, W, ph0, lr=0.05, graph=True)
+    for _ in range(3):
+        f.step()
+    torch.save(f.state_dict(), tmp_path / "phase_graph.pt")
+    g2 = optim.PhaseOptimiser(plan, L, T, W, torch.zeros_like(ph0), lr=0.05, graph=True)
+    g2.load_state_dict(torch.load(tmp_path / "phase_graph.pt"))
+    for _ in range(3):
+        g2.step()
+    assert g2.step_count == 6
+    assert torch.equal(g2.phase.detach(), e.phase.detach())
 
 
 @pytest.mark.parametrize("name,make", [
