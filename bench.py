@@ -371,9 +371,9 @@ def run_phase_opt_workload(stream, steps):
     return {"batch": 4, "holo": 1024, "layers": 8, "adam_steps": steps + 1, "adam_steps_timed": steps,
             "ms_per_adam_step": ms, "host_ms_per_adam_step": host_ms, "roofline": roof,
             "adam_steps_per_s": 1e3 / ms, "loss_first": l0, "loss_last": l1,
-            "note": "forward reconstruction + amplitude backward + propagation per hologram, fields recomputed "
-                    "in backward (checkpointing); the whole step (loss, backward, fused Adam) captured in a CUDA "
-                    "graph and replayed"}
+            "note": "forward reconstruction + amplitude backward + propagation of the 4 holograms, each GEMM "
+                    "stage once over the (hologram, layer) pairs; fields recomputed in backward (checkpointing); "
+                    "the whole step (loss, backward, fused Adam) captured in a CUDA graph and replayed"}
 
 
 # ---------------------------------------------------------------------------------------

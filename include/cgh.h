@@ -364,6 +364,21 @@ int cgh_reconstruct(const cgh_plan* plan, const float* holo, float* fields,
                     const uint8_t* layer_idx, float* amplitude, void* stream);
 
 /*
+ * cgh_reconstruct_batch - cgh_reconstruct of n_holo holograms in one pass: both GEMM stages
+ * run once over the (hologram, layer) pairs, which fills the GPU better than n_holo calls.
+ * No counterpart in the paper (the batch of phase-only holograms of the optimisation).
+ *   holos      complex64 [n_holo][holo_h][holo_w]
+ *   fields     complex64 [n_holo][Z][obj_h][obj_w] output, or NULL (plan scratch)
+ *   layer_idx  uint8 [obj_h][obj_w], shared by the holograms (needed when amplitude != NULL)
+ *   amplitude  float [n_holo][obj_h][obj_w] output, or NULL
+ * 1 <= n_holo <= 64.  The plan keeps scratch for the largest batch seen: a call with a larger
+ * batch than before reallocates it and synchronises `stream` (make it outside stream capture).
+ * The results equal n_holo calls of cgh_reconstruct bit for bit.  Errors: as cgh_reconstruct.
+ */
+int cgh_reconstruct_batch(const cgh_plan* plan, const float* holos, int n_holo, float* fields,
+                          const uint8_t* layer_idx, float* amplitude, void* stream);
+
+/*
  * cgh_reconstruct_asm - reconstruction by the inverse angular spectrum method, the one the
  * paper renders its results with (Section 2, last paragraph: "inverse angular spectrum ...
  * using the same parameters of the scene").
@@ -376,7 +391,7 @@ int cgh_reconstruct(const cgh_plan* plan, const float* holo, float* fields,
  *     R_z(i, j) = p^2/(lambda*z) * IDFT_PxP(X * T_z)(s*i, s*j)   (IDFT normalised by 1/P^2).
  * The carrier exp(j*2*pi*z/lambda) is left out of T_z (the holograms omit it) and the
  * p^2/(lambda*z) factor makes an unbounded point fringe reconstruct to its amplitude.
- * All arithmetic FP32: hand-written shared-memory FFTs (radix 8), the phase of T_z
+ * All arithmetic FP32: hand-written shared-memory FFTs (radix 16), the phase of T_z
  * reduced exactly in 64-bit fixed point.  Square power-of-two hologram, s in {1, 2, 4, 8},
  * P and P/s in [64, 4096].
  *   holo       complex64 [holo_h][holo_w]
@@ -401,6 +416,18 @@ int cgh_reconstruct_asm(const cgh_plan* plan, const float* holo, float* fields, 
  * Same geometry limits and operands as cgh_reconstruct.  Errors: as cgh_reconstruct.
  */
 int cgh_propagate(const cgh_plan* plan, const float* fields, float* holo, int accumulate, void* stream);
+
+/*
+ * cgh_propagate_batch - cgh_propagate of n_holo field stacks: the first GEMM stage runs once
+ * over the (hologram, layer) pairs, the second once per hologram.  No counterpart in the paper.
+ *   fields  complex64 [n_holo][Z][obj_h][obj_w];  holos complex64 [n_holo][holo_h][holo_w]
+ *   accumulate  0: holos = result;  1: holos += result
+ * 1 <= n_holo <= 64; scratch as cgh_reconstruct_batch.  With a plan created with
+ * CGH_PLAN_DETERMINISTIC the results equal n_holo calls of cgh_propagate bit for bit.
+ * Errors: as cgh_reconstruct.
+ */
+int cgh_propagate_batch(const cgh_plan* plan, const float* fields, int n_holo, float* holos, int accumulate,
+                        void* stream);
 
 /*
  * cgh_adjoint - adjoint of the (real-input) progressive operator intensity -> hologram.
@@ -447,6 +474,14 @@ int cgh_progressive_apply(const cgh_plan* plan, const float* object, const int32
  */
 int cgh_amplitude_backward(const cgh_plan* plan, const float* fields, const uint8_t* layer_idx,
                            const float* grad_amp, float* grad_fields, void* stream);
+
+/*
+ * cgh_amplitude_backward_batch - cgh_amplitude_backward of n_holo field stacks (fields and
+ * grad_fields [n_holo][Z][obj_h][obj_w], grad_amp [n_holo][obj_h][obj_w], one layer map).
+ * No counterpart in the paper.  Errors: CGH_ERR_ARG, CGH_ERR_CUDA.
+ */
+int cgh_amplitude_backward_batch(const cgh_plan* plan, const float* fields, int n_holo, const uint8_t* layer_idx,
+                                 const float* grad_amp, float* grad_fields, void* stream);
 
 /*
  * cgh_phase_to_field / cgh_phase_grad - phase-only holograms: field = exp(j*phase) and, for

@@ -61,6 +61,9 @@ SIGNATURES = {
     "cgh_adjoint": (_I, [_P, _P, ctypes.POINTER(_P), _P, _P, _P, _P]),
     "cgh_progressive_apply": (_I, [_P, _P, ctypes.POINTER(_P), _P, _P, _P, _I, _P]),
     "cgh_amplitude_backward": (_I, [_P, _P, _P, _P, _P, _P]),
+    "cgh_reconstruct_batch": (_I, [_P, _P, _I, _P, _P, _P, _P]),
+    "cgh_propagate_batch": (_I, [_P, _P, _I, _P, _I, _P]),
+    "cgh_amplitude_backward_batch": (_I, [_P, _P, _I, _P, _P, _P, _P]),
     "cgh_phase_to_field": (_I, [_P, _P, ctypes.c_longlong, _P]),
     "cgh_phase_grad": (_I, [_P, _P, _P, ctypes.c_longlong, _P]),
     "cgh_ssim": (_I, [_P, _P, _I, _I, _I, _P, _P, _P]),
@@ -345,6 +348,40 @@ class Plan:
         check(lib().cgh_reconstruct_asm(self.handle, _ptr(holo), _ptr(f), _ptr(layer), _ptr(a), int(pad),
                                         1 if band_limit else 0, _stream(stream)))
         return f, a
+
+    def reconstruct_batch(self, holos, layer=None, fields=True, amplitude=True, stream=None):
+        """cgh_reconstruct_batch: holos [n, holo, holo] complex64 -> (fields [n, Z, obj, obj]
+        complex64 or None, amplitude [n, obj, obj] float32 or None)."""
+        import torch
+        n = holos.shape[0]
+        if fields is True:
+            fields = torch.empty((n, self.n_layers, self.obj_h, self.obj_w), dtype=torch.complex64,
+                                 device=self.device)
+        if amplitude is True:
+            amplitude = torch.empty((n, self.obj_h, self.obj_w), dtype=torch.float32, device=self.device)
+        f = fields if fields is not False else None
+        a = amplitude if amplitude is not False else None
+        check(lib().cgh_reconstruct_batch(self.handle, _ptr(holos), int(n), _ptr(f), _ptr(layer), _ptr(a),
+                                          _stream(stream)))
+        return f, a
+
+    def propagate_batch(self, fields, holos=None, accumulate=False, stream=None):
+        """cgh_propagate_batch: fields [n, Z, obj, obj] complex64 -> holos [n, holo, holo]."""
+        import torch
+        n = fields.shape[0]
+        if holos is None:
+            holos = torch.empty((n, self.holo_h, self.holo_w), dtype=torch.complex64, device=self.device)
+        check(lib().cgh_propagate_batch(self.handle, _ptr(fields), int(n), _ptr(holos), 1 if accumulate else 0,
+                                        _stream(stream)))
+        return holos
+
+    def amplitude_backward_batch(self, fields, layer, grad_amp, out=None, stream=None):
+        import torch
+        if out is None:
+            out = torch.empty_like(fields)
+        check(lib().cgh_amplitude_backward_batch(self.handle, _ptr(fields), int(fields.shape[0]), _ptr(layer),
+                                                 _ptr(grad_amp), _ptr(out), _stream(stream)))
+        return out
 
     def propagate(self, fields, holo=None, accumulate=False, stream=None):
         import torch

@@ -368,21 +368,34 @@ int cgh_pointcloud_direct(const cgh_plan* p, const uint8_t* intensity, const flo
   return CGH_OK;
 }
 
-int cgh_reconstruct(const cgh_plan* p, const float* holo, float* fields, const uint8_t* layer_idx,
-                    float* amplitude, void* stream) {
-  if (!p || !holo) return cgh_fail(CGH_ERR_ARG, "cgh_reconstruct: NULL argument");
+int cgh_reconstruct_batch(const cgh_plan* p, const float* holos, int n_holo, float* fields,
+                          const uint8_t* layer_idx, float* amplitude, void* stream) {
+  if (!p || !holos) return cgh_fail(CGH_ERR_ARG, "cgh_reconstruct: NULL argument");
+  if (n_holo < 1) return cgh_fail(CGH_ERR_ARG, "cgh_reconstruct: %d holograms", n_holo);
   if (amplitude && !layer_idx) return cgh_fail(CGH_ERR_ARG, "cgh_reconstruct: amplitude needs layer_idx");
   if (!fields && !amplitude) return cgh_fail(CGH_ERR_ARG, "cgh_reconstruct: nothing to compute");
-  if (((uintptr_t)holo & 7) || ((uintptr_t)fields & 7))
+  if (((uintptr_t)holos & 7) || ((uintptr_t)fields & 7))
     return cgh_fail(CGH_ERR_ARG, "cgh_reconstruct: complex arrays must be 8-byte aligned");
-  return tc_reconstruct(p, (const float2*)holo, (float2*)fields, layer_idx, amplitude, (cudaStream_t)stream);
+  return tc_reconstruct(p, (const float2*)holos, n_holo, (float2*)fields, layer_idx, amplitude,
+                        (cudaStream_t)stream);
+}
+
+int cgh_reconstruct(const cgh_plan* p, const float* holo, float* fields, const uint8_t* layer_idx,
+                    float* amplitude, void* stream) {
+  return cgh_reconstruct_batch(p, holo, 1, fields, layer_idx, amplitude, stream);
+}
+
+int cgh_propagate_batch(const cgh_plan* p, const float* fields, int n_holo, float* holos, int accumulate,
+                        void* stream) {
+  if (!p || !fields || !holos) return cgh_fail(CGH_ERR_ARG, "cgh_propagate: NULL argument");
+  if (n_holo < 1) return cgh_fail(CGH_ERR_ARG, "cgh_propagate: %d holograms", n_holo);
+  if (((uintptr_t)holos & 7) || ((uintptr_t)fields & 7))
+    return cgh_fail(CGH_ERR_ARG, "cgh_propagate: complex arrays must be 8-byte aligned");
+  return field_propagate(p, (const float2*)fields, n_holo, (float2*)holos, accumulate, (cudaStream_t)stream);
 }
 
 int cgh_propagate(const cgh_plan* p, const float* fields, float* holo, int accumulate, void* stream) {
-  if (!p || !fields || !holo) return cgh_fail(CGH_ERR_ARG, "cgh_propagate: NULL argument");
-  if (((uintptr_t)holo & 7) || ((uintptr_t)fields & 7))
-    return cgh_fail(CGH_ERR_ARG, "cgh_propagate: complex arrays must be 8-byte aligned");
-  return field_propagate(p, (const float2*)fields, (float2*)holo, accumulate, (cudaStream_t)stream);
+  return cgh_propagate_batch(p, fields, 1, holo, accumulate, stream);
 }
 
 int cgh_adjoint(const cgh_plan* p, const float* grad_holo, const int32_t* const* lists, const int32_t* d_counts,
@@ -405,12 +418,18 @@ int cgh_progressive_apply(const cgh_plan* p, const float* object, const int32_t*
   return field_forward(p, object, lists, d_counts, layer_idx, (float2*)holo, accumulate, (cudaStream_t)stream);
 }
 
-int cgh_amplitude_backward(const cgh_plan* p, const float* fields, const uint8_t* layer_idx, const float* grad_amp,
-                           float* grad_fields, void* stream) {
+int cgh_amplitude_backward_batch(const cgh_plan* p, const float* fields, int n_holo, const uint8_t* layer_idx,
+                                 const float* grad_amp, float* grad_fields, void* stream) {
   if (!p || !fields || !layer_idx || !grad_amp || !grad_fields)
     return cgh_fail(CGH_ERR_ARG, "cgh_amplitude_backward: NULL argument");
-  return field_amplitude_backward(p, (const float2*)fields, layer_idx, grad_amp, (float2*)grad_fields,
+  if (n_holo < 1) return cgh_fail(CGH_ERR_ARG, "cgh_amplitude_backward: %d holograms", n_holo);
+  return field_amplitude_backward(p, (const float2*)fields, n_holo, layer_idx, grad_amp, (float2*)grad_fields,
                                   (cudaStream_t)stream);
+}
+
+int cgh_amplitude_backward(const cgh_plan* p, const float* fields, const uint8_t* layer_idx, const float* grad_amp,
+                           float* grad_fields, void* stream) {
+  return cgh_amplitude_backward_batch(p, fields, 1, layer_idx, grad_amp, grad_fields, stream);
 }
 
 int cgh_profile(cgh_plan* p, int enable) {

@@ -205,7 +205,7 @@ int select_scan_blocks(int n_layers, int nchunks);
 // Separable tensor-core path (kernels_tc.cu).
 int tc_progressive(const cgh_plan* p, const int32_t* coef, const int32_t* const* lists,
                    const int32_t* d_counts, float2* holo, int accumulate, int form, cudaStream_t st);
-int tc_reconstruct(const cgh_plan* p, const float2* holo, float2* fields, const uint8_t* L,
+int tc_reconstruct(const cgh_plan* p, const float2* holo, int n, float2* fields, const uint8_t* L,
                    float* amp, cudaStream_t st);
 void tc_destroy(cgh_plan* p);
 int tc_layer_dims(const cgh_plan* p, int* kr, int* kc, cudaStream_t st);
@@ -218,13 +218,13 @@ int tc_build_flags(const cgh_plan* p, const int32_t* const* lists, const int32_t
 
 // Fields: reconstruction, propagation, adjoints (kernels_field.cu).
 int field_init_attributes();
-int field_propagate(const cgh_plan* p, const float2* fields, float2* holo, int accumulate, cudaStream_t st);
+int field_propagate(const cgh_plan* p, const float2* fields, int n, float2* holo, int accumulate, cudaStream_t st);
 int field_forward(const cgh_plan* p, const float* obj, const int32_t* const* lists, const int32_t* d_counts,
                   const uint8_t* L, float2* holo, int accumulate, cudaStream_t st);
 int field_adjoint(const cgh_plan* p, const float2* grad_holo, const int32_t* const* lists,
                   const int32_t* d_counts, const uint8_t* L, float* grad_obj, cudaStream_t st);
-int field_amplitude_backward(const cgh_plan* p, const float2* fields, const uint8_t* L, const float* grad_amp,
-                             float2* grad_fields, cudaStream_t st);
+int field_amplitude_backward(const cgh_plan* p, const float2* fields, int n, const uint8_t* L,
+                             const float* grad_amp, float2* grad_fields, cudaStream_t st);
 void field_destroy(cgh_plan* p);
 struct CUtensorMap_st;
 int eops_get(const cgh_plan* p, int f16, const struct CUtensorMap_st** mEZ, const struct CUtensorMap_st** mEZt,

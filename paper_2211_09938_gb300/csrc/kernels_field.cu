@@ -345,14 +345,21 @@ int eops_get_hi(const cgh_plan* p, int f16, const CUtensorMap** mEZh, const CUte
   return CGH_OK;
 }
 
+// Reconstruction and propagation scratch for batches of up to `cap` holograms: the data
+// planes stack the holograms (Ht rows b*Nh + n, T and Fp rows (b*Z + z)*No + i, Yp columns
+// (b*Z + z)*No + i), so that one launch per GEMM stage covers the batch (units (b, z) decoded
+// by the stacked-problem fields of mode 3); the propagation's last stage runs per hologram on
+// a view of Yp (mYpb[b]).
+#define FIELD_MAX_BATCH 64
 struct cgh_field_state {
-  int No, Nh, Z;
+  int No, Nh, Z, cap;
   uint16_t* GZ;                // conj(E_z) by rows i (built once)
-  uint16_t *Ht, *T, *Fp, *Yp;  // data planes
-  float2* F;                   // fields scratch [Z][No][No]
+  uint16_t *Ht, *T, *Fp, *Yp;  // data planes, for `cap` holograms
+  float2* F;                   // fields scratch [cap][Z][No][No]
   long long gz_plane, ht_plane, t_plane, fp_plane, yp_plane;
   CUtensorMap mGZ, mHt, mT, mFp, mYp;
-  const CUtensorMap *mEZ, *mEZt;  // bf16 geometry operands (cgh_eops)
+  CUtensorMap mYpb[FIELD_MAX_BATCH];  // hologram b's columns of Yp
+  const CUtensorMap *mEZ, *mEZt;      // bf16 geometry operands (cgh_eops)
   int built;
 };
 
@@ -365,22 +372,51 @@ int field_init_attributes() {
   return CGH_OK;
 }
 
-void field_destroy(cgh_plan* p) {
-  cgh_field_state* f = p->fs;
-  if (!f) return;
-  cudaFree(f->GZ);
+static void field_free_data(cgh_field_state* f) {
   cudaFree(f->Ht);
   cudaFree(f->T);
   cudaFree(f->Fp);
   cudaFree(f->Yp);
   cudaFree(f->F);
+  f->Ht = f->T = f->Fp = f->Yp = nullptr;
+  f->F = nullptr;
+  f->cap = 0;
+}
+
+void field_destroy(cgh_plan* p) {
+  cgh_field_state* f = p->fs;
+  if (!f) return;
+  cudaFree(f->GZ);
+  field_free_data(f);
   free(f);
   p->fs = nullptr;
 }
 
-static int field_ensure(const cgh_plan* pc, cudaStream_t st) {
+// A 4-plane hi+lo map over a column range of a wider row-major array: rows x cols from
+// `base`, ld elements between rows, plane_stride elements between planes.
+static int make_plane_view(CUtensorMap* map, const void* base, long long rows, long long cols, long long ld,
+                           long long plane_stride) {
+  if (get_encoder() != CGH_OK) return CGH_ERR_CUDA;
+  if (((uintptr_t)base & 15) || (ld * 2) % 16 || (cols * 2) % 16)
+    return cgh_fail(CGH_ERR_ARG, "tensor map: base must be 16-byte aligned and rows a multiple of 16 bytes");
+  cuuint64_t dims[3] = {(cuuint64_t)cols, (cuuint64_t)rows, 4};
+  cuuint64_t strides[2] = {(cuuint64_t)(ld * 2), (cuuint64_t)(plane_stride * 2)};
+  cuuint32_t box[3] = {TC_BK, 128, 4};
+  cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_UINT16, 3, const_cast<void*>(base), dims, strides, box, estr,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return cgh_fail(CGH_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+  return CGH_OK;
+}
+
+// The plan's field state with room for n holograms: the geometry operand once, the data planes
+// (re)allocated when n exceeds the capacity (outside stream capture: the first call with the
+// largest batch must run eagerly).
+static int field_ensure(const cgh_plan* pc, cudaStream_t st, int n = 1) {
   cgh_plan* p = const_cast<cgh_plan*>(pc);
-  if (p->fs && p->fs->built) return CGH_OK;
+  if (n < 1 || n > FIELD_MAX_BATCH) return cgh_fail(CGH_ERR_ARG, "fields: batch %d not in [1, %d]", n, FIELD_MAX_BATCH);
+  if (p->fs && p->fs->built && p->fs->cap >= n) return CGH_OK;
   if (p->obj_h != p->obj_w || p->holo_h != p->holo_w)
     return cgh_fail(CGH_ERR_UNSUPPORTED, "fields: square object and hologram required");
   const int No = p->obj_h, Nh = p->holo_h, Z = p->n_layers;
@@ -390,40 +426,50 @@ static int field_ensure(const cgh_plan* pc, cudaStream_t st) {
   cgh_field_state* f = p->fs ? p->fs : (cgh_field_state*)calloc(1, sizeof(cgh_field_state));
   if (!f) return cgh_fail(CGH_ERR_NOMEM, "fields: host allocation");
   p->fs = f;
-  f->No = No;
-  f->Nh = Nh;
-  f->Z = Z;
-  f->mEZ = &p->eops->mEZ[0];
-  f->mEZt = &p->eops->mEZt[0];
-  f->gz_plane = (long long)Z * No * Nh;
-  f->ht_plane = (long long)Nh * Nh;
-  f->t_plane = (long long)Z * No * Nh;
-  f->fp_plane = (long long)Z * No * No;
-  f->yp_plane = (long long)Nh * Z * No;
 #define FS_TRY(expr, what)                     \
   do {                                         \
     rc = cgh_cuda_check((expr), (what));       \
     if (rc != CGH_OK) goto fail;               \
   } while (0)
-  FS_TRY(cudaMalloc(&f->GZ, 4 * f->gz_plane * 2), "fields: GZ");
-  FS_TRY(cudaMalloc(&f->Ht, 4 * f->ht_plane * 2), "fields: Ht");
-  FS_TRY(cudaMalloc(&f->T, 4 * f->t_plane * 2), "fields: T");
-  FS_TRY(cudaMalloc(&f->Fp, 4 * f->fp_plane * 2), "fields: Fp");
-  FS_TRY(cudaMalloc(&f->Yp, 4 * f->yp_plane * 2), "fields: Yp");
-  FS_TRY(cudaMalloc(&f->F, (size_t)Z * No * No * sizeof(float2)), "fields: F");
-#undef FS_TRY
-  if ((rc = make_plane_map(&f->mGZ, f->GZ, 4, (long long)Z * No, Nh)) != CGH_OK) goto fail;
-  if ((rc = make_plane_map(&f->mHt, f->Ht, 4, Nh, Nh)) != CGH_OK) goto fail;
-  if ((rc = make_plane_map(&f->mT, f->T, 4, (long long)Z * No, Nh)) != CGH_OK) goto fail;
-  if ((rc = make_plane_map(&f->mFp, f->Fp, 4, (long long)Z * No, No)) != CGH_OK) goto fail;
-  if ((rc = make_plane_map(&f->mYp, f->Yp, 4, Nh, (long long)Z * No)) != CGH_OK) goto fail;
-  {
+  if (!f->GZ) {
+    f->No = No;
+    f->Nh = Nh;
+    f->Z = Z;
+    f->mEZ = &p->eops->mEZ[0];
+    f->mEZt = &p->eops->mEZt[0];
+    f->gz_plane = (long long)Z * No * Nh;
+    FS_TRY(cudaMalloc(&f->GZ, 4 * f->gz_plane * 2), "fields: GZ");
+    if ((rc = make_plane_map(&f->mGZ, f->GZ, 4, (long long)Z * No, Nh)) != CGH_OK) goto fail;
     dim3 blk(8, 32);
     k_fe_build<0, false><<<dim3((Nh / 8 + 7) / 8, (Z * No + 31) / 32), blk, 0, st>>>(
         p->d_tab, p->tab_len, p->tab_off, p->s, No, Z * No, Nh, f->GZ, f->gz_plane);
-    rc = cgh_cuda_check(cudaGetLastError(), "fields: operand build");
-    if (rc != CGH_OK) goto fail;
+    FS_TRY(cudaGetLastError(), "fields: operand build");
   }
+  if (f->cap < n) {
+    // the kernels of a previous call may still read the old planes
+    FS_TRY(cudaStreamSynchronize(st), "fields: grow");
+    field_free_data(f);
+    const long long c = n;
+    f->ht_plane = c * Nh * Nh;
+    f->t_plane = c * Z * No * Nh;
+    f->fp_plane = c * Z * No * No;
+    f->yp_plane = (long long)Nh * c * Z * No;
+    FS_TRY(cudaMalloc(&f->Ht, 4 * f->ht_plane * 2), "fields: Ht");
+    FS_TRY(cudaMalloc(&f->T, 4 * f->t_plane * 2), "fields: T");
+    FS_TRY(cudaMalloc(&f->Fp, 4 * f->fp_plane * 2), "fields: Fp");
+    FS_TRY(cudaMalloc(&f->Yp, 4 * f->yp_plane * 2), "fields: Yp");
+    FS_TRY(cudaMalloc(&f->F, (size_t)c * Z * No * No * sizeof(float2)), "fields: F");
+    if ((rc = make_plane_map(&f->mHt, f->Ht, 4, c * Nh, Nh)) != CGH_OK) goto fail;
+    if ((rc = make_plane_map(&f->mT, f->T, 4, c * Z * No, Nh)) != CGH_OK) goto fail;
+    if ((rc = make_plane_map(&f->mFp, f->Fp, 4, c * Z * No, No)) != CGH_OK) goto fail;
+    if ((rc = make_plane_map(&f->mYp, f->Yp, 4, Nh, c * Z * No)) != CGH_OK) goto fail;
+    for (int b = 0; b < n; ++b)
+      if ((rc = make_plane_view(&f->mYpb[b], f->Yp + (size_t)b * Z * No, Nh, (long long)Z * No, c * Z * No,
+                                f->yp_plane)) != CGH_OK)
+        goto fail;
+    f->cap = n;
+  }
+#undef FS_TRY
   f->built = 1;
   return CGH_OK;
 fail:
@@ -431,12 +477,14 @@ fail:
   return rc;
 }
 
-// R_z = E_z^H H conj(E_z) for every layer into f->F (or `fields` when given).
-static int field_reconstruct_into(const cgh_plan* p, const float2* holo, float2* fields, cudaStream_t st) {
+// R_{b,z} = E_z^H H_b conj(E_z) for n holograms (holo [n][Nh][Nh]) and every layer, into
+// fields [n][Z][No][No].  One launch per GEMM stage over the (hologram, layer) units.
+static int field_reconstruct_into(const cgh_plan* p, const float2* holo, int n, float2* fields, cudaStream_t st) {
   cgh_field_state* f = p->fs;
   const int No = f->No, Nh = f->Nh, Z = f->Z;
-  k_split_transpose<<<dim3((Nh + 31) / 32, (Nh + 31) / 32), dim3(32, 8), 0, st>>>(holo, Nh, Nh, f->Ht,
-                                                                                 f->ht_plane, 1.0f);
+  for (int b = 0; b < n; ++b)
+    k_split_transpose<<<dim3((Nh + 31) / 32, (Nh + 31) / 32), dim3(32, 8), 0, st>>>(
+        holo + (size_t)b * Nh * Nh, Nh, Nh, f->Ht + (size_t)b * Nh * Nh, f->ht_plane, 1.0f);
   int rc = cgh_cuda_check(cudaGetLastError(), "reconstruct: transpose");
   if (rc != CGH_OK) return rc;
   TcGemmArgs a;
@@ -445,9 +493,11 @@ static int field_reconstruct_into(const cgh_plan* p, const float2* holo, float2*
   a.n_layers = Z;
   a.status = p->d_status;
   a.scale = 1.0f;
-  // R1: T_z[i][n] = sum_m conj(E_z[m][i]) H[m][n]
+  // R1: T_{b,z}[i][n] = sum_m conj(E_z[m][i]) H_b[m][n]; unit zz = b Z + z
   a.a_rows_per_z = No;
-  a.b_rows_per_z = 0;
+  a.a_zmod = Z;
+  a.b_rows_per_z = Nh;
+  a.b_zdiv = Z;
   a.out_rows_per_z = No;
   a.out_cols_per_z = 0;
   a.M = No;
@@ -456,12 +506,15 @@ static int field_reconstruct_into(const cgh_plan* p, const float2* holo, float2*
   a.Y = f->T;
   a.y_plane = f->t_plane;
   a.ldy = Nh;
-  a.y_rows = Z * No;
+  a.y_rows = f->cap * Z * No;  // the store map's extent
   rc = cgh_cuda_check(launch_gemm<KIND_CC, EPI_Y, false>(f->mGZ, f->mHt, f->mT, a,
-                                                         dim3((No + 127) / 128, (Nh + 127) / 128, Z), st),
+                                                         dim3((No + 127) / 128, (Nh + 127) / 128, n * Z), st),
                       "reconstruct: R1");
   if (rc != CGH_OK) return rc;
-  // R2: R_z[i][j] = sum_n T_z[i][n] conj(E_z[n][j])
+  // R2: R_{b,z}[i][j] = sum_n T_{b,z}[i][n] conj(E_z[n][j])
+  a.a_zmod = 0;
+  a.b_zdiv = 0;
+  a.b_zmod = Z;
   a.b_rows_per_z = No;
   a.M = No;
   a.N = No;
@@ -470,18 +523,21 @@ static int field_reconstruct_into(const cgh_plan* p, const float2* holo, float2*
   a.ldf = No;
   a.h_vec4 = ((No & 1) == 0) && (((uintptr_t)fields & 15) == 0);
   return cgh_cuda_check(launch_gemm<KIND_CC, EPI_F, false>(f->mT, f->mGZ, f->mGZ, a,
-                                                           dim3((No + 127) / 128, (No + 127) / 128, Z), st),
+                                                           dim3((No + 127) / 128, (No + 127) / 128, n * Z), st),
                         "reconstruct: R2");
 }
 
-int field_propagate(const cgh_plan* p, const float2* fields, float2* holo, int accumulate, cudaStream_t st) {
-  int rc = field_ensure(p, st);
+// H_b (+)= sum_z E_z F_{b,z} E_z^T for n field stacks (fields [n][Z][No][No]) into holo
+// [n][Nh][Nh]: the first stage over the (hologram, layer) units in one launch, the second per
+// hologram (a split-K GEMM over its layers' stacked rows).
+int field_propagate(const cgh_plan* p, const float2* fields, int n, float2* holo, int accumulate, cudaStream_t st) {
+  int rc = field_ensure(p, st, n);
   if (rc != CGH_OK) return rc;
   cgh_field_state* f = p->fs;
   const int No = f->No, Nh = f->Nh, Z = f->Z;
   prof_mark(p, CGH_PROF_PROPAGATE, 0, st);
-  k_split_rows<<<dim3((No / 8 + 7) / 8, (Z * No + 31) / 32), dim3(8, 32), 0, st>>>(fields, (long long)Z * No, No,
-                                                                                  f->Fp, f->fp_plane);
+  k_split_rows<<<dim3((No / 8 + 7) / 8, (n * Z * No + 31) / 32), dim3(8, 32), 0, st>>>(
+      fields, (long long)n * Z * No, No, f->Fp, f->fp_plane);
   rc = cgh_cuda_check(cudaGetLastError(), "propagate: split");
   if (rc != CGH_OK) return rc;
   TcGemmArgs a;
@@ -490,8 +546,9 @@ int field_propagate(const cgh_plan* p, const float2* fields, float2* holo, int a
   a.n_layers = Z;
   a.status = p->d_status;
   a.scale = 1.0f;
-  // P1: Y^T[n][z*No + i] = sum_j E_z[n][j] F_z[i][j]
+  // P1: Y^T[n][(b Z + z) No + i] = sum_j E_z[n][j] F_{b,z}[i][j]
   a.a_rows_per_z = Nh;
+  a.a_zmod = Z;
   a.b_rows_per_z = No;
   a.out_rows_per_z = 0;
   a.out_cols_per_z = No;
@@ -500,29 +557,13 @@ int field_propagate(const cgh_plan* p, const float2* fields, float2* holo, int a
   a.K = No;
   a.Y = f->Yp;
   a.y_plane = f->yp_plane;
-  a.ldy = Z * No;
+  a.ldy = f->cap * Z * No;
   a.y_rows = Nh;
   rc = cgh_cuda_check(launch_gemm<KIND_CC, EPI_Y, false>(*f->mEZt, f->mFp, f->mYp, a,
-                                                         dim3((Nh + 127) / 128, (No + 127) / 128, Z), st),
+                                                         dim3((Nh + 127) / 128, (No + 127) / 128, n * Z), st),
                       "propagate: P1");
   if (rc != CGH_OK) return rc;
-  if (!accumulate) {
-    rc = cgh_cuda_check(cudaMemsetAsync(holo, 0, (size_t)Nh * Nh * sizeof(float2), st), "propagate: clear");
-    if (rc != CGH_OK) return rc;
-  }
-  // P2: H[m][n] += sum_kappa E[m][kappa] Y^T[n][kappa], kappa = z*No + i
-  TcGemmArgs b;
-  memset(&b, 0, sizeof(b));
-  b.mode = 2;
-  b.n_layers = Z;
-  b.K = Z * No;
-  b.M = Nh;
-  b.N = Nh;
-  b.scale = 1.0f;
-  b.H = holo;
-  b.ldh = Nh;
-  b.h_vec4 = ((Nh & 1) == 0) && (((uintptr_t)holo & 15) == 0);
-  b.status = p->d_status;
+  // P2: H_b[m][n] += sum_kappa E[m][kappa] Y^T[n][b Z No + kappa], kappa = z No + i
   const int tm = (Nh + 127) / 128;
   int S = 1;
   if (!p->deterministic) {
@@ -537,35 +578,57 @@ int field_propagate(const cgh_plan* p, const float2* fields, float2* holo, int a
       if (eff > best + 1e-9) best = eff, S = q;
     }
   }
-  rc = cgh_cuda_check(launch_gemm<KIND_CC, EPI_H, false>(*f->mEZ, f->mYp, f->mYp, b, dim3(tm, tm, S), st),
-                      "propagate: P2");
+  for (int bh = 0; bh < n; ++bh) {
+    float2* H = holo + (size_t)bh * Nh * Nh;
+    if (!accumulate) {
+      rc = cgh_cuda_check(cudaMemsetAsync(H, 0, (size_t)Nh * Nh * sizeof(float2), st), "propagate: clear");
+      if (rc != CGH_OK) return rc;
+    }
+    TcGemmArgs c;
+    memset(&c, 0, sizeof(c));
+    c.mode = 2;
+    c.n_layers = Z;
+    c.K = Z * No;
+    c.M = Nh;
+    c.N = Nh;
+    c.scale = 1.0f;
+    c.H = H;
+    c.ldh = Nh;
+    c.h_vec4 = ((Nh & 1) == 0) && (((uintptr_t)H & 15) == 0);
+    c.status = p->d_status;
+    rc = cgh_cuda_check(launch_gemm<KIND_CC, EPI_H, false>(*f->mEZ, f->mYpb[bh], f->mYpb[bh], c, dim3(tm, tm, S), st),
+                        "propagate: P2");
+    if (rc != CGH_OK) return rc;
+  }
   prof_mark(p, CGH_PROF_PROPAGATE, 1, st);
-  return rc;
+  return CGH_OK;
 }
 
-int tc_reconstruct(const cgh_plan* p, const float2* holo, float2* fields, const uint8_t* L, float* amp,
+int tc_reconstruct(const cgh_plan* p, const float2* holo, int n, float2* fields, const uint8_t* L, float* amp,
                    cudaStream_t st) {
-  int rc = field_ensure(p, st);
+  int rc = field_ensure(p, st, n);
   if (rc != CGH_OK) return rc;
   cgh_field_state* f = p->fs;
   float2* out = fields ? fields : f->F;
   prof_mark(p, CGH_PROF_RECON, 0, st);
-  rc = field_reconstruct_into(p, holo, out, st);
+  rc = field_reconstruct_into(p, holo, n, out, st);
   if (rc != CGH_OK) return rc;
   if (amp) {
-    const int n = f->No * f->No;
-    k_amplitude<<<(n + 255) / 256, 256, 0, st>>>(out, L, n, f->Z, amp);
+    const int np = f->No * f->No;
+    for (int b = 0; b < n; ++b)
+      k_amplitude<<<(np + 255) / 256, 256, 0, st>>>(out + (size_t)b * f->Z * np, L, np, f->Z, amp + (size_t)b * np);
     rc = cgh_cuda_check(cudaGetLastError(), "reconstruct: amplitude");
   }
   prof_mark(p, CGH_PROF_RECON, 1, st);
   return rc;
 }
 
-int field_amplitude_backward(const cgh_plan* p, const float2* fields, const uint8_t* L, const float* grad_amp,
+int field_amplitude_backward(const cgh_plan* p, const float2* fields, int n, const uint8_t* L, const float* grad_amp,
                              float2* grad_fields, cudaStream_t st) {
-  const int n = p->obj_h * p->obj_w;
-  k_amplitude_backward<<<dim3((n + 255) / 256, p->n_layers), 256, 0, st>>>(fields, L, n, p->n_layers, grad_amp,
-                                                                          grad_fields);
+  const int np = p->obj_h * p->obj_w, Z = p->n_layers;
+  for (int b = 0; b < n; ++b)
+    k_amplitude_backward<<<dim3((np + 255) / 256, Z), 256, 0, st>>>(
+        fields + (size_t)b * Z * np, L, np, Z, grad_amp + (size_t)b * np, grad_fields + (size_t)b * Z * np);
   return cgh_cuda_check(cudaGetLastError(), "amplitude backward");
 }
 
@@ -577,7 +640,7 @@ int field_adjoint(const cgh_plan* p, const float2* grad_holo, const int32_t* con
   TcFlags fl;
   rc = tc_build_flags(p, lists, d_counts, &fl, st);
   if (rc != CGH_OK) return rc;
-  rc = field_reconstruct_into(p, grad_holo, f->F, st);
+  rc = field_reconstruct_into(p, grad_holo, 1, f->F, st);
   if (rc != CGH_OK) return rc;
   rc = cgh_cuda_check(cudaMemsetAsync(grad_obj, 0, (size_t)f->No * f->No * sizeof(float), st), "adjoint: clear");
   if (rc != CGH_OK) return rc;
@@ -598,7 +661,7 @@ int field_forward(const cgh_plan* p, const float* obj, const int32_t* const* lis
   k_forward_project<<<grid, blk, 0, st>>>(obj, L, fl, f->No, f->No, f->Z, f->F);
   rc = cgh_cuda_check(cudaGetLastError(), "progressive apply: projection");
   if (rc != CGH_OK) return rc;
-  return field_propagate(p, f->F, holo, accumulate, st);
+  return field_propagate(p, f->F, 1, holo, accumulate, st);
 }
 
 extern "C" int cgh_phase_to_field(const float* phase, float* field, long long n, void* stream) {

@@ -149,6 +149,8 @@ struct TcGemmArgs {
   int a_rows_per_z;  // modes 1, 3: row offset of A per layer
   int b_rows_per_z;  // mode 3: row offset of B per layer
   int out_rows_per_z, out_cols_per_z;  // mode 3: output offsets per layer
+  int a_zmod, b_zdiv, b_zmod;  // mode 3, stacked problems: A's layer is zz % a_zmod and B's
+                               // (zz / b_zdiv) % b_zmod (0: zz itself), zz the unit's layer
   const int* kr_pad; // [Z] padded compacted row counts
   const int* kc_pad; // [Z] padded compacted column counts
   int n_layers;
@@ -361,8 +363,11 @@ __device__ __forceinline__ bool decode_tile(const TcGemmArgs& a, int t, const in
   ti.col_lim = a.N;
   ti.akm = nullptr;
   if (a.mode == 3) {
-    ti.a_row = zz * a.a_rows_per_z + mt * TC_BM;
-    ti.b_row = zz * a.b_rows_per_z + nt * TC_BN;
+    const int za = a.a_zmod ? zz % a.a_zmod : zz;
+    int zb = a.b_zdiv ? zz / a.b_zdiv : zz;
+    if (a.b_zmod) zb %= a.b_zmod;
+    ti.a_row = za * a.a_rows_per_z + mt * TC_BM;
+    ti.b_row = zb * a.b_rows_per_z + nt * TC_BN;
     ti.k_lo = 0;
     ti.nk = a.K / TC_BK;
     ti.out_row0 = zz * a.out_rows_per_z + mt * TC_BM;

@@ -51,6 +51,45 @@ def reconstruct_amplitude(phase, plan, layer, checkpoint=True):
     return PhaseReconstruction.apply(phase, plan, layer, checkpoint)
 
 
+class PhaseReconstructionBatch(torch.autograd.Function):
+    """phase [B, holo, holo] float32  ->  composite amplitudes [B, obj, obj] float32, as
+    PhaseReconstruction per hologram, with each GEMM stage run once over the batch
+    (cgh_reconstruct_batch; backward by cgh_amplitude_backward_batch and
+    cgh_propagate_batch).  The same numbers as B single reconstructions."""
+
+    @staticmethod
+    def forward(ctx, phase, plan, layer, checkpoint=True):
+        phase = phase.contiguous()
+        H = phase_to_field(phase)
+        F, amp = plan.reconstruct_batch(H, layer)
+        ctx.plan = plan
+        ctx.layer = layer
+        ctx.checkpoint = bool(checkpoint)
+        if ctx.checkpoint:
+            ctx.save_for_backward(phase)
+        else:
+            ctx.save_for_backward(phase, H, F)
+        return amp
+
+    @staticmethod
+    def backward(ctx, g_amp):
+        plan = ctx.plan
+        if ctx.checkpoint:
+            (phase,) = ctx.saved_tensors
+            H = phase_to_field(phase)
+            F, _ = plan.reconstruct_batch(H, ctx.layer, amplitude=False)
+        else:
+            phase, H, F = ctx.saved_tensors
+        gF = plan.amplitude_backward_batch(F, ctx.layer, g_amp.contiguous().float())
+        gH = plan.propagate_batch(gF)
+        return phase_grad(H, gH), None, None, None
+
+
+def reconstruct_amplitudes(phase, plan, layer, checkpoint=True):
+    """Composite amplitudes of a batch of phase-only holograms [B, holo, holo]."""
+    return PhaseReconstructionBatch.apply(phase, plan, layer, checkpoint)
+
+
 class ProgressiveOperator(torch.autograd.Function):
     """object [obj, obj] float32  ->  progressive hologram [holo, holo] complex64:
     H = sum_z E_z P_z(object [layer = z]) E_z^T (Eq. 3, Section 2 steps 2-5, for a real
@@ -113,27 +152,32 @@ class PhaseOptimiser:
         self.step_count = 0
         nb = self.phase.shape[0]
         # the loss's constants in float64, cast once
-        self._t64 = [targets[b].double() for b in range(nb)]
+        self._t64 = torch.stack([targets[b] for b in range(nb)]).double()
         self._w64 = weights.double()
-        # concurrent: the holograms of the batch run on their own streams, each with its own
-        # plan (plan scratch is per plan), so that their GEMMs and small kernels overlap on the
-        # GPU; autograd runs every hologram's backward on the stream of its forward.  Measured
-        # at batch 4, 1024^2, 8 layers: 2.96 ms per Adam step against 2.66 ms in order (the
-        # four plans' operands compete for L2), so it is off by default.
+        # By default the batch goes through each GEMM stage at once (PhaseReconstructionBatch).
+        # concurrent: the holograms run one by one on their own streams instead, each with its
+        # own plan (plan scratch is per plan), so that their GEMMs and small kernels overlap on
+        # the GPU; autograd runs every hologram's backward on the stream of its forward.
+        # Measured at batch 4, 1024^2, 8 layers: 2.96 ms per Adam step against 2.66 ms one by
+        # one in order (the four plans' operands compete for L2), so it is off by default.
         self.plans = [plan] + ([plan.clone() for _ in range(nb - 1)] if concurrent else [plan] * (nb - 1))
         self.streams = [torch.cuda.Stream() for _ in range(nb)] if concurrent else None
         with torch.no_grad():
             self.kappa = [fit_kappa(reconstruct_amplitude(self.phase[b], plan, layer, False), targets[b])
                           for b in range(nb)]
+        self._set_kappa()
+
+    def _set_kappa(self):
+        # the scales as a device tensor [B, 1, 1], made outside any capture
+        self._k64 = torch.tensor(self.kappa, dtype=torch.float64, device=self.phase.device).view(-1, 1, 1)
 
     def loss(self):
         nb = self.phase.shape[0]
         if self.streams is None:
-            total = 0.0
-            for b in range(nb):
-                amp = reconstruct_amplitude(self.phase[b], self.plans[b], self.layer, self.checkpoint)
-                total = total + weighted_loss(amp, self._t64[b], self._w64, self.kappa[b])
-            return total
+            # the whole batch through each GEMM stage at once
+            amps = reconstruct_amplitudes(self.phase, self.plan, self.layer, self.checkpoint)
+            d = amps.double() / self._k64 - self._t64
+            return (self._w64 * d * d).sum()
         cur = torch.cuda.current_stream()
         parts = []
         for b in range(nb):
@@ -202,4 +246,5 @@ class PhaseOptimiser:
         self.opt.load_state_dict(st["adam"])
         self.step_count = int(st["step"])
         self.kappa = list(st["kappa"])
+        self._set_kappa()
         self.graph = None  # the captured step holds the old state tensors: capture again

@@ -138,6 +138,36 @@ def test_amplitude_backward_and_phase_kernels(torch_cuda):
     assert np.allclose(gp, np.imag(g * np.conj(H)), atol=1e-5)
 
 
+@pytest.mark.parametrize("n,holo,nl", [(64, 128, 4), (512, 1024, 8)])
+def test_batched_reconstruction_and_propagation_equal_single_calls(torch_cuda, n, holo, nl):
+    """cgh_reconstruct_batch / cgh_propagate_batch / cgh_amplitude_backward_batch run each
+    GEMM stage once over the (hologram, layer) pairs: on a deterministic plan the results
+    equal one call per hologram bit for bit, through batch sizes that grow the plan's scratch
+    and one that fits it."""
+    torch = torch_cuda
+    from paper_2211_09938_gb300 import Plan
+    sc = scenes.random_scene(77 + n, n, holo, nl)
+    plan = Plan.for_scene(sc, flags=Plan.DETERMINISTIC)
+    L = torch.from_numpy(sc["layer"]).cuda()
+    rng = np.random.default_rng(n)
+    for nb in (3, 2, 5):
+        H = torch.from_numpy(cplx(rng, nb, holo, holo).astype(np.complex64)).cuda()
+        F, A = plan.reconstruct_batch(H, L)
+        g = torch.from_numpy(rng.standard_normal((nb, n, n)).astype(np.float32)).cuda()
+        gF = plan.amplitude_backward_batch(F, L, g)
+        Hp = plan.propagate_batch(gF)
+        torch.cuda.synchronize()
+        for b in range(nb):
+            f1, a1 = plan.reconstruct(H[b], L)
+            gf1 = plan.amplitude_backward(f1, L, g[b])
+            h1 = plan.propagate(gf1)
+            torch.cuda.synchronize()
+            assert torch.equal(F[b], f1) and torch.equal(A[b], a1), (nb, b)
+            assert torch.equal(gF[b], gf1), (nb, b)
+            assert torch.equal(Hp[b], h1), (nb, b)
+    plan.close()
+
+
 def _opt_case(torch, n=64, holo=128, nl=4, seed=15, flags=0):
     from paper_2211_09938_gb300 import Plan
     sc = scenes.random_scene(seed, n, holo, nl)
