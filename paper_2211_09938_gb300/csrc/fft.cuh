@@ -183,7 +183,7 @@ __device__ __forceinline__ void fft_tile(float2* s, const float2* __restrict__ t
   static_assert(NP >= 2 && NP <= 3, "L in [64, 4096]");
   static_assert(L <= LMAX, "L too large");
 
-  // pass 0 (radix 8, NS = 1): global -> registers -> shared
+  // pass 0 (NS = 1): global -> registers -> shared
   {
     constexpr int R = pass_radix(L, 0), G = L / R, NG = B * G / T;
     static_assert((B * G) % T == 0, "tile does not divide among the threads");
