@@ -608,6 +608,10 @@ static int tc_run(const cgh_plan* p, const int32_t* coef, const int32_t* const* 
       return CGH_OK;
     }
   }
+  // both stages' A operands are the plan's fringe planes and their K sizes and maps come from
+  // the compaction, two or more kernels back: their first A loads may start early
+  a1.a_early = 1;
+  a2.a_early = 1;
   prof_mark(p, CGH_PROF_TC_STAGE1, 0, st);
   e = launch_gemm<K1, EPI_Y, F16>(*mEZt, t->mB1, t->mY, a1, tiles1, st);
   prof_mark(p, CGH_PROF_TC_STAGE1, 1, st);

@@ -177,6 +177,9 @@ struct TcGemmArgs {
   int* status;
   float4* zero_ptr[2];    // single-problem launches: regions the epilogue warps clear before their
   long long zero_n[2];    // first tile (float4 counts; for the next kernels or the next call)
+  int a_early;            // single-problem launches: no grid of the last two wrote A or the K
+                          // sizes and maps, so the first A loads may start before the wait
+                          // for the previous grid
 };
 
 template <int KIND>
@@ -348,7 +351,7 @@ __device__ __forceinline__ bool decode_stage1(const TcGemmArgs& a, int mt, int n
   ti.a_row = zz * a.a_rows_per_z + mt * TC_BM;
   ti.b_row = s_off[zz] + nt * TC_BN;
   ti.k_lo = 0;
-  ti.nk = a.kc_pad[zz] / TC_BK;
+  ti.nk = __ldcg(a.kc_pad + zz) / TC_BK;
   ti.out_col0 = s_off[zz] + nt * TC_BN;
   ti.col_lim = ti.out_col0 + ti.n_valid;
   if (a.a_kmap) ti.akm = a.a_kmap + (size_t)zz * a.a_kmap_ld;
@@ -398,6 +401,35 @@ __device__ __forceinline__ bool decode_tile(const TcGemmArgs& a, int t, const in
   return ti.nk > 0;
 }
 
+// Barriers of an NST-deep ring, the two accumulator buffers and the drain, and (ALLOC) the
+// 512 tensor-memory columns, then a CTA barrier.  Touches nothing another grid writes.
+template <int NST, bool ALLOC>
+__device__ __forceinline__ void tc_gemm_setup(uint64_t* full_bar, uint64_t* empty_bar, uint64_t* tfull_bar,
+                                              uint64_t* tempty_bar, uint64_t* done_bar, uint32_t* s_tmem_p,
+                                              volatile int* s_abort_p) {
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < NST; ++s) {
+      mbar_init(&full_bar[s], 1);
+      mbar_init(&empty_bar[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&tfull_bar[b], 1);
+      mbar_init(&tempty_bar[b], 4);
+    }
+    mbar_init(done_bar, 1);
+    *s_abort_p = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (ALLOC && (threadIdx.x >> 5) == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(smem_u32(s_tmem_p))
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+}
+
 // Persistent warp-specialised GEMM.  Warp 0 (one lane) streams operand tiles with TMA
 // through an NST-deep shared-memory ring; warp 1 owns the tensor memory (512 columns:
 // two accumulator buffers of Re | Im) and one lane issues the MMAs; warps 2-5 drain a
@@ -405,11 +437,16 @@ __device__ __forceinline__ bool decode_tile(const TcGemmArgs& a, int t, const in
 // other buffer.
 // TMEM: ALLOC allocates the 512 columns at the start (else *s_tmem_p holds an allocation
 // made earlier in the kernel), DEALLOC frees them at the end (else they stay allocated for
-// a later body in the same kernel).  Hooks of the source: before_load(ti, kt) runs in the
+// a later body in the same kernel).  SETUP: the body initialises its barriers, allocates and
+// then waits for the previous grid; else the kernel has done the first two (tc_gemm_setup)
+// and, with EARLY, every role waits for the previous grid itself: the producer first issues
+// the A loads of its first ring stages when src.a_early() (A and the K maps come from grids
+// two or more back), and the epilogue warps clear src's regions (src.zero_idle) after the wait.  Hooks of the source: before_load(ti, kt) runs in the
 // producer before the loads of K step kt (it may wait, bounded, for inputs that other CTAs
 // produce; false aborts), before_epilogue() before a tile's output is written (false
 // aborts), tile_stored(ti) after a tile's EPI_Y stores are complete and visible.
-template <int KIND, int EPI, bool F16, class Src, bool ALLOC = true, bool DEALLOC = true>
+template <int KIND, int EPI, bool F16, class Src, bool ALLOC = true, bool DEALLOC = true, bool SETUP = true,
+          bool EARLY = false>
 __device__ __forceinline__ void tc_gemm_body(const Src& src, uint8_t* smem, uint64_t* full_bar, uint64_t* empty_bar,
                                              uint64_t* tfull_bar, uint64_t* tempty_bar, uint64_t* done_bar,
                                              uint32_t* s_tmem_p, volatile int* s_abort_p) {
@@ -422,32 +459,22 @@ __device__ __forceinline__ void tc_gemm_body(const Src& src, uint8_t* smem, uint
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   int* const status = src.status();
 
-  if (threadIdx.x == 0) {
-    for (int s = 0; s < NST; ++s) {
-      mbar_init(&full_bar[s], 1);
-      mbar_init(&empty_bar[s], 1);
-    }
-    for (int b = 0; b < 2; ++b) {
-      mbar_init(&tfull_bar[b], 1);
-      mbar_init(&tempty_bar[b], 4);
-    }
-    mbar_init(done_bar, 1);
-    s_abort = 0;
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  if constexpr (SETUP) {
+    tc_gemm_setup<NST, ALLOC>(full_bar, empty_bar, tfull_bar, tempty_bar, done_bar, s_tmem_p, s_abort_p);
+    pdl_wait();  // barriers and tensor memory are set up; operands may now be read
   }
-  if (ALLOC && warp == 1) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(smem_u32(s_tmem_p))
-                 : "memory");
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-  }
-  tc_fence_before();
-  __syncthreads();
-  tc_fence_after();
-  pdl_wait();  // barriers and tensor memory are set up; operands may now be read
   const uint32_t tmem = *s_tmem_p;
   const uint32_t smem_base = smem_u32(smem);
 
+  if (EARLY && warp != 0) {
+    pdl_wait();
+    pdl_trigger();
+  }
   if (warp == 0) {
+    if (EARLY && lane != 0) {
+      pdl_wait();
+      pdl_trigger();
+    }
     if (lane == 0) {
       // ---- TMA producer
       int it = 0;
@@ -456,6 +483,26 @@ __device__ __forceinline__ void tc_gemm_body(const Src& src, uint8_t* smem, uint
       for (int s = 0; s < NST; ++s) issued[s] = false, issued_ph[s] = 0;
       bool ok = true;
       TileInfo ti;
+      // EARLY: the A halves of the first tile's first ring stages (fresh barriers: no wait
+      // for a free slot) go out before the wait for the previous grid
+      int npre = 0;
+      if constexpr (EARLY) {
+        if (src.a_early()) {
+          int c0 = src.begin();
+          if (src.next(c0, ti)) {
+            const CUtensorMap* mA = src.mapA(ti);
+            npre = min(NST, ti.nk);
+            for (int kt = 0; kt < npre; ++kt) {
+              mbar_arrive_expect_tx(&full_bar[kt], STAGE);
+              tma_load_3d(smem + kt * STAGE, mA, &full_bar[kt], ti.akm ? __ldcg(ti.akm + kt) : ti.k_lo + kt * TC_BK,
+                          ti.a_row, 0);
+              issued[kt] = true;
+            }
+          }
+        }
+        pdl_wait();
+        pdl_trigger();
+      }
       for (int cur = src.begin(); ok && src.next(cur, ti);) {
         const CUtensorMap* mA = src.mapA(ti);
         const CUtensorMap* mB = src.mapB(ti);
@@ -463,13 +510,17 @@ __device__ __forceinline__ void tc_gemm_body(const Src& src, uint8_t* smem, uint
         for (int kt = 0; kt < ti.nk; ++kt, ++it) {
           const int s = it % NST;
           const uint32_t ph = (uint32_t)(it / NST) & 1u;
-          if (!mbar_wait_bounded(&empty_bar[s], ph ^ 1u, &s_abort, status) || !src.before_load(ti, kt, &s_abort)) {
+          const bool pre = it < npre;  // A already in flight, barrier armed
+          if ((!pre && !mbar_wait_bounded(&empty_bar[s], ph ^ 1u, &s_abort, status)) ||
+              !src.before_load(ti, kt, &s_abort)) {
             ok = false;
             break;
           }
           uint8_t* st = smem + s * STAGE;
-          mbar_arrive_expect_tx(&full_bar[s], STAGE);
-          tma_load_3d(st, mA, &full_bar[s], ti.akm ? ti.akm[kt] : ti.k_lo + kt * TC_BK, ti.a_row, 0);
+          if (!pre) {
+            mbar_arrive_expect_tx(&full_bar[s], STAGE);
+            tma_load_3d(st, mA, &full_bar[s], ti.akm ? ti.akm[kt] : ti.k_lo + kt * TC_BK, ti.a_row, 0);
+          }
           tma_load_3d(st + NA * TC_PLANE_BYTES, mB, &full_bar[s], ti.k_lo + kt * TC_BK, ti.b_row, 0);
           issued[s] = true;
           issued_ph[s] = ph;
@@ -526,6 +577,7 @@ __device__ __forceinline__ void tc_gemm_body(const Src& src, uint8_t* smem, uint
     __syncwarp();
   } else {
     // ---- epilogue warps 2..5: TMEM lane quarter (warp % 4) -> 32 output rows
+    if constexpr (EARLY) src.zero_idle(threadIdx.x - 64);
     const int quarter = warp & 3;
     int local = 0, chunk = 0;
     bool prev_committed = false;  // (issuing thread) the previous chunk committed a store
@@ -755,6 +807,14 @@ struct TcSingleSrc {
   __device__ bool before_epilogue(volatile int*) const { return true; }
   __device__ bool publishes() const { return false; }
   __device__ void tile_stored(const TileInfo&) const {}
+  __device__ bool a_early() const { return a->a_early != 0; }
+  // the epilogue warps, idle until the first tile has accumulated, clear the regions asked for
+  __device__ void zero_idle(int e) const {
+    const long long t0 = (long long)blockIdx.x * 128 + e, nt = (long long)gridDim.x * 128;
+#pragma unroll 1
+    for (int r = 0; r < 2; ++r)
+      for (long long i = t0; i < a->zero_n[r]; i += nt) a->zero_ptr[r][i] = make_float4(0.f, 0.f, 0.f, 0.f);
+  }
 };
 
 template <int KIND, int EPI, bool F16>
@@ -771,10 +831,13 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm(const __grid_constant__ CUte
   __shared__ int s_off[CGH_MAX_LAYERS + 1];
   __shared__ int s_toff[CGH_MAX_LAYERS + 1];
   __shared__ int s_kr[CGH_MAX_LAYERS];
-  pdl_wait();
-  // the per-layer sizes, loaded in parallel (a serial loop of global loads in thread 0
-  // would cost a memory latency per layer before any role starts)
-  if (args.kr_pad && threadIdx.x < args.n_layers) s_kr[threadIdx.x] = args.kr_pad[threadIdx.x];
+  // barriers, tensor memory and the per-layer sizes (written by the compaction, two or more
+  // grids back) before the wait for the previous grid: a CTA that starts while the previous
+  // grid's last CTAs run does all of this, and issues its first A loads, in the meantime.  The
+  // sizes are loaded in parallel (a serial loop of global loads in thread 0 would cost a
+  // memory latency per layer before any role starts).
+  tc_gemm_setup<NST, true>(full_bar, empty_bar, tfull_bar, tempty_bar, &done_bar, &s_tmem, &s_abort);
+  if (args.kr_pad && threadIdx.x < args.n_layers) s_kr[threadIdx.x] = __ldcg(args.kr_pad + threadIdx.x);
   __syncthreads();
   if (threadIdx.x == 0) {
     int o = 0, u = 0;
@@ -787,17 +850,11 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm(const __grid_constant__ CUte
         s_toff[q + 1] = (u += args.tm * ((kr + TC_BN - 1) / TC_BN));
       }
   }
-  if (threadIdx.x >= 64) {  // the epilogue warps are idle until the first tile has accumulated
-    const long long t0 = (long long)blockIdx.x * 128 + (threadIdx.x - 64), nt = (long long)gridDim.x * 128;
-#pragma unroll 1
-    for (int r = 0; r < 2; ++r)
-      for (long long i = t0; i < args.zero_n[r]; i += nt) args.zero_ptr[r][i] = make_float4(0.f, 0.f, 0.f, 0.f);
-  }
   __syncthreads();
   TcSingleSrc src{&mapA, &mapB, &mapC, &args, s_off,
                   args.mode == 2 ? (args.kr_pad ? s_off[args.n_layers] : args.K) : 0, s_toff};
-  tc_gemm_body<KIND, EPI, F16>(src, smem, full_bar, empty_bar, tfull_bar, tempty_bar, &done_bar, &s_tmem,
-                               &s_abort);
+  tc_gemm_body<KIND, EPI, F16, TcSingleSrc, true, true, false, true>(src, smem, full_bar, empty_bar, tfull_bar,
+                                                                     tempty_bar, &done_bar, &s_tmem, &s_abort);
 }
 
 // One problem of a batch, in global memory: its tensor maps, arguments, first work unit
