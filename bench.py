@@ -824,12 +824,15 @@ def run_ours(args):
         stage1_flop = 3 * 4.0 * HOLO * sum(a_ * b_ for a_, b_ in zip(kr, kc))
         algo_flop = stage2_flop + (stage1_flop if fused else 0.0)
         peak_tf = pk.get("bf16_tflops", 1900.0)
+        pairs = not fused and plan.stage2_tiles_used() == Plan.TILES_PAIR
         roof = {"bound": "tensor",
                 "kernel": "k_tc_fused (both GEMM stages, one cooperative launch)" if fused
-                else "k_tc_gemm<KIND_CC,EPI_H> (stage 2, one CTA per 128x128 tile)",
+                else ("k_tc_gemm_pair<KIND_CC> (stage 2, a CTA pair per 256x128 tile)" if pairs
+                      else "k_tc_gemm<KIND_CC,EPI_H> (stage 2, one CTA per 128x128 tile)"),
                 "achieved": algo_flop / (k_ms / 1e3) / 1e12, "peak": peak_tf, "unit": "TFLOP/s",
                 "frac": algo_flop / (k_ms / 1e3) / 1e12 / peak_tf,
-                "traffic": kernel_traffic(("k_tc_fused" if fused else "k_tc_gemm stage 2") + f" ({form})"),
+                "traffic": kernel_traffic(("k_tc_fused" if fused else "k_tc_gemm_pair stage 2" if pairs
+                                           else "k_tc_gemm stage 2") + f" ({form})"),
                 "traffic_note": "ncu dram__bytes_read.sum + dram__bytes_write.sum per launch, from "
                                 "profiles/traffic.json (the ncu summary it names); null if the kernel changed "
                                 "since the counters were taken",

@@ -125,7 +125,7 @@ int cgh_plan_set_tuning(cgh_plan* plan, int max_ksteps_per_chain);
  * cgh_plan_set_stage2_tiles - tile shape of the separable form's stage-2 GEMM.
  *   CGH_TILES_AUTO  (default) CTA pairs when the call splits K stream-K style (not with
  *                   CGH_PLAN_DETERMINISTIC), the device holds CTA pairs and the hologram
- *                   has at least as many 128 x 128 tiles as the device has SMs
+ *                   has at least 64 tiles of 128 x 128 (1024 x 1024 and larger)
  *   CGH_TILES_CTA   one CTA per 128 x 128 output tile
  *   CGH_TILES_PAIR  two CTAs of a cluster per 256 x 128 output tile (tcgen05 cta_group::2:
  *                   each CTA stages its 128 rows of the fringe operand and half of the data
@@ -138,6 +138,15 @@ int cgh_plan_set_tuning(cgh_plan* plan, int max_ksteps_per_chain);
 #define CGH_TILES_CTA 1
 #define CGH_TILES_PAIR 2
 int cgh_plan_set_stage2_tiles(cgh_plan* plan, int tiles);
+
+/*
+ * cgh_plan_stage2_tiles_used - *tiles = the tile shape the plan's last separable-form call
+ * with two GEMM launches ran stage 2 with: CGH_TILES_CTA or CGH_TILES_PAIR (CGH_TILES_AUTO
+ * before the first such call, and unchanged by fused or batched calls).  Host-side state,
+ * recorded when the launch is enqueued; nothing is synchronised.  CGH_ERR_ARG for a NULL
+ * argument.  The paper has no counterpart (it reports which GPU kernel a call used).
+ */
+int cgh_plan_stage2_tiles_used(const cgh_plan* plan, int* tiles);
 
 /*
  * cgh_plan_set_fusion - 1: the separable form's two GEMM stages run as one cooperative

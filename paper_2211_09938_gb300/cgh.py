@@ -42,6 +42,7 @@ SIGNATURES = {
     "cgh_plan_destroy": (_I, [_P]),
     "cgh_plan_set_tuning": (_I, [_P, _I]),
     "cgh_plan_set_stage2_tiles": (_I, [_P, _I]),
+    "cgh_plan_stage2_tiles_used": (_I, [_P, _P]),
     "cgh_plan_set_fusion": (_I, [_P, _I]),
     "cgh_plan_set_contraction": (_I, [_P, _I]),
     "cgh_build_tables": (_I, [_P, _P]),
@@ -187,6 +188,13 @@ class Plan:
         """cgh_plan_set_stage2_tiles: TILES_AUTO, TILES_CTA (128x128 per CTA) or TILES_PAIR
         (256x128 per CTA pair, tcgen05 cta_group::2)."""
         check(lib().cgh_plan_set_stage2_tiles(self.handle, int(tiles)))
+
+    def stage2_tiles_used(self):
+        """cgh_plan_stage2_tiles_used: TILES_CTA or TILES_PAIR, the tile shape of the last
+        two-launch separable call's stage 2 (TILES_AUTO before any)."""
+        v = ctypes.c_int(0)
+        check(lib().cgh_plan_stage2_tiles_used(self.handle, ctypes.byref(v)))
+        return v.value
 
     def set_fusion(self, fused):
         """cgh_plan_set_fusion: both GEMM stages in one cooperative launch (True) or two

@@ -77,6 +77,12 @@ int cgh_plan_set_stage2_tiles(cgh_plan* p, int tiles) {
   return CGH_OK;
 }
 
+int cgh_plan_stage2_tiles_used(const cgh_plan* p, int* tiles) {
+  if (!p || !tiles) return cgh_fail(CGH_ERR_ARG, "cgh_plan_stage2_tiles_used: bad argument");
+  *tiles = p->stage2_used;
+  return CGH_OK;
+}
+
 int cgh_plan_set_fusion(cgh_plan* p, int fused) {
   if (!p || fused < 0 || fused > 1) return cgh_fail(CGH_ERR_ARG, "cgh_plan_set_fusion: bad argument");
   p->fusion = fused;

@@ -21,6 +21,7 @@ struct cgh_plan {
   int max_ksteps;     // cgh_plan_set_tuning: cap on K steps per stage-2 chain (0 = automatic)
   int contraction;    // cgh_plan_set_contraction: CGH_CONTRACT_AUTO / _ROWS / _COLS
   int stage2_tiles;   // cgh_plan_set_stage2_tiles: CGH_TILES_AUTO / _CTA / _PAIR
+  int stage2_used;    // the tile shape the last two-launch separable call ran stage 2 with
   int fusion;         // cgh_plan_set_fusion(plan, 1): both GEMM stages in one cooperative launch
   double pitch, wavelength;
   double z[CGH_MAX_LAYERS];

@@ -619,12 +619,16 @@ static int tc_run(const cgh_plan* p, const int32_t* coef, const int32_t* const* 
   t->flags_dirty = 0;
   prof_mark(p, CGH_PROF_TC_STAGE2, 0, st);
   e = cudaErrorNotSupported;
-  // CTA pairs when asked, or by default once the hologram has at least as many 128x128 tiles
-  // as the device has SMs (2048^2: 2-3% faster); below that (1024^2) one CTA per tile is as
-  // fast and re-reads less from DRAM (82 against 109 MB per launch at paper scale)
-  const bool pairs = p->stage2_tiles == CGH_TILES_PAIR ||
-                     (p->stage2_tiles == CGH_TILES_AUTO && tm * tn >= tc_num_sms());
-  if (streamk > 0 && pairs) e = launch_gemm_pair<K2, F16>(*mEZ, t->mY64, a2, tiles2, st);
+  // CTA pairs when asked, or by default once the hologram has at least 64 128x128 tiles
+  // (1024^2 and larger): with both kernels starting early behind stage 1, pairs take the
+  // paper-scale step from 0.1312 to 0.1292 ms (2048^2: 2-3% faster); smaller holograms keep
+  // one CTA per tile
+  const bool pairs = p->stage2_tiles == CGH_TILES_PAIR || (p->stage2_tiles == CGH_TILES_AUTO && tm * tn >= 64);
+  const_cast<cgh_plan*>(p)->stage2_used = CGH_TILES_CTA;
+  if (streamk > 0 && pairs) {
+    e = launch_gemm_pair<K2, F16>(*mEZ, t->mY64, a2, tiles2, st);
+    if (e == cudaSuccess) const_cast<cgh_plan*>(p)->stage2_used = CGH_TILES_PAIR;
+  }
   if (e == cudaErrorNotSupported) e = launch_gemm<K2, EPI_H, F16>(*mEZ, t->mY, t->mY, a2, tiles2, st);
   prof_mark(p, CGH_PROF_TC_STAGE2, 1, st);
   TC_CK(e, "tc: stage-2 GEMM");

@@ -150,8 +150,12 @@ struct PairSlice {
 
 // The body of stage 2 on CTA pairs over a source of work units (PairSingleSrc: one problem,
 // stream-K; PairBatchSrc: the units of a batch of problems).  Each role iterates its own
-// copy of src.iter(); both CTAs of a pair decode the same sequence.
-template <int KIND, bool F16, class PSrc>
+// copy of src.iter(); both CTAs of a pair decode the same sequence.  EARLY: the kernel has
+// loaded the K sizes before the wait for the previous grid (they come from grids two or more
+// back), the barriers and tensor memory are set up before that wait too, and each producer
+// issues its A halves of the first ring stages (the fringe planes) before it; only the B
+// halves, the stage-1 output, wait.
+template <int KIND, bool F16, class PSrc, bool EARLY = false>
 __device__ __forceinline__ void tc_gemm_pair_body(const PSrc& src) {
   using Cfg = TcCfg<KIND>;
   constexpr int NA = Cfg::NA, NST = pair_nst<KIND>();
@@ -188,11 +192,19 @@ __device__ __forceinline__ void tc_gemm_pair_body(const PSrc& src) {
   __syncthreads();
   cluster_sync_all();  // both CTAs' barriers exist before any remote signal
   tc_fence_after();
-  pdl_wait();  // the K sizes and the stage-1 output come from earlier kernels
+  if constexpr (!EARLY) pdl_wait();  // the K sizes and the stage-1 output come from earlier kernels
   const uint32_t tmem = s_tmem;
   const uint32_t smem_base = smem_u32(smem);
 
+  if (EARLY && warp != 0) {
+    pdl_wait();
+    pdl_trigger();
+  }
   if (warp == 0) {
+    if (EARLY && lane != 0) {
+      pdl_wait();
+      pdl_trigger();
+    }
     if (lane == 0) {
       // ---- TMA producer (both CTAs): own rows of A and B, completing on the even CTA's full[s]
       const uint32_t full0 = mapa_rank(smem_u32(&full_bar[0]), 0);
@@ -202,6 +214,24 @@ __device__ __forceinline__ void tc_gemm_pair_body(const PSrc& src) {
       for (int s = 0; s < NST; ++s) issued[s] = false, issued_ph[s] = 0;
       bool ok = true;
       TileInfo ti;
+      // EARLY: the A halves of the first unit's first ring stages (fresh barriers: no wait for
+      // a free slot) go out before the wait for the previous grid
+      int npre = 0;
+      if constexpr (EARLY) {
+        auto s0 = src.iter();
+        if (src.a_early() && s0.next(rank, ti)) {
+          const CUtensorMap* mA = src.mapA(ti);
+          npre = min(NST, ti.nk);
+          for (int kt = 0; kt < npre; ++kt) {
+            if (rank == 0) mbar_arrive_expect_tx(&full_bar[kt], 2 * STAGE);
+            tma_load_3d_pair(smem + kt * STAGE, mA, full0 + 8u * kt, ti.akm ? __ldcg(ti.akm + kt) : ti.k_lo + kt * TC_BK,
+                             ti.a_row, 0);
+            issued[kt] = true;
+          }
+        }
+        pdl_wait();
+        pdl_trigger();
+      }
       auto sl = src.iter();
       while (ok && sl.next(rank, ti)) {
         const CUtensorMap* mA = src.mapA(ti);
@@ -210,13 +240,16 @@ __device__ __forceinline__ void tc_gemm_pair_body(const PSrc& src) {
         for (int kt = 0; kt < ti.nk; ++kt, ++it) {
           const int s = it % NST;
           const uint32_t ph = (uint32_t)(it / NST) & 1u;
-          if (!mbar_wait_bounded(&empty_bar[s], ph ^ 1u, &s_abort, status)) {
+          const bool pre = it < npre;  // A already in flight, barrier armed
+          if (!pre && !mbar_wait_bounded(&empty_bar[s], ph ^ 1u, &s_abort, status)) {
             ok = false;
             break;
           }
           uint8_t* st = smem + s * STAGE;
-          if (rank == 0) mbar_arrive_expect_tx(&full_bar[s], 2 * STAGE);
-          tma_load_3d_pair(st, mA, full0 + 8u * s, ti.akm ? ti.akm[kt] : ti.k_lo + kt * TC_BK, ti.a_row, 0);
+          if (!pre) {
+            if (rank == 0) mbar_arrive_expect_tx(&full_bar[s], 2 * STAGE);
+            tma_load_3d_pair(st, mA, full0 + 8u * s, ti.akm ? ti.akm[kt] : ti.k_lo + kt * TC_BK, ti.a_row, 0);
+          }
           tma_load_3d_pair(st + NA * TC_PAIR_A_PLANE, mB, full0 + 8u * s, ti.k_lo + kt * TC_BK, ti.b_row, 0);
           issued[s] = true;
           issued_ph[s] = ph;
@@ -356,6 +389,7 @@ struct PairSingleSrc {
   __device__ void acquire_maps(const CUtensorMap*, const CUtensorMap*) const {}
   __device__ const TcGemmArgs& args(const TileInfo&) const { return *a; }
   __device__ int* status() const { return a->status; }
+  __device__ bool a_early() const { return a->a_early != 0; }
 };
 
 template <int KIND, bool F16>
@@ -364,8 +398,9 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm_pair(const __grid_constant__
                                                           const TcGemmArgs args) {
   __shared__ int s_kr[CGH_MAX_LAYERS];
   __shared__ int s_ktot;
-  pdl_wait();
-  if (threadIdx.x < args.n_layers) s_kr[threadIdx.x] = args.kr_pad[threadIdx.x];
+  // the K sizes come from the compaction, two or more grids back: read before the wait for
+  // the previous grid, which the body's roles make themselves
+  if (threadIdx.x < args.n_layers) s_kr[threadIdx.x] = __ldcg(args.kr_pad + threadIdx.x);
   __syncthreads();
   if (threadIdx.x == 0) {
     int o = 0;
@@ -383,7 +418,7 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm_pair(const __grid_constant__
     src.slice.cur = W * pair / npairs;
     src.slice.end = W * (pair + 1) / npairs;
   }
-  tc_gemm_pair_body<KIND, F16>(src);
+  tc_gemm_pair_body<KIND, F16, PairSingleSrc, true>(src);
 }
 
 // The stage-2 units of a batch on CTA pairs: per item (pair tiles along M) x (tiles along

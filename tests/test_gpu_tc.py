@@ -173,6 +173,11 @@ def test_stage2_cta_pairs_match_single_cta_and_oracle(torch_cuda, name, form):
     S = torch.from_numpy(sc["saliency"]).cuda()
     coeffs = plan.haar_decompose(I, L)
     lists, counts = plan.progressive_lists(S, L, scenes.THRESHOLDS_U8)
+    assert plan.stage2_tiles_used() == Plan.TILES_AUTO  # no separable call yet
+    plan.progressive_hologram(coeffs, lists, counts, form=form)
+    # the default: CTA pairs from 64 tiles of 128 x 128 (1024 x 1024 holograms and larger)
+    tiles_default = Plan.TILES_PAIR if -(-sc["holo"][0] // 128) * -(-sc["holo"][1] // 128) >= 64 else Plan.TILES_CTA
+    assert plan.stage2_tiles_used() == tiles_default
     got = {}
     for tiles in (Plan.TILES_CTA, Plan.TILES_PAIR):
         plan.set_stage2_tiles(tiles)
@@ -180,6 +185,7 @@ def test_stage2_cta_pairs_match_single_cta_and_oracle(torch_cuda, name, form):
         H2 = plan.progressive_hologram(coeffs, lists, counts, form=form)  # a second call, same plan
         torch.cuda.synchronize()
         assert plan.status() == 0
+        assert plan.stage2_tiles_used() == tiles  # the shape asked for is the one that ran
         got[tiles] = (H.cpu().numpy(), H2.cpu().numpy())
     ref_lists = O.progressive_lists(sc["saliency"], sc["layer"], plan.n_layers, scenes.THRESHOLDS_U8)
     Href = O.progressive_hologram(sc["intensity"], sc["layer"], ref_lists, O.geometry_of(sc))
