@@ -65,6 +65,10 @@ def test_host_argument_checks_without_gpu(L):
     assert L.cgh_progressive_hologram(None, None, None, None, None, 0, 0, None) == 1
     assert L.cgh_progressive_step(None, None, None, None, None, None, None, None, None, None, 0, 1, None) == 1
     assert b"cgh_progressive_step" in L.cgh_last_error()
+    tiles = ctypes.c_int(-1)
+    assert L.cgh_plan_stage2_tiles_used(None, ctypes.byref(tiles)) == 1
+    assert tiles.value == -1  # nothing written on error
+    assert L.cgh_plan_set_stage2_tiles(None, 0) == 1
     assert L.cgh_plan_destroy(None) == 0
     assert L.cgh_version() >= 10000
 
