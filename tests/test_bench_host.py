@@ -1,5 +1,6 @@
 """Host logic of bench.py (no GPU): the DRAM traffic taken from the committed ncu summary is
-reported only while the kernel's sources still hash to the value recorded with it."""
+reported only while the kernel's sources still hash to the value recorded with it; the
+whole-job value; the clock record taken beside each number (from a fake nvidia-smi)."""
 import json
 import os
 
@@ -66,3 +67,39 @@ def test_committed_traffic_entries_are_well_formed():
 def test_whole_job_value_is_all_ranks_over_the_slowest():
     # 2 ranks, 10 steps of 1e6 units each, slowest rank 5 ms in total: 4e9 units/s = 4 G
     assert abs(bench.whole_job_value(1e6, 10, 2, 5.0) - 4.0) < 1e-12
+
+
+def _fake_smi(tmp_path, lines):
+    exe = tmp_path / "nvidia-smi"
+    exe.write_text("#!/bin/sh\ncat <<'END'\n" + "\n".join(lines) + "\nEND\nexec sleep 30\n")
+    exe.chmod(0o755)
+    return str(tmp_path)
+
+
+def test_clock_sampler_summarises_clocks_and_throttle_reasons(tmp_path, monkeypatch):
+    """The clock record beside a bench number: median SM clock under load, the maximum, and
+    every throttle reason seen in any sample (a fake nvidia-smi prints the samples)."""
+    t = "2026/12/04 10:00:00.000"
+    lines = [f"{t}, 0, 2070, 2070, 800.5, 0x0, Not Active, Not Active, Not Active, Not Active",
+             f"{t}, 0, 2055, 2070, 1390.0, 0x4, Not Active, Not Active, Not Active, Active",
+             f"{t}, 0, 1980, 2070, 1200.0, 0x8, Active, Not Active, Not Active, Not Active",
+             "garbled line",
+             f"{t}, 0, [N/A], 2070, 10.0, 0x0, Not Active, Not Active, Not Active, Not Active"]
+    monkeypatch.setenv("PATH", _fake_smi(tmp_path, lines) + os.pathsep + os.environ["PATH"])
+    s = bench.ClockSampler(0)
+    s.start()
+    import time
+    time.sleep(0.5)
+    s.stop()
+    out = s.summary()
+    assert out["samples"] == 3  # the garbled and the non-numeric samples are skipped
+    assert out["sm_mhz"] == 2055 and out["sm_max_mhz"] == 2070 and out["power_w_max"] == 1390.0
+    assert out["reasons"] == ["hw_slowdown", "sw_power_cap"]
+
+
+def test_clock_sampler_without_nvidia_smi_says_so(tmp_path, monkeypatch):
+    monkeypatch.setenv("PATH", str(tmp_path))  # no nvidia-smi here
+    s = bench.ClockSampler(0)
+    s.start()
+    s.stop()
+    assert s.summary() == {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no nvidia-smi samples"], "samples": 0}
