@@ -1,5 +1,6 @@
 """Host logic of bench.py's multi-GPU (replica) path on CPU: two gloo ranks, each with its
-own step time; both see the maximum, and the whole-job value counts every rank's work."""
+own step time; both see the maximum, and the whole-job value counts every rank's work.  And
+the reference arm launched under torchrun with two ranks."""
 import os
 import socket
 
