@@ -285,7 +285,7 @@ class Plan:
         return holo
 
     def progressive_step(self, saliency, layer, coeffs, thresholds, counts=None, lists=None, holo=None,
-                         accumulate=False, form="tc_bf16x3", coeffs_ready=None, stream=None):
+                         accumulate=False, form="tc_fp16x3", coeffs_ready=None, stream=None):
         """Selection and superposition in one call (cgh_progressive_step): the outputs of
         progressive_lists followed by progressive_hologram.  coeffs_ready: a torch.cuda.Event
         the call waits for after the selection, before it reads coeffs (a DWT on another
@@ -529,7 +529,7 @@ class Batch:
     are bound at creation; run() enqueues every scene's hologram with one persistent
     launch per GEMM stage across all scenes."""
 
-    def __init__(self, plans, intensity, layer, saliency, thresholds, holos, form="tc_bf16x3",
+    def __init__(self, plans, intensity, layer, saliency, thresholds, holos, form="tc_fp16x3",
                  stream=None):
         n = len(plans)
         self.plans = list(plans)

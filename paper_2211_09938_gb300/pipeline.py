@@ -47,7 +47,7 @@ class ProgressivePipeline:
     concurrent: one plan and one set of compute streams per slot, so that the steps of
     consecutive scenes overlap (the extra plans are clones of `plan`)."""
 
-    def __init__(self, plan, thresholds, form="tc_bf16x3", depth=2, graphs=True, concurrent=False):
+    def __init__(self, plan, thresholds, form="tc_fp16x3", depth=2, graphs=True, concurrent=False):
         self.plan = plan
         self.thresholds = dict(thresholds)
         self.form = form

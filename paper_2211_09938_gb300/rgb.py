@@ -20,7 +20,7 @@ class RGBHologram:
     [holo_h, holo_w] CUDA tensors (outputs).  run() enqueues all three holograms."""
 
     def __init__(self, obj_shape, holo_shape, pitch, z, intensity_rgb, layer, saliency, thresholds, holos,
-                 wavelengths=WAVELENGTHS_RGB, form="tc_bf16x3", stream=None, flags=0):
+                 wavelengths=WAVELENGTHS_RGB, form="tc_fp16x3", stream=None, flags=0):
         if len(intensity_rgb) != 3 or len(holos) != 3 or len(wavelengths) != 3:
             raise ValueError("three channels expected")
         self.wavelengths = tuple(float(w) for w in wavelengths)
